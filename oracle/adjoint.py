@@ -1,0 +1,120 @@
+"""FP64 oracle: derivatives of the rendered patch w.r.t. the galaxy parameters
+theta = (flux, x, y, log r_e, e1, e2).
+
+TEST INFRASTRUCTURE (see ``oracle/__init__.py``).
+
+The paper has no gradients; they follow from differentiating its forward
+model.  Every step after the Fourier evaluation is linear, so with
+X = P_hat * M the pixel Jacobian is irfft2(P_hat * dM/dtheta) plus the
+derivative of the real-space sum.  From Eq. onegaussian:
+  dM/dflux = M / flux,  dM/dx = -2 pi i nu M,  dM/dy = -2 pi i omega M,
+  dG_i/dS_ab = -2 pi^2 v_i (dq/dS_ab) G_i with q = S11 nu^2 + 2 S12 nu om + S22 om^2,
+plus the ramp weights' dependence on n_sigma_i = (N/2) / sqrt(v_i trace S).
+The real-space Gaussian N(d; Sigma) has dN/dmu = N Sigma^-1 d and
+dN/dSigma = N (Sigma^-1 d d^T Sigma^-1 - Sigma^-1) / 2.
+S(log r_e, e1, e2) is the CD = I covariance of Appendix A:
+  S11 = r^2 (h + G e1), S12 = -r^2 G e2, S22 = r^2 (h - G e1),
+  h = (1 + beta^2)/2, G = (beta^2 - 1)/(2e), beta = (1 - e)/(1 + e).
+S is not differentiable at e = 0 (beta depends on |e|), so e > 0 is required.
+"""
+
+import numpy as np
+
+from . import render as R
+
+PARAMS = ("flux", "x", "y", "log_re", "e1", "e2")
+
+
+def shape_derivatives(log_re, e1, e2):
+    """dS/d(log r_e), dS/de1, dS/de2 as three 2x2 matrices (CD = I)."""
+    r2 = np.exp(2.0 * log_re)
+    e = np.hypot(e1, e2)
+    if not e > 0:
+        raise ValueError("the covariance is not differentiable at e = 0")
+    beta = (1 - e) / (1 + e)
+    dbeta = -2.0 / (1 + e) ** 2
+    h = 0.5 * (1 + beta * beta)
+    g = (beta * beta - 1) / (2 * e)
+    dh = beta * dbeta
+    dg = beta * dbeta / e - (beta * beta - 1) / (2 * e * e)
+    s = r2 * np.array([[h + g * e1, -g * e2], [-g * e2, h - g * e1]])
+    de1, de2 = e1 / e, e2 / e
+    d1 = r2 * np.array([[dh * de1 + dg * de1 * e1 + g, -dg * de1 * e2],
+                        [-dg * de1 * e2, dh * de1 - dg * de1 * e1 - g]])
+    d2 = r2 * np.array([[dh * de2 + dg * de2 * e1, -(dg * de2 * e2 + g)],
+                        [-(dg * de2 * e2 + g), dh * de2 - dg * de2 * e1]])
+    return [2.0 * s, d1, d2]
+
+
+def jacobian(gal, psf_hat, psf_mog, tables, n=None):
+    """(6, n, n) array: d pixel / d theta for one galaxy."""
+    n = int(gal["size"]) if n is None else int(n)
+    amps, covs, wf, wr, s, v, ns = R.galaxy_components(gal, tables, n)
+    flux = gal["flux"]
+    x0, y0 = 0.5 * n + gal["x"], 0.5 * n + gal["y"]
+    nu, om = R.frequencies(n)
+    NU, OM = nu[None, :], om[:, None]
+    tr = s[0, 0] + s[1, 1]
+    dq = {(0, 0): NU * NU, (0, 1): 2 * NU * OM, (1, 1): OM * OM}
+    slopes = np.array([R.ramp_slope(x) for x in ns])
+    dns = {(0, 0): -0.5 * ns / tr, (0, 1): np.zeros_like(ns), (1, 1): -0.5 * ns / tr}
+
+    # Fourier part: spectra of each derivative.
+    shape = (n, n // 2 + 1)
+    m = np.zeros(shape, complex)
+    dm_s = {ab: np.zeros(shape, complex) for ab in dq}
+    for i, (amp, cov) in enumerate(zip(amps, covs)):
+        gi = R.fourier_gaussian(cov, x0, y0, NU, OM)
+        m += amp * wf[i] * gi
+        for ab in dq:
+            dm_s[ab] += amp * gi * (slopes[i] * dns[ab][i] - wf[i] * 2 * np.pi ** 2 * v[i] * dq[ab])
+    dm = [m / flux, -2j * np.pi * NU * m, -2j * np.pi * OM * m]
+    ds = shape_derivatives(gal["log_re"], gal["e1"], gal["e2"])
+    for d in ds:
+        dm.append(d[0, 0] * dm_s[(0, 0)] + d[0, 1] * dm_s[(0, 1)] + d[1, 1] * dm_s[(1, 1)])
+    jac = np.stack([np.fft.irfft2(psf_hat * d, s=(n, n)) for d in dm])
+
+    # Real-space part.
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
+    rj = np.zeros((6, n, n))
+    for i, (amp, cov) in enumerate(zip(amps, covs)):
+        for w, mx, my, pxx, pxy, pyy in psf_mog:
+            sig = cov + np.array([[pxx, pxy], [pxy, pyy]])
+            nij = w * R.gaussian_2d(sig, x0 + mx, y0 + my, xx, yy)
+            inv = np.linalg.inv(sig)
+            dx, dy = xx - x0 - mx, yy - y0 - my
+            ux = inv[0, 0] * dx + inv[0, 1] * dy
+            uy = inv[1, 0] * dx + inv[1, 1] * dy
+            q = {(0, 0): 0.5 * (ux * ux - inv[0, 0]),
+                 (0, 1): 2 * 0.5 * (ux * uy - inv[0, 1]),
+                 (1, 1): 0.5 * (uy * uy - inv[1, 1])}
+            rj[0] += amp / flux * wr[i] * nij
+            rj[1] += amp * wr[i] * nij * ux
+            rj[2] += amp * wr[i] * nij * uy
+            for k, d in enumerate(ds):
+                acc = 0.0
+                for ab in q:
+                    dsab = d[ab]
+                    acc = acc + dsab * (-slopes[i] * dns[ab][i] + wr[i] * v[i] * q[ab])
+                rj[3 + k] += amp * nij * acc
+    return jac + rj
+
+
+def vjp(gal, psf_hat, psf_mog, tables, grad_pix, n=None):
+    """sum_p grad_pix[p] * d pixel[p] / d theta: the six gradients."""
+    return np.tensordot(jacobian(gal, psf_hat, psf_mog, tables, n), grad_pix, axes=([1, 2], [0, 1]))
+
+
+def finite_difference(gal, psf_hat, psf_mog, tables, step=1e-6, n=None):
+    """Central finite differences of the forward model: absolute step for
+    x, y, log r_e, e1, e2 and relative step (step * flux) for flux."""
+    out = []
+    for p in PARAMS:
+        h = step * gal["flux"] if p == "flux" else step
+        gp, gm = dict(gal), dict(gal)
+        gp[p] = gal[p] + h
+        gm[p] = gal[p] - h
+        ip = R.render(gp, None, psf_mog, tables, n=n, psf_hat=psf_hat)
+        im = R.render(gm, None, psf_mog, tables, n=n, psf_hat=psf_hat)
+        out.append((ip - im) / (2 * h))
+    return np.stack(out)

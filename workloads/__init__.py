@@ -1,0 +1,20 @@
+"""Seeded synthetic inputs shared by the CUDA path, its tests and the oracle.
+
+This package only draws random numbers and builds input arrays: galaxy
+parameters, pixelized PSF images, a Gaussian-mixture fit to each PSF (the
+input of the real-space path) and the committed Gaussian-mixture profile
+tables.  It holds none of the rendering arithmetic (the ellipse covariance,
+the aliasing split, the Fourier evaluation, the inverse FFT or the real-space
+convolution), so both sides can take their inputs from here without sharing
+any of the method.
+"""
+
+from .galaxies import (  # noqa: F401
+    PROFILE_EXP, PROFILE_DEV, PROFILE_SERSIC, SIZE_BUCKETS,
+    config0_galaxy, config1_galaxies, config2_galaxies, config3_problem,
+    serving_requests, bucket_size, Galaxies,
+)
+from .psf import (  # noqa: F401
+    gaussian_mixture_psf, config0_psf, config2_psfs, fit_psf_mog, PsfInput,
+)
+from .tables import load_profile_tables, ProfileTable  # noqa: F401
