@@ -1,0 +1,148 @@
+/*
+ * mogconv — hybrid Fourier / real-space Gaussian-mixture galaxy x PSF
+ * rendering on one GB300 (sm_103a).
+ *
+ * The method (Lang 2020, "A hybrid Fourier--Real Gaussian Mixture method for
+ * fast galaxy--PSF convolution", Section 2, Steps 1-8): a galaxy profile
+ * approximated by a mixture of Gaussians is transformed analytically to
+ * Fourier space (Eq. onegaussian), evaluated on the FFT grid of a pixelized
+ * PSF, multiplied by the PSF's FFT and the sub-pixel shift phase, and brought
+ * back to pixels by an inverse real FFT.  Mixture components too wide for the
+ * patch (Step 4) are instead convolved analytically with a Gaussian-mixture
+ * fit of the PSF and evaluated at the pixel centres, then added.
+ *
+ * Conventions shared by every entry point:
+ *  - A patch is N x N float32, row-major, row = y, column = x, pixel centres at
+ *    integer coordinates.  N is one of 32, 64, 128.
+ *  - The galaxy centre is (N/2 + x, N/2 + y) where (x, y) is its offset.
+ *  - Shapes: r_e = exp(log_re) pixels; e1, e2 ellipticity (Eqs. 2-5) with the
+ *    WCS matrix CD = identity (pixel units); the pixel covariance of a
+ *    component of profile variance v is v S with S from Appendix A.
+ *  - Aliasing split (Step 4): n_sigma = (N/2) / sqrt(trace(v S)); a component
+ *    is Fourier only for n_sigma >= 4, real only for n_sigma <= 3, and both in
+ *    between with weights w_F = 3t^2 - 2t^3 (t = n_sigma - 3), w_R = 1 - w_F.
+ *  - The inverse transform is the real inverse DFT of the half spectrum
+ *    nu = k/N (k = 0..N/2) by omega = l/N in FFT order, with the self-conjugate
+ *    bins contributing their real part (the numpy.fft.irfft2 convention).
+ *
+ * Memory: every pointer documented "device" must point to device memory of
+ * the context's device (e.g. from PyTorch); the library borrows it for the
+ * call.  The library owns only what it allocates itself: profile tables, PSF
+ * spectra and mixtures, a status word and its batch-planning scratch.
+ *
+ * Asynchrony and errors: render calls are asynchronous on the given CUDA
+ * stream (a cudaStream_t passed as void*; NULL = legacy default stream).
+ * Argument errors are returned synchronously.  Errors found on the device
+ * (non-finite parameters, a bounded wait that ran out, an unknown profile or
+ * PSF id) are recorded in a device status word that mog_sync_status() reads
+ * and clears; the affected patches are left unwritten.
+ */
+#ifndef MOGCONV_H
+#define MOGCONV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mog_ctx mog_ctx;
+typedef int mog_status;
+
+enum {
+  MOG_OK = 0,
+  MOG_ERR_ARG = -1,      /* invalid argument (synchronous) */
+  MOG_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+  MOG_ERR_NOMEM = -3,    /* allocation failed */
+  MOG_ERR_STATE = -4,    /* missing table / PSF / context state */
+  MOG_ERR_TIMEOUT = -5,  /* a bounded device wait ran out */
+  MOG_ERR_DEVICE = -6    /* a device-side parameter check failed */
+};
+
+enum { MOG_MAX_COMPONENTS = 12, MOG_MAX_PSF_COMPONENTS = 4, MOG_MAX_PSFS = 1024,
+       MOG_MAX_PROFILES = 8, MOG_MAX_NODES = 64 };
+
+/*
+ * A batch of G galaxies, structure of arrays, all device pointers of length
+ * `count`:
+ *   flux      total flux (the mixture amplitudes sum to 1)
+ *   x, y      offset of the centre from the patch centre (N/2, N/2), pixels
+ *   log_re    natural log of the effective radius in pixels
+ *   e1, e2    ellipticity components (Section 2, Step 3, Eqs. 2-5)
+ *   sersic_n  Sersic index where the profile table depends on n (Section 3)
+ *   profile   profile-table id (mog_set_profile_table)
+ *   psf       PSF id (mog_create_psf)
+ *   size      patch side N of this galaxy (32, 64 or 128)
+ *   offset    element offset of this galaxy's N*N patch in the output array
+ * Patches must not overlap.  The batch struct itself is host memory.
+ */
+typedef struct mog_batch {
+  int64_t count;
+  const float* flux;
+  const float* x;
+  const float* y;
+  const float* log_re;
+  const float* e1;
+  const float* e2;
+  const float* sersic_n;
+  const int32_t* profile;
+  const int32_t* psf;
+  const int32_t* size;
+  const int64_t* offset;
+} mog_batch;
+
+/* Creates a context on CUDA device `device` (makes it current).  *out gets
+ * the handle; destroy it with mog_destroy_context. */
+mog_status mog_create_context(mog_ctx** out, int device);
+mog_status mog_destroy_context(mog_ctx* ctx);
+
+/* Text of the last error recorded on this context (never NULL). */
+const char* mog_last_error(const mog_ctx* ctx);
+
+/*
+ * Installs a Gaussian-mixture profile table (Section 1 footnote: a mixture
+ * sum_i a_i N(0, v_i I), sum a_i = 1, in units of r_e).  Host arrays:
+ *   nodes[n_nodes]         Sersic index of each node (ascending, uniform
+ *                           spacing when n_nodes > 1)
+ *   amp[n_nodes * 12]      a_i per node, MOG_MAX_COMPONENTS slots, 0 = unused
+ *   var[n_nodes * 12]      v_i per node (> 0 in every slot)
+ * Between nodes a_i and log v_i are interpolated linearly in n (Section 3);
+ * n is clamped to the node range.  Replaces any table with that id.
+ * Synchronous (copies to device memory).
+ */
+mog_status mog_set_profile_table(mog_ctx* ctx, int profile_id, int n_nodes, const float* nodes,
+                                 const float* amp, const float* var);
+
+/*
+ * Registers a pixelized PSF (Section 2, Steps 1-2).  Host arrays:
+ *   pixels[h * w]   row-major, centre at pixel (h/2, w/2) (integer division)
+ *   mog[k * 6]      its Gaussian-mixture fit for real-space components, rows
+ *                   (weight, mean_x, mean_y, var_xx, var_xy, var_yy), means
+ *                   relative to the centre pixel; 1 <= k <= 4
+ * For every supported N the PSF is embedded with its centre at (N/2, N/2)
+ * (zero padded, or cropped without renormalisation) and its real 2-D FFT is
+ * computed on the device and kept resident until mog_destroy_psf.
+ * *psf_id receives the id (0 .. MOG_MAX_PSFS-1).  Synchronous.
+ */
+mog_status mog_create_psf(mog_ctx* ctx, const float* pixels, int h, int w, const float* mog, int k,
+                          int* psf_id);
+mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id);
+
+/*
+ * Renders every galaxy of the batch (Section 2, Steps 3-8) into `out`
+ * (device float32; galaxy g writes size[g]^2 values at out + offset[g]).
+ * Asynchronous on `stream`.
+ */
+mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
+
+/*
+ * Reads the device status word after synchronising `stream` and resets it.
+ * Returns MOG_OK or the first device error recorded since the last call.
+ */
+mog_status mog_sync_status(mog_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOGCONV_H */

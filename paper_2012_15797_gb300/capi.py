@@ -1,0 +1,146 @@
+"""ctypes binding of the C-ABI declared in include/mogconv.h.
+
+Argument marshalling only: every function here forwards to the entry point of
+the same name in lib/libmogconv.so and raises ``MogError`` on a non-zero
+status.  Device pointers are passed as integers (e.g. ``tensor.data_ptr()``),
+streams as the integer handle of a ``torch.cuda.Stream`` (``.cuda_stream``).
+The library must have been built (``paper_2012_15797_gb300.build.build()``);
+importing this module without it raises.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+MOG_OK = 0
+MOG_ERR_ARG = -1
+MOG_ERR_CUDA = -2
+MOG_ERR_NOMEM = -3
+MOG_ERR_STATE = -4
+MOG_ERR_TIMEOUT = -5
+MOG_ERR_DEVICE = -6
+MOG_MAX_COMPONENTS = 12
+MOG_MAX_PSF_COMPONENTS = 4
+MOG_MAX_PSFS = 1024
+MOG_MAX_PROFILES = 8
+MOG_MAX_NODES = 64
+
+EXPORTED = (
+    "mog_create_context", "mog_destroy_context", "mog_last_error", "mog_set_profile_table",
+    "mog_create_psf", "mog_destroy_psf", "mog_render_batch", "mog_sync_status",
+)
+
+
+class MogError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"mogconv error {status}: {msg}")
+        self.status = status
+
+
+class mog_batch(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int64),
+        ("flux", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+        ("log_re", ctypes.c_void_p), ("e1", ctypes.c_void_p), ("e2", ctypes.c_void_p),
+        ("sersic_n", ctypes.c_void_p), ("profile", ctypes.c_void_p), ("psf", ctypes.c_void_p),
+        ("size", ctypes.c_void_p), ("offset", ctypes.c_void_p),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB):
+        raise ImportError(f"CUDA library not built: {LIB} is missing (run paper_2012_15797_gb300.build.build())")
+    lib = ctypes.CDLL(LIB)
+    P, I, VP = ctypes.POINTER, ctypes.c_int, ctypes.c_void_p
+    FP = P(ctypes.c_float)
+    sig = {
+        "mog_create_context": ([P(VP), I], I),
+        "mog_destroy_context": ([VP], I),
+        "mog_last_error": ([VP], ctypes.c_char_p),
+        "mog_set_profile_table": ([VP, I, I, FP, FP, FP], I),
+        "mog_create_psf": ([VP, FP, I, I, FP, I, P(I)], I),
+        "mog_destroy_psf": ([VP, I], I),
+        "mog_render_batch": ([VP, P(mog_batch), VP, VP], I),
+        "mog_sync_status": ([VP, VP], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+def _check(ctx, status):
+    if status != MOG_OK:
+        msg = _lib.mog_last_error(ctx).decode() if ctx else ""
+        raise MogError(status, msg)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def mog_create_context(device=0):
+    h = ctypes.c_void_p()
+    _check(None, _lib.mog_create_context(ctypes.byref(h), int(device)))
+    return h
+
+
+def mog_destroy_context(ctx):
+    _check(None, _lib.mog_destroy_context(ctx))
+
+
+def mog_last_error(ctx):
+    return _lib.mog_last_error(ctx).decode()
+
+
+def mog_set_profile_table(ctx, profile_id, nodes, amp, var):
+    nodes = np.ascontiguousarray(nodes, dtype=np.float32)
+    amp = np.ascontiguousarray(amp, dtype=np.float32)
+    var = np.ascontiguousarray(var, dtype=np.float32)
+    n = nodes.shape[0]
+    assert amp.size == n * MOG_MAX_COMPONENTS and var.size == n * MOG_MAX_COMPONENTS
+    _check(ctx, _lib.mog_set_profile_table(ctx, int(profile_id), n, _fptr(nodes), _fptr(amp), _fptr(var)))
+
+
+def mog_create_psf(ctx, pixels, mog):
+    pixels = np.ascontiguousarray(pixels, dtype=np.float32)
+    mog = np.ascontiguousarray(mog, dtype=np.float32)
+    h, w = pixels.shape
+    k = mog.shape[0]
+    assert mog.shape == (k, 6)
+    out = ctypes.c_int(-1)
+    _check(ctx, _lib.mog_create_psf(ctx, _fptr(pixels), h, w, _fptr(mog), k, ctypes.byref(out)))
+    return out.value
+
+
+def mog_destroy_psf(ctx, psf_id):
+    _check(ctx, _lib.mog_destroy_psf(ctx, int(psf_id)))
+
+
+def make_batch(count, ptrs):
+    """``ptrs``: dict of device pointers (ints) for every batch field."""
+    b = mog_batch()
+    b.count = int(count)
+    for f, _ in mog_batch._fields_[1:]:
+        setattr(b, f, ctypes.c_void_p(int(ptrs[f])))
+    return b
+
+
+def mog_render_batch(ctx, batch, out_ptr, stream=0):
+    _check(ctx, _lib.mog_render_batch(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
+                                      ctypes.c_void_p(int(stream))))
+
+
+def mog_sync_status(ctx, stream=0):
+    _check(ctx, _lib.mog_sync_status(ctx, ctypes.c_void_p(int(stream))))

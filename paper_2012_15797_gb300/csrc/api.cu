@@ -1,0 +1,260 @@
+// C-ABI of include/mogconv.h: context, profile tables, PSFs, batched render.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace mog;
+
+struct mog_ctx {
+  int device = 0;
+  int num_sms = 0;
+  DevProfile* d_profiles = nullptr;
+  DevPsf* d_psfs = nullptr;
+  std::vector<DevPsf> h_psfs;
+  std::vector<float2*> psf_mem;  // one allocation per PSF holding every bucket's spectrum
+  int* d_status = nullptr;
+  PlanScratch plan{};
+  int64_t order_cap = 0;
+  double2* d_dft_scratch = nullptr;
+  std::string last_error;
+};
+
+namespace {
+
+mog_status fail(mog_ctx* ctx, mog_status code, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return code;
+}
+
+mog_status cuda_fail(mog_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? MOG_ERR_NOMEM : MOG_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define MOG_CUDA(ctx, expr)                                 \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+  } while (0)
+
+constexpr int SUPPORTED_BUCKETS = 0x7;  // 32, 64, 128
+
+BatchView view_of(const mog_batch* b) {
+  return BatchView{b->flux, b->x,      b->y,    b->log_re, b->e1,  b->e2,
+                   b->sersic_n, b->profile, b->psf, b->size, b->offset};
+}
+
+mog_status ensure_order_capacity(mog_ctx* ctx, int64_t count) {
+  if (count <= ctx->order_cap) return MOG_OK;
+  int64_t cap = ctx->order_cap ? ctx->order_cap : 1024;
+  while (cap < count) cap *= 2;
+  if (ctx->plan.order) MOG_CUDA(ctx, cudaFree(ctx->plan.order));
+  ctx->plan.order = nullptr;
+  ctx->order_cap = 0;
+  MOG_CUDA(ctx, cudaMalloc(&ctx->plan.order, sizeof(int32_t) * cap));
+  ctx->order_cap = cap;
+  return MOG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mog_status mog_create_context(mog_ctx** out, int device) {
+  if (!out) return MOG_ERR_ARG;
+  *out = nullptr;
+  mog_ctx* ctx = new mog_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_profiles, sizeof(DevProfile) * MOG_MAX_PROFILES);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_profiles, 0, sizeof(DevProfile) * MOG_MAX_PROFILES);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_psfs, sizeof(DevPsf) * MOG_MAX_PSFS);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_psfs, 0, sizeof(DevPsf) * MOG_MAX_PSFS);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  const size_t nkey = sizeof(int32_t) * NBUCKET * MOG_MAX_PSFS;
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->plan.hist, nkey);
+  if (e == cudaSuccess) e = cudaMemset(ctx->plan.hist, 0, nkey);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->plan.key_off, nkey);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->plan.small, sizeof(int32_t) * 4 * NBUCKET);
+  if (e == cudaSuccess) e = cudaMemset(ctx->plan.small, 0, sizeof(int32_t) * 4 * NBUCKET);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dft_scratch, sizeof(double2) * 256 * 129);
+  if (e != cudaSuccess) {
+    mog_destroy_context(ctx);
+    return e == cudaErrorMemoryAllocation ? MOG_ERR_NOMEM : MOG_ERR_CUDA;
+  }
+  ctx->h_psfs.assign(MOG_MAX_PSFS, DevPsf{});
+  ctx->psf_mem.assign(MOG_MAX_PSFS, nullptr);
+  *out = ctx;
+  return MOG_OK;
+}
+
+mog_status mog_destroy_context(mog_ctx* ctx) {
+  if (!ctx) return MOG_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  for (float2* p : ctx->psf_mem)
+    if (p) cudaFree(p);
+  cudaFree(ctx->d_profiles);
+  cudaFree(ctx->d_psfs);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->plan.hist);
+  cudaFree(ctx->plan.key_off);
+  cudaFree(ctx->plan.small);
+  cudaFree(ctx->plan.order);
+  cudaFree(ctx->d_dft_scratch);
+  delete ctx;
+  return MOG_OK;
+}
+
+const char* mog_last_error(const mog_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+mog_status mog_set_profile_table(mog_ctx* ctx, int profile_id, int n_nodes, const float* nodes, const float* amp,
+                                 const float* var) {
+  if (!ctx) return MOG_ERR_ARG;
+  if (profile_id < 0 || profile_id >= MOG_MAX_PROFILES)
+    return fail(ctx, MOG_ERR_ARG, "profile id %d outside [0, %d)", profile_id, MOG_MAX_PROFILES);
+  if (n_nodes < 1 || n_nodes > MOG_MAX_NODES || !nodes || !amp || !var)
+    return fail(ctx, MOG_ERR_ARG, "need 1..%d nodes and non-null arrays", MOG_MAX_NODES);
+  DevProfile h{};
+  h.n_nodes = n_nodes;
+  h.n0 = nodes[0];
+  h.inv_dn = 0.0f;
+  if (n_nodes > 1) {
+    const double dn = (double)nodes[n_nodes - 1] - nodes[0];
+    if (!(dn > 0)) return fail(ctx, MOG_ERR_ARG, "nodes must be ascending");
+    for (int i = 1; i < n_nodes; ++i) {
+      const double step = (double)nodes[i] - nodes[i - 1];
+      if (std::abs(step * (n_nodes - 1) - dn) > 1e-4 * dn) return fail(ctx, MOG_ERR_ARG, "nodes must be uniformly spaced");
+    }
+    h.inv_dn = (float)((n_nodes - 1) / dn);
+  }
+  for (int i = 0; i < n_nodes; ++i)
+    for (int c = 0; c < KMAX; ++c) {
+      const float a = amp[i * KMAX + c], v = var[i * KMAX + c];
+      if (!(a >= 0.0f) || !(v > 0.0f) || !std::isfinite(a) || !std::isfinite(v))
+        return fail(ctx, MOG_ERR_ARG, "node %d slot %d: need amp >= 0 and var > 0", i, c);
+      h.amp[i][c] = a;
+      h.logv[i][c] = logf(v);
+    }
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  MOG_CUDA(ctx, cudaMemcpy(ctx->d_profiles + profile_id, &h, sizeof(h), cudaMemcpyHostToDevice));
+  return MOG_OK;
+}
+
+mog_status mog_create_psf(mog_ctx* ctx, const float* pixels, int h, int w, const float* mogp, int k, int* psf_id) {
+  if (!ctx) return MOG_ERR_ARG;
+  if (!pixels || !mogp || !psf_id || h < 1 || w < 1 || h > 4096 || w > 4096)
+    return fail(ctx, MOG_ERR_ARG, "bad PSF image arguments");
+  if (k < 1 || k > KPSF) return fail(ctx, MOG_ERR_ARG, "PSF mixture needs 1..%d components", KPSF);
+  int id = -1;
+  for (int i = 0; i < MOG_MAX_PSFS; ++i)
+    if (ctx->h_psfs[i].k == 0) {
+      id = i;
+      break;
+    }
+  if (id < 0) return fail(ctx, MOG_ERR_STATE, "all %d PSF slots are in use", MOG_MAX_PSFS);
+  DevPsf rec{};
+  rec.k = k;
+  for (int j = 0; j < k; ++j) {
+    const float* m = mogp + 6 * j;
+    const double det = (double)m[3] * m[5] - (double)m[4] * m[4];
+    if (!(m[3] > 0) || !(m[5] > 0) || !(det > 0)) return fail(ctx, MOG_ERR_ARG, "PSF component %d covariance not positive", j);
+    for (int c = 0; c < 6; ++c) rec.mog[j][c] = m[c];
+  }
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  size_t total = 0;
+  size_t offs[NBUCKET];
+  for (int b = 0; b < NBUCKET; ++b) {
+    offs[b] = total;
+    total += psf_spec_elems(bucket_side(b));
+  }
+  float2* mem = nullptr;
+  MOG_CUDA(ctx, cudaMalloc(&mem, sizeof(float2) * total));
+  float* dpix = nullptr;
+  cudaError_t e = cudaMalloc(&dpix, sizeof(float) * h * w);
+  if (e == cudaSuccess) e = cudaMemcpy(dpix, pixels, sizeof(float) * h * w, cudaMemcpyHostToDevice);
+  for (int b = 0; b < NBUCKET && e == cudaSuccess; ++b) {
+    rec.spec[b] = mem + offs[b];
+    e = launch_psf_spectrum(dpix, h, w, bucket_side(b), ctx->d_dft_scratch, mem + offs[b], 0);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(dpix);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->d_psfs + id, &rec, sizeof(rec), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    return cuda_fail(ctx, e, "PSF spectrum");
+  }
+  ctx->h_psfs[id] = rec;
+  ctx->psf_mem[id] = mem;
+  *psf_id = id;
+  return MOG_OK;
+}
+
+mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id) {
+  if (!ctx) return MOG_ERR_ARG;
+  if (psf_id < 0 || psf_id >= MOG_MAX_PSFS || ctx->h_psfs[psf_id].k == 0)
+    return fail(ctx, MOG_ERR_ARG, "no PSF with id %d", psf_id);
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  MOG_CUDA(ctx, cudaDeviceSynchronize());
+  DevPsf empty{};
+  MOG_CUDA(ctx, cudaMemcpy(ctx->d_psfs + psf_id, &empty, sizeof(empty), cudaMemcpyHostToDevice));
+  cudaFree(ctx->psf_mem[psf_id]);
+  ctx->psf_mem[psf_id] = nullptr;
+  ctx->h_psfs[psf_id] = empty;
+  return MOG_OK;
+}
+
+mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  if (!batch || batch->count < 0) return fail(ctx, MOG_ERR_ARG, "null batch or negative count");
+  if (batch->count == 0) return MOG_OK;
+  if (batch->count > INT32_MAX) return fail(ctx, MOG_ERR_ARG, "at most 2^31-1 galaxies per call");
+  if (!out || !batch->flux || !batch->x || !batch->y || !batch->log_re || !batch->e1 || !batch->e2 ||
+      !batch->sersic_n || !batch->profile || !batch->psf || !batch->size || !batch->offset)
+    return fail(ctx, MOG_ERR_ARG, "null device pointer in batch");
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  mog_status st = ensure_order_capacity(ctx, batch->count);
+  if (st != MOG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const BatchView bv = view_of(batch);
+  MOG_CUDA(ctx, launch_plan(bv, batch->count, ctx->plan, SUPPORTED_BUCKETS, ctx->d_status, s));
+  RenderParams p{};
+  p.b = bv;
+  p.out = out;
+  p.profiles = ctx->d_profiles;
+  p.psfs = ctx->d_psfs;
+  p.order = ctx->plan.order;
+  p.bucket_start = ctx->plan.small;
+  p.bucket_count = ctx->plan.small + NBUCKET;
+  p.queue = ctx->plan.small + 2 * NBUCKET;
+  p.status = ctx->d_status;
+  for (int b = 0; b < NBUCKET; ++b)
+    if ((SUPPORTED_BUCKETS >> b) & 1) MOG_CUDA(ctx, launch_render_fwd(bucket_side(b), p, ctx->num_sms, s));
+  return MOG_OK;
+}
+
+mog_status mog_sync_status(mog_ctx* ctx, void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  MOG_CUDA(ctx, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int h = 0;
+  MOG_CUDA(ctx, cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  MOG_CUDA(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  if (h != 0) return fail(ctx, h, "device reported error %d", h);
+  return MOG_OK;
+}
+
+}  // extern "C"

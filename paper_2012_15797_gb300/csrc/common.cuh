@@ -1,0 +1,359 @@
+// Device-side building blocks shared by the render, adjoint, PSF and planning
+// kernels: table / PSF records, complex helpers, small DFTs, the shared-memory
+// Stockham passes, the bulk (TMA) copy with a bounded mbarrier wait, and the
+// per-galaxy set-up of Section 2, Steps 3-4.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mogconv.h"
+
+namespace mog {
+
+constexpr int KMAX = MOG_MAX_COMPONENTS;
+constexpr int KPSF = MOG_MAX_PSF_COMPONENTS;
+constexpr int RMAX = KMAX * KPSF;   // real-space terms per galaxy
+constexpr int NBUCKET = 4;          // patch sides 32, 64, 128, 256
+constexpr float LOG2E = 1.4426950408889634f;
+constexpr float PI_F = 3.14159265358979323846f;
+
+__host__ __device__ constexpr int bucket_of(int n) {
+  return n == 32 ? 0 : n == 64 ? 1 : n == 128 ? 2 : n == 256 ? 3 : -1;
+}
+__host__ __device__ constexpr int bucket_side(int b) { return 32 << b; }
+
+// Half-spectrum layout of a cached PSF FFT: [k][l], k = 0..N/2 (nu), l = 0..N-1
+// (omega, FFT order), row stride LSTRIDE float2 (padding keeps shared-memory
+// reads of consecutive l by neighbouring columns on distinct banks).
+__host__ __device__ constexpr int psf_lstride(int n) { return n <= 32 ? n + 4 : n + 8; }
+__host__ __device__ constexpr int psf_spec_elems(int n) { return (n / 2 + 1) * psf_lstride(n); }
+
+struct DevProfile {
+  int n_nodes;                 // 0 = not installed
+  float n0, inv_dn;            // first node and 1 / node spacing
+  float amp[MOG_MAX_NODES][KMAX];
+  float logv[MOG_MAX_NODES][KMAX];
+};
+
+struct DevPsf {
+  const float2* spec[NBUCKET];  // spectrum of the PSF embedded at (N/2, N/2), psf_lstride layout
+  int k;                        // mixture components; 0 = no PSF in this slot
+  float mog[KPSF][6];           // weight, mean x, mean y, vxx, vxy, vyy
+};
+
+// Status word: the first device-detected error wins.
+__device__ __forceinline__ void set_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------------
+// Complex helpers.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+// a * (s i) for s = +1 (inverse transform) or -1 (forward)
+template <int S>
+__device__ __forceinline__ float2 mul_si(float2 a) {
+  return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// 2^x on the special-function unit (the fast exp of Section 3's discussion).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ------------------------------------------------------------------------
+// Small in-register DFTs, sign S: +1 inverse (e^{+2 pi i/r}), -1 forward.
+// ------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <int S>
+__device__ __forceinline__ void dft4(float2* v) {
+  float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  float2 c = cadd(v[1], v[3]), d = mul_si<S>(csub(v[1], v[3]));
+  v[0] = cadd(a, c);
+  v[2] = csub(a, c);
+  v[1] = cadd(b, d);
+  v[3] = csub(b, d);
+}
+
+template <int S>
+__device__ __forceinline__ void dft8(float2* v) {
+  constexpr float R = 0.70710678118654752440f;
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<S>(e);
+  dft4<S>(o);
+  // w8^1 = (1 + S i)/sqrt2, w8^2 = S i, w8^3 = (-1 + S i)/sqrt2
+  float2 o1 = make_float2(R * (o[1].x - S * o[1].y), R * (o[1].y + S * o[1].x));
+  float2 o2 = mul_si<S>(o[2]);
+  float2 o3 = make_float2(R * (-o[3].x - S * o[3].y), R * (-o[3].y + S * o[3].x));
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
+}
+
+template <int R, int S>
+__device__ __forceinline__ void dft_r(float2* v) {
+  if constexpr (R == 8) dft8<S>(v);
+  else if constexpr (R == 4) dft4<S>(v);
+  else dft2<S>(v[0], v[1]);
+}
+
+// ------------------------------------------------------------------------
+// Stockham autosort FFT of length N held in shared memory, one FFT per group
+// of N/8 threads, 8 complex values per thread.  Radix schedule: 32 = 8*4,
+// 64 = 8*8, 128 = 8*8*2, 256 = 8*8*4.  A pass of radix R with current
+// sub-length Ns: butterfly b reads x[b + m N/R] (m < R), multiplies by
+// w_{Ns R}^{m (b mod Ns)}, takes an R-point DFT and writes
+// x'[(b / Ns) Ns R + (b mod Ns) + m Ns].  Thread j owns butterflies
+// b = j + q N/8 (q < 8/R).
+// Buffer index swizzle i + i/8 spreads the stride-8 accesses over banks.
+// ------------------------------------------------------------------------
+template <int N> struct Radix;
+template <> struct Radix<32> { static constexpr int P = 2; static constexpr int r[3] = {8, 4, 1}; };
+template <> struct Radix<64> { static constexpr int P = 2; static constexpr int r[3] = {8, 8, 1}; };
+template <> struct Radix<128> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 2}; };
+template <> struct Radix<256> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 4}; };
+
+template <int N>
+__device__ __forceinline__ int swz(int i) { return i + (i >> 3); }
+
+template <int N>
+__host__ __device__ constexpr int wstride() { return N + N / 8; }
+
+// Input of pass p (p >= 1): gather + twiddle + DFT into v[8].
+// tw[n] = e^{+2 pi i n / N}; forward passes use its conjugate.
+template <int N, int R, int S>
+__device__ __forceinline__ void stockham_load(const float2* buf, int j, int ns, const float2* tw, float2* v) {
+  constexpr int NB = 8 / R;
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int b = j + q * (N / 8);
+    const int k = b & (ns - 1);
+    const int tstep = N / (ns * R);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      float2 x = buf[swz<N>(b + m * (N / R))];
+      if (m > 0) {
+        float2 w = tw[(m * k * tstep) & (N - 1)];
+        x = (S > 0) ? cmul(x, w) : cmulc(x, w);
+      }
+      v[q * R + m] = x;
+    }
+    dft_r<R, S>(&v[q * R]);
+  }
+}
+
+// Output index n of value v[q R + m] after a pass of radix R at sub-length ns.
+template <int N, int R>
+__device__ __forceinline__ int stockham_out_index(int j, int ns, int q, int m) {
+  const int b = j + q * (N / 8);
+  return (b / ns) * ns * R + (b & (ns - 1)) + m * ns;
+}
+
+template <int N, int R>
+__device__ __forceinline__ void stockham_store(float2* buf, int j, int ns, const float2* v) {
+  constexpr int NB = 8 / R;
+#pragma unroll
+  for (int q = 0; q < NB; ++q)
+#pragma unroll
+    for (int m = 0; m < R; ++m) buf[swz<N>(stockham_out_index<N, R>(j, ns, q, m))] = v[q * R + m];
+}
+
+// ------------------------------------------------------------------------
+// Bulk (TMA) copy global -> shared with an mbarrier, bounded wait.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Issue a bulk copy of `bytes` (multiple of 16, both addresses 16-byte
+// aligned) and arm the barrier with the expected transaction count.
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for phase `parity` of the barrier; gives up after ~0.5 s and
+// returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 0) {
+      const uint64_t t = globaltimer_ns();
+      if (it == 0) t0 = t;
+      else if (t - t0 > 500000000ull) return false;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Steps 3-4 for one galaxy: pixel covariance S (Appendix A with CD = I), the
+// interpolated mixture (Section 3), the aliasing split and ramp, and the
+// compacted Fourier / real-space term lists.
+// ------------------------------------------------------------------------
+struct GalaxySetup {
+  int ok;             // 0: skip this galaxy (error recorded)
+  int nf, nr;         // Fourier components, real-space terms
+  int psf;
+  float s11, s12, s22;
+  float x, y;         // offset from the patch centre
+  float flux;
+  // Fourier components: amplitude flux a_i w_F / N^2, exponent -2 pi^2 v_i log2(e)
+  float famp[KMAX], fcoef[KMAX];
+  // Real-space terms (component i, PSF component j):
+  // rw * 2^(qa dx^2 + qb dx dy + qc dy^2), (dx, dy) = pixel - (mx, my)
+  float rw[RMAX], rqa[RMAX], rqb[RMAX], rqc[RMAX], rmx[RMAX], rmy[RMAX];
+};
+
+struct BatchView {
+  const float *flux, *x, *y, *log_re, *e1, *e2, *sersic_n;
+  const int32_t *profile, *psf, *size;
+  const int64_t* offset;
+};
+
+__device__ __forceinline__ float ramp_weight(float ns) {
+  float t = fminf(fmaxf(ns - 3.0f, 0.0f), 1.0f);
+  return t * t * (3.0f - 2.0f * t);
+}
+
+// Executed by one full warp; writes `gs` (shared memory).
+__device__ inline void galaxy_setup_warp(const BatchView& b, int64_t g, int n, const DevProfile* profiles,
+                                         const DevPsf* psfs, int* status, GalaxySetup* gs) {
+  const int lane = threadIdx.x & 31;
+  const float flux = b.flux[g], x = b.x[g], y = b.y[g], lre = b.log_re[g];
+  const float e1 = b.e1[g], e2 = b.e2[g], sn = b.sersic_n[g];
+  const int prof = b.profile[g], pid = b.psf[g];
+  const float e = sqrtf(e1 * e1 + e2 * e2);
+  bool ok = isfinite(flux) && isfinite(x) && isfinite(y) && isfinite(lre) && isfinite(e1) && isfinite(e2) &&
+            isfinite(sn) && e < 1.0f && lre < 30.0f;
+  ok = ok && prof >= 0 && prof < MOG_MAX_PROFILES && pid >= 0 && pid < MOG_MAX_PSFS;
+  const DevProfile* P = ok ? &profiles[prof] : nullptr;
+  const DevPsf* Q = ok ? &psfs[pid] : nullptr;
+  ok = ok && P->n_nodes > 0 && Q->k > 0;
+  if (!ok) {
+    if (lane == 0) {
+      set_status(status, MOG_ERR_DEVICE);
+      gs->ok = 0;
+    }
+    __syncwarp();
+    return;
+  }
+  // S = r^2 [ (1+b^2)/2 I + (b^2-1)/2 R ],  R = [[e1/e, -e2/e], [-e2/e, -e1/e]]
+  const float r2 = expf(2.0f * lre);
+  const float beta = (1.0f - e) / (1.0f + e);
+  const float h = 0.5f * (1.0f + beta * beta);
+  const float gq = 0.5f * (beta * beta - 1.0f);
+  const float c1 = e > 0.0f ? e1 / e : 0.0f, c2 = e > 0.0f ? e2 / e : 0.0f;
+  const float s11 = r2 * (h + gq * c1), s12 = -r2 * gq * c2, s22 = r2 * (h - gq * c1);
+  const float tr = s11 + s22;
+
+  // Mixture component `lane` at Sersic index sn.
+  float a = 0.0f, v = 1.0f;
+  if (lane < KMAX) {
+    if (P->n_nodes == 1) {
+      a = P->amp[0][lane];
+      v = expf(P->logv[0][lane]);
+    } else {
+      float u = (sn - P->n0) * P->inv_dn;
+      u = fminf(fmaxf(u, 0.0f), (float)(P->n_nodes - 1));
+      int j = min((int)u, P->n_nodes - 2);
+      float t = u - (float)j;
+      a = (1.0f - t) * P->amp[j][lane] + t * P->amp[j + 1][lane];
+      v = expf((1.0f - t) * P->logv[j][lane] + t * P->logv[j + 1][lane]);
+    }
+  }
+  const float ns = 0.5f * (float)n * rsqrtf(v * tr);
+  const float wf = ramp_weight(ns);
+  const bool four = lane < KMAX && a > 0.0f && wf > 0.0f;
+  const bool real = lane < KMAX && a > 0.0f && wf < 1.0f;
+  const unsigned mf = __ballot_sync(0xffffffffu, four);
+  const unsigned mr = __ballot_sync(0xffffffffu, real);
+  const unsigned lt = (1u << lane) - 1u;
+  const float inv_n2 = 1.0f / ((float)n * (float)n);
+  if (four) {
+    const int p = __popc(mf & lt);
+    gs->famp[p] = flux * a * wf * inv_n2;
+    gs->fcoef[p] = -2.0f * PI_F * PI_F * v * LOG2E;
+  }
+  const int kp = Q->k;
+  if (real) {
+    const int p = __popc(mr & lt);
+    const float cx = 0.5f * (float)n + x, cy = 0.5f * (float)n + y;
+    for (int jj = 0; jj < kp; ++jj) {
+      const float* m = Q->mog[jj];
+      const float vxx = v * s11 + m[3], vxy = v * s12 + m[4], vyy = v * s22 + m[5];
+      const float det = vxx * vyy - vxy * vxy;
+      const float idet = 1.0f / det;
+      const int t = p * kp + jj;
+      gs->rw[t] = flux * a * (1.0f - wf) * m[0] * rsqrtf(det) * (0.5f / PI_F);
+      gs->rqa[t] = -0.5f * LOG2E * vyy * idet;
+      gs->rqb[t] = LOG2E * vxy * idet;
+      gs->rqc[t] = -0.5f * LOG2E * vxx * idet;
+      gs->rmx[t] = cx + m[1];
+      gs->rmy[t] = cy + m[2];
+    }
+  }
+  if (lane == 0) {
+    gs->ok = 1;
+    gs->nf = __popc(mf);
+    gs->nr = __popc(mr) * kp;
+    gs->psf = pid;
+    gs->s11 = s11;
+    gs->s12 = s12;
+    gs->s22 = s22;
+    gs->x = x;
+    gs->y = y;
+    gs->flux = flux;
+  }
+  __syncwarp();
+}
+
+}  // namespace mog

@@ -1,0 +1,45 @@
+// Host-side declarations shared between the C-ABI implementation and the
+// kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mog {
+
+struct RenderParams {
+  BatchView b;
+  float* out;
+  const DevProfile* profiles;
+  const DevPsf* psfs;
+  const int32_t* order;         // galaxy indices grouped by (bucket, psf)
+  const int32_t* bucket_start;  // [NBUCKET] first position in `order`
+  const int32_t* bucket_count;  // [NBUCKET]
+  int32_t* queue;               // [NBUCKET] work counters, zeroed by the planner
+  int* status;
+};
+
+struct PlanScratch {
+  int32_t* hist;     // [NBUCKET * MOG_MAX_PSFS], zero between calls
+  int32_t* key_off;  // [NBUCKET * MOG_MAX_PSFS]
+  int32_t* small;    // bucket_start[4], bucket_count[4], queue[4]
+  int32_t* order;    // [capacity]
+};
+
+// Builds the bucket / PSF grouping of a batch on `s`.  `supported` is a
+// bitmask of buckets the caller can render; galaxies of other sizes are
+// reported through the status word and skipped.
+cudaError_t launch_plan(const BatchView& b, int64_t count, const PlanScratch& ps, int supported, int* status,
+                        cudaStream_t s);
+
+cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, cudaStream_t s);
+size_t render_fwd_smem(int n);
+
+// Spectrum of a PSF embedded with its centre at (n/2, n/2), written in the
+// psf_lstride layout.  `pix` is device memory (h x w float).
+cudaError_t launch_psf_spectrum(const float* pix, int h, int w, int n, double2* scratch, float2* spec,
+                                cudaStream_t s);
+
+}  // namespace mog

@@ -1,0 +1,100 @@
+"""PyTorch marshalling around the C-ABI: device memory and streams come from
+torch, every computation runs in the library's kernels."""
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import capi
+
+FLOAT_FIELDS = ("flux", "x", "y", "log_re", "e1", "e2", "sersic_n")
+INT_FIELDS = ("profile", "psf", "size")
+
+
+@dataclass
+class DeviceBatch:
+    """A batch of galaxies resident on the device (structure of arrays) plus
+    the packed-output layout: galaxy g owns out[offset[g] : offset[g] + size[g]^2]."""
+    tensors: dict
+    count: int
+    total: int           # output elements
+    sizes: np.ndarray    # host copy of the patch sides
+    offsets: np.ndarray  # host copy of the offsets
+
+    def ptrs(self):
+        return {k: v.data_ptr() for k, v in self.tensors.items()}
+
+
+def pack_offsets(sizes):
+    sizes = np.asarray(sizes, dtype=np.int64)
+    area = sizes * sizes
+    off = np.zeros(len(sizes), dtype=np.int64)
+    if len(sizes) > 1:
+        off[1:] = np.cumsum(area)[:-1]
+    return off, int(area.sum())
+
+
+def host_batch(gals, pin=False):
+    """Host tensors (optionally pinned) of a ``workloads.Galaxies`` batch."""
+    t = {}
+    for f in FLOAT_FIELDS:
+        t[f] = torch.from_numpy(np.ascontiguousarray(getattr(gals, f), dtype=np.float32))
+    for f in INT_FIELDS:
+        t[f] = torch.from_numpy(np.ascontiguousarray(getattr(gals, f), dtype=np.int32))
+    off, total = pack_offsets(gals.size)
+    t["offset"] = torch.from_numpy(off)
+    if pin:
+        t = {k: v.pin_memory() for k, v in t.items()}
+    return t, total
+
+
+def to_device(gals, device="cuda"):
+    t, total = host_batch(gals)
+    dev = {k: v.to(device) for k, v in t.items()}
+    return DeviceBatch(dev, len(gals), total, np.asarray(gals.size).copy(), t["offset"].numpy().copy())
+
+
+class Renderer:
+    """Owns a library context with its profile tables and PSFs."""
+
+    def __init__(self, tables, psfs, device=0):
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        self.ctx = capi.mog_create_context(device)
+        for pid, t in tables.items():
+            capi.mog_set_profile_table(self.ctx, pid, t.nodes, t.amp, t.var)
+        self.psf_ids = [capi.mog_create_psf(self.ctx, p.image, p.mog) for p in psfs]
+        if self.psf_ids != list(range(len(psfs))):
+            raise RuntimeError("fresh context expected PSF ids 0..P-1")
+
+    def close(self):
+        if self.ctx is not None:
+            capi.mog_destroy_context(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, batch, out=None, stream=None):
+        """Renders a DeviceBatch into a flat float32 device tensor."""
+        if out is None:
+            out = torch.empty(batch.total, dtype=torch.float32, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        b = capi.make_batch(batch.count, batch.ptrs())
+        capi.mog_render_batch(self.ctx, b, out.data_ptr(), s.cuda_stream)
+        return out
+
+    def sync_status(self, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        capi.mog_sync_status(self.ctx, s.cuda_stream)
+
+
+def patches(out, batch):
+    """List of (N, N) views of a packed output."""
+    o = out.reshape(-1)
+    return [o[int(batch.offsets[i]):int(batch.offsets[i]) + int(batch.sizes[i]) ** 2].view(
+        int(batch.sizes[i]), int(batch.sizes[i])) for i in range(batch.count)]

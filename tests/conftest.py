@@ -23,3 +23,21 @@ def tables():
 def psf0():
     from workloads import config0_psf
     return config0_psf()
+
+
+@pytest.fixture(scope="session")
+def gpu_renderer(tables, psf0):
+    """A library context with the profile tables, PSF 0 = the 2-Gaussian
+    PSF and PSFs 1..4 = Moffat-winged PSFs."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_15797_gb300.build import build
+    build()
+    from paper_2012_15797_gb300.renderer import Renderer
+    from workloads import config2_psfs
+    psfs = [psf0] + config2_psfs(4)
+    r = Renderer(tables, psfs)
+    r.psfs = psfs
+    yield r
+    r.close()
