@@ -1,0 +1,473 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the hybrid Fourier / real-space galaxy renderer.
+
+Workload (one step): render the fixed-size batch of 100,000 synthetic
+galaxies at 64 x 64 (50/50 exponential / de Vaucouleurs mixtures, r_e
+log-uniform 0.3-20 px, |e| <= 0.6, flux 1-1e4, sub-pixel offsets, one shared
+two-Gaussian PSF) with one call of the library's batched render.  Inputs are
+resident in HBM when the timed region starts.
+
+Prints one JSON line (rank 0).  Under torchrun each rank renders its own copy
+of the batch on its own GPU (replicas: no collective on the data path; the
+barrier and the max over ranks of the elapsed time are control only).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the plain reference of the
+method) on the host cores on bounded samples of the same workload.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+G_DEFAULT = 100_000
+N_PATCH = 64
+METRIC = "galaxy patches rendered/s at 64x64 (100k-galaxy fixed-size batch)"
+UNIT = "patches/s"
+PARAM_BYTES = 7 * 4 + 3 * 4 + 8      # float params, int ids, int64 offset
+SFU_PER_CLK_SM = 16                  # MUFU ex2 lanes per SM per clock
+FP32_FLOP_PER_CLK_SM = 256           # 128 FMA lanes x 2
+KERNEL_SOURCES = ("paper_2012_15797_gb300/csrc/render_fwd.cu", "paper_2012_15797_gb300/csrc/common.cuh")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "render_fwd_64_config1.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--galaxies", type=int, default=G_DEFAULT)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# Algorithmic work of the method per galaxy (what it must compute).
+# ----------------------------------------------------------------------------
+
+def split_counts(gals, tables, kpsf, n):
+    """Per galaxy: Fourier components (w_F > 0) and real-space terms
+    (components with w_F < 1 times PSF-mixture components), from the
+    aliasing split of Step 4."""
+    import numpy as np
+    nf = np.zeros(len(gals), dtype=np.int64)
+    nr = np.zeros(len(gals), dtype=np.int64)
+    e = np.hypot(gals.e1.astype(np.float64), gals.e2.astype(np.float64))
+    beta = (1 - e) / (1 + e)
+    tr = np.exp(2 * gals.log_re.astype(np.float64)) * (1 + beta * beta)
+    for pid, t in tables.items():
+        sel = np.nonzero(gals.profile == pid)[0]
+        if len(sel) == 0:
+            continue
+        if len(t.nodes) == 1:
+            a = np.broadcast_to(t.amp[0], (len(sel), t.amp.shape[1]))
+            v = np.broadcast_to(t.var[0], (len(sel), t.var.shape[1]))
+        else:
+            u = np.clip((gals.sersic_n[sel] - t.nodes[0]) / (t.nodes[1] - t.nodes[0]), 0, len(t.nodes) - 1)
+            j = np.minimum(u.astype(np.int64), len(t.nodes) - 2)
+            w = (u - j)[:, None]
+            a = (1 - w) * t.amp[j] + w * t.amp[j + 1]
+            v = np.exp((1 - w) * np.log(t.var[j]) + w * np.log(t.var[j + 1]))
+        ns = 0.5 * n / np.sqrt(v * tr[sel, None])
+        tt = np.clip(ns - 3.0, 0.0, 1.0)
+        wf = tt * tt * (3 - 2 * tt)
+        nf[sel] = ((a > 0) & (wf > 0)).sum(axis=1)
+        nr[sel] = ((a > 0) & (wf < 1)).sum(axis=1) * kpsf
+    return nf, nr
+
+
+def algorithmic_work(gals, tables, kpsf, n=N_PATCH):
+    nf, nr = split_counts(gals, tables, kpsf, n)
+    bins = n * (n // 2 + 1)
+    ex2 = float((nf * bins + nr * n * n).sum())
+    flops = float((5.0 * n * n * math.log2(n) + bins * (19.0 + 2.0 * nf) + 8.0 * nr * n * n).sum())
+    hbm = float(len(gals) * (n * n * 4 + PARAM_BYTES))
+    comps = float(nf.sum() + nr.sum() / kpsf)
+    return dict(ex2=ex2, flops=flops, hbm_bytes=hbm, real_fraction=float(nr.sum() / kpsf) / max(comps, 1.0),
+                fourier_components=float(nf.sum()), real_terms=float(nr.sum()))
+
+
+def peaks(num_sms):
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    src = "measured"
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        hbm = float(mp["hbm_gbs"]) * 1e9
+        mhz = float(mp.get("sm_max_mhz", 2070.0))
+    except (OSError, KeyError, ValueError):
+        hbm, mhz, src = 6.8e12, 2070.0, "fallback"
+    clk = mhz * 1e6
+    return dict(hbm=hbm, hbm_src=src, sfu=num_sms * SFU_PER_CLK_SM * clk, fp32=num_sms * FP32_FLOP_PER_CLK_SM * clk,
+                sm_mhz=mhz)
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(galaxies):
+    """DRAM bytes per launch from the committed ncu summary, scaled to
+    ``galaxies``; None when the kernel changed since the capture."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    per = re.search(r"dram_bytes_per_galaxy:\s*([0-9.eE+]+)", txt)
+    if not sha or not per or sha.group(1) != kernel_source_sha():
+        return None
+    return float(per.group(1)) * galaxies
+
+
+# ----------------------------------------------------------------------------
+# Clocks during the timed region.
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5], hwt=parts[6], swt=parts[7],
+                                 pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sms = sorted(r["sm"] for r in rows)
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": rows[0]["smax"], "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm): a spawn pool over the host cores.
+# ----------------------------------------------------------------------------
+
+_W = {}
+
+
+def _worker_init(seed_g):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from oracle import render as R
+    from workloads import config0_psf, config1_galaxies, load_profile_tables
+    _W["R"] = R
+    _W["tables"] = load_profile_tables()
+    _W["psf"] = config0_psf()
+    _W["gals"] = config1_galaxies(seed_g)
+    _W["hat"] = R.psf_spectrum(_W["psf"].image, N_PATCH)
+
+
+def _worker_render(idx):
+    R, gals = _W["R"], _W["gals"]
+    t = time.perf_counter()
+    for i in idx:
+        R.render(gals.row(int(i)), None, _W["psf"].mog, _W["tables"], psf_hat=_W["hat"])
+    return len(idx), time.perf_counter() - t
+
+
+def _worker_timed(args):
+    start, stride, budget = args
+    R, gals = _W["R"], _W["gals"]
+    t0 = time.perf_counter()
+    n = 0
+    i = start
+    while time.perf_counter() - t0 < budget and i < len(gals):
+        R.render(gals.row(int(i)), None, _W["psf"].mog, _W["tables"], psf_hat=_W["hat"])
+        n += 1
+        i += stride
+    return n
+
+
+def cpu_pool(galaxies):
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(cores, initializer=_worker_init, initargs=(galaxies,)), cores
+
+
+def cpu_baseline(galaxies, seconds):
+    pool, cores = cpu_pool(galaxies)
+    try:
+        pool.map(_worker_render, [[i] for i in range(cores)])     # warm the workers
+        t0 = time.perf_counter()
+        counts = pool.map(_worker_timed, [(c, cores, seconds) for c in range(cores)])
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    done = sum(counts)
+    return {"value": done / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} galaxies of the 100k fixed-size batch (indices interleaved over {cores} spawn "
+                      f"workers, {seconds:.0f} s wall budget), FP64 numpy oracle"}
+
+
+# ----------------------------------------------------------------------------
+# Distributed helpers (replicas).
+# ----------------------------------------------------------------------------
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != n_gpus and world > 1:
+        raise SystemExit(f"--gpus {n_gpus} but WORLD_SIZE={world}")
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# Arms.
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_2012_15797_gb300 import capi
+    from paper_2012_15797_gb300.build import build
+    if rank == 0 or world == 1:
+        build()
+    barrier(world)
+    from paper_2012_15797_gb300.renderer import Renderer, host_batch, to_device
+    from workloads import config0_psf, config1_galaxies, load_profile_tables
+
+    tables = load_profile_tables()
+    psf = config0_psf()
+    gals = config1_galaxies(args.galaxies)
+    r = Renderer(tables, [psf], device=local)
+    batch = to_device(gals, device=f"cuda:{local}")
+    out = torch.empty(batch.total, dtype=torch.float32, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 0)):
+        r.render(batch, out)
+    r.sync_status()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    capi.mog_set_timing(r.ctx, True)
+    capi.mog_read_timing(r.ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        r.render(batch, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    capi.mog_set_timing(r.ctx, False)
+    kms, kn = capi.mog_read_timing(r.ctx)
+    r.sync_status()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world)
+    value = world * args.galaxies * args.steps / (ms_max / 1e3)
+
+    # end to end through the same API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host, total = host_batch(gals, pin=True)
+        dev = batch.tensors
+        out_host = torch.empty(total, dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = out_host.numel() * 4
+        k2 = max(3, min(args.steps, 20))
+        for it in range(k2 + 2):
+            if it == 2:
+                barrier(world)
+                torch.cuda.synchronize()
+                e0.record(stream)
+            for key, v in host.items():
+                dev[key].copy_(v, non_blocking=True)
+            r.render(batch, out)
+            out_host.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        e2e = {"value": world * args.galaxies * k2 / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": k2}
+        r.sync_status()
+
+    if rank != 0:
+        r.close()
+        return
+
+    # roofline of the dominant kernel (64 x 64 render), from live CUDA events
+    props = torch.cuda.get_device_properties(local)
+    pk = peaks(props.multi_processor_count)
+    work = algorithmic_work(gals, tables, psf.mog.shape[0])
+    k_ms = kms[1] / max(kn[1], 1)
+    t = {"hbm": work["hbm_bytes"] / pk["hbm"], "sfu": work["ex2"] / pk["sfu"], "fp32": work["flops"] / pk["fp32"]}
+    bound = max(t, key=t.get)
+    fracs = {k: v / (k_ms / 1e3) for k, v in t.items()}
+    if bound == "hbm":
+        roof = {"bound": "hbm", "achieved": work["hbm_bytes"] / (k_ms / 1e3) / 1e9, "peak": pk["hbm"] / 1e9,
+                "unit": "GB/s"}
+    elif bound == "sfu":
+        roof = {"bound": "alu", "pipe": "MUFU ex2", "achieved": work["ex2"] / (k_ms / 1e3) / 1e12,
+                "peak": pk["sfu"] / 1e12, "unit": "Tex2/s"}
+    else:
+        roof = {"bound": "alu", "pipe": "FP32", "achieved": work["flops"] / (k_ms / 1e3) / 1e12,
+                "peak": pk["fp32"] / 1e12, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = recorded_traffic(args.galaxies)
+    roof["kernel"] = "render_fwd_kernel<64>"
+    roof["kernel_ms"] = k_ms
+    roof["peak_source"] = (f"{pk['hbm_src']} HBM copy GB/s (MEASURED_PEAKS.json)" if bound == "hbm" else
+                           f"{props.multi_processor_count} SMs x {SFU_PER_CLK_SM if bound == 'sfu' else FP32_FLOP_PER_CLK_SM}"
+                           f"/clk x {pk['sm_mhz']:.0f} MHz")
+    roof["fractions"] = {k: round(v, 4) for k, v in fracs.items()}
+    roof["algorithmic_per_launch"] = {"hbm_bytes": work["hbm_bytes"], "ex2": work["ex2"], "flops": work["flops"]}
+
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.galaxies, args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.galaxies} galaxies x 64x64 patches per GPU per step: 50/50 exp (6 comp) / "
+                               f"deV (10 comp), r_e log-U(0.3, 20) px, |e| U(0, 0.6), flux log-U(1, 1e4), "
+                               f"offsets U[-0.5, 0.5), one 2-Gaussian PSF (sigma 1.5/3.0) + 3-Gaussian fit",
+                   "galaxies_per_step": args.galaxies * world, "patch": N_PATCH, "parallelism": "replicas",
+                   "l2": f"each step writes {args.galaxies * N_PATCH * N_PATCH * 4 / 1e9:.2f} GB of patches "
+                         f"(> 129 MB L2), which evicts the {args.galaxies * PARAM_BYTES / 1e6:.1f} MB of parameters; "
+                         f"no separate flush"},
+        "real_space_component_fraction": work["real_fraction"],
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": args.steps * 4, "clocks": clocks,
+    }
+    print(json.dumps(line))
+    r.close()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pool, cores = cpu_pool(args.galaxies)
+    per = 2
+    try:
+        pool.map(_worker_render, [[i] for i in range(cores)])
+        nxt = 0
+
+        def step():
+            nonlocal nxt
+            chunks = [list(range(nxt + c * per, nxt + (c + 1) * per)) for c in range(cores)]
+            nxt = (nxt + cores * per) % (args.galaxies - cores * per)
+            return sum(n for n, _ in pool.map(_worker_render, chunks))
+
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        done = sum(step() for _ in range(args.steps))
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    value = done / wall
+    sample = (f"{cores * per} galaxies per step of the 100k fixed-size batch over {cores} spawn workers "
+              f"(FP64 numpy oracle)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall / max(args.steps, 1) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "the same 100k-galaxy 64x64 batch, bounded per-step samples", "patch": N_PATCH},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

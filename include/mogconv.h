@@ -89,6 +89,8 @@ typedef struct mog_batch {
   const int32_t* psf;
   const int32_t* size;
   const int64_t* offset;
+  uint32_t size_mask;  /* optional, host: bit b set if some galaxy has N = 32 << b;
+                          0 = unknown (every size's kernel is launched) */
 } mog_batch;
 
 /* Creates a context on CUDA device `device` (makes it current).  *out gets
@@ -134,6 +136,17 @@ mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id);
  * Asynchronous on `stream`.
  */
 mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
+
+/*
+ * Kernel timing for measurement: while enabled, every render-kernel launch is
+ * bracketed by CUDA events recorded on its own stream.  mog_read_timing
+ * waits for the recorded events and returns, per patch side N = 32 << b
+ * (b = 0..3), the summed kernel milliseconds ms[b] and launch counts n[b]
+ * since the previous read, then resets them.  Both arrays are host memory of
+ * 4 elements.
+ */
+mog_status mog_set_timing(mog_ctx* ctx, int enable);
+mog_status mog_read_timing(mog_ctx* ctx, double* ms, int64_t* launches);
 
 /*
  * Reads the device status word after synchronising `stream` and resets it.

@@ -31,6 +31,7 @@ MOG_MAX_NODES = 64
 EXPORTED = (
     "mog_create_context", "mog_destroy_context", "mog_last_error", "mog_set_profile_table",
     "mog_create_psf", "mog_destroy_psf", "mog_render_batch", "mog_sync_status",
+    "mog_set_timing", "mog_read_timing",
 )
 
 
@@ -47,6 +48,7 @@ class mog_batch(ctypes.Structure):
         ("log_re", ctypes.c_void_p), ("e1", ctypes.c_void_p), ("e2", ctypes.c_void_p),
         ("sersic_n", ctypes.c_void_p), ("profile", ctypes.c_void_p), ("psf", ctypes.c_void_p),
         ("size", ctypes.c_void_p), ("offset", ctypes.c_void_p),
+        ("size_mask", ctypes.c_uint32),
     ]
 
 
@@ -65,6 +67,8 @@ def _load():
         "mog_destroy_psf": ([VP, I], I),
         "mog_render_batch": ([VP, P(mog_batch), VP, VP], I),
         "mog_sync_status": ([VP, VP], I),
+        "mog_set_timing": ([VP, I], I),
+        "mog_read_timing": ([VP, P(ctypes.c_double), P(ctypes.c_int64)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -128,18 +132,32 @@ def mog_destroy_psf(ctx, psf_id):
     _check(ctx, _lib.mog_destroy_psf(ctx, int(psf_id)))
 
 
-def make_batch(count, ptrs):
-    """``ptrs``: dict of device pointers (ints) for every batch field."""
+def make_batch(count, ptrs, size_mask=0):
+    """``ptrs``: dict of device pointers (ints) for every batch field;
+    ``size_mask``: optional bitmask of the patch sides present."""
     b = mog_batch()
     b.count = int(count)
-    for f, _ in mog_batch._fields_[1:]:
+    for f, _ in mog_batch._fields_[1:-1]:
         setattr(b, f, ctypes.c_void_p(int(ptrs[f])))
+    b.size_mask = int(size_mask)
     return b
 
 
 def mog_render_batch(ctx, batch, out_ptr, stream=0):
     _check(ctx, _lib.mog_render_batch(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
                                       ctypes.c_void_p(int(stream))))
+
+
+def mog_set_timing(ctx, enable):
+    _check(ctx, _lib.mog_set_timing(ctx, 1 if enable else 0))
+
+
+def mog_read_timing(ctx):
+    """Returns (ms[4], launches[4]) per patch side 32, 64, 128, 256."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    _check(ctx, _lib.mog_read_timing(ctx, ms, n))
+    return list(ms), list(n)
 
 
 def mog_sync_status(ctx, stream=0):

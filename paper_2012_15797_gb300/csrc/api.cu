@@ -22,6 +22,16 @@ struct mog_ctx {
   int64_t order_cap = 0;
   double2* d_dft_scratch = nullptr;
   std::string last_error;
+  // measurement hooks
+  bool timing = false;
+  struct Timed {
+    int bucket;
+    cudaEvent_t a, b;
+  };
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double acc_ms[NBUCKET] = {0, 0, 0, 0};
+  int64_t acc_n[NBUCKET] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -54,6 +64,15 @@ constexpr int SUPPORTED_BUCKETS = 0x7;  // 32, 64, 128
 BatchView view_of(const mog_batch* b) {
   return BatchView{b->flux, b->x,      b->y,    b->log_re, b->e1,  b->e2,
                    b->sersic_n, b->profile, b->psf, b->size, b->offset};
+}
+
+cudaError_t take_event(mog_ctx* ctx, cudaEvent_t* ev) {
+  if (!ctx->event_pool.empty()) {
+    *ev = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return cudaSuccess;
+  }
+  return cudaEventCreate(ev);
 }
 
 mog_status ensure_order_capacity(mog_ctx* ctx, int64_t count) {
@@ -115,6 +134,11 @@ mog_status mog_destroy_context(mog_ctx* ctx) {
   cudaFree(ctx->plan.small);
   cudaFree(ctx->plan.order);
   cudaFree(ctx->d_dft_scratch);
+  for (auto& t : ctx->pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   delete ctx;
   return MOG_OK;
 }
@@ -241,8 +265,49 @@ mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, vo
   p.bucket_count = ctx->plan.small + NBUCKET;
   p.queue = ctx->plan.small + 2 * NBUCKET;
   p.status = ctx->d_status;
-  for (int b = 0; b < NBUCKET; ++b)
-    if ((SUPPORTED_BUCKETS >> b) & 1) MOG_CUDA(ctx, launch_render_fwd(bucket_side(b), p, ctx->num_sms, s));
+  const uint32_t want = batch->size_mask ? (batch->size_mask & SUPPORTED_BUCKETS) : SUPPORTED_BUCKETS;
+  for (int b = 0; b < NBUCKET; ++b) {
+    if (!((want >> b) & 1)) continue;
+    mog_ctx::Timed t{b, nullptr, nullptr};
+    if (ctx->timing) {
+      MOG_CUDA(ctx, take_event(ctx, &t.a));
+      MOG_CUDA(ctx, take_event(ctx, &t.b));
+      MOG_CUDA(ctx, cudaEventRecord(t.a, s));
+    }
+    MOG_CUDA(ctx, launch_render_fwd(bucket_side(b), p, ctx->num_sms, s));
+    if (ctx->timing) {
+      MOG_CUDA(ctx, cudaEventRecord(t.b, s));
+      ctx->pending.push_back(t);
+    }
+  }
+  return MOG_OK;
+}
+
+mog_status mog_set_timing(mog_ctx* ctx, int enable) {
+  if (!ctx) return MOG_ERR_ARG;
+  ctx->timing = enable != 0;
+  return MOG_OK;
+}
+
+mog_status mog_read_timing(mog_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx || !ms || !launches) return MOG_ERR_ARG;
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  for (auto& t : ctx->pending) {
+    MOG_CUDA(ctx, cudaEventSynchronize(t.b));
+    float e = 0.0f;
+    MOG_CUDA(ctx, cudaEventElapsedTime(&e, t.a, t.b));
+    ctx->acc_ms[t.bucket] += e;
+    ctx->acc_n[t.bucket] += 1;
+    ctx->event_pool.push_back(t.a);
+    ctx->event_pool.push_back(t.b);
+  }
+  ctx->pending.clear();
+  for (int b = 0; b < NBUCKET; ++b) {
+    ms[b] = ctx->acc_ms[b];
+    launches[b] = ctx->acc_n[b];
+    ctx->acc_ms[b] = 0.0;
+    ctx->acc_n[b] = 0;
+  }
   return MOG_OK;
 }
 

@@ -143,21 +143,36 @@ __device__ __forceinline__ int swz(int i) { return i + (i >> 3); }
 template <int N>
 __host__ __device__ constexpr int wstride() { return N + N / 8; }
 
-// Input of pass p (p >= 1): gather + twiddle + DFT into v[8].
-// tw[n] = e^{+2 pi i n / N}; forward passes use its conjugate.
+// Twiddle table of pass p (p >= 1) with radix R at sub-length Ns: entry
+// [(m - 1) N/R + b] = w_N^{m (b mod Ns) N / (Ns R)} for butterfly b < N/R and
+// m = 1..R-1 (w_N = e^{+2 pi i / N}).  Threads of an FFT read consecutive b,
+// so the reads are bank-conflict free; forward passes use the conjugate.
+template <int N, int R>
+__host__ __device__ constexpr int twiddle_elems() { return (R - 1) * (N / R); }
+
+template <int N, int R>
+__device__ __forceinline__ void fill_twiddles(float2* t, int ns, int tid, int nthreads) {
+  for (int i = tid; i < twiddle_elems<N, R>(); i += nthreads) {
+    const int m = i / (N / R) + 1, b = i % (N / R);
+    const int e = (m * (b & (ns - 1)) * (N / (ns * R))) & (N - 1);
+    float s, c;
+    sincospif(2.0f * (float)e / (float)N, &s, &c);
+    t[i] = make_float2(c, s);
+  }
+}
+
+// Input of a pass after the first: gather + twiddle + R-point DFTs into v[8].
 template <int N, int R, int S>
-__device__ __forceinline__ void stockham_load(const float2* buf, int j, int ns, const float2* tw, float2* v) {
+__device__ __forceinline__ void stockham_load(const float2* buf, int j, const float2* twt, float2* v) {
   constexpr int NB = 8 / R;
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = j + q * (N / 8);
-    const int k = b & (ns - 1);
-    const int tstep = N / (ns * R);
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       float2 x = buf[swz<N>(b + m * (N / R))];
       if (m > 0) {
-        float2 w = tw[(m * k * tstep) & (N - 1)];
+        const float2 w = twt[(m - 1) * (N / R) + b];
         x = (S > 0) ? cmul(x, w) : cmulc(x, w);
       }
       v[q * R + m] = x;
@@ -249,8 +264,9 @@ struct GalaxySetup {
   // Fourier components: amplitude flux a_i w_F / N^2, exponent -2 pi^2 v_i log2(e)
   float famp[KMAX], fcoef[KMAX];
   // Real-space terms (component i, PSF component j):
-  // rw * 2^(qa dx^2 + qb dx dy + qc dy^2), (dx, dy) = pixel - (mx, my)
-  float rw[RMAX], rqa[RMAX], rqb[RMAX], rqc[RMAX], rmx[RMAX], rmy[RMAX];
+  // rw * 2^(qa dx^2 + qb dx dy + qc dy^2), (dx, dy) = pixel - (mx, my);
+  // rrr = 2^(2 qa) steps the ratio of neighbouring pixels along a row
+  float rw[RMAX], rqa[RMAX], rqb[RMAX], rqc[RMAX], rmx[RMAX], rmy[RMAX], rrr[RMAX];
 };
 
 struct BatchView {
@@ -335,6 +351,7 @@ __device__ inline void galaxy_setup_warp(const BatchView& b, int64_t g, int n, c
       const int t = p * kp + jj;
       gs->rw[t] = flux * a * (1.0f - wf) * m[0] * rsqrtf(det) * (0.5f / PI_F);
       gs->rqa[t] = -0.5f * LOG2E * vyy * idet;
+      gs->rrr[t] = ex2(-LOG2E * vyy * idet);
       gs->rqb[t] = LOG2E * vxy * idet;
       gs->rqc[t] = -0.5f * LOG2E * vxx * idet;
       gs->rmx[t] = cx + m[1];

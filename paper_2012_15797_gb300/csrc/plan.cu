@@ -15,11 +15,16 @@ __device__ __forceinline__ int plan_key(const BatchView& b, int64_t i, int suppo
   return bk * MOG_MAX_PSFS + psf;
 }
 
+// Lanes of a warp with equal keys add once (one atomic per distinct key).
 __global__ void plan_histogram(BatchView b, int64_t count, int supported, int32_t* hist, int* status) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    const int key = plan_key(b, i, supported);
-    if (key < 0) set_status(status, MOG_ERR_DEVICE);
-    else atomicAdd(&hist[key], 1);
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const int key = i < count ? plan_key(b, i, supported) : -2;
+    if (key == -1) set_status(status, MOG_ERR_DEVICE);
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[key], __popc(peers));
   }
 }
 
@@ -74,9 +79,17 @@ __global__ void __launch_bounds__(1024) plan_scan(int32_t* hist, int32_t* key_of
 }
 
 __global__ void plan_scatter(BatchView b, int64_t count, int supported, int32_t* key_off, int32_t* order) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    const int key = plan_key(b, i, supported);
-    if (key >= 0) order[atomicAdd(&key_off[key], 1)] = (int32_t)i;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const int key = i < count ? plan_key(b, i, supported) : -2;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    int32_t pos = 0;
+    if (key >= 0 && lane == leader) pos = atomicAdd(&key_off[key], __popc(peers));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (key >= 0) order[pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
   }
 }
 

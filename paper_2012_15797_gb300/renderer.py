@@ -25,6 +25,15 @@ class DeviceBatch:
     def ptrs(self):
         return {k: v.data_ptr() for k, v in self.tensors.items()}
 
+    def size_mask(self):
+        m = 0
+        for n in np.unique(self.sizes):
+            b = {32: 0, 64: 1, 128: 2, 256: 3}.get(int(n))
+            if b is None:
+                return 0
+            m |= 1 << b
+        return m
+
 
 def pack_offsets(sizes):
     sizes = np.asarray(sizes, dtype=np.int64)
@@ -84,7 +93,7 @@ class Renderer:
         if out is None:
             out = torch.empty(batch.total, dtype=torch.float32, device=self.device)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
-        b = capi.make_batch(batch.count, batch.ptrs())
+        b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
         capi.mog_render_batch(self.ctx, b, out.data_ptr(), s.cuda_stream)
         return out
 
