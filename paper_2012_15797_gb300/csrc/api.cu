@@ -20,6 +20,7 @@ struct mog_ctx {
   int* d_status = nullptr;
   PlanScratch plan{};
   int64_t order_cap = 0;
+  unsigned char* records = nullptr;   // RECORD_BYTES per planned galaxy
   double2* d_dft_scratch = nullptr;
   std::string last_error;
   // measurement hooks
@@ -80,9 +81,12 @@ mog_status ensure_order_capacity(mog_ctx* ctx, int64_t count) {
   int64_t cap = ctx->order_cap ? ctx->order_cap : 1024;
   while (cap < count) cap *= 2;
   if (ctx->plan.order) MOG_CUDA(ctx, cudaFree(ctx->plan.order));
+  if (ctx->records) MOG_CUDA(ctx, cudaFree(ctx->records));
   ctx->plan.order = nullptr;
+  ctx->records = nullptr;
   ctx->order_cap = 0;
   MOG_CUDA(ctx, cudaMalloc(&ctx->plan.order, sizeof(int32_t) * cap));
+  MOG_CUDA(ctx, cudaMalloc(&ctx->records, (size_t)RECORD_BYTES * cap));
   ctx->order_cap = cap;
   return MOG_OK;
 }
@@ -133,6 +137,7 @@ mog_status mog_destroy_context(mog_ctx* ctx) {
   cudaFree(ctx->plan.key_off);
   cudaFree(ctx->plan.small);
   cudaFree(ctx->plan.order);
+  cudaFree(ctx->records);
   cudaFree(ctx->d_dft_scratch);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
@@ -264,7 +269,9 @@ mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, vo
   p.bucket_start = ctx->plan.small;
   p.bucket_count = ctx->plan.small + NBUCKET;
   p.queue = ctx->plan.small + 2 * NBUCKET;
+  p.records = ctx->records;
   p.status = ctx->d_status;
+  MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ctx->records, s));
   const uint32_t want = batch->size_mask ? (batch->size_mask & SUPPORTED_BUCKETS) : SUPPORTED_BUCKETS;
   for (int b = 0; b < NBUCKET; ++b) {
     if (!((want >> b) & 1)) continue;

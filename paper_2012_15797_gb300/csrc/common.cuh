@@ -137,6 +137,9 @@ template <> struct Radix<64> { static constexpr int P = 2; static constexpr int 
 template <> struct Radix<128> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 2}; };
 template <> struct Radix<256> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 4}; };
 
+// Work rows hold one length-N transform each, padded to N + N/8 float2 with
+// the index map i + i/8, which spreads the stride-8 accesses of the passes
+// over the banks at the cost of one add per access.
 template <int N>
 __device__ __forceinline__ int swz(int i) { return i + (i >> 3); }
 
@@ -163,17 +166,17 @@ __device__ __forceinline__ void fill_twiddles(float2* t, int ns, int tid, int nt
 
 // Input of a pass after the first: gather + twiddle + R-point DFTs into v[8].
 template <int N, int R, int S>
-__device__ __forceinline__ void stockham_load(const float2* buf, int j, const float2* twt, float2* v) {
+__device__ __forceinline__ void stockham_load(const float2* w, int j, const float2* twt, float2* v) {
   constexpr int NB = 8 / R;
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = j + q * (N / 8);
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      float2 x = buf[swz<N>(b + m * (N / R))];
+      float2 x = w[swz<N>(b + m * (N / R))];
       if (m > 0) {
-        const float2 w = twt[(m - 1) * (N / R) + b];
-        x = (S > 0) ? cmul(x, w) : cmulc(x, w);
+        const float2 t = twt[(m - 1) * (N / R) + b];
+        x = (S > 0) ? cmul(x, t) : cmulc(x, t);
       }
       v[q * R + m] = x;
     }
@@ -189,12 +192,12 @@ __device__ __forceinline__ int stockham_out_index(int j, int ns, int q, int m) {
 }
 
 template <int N, int R>
-__device__ __forceinline__ void stockham_store(float2* buf, int j, int ns, const float2* v) {
+__device__ __forceinline__ void stockham_store(float2* w, int j, int ns, const float2* v) {
   constexpr int NB = 8 / R;
 #pragma unroll
   for (int q = 0; q < NB; ++q)
 #pragma unroll
-    for (int m = 0; m < R; ++m) buf[swz<N>(stockham_out_index<N, R>(j, ns, q, m))] = v[q * R + m];
+    for (int m = 0; m < R; ++m) w[swz<N>(stockham_out_index<N, R>(j, ns, q, m))] = v[q * R + m];
 }
 
 // ------------------------------------------------------------------------
@@ -251,23 +254,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 // ------------------------------------------------------------------------
 // Steps 3-4 for one galaxy: pixel covariance S (Appendix A with CD = I), the
-// interpolated mixture (Section 3), the aliasing split and ramp, and the
-// compacted Fourier / real-space term lists.
+// interpolated mixture (Section 3), the aliasing split and ramp.  A prologue
+// kernel writes one 256-byte record per planned galaxy; the render kernels
+// prefetch the next record with a bulk copy while rendering the current one.
 // ------------------------------------------------------------------------
-struct GalaxySetup {
-  int ok;             // 0: skip this galaxy (error recorded)
-  int nf, nr;         // Fourier components, real-space terms
+struct __align__(16) GalaxyRecord {
+  int ok;              // 0: skip this galaxy (error recorded)
+  int nf, nrc;         // Fourier components, real-space components
   int psf;
-  float s11, s12, s22;
-  float x, y;         // offset from the patch centre
+  float s11, s12, s22; // S (pixel covariance per unit profile variance)
   float flux;
+  float x, y;          // offset from the patch centre
+  int64_t gal;         // index of the galaxy in the batch
+  int64_t off;         // element offset of its patch in the output
   // Fourier components: amplitude flux a_i w_F / N^2, exponent -2 pi^2 v_i log2(e)
   float famp[KMAX], fcoef[KMAX];
-  // Real-space terms (component i, PSF component j):
-  // rw * 2^(qa dx^2 + qb dx dy + qc dy^2), (dx, dy) = pixel - (mx, my);
-  // rrr = 2^(2 qa) steps the ratio of neighbouring pixels along a row
-  float rw[RMAX], rqa[RMAX], rqb[RMAX], rqc[RMAX], rmx[RMAX], rmy[RMAX], rrr[RMAX];
+  // real-space components: amplitude flux a_i (1 - w_F), profile variance v_i
+  float ramp[KMAX], rvar[KMAX];
 };
+static_assert(sizeof(GalaxyRecord) == 256, "record layout");
+constexpr int RECORD_BYTES = 256;   // stride of the record array (16-byte multiple)
 
 struct BatchView {
   const float *flux, *x, *y, *log_re, *e1, *e2, *sersic_n;
@@ -280,9 +286,9 @@ __device__ __forceinline__ float ramp_weight(float ns) {
   return t * t * (3.0f - 2.0f * t);
 }
 
-// Executed by one full warp; writes `gs` (shared memory).
-__device__ inline void galaxy_setup_warp(const BatchView& b, int64_t g, int n, const DevProfile* profiles,
-                                         const DevPsf* psfs, int* status, GalaxySetup* gs) {
+// Executed by one full warp (lane = mixture component); writes *out.
+__device__ inline void galaxy_record_warp(const BatchView& b, int64_t g, int n, const DevProfile* profiles,
+                                          const DevPsf* psfs, int* status, GalaxyRecord* out) {
   const int lane = threadIdx.x & 31;
   const float flux = b.flux[g], x = b.x[g], y = b.y[g], lre = b.log_re[g];
   const float e1 = b.e1[g], e2 = b.e2[g], sn = b.sersic_n[g];
@@ -292,14 +298,16 @@ __device__ inline void galaxy_setup_warp(const BatchView& b, int64_t g, int n, c
             isfinite(sn) && e < 1.0f && lre < 30.0f;
   ok = ok && prof >= 0 && prof < MOG_MAX_PROFILES && pid >= 0 && pid < MOG_MAX_PSFS;
   const DevProfile* P = ok ? &profiles[prof] : nullptr;
-  const DevPsf* Q = ok ? &psfs[pid] : nullptr;
-  ok = ok && P->n_nodes > 0 && Q->k > 0;
+  ok = ok && P->n_nodes > 0 && psfs[pid].k > 0;
+  const int64_t off = b.offset[g];
+  ok = ok && (off & 3) == 0;   // patches are stored as aligned float4 rows
   if (!ok) {
     if (lane == 0) {
       set_status(status, MOG_ERR_DEVICE);
-      gs->ok = 0;
+      out->ok = 0;
+      out->gal = g;
+      out->off = off;
     }
-    __syncwarp();
     return;
   }
   // S = r^2 [ (1+b^2)/2 I + (b^2-1)/2 R ],  R = [[e1/e, -e2/e], [-e2/e, -e1/e]]
@@ -336,41 +344,55 @@ __device__ inline void galaxy_setup_warp(const BatchView& b, int64_t g, int n, c
   const float inv_n2 = 1.0f / ((float)n * (float)n);
   if (four) {
     const int p = __popc(mf & lt);
-    gs->famp[p] = flux * a * wf * inv_n2;
-    gs->fcoef[p] = -2.0f * PI_F * PI_F * v * LOG2E;
+    out->famp[p] = flux * a * wf * inv_n2;
+    out->fcoef[p] = -2.0f * PI_F * PI_F * v * LOG2E;
   }
-  const int kp = Q->k;
   if (real) {
     const int p = __popc(mr & lt);
-    const float cx = 0.5f * (float)n + x, cy = 0.5f * (float)n + y;
-    for (int jj = 0; jj < kp; ++jj) {
-      const float* m = Q->mog[jj];
-      const float vxx = v * s11 + m[3], vxy = v * s12 + m[4], vyy = v * s22 + m[5];
-      const float det = vxx * vyy - vxy * vxy;
-      const float idet = 1.0f / det;
-      const int t = p * kp + jj;
-      gs->rw[t] = flux * a * (1.0f - wf) * m[0] * rsqrtf(det) * (0.5f / PI_F);
-      gs->rqa[t] = -0.5f * LOG2E * vyy * idet;
-      gs->rrr[t] = ex2(-LOG2E * vyy * idet);
-      gs->rqb[t] = LOG2E * vxy * idet;
-      gs->rqc[t] = -0.5f * LOG2E * vxx * idet;
-      gs->rmx[t] = cx + m[1];
-      gs->rmy[t] = cy + m[2];
-    }
+    out->ramp[p] = flux * a * (1.0f - wf);
+    out->rvar[p] = v;
   }
   if (lane == 0) {
-    gs->ok = 1;
-    gs->nf = __popc(mf);
-    gs->nr = __popc(mr) * kp;
-    gs->psf = pid;
-    gs->s11 = s11;
-    gs->s12 = s12;
-    gs->s22 = s22;
-    gs->x = x;
-    gs->y = y;
-    gs->flux = flux;
+    out->ok = 1;
+    out->nf = __popc(mf);
+    out->nrc = __popc(mr);
+    out->psf = pid;
+    out->s11 = s11;
+    out->s12 = s12;
+    out->s22 = s22;
+    out->flux = flux;
+    out->x = x;
+    out->y = y;
+    out->gal = g;
+    out->off = off;
   }
-  __syncwarp();
+}
+
+// Real-space terms of a galaxy: component c of the galaxy convolved with
+// component j of the PSF mixture is rw * 2^(qa dx^2 + qb dx dy + qc dy^2) at
+// (dx, dy) = pixel - (mx, my); rrr = 2^(2 qa) steps the ratio of neighbouring
+// pixels along a row.
+struct RealTerms {
+  float rw[RMAX], rqa[RMAX], rqb[RMAX], rqc[RMAX], rmx[RMAX], rmy[RMAX], rrr[RMAX];
+};
+
+// Term t = c * kpsf + j, computed by one thread.  psf_mog rows are
+// (weight, mean x, mean y, vxx, vxy, vyy).
+__device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*psf_mog)[6], int kpsf, int n, int t,
+                                          RealTerms* rt) {
+  const int c = t / kpsf, jj = t - c * kpsf;
+  const float* m = psf_mog[jj];
+  const float v = r.rvar[c];
+  const float vxx = v * r.s11 + m[3], vxy = v * r.s12 + m[4], vyy = v * r.s22 + m[5];
+  const float det = vxx * vyy - vxy * vxy;
+  const float idet = 1.0f / det;
+  rt->rw[t] = r.ramp[c] * m[0] * rsqrtf(det) * (0.5f / PI_F);
+  rt->rqa[t] = -0.5f * LOG2E * vyy * idet;
+  rt->rrr[t] = ex2(-LOG2E * vyy * idet);
+  rt->rqb[t] = LOG2E * vxy * idet;
+  rt->rqc[t] = -0.5f * LOG2E * vxx * idet;
+  rt->rmx[t] = 0.5f * (float)n + r.x + m[1];
+  rt->rmy[t] = 0.5f * (float)n + r.y + m[2];
 }
 
 }  // namespace mog

@@ -18,6 +18,7 @@ struct RenderParams {
   const int32_t* bucket_start;  // [NBUCKET] first position in `order`
   const int32_t* bucket_count;  // [NBUCKET]
   int32_t* queue;               // [NBUCKET] work counters, zeroed by the planner
+  const unsigned char* records; // RECORD_BYTES per planned position (GalaxyRecord)
   int* status;
 };
 
@@ -33,6 +34,9 @@ struct PlanScratch {
 // reported through the status word and skipped.
 cudaError_t launch_plan(const BatchView& b, int64_t count, const PlanScratch& ps, int supported, int* status,
                         cudaStream_t s);
+
+// Writes the GalaxyRecord of every planned position (Steps 3-4).
+cudaError_t launch_galaxy_prep(const RenderParams& p, int64_t count, unsigned char* records, cudaStream_t s);
 
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, cudaStream_t s);
 size_t render_fwd_smem(int n);

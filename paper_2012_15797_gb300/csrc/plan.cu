@@ -93,6 +93,23 @@ __global__ void plan_scatter(BatchView b, int64_t count, int supported, int32_t*
   }
 }
 
+// One warp per planned position (lane = mixture component).
+__global__ void galaxy_prep(RenderParams p, unsigned char* records) {
+  const int total = p.bucket_start[NBUCKET - 1] + p.bucket_count[NBUCKET - 1];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int pos = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pos < total; pos += warps) {
+    const int64_t g = p.order[pos];
+    galaxy_record_warp(p.b, g, p.b.size[g], p.profiles, p.psfs, p.status,
+                       reinterpret_cast<GalaxyRecord*>(records + (size_t)pos * RECORD_BYTES));
+  }
+}
+
+cudaError_t launch_galaxy_prep(const RenderParams& p, int64_t count, unsigned char* records, cudaStream_t s) {
+  const int64_t blocks = (count + 7) / 8;
+  galaxy_prep<<<(int)(blocks < 8192 ? (blocks > 0 ? blocks : 1) : 8192), 256, 0, s>>>(p, records);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_plan(const BatchView& b, int64_t count, const PlanScratch& ps, int supported, int* status,
                         cudaStream_t s) {
   static_assert(NKEY % 1024 == 0, "scan assumes NKEY multiple of 1024");

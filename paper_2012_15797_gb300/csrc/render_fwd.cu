@@ -2,7 +2,9 @@
 // launch.  One CTA renders one galaxy at a time and loops over a dynamic
 // queue of galaxies of its size bucket (grouped by PSF by the planner):
 //
-//   set-up (warp 0)   S, mixture at n, aliasing split, term lists (Steps 3-4)
+//   record            the galaxy's Steps 3-4 (S, mixture at n, aliasing split),
+//                     written by the prologue kernel and bulk-copied (TMA)
+//                     into a double buffer one galaxy ahead
 //   PSF spectrum      bulk (TMA) copy into shared memory when the PSF changes
 //   Fourier MoG       M(nu, om) P(nu, om) phase(nu) phase(om), evaluated by
 //                     the thread that owns the bin in the first FFT pass
@@ -38,7 +40,7 @@ struct FwdCfg {
   static constexpr int TW1 = twiddle_elems<N, R1>();
   static constexpr int TW2 = Radix<N>::P == 3 ? twiddle_elems<N, (R2 > 1 ? R2 : 2)>() : 0;
   static constexpr int MIN_BLOCKS = N == 32 ? 16 : N == 64 ? 3 : 1;
-  static constexpr int CHUNK = 4;
+  static constexpr int CHUNK = 8;
 
   static constexpr size_t off_psf = 0;
   static constexpr size_t off_wa = off_psf + sizeof(float2) * PSF_ELEMS;
@@ -46,9 +48,11 @@ struct FwdCfg {
   static constexpr size_t off_tw = off_wb + sizeof(float2) * W_ELEMS;
   static constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
   static constexpr size_t off_py = off_px + sizeof(float2) * H;
-  static constexpr size_t off_gs = (off_py + sizeof(float2) * N + 15) & ~size_t(15);
-  static constexpr size_t off_bar = (off_gs + sizeof(GalaxySetup) + 15) & ~size_t(15);
-  static constexpr size_t SMEM = off_bar + 16;
+  static constexpr size_t off_nyq = off_py + sizeof(float2) * N;
+  static constexpr size_t off_rec = (off_nyq + sizeof(float2) * N + 15) & ~size_t(15);
+  static constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);
+  static constexpr size_t off_bar = (off_rt + sizeof(RealTerms) + 15) & ~size_t(15);
+  static constexpr size_t SMEM = off_bar + 3 * sizeof(uint64_t);
 };
 
 // Passes after the first of an FFT held in row `w` of the work buffer; the
@@ -79,6 +83,8 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   constexpr int TPF = C::TPF, WS = C::WS, LS = C::LS;
   constexpr int B = bucket_of(N);
   constexpr float INV_N = 1.0f / N;
+  // a Fourier component is skipped over a warp's bins when 2^(c q) < 2^-40
+  constexpr float NEGLIGIBLE_LOG2 = -40.0f;
   extern __shared__ __align__(128) unsigned char smem[];
   float2* psf_hat = reinterpret_cast<float2*>(smem + C::off_psf);
   float2* WA = reinterpret_cast<float2*>(smem + C::off_wa);
@@ -87,240 +93,255 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   float2* tw2 = tw1 + C::TW1;
   float2* px = reinterpret_cast<float2*>(smem + C::off_px);
   float2* py = reinterpret_cast<float2*>(smem + C::off_py);
-  GalaxySetup& gs = *reinterpret_cast<GalaxySetup*>(smem + C::off_gs);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);
-  __shared__ int s_item;
+  float2* nyq = reinterpret_cast<float2*>(smem + C::off_nyq);
+  GalaxyRecord* rec = reinterpret_cast<GalaxyRecord*>(smem + C::off_rec);
+  RealTerms& rt = *reinterpret_cast<RealTerms*>(smem + C::off_rt);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);   // [0] PSF, [1..2] records
+  __shared__ int s_pos[2];
+  __shared__ float s_psf_mog[KPSF][6];
+  __shared__ int s_kpsf;
 
   const int tid = threadIdx.x;
   const int f = tid / TPF, j = tid % TPF;
   fill_twiddles<N, C::R1>(tw1, 8, tid, C::THREADS);
   if constexpr (Radix<N>::P == 3) fill_twiddles<N, C::R2>(tw2, N / C::R2, tid, C::THREADS);
-  if (tid == 0) mbar_init(bar, 1);
-  int cur_psf = -1;
-  uint32_t parity = 0;
   const int count = p.bucket_count[B];
-  const int start = p.bucket_start[B];
+  const unsigned char* records = p.records + (size_t)p.bucket_start[B] * RECORD_BYTES;
+  // work queue, used by thread 0 only: positions are taken CHUNK at a time and
+  // the next chunk is requested one chunk ahead, so the atomic's latency is
+  // off the critical path
+  int q_next = 0, q_end = 0, q_ahead = 0;
+  auto next_position = [&]() -> int {
+    if (q_next >= q_end) {
+      const int b0 = q_ahead;
+      if (b0 >= count) return -1;
+      q_next = b0;
+      q_end = min(b0 + C::CHUNK, count);
+      q_ahead = atomicAdd(&p.queue[B], C::CHUNK);
+    }
+    return q_next++;
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init(&bar[2], 1);
+    q_ahead = atomicAdd(&p.queue[B], C::CHUNK);
+    const int p0 = next_position();
+    s_pos[0] = p0;
+    if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1]);
+  }
   float2* wa = WA + f * WS;   // this group's row in pass A
   float2* wb = WB + f * WS;   // this group's row in pass B
-  __syncthreads();
+  int cur_psf = -1;
+  uint32_t psf_parity = 0, rec_parity = 0;   // rec_parity bit b: phase of record buffer b
 
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(&p.queue[B], C::CHUNK);
-    __syncthreads();
-    const int base = s_item;
-    if (base >= count) break;
-    const int end = min(base + C::CHUNK, count);
-    for (int it = base; it < end; ++it) {
-      const int64_t g = p.order[start + it];
-      __syncthreads();  // S1: the previous galaxy is fully stored
-      if (tid < 32) galaxy_setup_warp(p.b, g, N, p.profiles, p.psfs, p.status, &gs);
-      {
-        const float gx = p.b.x[g], gy = p.b.y[g];
-        for (int i = tid; i < C::H + N; i += C::THREADS) {
-          float s, c;
-          if (i < C::H) {
-            sincospif(-2.0f * gx * (float)i * INV_N, &s, &c);
-            px[i] = make_float2(c, s);
+  for (int buf = 0;; buf ^= 1) {
+    __syncthreads();  // S1: the previous galaxy is fully stored; s_pos[buf] is visible
+    const int pos = s_pos[buf];
+    if (pos < 0) break;
+    if (tid == 0) {
+      const int np = next_position();
+      s_pos[buf ^ 1] = np;
+      if (np >= 0)
+        bulk_load(&rec[buf ^ 1], records + (size_t)np * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1 + (buf ^ 1)]);
+    }
+    const bool rec_landed = mbar_wait(&bar[1 + buf], (rec_parity >> buf) & 1u);
+    rec_parity ^= 1u << buf;
+    const GalaxyRecord& r = rec[buf];
+    const bool need_psf = rec_landed && r.ok && r.psf != cur_psf;
+    bool psf_landed = true;
+    if (need_psf) {   // uniform: every thread reads the same record
+      if (tid == 0) bulk_load(psf_hat, p.psfs[r.psf].spec[B], sizeof(float2) * C::PSF_ELEMS, &bar[0]);
+      if (tid < KPSF * 6) s_psf_mog[tid / 6][tid % 6] = p.psfs[r.psf].mog[tid / 6][tid % 6];
+      if (tid == 0) s_kpsf = p.psfs[r.psf].k;
+      psf_landed = mbar_wait(&bar[0], psf_parity);
+      psf_parity ^= 1u;
+      cur_psf = r.psf;
+    }
+    if (__syncthreads_or(!rec_landed || !psf_landed)) {
+      if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
+      return;
+    }
+    if (!r.ok) continue;
+    float* dst = p.out + r.off;
+
+    // per-galaxy tables: shift phases, the nu = 1/2 column of the spectrum
+    // (needed at +omega and -omega by the packed transform) and the
+    // real-space terms, spread over the CTA as one task list
+    {
+      const float gx = r.x, gy = r.y;
+      const int kp = s_kpsf;
+      const int ntask = C::H + 2 * N + r.nrc * kp;
+      for (int i = tid; i < ntask; i += C::THREADS) {
+        float sn, cs;
+        if (i < C::H) {
+          sincospif(-2.0f * gx * (float)i * INV_N, &sn, &cs);
+          px[i] = make_float2(cs, sn);
+        } else if (i < C::H + N) {
+          const int l = i - C::H;
+          sincospif(-2.0f * gy * (float)(l < N / 2 ? l : l - N) * INV_N, &sn, &cs);
+          py[l] = make_float2(cs, sn);
+        } else if (i < C::H + 2 * N) {
+          const int l = i - C::H - N;
+          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+          const float q = fmaf(om, fmaf(r.s22, om, r.s12), 0.25f * r.s11);
+          float acc = 0.0f;
+          for (int c = 0; c < r.nf; ++c) acc = fmaf(r.famp[c], ex2(r.fcoef[c] * q), acc);
+          float sy, cy;
+          sincospif(-2.0f * gy * om, &sy, &cy);
+          sincospif(-gx, &sn, &cs);
+          nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(make_float2(cs, sn), make_float2(cy, sy))), acc);
+        } else {
+          real_term(r, s_psf_mog, kp, N, i - C::H - 2 * N, &rt);
+        }
+      }
+    }
+    __syncthreads();  // S2
+
+    // ---- Steps 5-6: Fourier mixture times PSF spectrum and phase, in registers ----
+    const int nf = r.nf;
+    const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
+    float2 v[8];
+    {
+      // column nu = f / N (group 0: nu = 0), 8 bins per thread
+      const float nu = f * INV_N;
+      const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
+      float q[8], s[8];
+      float qmin = 3.4e38f;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int l = j + m * TPF;
+        const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+        q[m] = fmaf(om, fmaf(s22, om, a1), a0);
+        qmin = fminf(qmin, q[m]);
+        s[m] = 0.0f;
+      }
+      for (int i = 0; i < nf; ++i) {
+        const float a = r.famp[i], c = r.fcoef[i];
+        if (!__any_sync(0xffffffffu, c * qmin > NEGLIGIBLE_LOG2)) continue;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) s[m] = fmaf(a, ex2(c * q[m]), s[m]);
+      }
+      const float2 pxf = px[f];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int l = j + m * TPF;
+        v[m] = cscale(cmul(psf_hat[f * LS + l], cmul(pxf, py[l])), s[m]);
+      }
+    }
+    if (f == 0) {
+      // Pack the Hermitian parts of the nu = 0 and nu = 1/2 columns as
+      // re + i im.  The nu = 0 column is Hermitian in omega by construction
+      // (its self-conjugate bin l = N/2 keeps its real part); the nu = 1/2
+      // column is symmetrised from both signs of omega.
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int l = j + m * TPF;
+        const float2 dc = (l == N / 2) ? make_float2(v[m].x, 0.0f) : v[m];
+        const float2 a = nyq[l], b = nyq[(N - l) & (N - 1)];
+        const float2 hn = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+        v[m] = make_float2(dc.x - hn.y, dc.y + hn.x);
+      }
+    }
+
+    // ---- Step 7a: inverse FFT of every column along omega ----
+    dft8<+1>(v);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) wa[swz<N>(8 * j + m)] = v[m];
+    __syncwarp();
+    fft_rest<N, +1>(wa, j, tw1, tw2, v);
+    {
+      // rows 2p (even lane) and 2p+1 (odd lane): Z_p[k] = A + iB and
+      // Z_p[N-k] = conj(A) + i conj(B) feed the row transform of pair p
+      constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
+      const bool odd = j & 1;
+#pragma unroll
+      for (int q = 0; q < 8 / R; ++q)
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const float2 mine = v[q * R + m];
+          float2 other;
+          other.x = __shfl_xor_sync(0xffffffffu, mine.x, 1);
+          other.y = __shfl_xor_sync(0xffffffffu, mine.y, 1);
+          const float2 A = odd ? other : mine, Bv = odd ? mine : other;
+          const int pr = stockham_out_index<N, R>(j, NS, q, m) >> 1;
+          float2* row = WB + pr * WS;
+          if (f > 0) {
+            if (!odd) row[swz<N>(f)] = make_float2(A.x - Bv.y, A.y + Bv.x);
+            else row[swz<N>(N - f)] = make_float2(A.x + Bv.y, Bv.x - A.y);
           } else {
-            const int l = i - C::H;
-            sincospif(-2.0f * gy * (float)(l < N / 2 ? l : l - N) * INV_N, &s, &c);
-            py[l] = make_float2(c, s);
+            if (!odd) row[swz<N>(0)] = make_float2(A.x, Bv.x);
+            else row[swz<N>(N / 2)] = make_float2(A.y, Bv.y);
           }
         }
-      }
-      __syncthreads();  // S2
-      if (!gs.ok) continue;
-      float* dst = p.out + p.b.offset[g];
-      if (reinterpret_cast<uintptr_t>(dst) & 15) {
-        if (tid == 0) set_status(p.status, MOG_ERR_DEVICE);
-        continue;
-      }
-      if (gs.psf != cur_psf) {
-        const float2* src = p.psfs[gs.psf].spec[B];
-        if (tid == 0) bulk_load(psf_hat, src, sizeof(float2) * C::PSF_ELEMS, bar);
-        const bool landed = mbar_wait(bar, parity);
-        parity ^= 1u;
-        if (__syncthreads_or(!landed)) {
-          if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
-          return;
-        }
-        cur_psf = gs.psf;
-      }
+    }
+    __syncthreads();  // S3: every column has been transformed
 
-      // ---- Steps 5-6: Fourier mixture times PSF spectrum and phase, in registers ----
-      const int nf = gs.nf;
-      const float s11 = gs.s11, s12x2 = 2.0f * gs.s12, s22 = gs.s22;
-      float2 v[8];
-      if (f > 0) {
-        const float nu = f * INV_N;
-        const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
-        float q[8], s[8];
+    // ---- Step 7b: real inverse FFT of row pairs (2f, 2f + 1) along nu ----
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int l = j + m * TPF;
-          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
-          q[m] = fmaf(om, fmaf(s22, om, a1), a0);
-          s[m] = 0.0f;
-        }
-        for (int i = 0; i < nf; ++i) {
-          const float a = gs.famp[i], c = gs.fcoef[i];
+    for (int m = 0; m < 8; ++m) v[m] = wb[swz<N>(j + m * TPF)];
+    dft8<+1>(v);
+    __syncwarp();
 #pragma unroll
-          for (int m = 0; m < 8; ++m) s[m] = fmaf(a, ex2(c * q[m]), s[m]);
-        }
-        const float2 pxf = px[f];
+    for (int m = 0; m < 8; ++m) wb[swz<N>(8 * j + m)] = v[m];
+    __syncwarp();
+    fft_rest<N, +1>(wb, j, tw1, tw2, v);
+    __syncwarp();
+    {
+      // rows 2f and 2f+1 of the patch overwrite this transform's own row
+      constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
+      float* orow = reinterpret_cast<float*>(wb);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int l = j + m * TPF;
-          v[m] = cscale(cmul(psf_hat[f * LS + l], cmul(pxf, py[l])), s[m]);
-        }
-      } else {
-        // nu = 0 and nu = 1/2 columns; their Hermitian parts are packed as
-        // re + i im.  The value at -l comes from the lane that owns -l.
-        constexpr float NUQ = 0.5f;
-        const float b0 = s11 * NUQ * NUQ, b1 = s12x2 * NUQ;
-        float qd[8], qn[8], sd[8], sn[8];
+      for (int q = 0; q < 8 / R; ++q)
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int l = j + m * TPF;
-          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
-          qd[m] = s22 * om * om;
-          qn[m] = fmaf(om, fmaf(s22, om, b1), b0);
-          sd[m] = 0.0f;
-          sn[m] = 0.0f;
+        for (int m = 0; m < R; ++m) {
+          const int n = stockham_out_index<N, R>(j, NS, q, m);
+          orow[n] = v[q * R + m].x;
+          orow[N + n] = v[q * R + m].y;
         }
-        for (int i = 0; i < nf; ++i) {
-          const float a = gs.famp[i], c = gs.fcoef[i];
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            sd[m] = fmaf(a, ex2(c * qd[m]), sd[m]);
-            sn[m] = fmaf(a, ex2(c * qn[m]), sn[m]);
-          }
-        }
-        float2 xd[8], xn[8];
-        const float2 p0 = px[0], pn = px[N / 2];
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int l = j + m * TPF;
-          xd[m] = cscale(cmul(psf_hat[l], cmul(p0, py[l])), sd[m]);
-          xn[m] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(pn, py[l])), sn[m]);
-        }
-        constexpr unsigned GMASK = (TPF >= 32) ? 0xffffffffu : ((1u << TPF) - 1u);
-        const int src = (TPF - j) & (TPF - 1);  // lane owning -l (group 0 starts at lane 0)
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          // lane j serves lane (TPF - j) mod TPF, which wants register 7-m
-          // (or (8-m) mod 8 when that lane is 0)
-          const float2 sdv = (j != 0) ? xd[7 - m] : xd[(8 - m) & 7];
-          const float2 snv = (j != 0) ? xn[7 - m] : xn[(8 - m) & 7];
-          float2 dneg, nneg;
-          dneg.x = __shfl_sync(GMASK, sdv.x, src);
-          dneg.y = __shfl_sync(GMASK, sdv.y, src);
-          nneg.x = __shfl_sync(GMASK, snv.x, src);
-          nneg.y = __shfl_sync(GMASK, snv.y, src);
-          const float2 hd = make_float2(0.5f * (xd[m].x + dneg.x), 0.5f * (xd[m].y - dneg.y));
-          const float2 hn = make_float2(0.5f * (xn[m].x + nneg.x), 0.5f * (xn[m].y - nneg.y));
-          v[m] = make_float2(hd.x - hn.y, hd.y + hn.x);
-        }
-      }
+    }
+    __syncthreads();  // S4
 
-      // ---- Step 7a: inverse FFT of every column along omega ----
-      dft8<+1>(v);
+    // ---- Step 8: add the real-space terms and store ----
+    // Along a row a Gaussian term is 2^(E(dx)) with E quadratic in dx, so
+    // over 8 consecutive pixels g(dx+1) = g(dx) r(dx), r(dx+1) = r(dx) R8 with
+    // R8 = 2^(2 qa): two ex2 per 8 pixels.  Real-space terms are wide
+    // (n_sigma < 4), so a start value that underflows stays negligible.
+    const int nr = r.nrc * s_kpsf;
+    for (int idx = tid; idx < N * N / 8; idx += C::THREADS) {
+      const int yy = idx / (N / 8);
+      const int x0 = (idx % (N / 8)) * 8;
+      const float* orow = reinterpret_cast<const float*>(WB + (yy >> 1) * WS) + (yy & 1) * N + x0;
+      float4 o0 = *reinterpret_cast<const float4*>(orow);
+      float4 o1 = *reinterpret_cast<const float4*>(orow + 4);
+      if (nr > 0) {
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int t = 0; t < nr; ++t) {
+          const float qa = rt.rqa[t], dy = (float)yy - rt.rmy[t], dx = (float)x0 - rt.rmx[t];
+          const float ly = dy * rt.rqb[t];
+          const float e0 = fmaf(dx, fmaf(qa, dx, ly), rt.rqc[t] * dy * dy);
+          float g = rt.rw[t] * ex2(e0);
+          float rr = ex2(fmaf(qa, fmaf(2.0f, dx, 1.0f), ly));
+          const float r8 = rt.rrr[t];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) wa[swz<N>(8 * j + m)] = v[m];
-      __syncwarp();
-      fft_rest<N, +1>(wa, j, tw1, tw2, v);
-      {
-        // rows 2p (even lane) and 2p+1 (odd lane): Z_p[k] = A + iB and
-        // Z_p[N-k] = conj(A) + i conj(B) feed the row transform of pair p
-        constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
-        const bool odd = j & 1;
-#pragma unroll
-        for (int q = 0; q < 8 / R; ++q)
-#pragma unroll
-          for (int m = 0; m < R; ++m) {
-            const float2 mine = v[q * R + m];
-            float2 other;
-            other.x = __shfl_xor_sync(0xffffffffu, mine.x, 1);
-            other.y = __shfl_xor_sync(0xffffffffu, mine.y, 1);
-            const float2 A = odd ? other : mine, Bv = odd ? mine : other;
-            const int pr = stockham_out_index<N, R>(j, NS, q, m) >> 1;
-            float2* row = WB + pr * WS;
-            if (f > 0) {
-              if (!odd) row[swz<N>(f)] = make_float2(A.x - Bv.y, A.y + Bv.x);
-              else row[swz<N>(N - f)] = make_float2(A.x + Bv.y, Bv.x - A.y);
-            } else {
-              if (!odd) row[swz<N>(0)] = make_float2(A.x, Bv.x);
-              else row[swz<N>(N / 2)] = make_float2(A.y, Bv.y);
-            }
+          for (int u = 0; u < 8; ++u) {
+            acc[u] += g;
+            g *= rr;
+            rr *= r8;
           }
-      }
-      __syncthreads();  // S3: every column has been transformed
-
-      // ---- Step 7b: real inverse FFT of row pairs (2f, 2f + 1) along nu ----
-#pragma unroll
-      for (int m = 0; m < 8; ++m) v[m] = wb[swz<N>(j + m * TPF)];
-      dft8<+1>(v);
-      __syncwarp();
-#pragma unroll
-      for (int m = 0; m < 8; ++m) wb[swz<N>(8 * j + m)] = v[m];
-      __syncwarp();
-      fft_rest<N, +1>(wb, j, tw1, tw2, v);
-      __syncwarp();
-      {
-        constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
-        float* orow = reinterpret_cast<float*>(wb);   // rows 2f and 2f+1 of the patch
-#pragma unroll
-        for (int q = 0; q < 8 / R; ++q)
-#pragma unroll
-          for (int m = 0; m < R; ++m) {
-            const int n = stockham_out_index<N, R>(j, NS, q, m);
-            orow[n] = v[q * R + m].x;
-            orow[N + n] = v[q * R + m].y;
-          }
-      }
-      __syncthreads();  // S4
-
-      // ---- Step 8: add the real-space terms and store ----
-      // Along a row a Gaussian term is 2^(E(dx)) with E quadratic in dx, so
-      // over 8 consecutive pixels g(dx+1) = g(dx) r(dx), r(dx+1) = r(dx) R8 with
-      // R8 = 2^(2 qa): two ex2 per 8 pixels.  Real-space terms are wide
-      // (n_sigma < 4), so a start value that underflows stays negligible.
-      const int nr = gs.nr;
-      for (int idx = tid; idx < N * N / 8; idx += C::THREADS) {
-        const int yy = idx / (N / 8);
-        const int x0 = (idx % (N / 8)) * 8;
-        const float* orow = reinterpret_cast<const float*>(WB + (yy >> 1) * WS) + (yy & 1) * N + x0;
-        float4 o0 = *reinterpret_cast<const float4*>(orow);
-        float4 o1 = *reinterpret_cast<const float4*>(orow + 4);
-        if (nr > 0) {
-          float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          for (int t = 0; t < nr; ++t) {
-            const float qa = gs.rqa[t], dy = (float)yy - gs.rmy[t], dx = (float)x0 - gs.rmx[t];
-            const float ly = dy * gs.rqb[t];
-            const float e0 = fmaf(dx, fmaf(qa, dx, ly), gs.rqc[t] * dy * dy);
-            float g = gs.rw[t] * ex2(e0);
-            float r = ex2(fmaf(qa, fmaf(2.0f, dx, 1.0f), ly));
-            const float rr = gs.rrr[t];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              acc[u] += g;
-              g *= r;
-              r *= rr;
-            }
-          }
-          o0.x += acc[0];
-          o0.y += acc[1];
-          o0.z += acc[2];
-          o0.w += acc[3];
-          o1.x += acc[4];
-          o1.y += acc[5];
-          o1.z += acc[6];
-          o1.w += acc[7];
         }
-        float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
-        d[0] = o0;
-        d[1] = o1;
+        o0.x += acc[0];
+        o0.y += acc[1];
+        o0.z += acc[2];
+        o0.w += acc[3];
+        o1.x += acc[4];
+        o1.y += acc[5];
+        o1.z += acc[6];
+        o1.w += acc[7];
       }
+      float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
+      d[0] = o0;
+      d[1] = o1;
     }
   }
 }
