@@ -138,6 +138,22 @@ mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id);
 mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
 
 /*
+ * Adjoint of mog_render_batch (gradients for model fitting; the paper's
+ * forward model of Section 2 differentiated analytically): for every galaxy
+ * of the batch, given grad_out = dL/d(patch pixel) laid out exactly like the
+ * output of mog_render_batch (device float32, 16-byte aligned), writes
+ * grad_params[6 g + k] = dL/d theta_k with theta = (flux, x, y, log_re, e1,
+ * e2) (device float32, 6 * count values).  The Fourier part contracts the
+ * forward real 2-D DFT of grad_out with the derivatives of Eq. onegaussian;
+ * the real-space part differentiates the Gaussian terms in pixel space; the
+ * aliasing ramp weights are differentiated too.  S(e1, e2) is not
+ * differentiable at e = 0; there the direction e1/e = 1 is used.
+ * Asynchronous on `stream`.
+ */
+mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out,
+                               float* grad_params, void* stream);
+
+/*
  * Kernel timing for measurement: while enabled, every render-kernel launch is
  * bracketed by CUDA events recorded on its own stream.  mog_read_timing
  * waits for the recorded events and returns, per patch side N = 32 << b

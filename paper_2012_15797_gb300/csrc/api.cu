@@ -21,6 +21,7 @@ struct mog_ctx {
   PlanScratch plan{};
   int64_t order_cap = 0;
   unsigned char* records = nullptr;   // RECORD_BYTES per planned galaxy
+  unsigned char* adj_records = nullptr;   // sizeof(AdjRecord) per planned galaxy
   double2* d_dft_scratch = nullptr;
   std::string last_error;
   // measurement hooks
@@ -82,11 +83,14 @@ mog_status ensure_order_capacity(mog_ctx* ctx, int64_t count) {
   while (cap < count) cap *= 2;
   if (ctx->plan.order) MOG_CUDA(ctx, cudaFree(ctx->plan.order));
   if (ctx->records) MOG_CUDA(ctx, cudaFree(ctx->records));
+  if (ctx->adj_records) MOG_CUDA(ctx, cudaFree(ctx->adj_records));
   ctx->plan.order = nullptr;
   ctx->records = nullptr;
+  ctx->adj_records = nullptr;
   ctx->order_cap = 0;
   MOG_CUDA(ctx, cudaMalloc(&ctx->plan.order, sizeof(int32_t) * cap));
   MOG_CUDA(ctx, cudaMalloc(&ctx->records, (size_t)RECORD_BYTES * cap));
+  MOG_CUDA(ctx, cudaMalloc(&ctx->adj_records, sizeof(AdjRecord) * cap));
   ctx->order_cap = cap;
   return MOG_OK;
 }
@@ -138,6 +142,7 @@ mog_status mog_destroy_context(mog_ctx* ctx) {
   cudaFree(ctx->plan.small);
   cudaFree(ctx->plan.order);
   cudaFree(ctx->records);
+  cudaFree(ctx->adj_records);
   cudaFree(ctx->d_dft_scratch);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
@@ -246,32 +251,41 @@ mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id) {
   return MOG_OK;
 }
 
-mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
-  if (!ctx) return MOG_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+mog_status check_batch(mog_ctx* ctx, const mog_batch* batch) {
   if (!batch || batch->count < 0) return fail(ctx, MOG_ERR_ARG, "null batch or negative count");
-  if (batch->count == 0) return MOG_OK;
   if (batch->count > INT32_MAX) return fail(ctx, MOG_ERR_ARG, "at most 2^31-1 galaxies per call");
-  if (!out || !batch->flux || !batch->x || !batch->y || !batch->log_re || !batch->e1 || !batch->e2 ||
-      !batch->sersic_n || !batch->profile || !batch->psf || !batch->size || !batch->offset)
+  if (batch->count > 0 && (!batch->flux || !batch->x || !batch->y || !batch->log_re || !batch->e1 || !batch->e2 ||
+                           !batch->sersic_n || !batch->profile || !batch->psf || !batch->size || !batch->offset))
     return fail(ctx, MOG_ERR_ARG, "null device pointer in batch");
+  return MOG_OK;
+}
+
+// Plans the batch on stream s and fills the launch parameters.
+mog_status plan_batch(mog_ctx* ctx, const mog_batch* batch, float* out, cudaStream_t s, RenderParams* p) {
   MOG_CUDA(ctx, cudaSetDevice(ctx->device));
   mog_status st = ensure_order_capacity(ctx, batch->count);
   if (st != MOG_OK) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const BatchView bv = view_of(batch);
   MOG_CUDA(ctx, launch_plan(bv, batch->count, ctx->plan, SUPPORTED_BUCKETS, ctx->d_status, s));
-  RenderParams p{};
-  p.b = bv;
-  p.out = out;
-  p.profiles = ctx->d_profiles;
-  p.psfs = ctx->d_psfs;
-  p.order = ctx->plan.order;
-  p.bucket_start = ctx->plan.small;
-  p.bucket_count = ctx->plan.small + NBUCKET;
-  p.queue = ctx->plan.small + 2 * NBUCKET;
-  p.records = ctx->records;
-  p.status = ctx->d_status;
-  MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ctx->records, s));
+  *p = RenderParams{};
+  p->b = bv;
+  p->out = out;
+  p->profiles = ctx->d_profiles;
+  p->psfs = ctx->d_psfs;
+  p->order = ctx->plan.order;
+  p->bucket_start = ctx->plan.small;
+  p->bucket_count = ctx->plan.small + NBUCKET;
+  p->queue = ctx->plan.small + 2 * NBUCKET;
+  p->status = ctx->d_status;
+  return MOG_OK;
+}
+
+template <class Launch>
+mog_status launch_buckets(mog_ctx* ctx, const mog_batch* batch, cudaStream_t s, Launch&& launch) {
   const uint32_t want = batch->size_mask ? (batch->size_mask & SUPPORTED_BUCKETS) : SUPPORTED_BUCKETS;
   for (int b = 0; b < NBUCKET; ++b) {
     if (!((want >> b) & 1)) continue;
@@ -281,13 +295,49 @@ mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, vo
       MOG_CUDA(ctx, take_event(ctx, &t.b));
       MOG_CUDA(ctx, cudaEventRecord(t.a, s));
     }
-    MOG_CUDA(ctx, launch_render_fwd(bucket_side(b), p, ctx->num_sms, s));
+    MOG_CUDA(ctx, launch(bucket_side(b)));
     if (ctx->timing) {
       MOG_CUDA(ctx, cudaEventRecord(t.b, s));
       ctx->pending.push_back(t);
     }
   }
   return MOG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  mog_status st = check_batch(ctx, batch);
+  if (st != MOG_OK) return st;
+  if (batch->count == 0) return MOG_OK;
+  if (!out || (reinterpret_cast<uintptr_t>(out) & 15)) return fail(ctx, MOG_ERR_ARG, "out must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RenderParams p;
+  if ((st = plan_batch(ctx, batch, out, s, &p)) != MOG_OK) return st;
+  p.records = ctx->records;
+  MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ctx->records, s));
+  return launch_buckets(ctx, batch, s, [&](int n) { return launch_render_fwd(n, p, ctx->num_sms, s); });
+}
+
+mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,
+                               void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  mog_status st = check_batch(ctx, batch);
+  if (st != MOG_OK) return st;
+  if (batch->count == 0) return MOG_OK;
+  if (!grad_out || (reinterpret_cast<uintptr_t>(grad_out) & 15))
+    return fail(ctx, MOG_ERR_ARG, "grad_out must be 16-byte aligned");
+  if (!grad_params) return fail(ctx, MOG_ERR_ARG, "null grad_params");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RenderParams p;
+  if ((st = plan_batch(ctx, batch, nullptr, s, &p)) != MOG_OK) return st;
+  p.records = ctx->adj_records;
+  MOG_CUDA(ctx, launch_adjoint_prep(p, batch->count, ctx->adj_records, s));
+  return launch_buckets(ctx, batch, s,
+                        [&](int n) { return launch_render_bwd(n, p, grad_out, grad_params, ctx->num_sms, s); });
 }
 
 mog_status mog_set_timing(mog_ctx* ctx, int enable) {

@@ -368,6 +368,152 @@ __device__ inline void galaxy_record_warp(const BatchView& b, int64_t g, int n, 
   }
 }
 
+// Record of the adjoint (Section 2 Steps 3-4 plus the derivatives the
+// gradient needs).  With e_i = 2^(fcoef_i q):
+//   S  = sum famp_i e_i                  (spectrum value, as in the forward)
+//   Sq = sum fq_i e_i = dS/dq            (fq_i = famp_i (-2 pi^2 v_i))
+//   Sn = sum fn_i e_i = dS/dS11 = dS/dS22 through the ramp weights
+//                                        (fn_i = flux a_i w_F'(ns_i) (-ns_i / (2 tr S)) / N^2)
+// Real-space component c: value rbase_c rw_c N(.; v_c S + P_j); its ramp
+// derivative w.r.t. S11 and S22 is rbase_c rn_c N (rn_c = w_F' ns_c / (2 tr S)).
+// dS[k][ab]: derivative of (S11, S12, S22)[ab] w.r.t. (log r_e, e1, e2)[k].
+struct __align__(16) AdjRecord {
+  int ok, nf, nrc, psf;
+  float s11, s12, s22, flux;
+  float x, y, e1, e2;
+  int64_t gal, off;
+  float dS[3][3];
+  float pad[7];
+  float famp[KMAX], fcoef[KMAX], fq[KMAX], fn[KMAX];
+  float rbase[KMAX], rw[KMAX], rn[KMAX], rvar[KMAX];
+};
+static_assert(sizeof(AdjRecord) == 512, "adjoint record layout");
+
+// dS/d(log r_e, e1, e2) for CD = I:
+//   S11 = r^2 (h + G e1), S12 = -r^2 G e2, S22 = r^2 (h - G e1),
+//   h = (1 + beta^2)/2, G = (beta^2 - 1)/(2e), beta = (1 - e)/(1 + e).
+// At e = 0 the shape is not differentiable; the direction e1/e = 1 is used.
+__device__ inline void shape_jacobian(float lre, float e1, float e2, float dS[3][3]) {
+  const float r2 = expf(2.0f * lre);
+  float e = sqrtf(e1 * e1 + e2 * e2);
+  float c1 = 1.0f, c2 = 0.0f;
+  if (e > 0.0f) {
+    c1 = e1 / e;
+    c2 = e2 / e;
+  }
+  const float beta = (1.0f - e) / (1.0f + e);
+  const float dbeta = -2.0f / ((1.0f + e) * (1.0f + e));
+  const float h = 0.5f * (1.0f + beta * beta);
+  const float dh = beta * dbeta;
+  // G(e) = (beta^2 - 1) / (2 e) = -2 / (1 + e)^2 exactly, so G' = 4 / (1 + e)^3
+  const float G = -2.0f / ((1.0f + e) * (1.0f + e));
+  const float dG = 4.0f / ((1.0f + e) * (1.0f + e) * (1.0f + e));
+  dS[0][0] = 2.0f * r2 * (h + G * e1);
+  dS[0][1] = -2.0f * r2 * G * e2;
+  dS[0][2] = 2.0f * r2 * (h - G * e1);
+  // d/de1 with de/de1 = c1, d/de2 with de/de2 = c2
+  dS[1][0] = r2 * (dh * c1 + dG * c1 * e1 + G);
+  dS[1][1] = -r2 * dG * c1 * e2;
+  dS[1][2] = r2 * (dh * c1 - dG * c1 * e1 - G);
+  dS[2][0] = r2 * (dh * c2 + dG * c2 * e1);
+  dS[2][1] = -r2 * (dG * c2 * e2 + G);
+  dS[2][2] = r2 * (dh * c2 - dG * c2 * e1);
+}
+
+__device__ __forceinline__ float ramp_slope(float ns) {
+  const float t = ns - 3.0f;
+  return (t > 0.0f && t < 1.0f) ? 6.0f * t * (1.0f - t) : 0.0f;
+}
+
+// Executed by one full warp (lane = mixture component); writes *out.
+__device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n, const DevProfile* profiles,
+                                           const DevPsf* psfs, int* status, AdjRecord* out) {
+  const int lane = threadIdx.x & 31;
+  const float flux = b.flux[g], x = b.x[g], y = b.y[g], lre = b.log_re[g];
+  const float e1 = b.e1[g], e2 = b.e2[g], sn = b.sersic_n[g];
+  const int prof = b.profile[g], pid = b.psf[g];
+  const float e = sqrtf(e1 * e1 + e2 * e2);
+  bool ok = isfinite(flux) && isfinite(x) && isfinite(y) && isfinite(lre) && isfinite(e1) && isfinite(e2) &&
+            isfinite(sn) && e < 1.0f && lre < 30.0f && flux != 0.0f;
+  ok = ok && prof >= 0 && prof < MOG_MAX_PROFILES && pid >= 0 && pid < MOG_MAX_PSFS;
+  const DevProfile* P = ok ? &profiles[prof] : nullptr;
+  ok = ok && P->n_nodes > 0 && psfs[pid].k > 0;
+  const int64_t off = b.offset[g];
+  ok = ok && (off & 3) == 0;
+  if (!ok) {
+    if (lane == 0) {
+      set_status(status, MOG_ERR_DEVICE);
+      out->ok = 0;
+      out->gal = g;
+      out->off = off;
+    }
+    return;
+  }
+  const float r2 = expf(2.0f * lre);
+  const float beta = (1.0f - e) / (1.0f + e);
+  const float h = 0.5f * (1.0f + beta * beta);
+  const float gq = 0.5f * (beta * beta - 1.0f);
+  const float c1 = e > 0.0f ? e1 / e : 0.0f, c2 = e > 0.0f ? e2 / e : 0.0f;
+  const float s11 = r2 * (h + gq * c1), s12 = -r2 * gq * c2, s22 = r2 * (h - gq * c1);
+  const float tr = s11 + s22;
+  float a = 0.0f, v = 1.0f;
+  if (lane < KMAX) {
+    if (P->n_nodes == 1) {
+      a = P->amp[0][lane];
+      v = expf(P->logv[0][lane]);
+    } else {
+      float u = (sn - P->n0) * P->inv_dn;
+      u = fminf(fmaxf(u, 0.0f), (float)(P->n_nodes - 1));
+      int j = min((int)u, P->n_nodes - 2);
+      float t = u - (float)j;
+      a = (1.0f - t) * P->amp[j][lane] + t * P->amp[j + 1][lane];
+      v = expf((1.0f - t) * P->logv[j][lane] + t * P->logv[j + 1][lane]);
+    }
+  }
+  const float ns = 0.5f * (float)n * rsqrtf(v * tr);
+  const float wf = ramp_weight(ns);
+  const float dwf = ramp_slope(ns);
+  const bool four = lane < KMAX && a > 0.0f && wf > 0.0f;
+  const bool real = lane < KMAX && a > 0.0f && wf < 1.0f;
+  const unsigned mf = __ballot_sync(0xffffffffu, four);
+  const unsigned mr = __ballot_sync(0xffffffffu, real);
+  const unsigned lt = (1u << lane) - 1u;
+  const float inv_n2 = 1.0f / ((float)n * (float)n);
+  const float dns = -0.5f * ns / tr;   // d ns / d S11 = d ns / d S22
+  if (four) {
+    const int p = __popc(mf & lt);
+    const float fa = flux * a * wf * inv_n2;
+    out->famp[p] = fa;
+    out->fcoef[p] = -2.0f * PI_F * PI_F * v * LOG2E;
+    out->fq[p] = -2.0f * PI_F * PI_F * v * fa;
+    out->fn[p] = flux * a * dwf * dns * inv_n2;
+  }
+  if (real) {
+    const int p = __popc(mr & lt);
+    out->rbase[p] = flux * a;
+    out->rw[p] = 1.0f - wf;
+    out->rn[p] = -dwf * dns;
+    out->rvar[p] = v;
+  }
+  if (lane == 0) {
+    out->ok = 1;
+    out->nf = __popc(mf);
+    out->nrc = __popc(mr);
+    out->psf = pid;
+    out->s11 = s11;
+    out->s12 = s12;
+    out->s22 = s22;
+    out->flux = flux;
+    out->x = x;
+    out->y = y;
+    out->e1 = e1;
+    out->e2 = e2;
+    out->gal = g;
+    out->off = off;
+    shape_jacobian(lre, e1, e2, out->dS);
+  }
+}
+
 // Real-space terms of a galaxy: component c of the galaxy convolved with
 // component j of the PSF mixture is rw * 2^(qa dx^2 + qb dx dy + qc dy^2) at
 // (dx, dy) = pixel - (mx, my); rrr = 2^(2 qa) steps the ratio of neighbouring

@@ -38,6 +38,11 @@ cudaError_t launch_plan(const BatchView& b, int64_t count, const PlanScratch& ps
 // Writes the GalaxyRecord of every planned position (Steps 3-4).
 cudaError_t launch_galaxy_prep(const RenderParams& p, int64_t count, unsigned char* records, cudaStream_t s);
 
+// Adjoint: records (AdjRecord per planned position) and the fused kernel.
+cudaError_t launch_adjoint_prep(const RenderParams& p, int64_t count, unsigned char* records, cudaStream_t s);
+cudaError_t launch_render_bwd(int n, const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
+                              cudaStream_t s);
+
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, cudaStream_t s);
 size_t render_fwd_smem(int n);
 

@@ -1,0 +1,451 @@
+// Fused adjoint of the render: gradients of L w.r.t. (flux, x, y, log r_e,
+// e1, e2) for every galaxy, given g = dL/d pixel.
+//
+// The forward patch is pix = Re sum_{l,k} c_k X[l][k] e^{2 pi i (k x + l y)/N}
+// + (real-space terms), with c_k = 1 for k in {0, N/2} and 2 otherwise, so
+//   dL/dtheta = Re sum_{l,k} c_k conj(G[l][k]) dX[l][k]/dtheta + (real-space),
+// where G = rfft2(g) is the forward real 2-D DFT of the upstream gradient.
+// X = P phase(nu) phase(om) S with S = sum_i A_i 2^(c_i q) (Eq. onegaussian),
+// hence with Z = c_k conj(G) P phase:
+//   dL/dflux = Re sum Z S / flux,     dL/dx = 2 pi sum nu S Im Z,
+//   dL/dy    = 2 pi sum om S Im Z,    dL/dS_ab = Re sum Z dS/dS_ab,
+// dS/dS11 = Sq nu^2 + Sn, dS/dS12 = Sq 2 nu om, dS/dS22 = Sq om^2 + Sn.
+// The real-space Gaussian N(d; Sigma) contributes N Sigma^-1 d to d/dmu and
+// N (Sigma^-1 d d^T Sigma^-1 - Sigma^-1) / 2 to d/dSigma.  S(log r_e, e1, e2)
+// is chained at the end.
+//
+// One CTA per galaxy at a time, N^2/16 threads:
+//   rows      forward FFT of row pairs (2p, 2p+1) packed as g[2p] + i g[2p+1],
+//             untangled into the half spectrum of each row
+//   columns   forward FFT along y of every column k (k = 0 and N/2 packed)
+//   contract  each thread evaluates the mixture on the 8 bins it holds
+//   real      per-pixel analytic derivatives of the real-space terms
+//   reduce    warp shuffles, then one thread applies the chain rule
+#include "common.cuh"
+#include "internal.h"
+
+namespace mog {
+
+struct AdjTerms {
+  float base[RMAX], wr[RMAX], rn[RMAX], v[RMAX];
+  float i11[RMAX], i12[RMAX], i22[RMAX], mx[RMAX], my[RMAX];
+  float qa[RMAX], qb[RMAX], qc[RMAX];
+};
+
+template <int N>
+struct BwdCfg {
+  static constexpr int H = N / 2 + 1;
+  static constexpr int TPF = N / 8;
+  static constexpr int NFFT = N / 2;
+  static constexpr int THREADS = NFFT * TPF;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int LS = psf_lstride(N);
+  static constexpr int PSF_ELEMS = psf_spec_elems(N);
+  static constexpr int WS = wstride<N>();
+  static constexpr int W_ELEMS = NFFT * WS;
+  static constexpr int R1 = Radix<N>::r[1];
+  static constexpr int R2 = Radix<N>::r[2];
+  static constexpr int TW1 = twiddle_elems<N, R1>();
+  static constexpr int TW2 = Radix<N>::P == 3 ? twiddle_elems<N, (R2 > 1 ? R2 : 2)>() : 0;
+  static constexpr int MIN_BLOCKS = N == 32 ? 8 : N == 64 ? 2 : 1;
+  static constexpr int CHUNK = 8;
+  // N = 128 does not fit the PSF spectrum beside the work buffers and the
+  // gradient patch; it reads the (L2-resident) spectrum from global memory.
+  static constexpr bool STAGE_PSF = N <= 64;
+
+  static constexpr size_t off_psf = 0;
+  static constexpr size_t off_wa = off_psf + (STAGE_PSF ? sizeof(float2) * PSF_ELEMS : 0);
+  static constexpr size_t off_wb = off_wa + sizeof(float2) * W_ELEMS;
+  static constexpr size_t off_g = off_wb + sizeof(float2) * W_ELEMS;
+  static constexpr size_t off_tw = off_g + sizeof(float) * N * N;
+  static constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
+  static constexpr size_t off_py = off_px + sizeof(float2) * H;
+  static constexpr size_t off_nb = off_py + sizeof(float2) * N;       // nu = 1/2 column: P phase
+  static constexpr size_t off_ns = off_nb + sizeof(float2) * N;       // and (S, Sq, Sn)
+  static constexpr size_t off_rec = (off_ns + sizeof(float) * 4 * N + 15) & ~size_t(15);
+  static constexpr size_t off_terms = off_rec + 2 * sizeof(AdjRecord);
+  static constexpr size_t off_red = off_terms + sizeof(AdjTerms);
+  static constexpr size_t off_bar = (off_red + sizeof(float) * 8 * WARPS + 15) & ~size_t(15);
+  static constexpr size_t SMEM = off_bar + 4 * sizeof(uint64_t);
+};
+
+template <int N>
+struct BwdLast {
+  static constexpr int R = Radix<N>::r[Radix<N>::P - 1];
+  static constexpr int NS = N / R;
+};
+
+template <int N, int S>
+__device__ __forceinline__ void fft_rest_b(float2* w, int j, const float2* tw1, const float2* tw2, float2* v) {
+  constexpr int R1 = Radix<N>::r[1];
+  stockham_load<N, R1, S>(w, j, tw1, v);
+  if constexpr (Radix<N>::P == 3) {
+    constexpr int R2 = Radix<N>::r[2];
+    __syncwarp();
+    stockham_store<N, R1>(w, j, 8, v);
+    __syncwarp();
+    stockham_load<N, R2, S>(w, j, tw2, v);
+  }
+}
+
+// Adds one bin's contribution.  z = c_k conj(G) P phase; (s, sq, sn) the
+// weighted mixture sums at the bin.
+__device__ __forceinline__ void contract_bin(float2 z, float nu, float om, float s, float sq, float sn,
+                                             float* acc) {
+  acc[0] = fmaf(z.x, s, acc[0]);
+  acc[1] = fmaf(nu * s, z.y, acc[1]);
+  acc[2] = fmaf(om * s, z.y, acc[2]);
+  acc[3] = fmaf(z.x, fmaf(sq * nu, nu, sn), acc[3]);
+  acc[4] = fmaf(z.x, sq * 2.0f * nu * om, acc[4]);
+  acc[5] = fmaf(z.x, fmaf(sq * om, om, sn), acc[5]);
+}
+
+template <int N>
+__global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
+    render_bwd_kernel(RenderParams p, const float* __restrict__ grad_out, float* __restrict__ grad_params) {
+  using C = BwdCfg<N>;
+  constexpr int TPF = C::TPF, WS = C::WS, LS = C::LS;
+  constexpr int B = bucket_of(N);
+  constexpr float INV_N = 1.0f / N;
+  constexpr float TWO_PI = 2.0f * PI_F;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2* psf_smem = reinterpret_cast<float2*>(smem + C::off_psf);
+  const float2* psf_hat = psf_smem;
+  float2* WA = reinterpret_cast<float2*>(smem + C::off_wa);
+  float2* WB = reinterpret_cast<float2*>(smem + C::off_wb);
+  float* gbuf = reinterpret_cast<float*>(smem + C::off_g);
+  float2* tw1 = reinterpret_cast<float2*>(smem + C::off_tw);
+  float2* tw2 = tw1 + C::TW1;
+  float2* px = reinterpret_cast<float2*>(smem + C::off_px);
+  float2* py = reinterpret_cast<float2*>(smem + C::off_py);
+  float2* nyb = reinterpret_cast<float2*>(smem + C::off_nb);
+  float* nys = reinterpret_cast<float*>(smem + C::off_ns);   // [l][4]: S, Sq, Sn
+  AdjRecord* rec = reinterpret_cast<AdjRecord*>(smem + C::off_rec);
+  AdjTerms& at = *reinterpret_cast<AdjTerms*>(smem + C::off_terms);
+  float* red = reinterpret_cast<float*>(smem + C::off_red);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);  // [0] PSF, [1..2] records, [3] g
+  __shared__ int s_pos[2];
+  __shared__ float s_psf_mog[KPSF][6];
+  __shared__ int s_kpsf;
+
+  const int tid = threadIdx.x;
+  const int f = tid / TPF, j = tid % TPF;
+  const int lane = tid & 31, warp = tid >> 5;
+  fill_twiddles<N, C::R1>(tw1, 8, tid, C::THREADS);
+  if constexpr (Radix<N>::P == 3) fill_twiddles<N, C::R2>(tw2, N / C::R2, tid, C::THREADS);
+  const int count = p.bucket_count[B];
+  const unsigned char* records = p.records + (size_t)p.bucket_start[B] * sizeof(AdjRecord);
+  int q_next = 0, q_end = 0, q_ahead = 0;
+  auto next_position = [&]() -> int {
+    if (q_next >= q_end) {
+      const int b0 = q_ahead;
+      if (b0 >= count) return -1;
+      q_next = b0;
+      q_end = min(b0 + C::CHUNK, count);
+      q_ahead = atomicAdd(&p.queue[B], C::CHUNK);
+    }
+    return q_next++;
+  };
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+    q_ahead = atomicAdd(&p.queue[B], C::CHUNK);
+    const int p0 = next_position();
+    s_pos[0] = p0;
+    if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * sizeof(AdjRecord), sizeof(AdjRecord), &bar[1]);
+  }
+  int cur_psf = -1;
+  uint32_t psf_parity = 0, rec_parity = 0, g_parity = 0;
+  float2* wa = WA + f * WS;
+  float2* wb = WB + f * WS;
+
+  for (int buf = 0;; buf ^= 1) {
+    __syncthreads();  // S1
+    const int pos = s_pos[buf];
+    if (pos < 0) break;
+    if (tid == 0) {
+      const int np = next_position();
+      s_pos[buf ^ 1] = np;
+      if (np >= 0)
+        bulk_load(&rec[buf ^ 1], records + (size_t)np * sizeof(AdjRecord), sizeof(AdjRecord), &bar[1 + (buf ^ 1)]);
+    }
+    const bool rec_landed = mbar_wait(&bar[1 + buf], (rec_parity >> buf) & 1u);
+    rec_parity ^= 1u << buf;
+    const AdjRecord& r = rec[buf];
+    const bool go = rec_landed && r.ok;
+    if (go && tid == 0) bulk_load(gbuf, grad_out + r.off, sizeof(float) * N * N, &bar[3]);
+    const bool need_psf = go && r.psf != cur_psf;
+    bool psf_landed = true;
+    if (need_psf) {
+      if constexpr (C::STAGE_PSF) {
+        if (tid == 0) bulk_load(psf_smem, p.psfs[r.psf].spec[B], sizeof(float2) * C::PSF_ELEMS, &bar[0]);
+      } else {
+        psf_hat = p.psfs[r.psf].spec[B];
+      }
+      if (tid < KPSF * 6) s_psf_mog[tid / 6][tid % 6] = p.psfs[r.psf].mog[tid / 6][tid % 6];
+      if (tid == 0) s_kpsf = p.psfs[r.psf].k;
+      if constexpr (C::STAGE_PSF) {
+        psf_landed = mbar_wait(&bar[0], psf_parity);
+        psf_parity ^= 1u;
+      }
+      cur_psf = r.psf;
+    }
+    if (__syncthreads_or(!rec_landed || !psf_landed)) {
+      if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
+      return;
+    }
+    if (!r.ok) continue;
+
+    // ---- per-galaxy tables ----
+    {
+      const float gx = r.x, gy = r.y;
+      const int kp = s_kpsf;
+      const int ntask = C::H + 2 * N + r.nrc * kp;
+      for (int i = tid; i < ntask; i += C::THREADS) {
+        float sn, cs;
+        if (i < C::H) {
+          sincospif(-2.0f * gx * (float)i * INV_N, &sn, &cs);
+          px[i] = make_float2(cs, sn);
+        } else if (i < C::H + N) {
+          const int l = i - C::H;
+          sincospif(-2.0f * gy * (float)(l < N / 2 ? l : l - N) * INV_N, &sn, &cs);
+          py[l] = make_float2(cs, sn);
+        } else if (i < C::H + 2 * N) {
+          // the nu = 1/2 column: P phase and the three mixture sums
+          const int l = i - C::H - N;
+          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+          const float q = fmaf(om, fmaf(r.s22, om, r.s12), 0.25f * r.s11);
+          float s = 0.0f, sq = 0.0f, sn2 = 0.0f;
+          for (int c = 0; c < r.nf; ++c) {
+            const float e = ex2(r.fcoef[c] * q);
+            s = fmaf(r.famp[c], e, s);
+            sq = fmaf(r.fq[c], e, sq);
+            sn2 = fmaf(r.fn[c], e, sn2);
+          }
+          float sy, cy;
+          sincospif(-2.0f * gy * om, &sy, &cy);
+          sincospif(-gx, &sn, &cs);
+          nyb[l] = cmul(psf_hat[(N / 2) * LS + l], cmul(make_float2(cs, sn), make_float2(cy, sy)));
+          nys[4 * l + 0] = s;
+          nys[4 * l + 1] = sq;
+          nys[4 * l + 2] = sn2;
+        } else {
+          const int t = i - C::H - 2 * N;
+          const int c = t / kp, jj = t - c * kp;
+          const float* m = s_psf_mog[jj];
+          const float v = r.rvar[c];
+          const float vxx = v * r.s11 + m[3], vxy = v * r.s12 + m[4], vyy = v * r.s22 + m[5];
+          const float det = vxx * vyy - vxy * vxy;
+          const float idet = 1.0f / det;
+          at.base[t] = r.rbase[c] * m[0] * rsqrtf(det) * (0.5f / PI_F);
+          at.wr[t] = r.rw[c];
+          at.rn[t] = r.rn[c];
+          at.v[t] = v;
+          at.i11[t] = vyy * idet;
+          at.i12[t] = -vxy * idet;
+          at.i22[t] = vxx * idet;
+          at.qa[t] = -0.5f * LOG2E * vyy * idet;
+          at.qb[t] = LOG2E * vxy * idet;
+          at.qc[t] = -0.5f * LOG2E * vxx * idet;
+          at.mx[t] = 0.5f * (float)N + r.x + m[1];
+          at.my[t] = 0.5f * (float)N + r.y + m[2];
+        }
+      }
+    }
+    const bool g_landed = mbar_wait(&bar[3], g_parity);
+    g_parity ^= 1u;
+    if (__syncthreads_or(!g_landed)) {   // S2
+      if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
+      return;
+    }
+
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float2 v[8];
+    // ---- forward FFT of row pairs (2f, 2f+1) packed as g[2f] + i g[2f+1] ----
+    {
+      const float* ga = gbuf + (2 * f) * N;
+      const float* gb = gbuf + (2 * f + 1) * N;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = make_float2(ga[j + m * TPF], gb[j + m * TPF]);
+      dft8<-1>(v);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) wb[swz<N>(8 * j + m)] = v[m];
+      __syncwarp();
+      fft_rest_b<N, -1>(wb, j, tw1, tw2, v);
+      __syncwarp();
+      constexpr int R = BwdLast<N>::R, NS = BwdLast<N>::NS;
+      stockham_store<N, R>(wb, j, NS, v);
+      __syncwarp();
+      // untangle: row 2f has spectrum (Z[k] + conj Z[N-k]) / 2, row 2f+1 has
+      // (Z[k] - conj Z[N-k]) / (2i); write them as inputs of the column FFTs
+      for (int k = j; k <= N / 2; k += TPF) {
+        const float2 zk = wb[swz<N>(k)], zn = wb[swz<N>((N - k) & (N - 1))];
+        const float2 a = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+        const float2 b = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
+        if (k == 0) {
+          // rows' nu = 0 and nu = 1/2 values are real: packed as re + i im
+          const float2 zh = wb[swz<N>(N / 2)];
+          WA[swz<N>(2 * f)] = make_float2(zk.x, zh.x);
+          WA[swz<N>(2 * f + 1)] = make_float2(zk.y, zh.y);
+        } else if (k < N / 2) {
+          WA[k * WS + swz<N>(2 * f)] = a;
+          WA[k * WS + swz<N>(2 * f + 1)] = b;
+        }
+      }
+    }
+
+    // ---- real-space terms: analytic derivatives, pixel by pixel ----
+    {
+      const int nr = r.nrc * s_kpsf;
+      if (nr > 0) {
+        for (int pix = tid; pix < N * N; pix += C::THREADS) {
+          const float gw = gbuf[pix];
+          if (gw == 0.0f) continue;
+          const float xx = (float)(pix % N), yy = (float)(pix / N);
+          for (int t = 0; t < nr; ++t) {
+            const float dx = xx - at.mx[t], dy = yy - at.my[t];
+            const float e0 = fmaf(dx, fmaf(at.qa[t], dx, at.qb[t] * dy), at.qc[t] * dy * dy);
+            const float n = gw * at.base[t] * ex2(e0);
+            const float ux = fmaf(at.i11[t], dx, at.i12[t] * dy);
+            const float uy = fmaf(at.i12[t], dx, at.i22[t] * dy);
+            const float nw = n * at.wr[t];
+            const float nv = nw * at.v[t];
+            const float rr = n * at.rn[t];
+            acc[0] += nw;
+            acc[1] = fmaf(nw, ux, acc[1]);
+            acc[2] = fmaf(nw, uy, acc[2]);
+            acc[3] = fmaf(nv, 0.5f * fmaf(ux, ux, -at.i11[t]), acc[3] + rr);
+            acc[4] = fmaf(nv, fmaf(ux, uy, -at.i12[t]), acc[4]);
+            acc[5] = fmaf(nv, 0.5f * fmaf(uy, uy, -at.i22[t]), acc[5] + rr);
+          }
+        }
+        // the Fourier sums below carry 2 pi for x, y; pre-divide the real ones
+        acc[1] *= 1.0f / TWO_PI;
+        acc[2] *= 1.0f / TWO_PI;
+      }
+    }
+    __syncthreads();  // S3: every column input written
+
+    // ---- forward FFT of every column along y ----
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = wa[swz<N>(j + m * TPF)];
+    dft8<-1>(v);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) wa[swz<N>(8 * j + m)] = v[m];
+    __syncwarp();
+    fft_rest_b<N, -1>(wa, j, tw1, tw2, v);
+
+    // ---- contraction with the mixture's derivatives ----
+    {
+      constexpr int R = BwdLast<N>::R, NS = BwdLast<N>::NS;
+      const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
+      const int nf = r.nf;
+      // every lane of the warp reaches both __syncwarp calls; only the
+      // packed group's lanes store
+      __syncwarp();
+      if (f == 0) stockham_store<N, R>(wa, j, NS, v);   // packed U[l], natural order
+      __syncwarp();
+      const float nu = f * INV_N;
+      const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
+      const float ck = f == 0 ? 1.0f : 2.0f;
+      const float2 pxf = px[f];
+#pragma unroll
+      for (int q = 0; q < 8 / R; ++q)
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+          const int l = stockham_out_index<N, R>(j, NS, q, m);
+          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+          float2 gk = v[q * R + m];
+          float2 gn = make_float2(0.f, 0.f);
+          if (f == 0) {
+            const float2 u = wa[swz<N>(l)], un = wa[swz<N>((N - l) & (N - 1))];
+            gk = make_float2(0.5f * (u.x + un.x), 0.5f * (u.y - un.y));
+            const float dr = u.x - un.x, di = u.y + un.y;
+            gn = make_float2(0.5f * di, -0.5f * dr);
+          }
+          const float qv = fmaf(om, fmaf(s22, om, a1), a0);
+          float s = 0.0f, sq = 0.0f, sn = 0.0f;
+          for (int c = 0; c < nf; ++c) {
+            const float e = ex2(r.fcoef[c] * qv);
+            s = fmaf(r.famp[c], e, s);
+            sq = fmaf(r.fq[c], e, sq);
+            sn = fmaf(r.fn[c], e, sn);
+          }
+          const float2 bph = cmul(psf_hat[f * LS + l], cmul(pxf, py[l]));
+          const float2 z = cscale(cmulc(bph, gk), ck);   // c_k conj(G) P phase
+          contract_bin(z, nu, om, s, sq, sn, acc);
+          if (f == 0) {
+            const float2 zn = cmulc(nyb[l], gn);
+            contract_bin(zn, 0.5f, om, nys[4 * l], nys[4 * l + 1], nys[4 * l + 2], acc);
+          }
+        }
+    }
+
+    // ---- reduce the six sums over the CTA and apply the chain rule ----
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float x = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) red[warp * 8 + k] = x;
+    }
+    __syncthreads();  // S4
+    if (tid == 0) {
+      float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int w = 0; w < C::WARPS; ++w)
+        for (int k = 0; k < 6; ++k) t[k] += red[w * 8 + k];
+      float* out = grad_params + r.gal * 6;
+      out[0] = t[0] / r.flux;
+      out[1] = TWO_PI * t[1];
+      out[2] = TWO_PI * t[2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) out[3 + k] = t[3] * r.dS[k][0] + t[4] * r.dS[k][1] + t[5] * r.dS[k][2];
+    }
+  }
+}
+
+template <int N>
+static cudaError_t launch_bwd(const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
+                              cudaStream_t s) {
+  using C = BwdCfg<N>;
+  static int occ = -1;
+  if (occ < 0) {
+    cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_bwd_kernel<N>, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+  }
+  render_bwd_kernel<N><<<occ * num_sms, C::THREADS, C::SMEM, s>>>(p, grad_out, grad_params);
+  return cudaGetLastError();
+}
+
+// One warp per planned position (lane = mixture component).
+__global__ void adjoint_prep(RenderParams p, unsigned char* records) {
+  const int total = p.bucket_start[NBUCKET - 1] + p.bucket_count[NBUCKET - 1];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int pos = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pos < total; pos += warps) {
+    const int64_t g = p.order[pos];
+    adjoint_record_warp(p.b, g, p.b.size[g], p.profiles, p.psfs, p.status,
+                        reinterpret_cast<AdjRecord*>(records + (size_t)pos * sizeof(AdjRecord)));
+  }
+}
+
+cudaError_t launch_adjoint_prep(const RenderParams& p, int64_t count, unsigned char* records, cudaStream_t s) {
+  const int64_t blocks = (count + 7) / 8;
+  adjoint_prep<<<(int)(blocks < 8192 ? (blocks > 0 ? blocks : 1) : 8192), 256, 0, s>>>(p, records);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_bwd(int n, const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
+                              cudaStream_t s) {
+  switch (n) {
+    case 32: return launch_bwd<32>(p, grad_out, grad_params, num_sms, s);
+    case 64: return launch_bwd<64>(p, grad_out, grad_params, num_sms, s);
+    case 128: return launch_bwd<128>(p, grad_out, grad_params, num_sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace mog

@@ -97,6 +97,16 @@ class Renderer:
         capi.mog_render_batch(self.ctx, b, out.data_ptr(), s.cuda_stream)
         return out
 
+    def render_backward(self, batch, grad_out, grad_params=None, stream=None):
+        """Gradients (count, 6) of L w.r.t. (flux, x, y, log_re, e1, e2)
+        given grad_out = dL/d(packed output)."""
+        if grad_params is None:
+            grad_params = torch.empty(batch.count, 6, dtype=torch.float32, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
+        capi.mog_render_backward(self.ctx, b, grad_out.data_ptr(), grad_params.data_ptr(), s.cuda_stream)
+        return grad_params
+
     def sync_status(self, stream=None):
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         capi.mog_sync_status(self.ctx, s.cuda_stream)
@@ -107,3 +117,40 @@ def patches(out, batch):
     o = out.reshape(-1)
     return [o[int(batch.offsets[i]):int(batch.offsets[i]) + int(batch.sizes[i]) ** 2].view(
         int(batch.sizes[i]), int(batch.sizes[i])) for i in range(batch.count)]
+
+
+PARAM_FIELDS = ("flux", "x", "y", "log_re", "e1", "e2")
+
+
+class _Render(torch.autograd.Function):
+    """theta (6, G) float32 CUDA tensor, rows (flux, x, y, log_re, e1, e2);
+    returns the packed patches.  Backward runs the library's adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, theta, renderer, batch):
+        theta = theta.contiguous()
+        tensors = dict(batch.tensors)
+        for k, name in enumerate(PARAM_FIELDS):
+            tensors[name] = theta[k]
+        b = DeviceBatch(tensors, batch.count, batch.total, batch.sizes, batch.offsets)
+        out = renderer.render(b)
+        ctx.renderer = renderer
+        ctx.batch = b
+        ctx.save_for_backward(theta)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        grad_out = grad_out.contiguous()
+        g = ctx.renderer.render_backward(ctx.batch, grad_out)
+        return g.t(), None, None
+
+
+def render(theta, renderer, batch):
+    """Differentiable batched render: theta (6, G) -> packed patches."""
+    return _Render.apply(theta, renderer, batch)
+
+
+def theta_of(batch):
+    """(6, G) tensor of the differentiable parameters of a DeviceBatch."""
+    return torch.stack([batch.tensors[k] for k in PARAM_FIELDS])
