@@ -60,7 +60,7 @@ enum {
 };
 
 enum { MOG_MAX_COMPONENTS = 12, MOG_MAX_PSF_COMPONENTS = 4, MOG_MAX_PSFS = 1024,
-       MOG_MAX_PROFILES = 8, MOG_MAX_NODES = 64 };
+       MOG_MAX_PROFILES = 8, MOG_MAX_NODES = 64, MOG_NOALLOC_MAX_GALAXIES = 16384 };
 
 /*
  * A batch of G galaxies, structure of arrays, all device pointers of length
@@ -136,6 +136,27 @@ mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id);
  * Asynchronous on `stream`.
  */
 mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
+
+/*
+ * Same result as mog_render_batch, but the call allocates no memory: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  (The paper has no
+ * counterpart; this is an interface for callers that cannot let a library
+ * allocate on the render path: processes that reserve the GPU's memory up
+ * front and serve every buffer from their own arena, and latency-critical
+ * loops that cannot take cudaMalloc's possible device synchronisation.)
+ *
+ * The per-call scratch (planning counters, galaxy order, per-galaxy records)
+ * lives in one fixed device array of about 4.3 MB defined in the library,
+ * present on every GPU that loads it until the process exits.  At most
+ * MOG_NOALLOC_MAX_GALAXIES galaxies per call; larger batches are rejected
+ * with MOG_ERR_ARG (split them).  The first call on a device looks up the
+ * array's device address for that device (once); make that first call before
+ * any stream capture.  All calls share the one array: calls that overlap on
+ * the GPU (different streams, or different contexts on the same device) race
+ * and corrupt each other's output; serialise them.  The context, its tables
+ * and PSFs must have been created beforehand (those calls allocate).
+ */
+mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
 
 /*
  * Adjoint of mog_render_batch (gradients for model fitting; the paper's

@@ -31,8 +31,9 @@ MOG_MAX_NODES = 64
 EXPORTED = (
     "mog_create_context", "mog_destroy_context", "mog_last_error", "mog_set_profile_table",
     "mog_create_psf", "mog_destroy_psf", "mog_render_batch", "mog_sync_status",
-    "mog_set_timing", "mog_read_timing", "mog_render_backward",
+    "mog_set_timing", "mog_read_timing", "mog_render_backward", "mog_render_batch_noalloc",
 )
+MOG_NOALLOC_MAX_GALAXIES = 16384
 
 
 class MogError(RuntimeError):
@@ -67,6 +68,7 @@ def _load():
         "mog_destroy_psf": ([VP, I], I),
         "mog_render_batch": ([VP, P(mog_batch), VP, VP], I),
         "mog_render_backward": ([VP, P(mog_batch), VP, VP, VP], I),
+        "mog_render_batch_noalloc": ([VP, P(mog_batch), VP, VP], I),
         "mog_sync_status": ([VP, VP], I),
         "mog_set_timing": ([VP, I], I),
         "mog_read_timing": ([VP, P(ctypes.c_double), P(ctypes.c_int64)], I),
@@ -147,6 +149,13 @@ def make_batch(count, ptrs, size_mask=0):
 def mog_render_batch(ctx, batch, out_ptr, stream=0):
     _check(ctx, _lib.mog_render_batch(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
                                       ctypes.c_void_p(int(stream))))
+
+
+def mog_render_batch_noalloc(ctx, batch, out_ptr, stream=0):
+    """The allocation-free render (see include/mogconv.h): at most
+    MOG_NOALLOC_MAX_GALAXIES galaxies, calls that overlap on the GPU race."""
+    _check(ctx, _lib.mog_render_batch_noalloc(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
+                                              ctypes.c_void_p(int(stream))))
 
 
 def mog_render_backward(ctx, batch, grad_out_ptr, grad_params_ptr, stream=0):

@@ -340,6 +340,30 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
                         [&](int n) { return launch_render_bwd(n, p, grad_out, grad_params, ctx->num_sms, s); });
 }
 
+mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  mog_status st = check_batch(ctx, batch);
+  if (st != MOG_OK) return st;
+  if (batch->count == 0) return MOG_OK;
+  if (batch->count > MOG_NOALLOC_MAX_GALAXIES)
+    return fail(ctx, MOG_ERR_ARG, "mog_render_batch_noalloc renders at most %d galaxies per call (got %lld)",
+                MOG_NOALLOC_MAX_GALAXIES, (long long)batch->count);
+  if (!out || (reinterpret_cast<uintptr_t>(out) & 15)) return fail(ctx, MOG_ERR_ARG, "out must be 16-byte aligned");
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  unsigned char* base = nullptr;
+  MOG_CUDA(ctx, noalloc_scratch(ctx->device, &base));
+  RenderParams proto{};
+  proto.b = view_of(batch);
+  proto.out = out;
+  proto.profiles = ctx->d_profiles;
+  proto.psfs = ctx->d_psfs;
+  proto.status = ctx->d_status;
+  const uint32_t want = batch->size_mask ? (batch->size_mask & SUPPORTED_BUCKETS) : SUPPORTED_BUCKETS;
+  MOG_CUDA(ctx, render_noalloc(proto, batch->count, want, base, ctx->num_sms, ctx->d_status,
+                               static_cast<cudaStream_t>(stream)));
+  return MOG_OK;
+}
+
 mog_status mog_set_timing(mog_ctx* ctx, int enable) {
   if (!ctx) return MOG_ERR_ARG;
   ctx->timing = enable != 0;

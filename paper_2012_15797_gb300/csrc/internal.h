@@ -43,6 +43,12 @@ cudaError_t launch_adjoint_prep(const RenderParams& p, int64_t count, unsigned c
 cudaError_t launch_render_bwd(int n, const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
                               cudaStream_t s);
 
+// Allocation-free forward render (noalloc.cu): the scratch of one call lives
+// in a fixed device array; noalloc_scratch returns its address on `device`.
+cudaError_t noalloc_scratch(int device, unsigned char** out);
+cudaError_t render_noalloc(const RenderParams& proto, int64_t count, uint32_t want, unsigned char* base,
+                           int num_sms, int* status, cudaStream_t s);
+
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, cudaStream_t s);
 size_t render_fwd_smem(int n);
 
