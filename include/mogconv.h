@@ -13,7 +13,8 @@
  *
  * Conventions shared by every entry point:
  *  - A patch is N x N float32, row-major, row = y, column = x, pixel centres at
- *    integer coordinates.  N is one of 32, 64, 128.
+ *    integer coordinates.  N is one of 32, 64, 128, 256 for the render and
+ *    32, 64, 128 for the adjoint.
  *  - The galaxy centre is (N/2 + x, N/2 + y) where (x, y) is its offset.
  *  - Shapes: r_e = exp(log_re) pixels; e1, e2 ellipticity (Eqs. 2-5) with the
  *    WCS matrix CD = identity (pixel units); the pixel covariance of a
@@ -72,7 +73,7 @@ enum { MOG_MAX_COMPONENTS = 12, MOG_MAX_PSF_COMPONENTS = 4, MOG_MAX_PSFS = 1024,
  *   sersic_n  Sersic index where the profile table depends on n (Section 3)
  *   profile   profile-table id (mog_set_profile_table)
  *   psf       PSF id (mog_create_psf)
- *   size      patch side N of this galaxy (32, 64 or 128)
+ *   size      patch side N of this galaxy (32, 64, 128 or 256)
  *   offset    element offset of this galaxy's N*N patch in the output array
  * Patches must not overlap.  The batch struct itself is host memory.
  */

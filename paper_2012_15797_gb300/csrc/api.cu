@@ -61,7 +61,6 @@ mog_status cuda_fail(mog_ctx* ctx, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
   } while (0)
 
-constexpr int SUPPORTED_BUCKETS = 0x7;  // 32, 64, 128
 
 BatchView view_of(const mog_batch* b) {
   return BatchView{b->flux, b->x,      b->y,    b->log_re, b->e1,  b->e2,
@@ -265,12 +264,13 @@ mog_status check_batch(mog_ctx* ctx, const mog_batch* batch) {
 }
 
 // Plans the batch on stream s and fills the launch parameters.
-mog_status plan_batch(mog_ctx* ctx, const mog_batch* batch, float* out, cudaStream_t s, RenderParams* p) {
+mog_status plan_batch(mog_ctx* ctx, const mog_batch* batch, float* out, uint32_t supported, cudaStream_t s,
+                      RenderParams* p) {
   MOG_CUDA(ctx, cudaSetDevice(ctx->device));
   mog_status st = ensure_order_capacity(ctx, batch->count);
   if (st != MOG_OK) return st;
   const BatchView bv = view_of(batch);
-  MOG_CUDA(ctx, launch_plan(bv, batch->count, ctx->plan, SUPPORTED_BUCKETS, ctx->d_status, s));
+  MOG_CUDA(ctx, launch_plan(bv, batch->count, ctx->plan, supported, ctx->d_status, s));
   *p = RenderParams{};
   p->b = bv;
   p->out = out;
@@ -285,8 +285,9 @@ mog_status plan_batch(mog_ctx* ctx, const mog_batch* batch, float* out, cudaStre
 }
 
 template <class Launch>
-mog_status launch_buckets(mog_ctx* ctx, const mog_batch* batch, cudaStream_t s, Launch&& launch) {
-  const uint32_t want = batch->size_mask ? (batch->size_mask & SUPPORTED_BUCKETS) : SUPPORTED_BUCKETS;
+mog_status launch_buckets(mog_ctx* ctx, const mog_batch* batch, uint32_t supported, cudaStream_t s,
+                          Launch&& launch) {
+  const uint32_t want = batch->size_mask ? (batch->size_mask & supported) : supported;
   for (int b = 0; b < NBUCKET; ++b) {
     if (!((want >> b) & 1)) continue;
     mog_ctx::Timed t{b, nullptr, nullptr};
@@ -316,10 +317,10 @@ mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, vo
   if (!out || (reinterpret_cast<uintptr_t>(out) & 15)) return fail(ctx, MOG_ERR_ARG, "out must be 16-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RenderParams p;
-  if ((st = plan_batch(ctx, batch, out, s, &p)) != MOG_OK) return st;
+  if ((st = plan_batch(ctx, batch, out, FWD_BUCKETS, s, &p)) != MOG_OK) return st;
   p.records = ctx->records;
   MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ctx->records, s));
-  return launch_buckets(ctx, batch, s, [&](int n) { return launch_render_fwd(n, p, ctx->num_sms, s); });
+  return launch_buckets(ctx, batch, FWD_BUCKETS, s, [&](int n) { return launch_render_fwd(n, p, ctx->num_sms, s); });
 }
 
 mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,
@@ -333,10 +334,10 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
   if (!grad_params) return fail(ctx, MOG_ERR_ARG, "null grad_params");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RenderParams p;
-  if ((st = plan_batch(ctx, batch, nullptr, s, &p)) != MOG_OK) return st;
+  if ((st = plan_batch(ctx, batch, nullptr, BWD_BUCKETS, s, &p)) != MOG_OK) return st;
   p.records = ctx->adj_records;
   MOG_CUDA(ctx, launch_adjoint_prep(p, batch->count, ctx->adj_records, s));
-  return launch_buckets(ctx, batch, s,
+  return launch_buckets(ctx, batch, BWD_BUCKETS, s,
                         [&](int n) { return launch_render_bwd(n, p, grad_out, grad_params, ctx->num_sms, s); });
 }
 
@@ -358,7 +359,7 @@ mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float*
   proto.profiles = ctx->d_profiles;
   proto.psfs = ctx->d_psfs;
   proto.status = ctx->d_status;
-  const uint32_t want = batch->size_mask ? (batch->size_mask & SUPPORTED_BUCKETS) : SUPPORTED_BUCKETS;
+  const uint32_t want = batch->size_mask ? (batch->size_mask & FWD_BUCKETS) : FWD_BUCKETS;
   MOG_CUDA(ctx, render_noalloc(proto, batch->count, want, base, ctx->num_sms, ctx->d_status,
                                static_cast<cudaStream_t>(stream)));
   return MOG_OK;

@@ -50,6 +50,11 @@ cudaError_t render_noalloc(const RenderParams& proto, int64_t count, uint32_t wa
                            int num_sms, int* status, cudaStream_t s);
 
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, cudaStream_t s);
+cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, cudaStream_t s);
+
+// Patch sides each direction supports (bit b: N = 32 << b).
+constexpr uint32_t FWD_BUCKETS = 0xF;   // 32, 64, 128, 256
+constexpr uint32_t BWD_BUCKETS = 0x7;   // 32, 64, 128
 size_t render_fwd_smem(int n);
 
 // Spectrum of a PSF embedded with its centre at (n/2, n/2), written in the

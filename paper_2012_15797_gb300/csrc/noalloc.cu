@@ -67,7 +67,7 @@ cudaError_t render_noalloc(const RenderParams& proto, int64_t count, uint32_t wa
   // at zero; everything else is rewritten before it is read.
   cudaError_t e = cudaMemsetAsync(ps.hist, 0, KEYS * sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  e = launch_plan(proto.b, count, ps, 0x7 /* 32, 64, 128 */, status, s);
+  e = launch_plan(proto.b, count, ps, FWD_BUCKETS, status, s);
   if (e != cudaSuccess) return e;
   RenderParams p = proto;
   p.order = ps.order;

@@ -367,6 +367,7 @@ cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, cudaStr
     case 32: return launch_fwd<32>(p, num_sms, s);
     case 64: return launch_fwd<64>(p, num_sms, s);
     case 128: return launch_fwd<128>(p, num_sms, s);
+    case 256: return launch_render_fwd256(p, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }

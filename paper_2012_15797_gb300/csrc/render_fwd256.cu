@@ -1,0 +1,331 @@
+// Fused forward render for 256 x 256 patches (Section 2, Steps 3-8).
+//
+// The half spectrum (129 x 256 complex, 264 KB) does not fit in one CTA's
+// shared memory, so the transform between the two FFT directions goes through
+// the galaxy's own output patch, which stays L2-resident: the input of the
+// row transform of row pair p (256 complex, 2 KB) occupies exactly the bytes
+// of output rows 2p and 2p+1, which only that row transform overwrites.
+//
+// 1024 threads, one warp per length-256 transform:
+//   columns   4 rounds of 32 column IFFTs (round 0, warp 0: the packed nu = 0
+//             and nu = 1/2 columns); each round's row-pair values are staged in
+//             shared memory and written as coalesced 256-byte row segments
+//   rows      4 rounds of 32 row-pair IFFTs, each warp independent: load its
+//             row pair's input, transform, add the real-space terms, store
+//             the two pixel rows over the input
+// The PSF spectrum (272 KB) is read from global memory (L2-resident).
+#include "common.cuh"
+#include "internal.h"
+
+namespace mog {
+
+namespace {
+
+constexpr int N = 256;
+constexpr int H = N / 2 + 1;
+constexpr int TPF = N / 8;       // 32: one warp per transform
+constexpr int THREADS = 1024;
+constexpr int WARPS = THREADS / 32;
+constexpr int ROUNDS = (N / 2) / WARPS;   // 4
+constexpr int LS = psf_lstride(N);
+constexpr int WS = wstride<N>();
+constexpr int R1 = Radix<N>::r[1], R2 = Radix<N>::r[2];
+constexpr int TW1 = twiddle_elems<N, R1>(), TW2 = twiddle_elems<N, R2>();
+constexpr int CHUNK = 4;
+constexpr int B = bucket_of(N);
+
+constexpr size_t off_w = 0;                                              // WARPS rows of WS float2
+constexpr size_t off_sa = off_w + sizeof(float2) * WARPS * WS;            // staging [p][32]
+constexpr size_t off_sb = off_sa + sizeof(float2) * (N / 2) * WARPS;      // mirrored columns
+constexpr size_t off_tw = off_sb + sizeof(float2) * (N / 2) * WARPS;
+constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
+constexpr size_t off_py = off_px + sizeof(float2) * H;
+constexpr size_t off_nyq = off_py + sizeof(float2) * N;
+constexpr size_t off_rec = (off_nyq + sizeof(float2) * N + 15) & ~size_t(15);
+constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);
+constexpr size_t off_bar = (off_rt + sizeof(RealTerms) + 15) & ~size_t(15);
+constexpr size_t SMEM = off_bar + 2 * sizeof(uint64_t);
+
+__global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams p) {
+  constexpr float INV_N = 1.0f / N;
+  constexpr float NEGLIGIBLE_LOG2 = -40.0f;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2* W = reinterpret_cast<float2*>(smem + off_w);
+  float2* SA = reinterpret_cast<float2*>(smem + off_sa);
+  float2* SB = reinterpret_cast<float2*>(smem + off_sb);
+  float2* tw1 = reinterpret_cast<float2*>(smem + off_tw);
+  float2* tw2 = tw1 + TW1;
+  float2* px = reinterpret_cast<float2*>(smem + off_px);
+  float2* py = reinterpret_cast<float2*>(smem + off_py);
+  float2* nyq = reinterpret_cast<float2*>(smem + off_nyq);
+  GalaxyRecord* rec = reinterpret_cast<GalaxyRecord*>(smem + off_rec);
+  RealTerms& rt = *reinterpret_cast<RealTerms*>(smem + off_rt);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + off_bar);   // records
+  __shared__ int s_pos[2];
+  __shared__ float s_psf_mog[KPSF][6];
+  __shared__ int s_kpsf;
+
+  const int tid = threadIdx.x;
+  const int f = tid >> 5, j = tid & 31;   // warp = transform slot, lane = thread in it
+  fill_twiddles<N, R1>(tw1, 8, tid, THREADS);
+  fill_twiddles<N, R2>(tw2, N / R2, tid, THREADS);
+  const int count = p.bucket_count[B];
+  const unsigned char* records = p.records + (size_t)p.bucket_start[B] * RECORD_BYTES;
+  int q_next = 0, q_end = 0, q_ahead = 0;
+  auto next_position = [&]() -> int {
+    if (q_next >= q_end) {
+      const int b0 = q_ahead;
+      if (b0 >= count) return -1;
+      q_next = b0;
+      q_end = min(b0 + CHUNK, count);
+      q_ahead = atomicAdd(&p.queue[B], CHUNK);
+    }
+    return q_next++;
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    q_ahead = atomicAdd(&p.queue[B], CHUNK);
+    const int p0 = next_position();
+    s_pos[0] = p0;
+    if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * RECORD_BYTES, sizeof(GalaxyRecord), &bar[0]);
+  }
+  int cur_psf = -1;
+  const float2* psf_hat = nullptr;
+  uint32_t rec_parity = 0;
+  float2* w = W + f * WS;   // this warp's transform row
+
+  for (int buf = 0;; buf ^= 1) {
+    __syncthreads();  // the previous galaxy is fully stored
+    const int pos = s_pos[buf];
+    if (pos < 0) break;
+    if (tid == 0) {
+      const int np = next_position();
+      s_pos[buf ^ 1] = np;
+      if (np >= 0)
+        bulk_load(&rec[buf ^ 1], records + (size_t)np * RECORD_BYTES, sizeof(GalaxyRecord), &bar[buf ^ 1]);
+    }
+    const bool landed = mbar_wait(&bar[buf], (rec_parity >> buf) & 1u);
+    rec_parity ^= 1u << buf;
+    const GalaxyRecord& r = rec[buf];
+    if (landed && r.ok && r.psf != cur_psf) {
+      if (tid < KPSF * 6) s_psf_mog[tid / 6][tid % 6] = p.psfs[r.psf].mog[tid / 6][tid % 6];
+      if (tid == 0) s_kpsf = p.psfs[r.psf].k;
+      psf_hat = p.psfs[r.psf].spec[B];
+      cur_psf = r.psf;
+    }
+    if (__syncthreads_or(!landed)) {
+      if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
+      return;
+    }
+    if (!r.ok) continue;
+    float* dst = p.out + r.off;
+    float2* zbuf = reinterpret_cast<float2*>(dst);   // row-pair inputs, [p][k]
+
+    // per-galaxy tables
+    {
+      const float gx = r.x, gy = r.y;
+      const int kp = s_kpsf;
+      const int ntask = H + 2 * N + r.nrc * kp;
+      for (int i = tid; i < ntask; i += THREADS) {
+        float sn, cs;
+        if (i < H) {
+          sincospif(-2.0f * gx * (float)i * INV_N, &sn, &cs);
+          px[i] = make_float2(cs, sn);
+        } else if (i < H + N) {
+          const int l = i - H;
+          sincospif(-2.0f * gy * (float)(l < N / 2 ? l : l - N) * INV_N, &sn, &cs);
+          py[l] = make_float2(cs, sn);
+        } else if (i < H + 2 * N) {
+          const int l = i - H - N;
+          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+          const float q = fmaf(om, fmaf(r.s22, om, r.s12), 0.25f * r.s11);
+          float acc = 0.0f;
+          for (int c = 0; c < r.nf; ++c) acc = fmaf(r.famp[c], ex2(r.fcoef[c] * q), acc);
+          float sy, cy;
+          sincospif(-2.0f * gy * om, &sy, &cy);
+          sincospif(-gx, &sn, &cs);
+          nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(make_float2(cs, sn), make_float2(cy, sy))), acc);
+        } else {
+          real_term(r, s_psf_mog, kp, N, i - H - 2 * N, &rt);
+        }
+      }
+    }
+    __syncthreads();
+
+    const int nf = r.nf;
+    const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
+    float2 v[8];
+    // ---- Steps 5-7a: columns k = 32 round + warp ----
+    for (int round = 0; round < ROUNDS; ++round) {
+      const int k = WARPS * round + f;
+      {
+        const float nu = k * INV_N;
+        const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
+        float q[8], s[8];
+        float qmin = 3.4e38f;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int l = j + m * TPF;
+          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+          q[m] = fmaf(om, fmaf(s22, om, a1), a0);
+          qmin = fminf(qmin, q[m]);
+          s[m] = 0.0f;
+        }
+        for (int i = 0; i < nf; ++i) {
+          const float a = r.famp[i], c = r.fcoef[i];
+          if (!__any_sync(0xffffffffu, c * qmin > NEGLIGIBLE_LOG2)) continue;
+#pragma unroll
+          for (int m = 0; m < 8; ++m) s[m] = fmaf(a, ex2(c * q[m]), s[m]);
+        }
+        const float2 pxk = px[k];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int l = j + m * TPF;
+          v[m] = cscale(cmul(__ldg(&psf_hat[k * LS + l]), cmul(pxk, py[l])), s[m]);
+        }
+        if (k == 0) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const int l = j + m * TPF;
+            const float2 dc = (l == N / 2) ? make_float2(v[m].x, 0.0f) : v[m];
+            const float2 a = nyq[l], b = nyq[(N - l) & (N - 1)];
+            const float2 hn = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+            v[m] = make_float2(dc.x - hn.y, dc.y + hn.x);
+          }
+        }
+      }
+      dft8<+1>(v);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) w[swz<N>(8 * j + m)] = v[m];
+      __syncwarp();
+      stockham_load<N, R1, +1>(w, j, tw1, v);
+      __syncwarp();
+      stockham_store<N, R1>(w, j, 8, v);
+      __syncwarp();
+      stockham_load<N, R2, +1>(w, j, tw2, v);
+      // rows 2p (even lane), 2p+1 (odd lane): stage Z_p[k] and Z_p[N-k]
+      {
+        constexpr int NS = N / R2;
+        const bool odd = j & 1;
+#pragma unroll
+        for (int qq = 0; qq < 8 / R2; ++qq)
+#pragma unroll
+          for (int m = 0; m < R2; ++m) {
+            const float2 mine = v[qq * R2 + m];
+            float2 other;
+            other.x = __shfl_xor_sync(0xffffffffu, mine.x, 1);
+            other.y = __shfl_xor_sync(0xffffffffu, mine.y, 1);
+            const float2 A = odd ? other : mine, Bv = odd ? mine : other;
+            const int pr = stockham_out_index<N, R2>(j, NS, qq, m) >> 1;
+            if (k > 0) {
+              if (!odd) SA[pr * WARPS + f] = make_float2(A.x - Bv.y, A.y + Bv.x);
+              else SB[pr * WARPS + f] = make_float2(A.x + Bv.y, Bv.x - A.y);
+            } else {
+              // column 0 in SA, column N/2 in SB's slot 0
+              if (!odd) SA[pr * WARPS] = make_float2(A.x, Bv.x);
+              else SB[pr * WARPS] = make_float2(A.y, Bv.y);
+            }
+          }
+      }
+      __syncthreads();
+      // coalesced copy: row pair p gets columns 32 round + t and N - 32 round - t
+      for (int i = tid; i < (N / 2) * WARPS * 2; i += THREADS) {
+        const int pr = i / (2 * WARPS), t = i % (2 * WARPS);
+        if (t < WARPS) {
+          zbuf[pr * N + WARPS * round + t] = SA[pr * WARPS + t];
+        } else {
+          const int u = t - WARPS;
+          const int col = (round == 0 && u == 0) ? N / 2 : N - WARPS * round - u;
+          zbuf[pr * N + col] = SB[pr * WARPS + u];
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- Step 7b + 8: row pairs p = 32 round + warp, each warp on its own ----
+    const int nr = r.nrc * s_kpsf;
+    for (int round = 0; round < ROUNDS; ++round) {
+      const int pr = WARPS * round + f;
+      const float2* zin = zbuf + pr * N;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = __ldcg(&zin[j + m * TPF]);
+      dft8<+1>(v);
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < 8; ++m) w[swz<N>(8 * j + m)] = v[m];
+      __syncwarp();
+      stockham_load<N, R1, +1>(w, j, tw1, v);
+      __syncwarp();
+      stockham_store<N, R1>(w, j, 8, v);
+      __syncwarp();
+      stockham_load<N, R2, +1>(w, j, tw2, v);
+      __syncwarp();
+      {
+        constexpr int NS = N / R2;
+        float* orow = reinterpret_cast<float*>(w);
+#pragma unroll
+        for (int qq = 0; qq < 8 / R2; ++qq)
+#pragma unroll
+          for (int m = 0; m < R2; ++m) {
+            const int n = stockham_out_index<N, R2>(j, NS, qq, m);
+            orow[n] = v[qq * R2 + m].x;
+            orow[N + n] = v[qq * R2 + m].y;
+          }
+      }
+      __syncwarp();
+      // 512 pixels (rows 2pr, 2pr+1), 8 consecutive per lane and step
+      for (int idx = j; idx < 2 * N / 8; idx += 32) {
+        const int h = idx / (N / 8), x0 = (idx % (N / 8)) * 8;
+        const int yy = 2 * pr + h;
+        const float* orow = reinterpret_cast<const float*>(w) + h * N + x0;
+        float4 o0 = *reinterpret_cast<const float4*>(orow);
+        float4 o1 = *reinterpret_cast<const float4*>(orow + 4);
+        if (nr > 0) {
+          float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          for (int t = 0; t < nr; ++t) {
+            const float qa = rt.rqa[t], dy = (float)yy - rt.rmy[t], dx = (float)x0 - rt.rmx[t];
+            const float ly = dy * rt.rqb[t];
+            const float e0 = fmaf(dx, fmaf(qa, dx, ly), rt.rqc[t] * dy * dy);
+            float g = rt.rw[t] * ex2(e0);
+            float rr = ex2(fmaf(qa, fmaf(2.0f, dx, 1.0f), ly));
+            const float r8 = rt.rrr[t];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              acc[u] += g;
+              g *= rr;
+              rr *= r8;
+            }
+          }
+          o0.x += acc[0];
+          o0.y += acc[1];
+          o0.z += acc[2];
+          o0.w += acc[3];
+          o1.x += acc[4];
+          o1.y += acc[5];
+          o1.z += acc[6];
+          o1.w += acc[7];
+        }
+        float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
+        d[0] = o0;
+        d[1] = o1;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(render_fwd256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  render_fwd256_kernel<<<num_sms, THREADS, SMEM, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace mog

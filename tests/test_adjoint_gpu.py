@@ -155,3 +155,20 @@ def test_autograd_matches_c_abi(gpu_renderer):
     assert torch.equal(theta.grad.t(), direct)
     ref = gpu_renderer.render(b)
     assert torch.equal(out.detach(), ref)
+
+
+def test_adjoint_rejects_256(gpu_renderer):
+    """The adjoint covers N = 32, 64, 128; a 256 galaxy is reported through
+    the status word and its gradient left unwritten."""
+    import torch
+    from paper_2012_15797_gb300.capi import MogError, MOG_ERR_DEVICE
+    from paper_2012_15797_gb300.renderer import to_device
+    gals = _gals([_row(size=64), _row(size=256)])
+    b = to_device(gals)
+    gp = torch.full((2, 6), -5.0, device="cuda")
+    gpu_renderer.render_backward(b, torch.ones(b.total, device="cuda"), gp)
+    with pytest.raises(MogError) as ei:
+        gpu_renderer.sync_status()
+    assert ei.value.status == MOG_ERR_DEVICE
+    g = gp.cpu().numpy()
+    assert np.all(g[1] == -5.0) and np.all(np.isfinite(g[0])) and not np.all(g[0] == -5.0)

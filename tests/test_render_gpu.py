@@ -46,7 +46,7 @@ EDGE = [
 ]
 
 
-@pytest.mark.parametrize("size", [32, 64, 128])
+@pytest.mark.parametrize("size", [32, 64, 128, 256])
 def test_edge_cases_each_size(gpu_renderer, tables, size):
     rows = [_row(size=size, **e) for e in EDGE]
     gals = _gals(rows)
@@ -55,7 +55,7 @@ def test_edge_cases_each_size(gpu_renderer, tables, size):
     check_parity(gpu, ora, gals)
 
 
-@pytest.mark.parametrize("size", [32, 64, 128])
+@pytest.mark.parametrize("size", [32, 64, 128, 256])
 def test_ramp_boundaries(gpu_renderer, tables, size):
     """Galaxies whose largest exp component sits at n_sigma = 2.9, 3, 3.5, 4
     and 4.1 (the aliasing split of Step 4 and its ramp)."""
@@ -82,8 +82,7 @@ def test_batch_fixed_size_ragged(gpu_renderer, tables):
 
 def test_batch_mixed_sizes_and_psfs(gpu_renderer, tables):
     gals = config2_galaxies(301, seed=12, n_psf=5)
-    keep = np.nonzero(gals.size <= 128)[0]
-    gals = gals.subset(keep)
+    assert set(np.unique(gals.size)) == {32, 64, 128, 256}
     gpu, _, _ = gpu_patches(gpu_renderer, gals)
     ora = oracle_patches(gals, gpu_renderer.psfs, tables)
     check_parity(gpu, ora, gals)
@@ -91,9 +90,9 @@ def test_batch_mixed_sizes_and_psfs(gpu_renderer, tables):
 
 def test_batch_equals_single(gpu_renderer):
     gals = config2_galaxies(64, seed=13, n_psf=5)
-    gals = gals.subset(np.nonzero(gals.size <= 128)[0])
     full, _, _ = gpu_patches(gpu_renderer, gals)
-    for i in (0, 5, len(gals) - 1):
+    big = int(np.nonzero(gals.size == 256)[0][0])
+    for i in (0, 5, big, len(gals) - 1):
         one, _, _ = gpu_patches(gpu_renderer, gals.subset([i]))
         assert np.array_equal(one[0], full[i])
 
