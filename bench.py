@@ -37,7 +37,7 @@ N_PATCH = 64
 METRIC = "galaxy patches rendered/s at 64x64 (100k-galaxy fixed-size batch)"
 UNIT = "patches/s"
 PARAM_BYTES = 7 * 4 + 3 * 4 + 8      # float params, int ids, int64 offset
-SFU_PER_CLK_SM = 16                  # MUFU ex2 lanes per SM per clock
+SFU_PER_CLK_SM = 32                  # MUFU ex2 per SM per clock (31.7 measured on GB300 with an ex2 probe)
 FP32_FLOP_PER_CLK_SM = 256           # 128 FMA lanes x 2
 KERNEL_SOURCES = ("paper_2012_15797_gb300/csrc/render_fwd.cu", "paper_2012_15797_gb300/csrc/common.cuh")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "render_fwd_64_config1.md")
@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the mixed-size / gradient / per-galaxy lines")
+    ap.add_argument("--extra-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -258,6 +260,136 @@ def cpu_baseline(galaxies, seconds):
 
 
 # ----------------------------------------------------------------------------
+# Secondary workloads: mixed sizes (graph + autotuner), render + gradient,
+# one launch per galaxy.
+# ----------------------------------------------------------------------------
+
+def _event_ms(fn, steps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def extra_mixed(tables, device, steps):
+    """200k galaxies, Sersic n U(0.5, 6), N = smallest of 32..256 >= 8 r_e,
+    64 PSFs: eager calls with default launch shapes vs one CUDA-graph launch
+    per step after the autotuner."""
+    import numpy as np
+    import torch
+    from paper_2012_15797_gb300 import capi
+    from paper_2012_15797_gb300.renderer import Renderer, to_device
+    from workloads import config2_galaxies, config2_psfs
+
+    psfs = config2_psfs(64)
+    gals = config2_galaxies(200_000)
+    r = Renderer(tables, psfs, device=device)
+    b = to_device(gals, device=f"cuda:{device}")
+    out = torch.empty(b.total, dtype=torch.float32, device=f"cuda:{device}")
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        r.render(b, out)
+    r.sync_status()
+    eager_ms = _event_ms(lambda: r.render(b, out), steps, st)
+    shapes = r.autotune(b, out, reps=2)
+    g = r.graph(b, out)
+    for _ in range(3):
+        g.launch()
+    capi.mog_set_timing(r.ctx, True)
+    capi.mog_read_timing(r.ctx)
+    tuned_eager_ms = _event_ms(lambda: r.render(b, out), steps, st)
+    kms, kn = capi.mog_read_timing(r.ctx)
+    capi.mog_set_timing(r.ctx, False)
+    graph_ms = _event_ms(g.launch, steps, st)
+    r.sync_status()
+    g.close()
+    sizes, counts = np.unique(gals.size, return_counts=True)
+    res = {
+        "workload": "200000 galaxies, Sersic n U(0.5, 6) (8-12 components), r_e log-U(0.3, 20) px, "
+                    "N = smallest of {32, 64, 128, 256} >= 8 r_e, 64 PSFs (2-Gaussian core + Moffat wings)",
+        "bucket_mix": {int(n): int(c) for n, c in zip(sizes, counts)},
+        "value_graph": len(gals) / (graph_ms / 1e3), "unit": UNIT, "ms_graph": graph_ms,
+        "value_eager_default_shapes": len(gals) / (eager_ms / 1e3), "ms_eager_default": eager_ms,
+        "ms_eager_tuned": tuned_eager_ms,
+        "kernel_ms_per_size": {32 << i: (kms[i] / kn[i] if kn[i] else None) for i in range(4)},
+        "autotuned_shapes": {f"{d}{n}": list(v) for (d, n), v in shapes.items()},
+        "bytes_written": int(b.total) * 4,
+    }
+    r.close()
+    return res
+
+
+def extra_render_grad(tables, psf, device, steps):
+    """50k galaxies at 64^2: render, inverse-variance-weighted residual
+    gradient (data from perturbed parameters + noise 0.01 peak), adjoint."""
+    import torch
+    from paper_2012_15797_gb300 import capi
+    from paper_2012_15797_gb300.renderer import Renderer, to_device
+    from workloads import config3_problem
+
+    model, truth, noise = config3_problem(50_000)
+    r = Renderer(tables, [psf], device=device)
+    dev = f"cuda:{device}"
+    data = r.render(to_device(truth, device=dev)).view(len(truth), 64, 64)
+    sigma = 0.01 * data.amax(dim=(1, 2), keepdim=True)
+    data = data + sigma * torch.from_numpy(noise).to(dev)
+    ivar = (1.0 / sigma ** 2).reshape(-1, 1, 1)
+    bm = to_device(model, device=dev)
+    out = torch.empty(bm.total, device=dev)
+    gpix = torch.empty(bm.total, device=dev)
+    gp = torch.empty(len(model), 6, device=dev)
+
+    def step():
+        r.render(bm, out)
+        torch.mul(out.view(-1, 64, 64) - data, 2.0 * ivar, out=gpix.view(-1, 64, 64))
+        r.render_backward(bm, gpix, gp)
+
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        step()
+    r.sync_status()
+    capi.mog_set_timing(r.ctx, True)
+    capi.mog_read_timing(r.ctx)
+    ms = _event_ms(step, steps, st)
+    kms, kn = capi.mog_read_timing(r.ctx)
+    capi.mog_set_timing(r.ctx, False)
+    r.sync_status()
+    res = {"workload": "50000 galaxies as the fixed-size batch; loss = sum ivar (model - data)^2, data from "
+                       "perturbed parameters + Gaussian noise sigma = 0.01 peak; gradients w.r.t. "
+                       "(flux, x, y, log r_e, e1, e2)",
+           "value": len(model) / (ms / 1e3), "unit": "patches rendered+grad/s", "ms_per_step": ms,
+           "kernel_ms_forward_plus_adjoint": kms[1] / max(kn[1], 1) * 2}
+    r.close()
+    return res
+
+
+def extra_per_galaxy(tables, psf, device, n=2000):
+    """The plain form: the same math with one library call (planner, record,
+    render launches) per galaxy."""
+    import torch
+    from paper_2012_15797_gb300.renderer import Renderer, to_device
+    from workloads import config1_galaxies
+
+    gals = config1_galaxies(n, seed=5)
+    r = Renderer(tables, [psf], device=device)
+    singles = [to_device(gals.subset([i]), device=f"cuda:{device}") for i in range(n)]
+    out = torch.empty(64 * 64, device=f"cuda:{device}")
+    for b in singles[:20]:
+        r.render(b, out)
+    r.sync_status()
+    ms = _event_ms(lambda: [r.render(b, out) for b in singles], 1, torch.cuda.current_stream())
+    r.close()
+    return {"value": n / (ms / 1e3), "unit": UNIT, "galaxies": n,
+            "note": "one mog_render_batch call per 64x64 galaxy of the fixed-size distribution"}
+
+
+# ----------------------------------------------------------------------------
 # Distributed helpers (replicas).
 # ----------------------------------------------------------------------------
 
@@ -403,6 +535,11 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.galaxies, args.cpu_seconds)
+    extra = None
+    if world == 1 and not args.no_extra:
+        extra = {"mixed_sizes": extra_mixed(tables, local, args.extra_steps),
+                 "render_grad": extra_render_grad(tables, psf, local, args.extra_steps),
+                 "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -418,6 +555,7 @@ def run_ours(args):
         "real_space_component_fraction": work["real_fraction"],
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": args.steps * 4, "clocks": clocks,
+        "extra": extra,
     }
     print(json.dumps(line))
     r.close()

@@ -176,6 +176,32 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
                                float* grad_params, void* stream);
 
 /*
+ * Autotuner (the batching feature): for each size bucket present in the
+ * batch (batch->size_mask, or all), times the render kernel over every
+ * launch shape (CTAs per SM from 1 to what fits x work-queue chunk of
+ * 1..32 galaxies) with CUDA events, `reps` renders per shape, and keeps the
+ * fastest in the context for later calls.  With non-null grad_out and
+ * grad_params the adjoint is tuned the same way.  Writes `out` and
+ * grad_params as a side effect.  report (host, optional, 16 ints) receives
+ * (ctas_per_sm, chunk) per [direction][bucket].  Synchronous.
+ */
+mog_status mog_autotune(mog_ctx* ctx, const mog_batch* batch, float* out, const float* grad_out,
+                        float* grad_params, void* stream, int reps, int* report);
+
+/*
+ * CUDA graph of one batched render: the planner, the record prologue and
+ * the per-size kernels (on parallel branches) captured once for fixed
+ * batch / output buffers; every mog_graph_launch renders whatever those
+ * buffers hold at launch time.  Capture makes one eager render first (sizing
+ * scratch, configuring kernels), so nothing allocates during capture.  The
+ * batch count and buffers are baked in; capture again when they change.
+ */
+typedef struct mog_graph mog_graph;
+mog_status mog_graph_capture(mog_ctx* ctx, const mog_batch* batch, float* out, mog_graph** graph);
+mog_status mog_graph_launch(mog_graph* graph, void* stream);
+mog_status mog_graph_destroy(mog_graph* graph);
+
+/*
  * Kernel timing for measurement: while enabled, every render-kernel launch is
  * bracketed by CUDA events recorded on its own stream.  mog_read_timing
  * waits for the recorded events and returns, per patch side N = 32 << b

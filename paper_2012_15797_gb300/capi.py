@@ -32,6 +32,7 @@ EXPORTED = (
     "mog_create_context", "mog_destroy_context", "mog_last_error", "mog_set_profile_table",
     "mog_create_psf", "mog_destroy_psf", "mog_render_batch", "mog_sync_status",
     "mog_set_timing", "mog_read_timing", "mog_render_backward", "mog_render_batch_noalloc",
+    "mog_autotune", "mog_graph_capture", "mog_graph_launch", "mog_graph_destroy",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -69,6 +70,10 @@ def _load():
         "mog_render_batch": ([VP, P(mog_batch), VP, VP], I),
         "mog_render_backward": ([VP, P(mog_batch), VP, VP, VP], I),
         "mog_render_batch_noalloc": ([VP, P(mog_batch), VP, VP], I),
+        "mog_autotune": ([VP, P(mog_batch), VP, VP, VP, VP, I, P(I)], I),
+        "mog_graph_capture": ([VP, P(mog_batch), VP, P(VP)], I),
+        "mog_graph_launch": ([VP, VP], I),
+        "mog_graph_destroy": ([VP], I),
         "mog_sync_status": ([VP, VP], I),
         "mog_set_timing": ([VP, I], I),
         "mog_read_timing": ([VP, P(ctypes.c_double), P(ctypes.c_int64)], I),
@@ -161,6 +166,35 @@ def mog_render_batch_noalloc(ctx, batch, out_ptr, stream=0):
 def mog_render_backward(ctx, batch, grad_out_ptr, grad_params_ptr, stream=0):
     _check(ctx, _lib.mog_render_backward(ctx, ctypes.byref(batch), ctypes.c_void_p(int(grad_out_ptr)),
                                          ctypes.c_void_p(int(grad_params_ptr)), ctypes.c_void_p(int(stream))))
+
+
+def mog_autotune(ctx, batch, out_ptr, grad_out_ptr=0, grad_params_ptr=0, stream=0, reps=3):
+    """Returns {("fwd"|"bwd", N): (ctas_per_sm, chunk)} for the tuned buckets."""
+    rep = (ctypes.c_int * 16)(*([0] * 16))
+    _check(ctx, _lib.mog_autotune(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
+                                  ctypes.c_void_p(int(grad_out_ptr)), ctypes.c_void_p(int(grad_params_ptr)),
+                                  ctypes.c_void_p(int(stream)), int(reps), rep))
+    out = {}
+    for d, name in enumerate(("fwd", "bwd")):
+        for b in range(4):
+            c, ch = rep[(d * 4 + b) * 2], rep[(d * 4 + b) * 2 + 1]
+            if c:
+                out[(name, 32 << b)] = (c, ch)
+    return out
+
+
+def mog_graph_capture(ctx, batch, out_ptr):
+    g = ctypes.c_void_p()
+    _check(ctx, _lib.mog_graph_capture(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)), ctypes.byref(g)))
+    return g
+
+
+def mog_graph_launch(graph, stream=0):
+    _check(None, _lib.mog_graph_launch(graph, ctypes.c_void_p(int(stream))))
+
+
+def mog_graph_destroy(graph):
+    _check(None, _lib.mog_graph_destroy(graph))
 
 
 def mog_set_timing(ctx, enable):

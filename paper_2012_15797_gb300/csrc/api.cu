@@ -34,6 +34,18 @@ struct mog_ctx {
   std::vector<cudaEvent_t> event_pool;
   double acc_ms[NBUCKET] = {0, 0, 0, 0};
   int64_t acc_n[NBUCKET] = {0, 0, 0, 0};
+  // launch shapes per bucket (mog_autotune) and the parallel branches
+  LaunchShape tune_fwd[NBUCKET], tune_bwd[NBUCKET];
+  cudaStream_t side[NBUCKET] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[NBUCKET] = {};
+  cudaStream_t capture = nullptr;
+};
+
+struct mog_graph {
+  mog_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -118,6 +130,12 @@ mog_status mog_create_context(mog_ctx** out, int device) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->plan.small, sizeof(int32_t) * 4 * NBUCKET);
   if (e == cudaSuccess) e = cudaMemset(ctx->plan.small, 0, sizeof(int32_t) * 4 * NBUCKET);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dft_scratch, sizeof(double2) * 256 * 129);
+  for (int b = 0; b < NBUCKET && e == cudaSuccess; ++b) {
+    e = cudaStreamCreateWithFlags(&ctx->side[b], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev[b], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     mog_destroy_context(ctx);
     return e == cudaErrorMemoryAllocation ? MOG_ERR_NOMEM : MOG_ERR_CUDA;
@@ -148,6 +166,12 @@ mog_status mog_destroy_context(mog_ctx* ctx) {
     cudaEventDestroy(t.b);
   }
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  for (int b = 0; b < NBUCKET; ++b) {
+    if (ctx->side[b]) cudaStreamDestroy(ctx->side[b]);
+    if (ctx->join_ev[b]) cudaEventDestroy(ctx->join_ev[b]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
   delete ctx;
   return MOG_OK;
 }
@@ -284,22 +308,37 @@ mog_status plan_batch(mog_ctx* ctx, const mog_batch* batch, float* out, uint32_t
   return MOG_OK;
 }
 
+// Launches one kernel per requested size bucket.  With more than one bucket
+// the kernels run on parallel branches (context side streams forked from and
+// joined back into `s` with events), so a CUDA graph captured around the call
+// holds them as parallel nodes and a bucket's tail overlaps the next one.
 template <class Launch>
 mog_status launch_buckets(mog_ctx* ctx, const mog_batch* batch, uint32_t supported, cudaStream_t s,
                           Launch&& launch) {
   const uint32_t want = batch->size_mask ? (batch->size_mask & supported) : supported;
+  const bool fork = __builtin_popcount(want) > 1;
+  if (fork) MOG_CUDA(ctx, cudaEventRecord(ctx->fork_ev, s));
   for (int b = 0; b < NBUCKET; ++b) {
     if (!((want >> b) & 1)) continue;
+    cudaStream_t bs = s;
+    if (fork) {
+      bs = ctx->side[b];
+      MOG_CUDA(ctx, cudaStreamWaitEvent(bs, ctx->fork_ev, 0));
+    }
     mog_ctx::Timed t{b, nullptr, nullptr};
     if (ctx->timing) {
       MOG_CUDA(ctx, take_event(ctx, &t.a));
       MOG_CUDA(ctx, take_event(ctx, &t.b));
-      MOG_CUDA(ctx, cudaEventRecord(t.a, s));
+      MOG_CUDA(ctx, cudaEventRecord(t.a, bs));
     }
-    MOG_CUDA(ctx, launch(bucket_side(b)));
+    MOG_CUDA(ctx, launch(bucket_side(b), bs));
     if (ctx->timing) {
-      MOG_CUDA(ctx, cudaEventRecord(t.b, s));
+      MOG_CUDA(ctx, cudaEventRecord(t.b, bs));
       ctx->pending.push_back(t);
+    }
+    if (fork) {
+      MOG_CUDA(ctx, cudaEventRecord(ctx->join_ev[b], bs));
+      MOG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->join_ev[b], 0));
     }
   }
   return MOG_OK;
@@ -320,7 +359,11 @@ mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, vo
   if ((st = plan_batch(ctx, batch, out, FWD_BUCKETS, s, &p)) != MOG_OK) return st;
   p.records = ctx->records;
   MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ctx->records, s));
-  return launch_buckets(ctx, batch, FWD_BUCKETS, s, [&](int n) { return launch_render_fwd(n, p, ctx->num_sms, s); });
+  return launch_buckets(ctx, batch, FWD_BUCKETS, s, [&](int n, cudaStream_t bs) {
+    RenderParams q = p;
+    q.chunk = ctx->tune_fwd[bucket_of(n)].chunk;
+    return launch_render_fwd(n, q, ctx->num_sms, ctx->tune_fwd[bucket_of(n)].ctas_per_sm, bs);
+  });
 }
 
 mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,
@@ -337,8 +380,11 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
   if ((st = plan_batch(ctx, batch, nullptr, BWD_BUCKETS, s, &p)) != MOG_OK) return st;
   p.records = ctx->adj_records;
   MOG_CUDA(ctx, launch_adjoint_prep(p, batch->count, ctx->adj_records, s));
-  return launch_buckets(ctx, batch, BWD_BUCKETS, s,
-                        [&](int n) { return launch_render_bwd(n, p, grad_out, grad_params, ctx->num_sms, s); });
+  return launch_buckets(ctx, batch, BWD_BUCKETS, s, [&](int n, cudaStream_t bs) {
+    RenderParams q = p;
+    q.chunk = ctx->tune_bwd[bucket_of(n)].chunk;
+    return launch_render_bwd(n, q, grad_out, grad_params, ctx->num_sms, ctx->tune_bwd[bucket_of(n)].ctas_per_sm, bs);
+  });
 }
 
 mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
@@ -362,6 +408,111 @@ mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float*
   const uint32_t want = batch->size_mask ? (batch->size_mask & FWD_BUCKETS) : FWD_BUCKETS;
   MOG_CUDA(ctx, render_noalloc(proto, batch->count, want, base, ctx->num_sms, ctx->d_status,
                                static_cast<cudaStream_t>(stream)));
+  return MOG_OK;
+}
+
+mog_status mog_autotune(mog_ctx* ctx, const mog_batch* batch, float* out, const float* grad_out, float* grad_params,
+                        void* stream, int reps, int* report) {
+  if (!ctx || reps < 1) return MOG_ERR_ARG;
+  mog_status st = check_batch(ctx, batch);
+  if (st != MOG_OK) return st;
+  if (batch->count == 0) return MOG_OK;
+  const bool timing_was = ctx->timing;
+  double ms[NBUCKET];
+  int64_t n[NBUCKET];
+  // drain anything recorded before
+  if ((st = mog_read_timing(ctx, ms, n)) != MOG_OK) return st;
+  static const int chunks[] = {1, 2, 4, 8, 16, 32};
+  for (int dir = 0; dir < 2; ++dir) {
+    if (dir == 1 && (!grad_out || !grad_params)) break;
+    LaunchShape* tune = dir == 0 ? ctx->tune_fwd : ctx->tune_bwd;
+    const uint32_t sup = dir == 0 ? FWD_BUCKETS : BWD_BUCKETS;
+    const uint32_t want = batch->size_mask ? (batch->size_mask & sup) : sup;
+    for (int b = 0; b < NBUCKET; ++b) {
+      if (!((want >> b) & 1)) continue;
+      const int n_side = bucket_side(b);
+      const int max_ctas = dir == 0 ? render_fwd_max_ctas(n_side) : render_bwd_max_ctas(n_side);
+      LaunchShape best = tune[b];
+      double best_ms = 1e300;
+      for (int c = 1; c <= max_ctas; ++c)
+        for (int ch : chunks) {
+          tune[b].ctas_per_sm = c;
+          tune[b].chunk = ch;
+          ctx->timing = true;
+          for (int r = 0; r < reps; ++r) {
+            st = dir == 0 ? mog_render_batch(ctx, batch, out, stream)
+                          : mog_render_backward(ctx, batch, grad_out, grad_params, stream);
+            if (st != MOG_OK) {
+              ctx->timing = timing_was;
+              return st;
+            }
+          }
+          ctx->timing = false;
+          if ((st = mog_read_timing(ctx, ms, n)) != MOG_OK) return st;
+          const double t = n[b] ? ms[b] / (double)n[b] : 1e300;
+          if (t < best_ms) {
+            best_ms = t;
+            best = tune[b];
+          }
+        }
+      tune[b] = best;
+      if (report) {
+        report[(dir * NBUCKET + b) * 2] = best.ctas_per_sm;
+        report[(dir * NBUCKET + b) * 2 + 1] = best.chunk;
+      }
+    }
+  }
+  ctx->timing = timing_was;
+  return MOG_OK;
+}
+
+mog_status mog_graph_capture(mog_ctx* ctx, const mog_batch* batch, float* out, mog_graph** graph) {
+  if (!ctx || !graph) return MOG_ERR_ARG;
+  *graph = nullptr;
+  mog_status st = check_batch(ctx, batch);
+  if (st != MOG_OK) return st;
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  // one eager call sizes the scratch and configures the kernels, so that
+  // nothing is allocated or configured while capturing
+  if ((st = mog_render_batch(ctx, batch, out, ctx->capture)) != MOG_OK) return st;
+  MOG_CUDA(ctx, cudaStreamSynchronize(ctx->capture));
+  const bool timing_was = ctx->timing;
+  ctx->timing = false;
+  MOG_CUDA(ctx, cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+  st = mog_render_batch(ctx, batch, out, ctx->capture);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->capture, &g);
+  ctx->timing = timing_was;
+  if (st != MOG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(ctx, e, "cudaGraphInstantiate");
+  }
+  mog_graph* h = new mog_graph();
+  h->ctx = ctx;
+  h->graph = g;
+  h->exec = exec;
+  *graph = h;
+  return MOG_OK;
+}
+
+mog_status mog_graph_launch(mog_graph* graph, void* stream) {
+  if (!graph) return MOG_ERR_ARG;
+  MOG_CUDA(graph->ctx, cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
+  return MOG_OK;
+}
+
+mog_status mog_graph_destroy(mog_graph* graph) {
+  if (!graph) return MOG_ERR_ARG;
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  if (graph->graph) cudaGraphDestroy(graph->graph);
+  delete graph;
   return MOG_OK;
 }
 

@@ -20,6 +20,15 @@ struct RenderParams {
   int32_t* queue;               // [NBUCKET] work counters, zeroed by the planner
   const unsigned char* records; // RECORD_BYTES per planned position (GalaxyRecord)
   int* status;
+  int chunk;                    // queue positions taken per request
+};
+
+// Launch shape of one size bucket: CTAs per SM (clamped to what fits) and
+// the work-queue chunk.  Chosen by mog_autotune; defaults: as many CTAs as
+// fit, chunk 8.
+struct LaunchShape {
+  int ctas_per_sm = 0;   // 0 = as many as fit
+  int chunk = 8;
 };
 
 struct PlanScratch {
@@ -41,7 +50,8 @@ cudaError_t launch_galaxy_prep(const RenderParams& p, int64_t count, unsigned ch
 // Adjoint: records (AdjRecord per planned position) and the fused kernel.
 cudaError_t launch_adjoint_prep(const RenderParams& p, int64_t count, unsigned char* records, cudaStream_t s);
 cudaError_t launch_render_bwd(int n, const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
-                              cudaStream_t s);
+                              int ctas_per_sm, cudaStream_t s);
+int render_bwd_max_ctas(int n);
 
 // Allocation-free forward render (noalloc.cu): the scratch of one call lives
 // in a fixed device array; noalloc_scratch returns its address on `device`.
@@ -49,8 +59,9 @@ cudaError_t noalloc_scratch(int device, unsigned char** out);
 cudaError_t render_noalloc(const RenderParams& proto, int64_t count, uint32_t want, unsigned char* base,
                            int num_sms, int* status, cudaStream_t s);
 
-cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, cudaStream_t s);
+cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, cudaStream_t s);
+int render_fwd_max_ctas(int n);
 
 // Patch sides each direction supports (bit b: N = 32 << b).
 constexpr uint32_t FWD_BUCKETS = 0xF;   // 32, 64, 128, 256

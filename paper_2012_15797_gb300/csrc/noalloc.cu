@@ -75,9 +75,10 @@ cudaError_t render_noalloc(const RenderParams& proto, int64_t count, uint32_t wa
   p.bucket_count = ps.small + NBUCKET;
   p.queue = ps.small + 2 * NBUCKET;
   p.records = records;
+  p.chunk = 8;
   e = launch_galaxy_prep(p, count, records, s);
   for (int b = 0; b < NBUCKET && e == cudaSuccess; ++b)
-    if ((want >> b) & 1) e = launch_render_fwd(bucket_side(b), p, num_sms, s);
+    if ((want >> b) & 1) e = launch_render_fwd(bucket_side(b), p, num_sms, 0, s);
   return e;
 }
 

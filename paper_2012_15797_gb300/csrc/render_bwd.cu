@@ -48,7 +48,6 @@ struct BwdCfg {
   static constexpr int TW1 = twiddle_elems<N, R1>();
   static constexpr int TW2 = Radix<N>::P == 3 ? twiddle_elems<N, (R2 > 1 ? R2 : 2)>() : 0;
   static constexpr int MIN_BLOCKS = N == 32 ? 8 : N == 64 ? 2 : 1;
-  static constexpr int CHUNK = 8;
   // N = 128 does not fit the PSF spectrum beside the work buffers and the
   // gradient patch; it reads the (L2-resident) spectrum from global memory.
   static constexpr bool STAGE_PSF = N <= 64;
@@ -141,14 +140,14 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
       const int b0 = q_ahead;
       if (b0 >= count) return -1;
       q_next = b0;
-      q_end = min(b0 + C::CHUNK, count);
-      q_ahead = atomicAdd(&p.queue[B], C::CHUNK);
+      q_end = min(b0 + p.chunk, count);
+      q_ahead = atomicAdd(&p.queue[B], p.chunk);
     }
     return q_next++;
   };
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
-    q_ahead = atomicAdd(&p.queue[B], C::CHUNK);
+    q_ahead = atomicAdd(&p.queue[B], p.chunk);
     const int p0 = next_position();
     s_pos[0] = p0;
     if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * sizeof(AdjRecord), sizeof(AdjRecord), &bar[1]);
@@ -405,20 +404,37 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
 }
 
 template <int N>
-static cudaError_t launch_bwd(const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
-                              cudaStream_t s) {
+static int bwd_occupancy() {
   using C = BwdCfg<N>;
   static int occ = -1;
   if (occ < 0) {
-    cudaError_t e = cudaFuncSetAttribute(render_bwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_bwd_kernel<N>, C::THREADS, C::SMEM);
-    if (e != cudaSuccess) return e;
+    if (cudaFuncSetAttribute(render_bwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_bwd_kernel<N>, C::THREADS, C::SMEM) != cudaSuccess)
+      return -1;
     if (occ < 1) occ = 1;
   }
-  render_bwd_kernel<N><<<occ * num_sms, C::THREADS, C::SMEM, s>>>(p, grad_out, grad_params);
+  return occ;
+}
+
+template <int N>
+static cudaError_t launch_bwd(const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
+                              int ctas_per_sm, cudaStream_t s) {
+  using C = BwdCfg<N>;
+  const int occ = bwd_occupancy<N>();
+  if (occ < 0) return cudaErrorInvalidConfiguration;
+  const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+  render_bwd_kernel<N><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p, grad_out, grad_params);
   return cudaGetLastError();
+}
+
+int render_bwd_max_ctas(int n) {
+  switch (n) {
+    case 32: return bwd_occupancy<32>();
+    case 64: return bwd_occupancy<64>();
+    case 128: return bwd_occupancy<128>();
+    default: return 0;
+  }
 }
 
 // One warp per planned position (lane = mixture component).
@@ -439,11 +455,11 @@ cudaError_t launch_adjoint_prep(const RenderParams& p, int64_t count, unsigned c
 }
 
 cudaError_t launch_render_bwd(int n, const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
-                              cudaStream_t s) {
+                              int ctas_per_sm, cudaStream_t s) {
   switch (n) {
-    case 32: return launch_bwd<32>(p, grad_out, grad_params, num_sms, s);
-    case 64: return launch_bwd<64>(p, grad_out, grad_params, num_sms, s);
-    case 128: return launch_bwd<128>(p, grad_out, grad_params, num_sms, s);
+    case 32: return launch_bwd<32>(p, grad_out, grad_params, num_sms, ctas_per_sm, s);
+    case 64: return launch_bwd<64>(p, grad_out, grad_params, num_sms, ctas_per_sm, s);
+    case 128: return launch_bwd<128>(p, grad_out, grad_params, num_sms, ctas_per_sm, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -40,7 +40,6 @@ struct FwdCfg {
   static constexpr int TW1 = twiddle_elems<N, R1>();
   static constexpr int TW2 = Radix<N>::P == 3 ? twiddle_elems<N, (R2 > 1 ? R2 : 2)>() : 0;
   static constexpr int MIN_BLOCKS = N == 32 ? 16 : N == 64 ? 3 : 1;
-  static constexpr int CHUNK = 8;
 
   static constexpr size_t off_psf = 0;
   static constexpr size_t off_wa = off_psf + sizeof(float2) * PSF_ELEMS;
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   if constexpr (Radix<N>::P == 3) fill_twiddles<N, C::R2>(tw2, N / C::R2, tid, C::THREADS);
   const int count = p.bucket_count[B];
   const unsigned char* records = p.records + (size_t)p.bucket_start[B] * RECORD_BYTES;
-  // work queue, used by thread 0 only: positions are taken CHUNK at a time and
+  // work queue, used by thread 0 only: positions are taken p.chunk at a time and
   // the next chunk is requested one chunk ahead, so the atomic's latency is
   // off the critical path
   int q_next = 0, q_end = 0, q_ahead = 0;
@@ -116,8 +115,8 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
       const int b0 = q_ahead;
       if (b0 >= count) return -1;
       q_next = b0;
-      q_end = min(b0 + C::CHUNK, count);
-      q_ahead = atomicAdd(&p.queue[B], C::CHUNK);
+      q_end = min(b0 + p.chunk, count);
+      q_ahead = atomicAdd(&p.queue[B], p.chunk);
     }
     return q_next++;
   };
@@ -125,7 +124,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_init(&bar[2], 1);
-    q_ahead = atomicAdd(&p.queue[B], C::CHUNK);
+    q_ahead = atomicAdd(&p.queue[B], p.chunk);
     const int p0 = next_position();
     s_pos[0] = p0;
     if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1]);
@@ -347,28 +346,46 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
 }
 
 template <int N>
-static cudaError_t launch_fwd(const RenderParams& p, int num_sms, cudaStream_t s) {
+static int fwd_occupancy() {
   using C = FwdCfg<N>;
   static int occ = -1;
   if (occ < 0) {
-    cudaError_t e = cudaFuncSetAttribute(render_fwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fwd_kernel<N>, C::THREADS, C::SMEM);
-    if (e != cudaSuccess) return e;
+    if (cudaFuncSetAttribute(render_fwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fwd_kernel<N>, C::THREADS, C::SMEM) != cudaSuccess)
+      return -1;
     if (occ < 1) occ = 1;
   }
-  render_fwd_kernel<N><<<occ * num_sms, C::THREADS, C::SMEM, s>>>(p);
+  return occ;
+}
+
+template <int N>
+static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  using C = FwdCfg<N>;
+  const int occ = fwd_occupancy<N>();
+  if (occ < 0) return cudaErrorInvalidConfiguration;
+  const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+  render_fwd_kernel<N><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, cudaStream_t s) {
+cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
   switch (n) {
-    case 32: return launch_fwd<32>(p, num_sms, s);
-    case 64: return launch_fwd<64>(p, num_sms, s);
-    case 128: return launch_fwd<128>(p, num_sms, s);
+    case 32: return launch_fwd<32>(p, num_sms, ctas_per_sm, s);
+    case 64: return launch_fwd<64>(p, num_sms, ctas_per_sm, s);
+    case 128: return launch_fwd<128>(p, num_sms, ctas_per_sm, s);
     case 256: return launch_render_fwd256(p, num_sms, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+int render_fwd_max_ctas(int n) {
+  switch (n) {
+    case 32: return fwd_occupancy<32>();
+    case 64: return fwd_occupancy<64>();
+    case 128: return fwd_occupancy<128>();
+    case 256: return 1;
+    default: return 0;
   }
 }
 

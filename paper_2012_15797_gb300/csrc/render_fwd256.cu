@@ -31,7 +31,6 @@ constexpr int LS = psf_lstride(N);
 constexpr int WS = wstride<N>();
 constexpr int R1 = Radix<N>::r[1], R2 = Radix<N>::r[2];
 constexpr int TW1 = twiddle_elems<N, R1>(), TW2 = twiddle_elems<N, R2>();
-constexpr int CHUNK = 4;
 constexpr int B = bucket_of(N);
 
 constexpr size_t off_w = 0;                                              // WARPS rows of WS float2
@@ -77,15 +76,15 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
       const int b0 = q_ahead;
       if (b0 >= count) return -1;
       q_next = b0;
-      q_end = min(b0 + CHUNK, count);
-      q_ahead = atomicAdd(&p.queue[B], CHUNK);
+      q_end = min(b0 + p.chunk, count);
+      q_ahead = atomicAdd(&p.queue[B], p.chunk);
     }
     return q_next++;
   };
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
-    q_ahead = atomicAdd(&p.queue[B], CHUNK);
+    q_ahead = atomicAdd(&p.queue[B], p.chunk);
     const int p0 = next_position();
     s_pos[0] = p0;
     if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * RECORD_BYTES, sizeof(GalaxyRecord), &bar[0]);

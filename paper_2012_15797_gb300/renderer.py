@@ -107,9 +107,44 @@ class Renderer:
         capi.mog_render_backward(self.ctx, b, grad_out.data_ptr(), grad_params.data_ptr(), s.cuda_stream)
         return grad_params
 
+    def autotune(self, batch, out, grad_out=None, grad_params=None, reps=3, stream=None):
+        """Times every launch shape per size bucket and keeps the fastest
+        (forward, and the adjoint when gradient buffers are given)."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
+        return capi.mog_autotune(self.ctx, b, out.data_ptr(), grad_out.data_ptr() if grad_out is not None else 0,
+                                 grad_params.data_ptr() if grad_params is not None else 0, s.cuda_stream, reps)
+
+    def graph(self, batch, out):
+        """A captured CUDA graph rendering `batch` into `out` on every launch."""
+        return Graph(self, batch, out)
+
     def sync_status(self, stream=None):
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         capi.mog_sync_status(self.ctx, s.cuda_stream)
+
+
+class Graph:
+    def __init__(self, renderer, batch, out):
+        self.renderer, self.batch, self.out = renderer, batch, out
+        self._b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
+        self.handle = capi.mog_graph_capture(renderer.ctx, self._b, out.data_ptr())
+
+    def launch(self, stream=None):
+        s = stream if stream is not None else torch.cuda.current_stream(self.renderer.device)
+        capi.mog_graph_launch(self.handle, s.cuda_stream)
+        return self.out
+
+    def close(self):
+        if self.handle is not None:
+            capi.mog_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def patches(out, batch):
