@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the mixed-size / gradient / per-galaxy lines")
     ap.add_argument("--extra-steps", type=int, default=20)
+    ap.add_argument("--only", choices=("fwd", "grad", "mixed"),
+                    help="profiling mode: run just this workload (--galaxies of it) for --warmup + --steps "
+                         "and print its time")
     return ap.parse_args()
 
 
@@ -599,8 +602,48 @@ def run_reference(args):
     }))
 
 
+def run_only(args):
+    """Small single-workload runs for profilers (no JSON bench line)."""
+    import torch
+    from paper_2012_15797_gb300.build import build
+    build()
+    from paper_2012_15797_gb300.renderer import Renderer, to_device
+    from workloads import config0_psf, config1_galaxies, config2_galaxies, config2_psfs, load_profile_tables
+    tables = load_profile_tables()
+    if args.only == "mixed":
+        psfs = config2_psfs(8)
+        gals = config2_galaxies(args.galaxies, n_psf=8)
+    else:
+        psfs = [config0_psf()]
+        gals = config1_galaxies(args.galaxies)
+    r = Renderer(tables, psfs)
+    b = to_device(gals)
+    out = torch.empty(b.total, device="cuda")
+    go = torch.randn(b.total, device="cuda") if args.only == "grad" else None
+
+    def step():
+        if args.only == "grad":
+            r.render_backward(b, go)
+        else:
+            r.render(b, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    r.sync_status()
+    print(json.dumps({"only": args.only, "galaxies": len(gals), "ms_per_step": (time.perf_counter() - t) / max(args.steps, 1) * 1e3}))
+    r.close()
+
+
 def main():
     args = parse_args()
+    if args.only:
+        run_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
