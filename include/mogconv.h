@@ -202,6 +202,66 @@ mog_status mog_graph_launch(mog_graph* graph, void* stream);
 mog_status mog_graph_destroy(mog_graph* graph);
 
 /*
+ * Serving: continuous batching of render + gradient requests from many
+ * concurrent model fits (the forward model of Section 2 and its adjoint,
+ * evaluated for chi^2 fitting).
+ *
+ * A fit's state stays on the device: its observed patches, inverse
+ * variances and the fixed fields of its galaxies, registered once with
+ * mog_server_add_fit (device pointers, caller-owned, kept valid while the
+ * server lives).  A request names a fit and galaxies [first, first + count)
+ * and carries their current parameters (host, count x 6: flux, x, y, log_re,
+ * e1, e2, copied at submission); its answer is written to the caller's host
+ * buffers when done: grads (count x 6) = d chi^2 / d parameters and chi2
+ * (count, may be NULL) with chi^2 = sum_pixels ivar (model - data)^2.
+ *
+ * A scheduler thread admits pending requests, oldest first, into one
+ * micro-batch while it fits the device-memory budget (admission by memory)
+ * and max_batch_galaxies (0: one request per batch, the one-launch-per-
+ * request form), and launches it on a free lane (stream); up to `lanes`
+ * micro-batches are in flight while new requests queue.  Latency is measured
+ * from submission to results available.
+ */
+typedef struct mog_server mog_server;
+typedef struct mog_server_config {
+  int64_t budget_bytes;        /* device memory for in-flight micro-batches */
+  int lanes;                   /* micro-batches in flight (1..16) */
+  int64_t max_batch_galaxies;  /* per micro-batch; 0 = one request per batch */
+} mog_server_config;
+typedef struct mog_fit_state {
+  int64_t count;               /* galaxies of the fit */
+  const float* sersic_n;       /* device, count */
+  const int32_t* profile;      /* device, count */
+  const int32_t* psf;          /* device, count */
+  const int32_t* size;         /* device, count: patch side (32..128 for gradients) */
+  const int64_t* data_offset;  /* device, count: offset of the observed patch in data (multiple of 4) */
+  const float* data;           /* device: observed patches */
+  const float* ivar;           /* device, count: inverse variance of each patch's pixels */
+} mog_fit_state;
+typedef struct mog_request {
+  int32_t fit;
+  int64_t first, count;
+  const float* params;         /* host, count x 6 */
+  float* grads;                /* host, count x 6 (out) */
+  float* chi2;                 /* host, count (out, optional) */
+} mog_request;
+mog_status mog_server_create(mog_ctx* ctx, const mog_server_config* cfg, mog_server** server);
+mog_status mog_server_add_fit(mog_server* server, const mog_fit_state* fit, int* fit_id);
+mog_status mog_server_submit(mog_server* server, const mog_request* req, uint64_t* ticket);
+/* Blocks until the request is done (or timeout_s passes: MOG_ERR_TIMEOUT). */
+mog_status mog_server_wait(mog_server* server, uint64_t ticket, double timeout_s, double* latency_s);
+/* Load generation: submits reqs[i] at arrival_s[i] seconds after the call,
+ * from a background thread; tickets[i] (host, n) is set at submission. */
+mog_status mog_server_replay(mog_server* server, const mog_request* reqs, const double* arrival_s, int64_t n,
+                             uint64_t* tickets);
+mog_status mog_server_replay_join(mog_server* server);
+/* out[6]: requests done, galaxies done, micro-batches, largest batch (galaxies),
+ * most lanes in flight at once, requests pending. */
+mog_status mog_server_stats(mog_server* server, int64_t* out);
+/* Finishes pending work (up to 60 s) and releases the server. */
+mog_status mog_server_destroy(mog_server* server);
+
+/*
  * Kernel timing for measurement: while enabled, every render-kernel launch is
  * bracketed by CUDA events recorded on its own stream.  mog_read_timing
  * waits for the recorded events and returns, per patch side N = 32 << b

@@ -33,6 +33,8 @@ EXPORTED = (
     "mog_create_psf", "mog_destroy_psf", "mog_render_batch", "mog_sync_status",
     "mog_set_timing", "mog_read_timing", "mog_render_backward", "mog_render_batch_noalloc",
     "mog_autotune", "mog_graph_capture", "mog_graph_launch", "mog_graph_destroy",
+    "mog_server_create", "mog_server_add_fit", "mog_server_submit", "mog_server_wait", "mog_server_replay",
+    "mog_server_replay_join", "mog_server_stats", "mog_server_destroy",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -52,6 +54,21 @@ class mog_batch(ctypes.Structure):
         ("size", ctypes.c_void_p), ("offset", ctypes.c_void_p),
         ("size_mask", ctypes.c_uint32),
     ]
+
+
+class mog_server_config(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("lanes", ctypes.c_int), ("max_batch_galaxies", ctypes.c_int64)]
+
+
+class mog_fit_state(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("sersic_n", ctypes.c_void_p), ("profile", ctypes.c_void_p),
+                ("psf", ctypes.c_void_p), ("size", ctypes.c_void_p), ("data_offset", ctypes.c_void_p),
+                ("data", ctypes.c_void_p), ("ivar", ctypes.c_void_p)]
+
+
+class mog_request(ctypes.Structure):
+    _fields_ = [("fit", ctypes.c_int32), ("first", ctypes.c_int64), ("count", ctypes.c_int64),
+                ("params", ctypes.c_void_p), ("grads", ctypes.c_void_p), ("chi2", ctypes.c_void_p)]
 
 
 def _load():
@@ -74,6 +91,14 @@ def _load():
         "mog_graph_capture": ([VP, P(mog_batch), VP, P(VP)], I),
         "mog_graph_launch": ([VP, VP], I),
         "mog_graph_destroy": ([VP], I),
+        "mog_server_create": ([VP, P(mog_server_config), P(VP)], I),
+        "mog_server_add_fit": ([VP, P(mog_fit_state), P(I)], I),
+        "mog_server_submit": ([VP, P(mog_request), P(ctypes.c_uint64)], I),
+        "mog_server_wait": ([VP, ctypes.c_uint64, ctypes.c_double, P(ctypes.c_double)], I),
+        "mog_server_replay": ([VP, P(mog_request), P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_uint64)], I),
+        "mog_server_replay_join": ([VP], I),
+        "mog_server_stats": ([VP, P(ctypes.c_int64)], I),
+        "mog_server_destroy": ([VP], I),
         "mog_sync_status": ([VP, VP], I),
         "mog_set_timing": ([VP, I], I),
         "mog_read_timing": ([VP, P(ctypes.c_double), P(ctypes.c_int64)], I),

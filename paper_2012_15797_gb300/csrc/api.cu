@@ -6,41 +6,9 @@
 #include <string>
 #include <vector>
 
-#include "internal.h"
+#include "ctx.h"
 
 using namespace mog;
-
-struct mog_ctx {
-  int device = 0;
-  int num_sms = 0;
-  DevProfile* d_profiles = nullptr;
-  DevPsf* d_psfs = nullptr;
-  std::vector<DevPsf> h_psfs;
-  std::vector<float2*> psf_mem;  // one allocation per PSF holding every bucket's spectrum
-  int* d_status = nullptr;
-  PlanScratch plan{};
-  int64_t order_cap = 0;
-  unsigned char* records = nullptr;   // RECORD_BYTES per planned galaxy
-  unsigned char* adj_records = nullptr;   // sizeof(AdjRecord) per planned galaxy
-  double2* d_dft_scratch = nullptr;
-  std::string last_error;
-  // measurement hooks
-  bool timing = false;
-  struct Timed {
-    int bucket;
-    cudaEvent_t a, b;
-  };
-  std::vector<Timed> pending;
-  std::vector<cudaEvent_t> event_pool;
-  double acc_ms[NBUCKET] = {0, 0, 0, 0};
-  int64_t acc_n[NBUCKET] = {0, 0, 0, 0};
-  // launch shapes per bucket (mog_autotune) and the parallel branches
-  LaunchShape tune_fwd[NBUCKET], tune_bwd[NBUCKET];
-  cudaStream_t side[NBUCKET] = {};
-  cudaEvent_t fork_ev = nullptr;
-  cudaEvent_t join_ev[NBUCKET] = {};
-  cudaStream_t capture = nullptr;
-};
 
 struct mog_graph {
   mog_ctx* ctx = nullptr;
@@ -48,7 +16,7 @@ struct mog_graph {
   cudaGraphExec_t exec = nullptr;
 };
 
-namespace {
+namespace mog {
 
 mog_status fail(mog_ctx* ctx, mog_status code, const char* fmt, ...) {
   if (ctx) {
@@ -67,12 +35,39 @@ mog_status cuda_fail(mog_ctx* ctx, cudaError_t e, const char* what) {
               cudaGetErrorString(e));
 }
 
-#define MOG_CUDA(ctx, expr)                                 \
-  do {                                                      \
-    cudaError_t e_ = (expr);                                \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
-  } while (0)
+cudaError_t workspace_init(Workspace* ws) {
+  const size_t nkey = sizeof(int32_t) * NBUCKET * MOG_MAX_PSFS;
+  cudaError_t e = cudaMalloc(&ws->plan.hist, nkey);
+  if (e == cudaSuccess) e = cudaMemset(ws->plan.hist, 0, nkey);
+  if (e == cudaSuccess) e = cudaMalloc(&ws->plan.key_off, nkey);
+  if (e == cudaSuccess) e = cudaMalloc(&ws->plan.small, sizeof(int32_t) * 4 * NBUCKET);
+  if (e == cudaSuccess) e = cudaMemset(ws->plan.small, 0, sizeof(int32_t) * 4 * NBUCKET);
+  for (int b = 0; b < NBUCKET && e == cudaSuccess; ++b) {
+    e = cudaStreamCreateWithFlags(&ws->side[b], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ws->join_ev[b], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ws->fork_ev, cudaEventDisableTiming);
+  return e;
+}
 
+void workspace_free(Workspace* ws) {
+  cudaFree(ws->plan.hist);
+  cudaFree(ws->plan.key_off);
+  cudaFree(ws->plan.small);
+  cudaFree(ws->plan.order);
+  cudaFree(ws->records);
+  cudaFree(ws->adj_records);
+  for (int b = 0; b < NBUCKET; ++b) {
+    if (ws->side[b]) cudaStreamDestroy(ws->side[b]);
+    if (ws->join_ev[b]) cudaEventDestroy(ws->join_ev[b]);
+  }
+  if (ws->fork_ev) cudaEventDestroy(ws->fork_ev);
+  *ws = Workspace{};
+}
+
+}  // namespace mog
+
+namespace {
 
 BatchView view_of(const mog_batch* b) {
   return BatchView{b->flux, b->x,      b->y,    b->log_re, b->e1,  b->e2,
@@ -88,21 +83,21 @@ cudaError_t take_event(mog_ctx* ctx, cudaEvent_t* ev) {
   return cudaEventCreate(ev);
 }
 
-mog_status ensure_order_capacity(mog_ctx* ctx, int64_t count) {
-  if (count <= ctx->order_cap) return MOG_OK;
-  int64_t cap = ctx->order_cap ? ctx->order_cap : 1024;
+mog_status ensure_capacity(mog_ctx* ctx, Workspace* ws, int64_t count) {
+  if (count <= ws->cap) return MOG_OK;
+  int64_t cap = ws->cap ? ws->cap : 1024;
   while (cap < count) cap *= 2;
-  if (ctx->plan.order) MOG_CUDA(ctx, cudaFree(ctx->plan.order));
-  if (ctx->records) MOG_CUDA(ctx, cudaFree(ctx->records));
-  if (ctx->adj_records) MOG_CUDA(ctx, cudaFree(ctx->adj_records));
-  ctx->plan.order = nullptr;
-  ctx->records = nullptr;
-  ctx->adj_records = nullptr;
-  ctx->order_cap = 0;
-  MOG_CUDA(ctx, cudaMalloc(&ctx->plan.order, sizeof(int32_t) * cap));
-  MOG_CUDA(ctx, cudaMalloc(&ctx->records, (size_t)RECORD_BYTES * cap));
-  MOG_CUDA(ctx, cudaMalloc(&ctx->adj_records, sizeof(AdjRecord) * cap));
-  ctx->order_cap = cap;
+  if (ws->plan.order) MOG_CUDA(ctx, cudaFree(ws->plan.order));
+  if (ws->records) MOG_CUDA(ctx, cudaFree(ws->records));
+  if (ws->adj_records) MOG_CUDA(ctx, cudaFree(ws->adj_records));
+  ws->plan.order = nullptr;
+  ws->records = nullptr;
+  ws->adj_records = nullptr;
+  ws->cap = 0;
+  MOG_CUDA(ctx, cudaMalloc(&ws->plan.order, sizeof(int32_t) * cap));
+  MOG_CUDA(ctx, cudaMalloc(&ws->records, (size_t)RECORD_BYTES * cap));
+  MOG_CUDA(ctx, cudaMalloc(&ws->adj_records, sizeof(AdjRecord) * cap));
+  ws->cap = cap;
   return MOG_OK;
 }
 
@@ -123,18 +118,8 @@ mog_status mog_create_context(mog_ctx** out, int device) {
   if (e == cudaSuccess) e = cudaMemset(ctx->d_psfs, 0, sizeof(DevPsf) * MOG_MAX_PSFS);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
-  const size_t nkey = sizeof(int32_t) * NBUCKET * MOG_MAX_PSFS;
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->plan.hist, nkey);
-  if (e == cudaSuccess) e = cudaMemset(ctx->plan.hist, 0, nkey);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->plan.key_off, nkey);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->plan.small, sizeof(int32_t) * 4 * NBUCKET);
-  if (e == cudaSuccess) e = cudaMemset(ctx->plan.small, 0, sizeof(int32_t) * 4 * NBUCKET);
+  if (e == cudaSuccess) e = workspace_init(&ctx->ws);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dft_scratch, sizeof(double2) * 256 * 129);
-  for (int b = 0; b < NBUCKET && e == cudaSuccess; ++b) {
-    e = cudaStreamCreateWithFlags(&ctx->side[b], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev[b], cudaEventDisableTiming);
-  }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     mog_destroy_context(ctx);
@@ -154,23 +139,13 @@ mog_status mog_destroy_context(mog_ctx* ctx) {
   cudaFree(ctx->d_profiles);
   cudaFree(ctx->d_psfs);
   cudaFree(ctx->d_status);
-  cudaFree(ctx->plan.hist);
-  cudaFree(ctx->plan.key_off);
-  cudaFree(ctx->plan.small);
-  cudaFree(ctx->plan.order);
-  cudaFree(ctx->records);
-  cudaFree(ctx->adj_records);
+  workspace_free(&ctx->ws);
   cudaFree(ctx->d_dft_scratch);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
   }
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
-  for (int b = 0; b < NBUCKET; ++b) {
-    if (ctx->side[b]) cudaStreamDestroy(ctx->side[b]);
-    if (ctx->join_ev[b]) cudaEventDestroy(ctx->join_ev[b]);
-  }
-  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
   delete ctx;
   return MOG_OK;
@@ -276,7 +251,7 @@ mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id) {
 
 }  // extern "C"
 
-namespace {
+namespace mog {
 
 mog_status check_batch(mog_ctx* ctx, const mog_batch* batch) {
   if (!batch || batch->count < 0) return fail(ctx, MOG_ERR_ARG, "null batch or negative count");
@@ -287,43 +262,47 @@ mog_status check_batch(mog_ctx* ctx, const mog_batch* batch) {
   return MOG_OK;
 }
 
+}  // namespace mog
+
+namespace {
+
 // Plans the batch on stream s and fills the launch parameters.
-mog_status plan_batch(mog_ctx* ctx, const mog_batch* batch, float* out, uint32_t supported, cudaStream_t s,
-                      RenderParams* p) {
+mog_status plan_batch(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, uint32_t supported,
+                      cudaStream_t s, RenderParams* p) {
   MOG_CUDA(ctx, cudaSetDevice(ctx->device));
-  mog_status st = ensure_order_capacity(ctx, batch->count);
+  mog_status st = ensure_capacity(ctx, ws, batch->count);
   if (st != MOG_OK) return st;
   const BatchView bv = view_of(batch);
-  MOG_CUDA(ctx, launch_plan(bv, batch->count, ctx->plan, supported, ctx->d_status, s));
+  MOG_CUDA(ctx, launch_plan(bv, batch->count, ws->plan, supported, ctx->d_status, s));
   *p = RenderParams{};
   p->b = bv;
   p->out = out;
   p->profiles = ctx->d_profiles;
   p->psfs = ctx->d_psfs;
-  p->order = ctx->plan.order;
-  p->bucket_start = ctx->plan.small;
-  p->bucket_count = ctx->plan.small + NBUCKET;
-  p->queue = ctx->plan.small + 2 * NBUCKET;
+  p->order = ws->plan.order;
+  p->bucket_start = ws->plan.small;
+  p->bucket_count = ws->plan.small + NBUCKET;
+  p->queue = ws->plan.small + 2 * NBUCKET;
   p->status = ctx->d_status;
   return MOG_OK;
 }
 
 // Launches one kernel per requested size bucket.  With more than one bucket
-// the kernels run on parallel branches (context side streams forked from and
-// joined back into `s` with events), so a CUDA graph captured around the call
-// holds them as parallel nodes and a bucket's tail overlaps the next one.
+// the kernels run on parallel branches (the workspace's side streams forked
+// from and joined back into `s` with events), so a CUDA graph captured around
+// the call holds them as parallel nodes and a bucket's tail overlaps the next.
 template <class Launch>
-mog_status launch_buckets(mog_ctx* ctx, const mog_batch* batch, uint32_t supported, cudaStream_t s,
+mog_status launch_buckets(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, uint32_t supported, cudaStream_t s,
                           Launch&& launch) {
   const uint32_t want = batch->size_mask ? (batch->size_mask & supported) : supported;
   const bool fork = __builtin_popcount(want) > 1;
-  if (fork) MOG_CUDA(ctx, cudaEventRecord(ctx->fork_ev, s));
+  if (fork) MOG_CUDA(ctx, cudaEventRecord(ws->fork_ev, s));
   for (int b = 0; b < NBUCKET; ++b) {
     if (!((want >> b) & 1)) continue;
     cudaStream_t bs = s;
     if (fork) {
-      bs = ctx->side[b];
-      MOG_CUDA(ctx, cudaStreamWaitEvent(bs, ctx->fork_ev, 0));
+      bs = ws->side[b];
+      MOG_CUDA(ctx, cudaStreamWaitEvent(bs, ws->fork_ev, 0));
     }
     mog_ctx::Timed t{b, nullptr, nullptr};
     if (ctx->timing) {
@@ -337,8 +316,8 @@ mog_status launch_buckets(mog_ctx* ctx, const mog_batch* batch, uint32_t support
       ctx->pending.push_back(t);
     }
     if (fork) {
-      MOG_CUDA(ctx, cudaEventRecord(ctx->join_ev[b], bs));
-      MOG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->join_ev[b], 0));
+      MOG_CUDA(ctx, cudaEventRecord(ws->join_ev[b], bs));
+      MOG_CUDA(ctx, cudaStreamWaitEvent(s, ws->join_ev[b], 0));
     }
   }
   return MOG_OK;
@@ -346,45 +325,56 @@ mog_status launch_buckets(mog_ctx* ctx, const mog_batch* batch, uint32_t support
 
 }  // namespace
 
-extern "C" {
+namespace mog {
 
-mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
-  if (!ctx) return MOG_ERR_ARG;
+mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s) {
   mog_status st = check_batch(ctx, batch);
   if (st != MOG_OK) return st;
   if (batch->count == 0) return MOG_OK;
   if (!out || (reinterpret_cast<uintptr_t>(out) & 15)) return fail(ctx, MOG_ERR_ARG, "out must be 16-byte aligned");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   RenderParams p;
-  if ((st = plan_batch(ctx, batch, out, FWD_BUCKETS, s, &p)) != MOG_OK) return st;
-  p.records = ctx->records;
-  MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ctx->records, s));
-  return launch_buckets(ctx, batch, FWD_BUCKETS, s, [&](int n, cudaStream_t bs) {
+  if ((st = plan_batch(ctx, ws, batch, out, FWD_BUCKETS, s, &p)) != MOG_OK) return st;
+  p.records = ws->records;
+  MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ws->records, s));
+  return launch_buckets(ctx, ws, batch, FWD_BUCKETS, s, [&](int n, cudaStream_t bs) {
     RenderParams q = p;
     q.chunk = ctx->tune_fwd[bucket_of(n)].chunk;
     return launch_render_fwd(n, q, ctx->num_sms, ctx->tune_fwd[bucket_of(n)].ctas_per_sm, bs);
   });
 }
 
-mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,
-                               void* stream) {
-  if (!ctx) return MOG_ERR_ARG;
+mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, const float* grad_out,
+                         float* grad_params, cudaStream_t s) {
   mog_status st = check_batch(ctx, batch);
   if (st != MOG_OK) return st;
   if (batch->count == 0) return MOG_OK;
   if (!grad_out || (reinterpret_cast<uintptr_t>(grad_out) & 15))
     return fail(ctx, MOG_ERR_ARG, "grad_out must be 16-byte aligned");
   if (!grad_params) return fail(ctx, MOG_ERR_ARG, "null grad_params");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   RenderParams p;
-  if ((st = plan_batch(ctx, batch, nullptr, BWD_BUCKETS, s, &p)) != MOG_OK) return st;
-  p.records = ctx->adj_records;
-  MOG_CUDA(ctx, launch_adjoint_prep(p, batch->count, ctx->adj_records, s));
-  return launch_buckets(ctx, batch, BWD_BUCKETS, s, [&](int n, cudaStream_t bs) {
+  if ((st = plan_batch(ctx, ws, batch, nullptr, BWD_BUCKETS, s, &p)) != MOG_OK) return st;
+  p.records = ws->adj_records;
+  MOG_CUDA(ctx, launch_adjoint_prep(p, batch->count, ws->adj_records, s));
+  return launch_buckets(ctx, ws, batch, BWD_BUCKETS, s, [&](int n, cudaStream_t bs) {
     RenderParams q = p;
     q.chunk = ctx->tune_bwd[bucket_of(n)].chunk;
     return launch_render_bwd(n, q, grad_out, grad_params, ctx->num_sms, ctx->tune_bwd[bucket_of(n)].ctas_per_sm, bs);
   });
+}
+
+}  // namespace mog
+
+extern "C" {
+
+mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  return render_with(ctx, &ctx->ws, batch, out, static_cast<cudaStream_t>(stream));
+}
+
+mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,
+                               void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  return backward_with(ctx, &ctx->ws, batch, grad_out, grad_params, static_cast<cudaStream_t>(stream));
 }
 
 mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {

@@ -1,0 +1,74 @@
+// Host-side library state shared by the C-ABI (api.cu) and the serving
+// runtime (server.cu).
+#pragma once
+
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace mog {
+
+// Per-call scratch of the batched render / adjoint: planner counters and
+// galaxy order, per-galaxy records, and the side streams the size buckets
+// run on.  Calls that may overlap on the GPU need separate workspaces.
+struct Workspace {
+  PlanScratch plan{};
+  int64_t cap = 0;                       // galaxies the order / records hold
+  unsigned char* records = nullptr;      // RECORD_BYTES per planned galaxy
+  unsigned char* adj_records = nullptr;  // sizeof(AdjRecord) per planned galaxy
+  cudaStream_t side[NBUCKET] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[NBUCKET] = {};
+};
+
+cudaError_t workspace_init(Workspace* ws);
+void workspace_free(Workspace* ws);
+
+}  // namespace mog
+
+struct mog_ctx {
+  int device = 0;
+  int num_sms = 0;
+  mog::DevProfile* d_profiles = nullptr;
+  mog::DevPsf* d_psfs = nullptr;
+  std::vector<mog::DevPsf> h_psfs;
+  std::vector<float2*> psf_mem;  // one allocation per PSF holding every bucket's spectrum
+  int* d_status = nullptr;
+  double2* d_dft_scratch = nullptr;
+  mog::Workspace ws;             // the workspace of the plain entry points
+  std::string last_error;
+  // measurement hooks
+  bool timing = false;
+  struct Timed {
+    int bucket;
+    cudaEvent_t a, b;
+  };
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double acc_ms[mog::NBUCKET] = {0, 0, 0, 0};
+  int64_t acc_n[mog::NBUCKET] = {0, 0, 0, 0};
+  // launch shapes per bucket (mog_autotune)
+  mog::LaunchShape tune_fwd[mog::NBUCKET], tune_bwd[mog::NBUCKET];
+  cudaStream_t capture = nullptr;
+};
+
+namespace mog {
+
+mog_status fail(mog_ctx* ctx, mog_status code, const char* fmt, ...);
+mog_status cuda_fail(mog_ctx* ctx, cudaError_t e, const char* what);
+
+#define MOG_CUDA(ctx, expr)                                      \
+  do {                                                           \
+    cudaError_t e_ = (expr);                                     \
+    if (e_ != cudaSuccess) return mog::cuda_fail(ctx, e_, #expr); \
+  } while (0)
+
+mog_status check_batch(mog_ctx* ctx, const mog_batch* batch);
+// Batched render / adjoint with an explicit workspace (grows it if needed).
+mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s);
+mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, const float* grad_out,
+                         float* grad_params, cudaStream_t s);
+
+}  // namespace mog

@@ -33,10 +33,14 @@ constexpr int R1 = Radix<N>::r[1], R2 = Radix<N>::r[2];
 constexpr int TW1 = twiddle_elems<N, R1>(), TW2 = twiddle_elems<N, R2>();
 constexpr int B = bucket_of(N);
 
+// Staging rows hold the 32 columns of a round for one row pair, padded to 33
+// so that the 32 lanes of a warp (16 row pairs each for the two column
+// halves) land on distinct banks; the mirrored array is offset by 8 float2.
+constexpr int SSTR = WARPS + 1;
 constexpr size_t off_w = 0;                                              // WARPS rows of WS float2
-constexpr size_t off_sa = off_w + sizeof(float2) * WARPS * WS;            // staging [p][32]
-constexpr size_t off_sb = off_sa + sizeof(float2) * (N / 2) * WARPS;      // mirrored columns
-constexpr size_t off_tw = off_sb + sizeof(float2) * (N / 2) * WARPS;
+constexpr size_t off_sa = off_w + sizeof(float2) * WARPS * WS;            // staging [p][SSTR]
+constexpr size_t off_sb = off_sa + sizeof(float2) * ((N / 2) * SSTR + 8); // mirrored columns
+constexpr size_t off_tw = off_sb + sizeof(float2) * (N / 2) * SSTR;
 constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
 constexpr size_t off_py = off_px + sizeof(float2) * H;
 constexpr size_t off_nyq = off_py + sizeof(float2) * N;
@@ -218,12 +222,12 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
             const float2 A = odd ? other : mine, Bv = odd ? mine : other;
             const int pr = stockham_out_index<N, R2>(j, NS, qq, m) >> 1;
             if (k > 0) {
-              if (!odd) SA[pr * WARPS + f] = make_float2(A.x - Bv.y, A.y + Bv.x);
-              else SB[pr * WARPS + f] = make_float2(A.x + Bv.y, Bv.x - A.y);
+              if (!odd) SA[pr * SSTR + f] = make_float2(A.x - Bv.y, A.y + Bv.x);
+              else SB[pr * SSTR + f] = make_float2(A.x + Bv.y, Bv.x - A.y);
             } else {
               // column 0 in SA, column N/2 in SB's slot 0
-              if (!odd) SA[pr * WARPS] = make_float2(A.x, Bv.x);
-              else SB[pr * WARPS] = make_float2(A.y, Bv.y);
+              if (!odd) SA[pr * SSTR] = make_float2(A.x, Bv.x);
+              else SB[pr * SSTR] = make_float2(A.y, Bv.y);
             }
           }
       }
@@ -232,11 +236,11 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
       for (int i = tid; i < (N / 2) * WARPS * 2; i += THREADS) {
         const int pr = i / (2 * WARPS), t = i % (2 * WARPS);
         if (t < WARPS) {
-          zbuf[pr * N + WARPS * round + t] = SA[pr * WARPS + t];
+          zbuf[pr * N + WARPS * round + t] = SA[pr * SSTR + t];
         } else {
           const int u = t - WARPS;
           const int col = (round == 0 && u == 0) ? N / 2 : N - WARPS * round - u;
-          zbuf[pr * N + col] = SB[pr * WARPS + u];
+          zbuf[pr * N + col] = SB[pr * SSTR + u];
         }
       }
       __syncthreads();

@@ -1,0 +1,131 @@
+"""Python handle of the library's serving runtime (continuous batching of
+render + gradient requests from many fits).  Marshalling only: scheduling,
+admission, batching and all device work run in the library (server.cu)."""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+class Server:
+    def __init__(self, renderer, budget_bytes=16 << 30, lanes=4, max_batch_galaxies=32768):
+        self.renderer = renderer
+        cfg = capi.mog_server_config(int(budget_bytes), int(lanes), int(max_batch_galaxies))
+        h = ctypes.c_void_p()
+        capi._check(renderer.ctx, capi.library().mog_server_create(renderer.ctx, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._fits = []       # keep device tensors alive
+        self._live = {}       # ticket -> (params, grads, chi2)
+
+    def add_fit(self, sersic_n, profile, psf, size, data_offset, data, ivar):
+        """Device tensors of one fit: float32 sersic_n, int32 profile, psf,
+        size, int64 data_offset, float32 data (packed patches), float32 ivar."""
+        t = dict(sersic_n=sersic_n, profile=profile, psf=psf, size=size, data_offset=data_offset, data=data, ivar=ivar)
+        for k, v in t.items():
+            assert v.is_cuda and v.is_contiguous(), k
+        fs = capi.mog_fit_state(int(size.numel()), *(t[k].data_ptr() for k in
+                                                     ("sersic_n", "profile", "psf", "size", "data_offset", "data",
+                                                      "ivar")))
+        fid = ctypes.c_int(-1)
+        capi._check(self.renderer.ctx, capi.library().mog_server_add_fit(self.handle, ctypes.byref(fs), ctypes.byref(fid)))
+        self._fits.append(t)
+        return fid.value
+
+    def _request(self, fit, first, params):
+        params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1, 6)
+        grads = np.full(params.shape, np.nan, dtype=np.float32)
+        chi2 = np.full(params.shape[0], np.nan, dtype=np.float32)
+        req = capi.mog_request(int(fit), int(first), int(params.shape[0]), params.ctypes.data, grads.ctypes.data,
+                               chi2.ctypes.data)
+        return req, (params, grads, chi2)
+
+    def submit(self, fit, first, params):
+        req, keep = self._request(fit, first, params)
+        t = ctypes.c_uint64()
+        capi._check(self.renderer.ctx, capi.library().mog_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._live[t.value] = keep
+        return t.value
+
+    def wait(self, ticket, timeout=60.0):
+        """Returns (grads (count, 6), chi2 (count,), latency seconds)."""
+        lat = ctypes.c_double()
+        st = capi.library().mog_server_wait(self.handle, ctypes.c_uint64(ticket), float(timeout), ctypes.byref(lat))
+        keep = self._live.pop(ticket)
+        capi._check(self.renderer.ctx, st)
+        return keep[1], keep[2], lat.value
+
+    def replay(self, requests, arrival_s):
+        """requests: list of (fit, first, params (count, 6)); submitted by a
+        library thread at arrival_s[i] seconds from now.  Returns the ticket
+        array (filled as requests are submitted) and the kept buffers."""
+        n = len(requests)
+        arr = (capi.mog_request * n)()
+        keeps = []
+        for i, (fit, first, params) in enumerate(requests):
+            arr[i], keep = self._request(fit, first, params)
+            keeps.append(keep)
+        times = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        tickets = np.zeros(n, dtype=np.uint64)
+        capi._check(self.renderer.ctx, capi.library().mog_server_replay(
+            self.handle, arr, times.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n,
+            tickets.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        self._replay_keep = (arr, times, tickets, keeps)
+        return tickets, keeps
+
+    def replay_join(self):
+        capi._check(self.renderer.ctx, capi.library().mog_server_replay_join(self.handle))
+
+    def wait_replayed(self, tickets, keeps, timeout=120.0):
+        """Waits for every replayed request; returns their latencies."""
+        self.replay_join()
+        lat = np.zeros(len(tickets))
+        for i, t in enumerate(tickets):
+            if int(t) == 0:
+                raise RuntimeError(f"replayed request {i} was not submitted")
+            l = ctypes.c_double()
+            capi._check(self.renderer.ctx, capi.library().mog_server_wait(self.handle, ctypes.c_uint64(int(t)),
+                                                                           float(timeout), ctypes.byref(l)))
+            lat[i] = l.value
+        return lat
+
+    def stats(self):
+        out = (ctypes.c_int64 * 6)()
+        capi._check(self.renderer.ctx, capi.library().mog_server_stats(self.handle, out))
+        keys = ("requests", "galaxies", "batches", "max_batch_galaxies", "max_lanes_in_flight", "pending")
+        return dict(zip(keys, list(out)))
+
+    def close(self):
+        if self.handle is not None:
+            capi.library().mog_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_fits(renderer, fits_gals, noise_seed=0, sigma_frac=0.01):
+    """Device fit state for a list of ``workloads.Galaxies`` (one per fit):
+    observed patches rendered from the galaxies' parameters (the fits'
+    'truth') plus Gaussian noise of sigma_frac times each patch's peak, and
+    ivar = 1 / sigma^2 per patch.  Returns a list of dicts of device tensors."""
+    from .renderer import to_device
+    gen = torch.Generator(device="cuda").manual_seed(noise_seed)
+    out = []
+    for gals in fits_gals:
+        b = to_device(gals)
+        img = renderer.render(b)
+        peaks = torch.stack([img[int(o):int(o) + int(n) ** 2].amax() for o, n in zip(b.offsets, b.sizes)])
+        sigma = sigma_frac * peaks
+        noise = torch.randn(img.shape, device="cuda", generator=gen)
+        scale = torch.repeat_interleave(sigma, torch.from_numpy(np.asarray(b.sizes, np.int64) ** 2).cuda())
+        data = img + scale * noise
+        out.append(dict(sersic_n=b.tensors["sersic_n"], profile=b.tensors["profile"], psf=b.tensors["psf"],
+                        size=b.tensors["size"], data_offset=b.tensors["offset"], data=data,
+                        ivar=(1.0 / sigma ** 2).float().contiguous()))
+    return out
