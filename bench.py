@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the mixed-size / gradient / per-galaxy lines")
     ap.add_argument("--extra-steps", type=int, default=20)
-    ap.add_argument("--only", choices=("fwd", "grad", "mixed"),
+    ap.add_argument("--only", choices=("fwd", "grad", "mixed", "serving"),
                     help="profiling mode: run just this workload (--galaxies of it) for --warmup + --steps "
                          "and print its time")
     return ap.parse_args()
@@ -392,6 +392,58 @@ def extra_per_galaxy(tables, psf, device, n=2000):
             "note": "one mog_render_batch call per 64x64 galaxy of the fixed-size distribution"}
 
 
+def extra_serving(tables, device, duration_ms=500.0, max_side=128):
+    """1000 concurrent fits of 512 galaxies (Sersic, sizes as the mixed
+    workload), render + gradient requests of 1-512 galaxies with Poisson
+    arrivals at 20k galaxies/ms, 64 PSFs resident, 16 GB admission budget.
+    Runs the offered load, then half the measured capacity, then the
+    one-launch-per-request form at that half load."""
+    import numpy as np
+    import torch
+    from paper_2012_15797_gb300.renderer import Renderer
+    from paper_2012_15797_gb300.serving import Server, make_fits
+    from workloads import config2_psfs, serving_workload
+
+    fits, arrival_ms, reqs = serving_workload(n_fits=1000, duration_ms=duration_ms, max_side=max_side)
+    r = Renderer(tables, config2_psfs(64), device=device)
+    state = make_fits(r, fits)
+    torch.cuda.synchronize()
+    gal = np.array([len(q[2]) for q in reqs], dtype=np.int64)
+
+    def run(times_s, **cfg):
+        srv = Server(r, **cfg)
+        for st in state:
+            srv.add_fit(**st)
+        warm = min(300, len(reqs))
+        t, k = srv.replay(reqs[:warm], np.zeros(warm))
+        srv.wait_replayed(t, k)
+        t0 = time.perf_counter()
+        t, k = srv.replay(reqs, times_s)
+        lat = srv.wait_replayed(t, k)
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        span = wall
+        return {"achieved_galaxies_per_s": float(gal.sum() / span), "requests": len(reqs),
+                "offered_galaxies_per_s": float(gal.sum() / max(times_s[-1], 1e-9)),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "micro_batches": stats["batches"] - 1,
+                "largest_micro_batch": stats["max_batch_galaxies"], "max_lanes_in_flight": stats["max_lanes_in_flight"]}
+
+    cfg = dict(budget_bytes=16 << 30, lanes=4, max_batch_galaxies=32768)
+    full = run(arrival_ms / 1e3, **cfg)
+    cap = full["achieved_galaxies_per_s"]
+    half_times = arrival_ms / 1e3 * (full["offered_galaxies_per_s"] / (0.5 * cap))
+    half = run(half_times, **cfg)
+    single = run(half_times, budget_bytes=16 << 30, lanes=1, max_batch_galaxies=0)
+    r.close()
+    return {"workload": f"1000 fits x 512 galaxies (Sersic n U(0.5, 6), sides <= {max_side}), 64 PSFs, "
+                        f"render + gradient requests of U{{1..512}} galaxies, Poisson arrivals, "
+                        f"{len(reqs)} requests over {duration_ms:.0f} ms at 20k galaxies/ms; 16 GB budget, 4 lanes",
+            "unit": "galaxies rendered+grad/s; latency = submission to results on the host",
+            "offered_load": full, "half_capacity_load": half, "one_launch_per_request_at_half_load": single}
+
+
 # ----------------------------------------------------------------------------
 # Distributed helpers (replicas).
 # ----------------------------------------------------------------------------
@@ -542,7 +594,8 @@ def run_ours(args):
     if world == 1 and not args.no_extra:
         extra = {"mixed_sizes": extra_mixed(tables, local, args.extra_steps),
                  "render_grad": extra_render_grad(tables, psf, local, args.extra_steps),
-                 "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local)}
+                 "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local),
+                 "serving": extra_serving(tables, local)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -605,6 +658,12 @@ def run_reference(args):
 def run_only(args):
     """Small single-workload runs for profilers (no JSON bench line)."""
     import torch
+    if args.only == "serving":
+        from paper_2012_15797_gb300.build import build
+        build()
+        from workloads import load_profile_tables
+        print(json.dumps(extra_serving(load_profile_tables(), 0, duration_ms=args.galaxies / 20.0)))
+        return
     from paper_2012_15797_gb300.build import build
     build()
     from paper_2012_15797_gb300.renderer import Renderer, to_device

@@ -20,7 +20,7 @@ class Server:
         self._fits = []       # keep device tensors alive
         self._live = {}       # ticket -> (params, grads, chi2)
 
-    def add_fit(self, sersic_n, profile, psf, size, data_offset, data, ivar):
+    def add_fit(self, sersic_n, profile, psf, size, data_offset, data, ivar, _keep=None):
         """Device tensors of one fit: float32 sersic_n, int32 profile, psf,
         size, int64 data_offset, float32 data (packed patches), float32 ivar."""
         t = dict(sersic_n=sersic_n, profile=profile, psf=psf, size=size, data_offset=data_offset, data=data, ivar=ivar)
@@ -31,7 +31,7 @@ class Server:
                                                       "ivar")))
         fid = ctypes.c_int(-1)
         capi._check(self.renderer.ctx, capi.library().mog_server_add_fit(self.handle, ctypes.byref(fs), ctypes.byref(fid)))
-        self._fits.append(t)
+        self._fits.append((t, _keep))
         return fid.value
 
     def _request(self, fit, first, params):
@@ -113,19 +113,34 @@ def make_fits(renderer, fits_gals, noise_seed=0, sigma_frac=0.01):
     """Device fit state for a list of ``workloads.Galaxies`` (one per fit):
     observed patches rendered from the galaxies' parameters (the fits'
     'truth') plus Gaussian noise of sigma_frac times each patch's peak, and
-    ivar = 1 / sigma^2 per patch.  Returns a list of dicts of device tensors."""
+    ivar = 1 / sigma^2 per patch.  All fits are rendered in one batch; each
+    fit's state is a set of views into the shared device tensors.  Returns a
+    list of dicts of device tensors."""
     from .renderer import to_device
+    from workloads import Galaxies
+    counts = [len(g) for g in fits_gals]
+    allg = Galaxies(**{f: np.concatenate([getattr(g, f) for g in fits_gals])
+                       for f in Galaxies.FLOAT_FIELDS + Galaxies.INT_FIELDS})
+    b = to_device(allg)
+    img = renderer.render(b)
+    npix = torch.from_numpy(np.asarray(b.sizes, np.int64) ** 2).cuda()
+    peaks = torch.segment_reduce(img, "max", lengths=npix)
+    sigma = sigma_frac * peaks
     gen = torch.Generator(device="cuda").manual_seed(noise_seed)
+    data = img + torch.repeat_interleave(sigma, npix) * torch.randn(img.shape, device="cuda", generator=gen)
+    ivar = (1.0 / sigma ** 2).float().contiguous()
+    del img
     out = []
-    for gals in fits_gals:
-        b = to_device(gals)
-        img = renderer.render(b)
-        peaks = torch.stack([img[int(o):int(o) + int(n) ** 2].amax() for o, n in zip(b.offsets, b.sizes)])
-        sigma = sigma_frac * peaks
-        noise = torch.randn(img.shape, device="cuda", generator=gen)
-        scale = torch.repeat_interleave(sigma, torch.from_numpy(np.asarray(b.sizes, np.int64) ** 2).cuda())
-        data = img + scale * noise
-        out.append(dict(sersic_n=b.tensors["sersic_n"], profile=b.tensors["profile"], psf=b.tensors["psf"],
-                        size=b.tensors["size"], data_offset=b.tensors["offset"], data=data,
-                        ivar=(1.0 / sigma ** 2).float().contiguous()))
+    start = 0
+    for c in counts:
+        sl = slice(start, start + c)
+        base = int(b.offsets[start])
+        out.append(dict(sersic_n=b.tensors["sersic_n"][sl], profile=b.tensors["profile"][sl],
+                        psf=b.tensors["psf"][sl], size=b.tensors["size"][sl],
+                        data_offset=(b.tensors["offset"][sl] - base).contiguous(),
+                        data=data[base:], ivar=ivar[sl]))
+        start += c
+    out_keep = (b, data, ivar)
+    for d in out:
+        d["_keep"] = out_keep
     return out

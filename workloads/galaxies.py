@@ -153,21 +153,40 @@ def config3_problem(g=50_000, seed=3):
     return model, truth, noise
 
 
-def serving_requests(n_fits=1000, seed=4, rate_per_ms=20_000.0, duration_ms=None,
-                     n_requests=None, max_size=512, n_psf=64):
-    """Serving workload: requests of 1..``max_size`` galaxies (uniform) from
-    ``n_fits`` concurrent fits, Poisson arrivals at ``rate_per_ms`` galaxies
-    per millisecond.  Galaxies are drawn as in ``config2_galaxies``.  Returns
-    ``(arrival_ms, fit_id, sizes, galaxies)`` where request r owns galaxies
-    ``[cumsum(sizes)[r-1], cumsum(sizes)[r])``."""
+def serving_workload(n_fits=1000, per_fit=512, seed=4, rate_per_ms=20_000.0, duration_ms=1000.0,
+                     max_size=512, n_psf=64, max_side=256):
+    """Serving workload: ``n_fits`` concurrent fits of ``per_fit`` galaxies
+    each (drawn as in ``config2_galaxies``, patch sides <= max_side), and
+    requests of 1..``max_size`` galaxies (uniform) arriving as a Poisson
+    process of ``rate_per_ms`` galaxies per millisecond for ``duration_ms``.
+    A request names a fit, a contiguous range of its galaxies and their
+    current parameters: the fit's values perturbed as in
+    ``config3_problem``.  Returns ``(fits, arrival_ms, requests)`` with
+    requests a list of (fit, first, params (count, 6) float32)."""
     rng = np.random.default_rng(seed)
+    pool = config2_galaxies(int(n_fits * per_fit * 1.6) + 64, seed + 1, n_psf=n_psf)
+    keep = np.nonzero(pool.size <= max_side)[0][:n_fits * per_fit]
+    pool = pool.subset(keep)
+    fits = [pool.subset(np.arange(f * per_fit, (f + 1) * per_fit)) for f in range(n_fits)]
     mean = 0.5 * (1 + max_size)
-    req_rate = rate_per_ms / mean
-    if n_requests is None:
-        n_requests = int(np.ceil(req_rate * (duration_ms or 100.0)))
-    gaps = rng.exponential(1.0 / req_rate, n_requests)
-    arrival = np.cumsum(gaps)
-    sizes = rng.integers(1, max_size + 1, n_requests).astype(np.int64)
-    fit_id = rng.integers(0, n_fits, n_requests)
-    gal = config2_galaxies(int(sizes.sum()), seed + 1, n_psf=n_psf)
-    return arrival, fit_id, sizes, gal
+    n_req = int(np.ceil(rate_per_ms / mean * duration_ms))
+    arrival = np.cumsum(rng.exponential(mean / rate_per_ms, n_req))
+    sizes = rng.integers(1, max_size + 1, n_req)
+    fit_id = rng.integers(0, n_fits, n_req)
+    params6 = [f.params6() for f in fits]
+    requests = []
+    for r in range(n_req):
+        c = int(min(sizes[r], per_fit))
+        first = int(rng.integers(0, per_fit - c + 1))
+        p = params6[fit_id[r]][first:first + c].copy()
+        z = rng.standard_normal((c, 6))
+        p[:, 0] *= 1.0 + 0.05 * z[:, 0]
+        p[:, 1:3] += 0.1 * z[:, 1:3]
+        p[:, 3] += 0.05 * z[:, 3]
+        p[:, 4:6] += 0.02 * z[:, 4:6]
+        emag = np.hypot(p[:, 4], p[:, 5])
+        scale = np.where(emag > 0.6, 0.6 / np.maximum(emag, 1e-30), 1.0)
+        p[:, 4] *= scale
+        p[:, 5] *= scale
+        requests.append((int(fit_id[r]), first, p.astype(np.float32)))
+    return fits, arrival, requests
