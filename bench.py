@@ -392,7 +392,7 @@ def extra_per_galaxy(tables, psf, device, n=2000):
             "note": "one mog_render_batch call per 64x64 galaxy of the fixed-size distribution"}
 
 
-def extra_serving(tables, device, duration_ms=500.0, max_side=128):
+def extra_serving(tables, device, duration_ms=500.0, max_side=256):
     """1000 concurrent fits of 512 galaxies (Sersic, sizes as the mixed
     workload), render + gradient requests of 1-512 galaxies with Poisson
     arrivals at 20k galaxies/ms, 64 PSFs resident, 16 GB admission budget.

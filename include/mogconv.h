@@ -13,8 +13,7 @@
  *
  * Conventions shared by every entry point:
  *  - A patch is N x N float32, row-major, row = y, column = x, pixel centres at
- *    integer coordinates.  N is one of 32, 64, 128, 256 for the render and
- *    32, 64, 128 for the adjoint.
+ *    integer coordinates.  N is one of 32, 64, 128, 256.
  *  - The galaxy centre is (N/2 + x, N/2 + y) where (x, y) is its offset.
  *  - Shapes: r_e = exp(log_re) pixels; e1, e2 ellipticity (Eqs. 2-5) with the
  *    WCS matrix CD = identity (pixel units); the pixel covariance of a
@@ -233,7 +232,7 @@ typedef struct mog_fit_state {
   const float* sersic_n;       /* device, count */
   const int32_t* profile;      /* device, count */
   const int32_t* psf;          /* device, count */
-  const int32_t* size;         /* device, count: patch side (32..128 for gradients) */
+  const int32_t* size;         /* device, count: patch side */
   const int64_t* data_offset;  /* device, count: offset of the observed patch in data (multiple of 4) */
   const float* data;           /* device: observed patches */
   const float* ivar;           /* device, count: inverse variance of each patch's pixels */

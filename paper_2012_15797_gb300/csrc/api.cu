@@ -57,6 +57,7 @@ void workspace_free(Workspace* ws) {
   cudaFree(ws->plan.order);
   cudaFree(ws->records);
   cudaFree(ws->adj_records);
+  cudaFree(ws->bwd256);
   for (int b = 0; b < NBUCKET; ++b) {
     if (ws->side[b]) cudaStreamDestroy(ws->side[b]);
     if (ws->join_ev[b]) cudaEventDestroy(ws->join_ev[b]);
@@ -351,6 +352,9 @@ mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, co
   if (!grad_out || (reinterpret_cast<uintptr_t>(grad_out) & 15))
     return fail(ctx, MOG_ERR_ARG, "grad_out must be 16-byte aligned");
   if (!grad_params) return fail(ctx, MOG_ERR_ARG, "null grad_params");
+  const uint32_t want = batch->size_mask ? (batch->size_mask & BWD_BUCKETS) : BWD_BUCKETS;
+  if ((want & 0x8) && !ws->bwd256)
+    MOG_CUDA(ctx, cudaMalloc(&ws->bwd256, render_bwd256_scratch_bytes(ctx->num_sms)));
   RenderParams p;
   if ((st = plan_batch(ctx, ws, batch, nullptr, BWD_BUCKETS, s, &p)) != MOG_OK) return st;
   p.records = ws->adj_records;
@@ -358,6 +362,7 @@ mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, co
   return launch_buckets(ctx, ws, batch, BWD_BUCKETS, s, [&](int n, cudaStream_t bs) {
     RenderParams q = p;
     q.chunk = ctx->tune_bwd[bucket_of(n)].chunk;
+    if (n == 256) return launch_render_bwd256(q, grad_out, grad_params, ws->bwd256, ctx->num_sms, bs);
     return launch_render_bwd(n, q, grad_out, grad_params, ctx->num_sms, ctx->tune_bwd[bucket_of(n)].ctas_per_sm, bs);
   });
 }

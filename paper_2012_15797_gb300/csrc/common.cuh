@@ -541,4 +541,86 @@ __device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*p
   rt->rmy[t] = 0.5f * (float)n + r.y + m[2];
 }
 
+// ------------------------------------------------------------------------
+// Adjoint helpers shared by every patch side.
+// ------------------------------------------------------------------------
+struct AdjTerms {
+  float base[RMAX], wr[RMAX], rn[RMAX], v[RMAX];
+  float i11[RMAX], i12[RMAX], i22[RMAX], mx[RMAX], my[RMAX];
+  float qa[RMAX], qb[RMAX], qc[RMAX];
+};
+
+// Real-space term t = c * kpsf + j of the adjoint record (one thread).
+__device__ __forceinline__ void adj_real_term(const AdjRecord& r, const float (*psf_mog)[6], int kp, int n, int t,
+                                              AdjTerms* at) {
+  const int c = t / kp, jj = t - c * kp;
+  const float* m = psf_mog[jj];
+  const float v = r.rvar[c];
+  const float vxx = v * r.s11 + m[3], vxy = v * r.s12 + m[4], vyy = v * r.s22 + m[5];
+  const float det = vxx * vyy - vxy * vxy;
+  const float idet = 1.0f / det;
+  at->base[t] = r.rbase[c] * m[0] * rsqrtf(det) * (0.5f / PI_F);
+  at->wr[t] = r.rw[c];
+  at->rn[t] = r.rn[c];
+  at->v[t] = v;
+  at->i11[t] = vyy * idet;
+  at->i12[t] = -vxy * idet;
+  at->i22[t] = vxx * idet;
+  at->qa[t] = -0.5f * LOG2E * vyy * idet;
+  at->qb[t] = LOG2E * vxy * idet;
+  at->qc[t] = -0.5f * LOG2E * vxx * idet;
+  at->mx[t] = 0.5f * (float)n + r.x + m[1];
+  at->my[t] = 0.5f * (float)n + r.y + m[2];
+}
+
+// Adds one bin's contribution.  z = c_k conj(G) P phase; (s, sq, sn) the
+// weighted mixture sums at the bin.
+__device__ __forceinline__ void contract_bin(float2 z, float nu, float om, float s, float sq, float sn,
+                                             float* acc) {
+  acc[0] = fmaf(z.x, s, acc[0]);
+  acc[1] = fmaf(nu * s, z.y, acc[1]);
+  acc[2] = fmaf(om * s, z.y, acc[2]);
+  acc[3] = fmaf(z.x, fmaf(sq * nu, nu, sn), acc[3]);
+  acc[4] = fmaf(z.x, sq * 2.0f * nu * om, acc[4]);
+  acc[5] = fmaf(z.x, fmaf(sq * om, om, sn), acc[5]);
+}
+
+// Real-space part of the adjoint over all pixels of an N x N patch (g read
+// from `gp`, shared or global memory); the x and y sums are divided by 2 pi
+// because the caller multiplies the total by 2 pi.
+template <int N>
+__device__ __forceinline__ void adj_real_space(const float* gp, const AdjTerms& at, int nr, int tid, int nthreads,
+                                               float* acc) {
+  if (nr <= 0) return;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
+  for (int pix = tid; pix < N * N; pix += nthreads) {
+    const float gw = gp[pix];
+    if (gw == 0.0f) continue;
+    const float xx = (float)(pix % N), yy = (float)(pix / N);
+    for (int t = 0; t < nr; ++t) {
+      const float dx = xx - at.mx[t], dy = yy - at.my[t];
+      const float e0 = fmaf(dx, fmaf(at.qa[t], dx, at.qb[t] * dy), at.qc[t] * dy * dy);
+      const float n = gw * at.base[t] * ex2(e0);
+      const float ux = fmaf(at.i11[t], dx, at.i12[t] * dy);
+      const float uy = fmaf(at.i12[t], dx, at.i22[t] * dy);
+      const float nw = n * at.wr[t];
+      const float nv = nw * at.v[t];
+      const float rr = n * at.rn[t];
+      a0 += nw;
+      a1 = fmaf(nw, ux, a1);
+      a2 = fmaf(nw, uy, a2);
+      a3 = fmaf(nv, 0.5f * fmaf(ux, ux, -at.i11[t]), a3 + rr);
+      a4 = fmaf(nv, fmaf(ux, uy, -at.i12[t]), a4);
+      a5 = fmaf(nv, 0.5f * fmaf(uy, uy, -at.i22[t]), a5 + rr);
+    }
+  }
+  constexpr float INV_2PI = 0.15915494309189535f;
+  acc[0] += a0;
+  acc[1] += a1 * INV_2PI;
+  acc[2] += a2 * INV_2PI;
+  acc[3] += a3;
+  acc[4] += a4;
+  acc[5] += a5;
+}
+
 }  // namespace mog

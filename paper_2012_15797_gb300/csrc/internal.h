@@ -52,6 +52,10 @@ cudaError_t launch_adjoint_prep(const RenderParams& p, int64_t count, unsigned c
 cudaError_t launch_render_bwd(int n, const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
                               int ctas_per_sm, cudaStream_t s);
 int render_bwd_max_ctas(int n);
+// 256 x 256 adjoint: needs render_bwd256_scratch_bytes(num_sms) of global scratch.
+size_t render_bwd256_scratch_bytes(int num_sms);
+cudaError_t launch_render_bwd256(const RenderParams& p, const float* grad_out, float* grad_params, float2* scratch,
+                                 int num_sms, cudaStream_t s);
 
 // Allocation-free forward render (noalloc.cu): the scratch of one call lives
 // in a fixed device array; noalloc_scratch returns its address on `device`.
@@ -65,7 +69,7 @@ int render_fwd_max_ctas(int n);
 
 // Patch sides each direction supports (bit b: N = 32 << b).
 constexpr uint32_t FWD_BUCKETS = 0xF;   // 32, 64, 128, 256
-constexpr uint32_t BWD_BUCKETS = 0x7;   // 32, 64, 128
+constexpr uint32_t BWD_BUCKETS = 0xF;   // 32, 64, 128, 256
 size_t render_fwd_smem(int n);
 
 // Spectrum of a PSF embedded with its centre at (n/2, n/2), written in the

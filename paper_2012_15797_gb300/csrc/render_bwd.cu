@@ -26,12 +26,6 @@
 
 namespace mog {
 
-struct AdjTerms {
-  float base[RMAX], wr[RMAX], rn[RMAX], v[RMAX];
-  float i11[RMAX], i12[RMAX], i22[RMAX], mx[RMAX], my[RMAX];
-  float qa[RMAX], qb[RMAX], qc[RMAX];
-};
-
 template <int N>
 struct BwdCfg {
   static constexpr int H = N / 2 + 1;
@@ -85,18 +79,6 @@ __device__ __forceinline__ void fft_rest_b(float2* w, int j, const float2* tw1, 
     __syncwarp();
     stockham_load<N, R2, S>(w, j, tw2, v);
   }
-}
-
-// Adds one bin's contribution.  z = c_k conj(G) P phase; (s, sq, sn) the
-// weighted mixture sums at the bin.
-__device__ __forceinline__ void contract_bin(float2 z, float nu, float om, float s, float sq, float sn,
-                                             float* acc) {
-  acc[0] = fmaf(z.x, s, acc[0]);
-  acc[1] = fmaf(nu * s, z.y, acc[1]);
-  acc[2] = fmaf(om * s, z.y, acc[2]);
-  acc[3] = fmaf(z.x, fmaf(sq * nu, nu, sn), acc[3]);
-  acc[4] = fmaf(z.x, sq * 2.0f * nu * om, acc[4]);
-  acc[5] = fmaf(z.x, fmaf(sq * om, om, sn), acc[5]);
 }
 
 template <int N>
@@ -228,25 +210,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
           nys[4 * l + 1] = sq;
           nys[4 * l + 2] = sn2;
         } else {
-          const int t = i - C::H - 2 * N;
-          const int c = t / kp, jj = t - c * kp;
-          const float* m = s_psf_mog[jj];
-          const float v = r.rvar[c];
-          const float vxx = v * r.s11 + m[3], vxy = v * r.s12 + m[4], vyy = v * r.s22 + m[5];
-          const float det = vxx * vyy - vxy * vxy;
-          const float idet = 1.0f / det;
-          at.base[t] = r.rbase[c] * m[0] * rsqrtf(det) * (0.5f / PI_F);
-          at.wr[t] = r.rw[c];
-          at.rn[t] = r.rn[c];
-          at.v[t] = v;
-          at.i11[t] = vyy * idet;
-          at.i12[t] = -vxy * idet;
-          at.i22[t] = vxx * idet;
-          at.qa[t] = -0.5f * LOG2E * vyy * idet;
-          at.qb[t] = LOG2E * vxy * idet;
-          at.qc[t] = -0.5f * LOG2E * vxx * idet;
-          at.mx[t] = 0.5f * (float)N + r.x + m[1];
-          at.my[t] = 0.5f * (float)N + r.y + m[2];
+          adj_real_term(r, s_psf_mog, kp, N, i - C::H - 2 * N, &at);
         }
       }
     }
@@ -293,35 +257,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     }
 
     // ---- real-space terms: analytic derivatives, pixel by pixel ----
-    {
-      const int nr = r.nrc * s_kpsf;
-      if (nr > 0) {
-        for (int pix = tid; pix < N * N; pix += C::THREADS) {
-          const float gw = gbuf[pix];
-          if (gw == 0.0f) continue;
-          const float xx = (float)(pix % N), yy = (float)(pix / N);
-          for (int t = 0; t < nr; ++t) {
-            const float dx = xx - at.mx[t], dy = yy - at.my[t];
-            const float e0 = fmaf(dx, fmaf(at.qa[t], dx, at.qb[t] * dy), at.qc[t] * dy * dy);
-            const float n = gw * at.base[t] * ex2(e0);
-            const float ux = fmaf(at.i11[t], dx, at.i12[t] * dy);
-            const float uy = fmaf(at.i12[t], dx, at.i22[t] * dy);
-            const float nw = n * at.wr[t];
-            const float nv = nw * at.v[t];
-            const float rr = n * at.rn[t];
-            acc[0] += nw;
-            acc[1] = fmaf(nw, ux, acc[1]);
-            acc[2] = fmaf(nw, uy, acc[2]);
-            acc[3] = fmaf(nv, 0.5f * fmaf(ux, ux, -at.i11[t]), acc[3] + rr);
-            acc[4] = fmaf(nv, fmaf(ux, uy, -at.i12[t]), acc[4]);
-            acc[5] = fmaf(nv, 0.5f * fmaf(uy, uy, -at.i22[t]), acc[5] + rr);
-          }
-        }
-        // the Fourier sums below carry 2 pi for x, y; pre-divide the real ones
-        acc[1] *= 1.0f / TWO_PI;
-        acc[2] *= 1.0f / TWO_PI;
-      }
-    }
+    adj_real_space<N>(gbuf, at, r.nrc * s_kpsf, tid, C::THREADS, acc);
     __syncthreads();  // S3: every column input written
 
     // ---- forward FFT of every column along y ----
@@ -433,6 +369,7 @@ int render_bwd_max_ctas(int n) {
     case 32: return bwd_occupancy<32>();
     case 64: return bwd_occupancy<64>();
     case 128: return bwd_occupancy<128>();
+    case 256: return 1;
     default: return 0;
   }
 }

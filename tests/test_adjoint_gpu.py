@@ -82,7 +82,7 @@ def test_adjoint_edge_cases(gpu_renderer, tables, size):
     check(gpu_grads(gpu_renderer, gals, gp), oracle_grads(gals, gpu_renderer.psfs, tables, gp), gals, gp)
 
 
-@pytest.mark.parametrize("size", [32, 64, 128])
+@pytest.mark.parametrize("size", [32, 64, 128, 256])
 def test_adjoint_ramp_region(gpu_renderer, tables, size):
     vmax = tables[0].var[0][0]
     rows = []
@@ -96,7 +96,7 @@ def test_adjoint_ramp_region(gpu_renderer, tables, size):
 
 def test_adjoint_batch_mixed(gpu_renderer, tables):
     gals = config2_galaxies(160, seed=21, n_psf=5)
-    gals = gals.subset(np.nonzero(gals.size <= 128)[0])
+    assert 256 in set(gals.size)
     gp = _random_grad(gals, 3)
     check(gpu_grads(gpu_renderer, gals, gp), oracle_grads(gals, gpu_renderer.psfs, tables, gp), gals, gp)
 
@@ -157,18 +157,8 @@ def test_autograd_matches_c_abi(gpu_renderer):
     assert torch.equal(out.detach(), ref)
 
 
-def test_adjoint_rejects_256(gpu_renderer):
-    """The adjoint covers N = 32, 64, 128; a 256 galaxy is reported through
-    the status word and its gradient left unwritten."""
-    import torch
-    from paper_2012_15797_gb300.capi import MogError, MOG_ERR_DEVICE
-    from paper_2012_15797_gb300.renderer import to_device
-    gals = _gals([_row(size=64), _row(size=256)])
-    b = to_device(gals)
-    gp = torch.full((2, 6), -5.0, device="cuda")
-    gpu_renderer.render_backward(b, torch.ones(b.total, device="cuda"), gp)
-    with pytest.raises(MogError) as ei:
-        gpu_renderer.sync_status()
-    assert ei.value.status == MOG_ERR_DEVICE
-    g = gp.cpu().numpy()
-    assert np.all(g[1] == -5.0) and np.all(np.isfinite(g[0])) and not np.all(g[0] == -5.0)
+@pytest.mark.parametrize("size", [256])
+def test_adjoint_256(gpu_renderer, tables, size):
+    gals = _gals([_row(size=size, **e) for e in EDGE[:6]])
+    gp = _random_grad(gals, 99)
+    check(gpu_grads(gpu_renderer, gals, gp), oracle_grads(gals, gpu_renderer.psfs, tables, gp), gals, gp)

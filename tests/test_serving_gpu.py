@@ -15,8 +15,7 @@ pytestmark = pytest.mark.gpu
 def _fits(n_fits=3, per_fit=300, seed=61):
     fits = []
     for f in range(n_fits):
-        g = config2_galaxies(2 * per_fit, seed=seed + f, n_psf=5)
-        g = g.subset(np.nonzero(g.size <= 128)[0][:per_fit])
+        g = config2_galaxies(per_fit, seed=seed + f, n_psf=5)
         fits.append(g)
     return fits
 
