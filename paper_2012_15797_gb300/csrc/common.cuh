@@ -165,17 +165,24 @@ __device__ __forceinline__ void fill_twiddles(float2* t, int ns, int tid, int nt
 }
 
 // Input of a pass after the first: gather + twiddle + R-point DFTs into v[8].
+// Every stride here is a multiple of 8, so swz(b + m S) = swz(b) + m 9S/8 and
+// only the butterfly base needs index arithmetic.
 template <int N, int R, int S>
-__device__ __forceinline__ void stockham_load(const float2* w, int j, const float2* twt, float2* v) {
+__device__ __forceinline__ void stockham_load(const float2* buf, int j, const float2* twt, float2* v) {
   constexpr int NB = 8 / R;
+  constexpr int STRIDE = N / R;
+  static_assert(STRIDE % 8 == 0, "pass stride must be a multiple of 8");
+  constexpr int STEP = STRIDE + STRIDE / 8;
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = j + q * (N / 8);
+    const float2* src = buf + b + (b >> 3);
+    const float2* tw = twt + b;
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      float2 x = w[swz<N>(b + m * (N / R))];
+      float2 x = src[m * STEP];
       if (m > 0) {
-        const float2 t = twt[(m - 1) * (N / R) + b];
+        const float2 t = tw[(m - 1) * STRIDE];
         x = (S > 0) ? cmul(x, t) : cmulc(x, t);
       }
       v[q * R + m] = x;
@@ -192,12 +199,35 @@ __device__ __forceinline__ int stockham_out_index(int j, int ns, int q, int m) {
 }
 
 template <int N, int R>
-__device__ __forceinline__ void stockham_store(float2* w, int j, int ns, const float2* v) {
+__device__ __forceinline__ void stockham_store(float2* buf, int j, int ns, const float2* v) {
   constexpr int NB = 8 / R;
 #pragma unroll
-  for (int q = 0; q < NB; ++q)
+  for (int q = 0; q < NB; ++q) {
+    const int b = j + q * (N / 8);
+    const int n0 = (b / ns) * ns * R + (b & (ns - 1));
+    float2* dst = buf + n0 + (n0 >> 3);
+    const int step = ns + ns / 8;   // ns is 8 or a larger multiple of 8
 #pragma unroll
-    for (int m = 0; m < R; ++m) w[swz<N>(stockham_out_index<N, R>(j, ns, q, m))] = v[q * R + m];
+    for (int m = 0; m < R; ++m) dst[m * step] = v[q * R + m];
+  }
+}
+
+// First-pass store (sub-length 1): value m of lane j goes to swz(8 j + m).
+__device__ __forceinline__ void first_pass_store(float2* buf, int j, const float2* v) {
+  float2* dst = buf + 9 * j;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) dst[m] = v[m];
+}
+
+// First-pass load of element j + m TPF (TPF = N/8 lanes per transform):
+// swz(j + c) = j + j/8 + c + c/8 for c = m TPF (c multiple of 8, or TPF = 4
+// with j < 4).
+template <int N>
+__device__ __forceinline__ void first_pass_load(const float2* buf, int j, float2* v) {
+  constexpr int TPF = N / 8;
+  const float2* src = buf + j + (j >> 3);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = src[m * TPF + ((m * TPF) >> 3)];
 }
 
 // ------------------------------------------------------------------------
