@@ -54,8 +54,8 @@ struct FwdCfg {
   static constexpr size_t off_py = off_px + sizeof(float2) * H;
   static constexpr size_t off_nyq = off_py + sizeof(float2) * N;
   static constexpr size_t off_rec = (off_nyq + sizeof(float2) * N + 15) & ~size_t(15);
-  static constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);
-  static constexpr size_t off_bar = (off_rt + sizeof(RealTerms) + 15) & ~size_t(15);
+  static constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);   // two tables, one per record buffer
+  static constexpr size_t off_bar = (off_rt + 2 * sizeof(RealTerms) + 15) & ~size_t(15);
   static constexpr size_t SMEM = off_bar + 3 * sizeof(uint64_t);
 };
 
@@ -99,11 +99,11 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   float2* py = reinterpret_cast<float2*>(smem + C::off_py);
   float2* nyq = reinterpret_cast<float2*>(smem + C::off_nyq);
   GalaxyRecord* rec = reinterpret_cast<GalaxyRecord*>(smem + C::off_rec);
-  RealTerms& rt = *reinterpret_cast<RealTerms*>(smem + C::off_rt);
+  RealTerms* rts = reinterpret_cast<RealTerms*>(smem + C::off_rt);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);   // [0] PSF, [1..2] records
   __shared__ int s_pos[2];
-  __shared__ float s_psf_mog[KPSF][6];
-  __shared__ int s_kpsf;
+  __shared__ float* s_dst[2];   // per record buffer: output patch and real-space term count
+  __shared__ int s_nr[2];
 
   const int tid = threadIdx.x;
   const int f = tid / TPF, j = tid % TPF;
@@ -138,9 +138,16 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   float2* wb = WB + f * WS;   // this group's row in pass B
   int cur_psf = -1;
   uint32_t psf_parity = 0, rec_parity = 0;   // rec_parity bit b: phase of record buffer b
+  __syncthreads();
 
+  // Three CTA barriers per galaxy (S2, S3 and, for N = 64, the work-row
+  // barrier).  There is none between galaxies: a group stores the two rows it
+  // transformed itself, so warps run on into the next galaxy's tables while
+  // others still store.  That is safe because every read of galaxy i's record,
+  // PSF spectrum, px/py/nyq tables and work rows by other warps is ordered
+  // before S3(i) or S2(i + 1), which the writer of galaxy i + 1's copies has
+  // passed, and the real-space tables alternate with the record buffers.
   for (int buf = 0;; buf ^= 1) {
-    __syncthreads();  // S1: the previous galaxy is fully stored; s_pos[buf] is visible
     const int pos = s_pos[buf];
     if (pos < 0) break;
     if (tid == 0) {
@@ -156,26 +163,28 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     bool psf_landed = true;
     if (need_psf) {   // uniform: every thread reads the same record
       if (tid == 0) bulk_load(psf_hat, p.psfs[r.psf].spec[B], sizeof(float2) * C::PSF_ELEMS, &bar[0]);
-      if (tid < KPSF * 6) s_psf_mog[tid / 6][tid % 6] = p.psfs[r.psf].mog[tid / 6][tid % 6];
-      if (tid == 0) s_kpsf = p.psfs[r.psf].k;
       psf_landed = mbar_wait(&bar[0], psf_parity);
       psf_parity ^= 1u;
       cur_psf = r.psf;
     }
-    if (__syncthreads_or(!rec_landed || !psf_landed)) {
-      if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
-      return;
-    }
-    if (!r.ok) continue;
-    float* dst = p.out + r.off;
+    const bool landed = rec_landed && psf_landed;
+    const bool work = landed && r.ok;
+    RealTerms& rt = rts[buf];
 
     // per-galaxy tables: shift phases, the nu = 1/2 column of the spectrum
     // (needed at +omega and -omega by the packed transform) and the
     // real-space terms, spread over the CTA as one task list
-    {
+    if (work) {
+      const DevPsf& ps = p.psfs[cur_psf];
+      const int kp = ps.k, nrt = r.nrc * kp;
+      // what the store needs of the record is copied out: the record buffer
+      // is refilled while slower warps may still be storing
+      if (tid == 0) {
+        s_dst[buf] = p.out + r.off;
+        s_nr[buf] = nrt;
+      }
       const float gx = r.x, gy = r.y;
-      const int kp = s_kpsf;
-      const int ntask = C::H + 2 * N + r.nrc * kp;
+      const int ntask = C::H + 2 * N + nrt;
       for (int i = tid; i < ntask; i += C::THREADS) {
         float sn, cs;
         if (i < C::H) {
@@ -196,11 +205,16 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
           sincospif(-gx, &sn, &cs);
           nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(make_float2(cs, sn), make_float2(cy, sy))), acc);
         } else {
-          real_term(r, s_psf_mog, kp, N, i - C::H - 2 * N, &rt);
+          real_term(r, ps.mog, kp, N, i - C::H - 2 * N, &rt);
         }
       }
     }
-    __syncthreads();  // S2
+    // S2: the tables are complete and every warp has stored the previous galaxy
+    if (__syncthreads_or(!landed)) {
+      if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
+      return;
+    }
+    if (!work) continue;   // uniform once every wait has landed
 
     // ---- Steps 5-6: Fourier mixture times PSF spectrum and phase, in registers ----
     const int nf = r.nf;
@@ -290,10 +304,10 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     __syncwarp();
     fft_rest<N, +1>(wb, j, tw1, tw2, v);
     __syncwarp();
+    float* orow = reinterpret_cast<float*>(wb);
     {
       // rows 2f and 2f+1 of the patch overwrite this transform's own row
       constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
-      float* orow = reinterpret_cast<float*>(wb);
 #pragma unroll
       for (int q = 0; q < 8 / R; ++q)
 #pragma unroll
@@ -303,20 +317,22 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
           orow[N + n] = v[q * R + m].y;
         }
     }
-    __syncthreads();  // S4
+    __syncwarp();   // the group's two rows are complete
+    float* dst = s_dst[buf];
+    const int nr = s_nr[buf];
 
-    // ---- Step 8: add the real-space terms and store ----
+    // ---- Step 8: add the real-space terms and store rows 2f and 2f+1 ----
     // Along a row a Gaussian term is 2^(E(dx)) with E quadratic in dx, so
     // over 8 consecutive pixels g(dx+1) = g(dx) r(dx), r(dx+1) = r(dx) R8 with
     // R8 = 2^(2 qa): two ex2 per 8 pixels.  Real-space terms are wide
     // (n_sigma < 4), so a start value that underflows stays negligible.
-    const int nr = r.nrc * s_kpsf;
-    for (int idx = tid; idx < N * N / 8; idx += C::THREADS) {
-      const int yy = idx / (N / 8);
-      const int x0 = (idx % (N / 8)) * 8;
-      const float* orow = reinterpret_cast<const float*>(WB + (yy >> 1) * WS) + (yy & 1) * N + x0;
-      float4 o0 = *reinterpret_cast<const float4*>(orow);
-      float4 o1 = *reinterpret_cast<const float4*>(orow + 4);
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int yy = 2 * f + h;
+      const int x0 = 8 * j;
+      const float* src = orow + h * N + x0;
+      float4 o0 = *reinterpret_cast<const float4*>(src);
+      float4 o1 = *reinterpret_cast<const float4*>(src + 4);
       if (nr > 0) {
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int t = 0; t < nr; ++t) {
