@@ -571,6 +571,56 @@ __device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*p
   rt->rmy[t] = 0.5f * (float)n + r.y + m[2];
 }
 
+// Number of table entries for nr real-space terms: terms are evaluated in
+// pairs (the two halves of packed f32x2 instructions), so an odd count is
+// padded with one term that contributes exactly zero.
+__host__ __device__ constexpr int real_terms_padded(int nr) { return (nr + 1) & ~1; }
+
+__device__ __forceinline__ void real_term_zero(int t, RealTerms* rt) {
+  rt->rw[t] = 0.0f;   // flat exponent (2^0 = 1) times weight 0
+  rt->rqa[t] = 0.0f;
+  rt->rqb[t] = 0.0f;
+  rt->rqc[t] = 0.0f;
+  rt->rmx[t] = 0.0f;
+  rt->rmy[t] = 0.0f;
+  rt->rrr[t] = 1.0f;
+}
+
+// Adds the real-space terms [0, nr2) (nr2 even) to the 8 pixels
+// (x0 + u, yy), u = 0..7.  Along a row a term is 2^(E(dx)) with E quadratic
+// in dx, so g(dx+1) = g(dx) r(dx) and r(dx+1) = r(dx) R8 with R8 = 2^(2 qa):
+// two ex2 per term and 8 pixels.  Terms 2i and 2i+1 run in the two halves of
+// packed f32x2 instructions, so each pixel step is three instructions for two
+// terms.  Real-space terms are wide (n_sigma < 4), so a start value that
+// underflows stays negligible over the 8 pixels.
+__device__ __forceinline__ void real_space_8(const RealTerms& rt, int nr2, float yy, float x0, float (&out)[8]) {
+  const float2 Y = make_float2(yy, yy), X = make_float2(x0, x0);
+  const float2 NEG = make_float2(-1.0f, -1.0f), TWO = make_float2(2.0f, 2.0f), ONE = make_float2(1.0f, 1.0f);
+  float2 acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.0f, 0.0f);
+  for (int t = 0; t < nr2; t += 2) {
+    const float2 qa = *reinterpret_cast<const float2*>(&rt.rqa[t]);
+    const float2 dy = __ffma2_rn(*reinterpret_cast<const float2*>(&rt.rmy[t]), NEG, Y);
+    const float2 dx = __ffma2_rn(*reinterpret_cast<const float2*>(&rt.rmx[t]), NEG, X);
+    const float2 ly = __fmul2_rn(dy, *reinterpret_cast<const float2*>(&rt.rqb[t]));
+    const float2 e0 = __ffma2_rn(dx, __ffma2_rn(qa, dx, ly),
+                                 __fmul2_rn(__fmul2_rn(*reinterpret_cast<const float2*>(&rt.rqc[t]), dy), dy));
+    const float2 e1 = __ffma2_rn(qa, __ffma2_rn(TWO, dx, ONE), ly);
+    float2 g = __fmul2_rn(*reinterpret_cast<const float2*>(&rt.rw[t]), make_float2(ex2(e0.x), ex2(e0.y)));
+    float2 rr = make_float2(ex2(e1.x), ex2(e1.y));
+    const float2 r8 = *reinterpret_cast<const float2*>(&rt.rrr[t]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      acc[u] = __fadd2_rn(acc[u], g);
+      g = __fmul2_rn(g, rr);
+      rr = __fmul2_rn(rr, r8);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) out[u] += acc[u].x + acc[u].y;
+}
+
 // ------------------------------------------------------------------------
 // Adjoint helpers shared by every patch side.
 // ------------------------------------------------------------------------

@@ -102,8 +102,9 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   RealTerms* rts = reinterpret_cast<RealTerms*>(smem + C::off_rt);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);   // [0] PSF, [1..2] records
   __shared__ int s_pos[2];
-  __shared__ float* s_dst[2];   // per record buffer: output patch and real-space term count
+  __shared__ float* s_dst[2];   // per record buffer: output patch and padded real-space term count
   __shared__ int s_nr[2];
+  __shared__ float4 s_fc[KMAX];   // Fourier components as (a, a, c, c): operand pairs of f32x2
 
   const int tid = threadIdx.x;
   const int f = tid / TPF, j = tid % TPF;
@@ -176,15 +177,15 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     // real-space terms, spread over the CTA as one task list
     if (work) {
       const DevPsf& ps = p.psfs[cur_psf];
-      const int kp = ps.k, nrt = r.nrc * kp;
+      const int kp = ps.k, nrt = r.nrc * kp, nr2 = real_terms_padded(nrt);
       // what the store needs of the record is copied out: the record buffer
       // is refilled while slower warps may still be storing
       if (tid == 0) {
         s_dst[buf] = p.out + r.off;
-        s_nr[buf] = nrt;
+        s_nr[buf] = nr2;
       }
       const float gx = r.x, gy = r.y;
-      const int ntask = C::H + 2 * N + nrt;
+      const int t0 = C::H + 2 * N, ntask = t0 + nr2 + r.nf;
       for (int i = tid; i < ntask; i += C::THREADS) {
         float sn, cs;
         if (i < C::H) {
@@ -205,7 +206,10 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
           sincospif(-gx, &sn, &cs);
           nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(make_float2(cs, sn), make_float2(cy, sy))), acc);
         } else {
-          real_term(r, ps.mog, kp, N, i - C::H - 2 * N, &rt);
+          const int t = i - t0;
+          if (t < nrt) real_term(r, ps.mog, kp, N, t, &rt);
+          else if (t < nr2) real_term_zero(t, &rt);
+          else s_fc[t - nr2] = make_float4(r.famp[t - nr2], r.famp[t - nr2], r.fcoef[t - nr2], r.fcoef[t - nr2]);
         }
       }
     }
@@ -225,27 +229,33 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
       const float nu = f * INV_N;
       const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
       const float omj = (float)j * INV_N;
-      float q[8], s[8];
+      // bins (2k, 2k+1) of the thread share packed f32x2 instructions
+      float2 q[4], s[4];
       float qmin = 3.4e38f;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
+      for (int k = 0; k < 4; ++k) {
         // l = j + m TPF is below N/2 exactly for m < 4
-        const float om = omj + (float)(m * TPF - (m >= 4 ? N : 0)) * INV_N;
-        q[m] = fmaf(om, fmaf(s22, om, a1), a0);
-        qmin = fminf(qmin, q[m]);
-        s[m] = 0.0f;
+        const float om0 = omj + (float)(2 * k * TPF - (2 * k >= 4 ? N : 0)) * INV_N;
+        const float om1 = omj + (float)((2 * k + 1) * TPF - (2 * k + 1 >= 4 ? N : 0)) * INV_N;
+        q[k] = make_float2(fmaf(om0, fmaf(s22, om0, a1), a0), fmaf(om1, fmaf(s22, om1, a1), a0));
+        qmin = fminf(qmin, fminf(q[k].x, q[k].y));
+        s[k] = make_float2(0.0f, 0.0f);
       }
       for (int i = 0; i < nf; ++i) {
-        const float a = r.famp[i], c = r.fcoef[i];
-        if (!__any_sync(0xffffffffu, c * qmin > NEGLIGIBLE_LOG2)) continue;
+        const float4 ac = s_fc[i];
+        if (!__any_sync(0xffffffffu, ac.z * qmin > NEGLIGIBLE_LOG2)) continue;
+        const float2 a2 = make_float2(ac.x, ac.y), c2 = make_float2(ac.z, ac.w);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) s[m] = fmaf(a, ex2(c * q[m]), s[m]);
+        for (int k = 0; k < 4; ++k) {
+          const float2 e = __fmul2_rn(c2, q[k]);
+          s[k] = __ffma2_rn(a2, make_float2(ex2(e.x), ex2(e.y)), s[k]);
+        }
       }
       const float2 pxf = px[f];
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
         const int l = j + m * TPF;
-        v[m] = cscale(cmul(psf_hat[f * LS + l], cmul(pxf, py[l])), s[m]);
+        v[m] = cscale(cmul(psf_hat[f * LS + l], cmul(pxf, py[l])), (m & 1) ? s[m >> 1].y : s[m >> 1].x);
       }
     }
     if (f == 0) {
@@ -322,45 +332,17 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     const int nr = s_nr[buf];
 
     // ---- Step 8: add the real-space terms and store rows 2f and 2f+1 ----
-    // Along a row a Gaussian term is 2^(E(dx)) with E quadratic in dx, so
-    // over 8 consecutive pixels g(dx+1) = g(dx) r(dx), r(dx+1) = r(dx) R8 with
-    // R8 = 2^(2 qa): two ex2 per 8 pixels.  Real-space terms are wide
-    // (n_sigma < 4), so a start value that underflows stays negligible.
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       const int yy = 2 * f + h;
       const int x0 = 8 * j;
       const float* src = orow + h * N + x0;
-      float4 o0 = *reinterpret_cast<const float4*>(src);
-      float4 o1 = *reinterpret_cast<const float4*>(src + 4);
-      if (nr > 0) {
-        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int t = 0; t < nr; ++t) {
-          const float qa = rt.rqa[t], dy = (float)yy - rt.rmy[t], dx = (float)x0 - rt.rmx[t];
-          const float ly = dy * rt.rqb[t];
-          const float e0 = fmaf(dx, fmaf(qa, dx, ly), rt.rqc[t] * dy * dy);
-          float g = rt.rw[t] * ex2(e0);
-          float rr = ex2(fmaf(qa, fmaf(2.0f, dx, 1.0f), ly));
-          const float r8 = rt.rrr[t];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            acc[u] += g;
-            g *= rr;
-            rr *= r8;
-          }
-        }
-        o0.x += acc[0];
-        o0.y += acc[1];
-        o0.z += acc[2];
-        o0.w += acc[3];
-        o1.x += acc[4];
-        o1.y += acc[5];
-        o1.z += acc[6];
-        o1.w += acc[7];
-      }
+      const float4 i0 = *reinterpret_cast<const float4*>(src), i1 = *reinterpret_cast<const float4*>(src + 4);
+      float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+      if (nr > 0) real_space_8(rt, nr, (float)yy, (float)x0, o);
       float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
-      d[0] = o0;
-      d[1] = o1;
+      d[0] = make_float4(o[0], o[1], o[2], o[3]);
+      d[1] = make_float4(o[4], o[5], o[6], o[7]);
     }
   }
 }

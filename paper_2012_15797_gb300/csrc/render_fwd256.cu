@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
     {
       const float gx = r.x, gy = r.y;
       const int kp = s_kpsf;
-      const int ntask = H + 2 * N + r.nrc * kp;
+      const int nrt = r.nrc * kp, ntask = H + 2 * N + real_terms_padded(nrt);
       for (int i = tid; i < ntask; i += THREADS) {
         float sn, cs;
         if (i < H) {
@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
           sincospif(-gx, &sn, &cs);
           nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(make_float2(cs, sn), make_float2(cy, sy))), acc);
         } else {
-          real_term(r, s_psf_mog, kp, N, i - H - 2 * N, &rt);
+          const int t = i - H - 2 * N;
+          if (t < nrt) real_term(r, s_psf_mog, kp, N, t, &rt);
+          else real_term_zero(t, &rt);
         }
       }
     }
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
     }
 
     // ---- Step 7b + 8: row pairs p = 32 round + warp, each warp on its own ----
-    const int nr = r.nrc * s_kpsf;
+    const int nr = real_terms_padded(r.nrc * s_kpsf);
     for (int round = 0; round < ROUNDS; ++round) {
       const int pr = WARPS * round + f;
       const float2* zin = zbuf + pr * N;
@@ -282,36 +284,12 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
         const int h = idx / (N / 8), x0 = (idx % (N / 8)) * 8;
         const int yy = 2 * pr + h;
         const float* orow = reinterpret_cast<const float*>(w) + h * N + x0;
-        float4 o0 = *reinterpret_cast<const float4*>(orow);
-        float4 o1 = *reinterpret_cast<const float4*>(orow + 4);
-        if (nr > 0) {
-          float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          for (int t = 0; t < nr; ++t) {
-            const float qa = rt.rqa[t], dy = (float)yy - rt.rmy[t], dx = (float)x0 - rt.rmx[t];
-            const float ly = dy * rt.rqb[t];
-            const float e0 = fmaf(dx, fmaf(qa, dx, ly), rt.rqc[t] * dy * dy);
-            float g = rt.rw[t] * ex2(e0);
-            float rr = ex2(fmaf(qa, fmaf(2.0f, dx, 1.0f), ly));
-            const float r8 = rt.rrr[t];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              acc[u] += g;
-              g *= rr;
-              rr *= r8;
-            }
-          }
-          o0.x += acc[0];
-          o0.y += acc[1];
-          o0.z += acc[2];
-          o0.w += acc[3];
-          o1.x += acc[4];
-          o1.y += acc[5];
-          o1.z += acc[6];
-          o1.w += acc[7];
-        }
+        const float4 i0 = *reinterpret_cast<const float4*>(orow), i1 = *reinterpret_cast<const float4*>(orow + 4);
+        float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+        if (nr > 0) real_space_8(rt, nr, (float)yy, (float)x0, o);
         float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
-        d[0] = o0;
-        d[1] = o1;
+        d[0] = make_float4(o[0], o[1], o[2], o[3]);
+        d[1] = make_float4(o[4], o[5], o[6], o[7]);
       }
       __syncwarp();
     }
