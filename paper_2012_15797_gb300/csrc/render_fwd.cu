@@ -34,7 +34,9 @@ struct FwdCfg {
   static constexpr int THREADS = NFFT * TPF;
   static constexpr int LS = psf_lstride(N);
   static constexpr int PSF_ELEMS = psf_spec_elems(N);
-  static constexpr int WS = wstride<N>();    // FFT work row stride (float2)
+  // FFT work row stride (float2); for N = 128 two more float2 spread the
+  // pairing writes (rows p of one instruction otherwise share 4 bank groups)
+  static constexpr int WS = wstride<N>() + (N == 128 ? 2 : 0);
   static constexpr int W_ELEMS = NFFT * WS;
   static constexpr int R1 = Radix<N>::r[1];
   static constexpr int R2 = Radix<N>::r[2];
