@@ -586,19 +586,21 @@ __device__ __forceinline__ void real_term_zero(int t, RealTerms* rt) {
   rt->rrr[t] = 1.0f;
 }
 
-// Adds the real-space terms [0, nr2) (nr2 even) to the 8 pixels
-// (x0 + u, yy), u = 0..7.  Along a row a term is 2^(E(dx)) with E quadratic
-// in dx, so g(dx+1) = g(dx) r(dx) and r(dx+1) = r(dx) R8 with R8 = 2^(2 qa):
-// two ex2 per term and 8 pixels.  Terms 2i and 2i+1 run in the two halves of
+// Adds the real-space terms [0, nr2) (nr2 even) to the L consecutive pixels
+// (x0 + u, yy), u = 0..L-1.  Along a row a term is 2^(E(dx)) with E quadratic
+// in dx, so g(dx+1) = g(dx) r(dx) and r(dx+1) = r(dx) R with R = 2^(2 qa):
+// two ex2 per term and run.  Terms 2i and 2i+1 run in the two halves of
 // packed f32x2 instructions, so each pixel step is three instructions for two
 // terms.  Real-space terms are wide (n_sigma < 4), so a start value that
-// underflows stays negligible over the 8 pixels.
-__device__ __forceinline__ void real_space_8(const RealTerms& rt, int nr2, float yy, float x0, float (&out)[8]) {
+// underflows stays negligible over a run of at most 8 pixels.
+template <int L>
+__device__ __forceinline__ void real_space_run(const RealTerms& rt, int nr2, float yy, float x0, float (&out)[L]) {
   const float2 Y = make_float2(yy, yy), X = make_float2(x0, x0);
   const float2 NEG = make_float2(-1.0f, -1.0f), TWO = make_float2(2.0f, 2.0f), ONE = make_float2(1.0f, 1.0f);
-  float2 acc[8];
+  static_assert(L >= 1 && L <= 8, "runs of at most 8 pixels");
+  float2 acc[L];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) acc[u] = make_float2(0.0f, 0.0f);
+  for (int u = 0; u < L; ++u) acc[u] = make_float2(0.0f, 0.0f);
   for (int t = 0; t < nr2; t += 2) {
     const float2 qa = *reinterpret_cast<const float2*>(&rt.rqa[t]);
     const float2 dy = __ffma2_rn(*reinterpret_cast<const float2*>(&rt.rmy[t]), NEG, Y);
@@ -611,14 +613,14 @@ __device__ __forceinline__ void real_space_8(const RealTerms& rt, int nr2, float
     float2 rr = make_float2(ex2(e1.x), ex2(e1.y));
     const float2 r8 = *reinterpret_cast<const float2*>(&rt.rrr[t]);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < L; ++u) {
       acc[u] = __fadd2_rn(acc[u], g);
       g = __fmul2_rn(g, rr);
       rr = __fmul2_rn(rr, r8);
     }
   }
 #pragma unroll
-  for (int u = 0; u < 8; ++u) out[u] += acc[u].x + acc[u].y;
+  for (int u = 0; u < L; ++u) out[u] += acc[u].x + acc[u].y;
 }
 
 // ------------------------------------------------------------------------

@@ -34,9 +34,20 @@ struct FwdCfg {
   static constexpr int THREADS = NFFT * TPF;
   static constexpr int LS = psf_lstride(N);
   static constexpr int PSF_ELEMS = psf_spec_elems(N);
-  // FFT work row stride (float2); for N = 128 two more float2 spread the
-  // pairing writes (rows p of one instruction otherwise share 4 bank groups)
-  static constexpr int WS = wstride<N>() + (N == 128 ? 2 : 0);
+  // FFT work row stride (float2).  A row touches wstride<N>() = N + N/8
+  // slots.  N = 128: two more float2 spread the pairing writes (rows p of one
+  // instruction otherwise share 4 bank groups).  N = 64: 88 = 16 more, room
+  // for the row shift below.
+  static constexpr int WS = wstride<N>() + (N == 128 ? 2 : N == 64 ? 16 : 0);
+  // Row r of a work buffer starts at r WS + SKEW ((r >> 1) & 1): for N = 64
+  // rows 2-3 of every 4 move by 4 float2, which spreads the pairing writes
+  // (4 consecutive rows per instruction) and the output-row stores over the
+  // banks while neighbouring rows keep complementary bank halves for the FFT
+  // passes.  The shift is even (rows stay 16-byte aligned) and below
+  // WS - wstride<N>() (rows do not overlap).
+  static constexpr int SKEW = N == 64 ? 4 : 0;
+  static_assert(SKEW <= WS - wstride<N>(), "shifted rows must not overlap");
+  __host__ __device__ static constexpr int row(int r) { return r * WS + SKEW * ((r >> 1) & 1); }
   static constexpr int W_ELEMS = NFFT * WS;
   static constexpr int R1 = Radix<N>::r[1];
   static constexpr int R2 = Radix<N>::r[2];
@@ -86,7 +97,7 @@ template <int N>
 __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     render_fwd_kernel(RenderParams p) {
   using C = FwdCfg<N>;
-  constexpr int TPF = C::TPF, WS = C::WS, LS = C::LS;
+  constexpr int TPF = C::TPF, LS = C::LS;
   constexpr int B = bucket_of(N);
   constexpr float INV_N = 1.0f / N;
   // a Fourier component is skipped over a warp's bins when 2^(c q) < 2^-40
@@ -137,8 +148,8 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     s_pos[0] = p0;
     if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1]);
   }
-  float2* wa = WA + f * WS;   // this group's row in pass A
-  float2* wb = WB + f * WS;   // this group's row in pass B
+  float2* wa = WA + C::row(f);   // this group's row in pass A
+  float2* wb = WB + C::row(f);   // this group's row in pass B
   int cur_psf = -1;
   uint32_t psf_parity = 0, rec_parity = 0;   // rec_parity bit b: phase of record buffer b
   __syncthreads();
@@ -296,7 +307,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
           other.y = __shfl_xor_sync(0xffffffffu, mine.y, 1);
           const float2 A = odd ? other : mine, Bv = odd ? mine : other;
           const int pr = stockham_out_index<N, R>(j, NS, q, m) >> 1;
-          float2* row = WB + pr * WS;
+          float2* row = WB + C::row(pr);
           if (f > 0) {
             if (!odd) row[swz<N>(f)] = make_float2(A.x - Bv.y, A.y + Bv.x);
             else row[swz<N>(N - f)] = make_float2(A.x + Bv.y, Bv.x - A.y);
@@ -334,6 +345,8 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     const int nr = s_nr[buf];
 
     // ---- Step 8: add the real-space terms and store rows 2f and 2f+1 ----
+    // Each thread stores pixels 8j .. 8j+7 of both rows (runs of 4 with
+    // conflict-free reads were measured slower: twice the ex2 and term set-ups).
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       const int yy = 2 * f + h;
@@ -341,7 +354,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
       const float* src = orow + h * N + x0;
       const float4 i0 = *reinterpret_cast<const float4*>(src), i1 = *reinterpret_cast<const float4*>(src + 4);
       float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
-      if (nr > 0) real_space_8(rt, nr, (float)yy, (float)x0, o);
+      if (nr > 0) real_space_run(rt, nr, (float)yy, (float)x0, o);
       float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
       d[0] = make_float4(o[0], o[1], o[2], o[3]);
       d[1] = make_float4(o[4], o[5], o[6], o[7]);
