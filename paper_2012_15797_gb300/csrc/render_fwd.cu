@@ -329,15 +329,19 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     __syncwarp();
     float* orow = reinterpret_cast<float*>(wb);
     {
-      // rows 2f and 2f+1 of the patch overwrite this transform's own row
+      // Rows 2f and 2f+1 of the patch overwrite this transform's own row.
+      // Pixel x is kept at x ^ 4 [bit 5 of x]: the 16-byte pieces 8..15 of a
+      // row swap in pairs, so the 8 lanes that read pieces 2j (then 2j+1)
+      // below touch 8 different bank groups.
       constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
 #pragma unroll
       for (int q = 0; q < 8 / R; ++q)
 #pragma unroll
         for (int m = 0; m < R; ++m) {
           const int n = stockham_out_index<N, R>(j, NS, q, m);
-          orow[n] = v[q * R + m].x;
-          orow[N + n] = v[q * R + m].y;
+          const int x = n ^ (((n >> 5) & 1) << 2);
+          orow[x] = v[q * R + m].x;
+          orow[N + x] = v[q * R + m].y;
         }
     }
     __syncwarp();   // the group's two rows are complete
@@ -351,8 +355,10 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     for (int h = 0; h < 2; ++h) {
       const int yy = 2 * f + h;
       const int x0 = 8 * j;
-      const float* src = orow + h * N + x0;
-      const float4 i0 = *reinterpret_cast<const float4*>(src), i1 = *reinterpret_cast<const float4*>(src + 4);
+      const int sw = ((j >> 2) & 1) << 2;   // pieces 2j, 2j+1 swapped in the upper half of the row
+      const float* src = orow + h * N;
+      const float4 i0 = *reinterpret_cast<const float4*>(src + (x0 ^ sw));
+      const float4 i1 = *reinterpret_cast<const float4*>(src + ((x0 + 4) ^ sw));
       float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
       if (nr > 0) real_space_run(rt, nr, (float)yy, (float)x0, o);
       float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
