@@ -10,6 +10,8 @@ the ``workloads`` package, which holds no rendering arithmetic).
 
 Modules:
   render.py   Section 2 Steps 1-8 in the paper's order (forward model),
+  lanczos.py  the Step 8 variant that does the sub-pixel shift by Lanczos
+              convolution of the final model,
   adjoint.py  analytic derivatives of the forward model w.r.t.
               (flux, x, y, log r_e, e1, e2) and a central finite-difference
               check,
