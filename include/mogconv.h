@@ -138,6 +138,20 @@ mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id);
 mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
 
 /*
+ * The Section 2, Step 8 variant with the sub-pixel shift done by Lanczos
+ * convolution of the final model instead of by the Fourier phase of
+ * Eq. onegaussian.  Each offset x splits into n = floor(x + 1/2), rendered
+ * exactly, and d = x - n in [-1/2, 1/2); the model (Fourier part plus
+ * real-space terms) is then convolved, periodically over the patch, with the
+ * normalised Lanczos-3 weights w_a = L(a - d) / sum_b L(b - d), a = -3..3,
+ * L(t) = sinc(t) sinc(t/3), along x and then y.  Arguments, layout,
+ * ownership and asynchrony as mog_render_batch.  Patch sides 32, 64 and 128;
+ * galaxies of side 256 are skipped and reported as MOG_ERR_DEVICE through
+ * the status word (mog_sync_status), like other unsupported sizes.
+ */
+mog_status mog_render_batch_lanczos(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
+
+/*
  * Same result as mog_render_batch, but the call allocates no memory: no
  * cudaMalloc, no cudaFree, no allocating library routine.  (The paper has no
  * counterpart; this is an interface for callers that cannot let a library

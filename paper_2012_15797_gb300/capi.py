@@ -34,7 +34,7 @@ EXPORTED = (
     "mog_set_timing", "mog_read_timing", "mog_render_backward", "mog_render_batch_noalloc",
     "mog_autotune", "mog_graph_capture", "mog_graph_launch", "mog_graph_destroy",
     "mog_server_create", "mog_server_add_fit", "mog_server_submit", "mog_server_wait", "mog_server_replay",
-    "mog_server_replay_join", "mog_server_stats", "mog_server_destroy",
+    "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -85,6 +85,7 @@ def _load():
         "mog_create_psf": ([VP, FP, I, I, FP, I, P(I)], I),
         "mog_destroy_psf": ([VP, I], I),
         "mog_render_batch": ([VP, P(mog_batch), VP, VP], I),
+        "mog_render_batch_lanczos": ([VP, P(mog_batch), VP, VP], I),
         "mog_render_backward": ([VP, P(mog_batch), VP, VP, VP], I),
         "mog_render_batch_noalloc": ([VP, P(mog_batch), VP, VP], I),
         "mog_autotune": ([VP, P(mog_batch), VP, VP, VP, VP, I, P(I)], I),
@@ -179,6 +180,11 @@ def make_batch(count, ptrs, size_mask=0):
 def mog_render_batch(ctx, batch, out_ptr, stream=0):
     _check(ctx, _lib.mog_render_batch(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
                                       ctypes.c_void_p(int(stream))))
+
+
+def mog_render_batch_lanczos(ctx, batch, out_ptr, stream=0):
+    _check(ctx, _lib.mog_render_batch_lanczos(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
+                                              ctypes.c_void_p(int(stream))))
 
 
 def mog_render_batch_noalloc(ctx, batch, out_ptr, stream=0):

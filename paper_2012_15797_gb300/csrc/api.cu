@@ -328,16 +328,19 @@ mog_status launch_buckets(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, u
 
 namespace mog {
 
-mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s) {
+mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s,
+                       bool lanczos) {
   mog_status st = check_batch(ctx, batch);
   if (st != MOG_OK) return st;
   if (batch->count == 0) return MOG_OK;
   if (!out || (reinterpret_cast<uintptr_t>(out) & 15)) return fail(ctx, MOG_ERR_ARG, "out must be 16-byte aligned");
+  const uint32_t buckets = lanczos ? LZ_BUCKETS : FWD_BUCKETS;
   RenderParams p;
-  if ((st = plan_batch(ctx, ws, batch, out, FWD_BUCKETS, s, &p)) != MOG_OK) return st;
+  if ((st = plan_batch(ctx, ws, batch, out, buckets, s, &p)) != MOG_OK) return st;
   p.records = ws->records;
+  p.lanczos = lanczos ? 1 : 0;
   MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ws->records, s));
-  return launch_buckets(ctx, ws, batch, FWD_BUCKETS, s, [&](int n, cudaStream_t bs) {
+  return launch_buckets(ctx, ws, batch, buckets, s, [&](int n, cudaStream_t bs) {
     RenderParams q = p;
     q.chunk = ctx->tune_fwd[bucket_of(n)].chunk;
     return launch_render_fwd(n, q, ctx->num_sms, ctx->tune_fwd[bucket_of(n)].ctas_per_sm, bs);
@@ -374,6 +377,11 @@ extern "C" {
 mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
   if (!ctx) return MOG_ERR_ARG;
   return render_with(ctx, &ctx->ws, batch, out, static_cast<cudaStream_t>(stream));
+}
+
+mog_status mog_render_batch_lanczos(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  return render_with(ctx, &ctx->ws, batch, out, static_cast<cudaStream_t>(stream), true);
 }
 
 mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,

@@ -294,13 +294,14 @@ struct __align__(16) GalaxyRecord {
   int psf;
   float s11, s12, s22; // S (pixel covariance per unit profile variance)
   float flux;
-  float x, y;          // offset from the patch centre
+  float x, y;          // offset from the patch centre (its integer part in Lanczos mode)
   int64_t gal;         // index of the galaxy in the batch
   int64_t off;         // element offset of its patch in the output
   // Fourier components: amplitude flux a_i w_F / N^2, exponent -2 pi^2 v_i log2(e)
   float famp[KMAX], fcoef[KMAX];
   // real-space components: amplitude flux a_i (1 - w_F), profile variance v_i
   float ramp[KMAX], rvar[KMAX];
+  float lx, ly;        // Lanczos mode: the fractional offset in [-1/2, 1/2); else 0
 };
 static_assert(sizeof(GalaxyRecord) == 256, "record layout");
 constexpr int RECORD_BYTES = 256;   // stride of the record array (16-byte multiple)
@@ -317,8 +318,10 @@ __device__ __forceinline__ float ramp_weight(float ns) {
 }
 
 // Executed by one full warp (lane = mixture component); writes *out.
+// With `lanczos` the offset is split into an integer part, rendered exactly,
+// and a fraction in [-1/2, 1/2) left to the Lanczos shift.
 __device__ inline void galaxy_record_warp(const BatchView& b, int64_t g, int n, const DevProfile* profiles,
-                                          const DevPsf* psfs, int* status, GalaxyRecord* out) {
+                                          const DevPsf* psfs, int* status, bool lanczos, GalaxyRecord* out) {
   const int lane = threadIdx.x & 31;
   const float flux = b.flux[g], x = b.x[g], y = b.y[g], lre = b.log_re[g];
   const float e1 = b.e1[g], e2 = b.e2[g], sn = b.sersic_n[g];
@@ -391,11 +394,49 @@ __device__ inline void galaxy_record_warp(const BatchView& b, int64_t g, int n, 
     out->s12 = s12;
     out->s22 = s22;
     out->flux = flux;
-    out->x = x;
-    out->y = y;
+    const float ix = lanczos ? floorf(x + 0.5f) : x, iy = lanczos ? floorf(y + 0.5f) : y;
+    out->x = ix;
+    out->y = iy;
+    out->lx = x - ix;
+    out->ly = y - iy;
     out->gal = g;
     out->off = off;
   }
+}
+
+// ------------------------------------------------------------------------
+// Lanczos-3 sub-pixel shift (Section 2, Step 8 variant).  A shift by d is the
+// periodic convolution J(x) = sum_{a=-3..3} w_a I(x - a) with
+// w_a = L(a - d) / sum_b L(b - d), L(t) = sinc(t) sinc(t/3) on |t| < 3.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ void lanczos_weights(float d, float (&w)[7]) {
+  float sum = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const float t = (float)(i - 3) - d;
+    float v = 0.0f;
+    if (t == 0.0f) v = 1.0f;
+    else if (fabsf(t) < 3.0f) v = 3.0f * sinpif(t) * sinpif(t * (1.0f / 3.0f)) / (PI_F * PI_F * t * t);
+    w[i] = v;
+    sum += v;
+  }
+  const float inv = 1.0f / sum;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) w[i] *= inv;
+}
+
+// Transfer function of that convolution at frequency f (cycles per pixel):
+// H(f) = sum_a w_a e^{-2 pi i f a}.  Multiplying a spectrum by H(nu) H(omega)
+// is the periodic 2-D convolution of its inverse transform.
+__device__ __forceinline__ float2 lanczos_response(const float (&w)[7], float f) {
+  float s1, c1;
+  sincospif(-2.0f * f, &s1, &c1);            // z = e^{-2 pi i f}
+  const float c2 = c1 * c1 - s1 * s1, s2 = 2.0f * c1 * s1;
+  const float c3 = c2 * c1 - s2 * s1, s3 = c2 * s1 + s2 * c1;
+  // sum_a w_a z^a, a = -3..3, with z^-a = conj(z^a)
+  const float re = w[3] + (w[4] + w[2]) * c1 + (w[5] + w[1]) * c2 + (w[6] + w[0]) * c3;
+  const float im = (w[4] - w[2]) * s1 + (w[5] - w[1]) * s2 + (w[6] - w[0]) * s3;
+  return make_float2(re, im);
 }
 
 // Record of the adjoint (Section 2 Steps 3-4 plus the derivatives the

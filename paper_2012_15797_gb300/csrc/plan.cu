@@ -99,7 +99,7 @@ __global__ void galaxy_prep(RenderParams p, unsigned char* records) {
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int pos = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pos < total; pos += warps) {
     const int64_t g = p.order[pos];
-    galaxy_record_warp(p.b, g, p.b.size[g], p.profiles, p.psfs, p.status,
+    galaxy_record_warp(p.b, g, p.b.size[g], p.profiles, p.psfs, p.status, p.lanczos != 0,
                        reinterpret_cast<GalaxyRecord*>(records + (size_t)pos * RECORD_BYTES));
   }
 }

@@ -93,7 +93,102 @@ struct LastPass {
   static constexpr int NS = N / R;
 };
 
+// Position of pixel x in an output row: the 16-byte pieces 8..15 swap in
+// pairs (x ^ 4 when bit 5 of x is set), so that the 8 lanes of a group that
+// read pieces 2j, 2j+1 touch 8 different bank groups.
+__device__ __forceinline__ int out_pos(int x) { return x ^ (((x >> 5) & 1) << 2); }
+
+// Lanczos variant, galaxies with real-space terms: out = F + Lz(R), F the
+// (already shifted) Fourier part in the group's own rows, R the real-space
+// terms at the integer offset, Lz the periodic Lanczos convolution, done
+// along x in the group's rows, then (after a CTA barrier) along y.
 template <int N>
+__device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, const RealTerms& rt, int nr,
+                                                       const float* wl, int f, int j, float* dst) {
+  using C = FwdCfg<N>;
+  const int x0 = 8 * j;
+  const int p0 = out_pos(x0), p1 = out_pos(x0 + 4);
+  float F[2][8], X[2][8];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float4 a = *reinterpret_cast<const float4*>(orow + h * N + p0);
+    const float4 b = *reinterpret_cast<const float4*>(orow + h * N + p1);
+    F[h][0] = a.x; F[h][1] = a.y; F[h][2] = a.z; F[h][3] = a.w;
+    F[h][4] = b.x; F[h][5] = b.y; F[h][6] = b.z; F[h][7] = b.w;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) X[h][u] = 0.0f;
+    real_space_run(rt, nr, (float)(2 * f + h), (float)x0, X[h]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    *reinterpret_cast<float4*>(orow + h * N + p0) = make_float4(X[h][0], X[h][1], X[h][2], X[h][3]);
+    *reinterpret_cast<float4*>(orow + h * N + p1) = make_float4(X[h][4], X[h][5], X[h][6], X[h][7]);
+  }
+  __syncwarp();
+  // along x: J(x) = sum_a w_a R(x - a), x = x0 + u, over the window x0-3 .. x0+10
+  float wx[7];
+#pragma unroll
+  for (int a = 0; a < 7; ++a) wx[a] = wl[a];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float win[14];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) win[3 + u] = X[h][u];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      win[a] = orow[h * N + out_pos((x0 - 3 + a) & (N - 1))];
+      win[11 + a] = orow[h * N + out_pos((x0 + 8 + a) & (N - 1))];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 7; ++a) acc = fmaf(wx[a], win[3 + u - (a - 3)], acc);
+      X[h][u] = acc;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    *reinterpret_cast<float4*>(orow + h * N + p0) = make_float4(X[h][0], X[h][1], X[h][2], X[h][3]);
+    *reinterpret_cast<float4*>(orow + h * N + p1) = make_float4(X[h][4], X[h][5], X[h][6], X[h][7]);
+  }
+  __syncthreads();   // every row has been convolved along x
+  // along y: rows 2f - 3 .. 2f + 4 feed rows 2f (taps b = 3 - rr) and 2f+1 (b = 4 - rr)
+  float wy[7];
+#pragma unroll
+  for (int a = 0; a < 7; ++a) wy[a] = wl[8 + a];
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr) {
+    const int row = (2 * f - 3 + rr) & (N - 1);
+    const float* src = reinterpret_cast<const float*>(WB + C::row(row >> 1)) + (row & 1) * N;
+    const float4 a = *reinterpret_cast<const float4*>(src + p0);
+    const float4 b = *reinterpret_cast<const float4*>(src + p1);
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    if (rr <= 6) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) F[0][u] = fmaf(wy[6 - rr], v[u], F[0][u]);
+    }
+    if (rr >= 1) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) F[1][u] = fmaf(wy[7 - rr], v[u], F[1][u]);
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float4* d = reinterpret_cast<float4*>(dst + (2 * f + h) * N + x0);
+    d[0] = make_float4(F[h][0], F[h][1], F[h][2], F[h][3]);
+    d[1] = make_float4(F[h][4], F[h][5], F[h][6], F[h][7]);
+  }
+}
+
+// LZ: the Lanczos sub-pixel-shift variant (records carry the integer offset
+// and the fraction).  The periodic Lanczos convolution of the Fourier part is
+// the multiplication of its spectrum by H(nu) H(omega), folded into the
+// shift-phase tables; the real-space part, when a galaxy has one, is
+// convolved in shared memory along x, then y, before it is added.
+template <int N, bool LZ>
 __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     render_fwd_kernel(RenderParams p) {
   using C = FwdCfg<N>;
@@ -118,6 +213,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   __shared__ float* s_dst[2];   // per record buffer: output patch and padded real-space term count
   __shared__ int s_nr[2];
   __shared__ float4 s_fc[KMAX];   // Fourier components as (a, a, c, c): operand pairs of f32x2
+  __shared__ float s_lzw[2][16];  // LZ, per record buffer: Lanczos weights along x [0, 7) and y [8, 15)
 
   const int tid = threadIdx.x;
   const int f = tid / TPF, j = tid % TPF;
@@ -203,11 +299,30 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
         float sn, cs;
         if (i < C::H) {
           sincospif(-2.0f * gx * (float)i * INV_N, &sn, &cs);
-          px[i] = make_float2(cs, sn);
+          float2 ph = make_float2(cs, sn);
+          if constexpr (LZ) {
+            float w[7];
+            lanczos_weights(r.lx, w);
+            ph = cmul(ph, lanczos_response(w, (float)i * INV_N));
+            if (i == 0)
+#pragma unroll
+              for (int u = 0; u < 7; ++u) s_lzw[buf][u] = w[u];
+          }
+          px[i] = ph;
         } else if (i < C::H + N) {
           const int l = i - C::H;
-          sincospif(-2.0f * gy * (float)(l < N / 2 ? l : l - N) * INV_N, &sn, &cs);
-          py[l] = make_float2(cs, sn);
+          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+          sincospif(-2.0f * gy * om, &sn, &cs);
+          float2 ph = make_float2(cs, sn);
+          if constexpr (LZ) {
+            float w[7];
+            lanczos_weights(r.ly, w);
+            ph = cmul(ph, lanczos_response(w, om));
+            if (l == 0)
+#pragma unroll
+              for (int u = 0; u < 7; ++u) s_lzw[buf][8 + u] = w[u];
+          }
+          py[l] = ph;
         } else if (i < C::H + 2 * N) {
           const int l = i - C::H - N;
           const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
@@ -217,7 +332,15 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
           sincospif(-gx, &sn, &cs);
-          nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(make_float2(cs, sn), make_float2(cy, sy))), acc);
+          float2 phx = make_float2(cs, sn), phy = make_float2(cy, sy);
+          if constexpr (LZ) {
+            float w[7];
+            lanczos_weights(r.lx, w);
+            phx = cmul(phx, lanczos_response(w, 0.5f));
+            lanczos_weights(r.ly, w);
+            phy = cmul(phy, lanczos_response(w, om));
+          }
+          nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(phx, phy)), acc);
         } else {
           const int t = i - t0;
           if (t < nrt) real_term(r, ps.mog, kp, N, t, &rt);
@@ -349,6 +472,12 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     const int nr = s_nr[buf];
 
     // ---- Step 8: add the real-space terms and store rows 2f and 2f+1 ----
+    if constexpr (LZ) {
+      if (nr > 0) {   // uniform over the CTA
+        lanczos_real_and_store<N>(WB, orow, rt, nr, s_lzw[buf], f, j, dst);
+        continue;
+      }
+    }
     // Each thread stores pixels 8j .. 8j+7 of both rows (runs of 4 with
     // conflict-free reads were measured slower: twice the ex2 and term set-ups).
 #pragma unroll 1
@@ -368,28 +497,35 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   }
 }
 
-template <int N>
+template <int N, bool LZ = false>
 static int fwd_occupancy() {
   using C = FwdCfg<N>;
   static int occ = -1;
   if (occ < 0) {
-    if (cudaFuncSetAttribute(render_fwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
+    if (cudaFuncSetAttribute(render_fwd_kernel<N, LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fwd_kernel<N>, C::THREADS, C::SMEM) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fwd_kernel<N, LZ>, C::THREADS, C::SMEM) !=
+            cudaSuccess)
       return -1;
     if (occ < 1) occ = 1;
   }
   return occ;
 }
 
-template <int N>
-static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+template <int N, bool LZ>
+static cudaError_t launch_fwd_mode(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
   using C = FwdCfg<N>;
-  const int occ = fwd_occupancy<N>();
+  const int occ = fwd_occupancy<N, LZ>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_fwd_kernel<N><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
+  render_fwd_kernel<N, LZ><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
   return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  return p.lanczos ? launch_fwd_mode<N, true>(p, num_sms, ctas_per_sm, s)
+                   : launch_fwd_mode<N, false>(p, num_sms, ctas_per_sm, s);
 }
 
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
@@ -397,7 +533,7 @@ cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int cta
     case 32: return launch_fwd<32>(p, num_sms, ctas_per_sm, s);
     case 64: return launch_fwd<64>(p, num_sms, ctas_per_sm, s);
     case 128: return launch_fwd<128>(p, num_sms, ctas_per_sm, s);
-    case 256: return launch_render_fwd256(p, num_sms, s);
+    case 256: return p.lanczos ? cudaErrorInvalidValue : launch_render_fwd256(p, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -88,13 +88,19 @@ class Renderer:
         except Exception:
             pass
 
-    def render(self, batch, out=None, stream=None):
-        """Renders a DeviceBatch into a flat float32 device tensor."""
+    def render(self, batch, out=None, stream=None, shift="phase"):
+        """Renders a DeviceBatch into a flat float32 device tensor.  ``shift``
+        selects how the sub-pixel offset is applied: "phase" (Fourier shift
+        phase) or "lanczos" (Lanczos-3 convolution of the final model; sides
+        32-128)."""
+        if shift not in ("phase", "lanczos"):
+            raise ValueError(f"unknown shift {shift!r}")
         if out is None:
             out = torch.empty(batch.total, dtype=torch.float32, device=self.device)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
-        capi.mog_render_batch(self.ctx, b, out.data_ptr(), s.cuda_stream)
+        fn = capi.mog_render_batch if shift == "phase" else capi.mog_render_batch_lanczos
+        fn(self.ctx, b, out.data_ptr(), s.cuda_stream)
         return out
 
     def render_backward(self, batch, grad_out, grad_params=None, stream=None):
