@@ -145,9 +145,7 @@ mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, vo
  * real-space terms) is then convolved, periodically over the patch, with the
  * normalised Lanczos-3 weights w_a = L(a - d) / sum_b L(b - d), a = -3..3,
  * L(t) = sinc(t) sinc(t/3), along x and then y.  Arguments, layout,
- * ownership and asynchrony as mog_render_batch.  Patch sides 32, 64 and 128;
- * galaxies of side 256 are skipped and reported as MOG_ERR_DEVICE through
- * the status word (mog_sync_status), like other unsupported sizes.
+ * ownership, asynchrony and errors as mog_render_batch (all patch sides).
  */
 mog_status mog_render_batch_lanczos(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
 

@@ -57,6 +57,7 @@ void workspace_free(Workspace* ws) {
   cudaFree(ws->plan.order);
   cudaFree(ws->records);
   cudaFree(ws->adj_records);
+  cudaFree(ws->lzw);
   cudaFree(ws->bwd256);
   for (int b = 0; b < NBUCKET; ++b) {
     if (ws->side[b]) cudaStreamDestroy(ws->side[b]);
@@ -91,13 +92,16 @@ mog_status ensure_capacity(mog_ctx* ctx, Workspace* ws, int64_t count) {
   if (ws->plan.order) MOG_CUDA(ctx, cudaFree(ws->plan.order));
   if (ws->records) MOG_CUDA(ctx, cudaFree(ws->records));
   if (ws->adj_records) MOG_CUDA(ctx, cudaFree(ws->adj_records));
+  if (ws->lzw) MOG_CUDA(ctx, cudaFree(ws->lzw));
   ws->plan.order = nullptr;
   ws->records = nullptr;
   ws->adj_records = nullptr;
+  ws->lzw = nullptr;
   ws->cap = 0;
   MOG_CUDA(ctx, cudaMalloc(&ws->plan.order, sizeof(int32_t) * cap));
   MOG_CUDA(ctx, cudaMalloc(&ws->records, (size_t)RECORD_BYTES * cap));
   MOG_CUDA(ctx, cudaMalloc(&ws->adj_records, sizeof(AdjRecord) * cap));
+  MOG_CUDA(ctx, cudaMalloc(&ws->lzw, sizeof(float) * 16 * cap));
   ws->cap = cap;
   return MOG_OK;
 }
@@ -339,6 +343,7 @@ mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, floa
   if ((st = plan_batch(ctx, ws, batch, out, buckets, s, &p)) != MOG_OK) return st;
   p.records = ws->records;
   p.lanczos = lanczos ? 1 : 0;
+  p.lzw = ws->lzw;
   MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ws->records, s));
   return launch_buckets(ctx, ws, batch, buckets, s, [&](int n, cudaStream_t bs) {
     RenderParams q = p;

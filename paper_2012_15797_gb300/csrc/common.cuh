@@ -409,20 +409,17 @@ __device__ inline void galaxy_record_warp(const BatchView& b, int64_t g, int n, 
 // periodic convolution J(x) = sum_{a=-3..3} w_a I(x - a) with
 // w_a = L(a - d) / sum_b L(b - d), L(t) = sinc(t) sinc(t/3) on |t| < 3.
 // ------------------------------------------------------------------------
-__device__ __forceinline__ void lanczos_weights(float d, float (&w)[7]) {
-  float sum = 0.0f;
+__device__ __forceinline__ float lanczos_tap(float t) {
+  if (t == 0.0f) return 1.0f;
+  if (fabsf(t) >= 3.0f) return 0.0f;
+  return 3.0f * sinpif(t) * sinpif(t * (1.0f / 3.0f)) / (PI_F * PI_F * t * t);
+}
+
+// The weights of one galaxy, written by the record prologue (16 floats per
+// planned position: x at [0, 7), y at [8, 15)).
+__device__ __forceinline__ void load_weights(const float* lzw, int off, float (&w)[7]) {
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    const float t = (float)(i - 3) - d;
-    float v = 0.0f;
-    if (t == 0.0f) v = 1.0f;
-    else if (fabsf(t) < 3.0f) v = 3.0f * sinpif(t) * sinpif(t * (1.0f / 3.0f)) / (PI_F * PI_F * t * t);
-    w[i] = v;
-    sum += v;
-  }
-  const float inv = 1.0f / sum;
-#pragma unroll
-  for (int i = 0; i < 7; ++i) w[i] *= inv;
+  for (int u = 0; u < 7; ++u) w[u] = __ldg(lzw + off + u);
 }
 
 // Transfer function of that convolution at frequency f (cycles per pixel):

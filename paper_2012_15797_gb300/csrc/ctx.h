@@ -18,6 +18,7 @@ struct Workspace {
   int64_t cap = 0;                       // galaxies the order / records hold
   unsigned char* records = nullptr;      // RECORD_BYTES per planned galaxy
   unsigned char* adj_records = nullptr;  // sizeof(AdjRecord) per planned galaxy
+  float* lzw = nullptr;                  // 16 floats per planned galaxy (Lanczos weights)
   float2* bwd256 = nullptr;              // per-CTA scratch of the 256 x 256 adjoint
   cudaStream_t side[NBUCKET] = {};
   cudaEvent_t fork_ev = nullptr;

@@ -21,7 +21,8 @@ struct RenderParams {
   const unsigned char* records; // RECORD_BYTES per planned position (GalaxyRecord)
   int* status;
   int chunk;                    // queue positions taken per request
-  int lanczos = 0;              // 1: sub-pixel shift by Lanczos convolution (N <= 128)
+  int lanczos = 0;              // 1: sub-pixel shift by Lanczos convolution
+  float* lzw = nullptr;         // lanczos: 16 floats per planned position, weights along x [0, 7), y [8, 15)
 };
 
 // Launch shape of one size bucket: CTAs per SM (clamped to what fits) and
@@ -70,7 +71,7 @@ int render_fwd_max_ctas(int n);
 
 // Patch sides each direction supports (bit b: N = 32 << b).
 constexpr uint32_t FWD_BUCKETS = 0xF;   // 32, 64, 128, 256
-constexpr uint32_t LZ_BUCKETS = 0x7;    // Lanczos variant: 32, 64, 128
+constexpr uint32_t LZ_BUCKETS = 0xF;    // Lanczos variant: 32, 64, 128, 256
 constexpr uint32_t BWD_BUCKETS = 0xF;   // 32, 64, 128, 256
 size_t render_fwd_smem(int n);
 

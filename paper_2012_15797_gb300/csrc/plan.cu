@@ -101,6 +101,19 @@ __global__ void galaxy_prep(RenderParams p, unsigned char* records) {
     const int64_t g = p.order[pos];
     galaxy_record_warp(p.b, g, p.b.size[g], p.profiles, p.psfs, p.status, p.lanczos != 0,
                        reinterpret_cast<GalaxyRecord*>(records + (size_t)pos * RECORD_BYTES));
+    if (p.lanczos) {
+      // Lanczos weights once per galaxy: lanes 0-6 along x, 8-14 along y
+      const int lane = threadIdx.x & 31;
+      const float c = (lane & 8) ? p.b.y[g] : p.b.x[g];
+      const float d = c - floorf(c + 0.5f);
+      const int t = (lane & 7) - 3;
+      float w = 0.0f;
+      if (lane < 16 && (lane & 7) < 7) w = lanczos_tap((float)t - d);
+      float sum = w;
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane < 16) p.lzw[(size_t)pos * 16 + lane] = (lane & 7) < 7 ? w / sum : 0.0f;
+    }
   }
 }
 

@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
         s_nr[buf] = nr2;
       }
       const float gx = r.x, gy = r.y;
+      const float* lzw = LZ ? p.lzw + ((size_t)p.bucket_start[B] + pos) * 16 : nullptr;
       const int t0 = C::H + 2 * N, ntask = t0 + nr2 + r.nf;
       for (int i = tid; i < ntask; i += C::THREADS) {
         float sn, cs;
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
           float2 ph = make_float2(cs, sn);
           if constexpr (LZ) {
             float w[7];
-            lanczos_weights(r.lx, w);
+            load_weights(lzw, 0, w);
             ph = cmul(ph, lanczos_response(w, (float)i * INV_N));
             if (i == 0)
 #pragma unroll
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
           float2 ph = make_float2(cs, sn);
           if constexpr (LZ) {
             float w[7];
-            lanczos_weights(r.ly, w);
+            load_weights(lzw, 8, w);
             ph = cmul(ph, lanczos_response(w, om));
             if (l == 0)
 #pragma unroll
@@ -335,9 +336,9 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
           float2 phx = make_float2(cs, sn), phy = make_float2(cy, sy);
           if constexpr (LZ) {
             float w[7];
-            lanczos_weights(r.lx, w);
+            load_weights(lzw, 0, w);
             phx = cmul(phx, lanczos_response(w, 0.5f));
-            lanczos_weights(r.ly, w);
+            load_weights(lzw, 8, w);
             phy = cmul(phy, lanczos_response(w, om));
           }
           nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(phx, phy)), acc);
@@ -533,7 +534,7 @@ cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int cta
     case 32: return launch_fwd<32>(p, num_sms, ctas_per_sm, s);
     case 64: return launch_fwd<64>(p, num_sms, ctas_per_sm, s);
     case 128: return launch_fwd<128>(p, num_sms, ctas_per_sm, s);
-    case 256: return p.lanczos ? cudaErrorInvalidValue : launch_render_fwd256(p, num_sms, s);
+    case 256: return launch_render_fwd256(p, num_sms, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -14,6 +14,13 @@
 //             row pair's input, transform, add the real-space terms, store
 //             the two pixel rows over the input
 // The PSF spectrum (272 KB) is read from global memory (L2-resident).
+//
+// Lanczos variant (LZ): the Fourier part is shifted through the phase tables
+// (the Lanczos transfer function H(nu) H(omega)); a galaxy with real-space
+// terms then gets its real-space part convolved and added in two strips of
+// 128 rows: the 134 rows each strip needs are evaluated and convolved along x
+// (one warp per row, neighbours by shuffle) into shared memory that the
+// transforms no longer use, then convolved along y and added to the patch.
 #include "common.cuh"
 #include "internal.h"
 
@@ -48,7 +55,74 @@ constexpr size_t off_rec = (off_nyq + sizeof(float2) * N + 15) & ~size_t(15);
 constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);
 constexpr size_t off_bar = (off_rt + sizeof(RealTerms) + 15) & ~size_t(15);
 constexpr size_t SMEM = off_bar + 2 * sizeof(uint64_t);
+constexpr int STRIP = 128;                                                // output rows per strip
+static_assert(sizeof(float) * (STRIP + 6) * N <= off_tw, "Lanczos strip must fit below the twiddles");
 
+// LZ, galaxy with real-space terms: patch += Lz(R), R the real-space terms at
+// the integer offset, Lz the periodic Lanczos convolution with weights wl
+// (x: [0, 7), y: [8, 15)).  Called by all threads after the patch holds the
+// Fourier part; `strip` is shared memory of (STRIP + 6) rows.
+__device__ __forceinline__ void lanczos_real_256(const RealTerms& rt, int nr, const float* wl, float* strip,
+                                                 float* dst, int f, int j) {
+  const int x0 = 8 * j;
+  float wx[7], wy[7];
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+    wx[a] = wl[a];
+    wy[a] = wl[8 + a];
+  }
+  for (int y0 = 0; y0 < N; y0 += STRIP) {
+    // rows y0 - 3 .. y0 + STRIP + 2 (mod N), convolved along x
+    for (int i = f; i < STRIP + 6; i += WARPS) {
+      const int yy = (y0 - 3 + i) & (N - 1);
+      float R[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) R[u] = 0.0f;
+      real_space_run(rt, nr, (float)yy, (float)x0, R);
+      float win[14];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) win[3 + u] = R[u];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {   // x0 - 3 + a from the lane below, x0 + 8 + a from the lane above
+        win[a] = __shfl_sync(0xffffffffu, R[5 + a], (j + 31) & 31);
+        win[11 + a] = __shfl_sync(0xffffffffu, R[a], (j + 1) & 31);
+      }
+      float X[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 7; ++a) acc = fmaf(wx[a], win[3 + u - (a - 3)], acc);
+        X[u] = acc;
+      }
+      float4* srow = reinterpret_cast<float4*>(strip + i * N + x0);
+      srow[0] = make_float4(X[0], X[1], X[2], X[3]);
+      srow[1] = make_float4(X[4], X[5], X[6], X[7]);
+    }
+    __syncthreads();
+    // output rows y0 + o: sum_b wy_b X(y - b), strip rows o + 3 - b
+    for (int o = f; o < STRIP; o += WARPS) {
+      float acc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] = 0.0f;
+#pragma unroll
+      for (int b = 0; b < 7; ++b) {
+        const float4* srow = reinterpret_cast<const float4*>(strip + (o + 6 - b) * N + x0);
+        const float4 p0 = srow[0], p1 = srow[1];
+        const float v[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = fmaf(wy[b], v[u], acc[u]);
+      }
+      float4* d = reinterpret_cast<float4*>(dst + (y0 + o) * N + x0);
+      const float4 f0 = d[0], f1 = d[1];   // the Fourier part, written by this CTA
+      d[0] = make_float4(f0.x + acc[0], f0.y + acc[1], f0.z + acc[2], f0.w + acc[3]);
+      d[1] = make_float4(f1.x + acc[4], f1.y + acc[5], f1.z + acc[6], f1.w + acc[7]);
+    }
+    __syncthreads();
+  }
+}
+
+template <bool LZ>
 __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams p) {
   constexpr float INV_N = 1.0f / N;
   constexpr float NEGLIGIBLE_LOG2 = -40.0f;
@@ -67,6 +141,7 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
   __shared__ int s_pos[2];
   __shared__ float s_psf_mog[KPSF][6];
   __shared__ int s_kpsf;
+  __shared__ float s_lzw[16];   // LZ: Lanczos weights along x [0, 7) and y [8, 15)
 
   const int tid = threadIdx.x;
   const int f = tid >> 5, j = tid & 31;   // warp = transform slot, lane = thread in it
@@ -128,17 +203,37 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
     // per-galaxy tables
     {
       const float gx = r.x, gy = r.y;
+      const float* lzw = LZ ? p.lzw + ((size_t)p.bucket_start[B] + pos) * 16 : nullptr;
       const int kp = s_kpsf;
       const int nrt = r.nrc * kp, ntask = H + 2 * N + real_terms_padded(nrt);
       for (int i = tid; i < ntask; i += THREADS) {
         float sn, cs;
         if (i < H) {
           sincospif(-2.0f * gx * (float)i * INV_N, &sn, &cs);
-          px[i] = make_float2(cs, sn);
+          float2 ph = make_float2(cs, sn);
+          if constexpr (LZ) {
+            float wv[7];
+            load_weights(lzw, 0, wv);
+            ph = cmul(ph, lanczos_response(wv, (float)i * INV_N));
+            if (i == 0)
+#pragma unroll
+              for (int u = 0; u < 7; ++u) s_lzw[u] = wv[u];
+          }
+          px[i] = ph;
         } else if (i < H + N) {
           const int l = i - H;
-          sincospif(-2.0f * gy * (float)(l < N / 2 ? l : l - N) * INV_N, &sn, &cs);
-          py[l] = make_float2(cs, sn);
+          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+          sincospif(-2.0f * gy * om, &sn, &cs);
+          float2 ph = make_float2(cs, sn);
+          if constexpr (LZ) {
+            float wv[7];
+            load_weights(lzw, 8, wv);
+            ph = cmul(ph, lanczos_response(wv, om));
+            if (l == 0)
+#pragma unroll
+              for (int u = 0; u < 7; ++u) s_lzw[8 + u] = wv[u];
+          }
+          py[l] = ph;
         } else if (i < H + 2 * N) {
           const int l = i - H - N;
           const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
@@ -148,7 +243,15 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
           sincospif(-gx, &sn, &cs);
-          nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(make_float2(cs, sn), make_float2(cy, sy))), acc);
+          float2 phx = make_float2(cs, sn), phy = make_float2(cy, sy);
+          if constexpr (LZ) {
+            float wv[7];
+            load_weights(lzw, 0, wv);
+            phx = cmul(phx, lanczos_response(wv, 0.5f));
+            load_weights(lzw, 8, wv);
+            phy = cmul(phy, lanczos_response(wv, om));
+          }
+          nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(phx, phy)), acc);
         } else {
           const int t = i - H - 2 * N;
           if (t < nrt) real_term(r, s_psf_mog, kp, N, t, &rt);
@@ -286,27 +389,39 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
         const float* orow = reinterpret_cast<const float*>(w) + h * N + x0;
         const float4 i0 = *reinterpret_cast<const float4*>(orow), i1 = *reinterpret_cast<const float4*>(orow + 4);
         float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
-        if (nr > 0) real_space_run(rt, nr, (float)yy, (float)x0, o);
+        if (nr > 0 && !LZ) real_space_run(rt, nr, (float)yy, (float)x0, o);
         float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
         d[0] = make_float4(o[0], o[1], o[2], o[3]);
         d[1] = make_float4(o[4], o[5], o[6], o[7]);
       }
       __syncwarp();
     }
+    if constexpr (LZ) {
+      if (nr > 0) {   // uniform over the CTA
+        __syncthreads();   // the whole Fourier part is in the patch; W, SA, SB are free
+        lanczos_real_256(rt, nr, s_lzw, reinterpret_cast<float*>(smem), dst, f, j);
+      }
+    }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, cudaStream_t s) {
+template <bool LZ>
+static cudaError_t launch_fwd256(const RenderParams& p, int num_sms, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(render_fwd256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(render_fwd256_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  render_fwd256_kernel<<<num_sms, THREADS, SMEM, s>>>(p);
+  render_fwd256_kernel<LZ><<<num_sms, THREADS, SMEM, s>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, cudaStream_t s) {
+  return p.lanczos ? launch_fwd256<true>(p, num_sms, s) : launch_fwd256<false>(p, num_sms, s);
 }
 
 }  // namespace mog

@@ -91,8 +91,7 @@ class Renderer:
     def render(self, batch, out=None, stream=None, shift="phase"):
         """Renders a DeviceBatch into a flat float32 device tensor.  ``shift``
         selects how the sub-pixel offset is applied: "phase" (Fourier shift
-        phase) or "lanczos" (Lanczos-3 convolution of the final model; sides
-        32-128)."""
+        phase) or "lanczos" (Lanczos-3 convolution of the final model)."""
         if shift not in ("phase", "lanczos"):
             raise ValueError(f"unknown shift {shift!r}")
         if out is None:
