@@ -12,6 +12,7 @@ Modules:
   render.py   Section 2 Steps 1-8 in the paper's order (forward model),
   lanczos.py  the Step 8 variant that does the sub-pixel shift by Lanczos
               convolution of the final model,
+  eigenpsf.py rendering with a spatially varying (eigen-)PSF (Step 2),
   adjoint.py  analytic derivatives of the forward model w.r.t.
               (flux, x, y, log r_e, e1, e2) and a central finite-difference
               check,

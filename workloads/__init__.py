@@ -16,5 +16,6 @@ from .galaxies import (  # noqa: F401
 )
 from .psf import (  # noqa: F401
     gaussian_mixture_psf, config0_psf, config2_psfs, fit_psf_mog, PsfInput,
+    EigenPsfInput, eigen_psf, eigen_positions,
 )
 from .tables import load_profile_tables, ProfileTable  # noqa: F401

@@ -145,3 +145,79 @@ def config2_psfs(n=64, seed=22, size=64, k_fit=3, fit=True):
         img = (img / img.sum()).astype(np.float32)
         out.append(PsfInput(image=img, mog=fit_psf_mog(img, k_fit) if fit else None))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Spatially varying PSFs as eigen-PSF models (Section 2, Step 2): the PSF at
+# image position (u, v) is sum_c m_c(X, Y) E_c, X = (u - u0) / su,
+# Y = (v - v0) / sv, with the monomials m_c of total degree <= D in the order
+# 1, X, Y, X^2, X Y, Y^2 and pixelized components E_c, as PSF-modelling tools
+# produce them.  The Gaussian mixture for real-space terms shares its shapes
+# across components and varies only its amplitudes the same way.
+# ---------------------------------------------------------------------------
+
+@dataclass
+class EigenPsfInput:
+    components: np.ndarray   # (K, h, w) float32, K = (D + 1)(D + 2) / 2
+    degree: int
+    norm: tuple              # (u0, v0, su, sv)
+    mog_shape: np.ndarray    # (k, 5) float64: mx, my, vxx, vxy, vyy
+    mog_amp: np.ndarray      # (K, k) float64: amplitude of each shape in each component
+
+
+def eigen_monomials(u, v, degree, norm):
+    """(K,) or (K, n) monomials 1, X, Y, X^2, X Y, Y^2 (up to ``degree``)."""
+    u0, v0, su, sv = norm
+    X = (np.asarray(u, dtype=np.float64) - u0) / su
+    Y = (np.asarray(v, dtype=np.float64) - v0) / sv
+    out = []
+    for t in range(degree + 1):
+        for j in range(t + 1):
+            out.append(X ** (t - j) * Y ** j)
+    return np.array(out)
+
+
+def varying_psf_image(X, Y, size=64):
+    """The synthetic field PSF at normalised position (X, Y) in [-1, 1]^2: a
+    0.8 / 0.2 two-Gaussian core whose width and ellipticity drift smoothly
+    across the image, sampled at pixel centres and normalised."""
+    s = 1.6 + 0.3 * X - 0.2 * Y + 0.15 * X * Y
+    e1, e2 = 0.06 * X, 0.05 * Y
+    dx, dy = _grid(size)
+    img = np.zeros((size, size))
+    for w, sc in ((0.8, 1.0), (0.2, 2.0)):
+        v = (s * sc) ** 2
+        img += w * _gauss_pix(dx, dy, v * (1 + e1), v * e2, v * (1 - e1))
+    return img / img.sum()
+
+
+def eigen_psf(degree=2, size=64, image_size=4096.0, grid=7, k_fit=3):
+    """Eigen-PSF model of ``varying_psf_image`` over an ``image_size``-pixel
+    square image: each pixel's polynomial coefficients fitted by least squares
+    to the PSF sampled on a ``grid`` x ``grid`` lattice of positions (as
+    PSF-modelling tools do with stars), and a shared-shape Gaussian mixture
+    whose amplitudes are fitted per component."""
+    h = image_size / 2.0
+    norm = (h, h, h, h)
+    g = np.linspace(-1.0, 1.0, grid)
+    XX, YY = np.meshgrid(g, g)
+    pos = np.stack([XX.ravel(), YY.ravel()], axis=1)
+    imgs = np.stack([varying_psf_image(X, Y, size).ravel() for X, Y in pos])
+    M = eigen_monomials(h + h * pos[:, 0], h + h * pos[:, 1], degree, norm).T   # (n_pos, K)
+    coef, *_ = np.linalg.lstsq(M, imgs, rcond=None)
+    comps = coef.reshape(-1, size, size)
+    # shared shapes: centred isotropic Gaussians spanning the core widths (a
+    # free fit gives nearly equal shapes and ill-conditioned amplitudes)
+    shapes = np.array([[0.0, 0.0, s * s, 0.0, s * s] for s in (1.3, 1.9, 3.6)[:k_fit]])
+    dx, dy = _grid(size)
+    G = np.stack([_gauss_pix(dx - mx, dy - my, vxx, vxy, vyy).ravel() for mx, my, vxx, vxy, vyy in shapes], axis=1)
+    amp, *_ = np.linalg.lstsq(G, comps.reshape(len(comps), -1).T, rcond=None)
+    return EigenPsfInput(components=comps.astype(np.float32), degree=degree, norm=norm,
+                         mog_shape=shapes, mog_amp=amp.T.copy())
+
+
+def eigen_positions(g, seed=24, image_size=4096.0):
+    """Image positions (u, v) of ``g`` galaxies, uniform over the image."""
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(0.0, image_size, g).astype(np.float32),
+            rng.uniform(0.0, image_size, g).astype(np.float32))
