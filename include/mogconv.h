@@ -74,6 +74,10 @@ enum { MOG_MAX_COMPONENTS = 12, MOG_MAX_PSF_COMPONENTS = 4, MOG_MAX_PSFS = 1024,
  *   psf       PSF id (mog_create_psf)
  *   size      patch side N of this galaxy (32, 64, 128 or 256)
  *   offset    element offset of this galaxy's N*N patch in the output array
+ *   img_x, img_y  position of the galaxy in its image (pixels), read only for
+ *             galaxies whose PSF is an eigen-PSF (mog_create_eigen_psf); may
+ *             be NULL when no galaxy uses one (such galaxies are then skipped
+ *             and reported as MOG_ERR_DEVICE)
  * Patches must not overlap.  The batch struct itself is host memory.
  */
 typedef struct mog_batch {
@@ -91,6 +95,8 @@ typedef struct mog_batch {
   const int64_t* offset;
   uint32_t size_mask;  /* optional, host: bit b set if some galaxy has N = 32 << b;
                           0 = unknown (every size's kernel is launched) */
+  const float* img_x;
+  const float* img_y;
 } mog_batch;
 
 /* Creates a context on CUDA device `device` (makes it current).  *out gets
@@ -131,6 +137,27 @@ mog_status mog_create_psf(mog_ctx* ctx, const float* pixels, int h, int w, const
 mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id);
 
 /*
+ * Registers a spatially varying PSF given as an eigen-PSF model (Section 2,
+ * Step 2): at image position (u, v) the pixelized PSF is sum_c m_c E_c, with
+ * X = (u - norm[0]) / norm[2], Y = (v - norm[1]) / norm[3] and m_c the
+ * polynomial terms of total degree <= `degree` (0..2) in the order 1, X, Y,
+ * X^2, X Y, Y^2; K = (degree + 1)(degree + 2) / 2 components.  Host arrays:
+ *   components[K * h * w]  the pixelized E_c, row-major, centre at (h/2, w/2)
+ *   norm[4]                u0, v0, su, sv (su, sv != 0)
+ *   mog_shape[k * 5]       shapes shared by the components' Gaussian
+ *                          mixtures: (mean_x, mean_y, var_xx, var_xy, var_yy)
+ *   mog_amp[K * k]         amplitude of shape j in component c at [c * k + j]
+ * (1 <= k <= 4).  The FFT of every component is computed once for every N
+ * and kept resident; a render forms sum_c m_c FFT(E_c) for each galaxy from
+ * its img_x, img_y, and the real-space mixture with amplitudes
+ * sum_c m_c A[c, j].  *psf_id receives an id used like mog_create_psf's.
+ * Synchronous.  Freed by mog_destroy_psf.
+ */
+mog_status mog_create_eigen_psf(mog_ctx* ctx, const float* components, int K, int h, int w, int degree,
+                                const float* norm, const float* mog_shape, const float* mog_amp, int k,
+                                int* psf_id);
+
+/*
  * Renders every galaxy of the batch (Section 2, Steps 3-8) into `out`
  * (device float32; galaxy g writes size[g]^2 values at out + offset[g]).
  * Asynchronous on `stream`.
@@ -167,6 +194,8 @@ mog_status mog_render_batch_lanczos(mog_ctx* ctx, const mog_batch* batch, float*
  * the GPU (different streams, or different contexts on the same device) race
  * and corrupt each other's output; serialise them.  The context, its tables
  * and PSFs must have been created beforehand (those calls allocate).
+ * Galaxies whose PSF is an eigen-PSF are skipped and reported as
+ * MOG_ERR_DEVICE (their per-galaxy PSF terms have no place in the array).
  */
 mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
 
@@ -181,7 +210,8 @@ mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float*
  * the real-space part differentiates the Gaussian terms in pixel space; the
  * aliasing ramp weights are differentiated too.  S(e1, e2) is not
  * differentiable at e = 0; there the direction e1/e = 1 is used.
- * Asynchronous on `stream`.
+ * Constant PSFs only: galaxies whose PSF is an eigen-PSF are skipped and
+ * reported as MOG_ERR_DEVICE.  Asynchronous on `stream`.
  */
 mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out,
                                float* grad_params, void* stream);

@@ -35,6 +35,7 @@ EXPORTED = (
     "mog_autotune", "mog_graph_capture", "mog_graph_launch", "mog_graph_destroy",
     "mog_server_create", "mog_server_add_fit", "mog_server_submit", "mog_server_wait", "mog_server_replay",
     "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
+    "mog_create_eigen_psf",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -53,6 +54,7 @@ class mog_batch(ctypes.Structure):
         ("sersic_n", ctypes.c_void_p), ("profile", ctypes.c_void_p), ("psf", ctypes.c_void_p),
         ("size", ctypes.c_void_p), ("offset", ctypes.c_void_p),
         ("size_mask", ctypes.c_uint32),
+        ("img_x", ctypes.c_void_p), ("img_y", ctypes.c_void_p),
     ]
 
 
@@ -83,6 +85,7 @@ def _load():
         "mog_last_error": ([VP], ctypes.c_char_p),
         "mog_set_profile_table": ([VP, I, I, FP, FP, FP], I),
         "mog_create_psf": ([VP, FP, I, I, FP, I, P(I)], I),
+        "mog_create_eigen_psf": ([VP, FP, I, I, I, I, FP, FP, FP, I, P(I)], I),
         "mog_destroy_psf": ([VP, I], I),
         "mog_render_batch": ([VP, P(mog_batch), VP, VP], I),
         "mog_render_batch_lanczos": ([VP, P(mog_batch), VP, VP], I),
@@ -162,6 +165,20 @@ def mog_create_psf(ctx, pixels, mog):
     return out.value
 
 
+def mog_create_eigen_psf(ctx, components, degree, norm, mog_shape, mog_amp):
+    comps = np.ascontiguousarray(components, dtype=np.float32)
+    K, h, w = comps.shape
+    norm = np.ascontiguousarray(norm, dtype=np.float32)
+    shape = np.ascontiguousarray(mog_shape, dtype=np.float32)
+    amp = np.ascontiguousarray(mog_amp, dtype=np.float32)
+    k = shape.shape[0]
+    assert norm.shape == (4,) and shape.shape == (k, 5) and amp.shape == (K, k)
+    out = ctypes.c_int(-1)
+    _check(ctx, _lib.mog_create_eigen_psf(ctx, _fptr(comps), K, h, w, int(degree), _fptr(norm), _fptr(shape),
+                                          _fptr(amp), k, ctypes.byref(out)))
+    return out.value
+
+
 def mog_destroy_psf(ctx, psf_id):
     _check(ctx, _lib.mog_destroy_psf(ctx, int(psf_id)))
 
@@ -171,8 +188,9 @@ def make_batch(count, ptrs, size_mask=0):
     ``size_mask``: optional bitmask of the patch sides present."""
     b = mog_batch()
     b.count = int(count)
-    for f, _ in mog_batch._fields_[1:-1]:
-        setattr(b, f, ctypes.c_void_p(int(ptrs[f])))
+    for f, kind in mog_batch._fields_[1:]:
+        if kind is ctypes.c_void_p:
+            setattr(b, f, ctypes.c_void_p(int(ptrs[f])) if ptrs.get(f) is not None else None)
     b.size_mask = int(size_mask)
     return b
 

@@ -58,6 +58,7 @@ void workspace_free(Workspace* ws) {
   cudaFree(ws->records);
   cudaFree(ws->adj_records);
   cudaFree(ws->lzw);
+  cudaFree(ws->pcoef);
   cudaFree(ws->bwd256);
   for (int b = 0; b < NBUCKET; ++b) {
     if (ws->side[b]) cudaStreamDestroy(ws->side[b]);
@@ -72,8 +73,8 @@ void workspace_free(Workspace* ws) {
 namespace {
 
 BatchView view_of(const mog_batch* b) {
-  return BatchView{b->flux, b->x,      b->y,    b->log_re, b->e1,  b->e2,
-                   b->sersic_n, b->profile, b->psf, b->size, b->offset};
+  return BatchView{b->flux,    b->x,       b->y,   b->log_re, b->e1,     b->e2,   b->sersic_n,
+                   b->profile, b->psf,     b->size, b->offset, b->img_x, b->img_y};
 }
 
 cudaError_t take_event(mog_ctx* ctx, cudaEvent_t* ev) {
@@ -93,15 +94,18 @@ mog_status ensure_capacity(mog_ctx* ctx, Workspace* ws, int64_t count) {
   if (ws->records) MOG_CUDA(ctx, cudaFree(ws->records));
   if (ws->adj_records) MOG_CUDA(ctx, cudaFree(ws->adj_records));
   if (ws->lzw) MOG_CUDA(ctx, cudaFree(ws->lzw));
+  if (ws->pcoef) MOG_CUDA(ctx, cudaFree(ws->pcoef));
   ws->plan.order = nullptr;
   ws->records = nullptr;
   ws->adj_records = nullptr;
   ws->lzw = nullptr;
+  ws->pcoef = nullptr;
   ws->cap = 0;
   MOG_CUDA(ctx, cudaMalloc(&ws->plan.order, sizeof(int32_t) * cap));
   MOG_CUDA(ctx, cudaMalloc(&ws->records, (size_t)RECORD_BYTES * cap));
   MOG_CUDA(ctx, cudaMalloc(&ws->adj_records, sizeof(AdjRecord) * cap));
   MOG_CUDA(ctx, cudaMalloc(&ws->lzw, sizeof(float) * 16 * cap));
+  MOG_CUDA(ctx, cudaMalloc(&ws->pcoef, sizeof(float) * PCOEF * cap));
   ws->cap = cap;
   return MOG_OK;
 }
@@ -240,6 +244,69 @@ mog_status mog_create_psf(mog_ctx* ctx, const float* pixels, int h, int w, const
   return MOG_OK;
 }
 
+mog_status mog_create_eigen_psf(mog_ctx* ctx, const float* components, int K, int h, int w, int degree,
+                                const float* norm, const float* mog_shape, const float* mog_amp, int k,
+                                int* psf_id) {
+  if (!ctx) return MOG_ERR_ARG;
+  if (!components || !norm || !mog_shape || !mog_amp || !psf_id || h < 1 || w < 1 || h > 4096 || w > 4096)
+    return fail(ctx, MOG_ERR_ARG, "bad eigen-PSF arguments");
+  if (degree < 0 || degree > 2 || K != (degree + 1) * (degree + 2) / 2)
+    return fail(ctx, MOG_ERR_ARG, "eigen-PSF needs degree 0..2 and K = (degree+1)(degree+2)/2 components");
+  if (k < 1 || k > KPSF) return fail(ctx, MOG_ERR_ARG, "PSF mixture needs 1..%d components", KPSF);
+  if (!(norm[2] != 0.0f) || !(norm[3] != 0.0f)) return fail(ctx, MOG_ERR_ARG, "eigen-PSF scales must be non-zero");
+  int id = -1;
+  for (int i = 0; i < MOG_MAX_PSFS; ++i)
+    if (ctx->h_psfs[i].k == 0) {
+      id = i;
+      break;
+    }
+  if (id < 0) return fail(ctx, MOG_ERR_STATE, "all %d PSF slots are in use", MOG_MAX_PSFS);
+  DevPsf rec{};
+  rec.k = k;
+  rec.k_eig = K;
+  rec.degree = degree;
+  for (int i = 0; i < 4; ++i) rec.norm[i] = norm[i];
+  for (int j = 0; j < k; ++j) {
+    const float* m = mog_shape + 5 * j;
+    const double det = (double)m[2] * m[4] - (double)m[3] * m[3];
+    if (!(m[2] > 0) || !(m[4] > 0) || !(det > 0)) return fail(ctx, MOG_ERR_ARG, "PSF shape %d covariance not positive", j);
+    rec.mog[j][0] = 0.0f;
+    for (int c = 0; c < 5; ++c) rec.mog[j][1 + c] = m[c];
+    for (int c = 0; c < K; ++c) rec.amp[c][j] = mog_amp[c * k + j];
+  }
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  size_t total = 0;
+  size_t offs[NBUCKET];
+  for (int b = 0; b < NBUCKET; ++b) {
+    offs[b] = total;
+    total += (size_t)K * psf_spec_elems(bucket_side(b));
+  }
+  float2* mem = nullptr;
+  MOG_CUDA(ctx, cudaMalloc(&mem, sizeof(float2) * total));
+  float* dpix = nullptr;
+  cudaError_t e = cudaMalloc(&dpix, sizeof(float) * (size_t)K * h * w);
+  if (e == cudaSuccess) e = cudaMemcpy(dpix, components, sizeof(float) * (size_t)K * h * w, cudaMemcpyHostToDevice);
+  for (int b = 0; b < NBUCKET && e == cudaSuccess; ++b) {
+    rec.spec[b] = mem + offs[b];
+    const size_t elems = psf_spec_elems(bucket_side(b));
+    for (int c = 0; c < K && e == cudaSuccess; ++c)
+      e = launch_psf_spectrum(dpix + (size_t)c * h * w, h, w, bucket_side(b), ctx->d_dft_scratch,
+                              mem + offs[b] + c * elems, 0);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(dpix);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->d_psfs + id, &rec, sizeof(rec), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    return cuda_fail(ctx, e, "eigen-PSF spectra");
+  }
+  ctx->h_psfs[id] = rec;
+  ctx->psf_mem[id] = mem;
+  ctx->eigen_psfs += 1;
+  *psf_id = id;
+  return MOG_OK;
+}
+
 mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id) {
   if (!ctx) return MOG_ERR_ARG;
   if (psf_id < 0 || psf_id >= MOG_MAX_PSFS || ctx->h_psfs[psf_id].k == 0)
@@ -250,6 +317,7 @@ mog_status mog_destroy_psf(mog_ctx* ctx, int psf_id) {
   MOG_CUDA(ctx, cudaMemcpy(ctx->d_psfs + psf_id, &empty, sizeof(empty), cudaMemcpyHostToDevice));
   cudaFree(ctx->psf_mem[psf_id]);
   ctx->psf_mem[psf_id] = nullptr;
+  if (ctx->h_psfs[psf_id].k_eig > 0) ctx->eigen_psfs -= 1;
   ctx->h_psfs[psf_id] = empty;
   return MOG_OK;
 }
@@ -289,6 +357,8 @@ mog_status plan_batch(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float
   p->bucket_count = ws->plan.small + NBUCKET;
   p->queue = ws->plan.small + 2 * NBUCKET;
   p->status = ctx->d_status;
+  p->pcoef = ws->pcoef;
+  p->eigen = ctx->eigen_psfs > 0 ? 1 : 0;
   return MOG_OK;
 }
 

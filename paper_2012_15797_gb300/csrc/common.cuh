@@ -36,11 +36,31 @@ struct DevProfile {
   float logv[MOG_MAX_NODES][KMAX];
 };
 
+constexpr int KEIG = 6;   // eigen-PSF components (polynomial degree <= 2)
+
 struct DevPsf {
   const float2* spec[NBUCKET];  // spectrum of the PSF embedded at (N/2, N/2), psf_lstride layout
   int k;                        // mixture components; 0 = no PSF in this slot
   float mog[KPSF][6];           // weight, mean x, mean y, vxx, vxy, vyy
+  // eigen-PSF (k_eig > 0): spec[b] holds k_eig component spectra back to back
+  // (psf_spec_elems(N) each); the mixture weight of shape j at (u, v) is
+  // sum_c m_c amp[c][j] (mog[j][0] unused)
+  int k_eig, degree;
+  float norm[4];                // u0, v0, su, sv
+  float amp[KEIG][KPSF];
 };
+
+// Polynomial terms 1, X, Y, X^2, X Y, Y^2 of an eigen-PSF at image position
+// (u, v); the first k_eig = (degree + 1)(degree + 2) / 2 are used.
+__device__ __forceinline__ void eigen_terms(const DevPsf& ps, float u, float v, float (&m)[KEIG]) {
+  const float X = (u - ps.norm[0]) / ps.norm[2], Y = (v - ps.norm[1]) / ps.norm[3];
+  m[0] = 1.0f;
+  m[1] = X;
+  m[2] = Y;
+  m[3] = X * X;
+  m[4] = X * Y;
+  m[5] = Y * Y;
+}
 
 // Status word: the first device-detected error wins.
 __device__ __forceinline__ void set_status(int* status, int code) {
@@ -310,7 +330,43 @@ struct BatchView {
   const float *flux, *x, *y, *log_re, *e1, *e2, *sersic_n;
   const int32_t *profile, *psf, *size;
   const int64_t* offset;
+  const float *img_x, *img_y;   // may be null (needed for eigen-PSFs only)
 };
+
+// Per planned position: eigen-PSF polynomial terms [0, 6) and the mixture
+// weights at the galaxy's position [8, 12) (written by the record prologue).
+constexpr int PCOEF = 16;
+
+// Spectrum bin e of the PSF at a galaxy's position: sum_c m_c S_c[e] over
+// the k_eig component spectra of `elems` bins each.
+__device__ __forceinline__ float2 eigen_bin(const float2* spec, int elems, int k_eig, const float* m, int e) {
+  float2 acc = make_float2(0.0f, 0.0f);
+  for (int c = 0; c < k_eig; ++c) {
+    const float2 s = __ldg(spec + (size_t)c * elems + e);
+    acc.x = fmaf(m[c], s.x, acc.x);
+    acc.y = fmaf(m[c], s.y, acc.y);
+  }
+  return acc;
+}
+
+// One warp: the eigen-PSF terms of galaxy g at planned position `pos`.
+__device__ __forceinline__ void eigen_coefficients_warp(const BatchView& b, int64_t g, const DevPsf* psfs,
+                                                        float* pcoef, int pos) {
+  const int lane = threadIdx.x & 31;
+  const int pid = b.psf[g];
+  if (pid < 0 || pid >= MOG_MAX_PSFS) return;
+  const DevPsf& ps = psfs[pid];
+  if (ps.k_eig == 0 || !b.img_x || !b.img_y) return;
+  float m[KEIG];
+  eigen_terms(ps, b.img_x[g], b.img_y[g], m);
+  float* out = pcoef + (size_t)pos * PCOEF;
+  if (lane < KEIG) out[lane] = lane < ps.k_eig ? m[lane] : 0.0f;
+  if (lane < KPSF) {
+    float w = 0.0f;
+    for (int c = 0; c < ps.k_eig; ++c) w = fmaf(m[c], ps.amp[c][lane], w);
+    out[8 + lane] = w;
+  }
+}
 
 __device__ __forceinline__ float ramp_weight(float ns) {
   float t = fminf(fmaxf(ns - 3.0f, 0.0f), 1.0f);
@@ -319,9 +375,12 @@ __device__ __forceinline__ float ramp_weight(float ns) {
 
 // Executed by one full warp (lane = mixture component); writes *out.
 // With `lanczos` the offset is split into an integer part, rendered exactly,
-// and a fraction in [-1/2, 1/2) left to the Lanczos shift.
+// and a fraction in [-1/2, 1/2) left to the Lanczos shift.  `eigen_ok`: the
+// caller has per-position storage for eigen-PSF terms (else such galaxies
+// are rejected).
 __device__ inline void galaxy_record_warp(const BatchView& b, int64_t g, int n, const DevProfile* profiles,
-                                          const DevPsf* psfs, int* status, bool lanczos, GalaxyRecord* out) {
+                                          const DevPsf* psfs, int* status, bool lanczos, bool eigen_ok,
+                                          GalaxyRecord* out) {
   const int lane = threadIdx.x & 31;
   const float flux = b.flux[g], x = b.x[g], y = b.y[g], lre = b.log_re[g];
   const float e1 = b.e1[g], e2 = b.e2[g], sn = b.sersic_n[g];
@@ -332,6 +391,8 @@ __device__ inline void galaxy_record_warp(const BatchView& b, int64_t g, int n, 
   ok = ok && prof >= 0 && prof < MOG_MAX_PROFILES && pid >= 0 && pid < MOG_MAX_PSFS;
   const DevProfile* P = ok ? &profiles[prof] : nullptr;
   ok = ok && P->n_nodes > 0 && psfs[pid].k > 0;
+  ok = ok && (psfs[pid].k_eig == 0 ||
+              (eigen_ok && b.img_x && b.img_y && isfinite(b.img_x[g]) && isfinite(b.img_y[g])));
   const int64_t off = b.offset[g];
   ok = ok && (off & 3) == 0;   // patches are stored as aligned float4 rows
   if (!ok) {
@@ -506,6 +567,7 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
   ok = ok && prof >= 0 && prof < MOG_MAX_PROFILES && pid >= 0 && pid < MOG_MAX_PSFS;
   const DevProfile* P = ok ? &profiles[prof] : nullptr;
   ok = ok && P->n_nodes > 0 && psfs[pid].k > 0;
+  ok = ok && psfs[pid].k_eig == 0;   // the adjoint takes constant PSFs only
   const int64_t off = b.offset[g];
   ok = ok && (off & 3) == 0;
   if (!ok) {
@@ -592,15 +654,18 @@ struct RealTerms {
 
 // Term t = c * kpsf + j, computed by one thread.  psf_mog rows are
 // (weight, mean x, mean y, vxx, vxy, vyy).
-__device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*psf_mog)[6], int kpsf, int n, int t,
-                                          RealTerms* rt) {
+// eig_w: mixture weights at the galaxy's position for an eigen-PSF (null for
+// a constant PSF, whose weights are psf_mog[j][0]).
+__device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*psf_mog)[6], const float* eig_w,
+                                          int kpsf, int n, int t, RealTerms* rt) {
   const int c = t / kpsf, jj = t - c * kpsf;
   const float* m = psf_mog[jj];
+  const float wj = eig_w ? eig_w[jj] : m[0];
   const float v = r.rvar[c];
   const float vxx = v * r.s11 + m[3], vxy = v * r.s12 + m[4], vyy = v * r.s22 + m[5];
   const float det = vxx * vyy - vxy * vxy;
   const float idet = 1.0f / det;
-  rt->rw[t] = r.ramp[c] * m[0] * rsqrtf(det) * (0.5f / PI_F);
+  rt->rw[t] = r.ramp[c] * wj * rsqrtf(det) * (0.5f / PI_F);
   rt->rqa[t] = -0.5f * LOG2E * vyy * idet;
   rt->rrr[t] = ex2(-LOG2E * vyy * idet);
   rt->rqb[t] = LOG2E * vxy * idet;

@@ -19,6 +19,7 @@ struct Workspace {
   unsigned char* records = nullptr;      // RECORD_BYTES per planned galaxy
   unsigned char* adj_records = nullptr;  // sizeof(AdjRecord) per planned galaxy
   float* lzw = nullptr;                  // 16 floats per planned galaxy (Lanczos weights)
+  float* pcoef = nullptr;                // PCOEF floats per planned galaxy (eigen-PSF terms)
   float2* bwd256 = nullptr;              // per-CTA scratch of the 256 x 256 adjoint
   cudaStream_t side[NBUCKET] = {};
   cudaEvent_t fork_ev = nullptr;
@@ -37,6 +38,7 @@ struct mog_ctx {
   mog::DevPsf* d_psfs = nullptr;
   std::vector<mog::DevPsf> h_psfs;
   std::vector<float2*> psf_mem;  // one allocation per PSF holding every bucket's spectrum
+  int eigen_psfs = 0;            // registered eigen-PSFs (the kernels that handle them are launched only then)
   int* d_status = nullptr;
   double2* d_dft_scratch = nullptr;
   mog::Workspace ws;             // the workspace of the plain entry points

@@ -23,6 +23,8 @@ struct RenderParams {
   int chunk;                    // queue positions taken per request
   int lanczos = 0;              // 1: sub-pixel shift by Lanczos convolution
   float* lzw = nullptr;         // lanczos: 16 floats per planned position, weights along x [0, 7), y [8, 15)
+  float* pcoef = nullptr;       // PCOEF floats per planned position (eigen-PSF terms and mixture weights)
+  int eigen = 0;                // 1: some PSF of the context is an eigen-PSF (launch the kernels that handle it)
 };
 
 // Launch shape of one size bucket: CTAs per SM (clamped to what fits) and

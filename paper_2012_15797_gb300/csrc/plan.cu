@@ -99,8 +99,9 @@ __global__ void galaxy_prep(RenderParams p, unsigned char* records) {
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int pos = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pos < total; pos += warps) {
     const int64_t g = p.order[pos];
-    galaxy_record_warp(p.b, g, p.b.size[g], p.profiles, p.psfs, p.status, p.lanczos != 0,
+    galaxy_record_warp(p.b, g, p.b.size[g], p.profiles, p.psfs, p.status, p.lanczos != 0, p.pcoef != nullptr,
                        reinterpret_cast<GalaxyRecord*>(records + (size_t)pos * RECORD_BYTES));
+    if (p.pcoef) eigen_coefficients_warp(p.b, g, p.psfs, p.pcoef, pos);
     if (p.lanczos) {
       // Lanczos weights once per galaxy: lanes 0-6 along x, 8-14 along y
       const int lane = threadIdx.x & 31;

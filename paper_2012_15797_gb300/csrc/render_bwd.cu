@@ -382,6 +382,7 @@ __global__ void adjoint_prep(RenderParams p, unsigned char* records) {
     const int64_t g = p.order[pos];
     adjoint_record_warp(p.b, g, p.b.size[g], p.profiles, p.psfs, p.status,
                         reinterpret_cast<AdjRecord*>(records + (size_t)pos * sizeof(AdjRecord)));
+    if (p.pcoef) eigen_coefficients_warp(p.b, g, p.psfs, p.pcoef, pos);
   }
 }
 

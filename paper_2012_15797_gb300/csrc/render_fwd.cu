@@ -188,7 +188,9 @@ __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, 
 // the multiplication of its spectrum by H(nu) H(omega), folded into the
 // shift-phase tables; the real-space part, when a galaxy has one, is
 // convolved in shared memory along x, then y, before it is added.
-template <int N, bool LZ>
+// EIG: some PSF of the context is an eigen-PSF (the variant without it has
+// none of that code).
+template <int N, bool LZ, bool EIG>
 __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     render_fwd_kernel(RenderParams p) {
   using C = FwdCfg<N>;
@@ -220,7 +222,8 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   fill_twiddles<N, C::R1>(tw1, 8, tid, C::THREADS);
   if constexpr (Radix<N>::P == 3) fill_twiddles<N, C::R2>(tw2, N / C::R2, tid, C::THREADS);
   const int count = p.bucket_count[B];
-  const unsigned char* records = p.records + (size_t)p.bucket_start[B] * RECORD_BYTES;
+  const int first = p.bucket_start[B];   // planned position of this bucket's first galaxy
+  const unsigned char* records = p.records + (size_t)first * RECORD_BYTES;
   // work queue, used by thread 0 only: positions are taken p.chunk at a time and
   // the next chunk is requested one chunk ahead, so the atomic's latency is
   // off the critical path
@@ -271,7 +274,16 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     const GalaxyRecord& r = rec[buf];
     const bool need_psf = rec_landed && r.ok && r.psf != cur_psf;
     bool psf_landed = true;
-    if (need_psf) {   // uniform: every thread reads the same record
+    // eigen-PSF: the spectrum at the galaxy's position, sum_c m_c S_c, is
+    // formed in shared memory by every thread (read after S2); the set-up
+    // tasks below take the bins they need straight from the components
+    const float* pc = p.pcoef + ((size_t)first + pos) * PCOEF;
+    const bool eig = EIG && need_psf && p.psfs[r.psf].k_eig > 0;
+    if (eig) {
+      const DevPsf& ps = p.psfs[r.psf];
+      for (int e = tid; e < C::PSF_ELEMS; e += C::THREADS) psf_hat[e] = eigen_bin(ps.spec[B], C::PSF_ELEMS, ps.k_eig, pc, e);
+      cur_psf = -1;   // the next galaxy forms its own
+    } else if (need_psf) {   // uniform: every thread reads the same record
       if (tid == 0) bulk_load(psf_hat, p.psfs[r.psf].spec[B], sizeof(float2) * C::PSF_ELEMS, &bar[0]);
       psf_landed = mbar_wait(&bar[0], psf_parity);
       psf_parity ^= 1u;
@@ -285,7 +297,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     // (needed at +omega and -omega by the packed transform) and the
     // real-space terms, spread over the CTA as one task list
     if (work) {
-      const DevPsf& ps = p.psfs[cur_psf];
+      const DevPsf& ps = p.psfs[r.psf];
       const int kp = ps.k, nrt = r.nrc * kp, nr2 = real_terms_padded(nrt);
       // what the store needs of the record is copied out: the record buffer
       // is refilled while slower warps may still be storing
@@ -294,7 +306,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
         s_nr[buf] = nr2;
       }
       const float gx = r.x, gy = r.y;
-      const float* lzw = LZ ? p.lzw + ((size_t)p.bucket_start[B] + pos) * 16 : nullptr;
+      const float* lzw = LZ ? p.lzw + ((size_t)first + pos) * 16 : nullptr;
       const int t0 = C::H + 2 * N, ntask = t0 + nr2 + r.nf;
       for (int i = tid; i < ntask; i += C::THREADS) {
         float sn, cs;
@@ -341,10 +353,12 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
             load_weights(lzw, 8, w);
             phy = cmul(phy, lanczos_response(w, om));
           }
-          nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(phx, phy)), acc);
+          const float2 pn = eig ? eigen_bin(ps.spec[B], C::PSF_ELEMS, ps.k_eig, pc, (N / 2) * LS + l)
+                                : psf_hat[(N / 2) * LS + l];
+          nyq[l] = cscale(cmul(pn, cmul(phx, phy)), acc);
         } else {
           const int t = i - t0;
-          if (t < nrt) real_term(r, ps.mog, kp, N, t, &rt);
+          if (t < nrt) real_term(r, ps.mog, eig ? pc + 8 : nullptr, kp, N, t, &rt);
           else if (t < nr2) real_term_zero(t, &rt);
           else s_fc[t - nr2] = make_float4(r.famp[t - nr2], r.famp[t - nr2], r.fcoef[t - nr2], r.fcoef[t - nr2]);
         }
@@ -498,14 +512,15 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
   }
 }
 
-template <int N, bool LZ = false>
+template <int N, bool LZ = false, bool EIG = false>
 static int fwd_occupancy() {
   using C = FwdCfg<N>;
   static int occ = -1;
   if (occ < 0) {
-    if (cudaFuncSetAttribute(render_fwd_kernel<N, LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
+    if (cudaFuncSetAttribute(render_fwd_kernel<N, LZ, EIG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)C::SMEM) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fwd_kernel<N, LZ>, C::THREADS, C::SMEM) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fwd_kernel<N, LZ, EIG>, C::THREADS, C::SMEM) !=
             cudaSuccess)
       return -1;
     if (occ < 1) occ = 1;
@@ -513,20 +528,23 @@ static int fwd_occupancy() {
   return occ;
 }
 
-template <int N, bool LZ>
+template <int N, bool LZ, bool EIG>
 static cudaError_t launch_fwd_mode(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
   using C = FwdCfg<N>;
-  const int occ = fwd_occupancy<N, LZ>();
+  const int occ = fwd_occupancy<N, LZ, EIG>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_fwd_kernel<N, LZ><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
+  render_fwd_kernel<N, LZ, EIG><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
-  return p.lanczos ? launch_fwd_mode<N, true>(p, num_sms, ctas_per_sm, s)
-                   : launch_fwd_mode<N, false>(p, num_sms, ctas_per_sm, s);
+  if (p.eigen)
+    return p.lanczos ? launch_fwd_mode<N, true, true>(p, num_sms, ctas_per_sm, s)
+                     : launch_fwd_mode<N, false, true>(p, num_sms, ctas_per_sm, s);
+  return p.lanczos ? launch_fwd_mode<N, true, false>(p, num_sms, ctas_per_sm, s)
+                   : launch_fwd_mode<N, false, false>(p, num_sms, ctas_per_sm, s);
 }
 
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {

@@ -35,6 +35,7 @@ constexpr int THREADS = 1024;
 constexpr int WARPS = THREADS / 32;
 constexpr int ROUNDS = (N / 2) / WARPS;   // 4
 constexpr int LS = psf_lstride(N);
+constexpr int PSF_ELEMS = psf_spec_elems(N);
 constexpr int WS = wstride<N>();
 constexpr int R1 = Radix<N>::r[1], R2 = Radix<N>::r[2];
 constexpr int TW1 = twiddle_elems<N, R1>(), TW2 = twiddle_elems<N, R2>();
@@ -122,7 +123,7 @@ __device__ __forceinline__ void lanczos_real_256(const RealTerms& rt, int nr, co
   }
 }
 
-template <bool LZ>
+template <bool LZ, bool EIG>
 __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams p) {
   constexpr float INV_N = 1.0f / N;
   constexpr float NEGLIGIBLE_LOG2 = -40.0f;
@@ -142,13 +143,15 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
   __shared__ float s_psf_mog[KPSF][6];
   __shared__ int s_kpsf;
   __shared__ float s_lzw[16];   // LZ: Lanczos weights along x [0, 7) and y [8, 15)
+  __shared__ float s_eigm[KEIG];  // eigen-PSF terms of the current galaxy
 
   const int tid = threadIdx.x;
   const int f = tid >> 5, j = tid & 31;   // warp = transform slot, lane = thread in it
   fill_twiddles<N, R1>(tw1, 8, tid, THREADS);
   fill_twiddles<N, R2>(tw2, N / R2, tid, THREADS);
   const int count = p.bucket_count[B];
-  const unsigned char* records = p.records + (size_t)p.bucket_start[B] * RECORD_BYTES;
+  const int first = p.bucket_start[B];   // planned position of this bucket's first galaxy
+  const unsigned char* records = p.records + (size_t)first * RECORD_BYTES;
   int q_next = 0, q_end = 0, q_ahead = 0;
   auto next_position = [&]() -> int {
     if (q_next >= q_end) {
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
     s_pos[0] = p0;
     if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * RECORD_BYTES, sizeof(GalaxyRecord), &bar[0]);
   }
-  int cur_psf = -1;
+  int cur_psf = -1, k_eig = 0;
   const float2* psf_hat = nullptr;
   uint32_t rec_parity = 0;
   float2* w = W + f * WS;   // this warp's transform row
@@ -187,10 +190,17 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
     rec_parity ^= 1u << buf;
     const GalaxyRecord& r = rec[buf];
     if (landed && r.ok && r.psf != cur_psf) {
-      if (tid < KPSF * 6) s_psf_mog[tid / 6][tid % 6] = p.psfs[r.psf].mog[tid / 6][tid % 6];
-      if (tid == 0) s_kpsf = p.psfs[r.psf].k;
-      psf_hat = p.psfs[r.psf].spec[B];
-      cur_psf = r.psf;
+      // eigen-PSF: the spectrum at the galaxy's position is sum_c m_c S_c,
+      // formed bin by bin where it is read; mixture weights at that position
+      const DevPsf& ps = p.psfs[r.psf];
+      const float* pc = p.pcoef + ((size_t)first + pos) * PCOEF;
+      k_eig = EIG ? ps.k_eig : 0;
+      if (tid < KPSF * 6)
+        s_psf_mog[tid / 6][tid % 6] = (k_eig > 0 && tid % 6 == 0) ? pc[8 + tid / 6] : ps.mog[tid / 6][tid % 6];
+      if (tid < KEIG) s_eigm[tid] = k_eig > 0 ? pc[tid] : 0.0f;   // pcoef is only read for eigen-PSFs
+      if (tid == 0) s_kpsf = ps.k;
+      psf_hat = ps.spec[B];
+      cur_psf = k_eig > 0 ? -1 : r.psf;
     }
     if (__syncthreads_or(!landed)) {
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
@@ -203,7 +213,7 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
     // per-galaxy tables
     {
       const float gx = r.x, gy = r.y;
-      const float* lzw = LZ ? p.lzw + ((size_t)p.bucket_start[B] + pos) * 16 : nullptr;
+      const float* lzw = LZ ? p.lzw + ((size_t)first + pos) * 16 : nullptr;
       const int kp = s_kpsf;
       const int nrt = r.nrc * kp, ntask = H + 2 * N + real_terms_padded(nrt);
       for (int i = tid; i < ntask; i += THREADS) {
@@ -251,10 +261,12 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
             load_weights(lzw, 8, wv);
             phy = cmul(phy, lanczos_response(wv, om));
           }
-          nyq[l] = cscale(cmul(psf_hat[(N / 2) * LS + l], cmul(phx, phy)), acc);
+          const float2 pn = k_eig ? eigen_bin(psf_hat, PSF_ELEMS, k_eig, s_eigm, (N / 2) * LS + l)
+                                  : psf_hat[(N / 2) * LS + l];
+          nyq[l] = cscale(cmul(pn, cmul(phx, phy)), acc);
         } else {
           const int t = i - H - 2 * N;
-          if (t < nrt) real_term(r, s_psf_mog, kp, N, t, &rt);
+          if (t < nrt) real_term(r, s_psf_mog, nullptr, kp, N, t, &rt);
           else real_term_zero(t, &rt);
         }
       }
@@ -290,7 +302,8 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
           const int l = j + m * TPF;
-          v[m] = cscale(cmul(__ldg(&psf_hat[k * LS + l]), cmul(pxk, py[l])), s[m]);
+          const float2 pv = k_eig ? eigen_bin(psf_hat, PSF_ELEMS, k_eig, s_eigm, k * LS + l) : __ldg(&psf_hat[k * LS + l]);
+          v[m] = cscale(cmul(pv, cmul(pxk, py[l])), s[m]);
         }
         if (k == 0) {
 #pragma unroll
@@ -407,21 +420,22 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
 
 }  // namespace
 
-template <bool LZ>
+template <bool LZ, bool EIG>
 static cudaError_t launch_fwd256(const RenderParams& p, int num_sms, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
     cudaError_t e =
-        cudaFuncSetAttribute(render_fwd256_kernel<LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        cudaFuncSetAttribute(render_fwd256_kernel<LZ, EIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  render_fwd256_kernel<LZ><<<num_sms, THREADS, SMEM, s>>>(p);
+  render_fwd256_kernel<LZ, EIG><<<num_sms, THREADS, SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, cudaStream_t s) {
-  return p.lanczos ? launch_fwd256<true>(p, num_sms, s) : launch_fwd256<false>(p, num_sms, s);
+  if (p.eigen) return p.lanczos ? launch_fwd256<true, true>(p, num_sms, s) : launch_fwd256<false, true>(p, num_sms, s);
+  return p.lanczos ? launch_fwd256<true, false>(p, num_sms, s) : launch_fwd256<false, false>(p, num_sms, s);
 }
 
 }  // namespace mog

@@ -44,8 +44,10 @@ def pack_offsets(sizes):
     return off, int(area.sum())
 
 
-def host_batch(gals, pin=False):
-    """Host tensors (optionally pinned) of a ``workloads.Galaxies`` batch."""
+def host_batch(gals, pin=False, positions=None):
+    """Host tensors (optionally pinned) of a ``workloads.Galaxies`` batch;
+    ``positions`` = (img_x, img_y) image positions, needed by galaxies whose
+    PSF is an eigen-PSF."""
     t = {}
     for f in FLOAT_FIELDS:
         t[f] = torch.from_numpy(np.ascontiguousarray(getattr(gals, f), dtype=np.float32))
@@ -53,13 +55,16 @@ def host_batch(gals, pin=False):
         t[f] = torch.from_numpy(np.ascontiguousarray(getattr(gals, f), dtype=np.int32))
     off, total = pack_offsets(gals.size)
     t["offset"] = torch.from_numpy(off)
+    if positions is not None:
+        t["img_x"] = torch.from_numpy(np.ascontiguousarray(positions[0], dtype=np.float32))
+        t["img_y"] = torch.from_numpy(np.ascontiguousarray(positions[1], dtype=np.float32))
     if pin:
         t = {k: v.pin_memory() for k, v in t.items()}
     return t, total
 
 
-def to_device(gals, device="cuda"):
-    t, total = host_batch(gals)
+def to_device(gals, device="cuda", positions=None):
+    t, total = host_batch(gals, positions=positions)
     dev = {k: v.to(device) for k, v in t.items()}
     return DeviceBatch(dev, len(gals), total, np.asarray(gals.size).copy(), t["offset"].numpy().copy())
 
@@ -73,7 +78,10 @@ class Renderer:
         self.ctx = capi.mog_create_context(device)
         for pid, t in tables.items():
             capi.mog_set_profile_table(self.ctx, pid, t.nodes, t.amp, t.var)
-        self.psf_ids = [capi.mog_create_psf(self.ctx, p.image, p.mog) for p in psfs]
+        self.psf_ids = [capi.mog_create_psf(self.ctx, p.image, p.mog) if hasattr(p, "image")
+                        else capi.mog_create_eigen_psf(self.ctx, p.components, p.degree, p.norm, p.mog_shape,
+                                                       p.mog_amp)
+                        for p in psfs]
         if self.psf_ids != list(range(len(psfs))):
             raise RuntimeError("fresh context expected PSF ids 0..P-1")
 
