@@ -297,7 +297,9 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     // (needed at +omega and -omega by the packed transform) and the
     // real-space terms, spread over the CTA as one task list
     if (work) {
-      const DevPsf& ps = p.psfs[r.psf];
+      // the PSF id from a register (cur_psf) unless eigen-PSFs reset it: one
+      // shared-memory load less on the path to the set-up tasks
+      const DevPsf& ps = p.psfs[EIG ? r.psf : cur_psf];
       const int kp = ps.k, nrt = r.nrc * kp, nr2 = real_terms_padded(nrt);
       // what the store needs of the record is copied out: the record buffer
       // is refilled while slower warps may still be storing
