@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the mixed-size / gradient / per-galaxy lines")
     ap.add_argument("--extra-steps", type=int, default=20)
-    ap.add_argument("--only", choices=("fwd", "grad", "mixed", "serving", "lanczos"),
+    ap.add_argument("--only", choices=("fwd", "grad", "mixed", "serving", "lanczos", "eigen"),
                     help="profiling mode: run just this workload (--galaxies of it) for --warmup + --steps "
                          "and print its time")
     return ap.parse_args()
@@ -401,6 +401,37 @@ def extra_lanczos(tables, psf, device, steps):
             "kernel_ms": kms[1] / max(kn[1], 1)}
 
 
+def extra_eigen(tables, psf, device, steps):
+    """The fixed-size batch (100k x 64^2) on a spatially varying PSF: a
+    degree-2 eigen-PSF model (6 pixelized components) with galaxies at
+    uniform positions in a 4096^2 image; every galaxy forms its own PSF
+    spectrum from the 6 component spectra."""
+    import torch
+    from paper_2012_15797_gb300 import capi
+    from paper_2012_15797_gb300.renderer import Renderer, to_device
+    from workloads import config1_galaxies, eigen_positions, eigen_psf
+
+    gals = config1_galaxies()
+    gals.psf[:] = 1
+    r = Renderer(tables, [psf, eigen_psf()], device=device)
+    b = to_device(gals, device=f"cuda:{device}", positions=eigen_positions(len(gals)))
+    out = torch.empty(b.total, device=f"cuda:{device}")
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        r.render(b, out)
+    r.sync_status()
+    capi.mog_set_timing(r.ctx, True)
+    capi.mog_read_timing(r.ctx)
+    ms = _event_ms(lambda: r.render(b, out), steps, st)
+    kms, kn = capi.mog_read_timing(r.ctx)
+    capi.mog_set_timing(r.ctx, False)
+    r.sync_status()
+    r.close()
+    return {"workload": "the 100k-galaxy 64x64 batch on a degree-2 eigen-PSF (6 components), uniform positions",
+            "value": len(gals) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "kernel_ms": kms[1] / max(kn[1], 1)}
+
+
 def extra_per_galaxy(tables, psf, device, n=2000):
     """The plain form: the same math with one library call (planner, record,
     render launches) per galaxy."""
@@ -624,6 +655,7 @@ def run_ours(args):
         extra = {"mixed_sizes": extra_mixed(tables, local, args.extra_steps),
                  "render_grad": extra_render_grad(tables, psf, local, args.extra_steps),
                  "lanczos_shift": extra_lanczos(tables, psf, local, args.extra_steps),
+                 "eigen_psf": extra_eigen(tables, psf, local, args.extra_steps),
                  "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local),
                  "serving": extra_serving(tables, local)}
 
@@ -699,14 +731,21 @@ def run_only(args):
     from paper_2012_15797_gb300.renderer import Renderer, to_device
     from workloads import config0_psf, config1_galaxies, config2_galaxies, config2_psfs, load_profile_tables
     tables = load_profile_tables()
+    pos = None
     if args.only == "mixed":
         psfs = config2_psfs(8)
         gals = config2_galaxies(args.galaxies, n_psf=8)
+    elif args.only == "eigen":
+        from workloads import eigen_positions, eigen_psf
+        psfs = [config0_psf(), eigen_psf()]
+        gals = config1_galaxies(args.galaxies)
+        gals.psf[:] = 1
+        pos = eigen_positions(len(gals))
     else:
         psfs = [config0_psf()]
         gals = config1_galaxies(args.galaxies)
     r = Renderer(tables, psfs)
-    b = to_device(gals)
+    b = to_device(gals, positions=pos)
     out = torch.empty(b.total, device="cuda")
     go = torch.randn(b.total, device="cuda") if args.only == "grad" else None
 
