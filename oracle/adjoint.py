@@ -16,6 +16,8 @@ S(log r_e, e1, e2) is the CD = I covariance of Appendix A:
   S11 = r^2 (h + G e1), S12 = -r^2 G e2, S22 = r^2 (h - G e1),
   h = (1 + beta^2)/2, G = (beta^2 - 1)/(2e), beta = (1 - e)/(1 + e).
 S is not differentiable at e = 0 (beta depends on |e|), so e > 0 is required.
+With a WCS matrix CD the pixel covariance is A S A^T with A = CD^-1
+(Appendix A), which is linear in S, so its derivatives are A dS A^T.
 """
 
 import numpy as np
@@ -46,10 +48,11 @@ def shape_derivatives(log_re, e1, e2):
     return [2.0 * s, d1, d2]
 
 
-def jacobian(gal, psf_hat, psf_mog, tables, n=None):
-    """(6, n, n) array: d pixel / d theta for one galaxy."""
+def jacobian(gal, psf_hat, psf_mog, tables, n=None, cd=None):
+    """(6, n, n) array: d pixel / d theta for one galaxy (WCS matrix ``cd``,
+    identity when None)."""
     n = int(gal["size"]) if n is None else int(n)
-    amps, covs, wf, wr, s, v, ns = R.galaxy_components(gal, tables, n)
+    amps, covs, wf, wr, s, v, ns = R.galaxy_components(gal, tables, n, cd)
     flux = gal["flux"]
     x0, y0 = 0.5 * n + gal["x"], 0.5 * n + gal["y"]
     nu, om = R.frequencies(n)
@@ -70,6 +73,9 @@ def jacobian(gal, psf_hat, psf_mog, tables, n=None):
             dm_s[ab] += amp * gi * (slopes[i] * dns[ab][i] - wf[i] * 2 * np.pi ** 2 * v[i] * dq[ab])
     dm = [m / flux, -2j * np.pi * NU * m, -2j * np.pi * OM * m]
     ds = shape_derivatives(gal["log_re"], gal["e1"], gal["e2"])
+    if cd is not None:
+        a = np.linalg.inv(np.asarray(cd, dtype=np.float64))
+        ds = [a @ d @ a.T for d in ds]
     for d in ds:
         dm.append(d[0, 0] * dm_s[(0, 0)] + d[0, 1] * dm_s[(0, 1)] + d[1, 1] * dm_s[(1, 1)])
     jac = np.stack([np.fft.irfft2(psf_hat * d, s=(n, n)) for d in dm])
@@ -100,12 +106,12 @@ def jacobian(gal, psf_hat, psf_mog, tables, n=None):
     return jac + rj
 
 
-def vjp(gal, psf_hat, psf_mog, tables, grad_pix, n=None):
+def vjp(gal, psf_hat, psf_mog, tables, grad_pix, n=None, cd=None):
     """sum_p grad_pix[p] * d pixel[p] / d theta: the six gradients."""
-    return np.tensordot(jacobian(gal, psf_hat, psf_mog, tables, n), grad_pix, axes=([1, 2], [0, 1]))
+    return np.tensordot(jacobian(gal, psf_hat, psf_mog, tables, n, cd), grad_pix, axes=([1, 2], [0, 1]))
 
 
-def finite_difference(gal, psf_hat, psf_mog, tables, step=1e-6, n=None):
+def finite_difference(gal, psf_hat, psf_mog, tables, step=1e-6, n=None, cd=None):
     """Central finite differences of the forward model: absolute step for
     x, y, log r_e, e1, e2 and relative step (step * flux) for flux."""
     out = []
@@ -114,7 +120,7 @@ def finite_difference(gal, psf_hat, psf_mog, tables, step=1e-6, n=None):
         gp, gm = dict(gal), dict(gal)
         gp[p] = gal[p] + h
         gm[p] = gal[p] - h
-        ip = R.render(gp, None, psf_mog, tables, n=n, psf_hat=psf_hat)
-        im = R.render(gm, None, psf_mog, tables, n=n, psf_hat=psf_hat)
+        ip = R.render(gp, None, psf_mog, tables, n=n, psf_hat=psf_hat, cd=cd)
+        im = R.render(gm, None, psf_mog, tables, n=n, psf_hat=psf_hat, cd=cd)
         out.append((ip - im) / (2 * h))
     return np.stack(out)

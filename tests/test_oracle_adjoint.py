@@ -71,3 +71,19 @@ def test_subpixel_motion_is_smooth_for_point_source(tables, psf0):
         jac = A.jacobian(g, ph, psf0.mog, tables)
         fd = A.finite_difference(g, ph, psf0.mog, tables, step=1e-5)
         assert np.max(np.abs(jac[1] - fd[1])) < 1e-6 * np.abs(fd[1]).max()
+
+
+@pytest.mark.parametrize("cd", [np.array([[0.8, 0.25], [-0.15, 1.2]]), np.array([[-1.1, 0.4], [0.3, 0.9]])])
+def test_jacobian_with_wcs_matrix(cd, tables, psf0):
+    """A general WCS matrix (Appendix A): the analytic Jacobian against central
+    differences of the forward model rendered with the same CD."""
+    for lre, prof in ((np.log(3.0), 0), (np.log(9.0), 1)):
+        g = config0_galaxy().row(0)
+        g.update(log_re=lre, profile=prof, sersic_n=4.0 if prof == 1 else 1.0, e1=0.25, e2=-0.2, x=0.3, y=-0.1,
+                 flux=2.0, size=64)
+        ph = R.psf_spectrum(psf0.image, 64)
+        jac = A.jacobian(g, ph, psf0.mog, tables, cd=cd)
+        fd = A.finite_difference(g, ph, psf0.mog, tables, step=1e-5, cd=cd)
+        for k in range(6):
+            scale = np.abs(fd[k]).max()
+            assert np.max(np.abs(jac[k] - fd[k])) < 1e-6 * scale, A.PARAMS[k]
