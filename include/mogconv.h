@@ -15,9 +15,10 @@
  *  - A patch is N x N float32, row-major, row = y, column = x, pixel centres at
  *    integer coordinates.  N is one of 32, 64, 128, 256.
  *  - The galaxy centre is (N/2 + x, N/2 + y) where (x, y) is its offset.
- *  - Shapes: r_e = exp(log_re) pixels; e1, e2 ellipticity (Eqs. 2-5) with the
- *    WCS matrix CD = identity (pixel units); the pixel covariance of a
- *    component of profile variance v is v S with S from Appendix A.
+ *  - Shapes: r_e = exp(log_re) and e1, e2 ellipticity (Eqs. 2-5) in the
+ *    coordinates of the galaxy's WCS matrix CD (batch field cd; without it
+ *    CD = identity, i.e. pixel units); the pixel covariance of a component of
+ *    profile variance v is v S with S from Appendix A.
  *  - Aliasing split (Step 4): n_sigma = (N/2) / sqrt(trace(v S)); a component
  *    is Fourier only for n_sigma >= 4, real only for n_sigma <= 3, and both in
  *    between with weights w_F = 3t^2 - 2t^3 (t = n_sigma - 3), w_R = 1 - w_F.
@@ -78,6 +79,12 @@ enum { MOG_MAX_COMPONENTS = 12, MOG_MAX_PSF_COMPONENTS = 4, MOG_MAX_PSFS = 1024,
  *             galaxies whose PSF is an eigen-PSF (mog_create_eigen_psf); may
  *             be NULL when no galaxy uses one (such galaxies are then skipped
  *             and reported as MOG_ERR_DEVICE)
+ *   cd        optional, 4 floats per galaxy: the local WCS matrix
+ *             CD = [[cd[4g], cd[4g+1]], [cd[4g+2], cd[4g+3]]] taking pixel
+ *             offsets to the coordinates in which r_e, e1 and e2 are given;
+ *             the pixel covariance is CD^-1 S CD^-T (Appendix A).  NULL =
+ *             identity (pixel units).  A singular or non-finite CD skips the
+ *             galaxy (MOG_ERR_DEVICE).
  * Patches must not overlap.  The batch struct itself is host memory.
  */
 typedef struct mog_batch {
@@ -97,6 +104,7 @@ typedef struct mog_batch {
                           0 = unknown (every size's kernel is launched) */
   const float* img_x;
   const float* img_y;
+  const float* cd;
 } mog_batch;
 
 /* Creates a context on CUDA device `device` (makes it current).  *out gets

@@ -54,7 +54,7 @@ class mog_batch(ctypes.Structure):
         ("sersic_n", ctypes.c_void_p), ("profile", ctypes.c_void_p), ("psf", ctypes.c_void_p),
         ("size", ctypes.c_void_p), ("offset", ctypes.c_void_p),
         ("size_mask", ctypes.c_uint32),
-        ("img_x", ctypes.c_void_p), ("img_y", ctypes.c_void_p),
+        ("img_x", ctypes.c_void_p), ("img_y", ctypes.c_void_p), ("cd", ctypes.c_void_p),
     ]
 
 

@@ -74,7 +74,7 @@ namespace {
 
 BatchView view_of(const mog_batch* b) {
   return BatchView{b->flux,    b->x,       b->y,   b->log_re, b->e1,     b->e2,   b->sersic_n,
-                   b->profile, b->psf,     b->size, b->offset, b->img_x, b->img_y};
+                   b->profile, b->psf,     b->size, b->offset, b->img_x, b->img_y, b->cd};
 }
 
 cudaError_t take_event(mog_ctx* ctx, cudaEvent_t* ev) {

@@ -331,7 +331,36 @@ struct BatchView {
   const int32_t *profile, *psf, *size;
   const int64_t* offset;
   const float *img_x, *img_y;   // may be null (needed for eigen-PSFs only)
+  const float* cd;              // 4 per galaxy (WCS matrix, row-major), may be null (identity)
 };
+
+// The galaxy's WCS matrix CD = [[t, u], [v, w]] (identity without one) and
+// whether it is usable (finite, non-singular).
+__device__ __forceinline__ bool wcs_matrix(const BatchView& b, int64_t g, float (&cd)[4]) {
+  cd[0] = 1.0f;
+  cd[1] = 0.0f;
+  cd[2] = 0.0f;
+  cd[3] = 1.0f;
+  if (!b.cd) return true;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) cd[i] = b.cd[4 * g + i];
+  const float det = cd[0] * cd[3] - cd[1] * cd[2];
+  return isfinite(cd[0]) && isfinite(cd[1]) && isfinite(cd[2]) && isfinite(cd[3]) && isfinite(det) && det != 0.0f;
+}
+
+// M <- A M A^T with A = CD^-1 = [[w, -u], [-v, t]] / det for a symmetric M
+// given as (m11, m12, m22): the pixel covariance of a shape given in the
+// coordinates of the WCS (Appendix A).
+__device__ __forceinline__ void wcs_transform(const float (&cd)[4], float& m11, float& m12, float& m22) {
+  const float inv = 1.0f / (cd[0] * cd[3] - cd[1] * cd[2]);
+  const float a = cd[3] * inv, bq = -cd[1] * inv, c = -cd[2] * inv, d = cd[0] * inv;
+  const float n11 = a * a * m11 + 2.0f * a * bq * m12 + bq * bq * m22;
+  const float n12 = a * c * m11 + (a * d + bq * c) * m12 + bq * d * m22;
+  const float n22 = c * c * m11 + 2.0f * c * d * m12 + d * d * m22;
+  m11 = n11;
+  m12 = n12;
+  m22 = n22;
+}
 
 // Per planned position: eigen-PSF polynomial terms [0, 6) and the mixture
 // weights at the galaxy's position [8, 12) (written by the record prologue).
@@ -393,6 +422,8 @@ __device__ inline void galaxy_record_warp(const BatchView& b, int64_t g, int n, 
   ok = ok && P->n_nodes > 0 && psfs[pid].k > 0;
   ok = ok && (psfs[pid].k_eig == 0 ||
               (eigen_ok && b.img_x && b.img_y && isfinite(b.img_x[g]) && isfinite(b.img_y[g])));
+  float cdm[4];
+  ok = ok && wcs_matrix(b, g, cdm);
   const int64_t off = b.offset[g];
   ok = ok && (off & 3) == 0;   // patches are stored as aligned float4 rows
   if (!ok) {
@@ -410,7 +441,8 @@ __device__ inline void galaxy_record_warp(const BatchView& b, int64_t g, int n, 
   const float h = 0.5f * (1.0f + beta * beta);
   const float gq = 0.5f * (beta * beta - 1.0f);
   const float c1 = e > 0.0f ? e1 / e : 0.0f, c2 = e > 0.0f ? e2 / e : 0.0f;
-  const float s11 = r2 * (h + gq * c1), s12 = -r2 * gq * c2, s22 = r2 * (h - gq * c1);
+  float s11 = r2 * (h + gq * c1), s12 = -r2 * gq * c2, s22 = r2 * (h - gq * c1);
+  if (b.cd) wcs_transform(cdm, s11, s12, s22);
   const float tr = s11 + s22;
 
   // Mixture component `lane` at Sersic index sn.
@@ -568,6 +600,8 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
   const DevProfile* P = ok ? &profiles[prof] : nullptr;
   ok = ok && P->n_nodes > 0 && psfs[pid].k > 0;
   ok = ok && psfs[pid].k_eig == 0;   // the adjoint takes constant PSFs only
+  float cdm[4];
+  ok = ok && wcs_matrix(b, g, cdm);
   const int64_t off = b.offset[g];
   ok = ok && (off & 3) == 0;
   if (!ok) {
@@ -584,7 +618,8 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
   const float h = 0.5f * (1.0f + beta * beta);
   const float gq = 0.5f * (beta * beta - 1.0f);
   const float c1 = e > 0.0f ? e1 / e : 0.0f, c2 = e > 0.0f ? e2 / e : 0.0f;
-  const float s11 = r2 * (h + gq * c1), s12 = -r2 * gq * c2, s22 = r2 * (h - gq * c1);
+  float s11 = r2 * (h + gq * c1), s12 = -r2 * gq * c2, s22 = r2 * (h - gq * c1);
+  if (b.cd) wcs_transform(cdm, s11, s12, s22);
   const float tr = s11 + s22;
   float a = 0.0f, v = 1.0f;
   if (lane < KMAX) {
@@ -641,6 +676,8 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
     out->gal = g;
     out->off = off;
     shape_jacobian(lre, e1, e2, out->dS);
+    if (b.cd)
+      for (int k = 0; k < 3; ++k) wcs_transform(cdm, out->dS[k][0], out->dS[k][1], out->dS[k][2]);
   }
 }
 

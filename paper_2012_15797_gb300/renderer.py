@@ -44,10 +44,11 @@ def pack_offsets(sizes):
     return off, int(area.sum())
 
 
-def host_batch(gals, pin=False, positions=None):
+def host_batch(gals, pin=False, positions=None, cd=None):
     """Host tensors (optionally pinned) of a ``workloads.Galaxies`` batch;
     ``positions`` = (img_x, img_y) image positions, needed by galaxies whose
-    PSF is an eigen-PSF."""
+    PSF is an eigen-PSF; ``cd`` = (G, 2, 2) or (G, 4) WCS matrices (None:
+    pixel units)."""
     t = {}
     for f in FLOAT_FIELDS:
         t[f] = torch.from_numpy(np.ascontiguousarray(getattr(gals, f), dtype=np.float32))
@@ -58,13 +59,15 @@ def host_batch(gals, pin=False, positions=None):
     if positions is not None:
         t["img_x"] = torch.from_numpy(np.ascontiguousarray(positions[0], dtype=np.float32))
         t["img_y"] = torch.from_numpy(np.ascontiguousarray(positions[1], dtype=np.float32))
+    if cd is not None:
+        t["cd"] = torch.from_numpy(np.ascontiguousarray(np.asarray(cd).reshape(len(gals), 4), dtype=np.float32))
     if pin:
         t = {k: v.pin_memory() for k, v in t.items()}
     return t, total
 
 
-def to_device(gals, device="cuda", positions=None):
-    t, total = host_batch(gals, positions=positions)
+def to_device(gals, device="cuda", positions=None, cd=None):
+    t, total = host_batch(gals, positions=positions, cd=cd)
     dev = {k: v.to(device) for k, v in t.items()}
     return DeviceBatch(dev, len(gals), total, np.asarray(gals.size).copy(), t["offset"].numpy().copy())
 
