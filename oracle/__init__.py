@@ -13,6 +13,7 @@ Modules:
   lanczos.py  the Step 8 variant that does the sub-pixel shift by Lanczos
               convolution of the final model,
   eigenpsf.py rendering with a spatially varying (eigen-)PSF (Step 2),
+  composite.py bulge + disk composites (the sum of two profiles' models),
   adjoint.py  analytic derivatives of the forward model w.r.t.
               (flux, x, y, log r_e, e1, e2) and a central finite-difference
               check,

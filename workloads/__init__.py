@@ -12,7 +12,7 @@ any of the method.
 from .galaxies import (  # noqa: F401
     PROFILE_EXP, PROFILE_DEV, PROFILE_SERSIC, SIZE_BUCKETS,
     config0_galaxy, config1_galaxies, config2_galaxies, config3_problem,
-    serving_workload, bucket_size, Galaxies,
+    serving_workload, bucket_size, Galaxies, composite_galaxies,
 )
 from .psf import (  # noqa: F401
     gaussian_mixture_psf, config0_psf, config2_psfs, fit_psf_mog, PsfInput,

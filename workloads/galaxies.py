@@ -190,3 +190,29 @@ def serving_workload(n_fits=1000, per_fit=512, seed=4, rate_per_ms=20_000.0, dur
         p[:, 5] *= scale
         requests.append((int(fit_id[r]), first, p.astype(np.float32)))
     return fits, arrival, requests
+
+
+def composite_galaxies(g=100_000, seed=7, sizes=SIZE_BUCKETS):
+    """Bulge + disk composites (Section 1: a linear combination of n = 1 and
+    n = 4 profiles with one centre).  Returns ``(disk, bulge)`` batches that
+    share offsets, PSF and patch side: disk exponential with r_e log-uniform
+    0.5-15 px and |e| <= 0.6; bulge de Vaucouleurs with r_e = U(0.2, 0.6) x
+    the disk's and |e| <= 0.3; bulge fraction U(0, 1) of a total flux
+    log-uniform 1-1e4; offsets U[-0.5, 0.5)^2; PSF 0; side the smallest of
+    ``sizes`` >= 8 r_e(disk)."""
+    rng = np.random.default_rng(seed)
+    re_d = np.exp(rng.uniform(np.log(0.5), np.log(15.0), g))
+    re_b = re_d * rng.uniform(0.2, 0.6, g)
+    frac = rng.uniform(0.0, 1.0, g)
+    flux = np.exp(rng.uniform(0.0, np.log(1e4), g))
+    e1d, e2d = _shapes(rng, g, 0.6)
+    e1b, e2b = _shapes(rng, g, 0.3)
+    x = rng.uniform(-0.5, 0.5, g)
+    y = rng.uniform(-0.5, 0.5, g)
+    size = bucket_size(re_d, sizes)
+    common = dict(x=x, y=y, psf=np.zeros(g), size=size)
+    disk = _cast(flux=(1.0 - frac) * flux, log_re=np.log(re_d), e1=e1d, e2=e2d, sersic_n=np.ones(g),
+                 profile=np.full(g, PROFILE_EXP), **common)
+    bulge = _cast(flux=frac * flux, log_re=np.log(re_b), e1=e1b, e2=e2b, sersic_n=np.full(g, 4.0),
+                  profile=np.full(g, PROFILE_DEV), **common)
+    return disk, bulge
