@@ -185,6 +185,21 @@ mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, vo
 mog_status mog_render_batch_lanczos(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
 
 /*
+ * mog_render_batch with options, `flags` a bitwise or of:
+ *   MOG_RENDER_LANCZOS  the sub-pixel shift of mog_render_batch_lanczos
+ *   MOG_RENDER_ADD      add each model to what its patch already holds instead
+ *                       of overwriting it (out must hold valid values)
+ * MOG_RENDER_ADD renders composite galaxies, the linear combination of two
+ * profiles with one centre (Section 1: bulge-disk decomposition, e.g. n = 1
+ * plus n = 4): render the first profiles, then add the second ones with the
+ * same offsets, sizes and PSFs.  With 256 x 256 patches it uses a workspace
+ * scratch of N/2 x N complex values per SM (allocated on first use).  Other
+ * arguments, layout and errors as mog_render_batch.
+ */
+enum { MOG_RENDER_LANCZOS = 1, MOG_RENDER_ADD = 2 };
+mog_status mog_render_batch_ex(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream, unsigned flags);
+
+/*
  * Same result as mog_render_batch, but the call allocates no memory: no
  * cudaMalloc, no cudaFree, no allocating library routine.  (The paper has no
  * counterpart; this is an interface for callers that cannot let a library

@@ -35,7 +35,7 @@ EXPORTED = (
     "mog_autotune", "mog_graph_capture", "mog_graph_launch", "mog_graph_destroy",
     "mog_server_create", "mog_server_add_fit", "mog_server_submit", "mog_server_wait", "mog_server_replay",
     "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
-    "mog_create_eigen_psf",
+    "mog_create_eigen_psf", "mog_render_batch_ex",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -89,6 +89,7 @@ def _load():
         "mog_destroy_psf": ([VP, I], I),
         "mog_render_batch": ([VP, P(mog_batch), VP, VP], I),
         "mog_render_batch_lanczos": ([VP, P(mog_batch), VP, VP], I),
+        "mog_render_batch_ex": ([VP, P(mog_batch), VP, VP, ctypes.c_uint], I),
         "mog_render_backward": ([VP, P(mog_batch), VP, VP, VP], I),
         "mog_render_batch_noalloc": ([VP, P(mog_batch), VP, VP], I),
         "mog_autotune": ([VP, P(mog_batch), VP, VP, VP, VP, I, P(I)], I),
@@ -203,6 +204,14 @@ def mog_render_batch(ctx, batch, out_ptr, stream=0):
 def mog_render_batch_lanczos(ctx, batch, out_ptr, stream=0):
     _check(ctx, _lib.mog_render_batch_lanczos(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
                                               ctypes.c_void_p(int(stream))))
+
+
+MOG_RENDER_LANCZOS, MOG_RENDER_ADD = 1, 2
+
+
+def mog_render_batch_ex(ctx, batch, out_ptr, stream=0, flags=0):
+    _check(ctx, _lib.mog_render_batch_ex(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
+                                         ctypes.c_void_p(int(stream)), ctypes.c_uint(int(flags))))
 
 
 def mog_render_batch_noalloc(ctx, batch, out_ptr, stream=0):

@@ -403,17 +403,24 @@ mog_status launch_buckets(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, u
 namespace mog {
 
 mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s,
-                       bool lanczos) {
+                       bool lanczos, bool add) {
   mog_status st = check_batch(ctx, batch);
   if (st != MOG_OK) return st;
   if (batch->count == 0) return MOG_OK;
   if (!out || (reinterpret_cast<uintptr_t>(out) & 15)) return fail(ctx, MOG_ERR_ARG, "out must be 16-byte aligned");
   const uint32_t buckets = lanczos ? LZ_BUCKETS : FWD_BUCKETS;
+  const uint32_t want = batch->size_mask ? (batch->size_mask & buckets) : buckets;
+  // adding to the patch: the 256 x 256 kernel cannot use the patch as its
+  // transform intermediate, so it takes the workspace scratch
+  if (add && (want & 0x8) && !ws->bwd256)
+    MOG_CUDA(ctx, cudaMalloc(&ws->bwd256, render_bwd256_scratch_bytes(ctx->num_sms)));
   RenderParams p;
   if ((st = plan_batch(ctx, ws, batch, out, buckets, s, &p)) != MOG_OK) return st;
   p.records = ws->records;
   p.lanczos = lanczos ? 1 : 0;
   p.lzw = ws->lzw;
+  p.accumulate = add ? 1 : 0;
+  p.scratch256 = ws->bwd256;
   MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ws->records, s));
   return launch_buckets(ctx, ws, batch, buckets, s, [&](int n, cudaStream_t bs) {
     RenderParams q = p;
@@ -457,6 +464,13 @@ mog_status mog_render_batch(mog_ctx* ctx, const mog_batch* batch, float* out, vo
 mog_status mog_render_batch_lanczos(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
   if (!ctx) return MOG_ERR_ARG;
   return render_with(ctx, &ctx->ws, batch, out, static_cast<cudaStream_t>(stream), true);
+}
+
+mog_status mog_render_batch_ex(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream, unsigned flags) {
+  if (!ctx) return MOG_ERR_ARG;
+  if (flags & ~(unsigned)(MOG_RENDER_LANCZOS | MOG_RENDER_ADD)) return fail(ctx, MOG_ERR_ARG, "unknown render flags");
+  return render_with(ctx, &ctx->ws, batch, out, static_cast<cudaStream_t>(stream), (flags & MOG_RENDER_LANCZOS) != 0,
+                     (flags & MOG_RENDER_ADD) != 0);
 }
 
 mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,

@@ -362,6 +362,19 @@ __device__ __forceinline__ void wcs_transform(const float (&cd)[4], float& m11, 
   m22 = n22;
 }
 
+// Stores 8 consecutive patch values, or adds them to what the patch holds.
+__device__ __forceinline__ void store8(float* p, const float* o, bool add) {
+  float4* d = reinterpret_cast<float4*>(p);
+  float4 a = make_float4(o[0], o[1], o[2], o[3]), b = make_float4(o[4], o[5], o[6], o[7]);
+  if (add) {
+    const float4 pa = d[0], pb = d[1];
+    a = make_float4(pa.x + a.x, pa.y + a.y, pa.z + a.z, pa.w + a.w);
+    b = make_float4(pb.x + b.x, pb.y + b.y, pb.z + b.z, pb.w + b.w);
+  }
+  d[0] = a;
+  d[1] = b;
+}
+
 // Per planned position: eigen-PSF polynomial terms [0, 6) and the mixture
 // weights at the galaxy's position [8, 12) (written by the record prologue).
 constexpr int PCOEF = 16;

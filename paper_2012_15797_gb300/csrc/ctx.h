@@ -72,7 +72,7 @@ mog_status cuda_fail(mog_ctx* ctx, cudaError_t e, const char* what);
 mog_status check_batch(mog_ctx* ctx, const mog_batch* batch);
 // Batched render / adjoint with an explicit workspace (grows it if needed).
 mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s,
-                       bool lanczos = false);
+                       bool lanczos = false, bool add = false);
 mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, const float* grad_out,
                          float* grad_params, cudaStream_t s);
 

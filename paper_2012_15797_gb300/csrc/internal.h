@@ -25,6 +25,8 @@ struct RenderParams {
   float* lzw = nullptr;         // lanczos: 16 floats per planned position, weights along x [0, 7), y [8, 15)
   float* pcoef = nullptr;       // PCOEF floats per planned position (eigen-PSF terms and mixture weights)
   int eigen = 0;                // 1: some PSF of the context is an eigen-PSF (launch the kernels that handle it)
+  int accumulate = 0;           // 1: add the model to the patch instead of writing it
+  float2* scratch256 = nullptr; // accumulate, N = 256: per-CTA transform intermediate (N/2 x N complex)
 };
 
 // Launch shape of one size bucket: CTAs per SM (clamped to what fits) and

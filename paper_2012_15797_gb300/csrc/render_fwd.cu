@@ -104,7 +104,7 @@ __device__ __forceinline__ int out_pos(int x) { return x ^ (((x >> 5) & 1) << 2)
 // along x in the group's rows, then (after a CTA barrier) along y.
 template <int N>
 __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, const RealTerms& rt, int nr,
-                                                       const float* wl, int f, int j, float* dst) {
+                                                       const float* wl, int f, int j, float* dst, bool add) {
   using C = FwdCfg<N>;
   const int x0 = 8 * j;
   const int p0 = out_pos(x0), p1 = out_pos(x0 + 4);
@@ -177,9 +177,7 @@ __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, 
   }
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    float4* d = reinterpret_cast<float4*>(dst + (2 * f + h) * N + x0);
-    d[0] = make_float4(F[h][0], F[h][1], F[h][2], F[h][3]);
-    d[1] = make_float4(F[h][4], F[h][5], F[h][6], F[h][7]);
+    store8(dst + (2 * f + h) * N + x0, F[h], add);
   }
 }
 
@@ -491,7 +489,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     // ---- Step 8: add the real-space terms and store rows 2f and 2f+1 ----
     if constexpr (LZ) {
       if (nr > 0) {   // uniform over the CTA
-        lanczos_real_and_store<N>(WB, orow, rt, nr, s_lzw[buf], f, j, dst);
+        lanczos_real_and_store<N>(WB, orow, rt, nr, s_lzw[buf], f, j, dst, p.accumulate != 0);
         continue;
       }
     }
@@ -507,9 +505,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
       const float4 i1 = *reinterpret_cast<const float4*>(src + ((x0 + 4) ^ sw));
       float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
       if (nr > 0) real_space_run(rt, nr, (float)yy, (float)x0, o);
-      float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
-      d[0] = make_float4(o[0], o[1], o[2], o[3]);
-      d[1] = make_float4(o[4], o[5], o[6], o[7]);
+      store8(dst + yy * N + x0, o, p.accumulate != 0);
     }
   }
 }

@@ -208,7 +208,9 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
     }
     if (!r.ok) continue;
     float* dst = p.out + r.off;
-    float2* zbuf = reinterpret_cast<float2*>(dst);   // row-pair inputs, [p][k]
+    // row-pair inputs, [p][k]: the patch itself, or, when adding to what the
+    // patch holds, this CTA's slice of the workspace scratch
+    float2* zbuf = p.accumulate ? p.scratch256 + (size_t)blockIdx.x * (N / 2) * N : reinterpret_cast<float2*>(dst);
 
     // per-galaxy tables
     {
@@ -403,9 +405,7 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
         const float4 i0 = *reinterpret_cast<const float4*>(orow), i1 = *reinterpret_cast<const float4*>(orow + 4);
         float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
         if (nr > 0 && !LZ) real_space_run(rt, nr, (float)yy, (float)x0, o);
-        float4* d = reinterpret_cast<float4*>(dst + yy * N + x0);
-        d[0] = make_float4(o[0], o[1], o[2], o[3]);
-        d[1] = make_float4(o[4], o[5], o[6], o[7]);
+        store8(dst + yy * N + x0, o, p.accumulate != 0);
       }
       __syncwarp();
     }

@@ -99,19 +99,33 @@ class Renderer:
         except Exception:
             pass
 
-    def render(self, batch, out=None, stream=None, shift="phase"):
+    def render(self, batch, out=None, stream=None, shift="phase", add=False):
         """Renders a DeviceBatch into a flat float32 device tensor.  ``shift``
         selects how the sub-pixel offset is applied: "phase" (Fourier shift
-        phase) or "lanczos" (Lanczos-3 convolution of the final model)."""
+        phase) or "lanczos" (Lanczos-3 convolution of the final model).  With
+        ``add`` the models are added to what ``out`` holds."""
         if shift not in ("phase", "lanczos"):
             raise ValueError(f"unknown shift {shift!r}")
+        if add and out is None:
+            raise ValueError("add=True needs an output to add to")
         if out is None:
             out = torch.empty(batch.total, dtype=torch.float32, device=self.device)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
+        if add:
+            flags = capi.MOG_RENDER_ADD | (capi.MOG_RENDER_LANCZOS if shift == "lanczos" else 0)
+            capi.mog_render_batch_ex(self.ctx, b, out.data_ptr(), s.cuda_stream, flags)
+            return out
         fn = capi.mog_render_batch if shift == "phase" else capi.mog_render_batch_lanczos
         fn(self.ctx, b, out.data_ptr(), s.cuda_stream)
         return out
+
+    def render_composite(self, disk, bulge, out=None, stream=None, shift="phase"):
+        """Composite (bulge + disk) galaxies: the sum of two profiles sharing
+        the patch layout, PSF and centre.  ``disk`` and ``bulge`` are
+        DeviceBatches with the same sizes, offsets, PSFs and (x, y)."""
+        out = self.render(disk, out, stream, shift)
+        return self.render(bulge, out, stream, shift, add=True)
 
     def render_backward(self, batch, grad_out, grad_params=None, stream=None):
         """Gradients (count, 6) of L w.r.t. (flux, x, y, log_re, e1, e2)
