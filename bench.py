@@ -432,6 +432,35 @@ def extra_eigen(tables, psf, device, steps):
             "kernel_ms": kms[1] / max(kn[1], 1)}
 
 
+def extra_composite(tables, psf, device, steps):
+    """100k bulge + disk composites (exp disk, deV bulge, one centre), patch
+    sides 32-128 by the disk's radius: the disks rendered, then the bulges
+    added into the same patches (mog_render_batch_ex, MOG_RENDER_ADD)."""
+    import numpy as np
+    import torch
+    from paper_2012_15797_gb300 import capi
+    from paper_2012_15797_gb300.renderer import Renderer, to_device
+    from workloads import composite_galaxies
+
+    disk, bulge = composite_galaxies(100_000)
+    r = Renderer(tables, [psf], device=device)
+    bd = to_device(disk, device=f"cuda:{device}")
+    bb = to_device(bulge, device=f"cuda:{device}")
+    out = torch.empty(bd.total, device=f"cuda:{device}")
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        r.render_composite(bd, bb, out)
+    r.sync_status()
+    ms = _event_ms(lambda: r.render_composite(bd, bb, out), steps, st)
+    r.sync_status()
+    r.close()
+    sizes, counts = np.unique(disk.size, return_counts=True)
+    return {"workload": "100000 bulge + disk composites: exp disk r_e log-U(0.5, 15) px, deV bulge r_e 0.2-0.6 of "
+                        "the disk's, bulge fraction U(0, 1), sides by 8 r_e(disk)",
+            "bucket_mix": {int(n): int(c) for n, c in zip(sizes, counts)},
+            "value": len(disk) / (ms / 1e3), "unit": "composite patches/s", "ms_per_step": ms}
+
+
 def extra_per_galaxy(tables, psf, device, n=2000):
     """The plain form: the same math with one library call (planner, record,
     render launches) per galaxy."""
@@ -656,6 +685,7 @@ def run_ours(args):
                  "render_grad": extra_render_grad(tables, psf, local, args.extra_steps),
                  "lanczos_shift": extra_lanczos(tables, psf, local, args.extra_steps),
                  "eigen_psf": extra_eigen(tables, psf, local, args.extra_steps),
+                 "composite": extra_composite(tables, psf, local, args.extra_steps),
                  "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local),
                  "serving": extra_serving(tables, local)}
 
