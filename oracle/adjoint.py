@@ -16,6 +16,8 @@ S(log r_e, e1, e2) is the CD = I covariance of Appendix A:
   S11 = r^2 (h + G e1), S12 = -r^2 G e2, S22 = r^2 (h - G e1),
   h = (1 + beta^2)/2, G = (beta^2 - 1)/(2e), beta = (1 - e)/(1 + e).
 S is not differentiable at e = 0 (beta depends on |e|), so e > 0 is required.
+The Sersic index n moves the mixture itself (amplitudes a_i(n) and variances
+v_i(n), interpolated in the profile table): ``sersic_derivative``.
 With a WCS matrix CD the pixel covariance is A S A^T with A = CD^-1
 (Appendix A), which is linear in S, so its derivatives are A dS A^T.
 """
@@ -124,3 +126,64 @@ def finite_difference(gal, psf_hat, psf_mog, tables, step=1e-6, n=None, cd=None)
         im = R.render(gm, None, psf_mog, tables, n=n, psf_hat=psf_hat, cd=cd)
         out.append((ip - im) / (2 * h))
     return np.stack(out)
+
+
+def profile_mixture_dn(table, n):
+    """(a, v, da/dn, dv/dn) of every slot of a profile table at Sersic index
+    n: a and log v are linear in n between the bracketing nodes (Section 3),
+    so da/dn = (a_{j+1} - a_j) / dn and dv/dn = v (log v_{j+1} - log v_j) / dn
+    inside the node range; zero outside it and for one-node tables.  Slots
+    with a = 0 and da/dn = 0 are dropped."""
+    nodes = table.nodes
+    if len(nodes) == 1:
+        a, v = table.amp[0].copy(), table.var[0].copy()
+        da, dv = np.zeros_like(a), np.zeros_like(v)
+    else:
+        inside = nodes[0] <= float(n) <= nodes[-1]
+        nn = min(max(float(n), nodes[0]), nodes[-1])
+        j = min(int(np.searchsorted(nodes, nn, side="right")) - 1, len(nodes) - 2)
+        h = nodes[j + 1] - nodes[j]
+        tt = (nn - nodes[j]) / h
+        la, lb = np.log(table.var[j]), np.log(table.var[j + 1])
+        a = (1 - tt) * table.amp[j] + tt * table.amp[j + 1]
+        v = np.exp((1 - tt) * la + tt * lb)
+        da = (table.amp[j + 1] - table.amp[j]) / h if inside else np.zeros_like(a)
+        dv = v * (lb - la) / h if inside else np.zeros_like(v)
+    keep = (a > 0) | (da != 0)
+    return a[keep], v[keep], da[keep], dv[keep]
+
+
+def sersic_derivative(gal, psf_hat, psf_mog, tables, n=None, cd=None):
+    """(n, n) d pixel / d sersic_n: the mixture's amplitudes and variances
+    move with n, through the Fourier Gaussians, the ramp weights and the
+    real-space Gaussians (dN/dv = N (u^T S u - tr(Sigma^-1 S)) / 2 with
+    u = Sigma^-1 d, Sigma = v S + P)."""
+    n = int(gal["size"]) if n is None else int(n)
+    a, v, da, dv = profile_mixture_dn(tables[int(gal["profile"])], gal["sersic_n"])
+    s = R.ellipse_covariance(np.exp(gal["log_re"]), gal["e1"], gal["e2"], cd)
+    flux = gal["flux"]
+    x0, y0 = 0.5 * n + gal["x"], 0.5 * n + gal["y"]
+    nu, om = R.frequencies(n)
+    NU, OM = nu[None, :], om[:, None]
+    q = s[0, 0] * NU * NU + 2 * s[0, 1] * NU * OM + s[1, 1] * OM * OM
+    dm = np.zeros((n, n // 2 + 1), complex)
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
+    real = np.zeros((n, n))
+    for ai, vi, dai, dvi in zip(a, v, da, dv):
+        cov = vi * s
+        ns = R.n_sigma(cov, n)
+        wf, dwf = R.ramp(ns), R.ramp_slope(ns)
+        dns = -0.5 * ns / vi * dvi            # d n_sigma / dn
+        gi = R.fourier_gaussian(cov, x0, y0, NU, OM)
+        dm += flux * (dai * wf + ai * dwf * dns) * gi + flux * ai * wf * dvi * (-2 * np.pi ** 2 * q) * gi
+        for w, mx, my, pxx, pxy, pyy in psf_mog:
+            sig = cov + np.array([[pxx, pxy], [pxy, pyy]])
+            nij = w * R.gaussian_2d(sig, x0 + mx, y0 + my, xx, yy)
+            inv = np.linalg.inv(sig)
+            dx, dy = xx - x0 - mx, yy - y0 - my
+            ux = inv[0, 0] * dx + inv[0, 1] * dy
+            uy = inv[1, 0] * dx + inv[1, 1] * dy
+            usu = s[0, 0] * ux * ux + 2 * s[0, 1] * ux * uy + s[1, 1] * uy * uy
+            trs = np.trace(inv @ s)
+            real += flux * nij * ((dai * (1 - wf) - ai * dwf * dns) + ai * (1 - wf) * dvi * 0.5 * (usu - trs))
+    return np.fft.irfft2(psf_hat * dm, s=(n, n)) + real

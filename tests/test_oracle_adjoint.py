@@ -87,3 +87,27 @@ def test_jacobian_with_wcs_matrix(cd, tables, psf0):
         for k in range(6):
             scale = np.abs(fd[k]).max()
             assert np.max(np.abs(jac[k] - fd[k])) < 1e-6 * scale, A.PARAMS[k]
+
+
+@pytest.mark.parametrize("sn,lre,n", [(2.6, np.log(3.0), 64), (4.375, np.log(9.0), 64), (1.13, np.log(14.0), 32),
+                                       (5.3, np.log(0.6), 32)])
+def test_sersic_derivative_matches_central_differences(sn, lre, n, tables, psf0):
+    """d pixel / d n through the interpolated Sersic table (all-Fourier, ramp
+    and real-space cases), against central differences in n away from the
+    table's nodes (n = 0.5 + 0.25 k)."""
+    g = config0_galaxy().row(0)
+    g.update(profile=2, sersic_n=sn, log_re=lre, e1=0.2, e2=-0.15, x=0.3, y=-0.2, flux=3.0, size=n)
+    ph = R.psf_spectrum(psf0.image, n)
+    got = A.sersic_derivative(g, ph, psf0.mog, tables)
+    h = 1e-5
+    gp, gm = dict(g, sersic_n=sn + h), dict(g, sersic_n=sn - h)
+    fd = (R.render(gp, None, psf0.mog, tables, psf_hat=ph) - R.render(gm, None, psf0.mog, tables, psf_hat=ph)) / (2 * h)
+    assert np.max(np.abs(got - fd)) < 1e-6 * np.abs(fd).max()
+
+
+def test_sersic_derivative_zero_for_fixed_profiles_and_outside_the_table(tables, psf0):
+    g = config0_galaxy().row(0)
+    ph = R.psf_spectrum(psf0.image, 64)
+    for prof, sn in ((0, 1.0), (1, 4.0), (2, 6.7), (2, 0.2)):
+        g.update(profile=prof, sersic_n=sn, log_re=np.log(6.0))
+        assert np.all(A.sersic_derivative(g, ph, psf0.mog, tables) == 0.0)
