@@ -240,6 +240,21 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
                                float* grad_params, void* stream);
 
 /*
+ * mog_render_backward with options, `flags` a bitwise or of:
+ *   MOG_GRAD_SERSIC  also d L / d sersic_n, through the interpolation of the
+ *                    profile table in n (Section 3: amplitudes and variances
+ *                    linear in n and log n between nodes): grad_params then
+ *                    holds 7 values per galaxy, theta = (flux, x, y, log_re,
+ *                    e1, e2, sersic_n).  Zero for one-node (fixed) profiles
+ *                    and outside the node range; at a node the derivative of
+ *                    the interval above it.
+ * Other arguments and errors as mog_render_backward.
+ */
+enum { MOG_GRAD_SERSIC = 1 };
+mog_status mog_render_backward_ex(mog_ctx* ctx, const mog_batch* batch, const float* grad_out,
+                                  float* grad_params, void* stream, unsigned flags);
+
+/*
  * Autotuner (the batching feature): for each size bucket present in the
  * batch (batch->size_mask, or all), times the render kernel over every
  * launch shape (CTAs per SM from 1 to what fits x work-queue chunk of

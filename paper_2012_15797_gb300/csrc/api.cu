@@ -430,7 +430,7 @@ mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, floa
 }
 
 mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, const float* grad_out,
-                         float* grad_params, cudaStream_t s) {
+                         float* grad_params, cudaStream_t s, bool grad_n) {
   mog_status st = check_batch(ctx, batch);
   if (st != MOG_OK) return st;
   if (batch->count == 0) return MOG_OK;
@@ -443,6 +443,7 @@ mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, co
   RenderParams p;
   if ((st = plan_batch(ctx, ws, batch, nullptr, BWD_BUCKETS, s, &p)) != MOG_OK) return st;
   p.records = ws->adj_records;
+  p.grad_n = grad_n ? 1 : 0;
   MOG_CUDA(ctx, launch_adjoint_prep(p, batch->count, ws->adj_records, s));
   return launch_buckets(ctx, ws, batch, BWD_BUCKETS, s, [&](int n, cudaStream_t bs) {
     RenderParams q = p;
@@ -477,6 +478,14 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
                                void* stream) {
   if (!ctx) return MOG_ERR_ARG;
   return backward_with(ctx, &ctx->ws, batch, grad_out, grad_params, static_cast<cudaStream_t>(stream));
+}
+
+mog_status mog_render_backward_ex(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,
+                                  void* stream, unsigned flags) {
+  if (!ctx) return MOG_ERR_ARG;
+  if (flags & ~(unsigned)MOG_GRAD_SERSIC) return fail(ctx, MOG_ERR_ARG, "unknown gradient flags");
+  return backward_with(ctx, &ctx->ws, batch, grad_out, grad_params, static_cast<cudaStream_t>(stream),
+                       (flags & MOG_GRAD_SERSIC) != 0);
 }
 
 mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {

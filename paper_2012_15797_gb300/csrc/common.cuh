@@ -560,8 +560,11 @@ struct __align__(16) AdjRecord {
   float pad[7];
   float famp[KMAX], fcoef[KMAX], fq[KMAX], fn[KMAX];
   float rbase[KMAX], rw[KMAX], rn[KMAX], rvar[KMAX];
+  // d/d(Sersic n): Fourier d(amp)/dn = fdn + fdq q per component; real-space
+  // d/dn = rda N + rdv (u^T S u - tr(Sigma^-1 S)) N per unit Gaussian N
+  float fdn[KMAX], fdq[KMAX], rda[KMAX], rdv[KMAX];
 };
-static_assert(sizeof(AdjRecord) == 512, "adjoint record layout");
+static_assert(sizeof(AdjRecord) == 704, "adjoint record layout");
 
 // dS/d(log r_e, e1, e2) for CD = I:
 //   S11 = r^2 (h + G e1), S12 = -r^2 G e2, S22 = r^2 (h - G e1),
@@ -634,25 +637,33 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
   float s11 = r2 * (h + gq * c1), s12 = -r2 * gq * c2, s22 = r2 * (h - gq * c1);
   if (b.cd) wcs_transform(cdm, s11, s12, s22);
   const float tr = s11 + s22;
-  float a = 0.0f, v = 1.0f;
+  float a = 0.0f, v = 1.0f, da = 0.0f, dv = 0.0f;   // da, dv: d a / dn, d v / dn
   if (lane < KMAX) {
     if (P->n_nodes == 1) {
       a = P->amp[0][lane];
       v = expf(P->logv[0][lane]);
     } else {
-      float u = (sn - P->n0) * P->inv_dn;
-      u = fminf(fmaxf(u, 0.0f), (float)(P->n_nodes - 1));
+      const float u0 = (sn - P->n0) * P->inv_dn;
+      const bool inside = u0 >= 0.0f && u0 <= (float)(P->n_nodes - 1);
+      const float u = fminf(fmaxf(u0, 0.0f), (float)(P->n_nodes - 1));
       int j = min((int)u, P->n_nodes - 2);
       float t = u - (float)j;
       a = (1.0f - t) * P->amp[j][lane] + t * P->amp[j + 1][lane];
       v = expf((1.0f - t) * P->logv[j][lane] + t * P->logv[j + 1][lane]);
+      if (inside) {
+        da = (P->amp[j + 1][lane] - P->amp[j][lane]) * P->inv_dn;
+        dv = v * (P->logv[j + 1][lane] - P->logv[j][lane]) * P->inv_dn;
+      }
     }
   }
   const float ns = 0.5f * (float)n * rsqrtf(v * tr);
   const float wf = ramp_weight(ns);
   const float dwf = ramp_slope(ns);
-  const bool four = lane < KMAX && a > 0.0f && wf > 0.0f;
-  const bool real = lane < KMAX && a > 0.0f && wf < 1.0f;
+  // a slot with a = 0 whose amplitude grows with n still has a derivative
+  const bool act = lane < KMAX && (a > 0.0f || da != 0.0f);
+  const bool four = act && wf > 0.0f;
+  const bool real = act && wf < 1.0f;
+  const float dnsdn = -0.5f * ns / v * dv;   // d n_sigma / dn
   const unsigned mf = __ballot_sync(0xffffffffu, four);
   const unsigned mr = __ballot_sync(0xffffffffu, real);
   const unsigned lt = (1u << lane) - 1u;
@@ -665,6 +676,8 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
     out->fcoef[p] = -2.0f * PI_F * PI_F * v * LOG2E;
     out->fq[p] = -2.0f * PI_F * PI_F * v * fa;
     out->fn[p] = flux * a * dwf * dns * inv_n2;
+    out->fdn[p] = flux * inv_n2 * (da * wf + a * dwf * dnsdn);
+    out->fdq[p] = flux * inv_n2 * a * wf * (-2.0f * PI_F * PI_F) * dv;
   }
   if (real) {
     const int p = __popc(mr & lt);
@@ -672,6 +685,8 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
     out->rw[p] = 1.0f - wf;
     out->rn[p] = -dwf * dns;
     out->rvar[p] = v;
+    out->rda[p] = flux * (da * (1.0f - wf) - a * dwf * dnsdn);
+    out->rdv[p] = 0.5f * flux * a * (1.0f - wf) * dv;
   }
   if (lane == 0) {
     out->ok = 1;
@@ -783,6 +798,7 @@ struct AdjTerms {
   float base[RMAX], wr[RMAX], rn[RMAX], v[RMAX];
   float i11[RMAX], i12[RMAX], i22[RMAX], mx[RMAX], my[RMAX];
   float qa[RMAX], qb[RMAX], qc[RMAX];
+  float dna[RMAX], dnv[RMAX], trs[RMAX];   // d/dn: amplitude, variance factor, tr(Sigma^-1 S)
 };
 
 // Real-space term t = c * kpsf + j of the adjoint record (one thread).
@@ -794,7 +810,11 @@ __device__ __forceinline__ void adj_real_term(const AdjRecord& r, const float (*
   const float vxx = v * r.s11 + m[3], vxy = v * r.s12 + m[4], vyy = v * r.s22 + m[5];
   const float det = vxx * vyy - vxy * vxy;
   const float idet = 1.0f / det;
-  at->base[t] = r.rbase[c] * m[0] * rsqrtf(det) * (0.5f / PI_F);
+  const float norm = m[0] * rsqrtf(det) * (0.5f / PI_F);
+  at->base[t] = r.rbase[c] * norm;
+  at->dna[t] = r.rda[c] * norm;
+  at->dnv[t] = r.rdv[c] * norm;
+  at->trs[t] = (vyy * r.s11 - 2.0f * vxy * r.s12 + vxx * r.s22) * idet;
   at->wr[t] = r.rw[c];
   at->rn[t] = r.rn[c];
   at->v[t] = v;
@@ -823,11 +843,12 @@ __device__ __forceinline__ void contract_bin(float2 z, float nu, float om, float
 // Real-space part of the adjoint over all pixels of an N x N patch (g read
 // from `gp`, shared or global memory); the x and y sums are divided by 2 pi
 // because the caller multiplies the total by 2 pi.
-template <int N>
+// WN: also the Sersic-index sum acc[6], with S = (s11, s12, s22).
+template <int N, bool WN = false>
 __device__ __forceinline__ void adj_real_space(const float* gp, const AdjTerms& at, int nr, int tid, int nthreads,
-                                               float* acc) {
+                                               float* acc, float s11 = 0.f, float s12 = 0.f, float s22 = 0.f) {
   if (nr <= 0) return;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f;
   for (int pix = tid; pix < N * N; pix += nthreads) {
     const float gw = gp[pix];
     if (gw == 0.0f) continue;
@@ -835,9 +856,14 @@ __device__ __forceinline__ void adj_real_space(const float* gp, const AdjTerms& 
     for (int t = 0; t < nr; ++t) {
       const float dx = xx - at.mx[t], dy = yy - at.my[t];
       const float e0 = fmaf(dx, fmaf(at.qa[t], dx, at.qb[t] * dy), at.qc[t] * dy * dy);
-      const float n = gw * at.base[t] * ex2(e0);
+      const float ge = gw * ex2(e0);
+      const float n = ge * at.base[t];
       const float ux = fmaf(at.i11[t], dx, at.i12[t] * dy);
       const float uy = fmaf(at.i12[t], dx, at.i22[t] * dy);
+      if constexpr (WN) {
+        const float usu = fmaf(s11 * ux, ux, fmaf(2.0f * s12 * ux, uy, s22 * uy * uy));
+        a6 = fmaf(ge, fmaf(at.dnv[t], usu - at.trs[t], at.dna[t]), a6);
+      }
       const float nw = n * at.wr[t];
       const float nv = nw * at.v[t];
       const float rr = n * at.rn[t];
@@ -856,6 +882,7 @@ __device__ __forceinline__ void adj_real_space(const float* gp, const AdjTerms& 
   acc[3] += a3;
   acc[4] += a4;
   acc[5] += a5;
+  if constexpr (WN) acc[6] += a6;
 }
 
 }  // namespace mog

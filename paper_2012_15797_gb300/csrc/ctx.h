@@ -74,6 +74,7 @@ mog_status check_batch(mog_ctx* ctx, const mog_batch* batch);
 mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s,
                        bool lanczos = false, bool add = false);
 mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, const float* grad_out,
-                         float* grad_params, cudaStream_t s);
+                         float* grad_params, cudaStream_t s,
+                         bool grad_n = false);
 
 }  // namespace mog

@@ -26,6 +26,7 @@ struct RenderParams {
   float* pcoef = nullptr;       // PCOEF floats per planned position (eigen-PSF terms and mixture weights)
   int eigen = 0;                // 1: some PSF of the context is an eigen-PSF (launch the kernels that handle it)
   int accumulate = 0;           // 1: add the model to the patch instead of writing it
+  int grad_n = 0;               // adjoint: 1 = also d/d(Sersic n), 7 gradients per galaxy
   float2* scratch256 = nullptr; // accumulate, N = 256: per-CTA transform intermediate (N/2 x N complex)
 };
 

@@ -81,7 +81,8 @@ __device__ __forceinline__ void fft_rest_b(float2* w, int j, const float2* tw1, 
   }
 }
 
-template <int N>
+// WN: also d L / d(Sersic n), a seventh gradient per galaxy.
+template <int N, bool WN>
 __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     render_bwd_kernel(RenderParams p, const float* __restrict__ grad_out, float* __restrict__ grad_params) {
   using C = BwdCfg<N>;
@@ -195,12 +196,13 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
           const int l = i - C::H - N;
           const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
           const float q = fmaf(om, fmaf(r.s22, om, r.s12), 0.25f * r.s11);
-          float s = 0.0f, sq = 0.0f, sn2 = 0.0f;
+          float s = 0.0f, sq = 0.0f, sn2 = 0.0f, sd = 0.0f;
           for (int c = 0; c < r.nf; ++c) {
             const float e = ex2(r.fcoef[c] * q);
             s = fmaf(r.famp[c], e, s);
             sq = fmaf(r.fq[c], e, sq);
             sn2 = fmaf(r.fn[c], e, sn2);
+            if constexpr (WN) sd = fmaf(fmaf(r.fdq[c], q, r.fdn[c]), e, sd);
           }
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
@@ -209,6 +211,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
           nys[4 * l + 0] = s;
           nys[4 * l + 1] = sq;
           nys[4 * l + 2] = sn2;
+          nys[4 * l + 3] = sd;
         } else {
           adj_real_term(r, s_psf_mog, kp, N, i - C::H - 2 * N, &at);
         }
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
       return;
     }
 
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float2 v[8];
     // ---- forward FFT of row pairs (2f, 2f+1) packed as g[2f] + i g[2f+1] ----
     {
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     }
 
     // ---- real-space terms: analytic derivatives, pixel by pixel ----
-    adj_real_space<N>(gbuf, at, r.nrc * s_kpsf, tid, C::THREADS, acc);
+    adj_real_space<N, WN>(gbuf, at, r.nrc * s_kpsf, tid, C::THREADS, acc, r.s11, r.s12, r.s22);
     __syncthreads();  // S3: every column input written
 
     // ---- forward FFT of every column along y ----
@@ -299,26 +302,30 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
             gn = make_float2(0.5f * di, -0.5f * dr);
           }
           const float qv = fmaf(om, fmaf(s22, om, a1), a0);
-          float s = 0.0f, sq = 0.0f, sn = 0.0f;
+          float s = 0.0f, sq = 0.0f, sn = 0.0f, sd = 0.0f;
           for (int c = 0; c < nf; ++c) {
             const float e = ex2(r.fcoef[c] * qv);
             s = fmaf(r.famp[c], e, s);
             sq = fmaf(r.fq[c], e, sq);
             sn = fmaf(r.fn[c], e, sn);
+            if constexpr (WN) sd = fmaf(fmaf(r.fdq[c], qv, r.fdn[c]), e, sd);
           }
           const float2 bph = cmul(psf_hat[f * LS + l], cmul(pxf, py[l]));
           const float2 z = cscale(cmulc(bph, gk), ck);   // c_k conj(G) P phase
           contract_bin(z, nu, om, s, sq, sn, acc);
+          if constexpr (WN) acc[6] = fmaf(z.x, sd, acc[6]);
           if (f == 0) {
             const float2 zn = cmulc(nyb[l], gn);
             contract_bin(zn, 0.5f, om, nys[4 * l], nys[4 * l + 1], nys[4 * l + 2], acc);
+            if constexpr (WN) acc[6] = fmaf(zn.x, nys[4 * l + 3], acc[6]);
           }
         }
     }
 
-    // ---- reduce the six sums over the CTA and apply the chain rule ----
+    // ---- reduce the sums over the CTA and apply the chain rule ----
+    constexpr int NACC = WN ? 7 : 6;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NACC; ++k) {
       float x = acc[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -326,10 +333,11 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     }
     __syncthreads();  // S4
     if (tid == 0) {
-      float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float t[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       for (int w = 0; w < C::WARPS; ++w)
-        for (int k = 0; k < 6; ++k) t[k] += red[w * 8 + k];
-      float* out = grad_params + r.gal * 6;
+        for (int k = 0; k < NACC; ++k) t[k] += red[w * 8 + k];
+      float* out = grad_params + r.gal * NACC;
+      if constexpr (WN) out[6] = t[6];
       out[0] = t[0] / r.flux;
       out[1] = TWO_PI * t[1];
       out[2] = TWO_PI * t[2];
@@ -339,29 +347,37 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
   }
 }
 
-template <int N>
+template <int N, bool WN = false>
 static int bwd_occupancy() {
   using C = BwdCfg<N>;
   static int occ = -1;
   if (occ < 0) {
-    if (cudaFuncSetAttribute(render_bwd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
+    if (cudaFuncSetAttribute(render_bwd_kernel<N, WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_bwd_kernel<N>, C::THREADS, C::SMEM) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_bwd_kernel<N, WN>, C::THREADS, C::SMEM) !=
+            cudaSuccess)
       return -1;
     if (occ < 1) occ = 1;
   }
   return occ;
 }
 
+template <int N, bool WN>
+static cudaError_t launch_bwd_mode(const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
+                                   int ctas_per_sm, cudaStream_t s) {
+  using C = BwdCfg<N>;
+  const int occ = bwd_occupancy<N, WN>();
+  if (occ < 0) return cudaErrorInvalidConfiguration;
+  const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+  render_bwd_kernel<N, WN><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p, grad_out, grad_params);
+  return cudaGetLastError();
+}
+
 template <int N>
 static cudaError_t launch_bwd(const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
                               int ctas_per_sm, cudaStream_t s) {
-  using C = BwdCfg<N>;
-  const int occ = bwd_occupancy<N>();
-  if (occ < 0) return cudaErrorInvalidConfiguration;
-  const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_bwd_kernel<N><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p, grad_out, grad_params);
-  return cudaGetLastError();
+  return p.grad_n ? launch_bwd_mode<N, true>(p, grad_out, grad_params, num_sms, ctas_per_sm, s)
+                  : launch_bwd_mode<N, false>(p, grad_out, grad_params, num_sms, ctas_per_sm, s);
 }
 
 int render_bwd_max_ctas(int n) {

@@ -47,6 +47,7 @@ constexpr size_t off_red = off_terms + sizeof(AdjTerms);
 constexpr size_t off_bar = (off_red + sizeof(float) * 8 * WARPS + 15) & ~size_t(15);
 constexpr size_t SMEM = off_bar + 2 * sizeof(uint64_t);
 
+template <bool WN>   // WN: also d L / d(Sersic n), a seventh gradient per galaxy
 __global__ void __launch_bounds__(THREADS, 1)
     render_bwd256_kernel(RenderParams p, const float* __restrict__ grad_out, float* __restrict__ grad_params,
                          float2* __restrict__ scratch_all) {
@@ -144,12 +145,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int l = i - H - N;
           const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
           const float q = fmaf(om, fmaf(r.s22, om, r.s12), 0.25f * r.s11);
-          float s = 0.0f, sq = 0.0f, sn2 = 0.0f;
+          float s = 0.0f, sq = 0.0f, sn2 = 0.0f, sd = 0.0f;
           for (int c = 0; c < r.nf; ++c) {
             const float e = ex2(r.fcoef[c] * q);
             s = fmaf(r.famp[c], e, s);
             sq = fmaf(r.fq[c], e, sq);
             sn2 = fmaf(r.fn[c], e, sn2);
+            if constexpr (WN) sd = fmaf(fmaf(r.fdq[c], q, r.fdn[c]), e, sd);
           }
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           nys[4 * l + 0] = s;
           nys[4 * l + 1] = sq;
           nys[4 * l + 2] = sn2;
+          nys[4 * l + 3] = sd;
         } else {
           adj_real_term(r, s_psf_mog, kp, N, i - H - 2 * N, &at);
         }
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncthreads();
 
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float2 v[8];
     // ---- rows: forward FFT of row pairs, untangled, staged, written to scratch ----
     for (int round = 0; round < ROUNDS; ++round) {
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 
     // ---- real-space terms ----
-    adj_real_space<N>(gpatch, at, r.nrc * s_kpsf, tid, THREADS, acc);
+    adj_real_space<N, WN>(gpatch, at, r.nrc * s_kpsf, tid, THREADS, acc, r.s11, r.s12, r.s22);
     __syncthreads();   // scratch complete and visible
 
     // ---- columns: forward FFT along y, contraction ----
@@ -252,23 +255,31 @@ __global__ void __launch_bounds__(THREADS, 1)
             gn = make_float2(0.5f * (u.y + un.y), -0.5f * (u.x - un.x));
           }
           const float qv = fmaf(om, fmaf(s22, om, a1), a0);
-          float s = 0.0f, sq = 0.0f, sn = 0.0f;
+          float s = 0.0f, sq = 0.0f, sn = 0.0f, sd = 0.0f;
           for (int c = 0; c < nf; ++c) {
             const float e = ex2(r.fcoef[c] * qv);
             s = fmaf(r.famp[c], e, s);
             sq = fmaf(r.fq[c], e, sq);
             sn = fmaf(r.fn[c], e, sn);
+            if constexpr (WN) sd = fmaf(fmaf(r.fdq[c], qv, r.fdn[c]), e, sd);
           }
           const float2 bph = cmul(__ldg(&psf_hat[k * LS + l]), cmul(pxk, py[l]));
-          contract_bin(cscale(cmulc(bph, gk), ck), nu, om, s, sq, sn, acc);
-          if (k == 0) contract_bin(cmulc(nyb[l], gn), 0.5f, om, nys[4 * l], nys[4 * l + 1], nys[4 * l + 2], acc);
+          const float2 z = cscale(cmulc(bph, gk), ck);
+          contract_bin(z, nu, om, s, sq, sn, acc);
+          if constexpr (WN) acc[6] = fmaf(z.x, sd, acc[6]);
+          if (k == 0) {
+            const float2 zn = cmulc(nyb[l], gn);
+            contract_bin(zn, 0.5f, om, nys[4 * l], nys[4 * l + 1], nys[4 * l + 2], acc);
+            if constexpr (WN) acc[6] = fmaf(zn.x, nys[4 * l + 3], acc[6]);
+          }
         }
       __syncwarp();
     }
 
     // ---- reduce and chain rule ----
+    constexpr int NACC = WN ? 7 : 6;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < NACC; ++c) {
       float x = acc[c];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -276,10 +287,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     __syncthreads();
     if (tid == 0) {
-      float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float t[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       for (int ww = 0; ww < WARPS; ++ww)
-        for (int c = 0; c < 6; ++c) t[c] += red[ww * 8 + c];
-      float* out = grad_params + r.gal * 6;
+        for (int c = 0; c < NACC; ++c) t[c] += red[ww * 8 + c];
+      float* out = grad_params + r.gal * NACC;
+      if constexpr (WN) out[6] = t[6];
       out[0] = t[0] / r.flux;
       out[1] = TWO_PI * t[1];
       out[2] = TWO_PI * t[2];
@@ -297,11 +309,17 @@ cudaError_t launch_render_bwd256(const RenderParams& p, const float* grad_out, f
                                  int num_sms, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(render_bwd256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaError_t e = cudaFuncSetAttribute(render_bwd256_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(render_bwd256_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  render_bwd256_kernel<<<num_sms, THREADS, SMEM, s>>>(p, grad_out, grad_params, scratch);
+  if (p.grad_n)
+    render_bwd256_kernel<true><<<num_sms, THREADS, SMEM, s>>>(p, grad_out, grad_params, scratch);
+  else
+    render_bwd256_kernel<false><<<num_sms, THREADS, SMEM, s>>>(p, grad_out, grad_params, scratch);
   return cudaGetLastError();
 }
 

@@ -127,14 +127,20 @@ class Renderer:
         out = self.render(disk, out, stream, shift)
         return self.render(bulge, out, stream, shift, add=True)
 
-    def render_backward(self, batch, grad_out, grad_params=None, stream=None):
+    def render_backward(self, batch, grad_out, grad_params=None, stream=None, sersic=False):
         """Gradients (count, 6) of L w.r.t. (flux, x, y, log_re, e1, e2)
-        given grad_out = dL/d(packed output)."""
+        given grad_out = dL/d(packed output); with ``sersic`` (count, 7), the
+        last column d L / d sersic_n."""
+        k = 7 if sersic else 6
         if grad_params is None:
-            grad_params = torch.empty(batch.count, 6, dtype=torch.float32, device=self.device)
+            grad_params = torch.empty(batch.count, k, dtype=torch.float32, device=self.device)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
-        capi.mog_render_backward(self.ctx, b, grad_out.data_ptr(), grad_params.data_ptr(), s.cuda_stream)
+        if sersic:
+            capi.mog_render_backward_ex(self.ctx, b, grad_out.data_ptr(), grad_params.data_ptr(), s.cuda_stream,
+                                        capi.MOG_GRAD_SERSIC)
+        else:
+            capi.mog_render_backward(self.ctx, b, grad_out.data_ptr(), grad_params.data_ptr(), s.cuda_stream)
         return grad_params
 
     def autotune(self, batch, out, grad_out=None, grad_params=None, reps=3, stream=None):
