@@ -461,6 +461,33 @@ def extra_composite(tables, psf, device, steps):
             "value": len(disk) / (ms / 1e3), "unit": "composite patches/s", "ms_per_step": ms}
 
 
+def extra_sersic_grad(tables, device, steps):
+    """The 200k mixed-size Sersic batch: the adjoint (6 gradients per galaxy)
+    and the adjoint with d L / d sersic_n (7 gradients)."""
+    import torch
+    from paper_2012_15797_gb300.renderer import Renderer, to_device
+    from workloads import config2_galaxies, config2_psfs
+
+    gals = config2_galaxies(200_000)
+    r = Renderer(tables, config2_psfs(64), device=device)
+    b = to_device(gals, device=f"cuda:{device}")
+    go = torch.randn(b.total, device=f"cuda:{device}")
+    g6 = torch.empty(len(gals), 6, device=f"cuda:{device}")
+    g7 = torch.empty(len(gals), 7, device=f"cuda:{device}")
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        r.render_backward(b, go, g6)
+        r.render_backward(b, go, g7, sersic=True)
+    r.sync_status()
+    ms6 = _event_ms(lambda: r.render_backward(b, go, g6), steps, st)
+    ms7 = _event_ms(lambda: r.render_backward(b, go, g7, sersic=True), steps, st)
+    r.sync_status()
+    r.close()
+    return {"workload": "200000 galaxies as the mixed-size batch, adjoint only",
+            "ms_grad6": ms6, "ms_grad7_with_sersic_n": ms7, "value": len(gals) / (ms7 / 1e3),
+            "unit": "patches grad (7 gradients)/s"}
+
+
 def extra_per_galaxy(tables, psf, device, n=2000):
     """The plain form: the same math with one library call (planner, record,
     render launches) per galaxy."""
@@ -686,6 +713,7 @@ def run_ours(args):
                  "lanczos_shift": extra_lanczos(tables, psf, local, args.extra_steps),
                  "eigen_psf": extra_eigen(tables, psf, local, args.extra_steps),
                  "composite": extra_composite(tables, psf, local, args.extra_steps),
+                 "sersic_gradient": extra_sersic_grad(tables, local, args.extra_steps),
                  "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local),
                  "serving": extra_serving(tables, local)}
 
