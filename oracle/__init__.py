@@ -14,6 +14,7 @@ Modules:
               convolution of the final model,
   eigenpsf.py rendering with a spatially varying (eigen-)PSF (Step 2),
   composite.py bulge + disk composites (the sum of two profiles' models),
+  psf_fit.py  least-squares Gaussian-mixture fits of pixelized PSFs,
   adjoint.py  analytic derivatives of the forward model w.r.t.
               (flux, x, y, log r_e, e1, e2) and a central finite-difference
               check,
