@@ -251,6 +251,24 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
  * Other arguments and errors as mog_render_backward.
  */
 enum { MOG_GRAD_SERSIC = 1 };
+
+/*
+ * Fits a k-component Gaussian mixture (1 <= k <= 4) to each of `count`
+ * pixelized PSFs on the device: the mixture the real-space half convolves
+ * with (Section 2, Step 4; the chi-squared fit of Section 1).  images: device
+ * float32 [count][h][w], centre at (h/2, w/2).  Minimises
+ * sum_p (sum_j w_j N(p - c - m_j; V_j) - image[p])^2 by Levenberg-Marquardt
+ * (at most `iters` iterations, stopping earlier when chi^2 stalls) from a
+ * start set by the image's sum and second moment (widths s x 0.6, 1.1, 2.2,
+ * 4.0, weights 0.55, 0.35, 0.08, 0.015 of the sum); w_j > 0 and V_j positive
+ * definite by construction.  Writes rows[count][k][6] = (w, mean_x, mean_y,
+ * var_xx, var_xy, var_yy), decreasing weight, means relative to the centre:
+ * the layout mog_create_psf takes; chi2[count] (optional) the final chi^2.
+ * Device outputs; asynchronous on `stream`.  A local fit: the result is the
+ * minimum reached from that start.
+ */
+mog_status mog_fit_psf_mixture(mog_ctx* ctx, const float* images, int count, int h, int w, int k, int iters,
+                               float* rows, float* chi2, void* stream);
 mog_status mog_render_backward_ex(mog_ctx* ctx, const mog_batch* batch, const float* grad_out,
                                   float* grad_params, void* stream, unsigned flags);
 

@@ -35,7 +35,7 @@ EXPORTED = (
     "mog_autotune", "mog_graph_capture", "mog_graph_launch", "mog_graph_destroy",
     "mog_server_create", "mog_server_add_fit", "mog_server_submit", "mog_server_wait", "mog_server_replay",
     "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
-    "mog_create_eigen_psf", "mog_render_batch_ex", "mog_render_backward_ex",
+    "mog_create_eigen_psf", "mog_render_batch_ex", "mog_render_backward_ex", "mog_fit_psf_mixture",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -92,6 +92,7 @@ def _load():
         "mog_render_batch_ex": ([VP, P(mog_batch), VP, VP, ctypes.c_uint], I),
         "mog_render_backward": ([VP, P(mog_batch), VP, VP, VP], I),
         "mog_render_backward_ex": ([VP, P(mog_batch), VP, VP, VP, ctypes.c_uint], I),
+        "mog_fit_psf_mixture": ([VP, VP, I, I, I, I, I, VP, VP, VP], I),
         "mog_render_batch_noalloc": ([VP, P(mog_batch), VP, VP], I),
         "mog_autotune": ([VP, P(mog_batch), VP, VP, VP, VP, I, P(I)], I),
         "mog_graph_capture": ([VP, P(mog_batch), VP, P(VP)], I),
@@ -234,6 +235,13 @@ def mog_render_backward_ex(ctx, batch, grad_out_ptr, grad_params_ptr, stream=0, 
     _check(ctx, _lib.mog_render_backward_ex(ctx, ctypes.byref(batch), ctypes.c_void_p(int(grad_out_ptr)),
                                             ctypes.c_void_p(int(grad_params_ptr)), ctypes.c_void_p(int(stream)),
                                             ctypes.c_uint(int(flags))))
+
+
+def mog_fit_psf_mixture(ctx, images_ptr, count, h, w, k, iters, rows_ptr, chi2_ptr=0, stream=0):
+    _check(ctx, _lib.mog_fit_psf_mixture(ctx, ctypes.c_void_p(int(images_ptr)), int(count), int(h), int(w), int(k),
+                                         int(iters), ctypes.c_void_p(int(rows_ptr)),
+                                         ctypes.c_void_p(int(chi2_ptr)) if chi2_ptr else None,
+                                         ctypes.c_void_p(int(stream))))
 
 
 def mog_autotune(ctx, batch, out_ptr, grad_out_ptr=0, grad_params_ptr=0, stream=0, reps=3):

@@ -480,6 +480,19 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
   return backward_with(ctx, &ctx->ws, batch, grad_out, grad_params, static_cast<cudaStream_t>(stream));
 }
 
+mog_status mog_fit_psf_mixture(mog_ctx* ctx, const float* images, int count, int h, int w, int k, int iters,
+                               float* rows, float* chi2, void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  if (count < 0 || (count > 0 && (!images || !rows))) return fail(ctx, MOG_ERR_ARG, "bad PSF fit buffers");
+  if (h < 1 || w < 1 || h > 4096 || w > 4096) return fail(ctx, MOG_ERR_ARG, "PSF images must be 1..4096 on a side");
+  if (k < 1 || k > KPSF) return fail(ctx, MOG_ERR_ARG, "PSF mixture needs 1..%d components", KPSF);
+  if (iters < 1 || iters > 100000) return fail(ctx, MOG_ERR_ARG, "iterations must be 1..100000");
+  if (count == 0) return MOG_OK;
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  MOG_CUDA(ctx, launch_psf_fit(images, count, h, w, k, iters, rows, chi2, static_cast<cudaStream_t>(stream)));
+  return MOG_OK;
+}
+
 mog_status mog_render_backward_ex(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,
                                   void* stream, unsigned flags) {
   if (!ctx) return MOG_ERR_ARG;

@@ -82,6 +82,10 @@ size_t render_fwd_smem(int n);
 
 // Spectrum of a PSF embedded with its centre at (n/2, n/2), written in the
 // psf_lstride layout.  `pix` is device memory (h x w float).
+// Gaussian-mixture fits of `count` h x w PSF images (psf_fit.cu).
+cudaError_t launch_psf_fit(const float* images, int count, int h, int w, int k, int iters, float* rows,
+                           float* chi2, cudaStream_t s);
+
 cudaError_t launch_psf_spectrum(const float* pix, int h, int w, int n, double2* scratch, float2* spec,
                                 cudaStream_t s);
 

@@ -143,6 +143,18 @@ class Renderer:
             capi.mog_render_backward(self.ctx, b, grad_out.data_ptr(), grad_params.data_ptr(), s.cuda_stream)
         return grad_params
 
+    def fit_psf_mixtures(self, images, k=3, iters=400, stream=None):
+        """Gaussian-mixture fits of a (count, h, w) float32 device tensor of
+        PSF images: returns ((count, k, 6) rows, (count,) chi^2)."""
+        images = images.contiguous()
+        count, h, w = images.shape
+        rows = torch.empty(count, k, 6, dtype=torch.float32, device=self.device)
+        chi2 = torch.empty(count, dtype=torch.float32, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        capi.mog_fit_psf_mixture(self.ctx, images.data_ptr(), count, h, w, k, iters, rows.data_ptr(), chi2.data_ptr(),
+                                 s.cuda_stream)
+        return rows, chi2
+
     def autotune(self, batch, out, grad_out=None, grad_params=None, reps=3, stream=None):
         """Times every launch shape per size bucket and keeps the fastest
         (forward, and the adjoint when gradient buffers are given)."""
