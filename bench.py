@@ -488,6 +488,26 @@ def extra_sersic_grad(tables, device, steps):
             "unit": "patches grad (7 gradients)/s"}
 
 
+def extra_psf_fit(tables, device):
+    """3-component Gaussian-mixture fits of the 64 Moffat-winged 64x64 PSFs
+    of the mixed workload on the device (mog_fit_psf_mixture, 400 iterations
+    at most)."""
+    import numpy as np
+    import torch
+    from paper_2012_15797_gb300.renderer import Renderer
+    from workloads import config2_psfs
+
+    imgs = torch.from_numpy(np.stack([p.image for p in config2_psfs(64, fit=False)])).cuda(device)
+    r = Renderer(tables, [], device=device)
+    r.fit_psf_mixtures(imgs)
+    torch.cuda.synchronize()
+    ms = _event_ms(lambda: r.fit_psf_mixtures(imgs), 3, torch.cuda.current_stream())
+    r.sync_status()
+    r.close()
+    return {"workload": "64 PSFs of 64x64 (2-Gaussian core + Moffat wings), k = 3", "ms_per_call": ms,
+            "value": 64 / (ms / 1e3), "unit": "PSF fits/s"}
+
+
 def extra_per_galaxy(tables, psf, device, n=2000):
     """The plain form: the same math with one library call (planner, record,
     render launches) per galaxy."""
@@ -714,6 +734,7 @@ def run_ours(args):
                  "eigen_psf": extra_eigen(tables, psf, local, args.extra_steps),
                  "composite": extra_composite(tables, psf, local, args.extra_steps),
                  "sersic_gradient": extra_sersic_grad(tables, local, args.extra_steps),
+                 "psf_fit": extra_psf_fit(tables, local),
                  "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local),
                  "serving": extra_serving(tables, local)}
 
