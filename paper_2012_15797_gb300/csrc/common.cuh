@@ -799,6 +799,8 @@ struct AdjTerms {
   float i11[RMAX], i12[RMAX], i22[RMAX], mx[RMAX], my[RMAX];
   float qa[RMAX], qb[RMAX], qc[RMAX];
   float dna[RMAX], dnv[RMAX], trs[RMAX];   // d/dn: amplitude, variance factor, tr(Sigma^-1 S)
+  float rrr[RMAX];                        // 2^(2 qa): ratio step of neighbouring pixels along a row
+  float bw[RMAX], bwv[RMAX], brn[RMAX];   // base w_R, base w_R v, base rn
 };
 
 // Real-space term t = c * kpsf + j of the adjoint record (one thread).
@@ -824,6 +826,10 @@ __device__ __forceinline__ void adj_real_term(const AdjRecord& r, const float (*
   at->qa[t] = -0.5f * LOG2E * vyy * idet;
   at->qb[t] = LOG2E * vxy * idet;
   at->qc[t] = -0.5f * LOG2E * vxx * idet;
+  at->rrr[t] = ex2(-LOG2E * vyy * idet);
+  at->bw[t] = at->base[t] * r.rw[c];
+  at->bwv[t] = at->base[t] * r.rw[c] * v;
+  at->brn[t] = at->base[t] * r.rn[c];
   at->mx[t] = 0.5f * (float)n + r.x + m[1];
   at->my[t] = 0.5f * (float)n + r.y + m[2];
 }
@@ -842,37 +848,59 @@ __device__ __forceinline__ void contract_bin(float2 z, float nu, float om, float
 
 // Real-space part of the adjoint over all pixels of an N x N patch (g read
 // from `gp`, shared or global memory); the x and y sums are divided by 2 pi
-// because the caller multiplies the total by 2 pi.
+// because the caller multiplies the total by 2 pi.  A thread takes runs of 8
+// consecutive pixels of a row; along the run a term's Gaussian follows the
+// two-step multiplicative recurrence of the forward store (2 ex2 per term and
+// run; terms are wide, so an underflowing start stays negligible over 7
+// pixels) and u = Sigma^-1 d moves by (i11, i12) per pixel, so the pixel loop
+// only gathers the moments sum g E (1, ux, uy, ux^2, ux uy, uy^2); every
+// derivative of the term is a combination of those six.
 // WN: also the Sersic-index sum acc[6], with S = (s11, s12, s22).
 template <int N, bool WN = false>
 __device__ __forceinline__ void adj_real_space(const float* gp, const AdjTerms& at, int nr, int tid, int nthreads,
                                                float* acc, float s11 = 0.f, float s12 = 0.f, float s22 = 0.f) {
   if (nr <= 0) return;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f;
-  for (int pix = tid; pix < N * N; pix += nthreads) {
-    const float gw = gp[pix];
-    if (gw == 0.0f) continue;
-    const float xx = (float)(pix % N), yy = (float)(pix / N);
+  for (int run = tid; run < N * N / 8; run += nthreads) {
+    const int pix0 = run * 8;
+    const float yy = (float)(pix0 / N), x0 = (float)(pix0 % N);
+    const float4 ga = *reinterpret_cast<const float4*>(gp + pix0);
+    const float4 gb = *reinterpret_cast<const float4*>(gp + pix0 + 4);
+    const float gw[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
     for (int t = 0; t < nr; ++t) {
-      const float dx = xx - at.mx[t], dy = yy - at.my[t];
-      const float e0 = fmaf(dx, fmaf(at.qa[t], dx, at.qb[t] * dy), at.qc[t] * dy * dy);
-      const float ge = gw * ex2(e0);
-      const float n = ge * at.base[t];
-      const float ux = fmaf(at.i11[t], dx, at.i12[t] * dy);
-      const float uy = fmaf(at.i12[t], dx, at.i22[t] * dy);
-      if constexpr (WN) {
-        const float usu = fmaf(s11 * ux, ux, fmaf(2.0f * s12 * ux, uy, s22 * uy * uy));
-        a6 = fmaf(ge, fmaf(at.dnv[t], usu - at.trs[t], at.dna[t]), a6);
+      const float dx = x0 - at.mx[t], dy = yy - at.my[t];
+      const float qa = at.qa[t], ly = at.qb[t] * dy;
+      float e = ex2(fmaf(dx, fmaf(qa, dx, ly), at.qc[t] * dy * dy));
+      float rr = ex2(fmaf(qa, fmaf(2.0f, dx, 1.0f), ly));
+      const float r8 = at.rrr[t], i11 = at.i11[t], i12 = at.i12[t], i22 = at.i22[t];
+      float ux = fmaf(i11, dx, i12 * dy), uy = fmaf(i12, dx, i22 * dy);
+      float m0 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float ge = gw[u] * e;
+        const float gx = ge * ux, gy = ge * uy;
+        m0 += ge;
+        mx += gx;
+        my += gy;
+        mxx = fmaf(gx, ux, mxx);
+        mxy = fmaf(gx, uy, mxy);
+        myy = fmaf(gy, uy, myy);
+        e *= rr;
+        rr *= r8;
+        ux += i11;
+        uy += i12;
       }
-      const float nw = n * at.wr[t];
-      const float nv = nw * at.v[t];
-      const float rr = n * at.rn[t];
-      a0 += nw;
-      a1 = fmaf(nw, ux, a1);
-      a2 = fmaf(nw, uy, a2);
-      a3 = fmaf(nv, 0.5f * fmaf(ux, ux, -at.i11[t]), a3 + rr);
-      a4 = fmaf(nv, fmaf(ux, uy, -at.i12[t]), a4);
-      a5 = fmaf(nv, 0.5f * fmaf(uy, uy, -at.i22[t]), a5 + rr);
+      const float bw = at.bw[t], bwv = at.bwv[t], brn = at.brn[t];
+      a0 = fmaf(bw, m0, a0);
+      a1 = fmaf(bw, mx, a1);
+      a2 = fmaf(bw, my, a2);
+      a3 = fmaf(bwv, 0.5f * fmaf(-i11, m0, mxx), fmaf(brn, m0, a3));
+      a4 = fmaf(bwv, fmaf(-i12, m0, mxy), a4);
+      a5 = fmaf(bwv, 0.5f * fmaf(-i22, m0, myy), fmaf(brn, m0, a5));
+      if constexpr (WN) {
+        const float usu = fmaf(s11, mxx, fmaf(2.0f * s12, mxy, s22 * myy));
+        a6 = fmaf(at.dna[t], m0, fmaf(at.dnv[t], fmaf(-at.trs[t], m0, usu), a6));
+      }
     }
   }
   constexpr float INV_2PI = 0.15915494309189535f;
