@@ -233,8 +233,8 @@ mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float*
  * the real-space part differentiates the Gaussian terms in pixel space; the
  * aliasing ramp weights are differentiated too.  S(e1, e2) is not
  * differentiable at e = 0; there the direction e1/e = 1 is used.
- * Constant PSFs only: galaxies whose PSF is an eigen-PSF are skipped and
- * reported as MOG_ERR_DEVICE.  Asynchronous on `stream`.
+ * Eigen-PSFs are differentiated at each galaxy's fixed image position (the
+ * position is not a parameter).  Asynchronous on `stream`.
  */
 mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out,
                                float* grad_params, void* stream);

@@ -615,7 +615,7 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
   ok = ok && prof >= 0 && prof < MOG_MAX_PROFILES && pid >= 0 && pid < MOG_MAX_PSFS;
   const DevProfile* P = ok ? &profiles[prof] : nullptr;
   ok = ok && P->n_nodes > 0 && psfs[pid].k > 0;
-  ok = ok && psfs[pid].k_eig == 0;   // the adjoint takes constant PSFs only
+  ok = ok && (psfs[pid].k_eig == 0 || (b.img_x && b.img_y && isfinite(b.img_x[g]) && isfinite(b.img_y[g])));
   float cdm[4];
   ok = ok && wcs_matrix(b, g, cdm);
   const int64_t off = b.offset[g];

@@ -81,8 +81,10 @@ __device__ __forceinline__ void fft_rest_b(float2* w, int j, const float2* tw1, 
   }
 }
 
-// WN: also d L / d(Sersic n), a seventh gradient per galaxy.
-template <int N, bool WN>
+// WN: also d L / d(Sersic n), a seventh gradient per galaxy.  EIG: some PSF
+// of the context is an eigen-PSF (its spectrum at the galaxy's position is
+// formed per galaxy: in shared memory when N <= 64, bin by bin otherwise).
+template <int N, bool WN, bool EIG>
 __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     render_bwd_kernel(RenderParams p, const float* __restrict__ grad_out, float* __restrict__ grad_params) {
   using C = BwdCfg<N>;
@@ -109,14 +111,17 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
   __shared__ int s_pos[2];
   __shared__ float s_psf_mog[KPSF][6];
   __shared__ int s_kpsf;
+  __shared__ float s_eigm[KEIG];   // eigen-PSF terms of the current galaxy
 
   const int tid = threadIdx.x;
   const int f = tid / TPF, j = tid % TPF;
   const int lane = tid & 31, warp = tid >> 5;
+  int k_eig = 0;   // eigen components of the current galaxy's PSF (0: constant PSF)
   fill_twiddles<N, C::R1>(tw1, 8, tid, C::THREADS);
   if constexpr (Radix<N>::P == 3) fill_twiddles<N, C::R2>(tw2, N / C::R2, tid, C::THREADS);
   const int count = p.bucket_count[B];
-  const unsigned char* records = p.records + (size_t)p.bucket_start[B] * sizeof(AdjRecord);
+  const int first = p.bucket_start[B];
+  const unsigned char* records = p.records + (size_t)first * sizeof(AdjRecord);
   int q_next = 0, q_end = 0, q_ahead = 0;
   auto next_position = [&]() -> int {
     if (q_next >= q_end) {
@@ -158,18 +163,31 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     const bool need_psf = go && r.psf != cur_psf;
     bool psf_landed = true;
     if (need_psf) {
-      if constexpr (C::STAGE_PSF) {
-        if (tid == 0) bulk_load(psf_smem, p.psfs[r.psf].spec[B], sizeof(float2) * C::PSF_ELEMS, &bar[0]);
+      const DevPsf& ps = p.psfs[r.psf];
+      k_eig = EIG ? ps.k_eig : 0;
+      const float* pc = p.pcoef + ((size_t)first + pos) * PCOEF;
+      if (k_eig > 0) {
+        if constexpr (C::STAGE_PSF)
+          for (int e = tid; e < C::PSF_ELEMS; e += C::THREADS)
+            psf_smem[e] = eigen_bin(ps.spec[B], C::PSF_ELEMS, k_eig, pc, e);
+        else
+          psf_hat = ps.spec[B];
+        if (tid < KEIG) s_eigm[tid] = pc[tid];
+      } else if constexpr (C::STAGE_PSF) {
+        if (tid == 0) bulk_load(psf_smem, ps.spec[B], sizeof(float2) * C::PSF_ELEMS, &bar[0]);
       } else {
-        psf_hat = p.psfs[r.psf].spec[B];
+        psf_hat = ps.spec[B];
       }
-      if (tid < KPSF * 6) s_psf_mog[tid / 6][tid % 6] = p.psfs[r.psf].mog[tid / 6][tid % 6];
-      if (tid == 0) s_kpsf = p.psfs[r.psf].k;
+      if (tid < KPSF * 6)
+        s_psf_mog[tid / 6][tid % 6] = (k_eig > 0 && tid % 6 == 0) ? pc[8 + tid / 6] : ps.mog[tid / 6][tid % 6];
+      if (tid == 0) s_kpsf = ps.k;
       if constexpr (C::STAGE_PSF) {
-        psf_landed = mbar_wait(&bar[0], psf_parity);
-        psf_parity ^= 1u;
+        if (k_eig == 0) {
+          psf_landed = mbar_wait(&bar[0], psf_parity);
+          psf_parity ^= 1u;
+        }
       }
-      cur_psf = r.psf;
+      cur_psf = k_eig > 0 ? -1 : r.psf;   // an eigen-PSF is formed again for the next galaxy
     }
     if (__syncthreads_or(!rec_landed || !psf_landed)) {
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
@@ -207,7 +225,10 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
           sincospif(-gx, &sn, &cs);
-          nyb[l] = cmul(psf_hat[(N / 2) * LS + l], cmul(make_float2(cs, sn), make_float2(cy, sy)));
+          const float2 pn = (!C::STAGE_PSF && k_eig > 0)
+                                ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, (N / 2) * LS + l)
+                                : psf_hat[(N / 2) * LS + l];
+          nyb[l] = cmul(pn, cmul(make_float2(cs, sn), make_float2(cy, sy)));
           nys[4 * l + 0] = s;
           nys[4 * l + 1] = sq;
           nys[4 * l + 2] = sn2;
@@ -310,7 +331,9 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
             sn = fmaf(r.fn[c], e, sn);
             if constexpr (WN) sd = fmaf(fmaf(r.fdq[c], qv, r.fdn[c]), e, sd);
           }
-          const float2 bph = cmul(psf_hat[f * LS + l], cmul(pxf, py[l]));
+          const float2 pv = (!C::STAGE_PSF && k_eig > 0) ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, f * LS + l)
+                                                         : psf_hat[f * LS + l];
+          const float2 bph = cmul(pv, cmul(pxf, py[l]));
           const float2 z = cscale(cmulc(bph, gk), ck);   // c_k conj(G) P phase
           contract_bin(z, nu, om, s, sq, sn, acc);
           if constexpr (WN) acc[6] = fmaf(z.x, sd, acc[6]);
@@ -347,14 +370,14 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
   }
 }
 
-template <int N, bool WN = false>
+template <int N, bool WN = false, bool EIG = false>
 static int bwd_occupancy() {
   using C = BwdCfg<N>;
   static int occ = -1;
   if (occ < 0) {
-    if (cudaFuncSetAttribute(render_bwd_kernel<N, WN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_bwd_kernel<N, WN>, C::THREADS, C::SMEM) !=
+    if (cudaFuncSetAttribute(render_bwd_kernel<N, WN, EIG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)C::SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_bwd_kernel<N, WN, EIG>, C::THREADS, C::SMEM) !=
             cudaSuccess)
       return -1;
     if (occ < 1) occ = 1;
@@ -362,22 +385,25 @@ static int bwd_occupancy() {
   return occ;
 }
 
-template <int N, bool WN>
+template <int N, bool WN, bool EIG>
 static cudaError_t launch_bwd_mode(const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
                                    int ctas_per_sm, cudaStream_t s) {
   using C = BwdCfg<N>;
-  const int occ = bwd_occupancy<N, WN>();
+  const int occ = bwd_occupancy<N, WN, EIG>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_bwd_kernel<N, WN><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p, grad_out, grad_params);
+  render_bwd_kernel<N, WN, EIG><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p, grad_out, grad_params);
   return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t launch_bwd(const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
                               int ctas_per_sm, cudaStream_t s) {
-  return p.grad_n ? launch_bwd_mode<N, true>(p, grad_out, grad_params, num_sms, ctas_per_sm, s)
-                  : launch_bwd_mode<N, false>(p, grad_out, grad_params, num_sms, ctas_per_sm, s);
+  if (p.eigen)
+    return p.grad_n ? launch_bwd_mode<N, true, true>(p, grad_out, grad_params, num_sms, ctas_per_sm, s)
+                    : launch_bwd_mode<N, false, true>(p, grad_out, grad_params, num_sms, ctas_per_sm, s);
+  return p.grad_n ? launch_bwd_mode<N, true, false>(p, grad_out, grad_params, num_sms, ctas_per_sm, s)
+                  : launch_bwd_mode<N, false, false>(p, grad_out, grad_params, num_sms, ctas_per_sm, s);
 }
 
 int render_bwd_max_ctas(int n) {

@@ -28,6 +28,7 @@ constexpr int THREADS = 1024;
 constexpr int WARPS = THREADS / 32;
 constexpr int ROUNDS = (N / 2) / WARPS;   // 4
 constexpr int LS = psf_lstride(N);
+constexpr int PSF_ELEMS = psf_spec_elems(N);
 constexpr int WS = wstride<N>();
 constexpr int R1 = Radix<N>::r[1], R2 = Radix<N>::r[2];
 constexpr int TW1 = twiddle_elems<N, R1>(), TW2 = twiddle_elems<N, R2>();
@@ -47,7 +48,9 @@ constexpr size_t off_red = off_terms + sizeof(AdjTerms);
 constexpr size_t off_bar = (off_red + sizeof(float) * 8 * WARPS + 15) & ~size_t(15);
 constexpr size_t SMEM = off_bar + 2 * sizeof(uint64_t);
 
-template <bool WN>   // WN: also d L / d(Sersic n), a seventh gradient per galaxy
+// WN: also d L / d(Sersic n), a seventh gradient per galaxy.  EIG: some PSF of
+// the context is an eigen-PSF (its spectrum combined bin by bin where read).
+template <bool WN, bool EIG>
 __global__ void __launch_bounds__(THREADS, 1)
     render_bwd256_kernel(RenderParams p, const float* __restrict__ grad_out, float* __restrict__ grad_params,
                          float2* __restrict__ scratch_all) {
@@ -68,6 +71,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + off_bar);
   __shared__ int s_pos[2];
   __shared__ float s_psf_mog[KPSF][6];
+  __shared__ float s_eigm[KEIG];
   __shared__ int s_kpsf;
 
   const int tid = threadIdx.x;
@@ -96,7 +100,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     s_pos[0] = p0;
     if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * sizeof(AdjRecord), sizeof(AdjRecord), &bar[0]);
   }
-  int cur_psf = -1;
+  int cur_psf = -1, k_eig = 0;
   const float2* psf_hat = nullptr;
   uint32_t rec_parity = 0;
   float2* w = W + f * WS;
@@ -115,10 +119,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     rec_parity ^= 1u << buf;
     const AdjRecord& r = rec[buf];
     if (landed && r.ok && r.psf != cur_psf) {
-      if (tid < KPSF * 6) s_psf_mog[tid / 6][tid % 6] = p.psfs[r.psf].mog[tid / 6][tid % 6];
-      if (tid == 0) s_kpsf = p.psfs[r.psf].k;
-      psf_hat = p.psfs[r.psf].spec[B];
-      cur_psf = r.psf;
+      const DevPsf& ps = p.psfs[r.psf];
+      const float* pc = p.pcoef + ((size_t)p.bucket_start[B] + pos) * PCOEF;
+      k_eig = EIG ? ps.k_eig : 0;
+      if (tid < KPSF * 6)
+        s_psf_mog[tid / 6][tid % 6] = (k_eig > 0 && tid % 6 == 0) ? pc[8 + tid / 6] : ps.mog[tid / 6][tid % 6];
+      if (tid < KEIG) s_eigm[tid] = k_eig > 0 ? pc[tid] : 0.0f;
+      if (tid == 0) s_kpsf = ps.k;
+      psf_hat = ps.spec[B];
+      cur_psf = k_eig > 0 ? -1 : r.psf;
     }
     if (__syncthreads_or(!landed)) {
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
@@ -156,7 +165,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
           sincospif(-gx, &sn, &cs);
-          nyb[l] = cmul(__ldg(&psf_hat[(N / 2) * LS + l]), cmul(make_float2(cs, sn), make_float2(cy, sy)));
+          const float2 pn = k_eig > 0 ? eigen_bin(psf_hat, PSF_ELEMS, k_eig, s_eigm, (N / 2) * LS + l)
+                                      : __ldg(&psf_hat[(N / 2) * LS + l]);
+          nyb[l] = cmul(pn, cmul(make_float2(cs, sn), make_float2(cy, sy)));
           nys[4 * l + 0] = s;
           nys[4 * l + 1] = sq;
           nys[4 * l + 2] = sn2;
@@ -263,7 +274,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             sn = fmaf(r.fn[c], e, sn);
             if constexpr (WN) sd = fmaf(fmaf(r.fdq[c], qv, r.fdn[c]), e, sd);
           }
-          const float2 bph = cmul(__ldg(&psf_hat[k * LS + l]), cmul(pxk, py[l]));
+          const float2 pv = k_eig > 0 ? eigen_bin(psf_hat, PSF_ELEMS, k_eig, s_eigm, k * LS + l) : __ldg(&psf_hat[k * LS + l]);
+          const float2 bph = cmul(pv, cmul(pxk, py[l]));
           const float2 z = cscale(cmulc(bph, gk), ck);
           contract_bin(z, nu, om, s, sq, sn, acc);
           if constexpr (WN) acc[6] = fmaf(z.x, sd, acc[6]);
@@ -309,17 +321,16 @@ cudaError_t launch_render_bwd256(const RenderParams& p, const float* grad_out, f
                                  int num_sms, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(render_bwd256_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(render_bwd256_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaError_t e = cudaSuccess;
+    for (auto fn : {render_bwd256_kernel<false, false>, render_bwd256_kernel<true, false>,
+                    render_bwd256_kernel<false, true>, render_bwd256_kernel<true, true>})
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  if (p.grad_n)
-    render_bwd256_kernel<true><<<num_sms, THREADS, SMEM, s>>>(p, grad_out, grad_params, scratch);
-  else
-    render_bwd256_kernel<false><<<num_sms, THREADS, SMEM, s>>>(p, grad_out, grad_params, scratch);
+  auto fn = p.eigen ? (p.grad_n ? render_bwd256_kernel<true, true> : render_bwd256_kernel<false, true>)
+                    : (p.grad_n ? render_bwd256_kernel<true, false> : render_bwd256_kernel<false, false>);
+  fn<<<num_sms, THREADS, SMEM, s>>>(p, grad_out, grad_params, scratch);
   return cudaGetLastError();
 }
 

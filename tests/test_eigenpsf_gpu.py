@@ -150,3 +150,35 @@ def test_eigen_capable_kernels_match_for_constant_psfs(eig_renderer, gpu_rendere
     b = gpu_render(gpu_renderer, gals, pos)
     for i in range(len(gals)):
         assert np.array_equal(a[i], b[i]), i
+
+
+@pytest.mark.parametrize("size", [32, 64, 128, 256])
+def test_eigen_adjoint_each_size(eig_renderer, eig, psf0, tables, size):
+    """Gradients (and the Sersic-index gradient) with the PSF formed at each
+    galaxy's position, against the oracle's analytic vector-Jacobian product
+    with that PSF."""
+    import torch
+    from oracle import adjoint as A
+    from paper_2012_15797_gb300.renderer import to_device
+    rows = [_row(size=size, psf=p, **e) for p in (1, 0) for e in (
+        dict(e1=0.3, e2=-0.2), dict(log_re=np.log(7.0), profile=2, sersic_n=2.6, e1=-0.25, e2=0.1))]
+    gals = _gals(rows)
+    pos = (np.array([300.0, 3900.0, 2048.0, 10.0], np.float32), np.array([4000.0, 150.0, 2048.0, 900.0], np.float32))
+    rng = np.random.default_rng(111 + size)
+    grad = [rng.normal(size=(size, size)) for _ in range(len(gals))]
+    b = to_device(gals, positions=pos)
+    go = torch.from_numpy(np.concatenate([g.ravel() for g in grad]).astype(np.float32)).cuda()
+    got = eig_renderer.render_backward(b, go, sersic=True)
+    eig_renderer.sync_status()
+    got = got.double().cpu().numpy()
+    for i in range(len(gals)):
+        g = gals.row(i)
+        if g["psf"] == 1:
+            img, mog = E.psf_at(eig, float(pos[0][i]), float(pos[1][i]))
+        else:
+            img, mog = psf0.image, psf0.mog
+        ph = R.psf_spectrum(img, size)
+        ora = np.append(A.vjp(g, ph, mog, tables, grad[i]), np.sum(A.sersic_derivative(g, ph, mog, tables) * grad[i]))
+        flux = float(gals.flux[i])
+        scale = np.array([1.0] + [flux] * 6) * np.abs(grad[i]).sum()
+        assert np.all(np.abs(got[i] - ora) <= 1e-4 * np.abs(ora) + 1e-5 * scale), (i, got[i], ora)
