@@ -11,8 +11,8 @@
 //                     (Steps 5-6)
 //   column IFFT       N/2 complex IFFTs along omega (Stockham, shared memory);
 //                     the nu = 0 and nu = 1/2 columns are packed into one.  The
-//                     last pass pairs rows 2p, 2p+1 across neighbouring lanes
-//                     and writes the input of the row transform directly
+//                     last pass leaves rows p and p + N/2 in one thread, which
+//                     writes the input of their shared row transform directly
 //   row C2R           N/2 complex IFFTs, two real rows per transform (Step 7)
 //   real-space add    Gaussian terms added per pixel while storing float4
 //                     rows (Step 8)
@@ -117,7 +117,7 @@ __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, 
     F[h][4] = b.x; F[h][5] = b.y; F[h][6] = b.z; F[h][7] = b.w;
 #pragma unroll
     for (int u = 0; u < 8; ++u) X[h][u] = 0.0f;
-    real_space_run(rt, nr, (float)(2 * f + h), (float)x0, X[h]);
+    real_space_run(rt, nr, (float)(f + h * (N / 2)), (float)x0, X[h]);
   }
   __syncwarp();
 #pragma unroll
@@ -155,29 +155,25 @@ __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, 
     *reinterpret_cast<float4*>(orow + h * N + p1) = make_float4(X[h][4], X[h][5], X[h][6], X[h][7]);
   }
   __syncthreads();   // every row has been convolved along x
-  // along y: rows 2f - 3 .. 2f + 4 feed rows 2f (taps b = 3 - rr) and 2f+1 (b = 4 - rr)
+  // along y: J(y) = sum_d w[3 - d] R(y + d), d = -3 .. 3, for rows y = f and
+  // f + N/2; row r of the patch is half r / (N/2) of work row r mod N/2
   float wy[7];
 #pragma unroll
   for (int a = 0; a < 7; ++a) wy[a] = wl[8 + a];
 #pragma unroll
-  for (int rr = 0; rr < 8; ++rr) {
-    const int row = (2 * f - 3 + rr) & (N - 1);
-    const float* src = reinterpret_cast<const float*>(WB + C::row(row >> 1)) + (row & 1) * N;
-    const float4 a = *reinterpret_cast<const float4*>(src + p0);
-    const float4 b = *reinterpret_cast<const float4*>(src + p1);
-    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    if (rr <= 6) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) F[0][u] = fmaf(wy[6 - rr], v[u], F[0][u]);
-    }
-    if (rr >= 1) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) F[1][u] = fmaf(wy[7 - rr], v[u], F[1][u]);
-    }
-  }
-#pragma unroll
   for (int h = 0; h < 2; ++h) {
-    store8(dst + (2 * f + h) * N + x0, F[h], add);
+    const int y = f + h * (N / 2);
+#pragma unroll
+    for (int d = -3; d <= 3; ++d) {
+      const int row = (y + d) & (N - 1);
+      const float* src = reinterpret_cast<const float*>(WB + C::row(row & (N / 2 - 1))) + (row >= N / 2 ? N : 0);
+      const float4 a = *reinterpret_cast<const float4*>(src + p0);
+      const float4 b = *reinterpret_cast<const float4*>(src + p1);
+      const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int u = 0; u < 8; ++u) F[h][u] = fmaf(wy[3 - d], v[u], F[h][u]);
+    }
+    store8(dst + y * N + x0, F[h], add);
   }
 }
 
@@ -431,33 +427,30 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     fft_rest<N, +1>(wa, j, tw1, tw2, v);
     if constexpr (C::ALIAS_W) __syncthreads();   // every column's last loads are done
     {
-      // rows 2p (even lane) and 2p+1 (odd lane): Z_p[k] = A + iB and
-      // Z_p[N-k] = conj(A) + i conj(B) feed the row transform of pair p
+      // The last pass leaves rows n = j + q N/8 + m N/R of column f in this
+      // thread, so rows p and p + N/2 (outputs m and m + R/2, p < N/2) meet
+      // here without an exchange: Z_p[f] = A + iB and Z_p[N-f] = conj(A) +
+      // i conj(B) feed the row transform of pair p (any two real rows can
+      // share one complex transform).
       constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
-      const bool odd = j & 1;
 #pragma unroll
       for (int q = 0; q < 8 / R; ++q)
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-          const float2 mine = v[q * R + m];
-          float2 other;
-          other.x = __shfl_xor_sync(0xffffffffu, mine.x, 1);
-          other.y = __shfl_xor_sync(0xffffffffu, mine.y, 1);
-          const float2 A = odd ? other : mine, Bv = odd ? mine : other;
-          const int pr = stockham_out_index<N, R>(j, NS, q, m) >> 1;
-          float2* row = WB + C::row(pr);
+        for (int m = 0; m < R / 2; ++m) {
+          const float2 A = v[q * R + m], Bv = v[q * R + m + R / 2];
+          float2* row = WB + C::row(stockham_out_index<N, R>(j, NS, q, m));
           if (f > 0) {
-            if (!odd) row[swz<N>(f)] = make_float2(A.x - Bv.y, A.y + Bv.x);
-            else row[swz<N>(N - f)] = make_float2(A.x + Bv.y, Bv.x - A.y);
+            row[swz<N>(f)] = make_float2(A.x - Bv.y, A.y + Bv.x);
+            row[swz<N>(N - f)] = make_float2(A.x + Bv.y, Bv.x - A.y);
           } else {
-            if (!odd) row[swz<N>(0)] = make_float2(A.x, Bv.x);
-            else row[swz<N>(N / 2)] = make_float2(A.y, Bv.y);
+            row[swz<N>(0)] = make_float2(A.x, Bv.x);
+            row[swz<N>(N / 2)] = make_float2(A.y, Bv.y);
           }
         }
     }
     __syncthreads();  // S3: every column has been transformed
 
-    // ---- Step 7b: real inverse FFT of row pairs (2f, 2f + 1) along nu ----
+    // ---- Step 7b: real inverse FFT of row pairs (f, f + N/2) along nu ----
     first_pass_load<N>(wb, j, v);
     dft8<+1>(v);
     __syncwarp();
@@ -467,7 +460,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     __syncwarp();
     float* orow = reinterpret_cast<float*>(wb);
     {
-      // Rows 2f and 2f+1 of the patch overwrite this transform's own row.
+      // Rows f and f + N/2 of the patch overwrite this transform's own row.
       // Pixel x is kept at x ^ 4 [bit 5 of x]: the 16-byte pieces 8..15 of a
       // row swap in pairs, so the 8 lanes that read pieces 2j (then 2j+1)
       // below touch 8 different bank groups.
@@ -486,7 +479,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     float* dst = s_dst[buf];
     const int nr = s_nr[buf];
 
-    // ---- Step 8: add the real-space terms and store rows 2f and 2f+1 ----
+    // ---- Step 8: add the real-space terms and store rows f and f + N/2 ----
     if constexpr (LZ) {
       if (nr > 0) {   // uniform over the CTA
         lanczos_real_and_store<N>(WB, orow, rt, nr, s_lzw[buf], f, j, dst, p.accumulate != 0);
@@ -497,7 +490,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     // conflict-free reads were measured slower: twice the ex2 and term set-ups).
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
-      const int yy = 2 * f + h;
+      const int yy = f + h * (N / 2);
       const int x0 = 8 * j;
       const int sw = ((j >> 2) & 1) << 2;   // pieces 2j, 2j+1 swapped in the upper half of the row
       const float* src = orow + h * N;

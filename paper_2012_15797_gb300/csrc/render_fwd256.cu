@@ -3,8 +3,9 @@
 // The half spectrum (129 x 256 complex, 264 KB) does not fit in one CTA's
 // shared memory, so the transform between the two FFT directions goes through
 // the galaxy's own output patch, which stays L2-resident: the input of the
-// row transform of row pair p (256 complex, 2 KB) occupies exactly the bytes
-// of output rows 2p and 2p+1, which only that row transform overwrites.
+// row transform of row pair p (rows p and p + N/2; 256 complex, 2 KB)
+// occupies exactly the bytes of those two output rows (elements below N/2 in
+// row p, the rest in row p + N/2), which only that row transform overwrites.
 //
 // 1024 threads, one warp per length-256 transform:
 //   columns   4 rounds of 32 column IFFTs (round 0, warp 0: the packed nu = 0
@@ -29,6 +30,9 @@ namespace mog {
 namespace {
 
 constexpr int N = 256;
+
+// float2 offset of element c of row pair p's transform input in the patch
+__device__ __forceinline__ int zpos(int p, int c) { return (c < N / 2 ? p : p + N / 2) * (N / 2) + (c & (N / 2 - 1)); }
 constexpr int H = N / 2 + 1;
 constexpr int TPF = N / 8;       // 32: one warp per transform
 constexpr int THREADS = 1024;
@@ -327,27 +331,23 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
       stockham_store<N, R1>(w, j, 8, v);
       __syncwarp();
       stockham_load<N, R2, +1>(w, j, tw2, v);
-      // rows 2p (even lane), 2p+1 (odd lane): stage Z_p[k] and Z_p[N-k]
+      // rows p and p + N/2 (outputs m and m + R2/2 of this thread, p < N/2):
+      // stage Z_p[k] = A + iB and Z_p[N-k] = conj(A) + i conj(B)
       {
         constexpr int NS = N / R2;
-        const bool odd = j & 1;
 #pragma unroll
         for (int qq = 0; qq < 8 / R2; ++qq)
 #pragma unroll
-          for (int m = 0; m < R2; ++m) {
-            const float2 mine = v[qq * R2 + m];
-            float2 other;
-            other.x = __shfl_xor_sync(0xffffffffu, mine.x, 1);
-            other.y = __shfl_xor_sync(0xffffffffu, mine.y, 1);
-            const float2 A = odd ? other : mine, Bv = odd ? mine : other;
-            const int pr = stockham_out_index<N, R2>(j, NS, qq, m) >> 1;
+          for (int m = 0; m < R2 / 2; ++m) {
+            const float2 A = v[qq * R2 + m], Bv = v[qq * R2 + m + R2 / 2];
+            const int pr = stockham_out_index<N, R2>(j, NS, qq, m);
             if (k > 0) {
-              if (!odd) SA[pr * SSTR + f] = make_float2(A.x - Bv.y, A.y + Bv.x);
-              else SB[pr * SSTR + f] = make_float2(A.x + Bv.y, Bv.x - A.y);
+              SA[pr * SSTR + f] = make_float2(A.x - Bv.y, A.y + Bv.x);
+              SB[pr * SSTR + f] = make_float2(A.x + Bv.y, Bv.x - A.y);
             } else {
               // column 0 in SA, column N/2 in SB's slot 0
-              if (!odd) SA[pr * SSTR] = make_float2(A.x, Bv.x);
-              else SB[pr * SSTR] = make_float2(A.y, Bv.y);
+              SA[pr * SSTR] = make_float2(A.x, Bv.x);
+              SB[pr * SSTR] = make_float2(A.y, Bv.y);
             }
           }
       }
@@ -356,11 +356,11 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
       for (int i = tid; i < (N / 2) * WARPS * 2; i += THREADS) {
         const int pr = i / (2 * WARPS), t = i % (2 * WARPS);
         if (t < WARPS) {
-          zbuf[pr * N + WARPS * round + t] = SA[pr * SSTR + t];
+          zbuf[zpos(pr, WARPS * round + t)] = SA[pr * SSTR + t];
         } else {
           const int u = t - WARPS;
           const int col = (round == 0 && u == 0) ? N / 2 : N - WARPS * round - u;
-          zbuf[pr * N + col] = SB[pr * SSTR + u];
+          zbuf[zpos(pr, col)] = SB[pr * SSTR + u];
         }
       }
       __syncthreads();
@@ -370,9 +370,8 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
     const int nr = real_terms_padded(r.nrc * s_kpsf);
     for (int round = 0; round < ROUNDS; ++round) {
       const int pr = WARPS * round + f;
-      const float2* zin = zbuf + pr * N;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) v[m] = __ldcg(&zin[j + m * TPF]);
+      for (int m = 0; m < 8; ++m) v[m] = __ldcg(&zbuf[zpos(pr, j + m * TPF)]);
       dft8<+1>(v);
       __syncwarp();
 #pragma unroll
@@ -397,10 +396,10 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
           }
       }
       __syncwarp();
-      // 512 pixels (rows 2pr, 2pr+1), 8 consecutive per lane and step
+      // 512 pixels (rows pr, pr + N/2), 8 consecutive per lane and step
       for (int idx = j; idx < 2 * N / 8; idx += 32) {
         const int h = idx / (N / 8), x0 = (idx % (N / 8)) * 8;
-        const int yy = 2 * pr + h;
+        const int yy = pr + h * (N / 2);
         const float* orow = reinterpret_cast<const float*>(w) + h * N + x0;
         const float4 i0 = *reinterpret_cast<const float4*>(orow), i1 = *reinterpret_cast<const float4*>(orow + 4);
         float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
