@@ -275,6 +275,24 @@ __device__ __forceinline__ void bulk_load(void* dst_smem, const void* src_gmem, 
       : "memory");
 }
 
+// Arms the barrier for `bytes` of bulk copies issued afterwards (possibly by
+// several threads, each with bulk_copy).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One bulk copy (multiple of 16 bytes, 16-byte aligned addresses) counted
+// against a barrier armed by mbar_expect_tx.
+__device__ __forceinline__ void bulk_copy(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -834,6 +852,18 @@ __device__ __forceinline__ void adj_real_term(const AdjRecord& r, const float (*
   at->my[t] = 0.5f * (float)n + r.y + m[2];
 }
 
+// Zero-weight padding term (flat exponent, no contribution): the real-space
+// loop takes terms in pairs.
+__device__ __forceinline__ void adj_real_term_zero(int t, AdjTerms* at) {
+  at->base[t] = at->wr[t] = at->rn[t] = at->v[t] = 0.0f;
+  at->dna[t] = at->dnv[t] = at->trs[t] = 0.0f;
+  at->i11[t] = at->i12[t] = at->i22[t] = 0.0f;
+  at->qa[t] = at->qb[t] = at->qc[t] = 0.0f;
+  at->rrr[t] = 1.0f;
+  at->bw[t] = at->bwv[t] = at->brn[t] = 0.0f;
+  at->mx[t] = at->my[t] = 0.0f;
+}
+
 // Adds one bin's contribution.  z = c_k conj(G) P phase; (s, sq, sn) the
 // weighted mixture sums at the bin.
 __device__ __forceinline__ void contract_bin(float2 z, float nu, float om, float s, float sq, float sn,
@@ -847,59 +877,78 @@ __device__ __forceinline__ void contract_bin(float2 z, float nu, float om, float
 }
 
 // Real-space part of the adjoint over all pixels of an N x N patch (g read
-// from `gp`, shared or global memory); the x and y sums are divided by 2 pi
-// because the caller multiplies the total by 2 pi.  A thread takes runs of 8
-// consecutive pixels of a row; along the run a term's Gaussian follows the
-// two-step multiplicative recurrence of the forward store (2 ex2 per term and
-// run; terms are wide, so an underflowing start stays negligible over 7
-// pixels) and u = Sigma^-1 d moves by (i11, i12) per pixel, so the pixel loop
-// only gathers the moments sum g E (1, ux, uy, ux^2, ux uy, uy^2); every
-// derivative of the term is a combination of those six.
+// from `gp`, shared or global memory, rows `gstride` floats apart); the x
+// and y sums are divided by 2 pi because the caller multiplies the total by
+// 2 pi.  A thread takes runs of 8 consecutive pixels of a row and the terms
+// two at a time (packed f32x2; nr2 is even, padded with zero-weight terms).
+// Along a run a term's Gaussian E follows the two-step multiplicative
+// recurrence of the forward store (2 ex2 per term and run; terms are wide,
+// so an underflowing start stays negligible over 7 pixels).  With
+// u' = u - 3.5 the pixel's offset from the run's centre, u = Sigma^-1 d is
+// (ux, uy) + u' (i11, i12), so the moments sum g E (1, ux, uy, ux^2, ux uy,
+// uy^2) that every derivative of the term combines are fixed by
+// M_k = sum g E u'^k, k = 0, 1, 2: the pixel loop gathers only those three.
 // WN: also the Sersic-index sum acc[6], with S = (s11, s12, s22).
 template <int N, bool WN = false>
-__device__ __forceinline__ void adj_real_space(const float* gp, const AdjTerms& at, int nr, int tid, int nthreads,
-                                               float* acc, float s11 = 0.f, float s12 = 0.f, float s22 = 0.f) {
-  if (nr <= 0) return;
+__device__ __forceinline__ void adj_real_space(const float* gp, int gstride, const AdjTerms& at, int nr2, int tid,
+                                               int nthreads, float* acc, float s11 = 0.f, float s12 = 0.f,
+                                               float s22 = 0.f) {
+  if (nr2 <= 0) return;
+  const float2 NEG = make_float2(-1.0f, -1.0f), TWO = make_float2(2.0f, 2.0f), ONE = make_float2(1.0f, 1.0f);
   float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f, a6 = 0.f;
   for (int run = tid; run < N * N / 8; run += nthreads) {
     const int pix0 = run * 8;
-    const float yy = (float)(pix0 / N), x0 = (float)(pix0 % N);
-    const float4 ga = *reinterpret_cast<const float4*>(gp + pix0);
-    const float4 gb = *reinterpret_cast<const float4*>(gp + pix0 + 4);
+    const int y = pix0 / N, x = pix0 % N;
+    const float* gr = gp + y * gstride + x;
+    const float4 ga = *reinterpret_cast<const float4*>(gr);
+    const float4 gb = *reinterpret_cast<const float4*>(gr + 4);
     const float gw[8] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z, gb.w};
-    for (int t = 0; t < nr; ++t) {
-      const float dx = x0 - at.mx[t], dy = yy - at.my[t];
-      const float qa = at.qa[t], ly = at.qb[t] * dy;
-      float e = ex2(fmaf(dx, fmaf(qa, dx, ly), at.qc[t] * dy * dy));
-      float rr = ex2(fmaf(qa, fmaf(2.0f, dx, 1.0f), ly));
-      const float r8 = at.rrr[t], i11 = at.i11[t], i12 = at.i12[t], i22 = at.i22[t];
-      float ux = fmaf(i11, dx, i12 * dy), uy = fmaf(i12, dx, i22 * dy);
-      float m0 = 0.f, mx = 0.f, my = 0.f, mxx = 0.f, mxy = 0.f, myy = 0.f;
+    const float2 Y = make_float2((float)y, (float)y), X = make_float2((float)x, (float)x);
+    for (int t = 0; t < nr2; t += 2) {
+      const float2 qa = *reinterpret_cast<const float2*>(&at.qa[t]);
+      const float2 dy = __ffma2_rn(*reinterpret_cast<const float2*>(&at.my[t]), NEG, Y);
+      const float2 dx = __ffma2_rn(*reinterpret_cast<const float2*>(&at.mx[t]), NEG, X);
+      const float2 ly = __fmul2_rn(dy, *reinterpret_cast<const float2*>(&at.qb[t]));
+      const float2 e0 = __ffma2_rn(dx, __ffma2_rn(qa, dx, ly),
+                                   __fmul2_rn(__fmul2_rn(*reinterpret_cast<const float2*>(&at.qc[t]), dy), dy));
+      const float2 e1 = __ffma2_rn(qa, __ffma2_rn(TWO, dx, ONE), ly);
+      float2 e = make_float2(ex2(e0.x), ex2(e0.y));
+      float2 rr = make_float2(ex2(e1.x), ex2(e1.y));
+      const float2 r8 = *reinterpret_cast<const float2*>(&at.rrr[t]);
+      float2 m0 = make_float2(0.f, 0.f), m1 = m0, m2 = m0;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const float ge = gw[u] * e;
-        const float gx = ge * ux, gy = ge * uy;
-        m0 += ge;
-        mx += gx;
-        my += gy;
-        mxx = fmaf(gx, ux, mxx);
-        mxy = fmaf(gx, uy, mxy);
-        myy = fmaf(gy, uy, myy);
-        e *= rr;
-        rr *= r8;
-        ux += i11;
-        uy += i12;
+        const float c = (float)u - 3.5f;
+        const float2 ge = __fmul2_rn(e, make_float2(gw[u], gw[u]));
+        m0 = __fadd2_rn(m0, ge);
+        m1 = __ffma2_rn(ge, make_float2(c, c), m1);
+        m2 = __ffma2_rn(ge, make_float2(c * c, c * c), m2);
+        if (u < 7) {
+          e = __fmul2_rn(e, rr);
+          rr = __fmul2_rn(rr, r8);
+        }
       }
-      const float bw = at.bw[t], bwv = at.bwv[t], brn = at.brn[t];
-      a0 = fmaf(bw, m0, a0);
-      a1 = fmaf(bw, mx, a1);
-      a2 = fmaf(bw, my, a2);
-      a3 = fmaf(bwv, 0.5f * fmaf(-i11, m0, mxx), fmaf(brn, m0, a3));
-      a4 = fmaf(bwv, fmaf(-i12, m0, mxy), a4);
-      a5 = fmaf(bwv, 0.5f * fmaf(-i22, m0, myy), fmaf(brn, m0, a5));
-      if constexpr (WN) {
-        const float usu = fmaf(s11, mxx, fmaf(2.0f * s12, mxy, s22 * myy));
-        a6 = fmaf(at.dna[t], m0, fmaf(at.dnv[t], fmaf(-at.trs[t], m0, usu), a6));
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int tt = t + h;
+        const float M0 = h ? m0.y : m0.x, M1 = h ? m1.y : m1.x, M2 = h ? m2.y : m2.x;
+        const float i11 = at.i11[tt], i12 = at.i12[tt], i22 = at.i22[tt];
+        const float dxc = (h ? dx.y : dx.x) + 3.5f, dyh = h ? dy.y : dy.x;
+        const float ux = fmaf(i11, dxc, i12 * dyh), uy = fmaf(i12, dxc, i22 * dyh);   // at the run's centre
+        const float mx = fmaf(ux, M0, i11 * M1), my = fmaf(uy, M0, i12 * M1);
+        const float t1 = fmaf(ux, M1, i11 * M2), t2 = fmaf(uy, M1, i12 * M2);   // sum g E ux u', sum g E uy u'
+        const float mxx = fmaf(ux, mx, i11 * t1), mxy = fmaf(uy, mx, i12 * t1), myy = fmaf(uy, my, i12 * t2);
+        const float bw = at.bw[tt], bwv = at.bwv[tt], brn = at.brn[tt];
+        a0 = fmaf(bw, M0, a0);
+        a1 = fmaf(bw, mx, a1);
+        a2 = fmaf(bw, my, a2);
+        a3 = fmaf(bwv, 0.5f * fmaf(-i11, M0, mxx), fmaf(brn, M0, a3));
+        a4 = fmaf(bwv, fmaf(-i12, M0, mxy), a4);
+        a5 = fmaf(bwv, 0.5f * fmaf(-i22, M0, myy), fmaf(brn, M0, a5));
+        if constexpr (WN) {
+          const float usu = fmaf(s11, mxx, fmaf(2.0f * s12, mxy, s22 * myy));
+          a6 = fmaf(at.dna[tt], M0, fmaf(at.dnv[tt], fmaf(-at.trs[tt], M0, usu), a6));
+        }
       }
     }
   }

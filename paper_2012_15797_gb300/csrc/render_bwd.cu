@@ -15,10 +15,11 @@
 // is chained at the end.
 //
 // One CTA per galaxy at a time, N^2/16 threads:
-//   rows      forward FFT of row pairs (2p, 2p+1) packed as g[2p] + i g[2p+1],
+//   rows      forward FFT of row pairs (p, p + N/2) packed as g[p] + i g[p+N/2],
 //             untangled into the half spectrum of each row
 //   columns   forward FFT along y of every column k (k = 0 and N/2 packed)
 //   contract  each thread evaluates the mixture on the 8 bins it holds
+//             (components outer, bins (2k, 2k+1) in packed f32x2)
 //   real      per-pixel analytic derivatives of the real-space terms
 //   reduce    warp shuffles, then one thread applies the chain rule
 #include "common.cuh"
@@ -35,22 +36,43 @@ struct BwdCfg {
   static constexpr int WARPS = THREADS / 32;
   static constexpr int LS = psf_lstride(N);
   static constexpr int PSF_ELEMS = psf_spec_elems(N);
+  // WB rows: the row transforms (one per group).  WA rows: written by the
+  // untangle as column k (lanes of a warp: 8 or more k, four groups' rows),
+  // then transformed one per group.  Strides chosen against bank conflicts
+  // of both patterns: N = 64 shifts rows 2-3 of every 4 by 4 float2 in an
+  // 88-float2 stride, N = 128 uses an odd stride.
   static constexpr int WS = wstride<N>();
   static constexpr int W_ELEMS = NFFT * WS;
+  static constexpr int WSA = N == 64 ? 88 : N == 128 ? 145 : WS;
+  static constexpr int SKEWA = N == 64 ? 4 : 0;
+  static_assert(SKEWA <= WSA - WS, "shifted rows must not overlap");
+  __host__ __device__ static constexpr int rowA(int r) { return r * WSA + SKEWA * ((r >> 1) & 1); }
+  static constexpr int WA_ELEMS = NFFT * WSA;
+  // Gradient patch rows in shared memory (floats): N <= 64 pads them by 8 so
+  // that the row transforms' loads (rows p of four groups) hit distinct
+  // banks; N = 128 has no room and keeps them dense.
+  static constexpr int GS = N <= 64 ? N + 8 : N;
+  // N = 32: two gradient-patch buffers, the next galaxy's patch copied in
+  // while this one is processed.  N = 64 keeps one so that three CTAs fit
+  // per SM (more resident warps hide more latency than the prefetch does);
+  // N = 128 has room for one only.
+  static constexpr int NGB = N <= 32 ? 2 : 1;
   static constexpr int R1 = Radix<N>::r[1];
   static constexpr int R2 = Radix<N>::r[2];
   static constexpr int TW1 = twiddle_elems<N, R1>();
   static constexpr int TW2 = Radix<N>::P == 3 ? twiddle_elems<N, (R2 > 1 ? R2 : 2)>() : 0;
-  static constexpr int MIN_BLOCKS = N == 32 ? 8 : N == 64 ? 2 : 1;
-  // N = 128 does not fit the PSF spectrum beside the work buffers and the
-  // gradient patch; it reads the (L2-resident) spectrum from global memory.
-  static constexpr bool STAGE_PSF = N <= 64;
+  static constexpr int MIN_BLOCKS = N == 32 ? 8 : N == 64 ? 3 : 1;
+  // N = 32 stages the PSF spectrum in shared memory.  N = 64 reads the
+  // (L2-resident) spectrum from global memory, which leaves room for three
+  // CTAs per SM; N = 128 does not fit it beside the work buffers and the
+  // gradient patch.
+  static constexpr bool STAGE_PSF = N <= 32;
 
   static constexpr size_t off_psf = 0;
   static constexpr size_t off_wa = off_psf + (STAGE_PSF ? sizeof(float2) * PSF_ELEMS : 0);
-  static constexpr size_t off_wb = off_wa + sizeof(float2) * W_ELEMS;
-  static constexpr size_t off_g = off_wb + sizeof(float2) * W_ELEMS;
-  static constexpr size_t off_tw = off_g + sizeof(float) * N * N;
+  static constexpr size_t off_wb = off_wa + sizeof(float2) * WA_ELEMS;
+  static constexpr size_t off_g = (off_wb + sizeof(float2) * W_ELEMS + 15) & ~size_t(15);
+  static constexpr size_t off_tw = off_g + sizeof(float) * N * GS * NGB;
   static constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
   static constexpr size_t off_py = off_px + sizeof(float2) * H;
   static constexpr size_t off_nb = off_py + sizeof(float2) * N;       // nu = 1/2 column: P phase
@@ -59,7 +81,8 @@ struct BwdCfg {
   static constexpr size_t off_terms = off_rec + 2 * sizeof(AdjRecord);
   static constexpr size_t off_red = off_terms + sizeof(AdjTerms);
   static constexpr size_t off_bar = (off_red + sizeof(float) * 8 * WARPS + 15) & ~size_t(15);
-  static constexpr size_t SMEM = off_bar + 4 * sizeof(uint64_t);
+  static constexpr size_t SMEM = off_bar + 5 * sizeof(uint64_t);
+  static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB a CTA can have");
 };
 
 template <int N>
@@ -107,11 +130,15 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
   AdjRecord* rec = reinterpret_cast<AdjRecord*>(smem + C::off_rec);
   AdjTerms& at = *reinterpret_cast<AdjTerms*>(smem + C::off_terms);
   float* red = reinterpret_cast<float*>(smem + C::off_red);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);  // [0] PSF, [1..2] records, [3] g
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);  // [0] PSF, [1..2] records, [3..4] g buffers
   __shared__ int s_pos[2];
   __shared__ float s_psf_mog[KPSF][6];
   __shared__ int s_kpsf;
   __shared__ float s_eigm[KEIG];   // eigen-PSF terms of the current galaxy
+  // Fourier components as operand pairs of f32x2: (a, a, dq, dq), (c, c, dn, dn)
+  // and, for the Sersic gradient, (a_dq, a_dq, a_dn, a_dn)
+  __shared__ float4 s_fa[KMAX], s_fc[KMAX], s_fd[KMAX];
+  __shared__ int s_gready[2];   // per record buffer: its gradient patch was requested one galaxy ahead
 
   const int tid = threadIdx.x;
   const int f = tid / TPF, j = tid % TPF;
@@ -134,15 +161,28 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     return q_next++;
   };
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&bar[i], 1);
+    for (int i = 0; i < 5; ++i) mbar_init(&bar[i], 1);
     q_ahead = atomicAdd(&p.queue[B], p.chunk);
     const int p0 = next_position();
     s_pos[0] = p0;
     if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * sizeof(AdjRecord), sizeof(AdjRecord), &bar[1]);
   }
   int cur_psf = -1;
-  uint32_t psf_parity = 0, rec_parity = 0, g_parity = 0;
-  float2* wa = WA + f * WS;
+  uint32_t psf_parity = 0, rec_parity = 0, g_parity = 0;   // g_parity bit b: phase of g buffer b
+  if (tid < 2) s_gready[tid] = 0;
+  // gradient patch of record `rr` into buffer gb (warp 0; one bulk copy per
+  // padded row, or one copy of the dense patch)
+  auto request_g = [&](const AdjRecord& rr, float* gb, uint64_t* gbar) {
+    if constexpr (C::GS == N) {
+      if (lane == 0) bulk_load(gb, grad_out + rr.off, sizeof(float) * N * N, gbar);
+    } else {
+      if (lane == 0) mbar_expect_tx(gbar, sizeof(float) * N * N);
+      __syncwarp();
+      for (int y = lane; y < N; y += 32)
+        bulk_copy(gb + y * C::GS, grad_out + rr.off + (size_t)y * N, sizeof(float) * N, gbar);
+    }
+  };
+  float2* wa = WA + C::rowA(f);
   float2* wb = WB + f * WS;
 
   for (int buf = 0;; buf ^= 1) {
@@ -159,7 +199,11 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     rec_parity ^= 1u << buf;
     const AdjRecord& r = rec[buf];
     const bool go = rec_landed && r.ok;
-    if (go && tid == 0) bulk_load(gbuf, grad_out + r.off, sizeof(float) * N * N, &bar[3]);
+    const int gi = C::NGB == 2 ? buf : 0;   // this galaxy's gradient buffer
+    float* gcur = gbuf + gi * N * C::GS;
+    // s_gready was written before the previous S3 and is reset only by warp 0
+    // after the S2 below
+    if (go && warp == 0 && !s_gready[buf]) request_g(r, gcur, &bar[3 + gi]);
     const bool need_psf = go && r.psf != cur_psf;
     bool psf_landed = true;
     if (need_psf) {
@@ -199,7 +243,8 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     {
       const float gx = r.x, gy = r.y;
       const int kp = s_kpsf;
-      const int ntask = C::H + 2 * N + r.nrc * kp;
+      const int nrt = r.nrc * kp, nr2 = real_terms_padded(nrt);
+      const int ntask = C::H + 2 * N + nr2 + r.nf;
       for (int i = tid; i < ntask; i += C::THREADS) {
         float sn, cs;
         if (i < C::H) {
@@ -234,23 +279,54 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
           nys[4 * l + 2] = sn2;
           nys[4 * l + 3] = sd;
         } else {
-          adj_real_term(r, s_psf_mog, kp, N, i - C::H - 2 * N, &at);
+          const int t = i - C::H - 2 * N;
+          if (t < nrt) {
+            adj_real_term(r, s_psf_mog, kp, N, t, &at);
+          } else if (t < nr2) {
+            adj_real_term_zero(t, &at);
+          } else {
+            const int c = t - nr2;
+            s_fa[c] = make_float4(r.famp[c], r.famp[c], r.fq[c], r.fq[c]);
+            s_fc[c] = make_float4(r.fcoef[c], r.fcoef[c], r.fn[c], r.fn[c]);
+            if constexpr (WN) s_fd[c] = make_float4(r.fdq[c], r.fdq[c], r.fdn[c], r.fdn[c]);
+          }
         }
       }
     }
-    const bool g_landed = mbar_wait(&bar[3], g_parity);
-    g_parity ^= 1u;
+    const bool g_landed = mbar_wait(&bar[3 + gi], (g_parity >> gi) & 1u);
+    g_parity ^= 1u << gi;
     if (__syncthreads_or(!g_landed)) {   // S2
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
       return;
     }
+    if constexpr (C::NGB == 2) {
+      // the next galaxy's patch, into the other buffer: its last reader (the
+      // galaxy before this one) finished before the previous S3, and its
+      // record was requested at the top of this iteration
+      if (warp == 0) {
+        const int nb = buf ^ 1;
+        bool ready = false;
+        if (s_pos[nb] >= 0) {
+          // the copy below is issued by the whole warp: decide once for it
+          const bool landed = __all_sync(0xffffffffu, mbar_wait(&bar[1 + nb], (rec_parity >> nb) & 1u));
+          if (landed && rec[nb].ok) {
+            request_g(rec[nb], gbuf + nb * N * C::GS, &bar[3 + nb]);
+            ready = true;
+          }
+        }
+        if (lane == 0) {
+          s_gready[nb] = ready;
+          s_gready[buf] = 0;
+        }
+      }
+    }
 
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float2 v[8];
-    // ---- forward FFT of row pairs (2f, 2f+1) packed as g[2f] + i g[2f+1] ----
+    // ---- forward FFT of row pairs (f, f + N/2) packed as g[f] + i g[f + N/2] ----
     {
-      const float* ga = gbuf + (2 * f) * N;
-      const float* gb = gbuf + (2 * f + 1) * N;
+      const float* ga = gcur + f * C::GS;
+      const float* gb = gcur + (f + N / 2) * C::GS;
 #pragma unroll
       for (int m = 0; m < 8; ++m) v[m] = make_float2(ga[j + m * TPF], gb[j + m * TPF]);
       dft8<-1>(v);
@@ -262,8 +338,8 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
       constexpr int R = BwdLast<N>::R, NS = BwdLast<N>::NS;
       stockham_store<N, R>(wb, j, NS, v);
       __syncwarp();
-      // untangle: row 2f has spectrum (Z[k] + conj Z[N-k]) / 2, row 2f+1 has
-      // (Z[k] - conj Z[N-k]) / (2i); write them as inputs of the column FFTs
+      // untangle: row f has spectrum (Z[k] + conj Z[N-k]) / 2, row f + N/2
+      // has (Z[k] - conj Z[N-k]) / (2i); write them as inputs of the column FFTs
       for (int k = j; k <= N / 2; k += TPF) {
         const float2 zk = wb[swz<N>(k)], zn = wb[swz<N>((N - k) & (N - 1))];
         const float2 a = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
@@ -271,17 +347,18 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
         if (k == 0) {
           // rows' nu = 0 and nu = 1/2 values are real: packed as re + i im
           const float2 zh = wb[swz<N>(N / 2)];
-          WA[swz<N>(2 * f)] = make_float2(zk.x, zh.x);
-          WA[swz<N>(2 * f + 1)] = make_float2(zk.y, zh.y);
+          WA[swz<N>(f)] = make_float2(zk.x, zh.x);
+          WA[swz<N>(f + N / 2)] = make_float2(zk.y, zh.y);
         } else if (k < N / 2) {
-          WA[k * WS + swz<N>(2 * f)] = a;
-          WA[k * WS + swz<N>(2 * f + 1)] = b;
+          WA[C::rowA(k) + swz<N>(f)] = a;
+          WA[C::rowA(k) + swz<N>(f + N / 2)] = b;
         }
       }
     }
 
     // ---- real-space terms: analytic derivatives, pixel by pixel ----
-    adj_real_space<N, WN>(gbuf, at, r.nrc * s_kpsf, tid, C::THREADS, acc, r.s11, r.s12, r.s22);
+    adj_real_space<N, WN>(gcur, C::GS, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
+                          r.s22);
     __syncthreads();  // S3: every column input written
 
     // ---- forward FFT of every column along y ----
@@ -308,13 +385,53 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
       const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
       const float ck = f == 0 ? 1.0f : 2.0f;
       const float2 pxf = px[f];
+      // mixture sums at the thread's bins b = q R + m, components outer and
+      // bins (2k, 2k+1) in packed f32x2, BH bins per sweep over the
+      // components (N >= 64 takes two sweeps of 4, which keeps the registers
+      // at three CTAs per SM for N = 64 and at 64 for N = 128's 1024
+      // threads).  No warp-level skip of negligible components: the
+      // per-component vote cost more than the work it saved (measured).
+      constexpr int BH = N >= 64 ? 4 : 8;
 #pragma unroll
-      for (int q = 0; q < 8 / R; ++q)
+      for (int b0 = 0; b0 < 8; b0 += BH) {
+        float2 qp[BH / 2], S[BH / 2], SQ[BH / 2], SN[BH / 2], SD[BH / 2];
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
+        for (int k = 0; k < BH / 2; ++k) {
+          float qq[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int b = b0 + 2 * k + h;
+            const int l = stockham_out_index<N, R>(j, NS, b / R, b % R);
+            const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+            qq[h] = fmaf(om, fmaf(s22, om, a1), a0);
+          }
+          qp[k] = make_float2(qq[0], qq[1]);
+          S[k] = SQ[k] = SN[k] = SD[k] = make_float2(0.0f, 0.0f);
+        }
+        for (int c = 0; c < nf; ++c) {
+          const float4 cn = s_fc[c];
+          const float4 aq = s_fa[c];
+          const float2 c2 = make_float2(cn.x, cn.y), n2 = make_float2(cn.z, cn.w);
+          const float2 a2 = make_float2(aq.x, aq.y), q2 = make_float2(aq.z, aq.w);
+          float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+          if constexpr (WN) dd = s_fd[c];
+#pragma unroll
+          for (int k = 0; k < BH / 2; ++k) {
+            const float2 x = __fmul2_rn(c2, qp[k]);
+            const float2 e = make_float2(ex2(x.x), ex2(x.y));
+            S[k] = __ffma2_rn(a2, e, S[k]);
+            SQ[k] = __ffma2_rn(q2, e, SQ[k]);
+            SN[k] = __ffma2_rn(n2, e, SN[k]);
+            if constexpr (WN)
+              SD[k] = __ffma2_rn(__ffma2_rn(make_float2(dd.x, dd.y), qp[k], make_float2(dd.z, dd.w)), e, SD[k]);
+          }
+        }
+#pragma unroll
+        for (int bb = 0; bb < BH; ++bb) {
+          const int b = b0 + bb, q = b / R, m = b % R;
           const int l = stockham_out_index<N, R>(j, NS, q, m);
           const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
-          float2 gk = v[q * R + m];
+          float2 gk = v[b];
           float2 gn = make_float2(0.f, 0.f);
           if (f == 0) {
             const float2 u = wa[swz<N>(l)], un = wa[swz<N>((N - l) & (N - 1))];
@@ -322,15 +439,10 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
             const float dr = u.x - un.x, di = u.y + un.y;
             gn = make_float2(0.5f * di, -0.5f * dr);
           }
-          const float qv = fmaf(om, fmaf(s22, om, a1), a0);
-          float s = 0.0f, sq = 0.0f, sn = 0.0f, sd = 0.0f;
-          for (int c = 0; c < nf; ++c) {
-            const float e = ex2(r.fcoef[c] * qv);
-            s = fmaf(r.famp[c], e, s);
-            sq = fmaf(r.fq[c], e, sq);
-            sn = fmaf(r.fn[c], e, sn);
-            if constexpr (WN) sd = fmaf(fmaf(r.fdq[c], qv, r.fdn[c]), e, sd);
-          }
+          const float s = (bb & 1) ? S[bb >> 1].y : S[bb >> 1].x;
+          const float sq = (bb & 1) ? SQ[bb >> 1].y : SQ[bb >> 1].x;
+          const float sn = (bb & 1) ? SN[bb >> 1].y : SN[bb >> 1].x;
+          const float sd = (bb & 1) ? SD[bb >> 1].y : SD[bb >> 1].x;
           const float2 pv = (!C::STAGE_PSF && k_eig > 0) ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, f * LS + l)
                                                          : psf_hat[f * LS + l];
           const float2 bph = cmul(pv, cmul(pxf, py[l]));
@@ -343,6 +455,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
             if constexpr (WN) acc[6] = fmaf(zn.x, nys[4 * l + 3], acc[6]);
           }
         }
+      }
     }
 
     // ---- reduce the sums over the CTA and apply the chain rule ----

@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     {
       const float gx = r.x, gy = r.y;
       const int kp = s_kpsf;
-      const int ntask = H + 2 * N + r.nrc * kp;
+      const int nrt = r.nrc * kp;
+      const int ntask = H + 2 * N + real_terms_padded(nrt);
       for (int i = tid; i < ntask; i += THREADS) {
         float sn, cs;
         if (i < H) {
@@ -173,7 +174,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           nys[4 * l + 2] = sn2;
           nys[4 * l + 3] = sd;
         } else {
-          adj_real_term(r, s_psf_mog, kp, N, i - H - 2 * N, &at);
+          const int t = i - H - 2 * N;
+          if (t < nrt) adj_real_term(r, s_psf_mog, kp, N, t, &at);
+          else adj_real_term_zero(t, &at);
         }
       }
     }
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 
     // ---- real-space terms ----
-    adj_real_space<N, WN>(gpatch, at, r.nrc * s_kpsf, tid, THREADS, acc, r.s11, r.s12, r.s22);
+    adj_real_space<N, WN>(gpatch, N, at, real_terms_padded(r.nrc * s_kpsf), tid, THREADS, acc, r.s11, r.s12, r.s22);
     __syncthreads();   // scratch complete and visible
 
     // ---- columns: forward FFT along y, contraction ----
