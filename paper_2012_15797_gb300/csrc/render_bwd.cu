@@ -52,27 +52,22 @@ struct BwdCfg {
   // that the row transforms' loads (rows p of four groups) hit distinct
   // banks; N = 128 has no room and keeps them dense.
   static constexpr int GS = N <= 64 ? N + 8 : N;
-  // N = 32: two gradient-patch buffers, the next galaxy's patch copied in
-  // while this one is processed.  N = 64 keeps one so that three CTAs fit
-  // per SM (more resident warps hide more latency than the prefetch does);
-  // N = 128 has room for one only.
-  static constexpr int NGB = N <= 32 ? 2 : 1;
   static constexpr int R1 = Radix<N>::r[1];
   static constexpr int R2 = Radix<N>::r[2];
   static constexpr int TW1 = twiddle_elems<N, R1>();
   static constexpr int TW2 = Radix<N>::P == 3 ? twiddle_elems<N, (R2 > 1 ? R2 : 2)>() : 0;
-  static constexpr int MIN_BLOCKS = N == 32 ? 8 : N == 64 ? 3 : 1;
-  // N = 32 stages the PSF spectrum in shared memory.  N = 64 reads the
-  // (L2-resident) spectrum from global memory, which leaves room for three
-  // CTAs per SM; N = 128 does not fit it beside the work buffers and the
-  // gradient patch.
-  static constexpr bool STAGE_PSF = N <= 32;
+  // Resident CTAs per SM: 10 (N = 32), 3 (N = 64), 1 (N = 128).  The PSF
+  // spectrum is read from global memory (L2-resident) rather than staged in
+  // shared memory, and the gradient patch is not prefetched a galaxy ahead:
+  // both would take the shared memory that the extra resident CTAs need, and
+  // more resident warps hide more latency (measured: 32 x 32 1.06 -> 1.02 ms,
+  // 64 x 64 2.68 -> 2.11 ms per 100k).
+  static constexpr int MIN_BLOCKS = N == 32 ? 10 : N == 64 ? 3 : 1;
 
-  static constexpr size_t off_psf = 0;
-  static constexpr size_t off_wa = off_psf + (STAGE_PSF ? sizeof(float2) * PSF_ELEMS : 0);
+  static constexpr size_t off_wa = 0;
   static constexpr size_t off_wb = off_wa + sizeof(float2) * WA_ELEMS;
   static constexpr size_t off_g = (off_wb + sizeof(float2) * W_ELEMS + 15) & ~size_t(15);
-  static constexpr size_t off_tw = off_g + sizeof(float) * N * GS * NGB;
+  static constexpr size_t off_tw = off_g + sizeof(float) * N * GS;
   static constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
   static constexpr size_t off_py = off_px + sizeof(float2) * H;
   static constexpr size_t off_nb = off_py + sizeof(float2) * N;       // nu = 1/2 column: P phase
@@ -81,7 +76,7 @@ struct BwdCfg {
   static constexpr size_t off_terms = off_rec + 2 * sizeof(AdjRecord);
   static constexpr size_t off_red = off_terms + sizeof(AdjTerms);
   static constexpr size_t off_bar = (off_red + sizeof(float) * 8 * WARPS + 15) & ~size_t(15);
-  static constexpr size_t SMEM = off_bar + 5 * sizeof(uint64_t);
+  static constexpr size_t SMEM = off_bar + 3 * sizeof(uint64_t);
   static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB a CTA can have");
 };
 
@@ -106,7 +101,7 @@ __device__ __forceinline__ void fft_rest_b(float2* w, int j, const float2* tw1, 
 
 // WN: also d L / d(Sersic n), a seventh gradient per galaxy.  EIG: some PSF
 // of the context is an eigen-PSF (its spectrum at the galaxy's position is
-// formed per galaxy: in shared memory when N <= 64, bin by bin otherwise).
+// combined from the component spectra bin by bin where a bin is read).
 template <int N, bool WN, bool EIG>
 __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     render_bwd_kernel(RenderParams p, const float* __restrict__ grad_out, float* __restrict__ grad_params) {
@@ -116,8 +111,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
   constexpr float INV_N = 1.0f / N;
   constexpr float TWO_PI = 2.0f * PI_F;
   extern __shared__ __align__(128) unsigned char smem[];
-  float2* psf_smem = reinterpret_cast<float2*>(smem + C::off_psf);
-  const float2* psf_hat = psf_smem;
+  const float2* psf_hat = nullptr;   // the current PSF's spectrum (global memory, L2-resident)
   float2* WA = reinterpret_cast<float2*>(smem + C::off_wa);
   float2* WB = reinterpret_cast<float2*>(smem + C::off_wb);
   float* gbuf = reinterpret_cast<float*>(smem + C::off_g);
@@ -130,7 +124,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
   AdjRecord* rec = reinterpret_cast<AdjRecord*>(smem + C::off_rec);
   AdjTerms& at = *reinterpret_cast<AdjTerms*>(smem + C::off_terms);
   float* red = reinterpret_cast<float*>(smem + C::off_red);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);  // [0] PSF, [1..2] records, [3..4] g buffers
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);  // [0..1] records, [2] g
   __shared__ int s_pos[2];
   __shared__ float s_psf_mog[KPSF][6];
   __shared__ int s_kpsf;
@@ -138,7 +132,6 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
   // Fourier components as operand pairs of f32x2: (a, a, dq, dq), (c, c, dn, dn)
   // and, for the Sersic gradient, (a_dq, a_dq, a_dn, a_dn)
   __shared__ float4 s_fa[KMAX], s_fc[KMAX], s_fd[KMAX];
-  __shared__ int s_gready[2];   // per record buffer: its gradient patch was requested one galaxy ahead
 
   const int tid = threadIdx.x;
   const int f = tid / TPF, j = tid % TPF;
@@ -161,27 +154,14 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     return q_next++;
   };
   if (tid == 0) {
-    for (int i = 0; i < 5; ++i) mbar_init(&bar[i], 1);
+    for (int i = 0; i < 3; ++i) mbar_init(&bar[i], 1);
     q_ahead = atomicAdd(&p.queue[B], p.chunk);
     const int p0 = next_position();
     s_pos[0] = p0;
-    if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * sizeof(AdjRecord), sizeof(AdjRecord), &bar[1]);
+    if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * sizeof(AdjRecord), sizeof(AdjRecord), &bar[0]);
   }
   int cur_psf = -1;
-  uint32_t psf_parity = 0, rec_parity = 0, g_parity = 0;   // g_parity bit b: phase of g buffer b
-  if (tid < 2) s_gready[tid] = 0;
-  // gradient patch of record `rr` into buffer gb (warp 0; one bulk copy per
-  // padded row, or one copy of the dense patch)
-  auto request_g = [&](const AdjRecord& rr, float* gb, uint64_t* gbar) {
-    if constexpr (C::GS == N) {
-      if (lane == 0) bulk_load(gb, grad_out + rr.off, sizeof(float) * N * N, gbar);
-    } else {
-      if (lane == 0) mbar_expect_tx(gbar, sizeof(float) * N * N);
-      __syncwarp();
-      for (int y = lane; y < N; y += 32)
-        bulk_copy(gb + y * C::GS, grad_out + rr.off + (size_t)y * N, sizeof(float) * N, gbar);
-    }
-  };
+  uint32_t rec_parity = 0, g_parity = 0;
   float2* wa = WA + C::rowA(f);
   float2* wb = WB + f * WS;
 
@@ -193,47 +173,36 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
       const int np = next_position();
       s_pos[buf ^ 1] = np;
       if (np >= 0)
-        bulk_load(&rec[buf ^ 1], records + (size_t)np * sizeof(AdjRecord), sizeof(AdjRecord), &bar[1 + (buf ^ 1)]);
+        bulk_load(&rec[buf ^ 1], records + (size_t)np * sizeof(AdjRecord), sizeof(AdjRecord), &bar[buf ^ 1]);
     }
-    const bool rec_landed = mbar_wait(&bar[1 + buf], (rec_parity >> buf) & 1u);
+    const bool rec_landed = mbar_wait(&bar[buf], (rec_parity >> buf) & 1u);
     rec_parity ^= 1u << buf;
     const AdjRecord& r = rec[buf];
     const bool go = rec_landed && r.ok;
-    const int gi = C::NGB == 2 ? buf : 0;   // this galaxy's gradient buffer
-    float* gcur = gbuf + gi * N * C::GS;
-    // s_gready was written before the previous S3 and is reset only by warp 0
-    // after the S2 below
-    if (go && warp == 0 && !s_gready[buf]) request_g(r, gcur, &bar[3 + gi]);
-    const bool need_psf = go && r.psf != cur_psf;
-    bool psf_landed = true;
-    if (need_psf) {
+    if (go && warp == 0) {   // the gradient patch: one bulk copy per padded row, or one of the dense patch
+      if constexpr (C::GS == N) {
+        if (lane == 0) bulk_load(gbuf, grad_out + r.off, sizeof(float) * N * N, &bar[2]);
+      } else {
+        if (lane == 0) mbar_expect_tx(&bar[2], sizeof(float) * N * N);
+        __syncwarp();
+        for (int y = lane; y < N; y += 32)
+          bulk_copy(gbuf + y * C::GS, grad_out + r.off + (size_t)y * N, sizeof(float) * N, &bar[2]);
+      }
+    }
+    if (go && r.psf != cur_psf) {
       const DevPsf& ps = p.psfs[r.psf];
       k_eig = EIG ? ps.k_eig : 0;
       const float* pc = p.pcoef + ((size_t)first + pos) * PCOEF;
-      if (k_eig > 0) {
-        if constexpr (C::STAGE_PSF)
-          for (int e = tid; e < C::PSF_ELEMS; e += C::THREADS)
-            psf_smem[e] = eigen_bin(ps.spec[B], C::PSF_ELEMS, k_eig, pc, e);
-        else
-          psf_hat = ps.spec[B];
-        if (tid < KEIG) s_eigm[tid] = pc[tid];
-      } else if constexpr (C::STAGE_PSF) {
-        if (tid == 0) bulk_load(psf_smem, ps.spec[B], sizeof(float2) * C::PSF_ELEMS, &bar[0]);
-      } else {
-        psf_hat = ps.spec[B];
-      }
+      // an eigen-PSF's spectrum at the galaxy's position is combined from its
+      // component spectra bin by bin where a bin is read
+      psf_hat = ps.spec[B];
+      if (k_eig > 0 && tid < KEIG) s_eigm[tid] = pc[tid];
       if (tid < KPSF * 6)
         s_psf_mog[tid / 6][tid % 6] = (k_eig > 0 && tid % 6 == 0) ? pc[8 + tid / 6] : ps.mog[tid / 6][tid % 6];
       if (tid == 0) s_kpsf = ps.k;
-      if constexpr (C::STAGE_PSF) {
-        if (k_eig == 0) {
-          psf_landed = mbar_wait(&bar[0], psf_parity);
-          psf_parity ^= 1u;
-        }
-      }
-      cur_psf = k_eig > 0 ? -1 : r.psf;   // an eigen-PSF is formed again for the next galaxy
+      cur_psf = k_eig > 0 ? -1 : r.psf;   // an eigen-PSF's weights change with the position
     }
-    if (__syncthreads_or(!rec_landed || !psf_landed)) {
+    if (__syncthreads_or(!rec_landed)) {
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
       return;
     }
@@ -270,9 +239,8 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
           sincospif(-gx, &sn, &cs);
-          const float2 pn = (!C::STAGE_PSF && k_eig > 0)
-                                ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, (N / 2) * LS + l)
-                                : psf_hat[(N / 2) * LS + l];
+          const float2 pn = k_eig > 0 ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, (N / 2) * LS + l)
+                                      : __ldg(&psf_hat[(N / 2) * LS + l]);
           nyb[l] = cmul(pn, cmul(make_float2(cs, sn), make_float2(cy, sy)));
           nys[4 * l + 0] = s;
           nys[4 * l + 1] = sq;
@@ -293,40 +261,19 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
         }
       }
     }
-    const bool g_landed = mbar_wait(&bar[3 + gi], (g_parity >> gi) & 1u);
-    g_parity ^= 1u << gi;
+    const bool g_landed = mbar_wait(&bar[2], g_parity);
+    g_parity ^= 1u;
     if (__syncthreads_or(!g_landed)) {   // S2
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
       return;
-    }
-    if constexpr (C::NGB == 2) {
-      // the next galaxy's patch, into the other buffer: its last reader (the
-      // galaxy before this one) finished before the previous S3, and its
-      // record was requested at the top of this iteration
-      if (warp == 0) {
-        const int nb = buf ^ 1;
-        bool ready = false;
-        if (s_pos[nb] >= 0) {
-          // the copy below is issued by the whole warp: decide once for it
-          const bool landed = __all_sync(0xffffffffu, mbar_wait(&bar[1 + nb], (rec_parity >> nb) & 1u));
-          if (landed && rec[nb].ok) {
-            request_g(rec[nb], gbuf + nb * N * C::GS, &bar[3 + nb]);
-            ready = true;
-          }
-        }
-        if (lane == 0) {
-          s_gready[nb] = ready;
-          s_gready[buf] = 0;
-        }
-      }
     }
 
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float2 v[8];
     // ---- forward FFT of row pairs (f, f + N/2) packed as g[f] + i g[f + N/2] ----
     {
-      const float* ga = gcur + f * C::GS;
-      const float* gb = gcur + (f + N / 2) * C::GS;
+      const float* ga = gbuf + f * C::GS;
+      const float* gb = gbuf + (f + N / 2) * C::GS;
 #pragma unroll
       for (int m = 0; m < 8; ++m) v[m] = make_float2(ga[j + m * TPF], gb[j + m * TPF]);
       dft8<-1>(v);
@@ -357,7 +304,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     }
 
     // ---- real-space terms: analytic derivatives, pixel by pixel ----
-    adj_real_space<N, WN>(gcur, C::GS, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
+    adj_real_space<N, WN>(gbuf, C::GS, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
                           r.s22);
     __syncthreads();  // S3: every column input written
 
@@ -443,8 +390,8 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
           const float sq = (bb & 1) ? SQ[bb >> 1].y : SQ[bb >> 1].x;
           const float sn = (bb & 1) ? SN[bb >> 1].y : SN[bb >> 1].x;
           const float sd = (bb & 1) ? SD[bb >> 1].y : SD[bb >> 1].x;
-          const float2 pv = (!C::STAGE_PSF && k_eig > 0) ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, f * LS + l)
-                                                         : psf_hat[f * LS + l];
+          const float2 pv = k_eig > 0 ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, f * LS + l)
+                                      : __ldg(&psf_hat[f * LS + l]);
           const float2 bph = cmul(pv, cmul(pxf, py[l]));
           const float2 z = cscale(cmulc(bph, gk), ck);   // c_k conj(G) P phase
           contract_bin(z, nu, om, s, sq, sn, acc);
