@@ -864,6 +864,44 @@ __device__ __forceinline__ void adj_real_term_zero(int t, AdjTerms* at) {
   at->mx[t] = at->my[t] = 0.0f;
 }
 
+// Mixture sums of the adjoint at K bin pairs (2k, 2k+1 packed in f32x2, q
+// values qp): S = sum a 2^(c q), SQ = sum a_q 2^(c q), SN = sum a_n 2^(c q)
+// and, with WN, SD = sum (a_dq q + a_dn) 2^(c q), components outer.  The
+// component tables hold operand pairs: fa = (a, a, a_q, a_q), fc = (c, c,
+// a_n, a_n), fd = (a_dq, a_dq, a_dn, a_dn).
+template <int K, bool WN>
+__device__ __forceinline__ void adj_mixture_sums(const float4* fa, const float4* fc, const float4* fd, int nf,
+                                                 const float2 (&qp)[K], float2 (&S)[K], float2 (&SQ)[K],
+                                                 float2 (&SN)[K], float2 (&SD)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) S[k] = SQ[k] = SN[k] = SD[k] = make_float2(0.0f, 0.0f);
+  for (int c = 0; c < nf; ++c) {
+    const float4 cn = fc[c], aq = fa[c];
+    const float2 c2 = make_float2(cn.x, cn.y), n2 = make_float2(cn.z, cn.w);
+    const float2 a2 = make_float2(aq.x, aq.y), q2 = make_float2(aq.z, aq.w);
+    float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (WN) dd = fd[c];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 x = __fmul2_rn(c2, qp[k]);
+      const float2 e = make_float2(ex2(x.x), ex2(x.y));
+      S[k] = __ffma2_rn(a2, e, S[k]);
+      SQ[k] = __ffma2_rn(q2, e, SQ[k]);
+      SN[k] = __ffma2_rn(n2, e, SN[k]);
+      if constexpr (WN)
+        SD[k] = __ffma2_rn(__ffma2_rn(make_float2(dd.x, dd.y), qp[k], make_float2(dd.z, dd.w)), e, SD[k]);
+    }
+  }
+}
+
+// The component tables of adj_mixture_sums for component c (one thread).
+__device__ __forceinline__ void adj_component_tables(const AdjRecord& r, int c, float4* fa, float4* fc,
+                                                     float4* fd) {
+  fa[c] = make_float4(r.famp[c], r.famp[c], r.fq[c], r.fq[c]);
+  fc[c] = make_float4(r.fcoef[c], r.fcoef[c], r.fn[c], r.fn[c]);
+  fd[c] = make_float4(r.fdq[c], r.fdq[c], r.fdn[c], r.fdn[c]);
+}
+
 // Adds one bin's contribution.  z = c_k conj(G) P phase; (s, sq, sn) the
 // weighted mixture sums at the bin.
 __device__ __forceinline__ void contract_bin(float2 z, float nu, float om, float s, float sq, float sn,

@@ -253,10 +253,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
           } else if (t < nr2) {
             adj_real_term_zero(t, &at);
           } else {
-            const int c = t - nr2;
-            s_fa[c] = make_float4(r.famp[c], r.famp[c], r.fq[c], r.fq[c]);
-            s_fc[c] = make_float4(r.fcoef[c], r.fcoef[c], r.fn[c], r.fn[c]);
-            if constexpr (WN) s_fd[c] = make_float4(r.fdq[c], r.fdq[c], r.fdn[c], r.fdn[c]);
+            adj_component_tables(r, t - nr2, s_fa, s_fc, s_fd);
           }
         }
       }
@@ -353,26 +350,8 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
             qq[h] = fmaf(om, fmaf(s22, om, a1), a0);
           }
           qp[k] = make_float2(qq[0], qq[1]);
-          S[k] = SQ[k] = SN[k] = SD[k] = make_float2(0.0f, 0.0f);
         }
-        for (int c = 0; c < nf; ++c) {
-          const float4 cn = s_fc[c];
-          const float4 aq = s_fa[c];
-          const float2 c2 = make_float2(cn.x, cn.y), n2 = make_float2(cn.z, cn.w);
-          const float2 a2 = make_float2(aq.x, aq.y), q2 = make_float2(aq.z, aq.w);
-          float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
-          if constexpr (WN) dd = s_fd[c];
-#pragma unroll
-          for (int k = 0; k < BH / 2; ++k) {
-            const float2 x = __fmul2_rn(c2, qp[k]);
-            const float2 e = make_float2(ex2(x.x), ex2(x.y));
-            S[k] = __ffma2_rn(a2, e, S[k]);
-            SQ[k] = __ffma2_rn(q2, e, SQ[k]);
-            SN[k] = __ffma2_rn(n2, e, SN[k]);
-            if constexpr (WN)
-              SD[k] = __ffma2_rn(__ffma2_rn(make_float2(dd.x, dd.y), qp[k], make_float2(dd.z, dd.w)), e, SD[k]);
-          }
-        }
+        adj_mixture_sums<BH / 2, WN>(s_fa, s_fc, s_fd, nf, qp, S, SQ, SN, SD);
 #pragma unroll
         for (int bb = 0; bb < BH; ++bb) {
           const int b = b0 + bb, q = b / R, m = b % R;

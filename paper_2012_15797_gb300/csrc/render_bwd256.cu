@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ float s_psf_mog[KPSF][6];
   __shared__ float s_eigm[KEIG];
   __shared__ int s_kpsf;
+  __shared__ float4 s_fa[KMAX], s_fc[KMAX], s_fd[KMAX];   // component tables of adj_mixture_sums
 
   const int tid = threadIdx.x;
   const int f = tid >> 5, j = tid & 31;
@@ -141,7 +142,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const float gx = r.x, gy = r.y;
       const int kp = s_kpsf;
       const int nrt = r.nrc * kp;
-      const int ntask = H + 2 * N + real_terms_padded(nrt);
+      const int nr2 = real_terms_padded(nrt);
+      const int ntask = H + 2 * N + nr2 + r.nf;
       for (int i = tid; i < ntask; i += THREADS) {
         float sn, cs;
         if (i < H) {
@@ -176,7 +178,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         } else {
           const int t = i - H - 2 * N;
           if (t < nrt) adj_real_term(r, s_psf_mog, kp, N, t, &at);
-          else adj_real_term_zero(t, &at);
+          else if (t < nr2) adj_real_term_zero(t, &at);
+          else adj_component_tables(r, t - nr2, s_fa, s_fc, s_fd);
         }
       }
     }
@@ -255,28 +258,39 @@ __global__ void __launch_bounds__(THREADS, 1)
       const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
       const float ck = k == 0 ? 1.0f : 2.0f;
       const float2 pxk = px[k];
+      // mixture sums, components outer, 4 bins per sweep (two sweeps)
 #pragma unroll
-      for (int qq = 0; qq < 8 / R2; ++qq)
+      for (int b0 = 0; b0 < 8; b0 += 4) {
+        float2 qp[2], S[2], SQ[2], SN[2], SD[2];
 #pragma unroll
-        for (int m = 0; m < R2; ++m) {
+        for (int kk = 0; kk < 2; ++kk) {
+          float qv[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int b = b0 + 2 * kk + h;
+            const int l = stockham_out_index<N, R2>(j, N / R2, b / R2, b % R2);
+            const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+            qv[h] = fmaf(om, fmaf(s22, om, a1), a0);
+          }
+          qp[kk] = make_float2(qv[0], qv[1]);
+        }
+        adj_mixture_sums<2, WN>(s_fa, s_fc, s_fd, nf, qp, S, SQ, SN, SD);
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+          const int b = b0 + bb, qq = b / R2, m = b % R2;
           const int l = stockham_out_index<N, R2>(j, N / R2, qq, m);
           const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
-          float2 gk = v[qq * R2 + m];
+          float2 gk = v[b];
           float2 gn = make_float2(0.f, 0.f);
           if (k == 0) {
             const float2 u = w[swz<N>(l)], un = w[swz<N>((N - l) & (N - 1))];
             gk = make_float2(0.5f * (u.x + un.x), 0.5f * (u.y - un.y));
             gn = make_float2(0.5f * (u.y + un.y), -0.5f * (u.x - un.x));
           }
-          const float qv = fmaf(om, fmaf(s22, om, a1), a0);
-          float s = 0.0f, sq = 0.0f, sn = 0.0f, sd = 0.0f;
-          for (int c = 0; c < nf; ++c) {
-            const float e = ex2(r.fcoef[c] * qv);
-            s = fmaf(r.famp[c], e, s);
-            sq = fmaf(r.fq[c], e, sq);
-            sn = fmaf(r.fn[c], e, sn);
-            if constexpr (WN) sd = fmaf(fmaf(r.fdq[c], qv, r.fdn[c]), e, sd);
-          }
+          const float s = (bb & 1) ? S[bb >> 1].y : S[bb >> 1].x;
+          const float sq = (bb & 1) ? SQ[bb >> 1].y : SQ[bb >> 1].x;
+          const float sn = (bb & 1) ? SN[bb >> 1].y : SN[bb >> 1].x;
+          const float sd = (bb & 1) ? SD[bb >> 1].y : SD[bb >> 1].x;
           const float2 pv = k_eig > 0 ? eigen_bin(psf_hat, PSF_ELEMS, k_eig, s_eigm, k * LS + l) : __ldg(&psf_hat[k * LS + l]);
           const float2 bph = cmul(pv, cmul(pxk, py[l]));
           const float2 z = cscale(cmulc(bph, gk), ck);
@@ -288,6 +302,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if constexpr (WN) acc[6] = fmaf(zn.x, nys[4 * l + 3], acc[6]);
           }
         }
+      }
       __syncwarp();
     }
 
