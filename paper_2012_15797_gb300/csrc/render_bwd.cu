@@ -62,12 +62,17 @@ struct BwdCfg {
   // both would take the shared memory that the extra resident CTAs need, and
   // more resident warps hide more latency (measured: 32 x 32 1.06 -> 1.02 ms,
   // 64 x 64 2.68 -> 2.11 ms per 100k).
-  static constexpr int MIN_BLOCKS = N == 32 ? 10 : N == 64 ? 3 : 1;
+  static constexpr int MIN_BLOCKS = N == 32 ? 10 : N == 64 ? 4 : 1;
+  // N = 64: the gradient patch and the row transforms' work rows share one
+  // region (both 18 KB): the real-space pass and the row transforms' first
+  // loads read the patch, then a CTA barrier, then the work rows are written
+  static constexpr bool ALIAS_G = N == 64;
+  static_assert(!ALIAS_G || sizeof(float) * N * GS <= sizeof(float2) * NFFT * WS, "patch must fit the work rows");
 
   static constexpr size_t off_wa = 0;
   static constexpr size_t off_wb = off_wa + sizeof(float2) * WA_ELEMS;
-  static constexpr size_t off_g = (off_wb + sizeof(float2) * W_ELEMS + 15) & ~size_t(15);
-  static constexpr size_t off_tw = off_g + sizeof(float) * N * GS;
+  static constexpr size_t off_g = ALIAS_G ? off_wb : (off_wb + sizeof(float2) * W_ELEMS + 15) & ~size_t(15);
+  static constexpr size_t off_tw = ALIAS_G ? off_wb + sizeof(float2) * W_ELEMS : off_g + sizeof(float) * N * GS;
   static constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
   static constexpr size_t off_py = off_px + sizeof(float2) * H;
   static constexpr size_t off_nb = off_py + sizeof(float2) * N;       // nu = 1/2 column: P phase
@@ -267,12 +272,16 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
 
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float2 v[8];
+    if constexpr (C::ALIAS_G)   // the patch is read before the work rows overwrite it
+      adj_real_space<N, WN>(gbuf, C::GS, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
+                            r.s22);
     // ---- forward FFT of row pairs (f, f + N/2) packed as g[f] + i g[f + N/2] ----
     {
       const float* ga = gbuf + f * C::GS;
       const float* gb = gbuf + (f + N / 2) * C::GS;
 #pragma unroll
       for (int m = 0; m < 8; ++m) v[m] = make_float2(ga[j + m * TPF], gb[j + m * TPF]);
+      if constexpr (C::ALIAS_G) __syncthreads();   // every row of the patch is in registers
       dft8<-1>(v);
 #pragma unroll
       for (int m = 0; m < 8; ++m) wb[swz<N>(8 * j + m)] = v[m];
@@ -301,8 +310,9 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     }
 
     // ---- real-space terms: analytic derivatives, pixel by pixel ----
-    adj_real_space<N, WN>(gbuf, C::GS, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
-                          r.s22);
+    if constexpr (!C::ALIAS_G)
+      adj_real_space<N, WN>(gbuf, C::GS, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
+                            r.s22);
     __syncthreads();  // S3: every column input written
 
     // ---- forward FFT of every column along y ----
