@@ -223,6 +223,35 @@ mog_status mog_render_batch_ex(mog_ctx* ctx, const mog_batch* batch, float* out,
 mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
 
 /*
+ * Renders a batch whose arrays and output live in host memory (the paper's
+ * workloads read galaxy parameters from catalogues and write model images;
+ * this is the entry point for callers that hold both on the host).  Same
+ * model as mog_render_batch; every pointer of `batch` and `out` is a host
+ * pointer.  The patches must be packed in galaxy order:
+ * offset[g + 1] = offset[g] + size[g]^2 (offset[0] >= 0), and
+ * out[offset[g] .. offset[g] + size[g]^2) receives galaxy g.
+ *
+ * The parameter arrays are copied to the device once (about 48 bytes per
+ * galaxy); the galaxies are then rendered in chunks of at most `chunk`
+ * galaxies (0: chunks of about 64 MiB of patches) and each chunk's patches
+ * copied back into `out`.  Chunks alternate between two streams with their
+ * own workspaces, so that the copy of one chunk's patches overlaps the render
+ * of the next.  For the copies to run asynchronously, `out` and the batch
+ * arrays should be page-locked (cudaHostAlloc / pinned); pageable memory
+ * works but serialises the copies.  The staging (the parameters and two
+ * chunks of patches) and the workspaces are allocated on first use, grown
+ * when a call needs more, and kept by the context.
+ *
+ * flags: 0 or MOG_RENDER_LANCZOS (MOG_RENDER_ADD is rejected: the output is
+ * not read).  Synchronous: returns when every patch is in `out`, or with the
+ * first error (after waiting for the copies already issued).  Device-side
+ * parameter errors are reported by mog_sync_status as for the other calls.
+ * Errors: MOG_ERR_ARG for a null pointer, a patch side outside {32, 64, 128,
+ * 256}, offsets that are not packed, or unknown flags.
+ */
+mog_status mog_render_batch_host(mog_ctx* ctx, const mog_batch* batch, float* out, int64_t chunk, unsigned flags);
+
+/*
  * Adjoint of mog_render_batch (gradients for model fitting; the paper's
  * forward model of Section 2 differentiated analytically): for every galaxy
  * of the batch, given grad_out = dL/d(patch pixel) laid out exactly like the

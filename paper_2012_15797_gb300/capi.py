@@ -36,6 +36,7 @@ EXPORTED = (
     "mog_server_create", "mog_server_add_fit", "mog_server_submit", "mog_server_wait", "mog_server_replay",
     "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
     "mog_create_eigen_psf", "mog_render_batch_ex", "mog_render_backward_ex", "mog_fit_psf_mixture",
+    "mog_render_batch_host",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -94,6 +95,7 @@ def _load():
         "mog_render_backward_ex": ([VP, P(mog_batch), VP, VP, VP, ctypes.c_uint], I),
         "mog_fit_psf_mixture": ([VP, VP, I, I, I, I, I, VP, VP, VP], I),
         "mog_render_batch_noalloc": ([VP, P(mog_batch), VP, VP], I),
+        "mog_render_batch_host": ([VP, P(mog_batch), VP, ctypes.c_int64, ctypes.c_uint], I),
         "mog_autotune": ([VP, P(mog_batch), VP, VP, VP, VP, I, P(I)], I),
         "mog_graph_capture": ([VP, P(mog_batch), VP, P(VP)], I),
         "mog_graph_launch": ([VP, VP], I),
@@ -214,6 +216,14 @@ MOG_RENDER_LANCZOS, MOG_RENDER_ADD = 1, 2
 def mog_render_batch_ex(ctx, batch, out_ptr, stream=0, flags=0):
     _check(ctx, _lib.mog_render_batch_ex(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
                                          ctypes.c_void_p(int(stream)), ctypes.c_uint(int(flags))))
+
+
+def mog_render_batch_host(ctx, batch, out_ptr, chunk=0, flags=0):
+    """Render of a batch held in host memory into a host output (see
+    include/mogconv.h): packed patches, chunks pipelined over two streams;
+    returns when the patches are in the output."""
+    _check(ctx, _lib.mog_render_batch_host(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
+                                           ctypes.c_int64(int(chunk)), ctypes.c_uint(int(flags))))
 
 
 def mog_render_batch_noalloc(ctx, batch, out_ptr, stream=0):

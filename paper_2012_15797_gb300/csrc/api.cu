@@ -149,6 +149,7 @@ mog_status mog_destroy_context(mog_ctx* ctx) {
   cudaFree(ctx->d_psfs);
   cudaFree(ctx->d_status);
   workspace_free(&ctx->ws);
+  host_lanes_free(ctx->host_lanes, 2);
   cudaFree(ctx->d_dft_scratch);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);

@@ -29,6 +29,22 @@ struct Workspace {
 cudaError_t workspace_init(Workspace* ws);
 void workspace_free(Workspace* ws);
 
+// One of the two lanes of mog_render_batch_host: a stream, a workspace and
+// device staging for one chunk's patches (lane 0 also holds the batch's
+// parameters).
+struct HostLane {
+  bool ready = false;
+  Workspace ws;
+  cudaStream_t s = nullptr;
+  cudaEvent_t uploaded = nullptr;    // lane 0: the parameters are on the device
+  unsigned char* params = nullptr;   // the parameter arrays, 256-byte aligned each
+  size_t params_bytes = 0;
+  float* out = nullptr;              // the chunk's patches
+  size_t out_elems = 0;
+};
+
+void host_lanes_free(HostLane* lanes, int n);
+
 }  // namespace mog
 
 struct mog_ctx {
@@ -42,6 +58,7 @@ struct mog_ctx {
   int* d_status = nullptr;
   double2* d_dft_scratch = nullptr;
   mog::Workspace ws;             // the workspace of the plain entry points
+  mog::HostLane host_lanes[2];   // mog_render_batch_host
   std::string last_error;
   // measurement hooks
   bool timing = false;

@@ -26,13 +26,19 @@ class DeviceBatch:
         return {k: v.data_ptr() for k, v in self.tensors.items()}
 
     def size_mask(self):
-        m = 0
-        for n in np.unique(self.sizes):
-            b = {32: 0, 64: 1, 128: 2, 256: 3}.get(int(n))
-            if b is None:
-                return 0
-            m |= 1 << b
-        return m
+        return size_mask(self.sizes)
+
+
+def size_mask(sizes):
+    """Bitmask of the patch sides present (bit b: N = 32 << b); 0 when a
+    side is not one of them (the library then reports it)."""
+    m = 0
+    for n in np.unique(np.asarray(sizes)):
+        b = {32: 0, 64: 1, 128: 2, 256: 3}.get(int(n))
+        if b is None:
+            return 0
+        m |= 1 << b
+    return m
 
 
 def pack_offsets(sizes):
@@ -118,6 +124,26 @@ class Renderer:
             return out
         fn = capi.mog_render_batch if shift == "phase" else capi.mog_render_batch_lanczos
         fn(self.ctx, b, out.data_ptr(), s.cuda_stream)
+        return out
+
+    def render_host(self, host, out=None, chunk=0, shift="phase"):
+        """Renders a batch held in host memory, ``host`` = ``host_batch(...)``
+        (tensors, pinned for asynchronous copies; packed offsets), into a host
+        float32 tensor (allocated pinned when ``out`` is None) through
+        mog_render_batch_host: chunks of at most ``chunk`` galaxies (0: about
+        64 MiB of patches), copies overlapping renders on two streams.
+        Synchronous."""
+        if shift not in ("phase", "lanczos"):
+            raise ValueError(f"unknown shift {shift!r}")
+        t, total = host
+        if out is None:
+            out = torch.empty(total, dtype=torch.float32).pin_memory()
+        if out.device.type != "cpu" or out.dtype != torch.float32 or out.numel() < total:
+            raise ValueError("out must be a host float32 tensor of the batch's total size")
+        # no size mask: the library works out each chunk's buckets itself
+        b = capi.make_batch(len(t["flux"]), {k: v.data_ptr() for k, v in t.items()})
+        capi.mog_render_batch_host(self.ctx, b, out.data_ptr(), chunk,
+                                   capi.MOG_RENDER_LANCZOS if shift == "lanczos" else 0)
         return out
 
     def render_composite(self, disk, bulge, out=None, stream=None, shift="phase"):
