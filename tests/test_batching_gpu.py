@@ -62,3 +62,39 @@ def test_graph_launch_matches_eager_and_sees_new_inputs(gpu_renderer):
     assert torch.equal(out, ref2)
     assert torch.allclose(ref2, 2.0 * ref, rtol=1e-5, atol=1e-6)
     g.close()
+
+
+def test_full_config2_graph_sampled(tables):
+    """The benchmark's mixed-size launch at full size: 200k galaxies (Sersic n
+    0.5-6, N = 32..256) with 64 Moffat-winged PSFs, launch shapes from the
+    autotuner, one CUDA-graph launch; every pixel written, and 32 sampled
+    patches (eight per patch side) within the method's tolerance of the FP64
+    oracle."""
+    import torch
+    from parity import check_parity, oracle_patches
+    from paper_2012_15797_gb300.renderer import Renderer, to_device
+    from workloads import config2_psfs
+    psfs = config2_psfs(64)
+    r = Renderer(tables, psfs)
+    try:
+        gals = config2_galaxies()
+        b = to_device(gals)
+        out = torch.empty(b.total, dtype=torch.float32, device="cuda")
+        r.autotune(b, out, reps=1)
+        g = r.graph(b, out)
+        out.fill_(float("nan"))
+        g.launch()
+        torch.cuda.synchronize()
+        r.sync_status()
+        g.close()
+        assert not torch.isnan(out).any()
+        rng = np.random.default_rng(7)
+        idx = np.sort(np.concatenate([rng.choice(np.flatnonzero(gals.size == n), 8, replace=False)
+                                      for n in (32, 64, 128, 256)]))
+        gpu = []
+        for i in idx:
+            n, o = int(b.sizes[i]), int(b.offsets[i])
+            gpu.append(out[o:o + n * n].view(n, n).double().cpu().numpy())
+        check_parity(gpu, oracle_patches(gals, psfs, tables, idx), gals, idx)
+    finally:
+        r.close()
