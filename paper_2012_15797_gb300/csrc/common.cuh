@@ -157,14 +157,23 @@ template <> struct Radix<64> { static constexpr int P = 2; static constexpr int 
 template <> struct Radix<128> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 2}; };
 template <> struct Radix<256> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 4}; };
 
-// Work rows hold one length-N transform each, padded to N + N/8 float2 with
-// the index map i + i/8, which spreads the stride-8 accesses of the passes
-// over the banks at the cost of one add per access.
+// Work rows hold one length-N transform each.  N = 32, 64, 256: index map
+// i + i/8 into rows padded to N + N/8 float2, which spreads the stride-8
+// accesses of the passes over the banks at the cost of one add per access.
+// N = 128, where one transform's 16 lanes are a half-warp (one shared-memory
+// wavefront of float2): i ^ ((i >> 3) & 15), a permutation inside each block
+// of 16 that gives the 16 lanes 16 different bank pairs in every pass
+// pattern, rows unpadded.  (With i + i/8 the 16th lane lands on the first
+// lane's banks in three of the five patterns: measured 2.9k extra
+// wavefronts per 128 x 128 galaxy.)
 template <int N>
-__device__ __forceinline__ int swz(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr bool swz_xor() { return N == 128; }
 
 template <int N>
-__host__ __device__ constexpr int wstride() { return N + N / 8; }
+__device__ __forceinline__ int swz(int i) { return swz_xor<N>() ? (i ^ ((i >> 3) & 15)) : i + (i >> 3); }
+
+template <int N>
+__host__ __device__ constexpr int wstride() { return swz_xor<N>() ? N : N + N / 8; }
 
 // Twiddle table of pass p (p >= 1) with radix R at sub-length Ns: entry
 // [(m - 1) N/R + b] = w_N^{m (b mod Ns) N / (Ns R)} for butterfly b < N/R and
@@ -185,8 +194,9 @@ __device__ __forceinline__ void fill_twiddles(float2* t, int ns, int tid, int nt
 }
 
 // Input of a pass after the first: gather + twiddle + R-point DFTs into v[8].
-// Every stride here is a multiple of 8, so swz(b + m S) = swz(b) + m 9S/8 and
-// only the butterfly base needs index arithmetic.
+// Every stride here is a multiple of 8, so with the i + i/8 map
+// swz(b + m S) = swz(b) + m 9S/8 and only the butterfly base needs index
+// arithmetic; the N = 128 permutation is applied per element.
 template <int N, int R, int S>
 __device__ __forceinline__ void stockham_load(const float2* buf, int j, const float2* twt, float2* v) {
   constexpr int NB = 8 / R;
@@ -200,7 +210,7 @@ __device__ __forceinline__ void stockham_load(const float2* buf, int j, const fl
     const float2* tw = twt + b;
 #pragma unroll
     for (int m = 0; m < R; ++m) {
-      float2 x = src[m * STEP];
+      float2 x = swz_xor<N>() ? buf[swz<N>(b + m * STRIDE)] : src[m * STEP];
       if (m > 0) {
         const float2 t = tw[(m - 1) * STRIDE];
         x = (S > 0) ? cmul(x, t) : cmulc(x, t);
@@ -228,15 +238,22 @@ __device__ __forceinline__ void stockham_store(float2* buf, int j, int ns, const
     float2* dst = buf + n0 + (n0 >> 3);
     const int step = ns + ns / 8;   // ns is 8 or a larger multiple of 8
 #pragma unroll
-    for (int m = 0; m < R; ++m) dst[m * step] = v[q * R + m];
+    for (int m = 0; m < R; ++m) {
+      if constexpr (swz_xor<N>()) buf[swz<N>(n0 + m * ns)] = v[q * R + m];
+      else dst[m * step] = v[q * R + m];
+    }
   }
 }
 
 // First-pass store (sub-length 1): value m of lane j goes to swz(8 j + m).
+template <int N>
 __device__ __forceinline__ void first_pass_store(float2* buf, int j, const float2* v) {
   float2* dst = buf + 9 * j;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) dst[m] = v[m];
+  for (int m = 0; m < 8; ++m) {
+    if constexpr (swz_xor<N>()) buf[swz<N>(8 * j + m)] = v[m];
+    else dst[m] = v[m];
+  }
 }
 
 // First-pass load of element j + m TPF (TPF = N/8 lanes per transform):
@@ -247,7 +264,7 @@ __device__ __forceinline__ void first_pass_load(const float2* buf, int j, float2
   constexpr int TPF = N / 8;
   const float2* src = buf + j + (j >> 3);
 #pragma unroll
-  for (int m = 0; m < 8; ++m) v[m] = src[m * TPF + ((m * TPF) >> 3)];
+  for (int m = 0; m < 8; ++m) v[m] = swz_xor<N>() ? buf[swz<N>(j + m * TPF)] : src[m * TPF + ((m * TPF) >> 3)];
 }
 
 // ------------------------------------------------------------------------

@@ -43,7 +43,7 @@ struct BwdCfg {
   // 88-float2 stride, N = 128 uses an odd stride.
   static constexpr int WS = wstride<N>();
   static constexpr int W_ELEMS = NFFT * WS;
-  static constexpr int WSA = N == 64 ? 88 : N == 128 ? 145 : WS;
+  static constexpr int WSA = N == 64 ? 88 : N == 128 ? 129 : WS;
   static constexpr int SKEWA = N == 64 ? 4 : 0;
   static_assert(SKEWA <= WSA - WS, "shifted rows must not overlap");
   __host__ __device__ static constexpr int rowA(int r) { return r * WSA + SKEWA * ((r >> 1) & 1); }

@@ -34,10 +34,11 @@ struct FwdCfg {
   static constexpr int THREADS = NFFT * TPF;
   static constexpr int LS = psf_lstride(N);
   static constexpr int PSF_ELEMS = psf_spec_elems(N);
-  // FFT work row stride (float2).  A row touches wstride<N>() = N + N/8
-  // slots.  N = 128: two more float2 spread the pairing writes (rows p of one
-  // instruction otherwise share 4 bank groups).  N = 64: 88 = 16 more, room
-  // for the row shift below.
+  // FFT work row stride (float2).  A row touches wstride<N>() slots.
+  // N = 128: two more float2 spread the pairing writes (16 rows per
+  // instruction) over 8 bank pairs; an odd stride would spread them over 16
+  // but would break the 16-byte alignment the output rows are read with.
+  // N = 64: 88 = 16 more, room for the row shift below.
   static constexpr int WS = wstride<N>() + (N == 128 ? 2 : N == 64 ? 16 : 0);
   // Row r of a work buffer starts at r WS + SKEW ((r >> 1) & 1): for N = 64
   // rows 2-3 of every 4 move by 4 float2, which spreads the pairing writes
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
 
     // ---- Step 7a: inverse FFT of every column along omega ----
     dft8<+1>(v);
-    first_pass_store(wa, j, v);
+    first_pass_store<N>(wa, j, v);
     __syncwarp();
     fft_rest<N, +1>(wa, j, tw1, tw2, v);
     if constexpr (C::ALIAS_W) __syncthreads();   // every column's last loads are done
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     first_pass_load<N>(wb, j, v);
     dft8<+1>(v);
     __syncwarp();
-    first_pass_store(wb, j, v);
+    first_pass_store<N>(wb, j, v);
     __syncwarp();
     fft_rest<N, +1>(wb, j, tw1, tw2, v);
     __syncwarp();
