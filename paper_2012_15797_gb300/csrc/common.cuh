@@ -157,17 +157,17 @@ template <> struct Radix<64> { static constexpr int P = 2; static constexpr int 
 template <> struct Radix<128> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 2}; };
 template <> struct Radix<256> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 4}; };
 
-// Work rows hold one length-N transform each.  N = 32, 64, 256: index map
+// Work rows hold one length-N transform each.  N = 32, 64: index map
 // i + i/8 into rows padded to N + N/8 float2, which spreads the stride-8
 // accesses of the passes over the banks at the cost of one add per access.
-// N = 128, where one transform's 16 lanes are a half-warp (one shared-memory
-// wavefront of float2): i ^ ((i >> 3) & 15), a permutation inside each block
-// of 16 that gives the 16 lanes 16 different bank pairs in every pass
-// pattern, rows unpadded.  (With i + i/8 the 16th lane lands on the first
-// lane's banks in three of the five patterns: measured 2.9k extra
-// wavefronts per 128 x 128 galaxy.)
+// N = 128, 256, where 16 lanes of one transform make a half-warp (one
+// shared-memory wavefront of float2): i ^ ((i >> 3) & 15), a permutation
+// inside each block of 16 that gives those 16 lanes 16 different bank pairs
+// in every pass pattern, rows unpadded.  (With i + i/8 the 16th lane lands
+// on the first lane's banks in three of the five patterns: measured 2.9k
+// extra wavefronts per 128 x 128 galaxy.)
 template <int N>
-__host__ __device__ constexpr bool swz_xor() { return N == 128; }
+__host__ __device__ constexpr bool swz_xor() { return N >= 128; }
 
 template <int N>
 __device__ __forceinline__ int swz(int i) { return swz_xor<N>() ? (i ^ ((i >> 3) & 15)) : i + (i >> 3); }

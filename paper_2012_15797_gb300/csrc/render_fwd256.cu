@@ -40,7 +40,9 @@ constexpr int WARPS = THREADS / 32;
 constexpr int ROUNDS = (N / 2) / WARPS;   // 4
 constexpr int LS = psf_lstride(N);
 constexpr int PSF_ELEMS = psf_spec_elems(N);
-constexpr int WS = wstride<N>();
+// transform rows keep N/8 float2 beyond wstride<N>(): the Lanczos strips
+// reuse that space
+constexpr int WS = wstride<N>() + N / 8;
 constexpr int R1 = Radix<N>::r[1], R2 = Radix<N>::r[2];
 constexpr int TW1 = twiddle_elems<N, R1>(), TW2 = twiddle_elems<N, R2>();
 constexpr int B = bucket_of(N);
