@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--galaxies", type=int, default=G_DEFAULT)
+    ap.add_argument("--size", type=int, default=0, choices=(0, 32, 64, 128, 256),
+                    help="with --only fwd/grad: the galaxies of that patch side out of a mixed-size draw of "
+                         "--galaxies (16 PSFs) instead of the 64x64 fixed-size batch")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -821,6 +824,11 @@ def run_only(args):
         gals = config1_galaxies(args.galaxies)
         gals.psf[:] = 1
         pos = eigen_positions(len(gals))
+    elif args.size:
+        import numpy as np
+        psfs = config2_psfs(16)
+        mixed = config2_galaxies(args.galaxies, n_psf=16)
+        gals = mixed.subset(np.flatnonzero(mixed.size == args.size))
     else:
         psfs = [config0_psf()]
         gals = config1_galaxies(args.galaxies)
