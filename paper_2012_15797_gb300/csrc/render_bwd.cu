@@ -341,11 +341,13 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
       const float2 pxf = px[f];
       // mixture sums at the thread's bins b = q R + m, components outer and
       // bins (2k, 2k+1) in packed f32x2, BH bins per sweep over the
-      // components (N >= 64 takes two sweeps of 4, which keeps the registers
-      // at three CTAs per SM for N = 64 and at 64 for N = 128's 1024
-      // threads).  No warp-level skip of negligible components: the
-      // per-component vote cost more than the work it saved (measured).
-      constexpr int BH = N >= 64 ? 4 : 8;
+      // components: N = 64 takes two sweeps of 4 (its register budget at
+      // four CTAs per SM), N = 128 four sweeps of 2 (64 registers for 1024
+      // threads: half the spills of two sweeps, 4.02 -> 3.95 ms for the
+      // 32.8k 128 x 128 galaxies of the mixed workload).  No warp-level skip
+      // of negligible components: the per-component vote cost more than the
+      // work it saved (measured).
+      constexpr int BH = N >= 128 ? 2 : N >= 64 ? 4 : 8;
 #pragma unroll
       for (int b0 = 0; b0 < 8; b0 += BH) {
         float2 qp[BH / 2], S[BH / 2], SQ[BH / 2], SN[BH / 2], SD[BH / 2];
