@@ -608,13 +608,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest x over the ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms):
+    """Whole-job units per second: every rank (replica) processes
+    units_per_rank in the slowest rank's ms."""
+    return world * units_per_rank / (ms / 1e3)
 
 
 # ----------------------------------------------------------------------------
@@ -667,7 +675,7 @@ def run_ours(args):
     r.sync_status()
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world)
-    value = world * args.galaxies * args.steps / (ms_max / 1e3)
+    value = job_throughput(args.galaxies * args.steps, world, ms_max)
 
     # end to end with host buffers, through the C-ABI call for host memory
     # (mog_render_batch_host: parameters copied in and patches copied out in
@@ -690,7 +698,7 @@ def run_ours(args):
         e2e_ms = (time.perf_counter() - t0) * 1e3
         barrier(world)
         e2e_ms = max_over_ranks(e2e_ms, world)
-        e2e = {"value": world * args.galaxies * k2 / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_throughput(args.galaxies * k2, world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": k2,
                "api": "mog_render_batch_host: pinned host parameters in, pinned host patches out, chunks of "
                       "64 MiB of patches pipelined over two streams; host clock around the synchronous call"}
