@@ -262,7 +262,26 @@ def cpu_baseline(galaxies, seconds):
     done = sum(counts)
     return {"value": done / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{done} galaxies of the 100k fixed-size batch (indices interleaved over {cores} spawn "
-                      f"workers, {seconds:.0f} s wall budget), FP64 numpy oracle"}
+                      f"workers, {seconds:.0f} s wall budget), FP64 numpy oracle",
+            "single_core": cpu_single_core(galaxies, max(2.0, seconds / 4))}
+
+
+def cpu_single_core(galaxies, seconds):
+    """The same oracle on one core (one spawn worker, one BLAS thread), for
+    a bounded wall time."""
+    import multiprocessing as mp
+    pool = mp.get_context("spawn").Pool(1, initializer=_worker_init, initargs=(galaxies,))
+    try:
+        pool.map(_worker_render, [list(range(20))])   # warm: first calls are slower
+        t0 = time.perf_counter()
+        done = pool.apply(_worker_timed, ((20, 1, seconds),))
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    return {"value": done / wall, "unit": UNIT, "cores": 1,
+            "sample": f"{done} galaxies of the 100k fixed-size batch in order from index 20, {seconds:.0f} s "
+                      f"wall budget"}
 
 
 # ----------------------------------------------------------------------------
