@@ -1,0 +1,144 @@
+"""Host-side checks of the shared-memory index maps the FFT kernels use
+(csrc/common.cuh: swz, wstride, stockham_out_index; csrc/render_fwd.cu and
+csrc/render_bwd.cu: work-row strides and skews).  The maps are mirrored here
+and tied to the source by the text checks in test_mirrors_match_the_source.
+
+Pinned: every map stays inside its row and is one-to-one (no access leaves a
+work row, no two elements share a slot); the real row transforms pair rows p
+and p + N/2 that the last column pass leaves in one thread, covering each pair
+once; and, by a model of the shared-memory banks (32 banks of 4 bytes; an
+8-byte access is served per half-warp, a 4-byte one per warp), the chosen maps
+make every pass pattern of a 128- or 256-point transform take the minimum
+number of wavefronts, which the i + i/8 map does not."""
+
+import os
+import re
+from collections import defaultdict
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2012_15797_gb300", "csrc")
+SIZES = (32, 64, 128, 256)
+LAST_RADIX = {32: 4, 64: 8, 128: 2, 256: 4}
+
+
+def swz_xor(n):
+    return n >= 128
+
+
+def swz(n, i):
+    return i ^ ((i >> 3) & 15) if swz_xor(n) else i + (i >> 3)
+
+
+def wstride(n):
+    return n if swz_xor(n) else n + n // 8
+
+
+def stockham_out_index(n, r, j, ns, q, m):
+    b = j + q * (n // 8)
+    return (b // ns) * ns * r + (b % ns) + m * ns
+
+
+def wavefronts(word_addrs, width):
+    """Shared-memory wavefronts of one warp-wide access of `width` 4-byte
+    words per lane (1: a warp at a time; 2: a half-warp at a time)."""
+    groups = [range(32)] if width == 1 else [range(0, 16), range(16, 32)]
+    total = 0
+    for g in groups:
+        banks = defaultdict(set)
+        for lane in g:
+            for w in range(width):
+                banks[(word_addrs[lane] + w) % 32].add(word_addrs[lane] + w)
+        total += max(len(s) for s in banks.values())
+    return total
+
+
+def test_mirrors_match_the_source():
+    common = open(os.path.join(CSRC, "common.cuh")).read()
+    assert "constexpr bool swz_xor() { return N >= 128; }" in common
+    assert "return swz_xor<N>() ? (i ^ ((i >> 3) & 15)) : i + (i >> 3);" in common
+    assert "return swz_xor<N>() ? N : N + N / 8;" in common
+    assert "return (b / ns) * ns * R + (b & (ns - 1)) + m * ns;" in common
+    fwd = open(os.path.join(CSRC, "render_fwd.cu")).read()
+    assert "static constexpr int WS = wstride<N>() + (N == 128 ? 2 : N == 64 ? 16 : 0);" in fwd
+    assert "static constexpr int SKEW = N == 64 ? 4 : 0;" in fwd
+    assert re.search(r"row\(int r\) \{ return r \* WS \+ SKEW \* \(\(r >> 1\) & 1\); \}", fwd)
+    bwd = open(os.path.join(CSRC, "render_bwd.cu")).read()
+    assert "static constexpr int WSA = N == 64 ? 88 : N == 128 ? 129 : WS;" in bwd
+    assert "static constexpr int SKEWA = N == 64 ? 4 : 0;" in bwd
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_index_map_is_one_to_one_inside_the_row(n):
+    slots = [swz(n, i) for i in range(n)]
+    assert len(set(slots)) == n
+    assert min(slots) >= 0 and max(slots) < wstride(n)
+
+
+@pytest.mark.parametrize("n", (32, 64, 128))
+def test_forward_work_rows_do_not_overlap(n):
+    ws = wstride(n) + (2 if n == 128 else 16 if n == 64 else 0)
+    skew = 4 if n == 64 else 0
+    assert skew <= ws - wstride(n)
+    rows = [r * ws + skew * ((r >> 1) & 1) for r in range(n // 2)]
+    for a, b in zip(rows, rows[1:]):
+        assert b - a >= wstride(n)
+    if n == 64:   # rows stay 16-byte aligned for the float4 output reads
+        assert all(r % 2 == 0 for r in rows)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_row_pairs_meet_in_one_thread(n):
+    """The last column pass leaves outputs m and m + R/2 of a thread in rows p
+    and p + N/2; over all threads those p cover [0, N/2) once."""
+    r = LAST_RADIX[n]
+    ns = n // r
+    seen = []
+    for j in range(n // 8):
+        for q in range(8 // r):
+            for m in range(r // 2):
+                p = stockham_out_index(n, r, j, ns, q, m)
+                assert stockham_out_index(n, r, j, ns, q, m + r // 2) == p + n // 2
+                seen.append(p)
+    assert sorted(seen) == list(range(n // 2))
+
+
+def _pass_patterns(n, index_map):
+    """Word addresses per warp instruction of the five pass access patterns
+    of one transform held by 16 (N = 128) or 32 (N = 256) lanes."""
+    tpf = n // 8
+    lanes = range(tpf) if tpf == 32 else list(range(16)) * 2
+    r1, r2 = 8, LAST_RADIX[n]
+    pats = []
+    for m in range(8):
+        pats.append([2 * index_map(8 * j + m) for j in lanes])                             # first-pass store
+        pats.append([2 * index_map(j + (n // r1) * m) for j in lanes])                     # pass-2 load
+        pats.append([2 * index_map((j // 8) * 64 + j % 8 + 8 * m) for j in lanes])         # pass-2 store
+        pats.append([2 * index_map(j + tpf * m) for j in lanes])                           # first-pass load
+    for q in range(8 // r2):
+        for m in range(r2):
+            pats.append([2 * index_map(j + tpf * q + (n // r2) * m) for j in lanes])      # pass-3 load
+    return pats
+
+
+@pytest.mark.parametrize("n", (128, 256))
+def test_large_transforms_take_the_minimum_wavefronts(n):
+    chosen = _pass_patterns(n, lambda i: swz(n, i))
+    assert all(wavefronts(p, 2) == 2 for p in chosen)   # 16 lanes x 8 bytes per half-warp: one wavefront each
+    # with i + i/8 a half-warp's 16th lane meets its first lane's banks
+    linear = _pass_patterns(n, lambda i: i + (i >> 3))
+    assert sum(wavefronts(p, 2) for p in linear) > 2 * len(linear)
+
+
+def test_adjoint_untangle_writes_spread_over_the_banks():
+    """The adjoint's untangle writes column k of 16 rows per half-warp for
+    N = 128: an odd row stride gives each lane its own bank pair."""
+    n, tpf, wsa = 128, 16, 129
+    for w in range(2):
+        for i in range(1, n // 2 // tpf):
+            addrs = []
+            for lane in range(32):
+                f, j = divmod(w * 32 + lane, tpf)
+                addrs.append(2 * ((j + tpf * i) * wsa + swz(n, f)))
+            assert wavefronts(addrs, 2) == 2
