@@ -68,16 +68,17 @@ def parse_args():
 # Algorithmic work of the method per galaxy (what it must compute).
 # ----------------------------------------------------------------------------
 
-def split_counts(gals, tables, kpsf, n):
+def split_counts(gals, tables, kpsf):
     """Per galaxy: Fourier components (w_F > 0) and real-space terms
     (components with w_F < 1 times PSF-mixture components), from the
-    aliasing split of Step 4."""
+    aliasing split of Step 4 at each galaxy's own patch side."""
     import numpy as np
     nf = np.zeros(len(gals), dtype=np.int64)
     nr = np.zeros(len(gals), dtype=np.int64)
     e = np.hypot(gals.e1.astype(np.float64), gals.e2.astype(np.float64))
     beta = (1 - e) / (1 + e)
     tr = np.exp(2 * gals.log_re.astype(np.float64)) * (1 + beta * beta)
+    side = np.asarray(gals.size, dtype=np.float64)
     for pid, t in tables.items():
         sel = np.nonzero(gals.profile == pid)[0]
         if len(sel) == 0:
@@ -91,7 +92,7 @@ def split_counts(gals, tables, kpsf, n):
             w = (u - j)[:, None]
             a = (1 - w) * t.amp[j] + w * t.amp[j + 1]
             v = np.exp((1 - w) * np.log(t.var[j]) + w * np.log(t.var[j + 1]))
-        ns = 0.5 * n / np.sqrt(v * tr[sel, None])
+        ns = 0.5 * side[sel, None] / np.sqrt(v * tr[sel, None])
         tt = np.clip(ns - 3.0, 0.0, 1.0)
         wf = tt * tt * (3 - 2 * tt)
         nf[sel] = ((a > 0) & (wf > 0)).sum(axis=1)
@@ -99,15 +100,75 @@ def split_counts(gals, tables, kpsf, n):
     return nf, nr
 
 
-def algorithmic_work(gals, tables, kpsf, n=N_PATCH):
-    nf, nr = split_counts(gals, tables, kpsf, n)
+def algorithmic_work(gals, tables, kpsf):
+    """What the forward method must compute for these galaxies (each at its
+    own patch side N), counted as the scope table of the hot path does:
+    HBM bytes = the patch written + the parameters read; MUFU ex2 = one per
+    Fourier component per half-spectrum bin + one per real-space term per
+    pixel; FP32 flops = 5 N^2 log2 N (the inverse real 2-D FFT) +
+    (14 + 2 n_F) per bin (quadratic form, PSF and phase products, and per
+    component a scale and an accumulate) + 8 per real-space term per pixel."""
+    import numpy as np
+    nf, nr = split_counts(gals, tables, kpsf)
+    n = np.asarray(gals.size, dtype=np.float64)
     bins = n * (n // 2 + 1)
     ex2 = float((nf * bins + nr * n * n).sum())
-    flops = float((5.0 * n * n * math.log2(n) + bins * (19.0 + 2.0 * nf) + 8.0 * nr * n * n).sum())
-    hbm = float(len(gals) * (n * n * 4 + PARAM_BYTES))
+    flops = float((5.0 * n * n * np.log2(n) + bins * (14.0 + 2.0 * nf) + 8.0 * nr * n * n).sum())
+    hbm = float((n * n * 4 + PARAM_BYTES).sum())
     comps = float(nf.sum() + nr.sum() / kpsf)
     return dict(ex2=ex2, flops=flops, hbm_bytes=hbm, real_fraction=float(nr.sum() / kpsf) / max(comps, 1.0),
                 fourier_components=float(nf.sum()), real_terms=float(nr.sum()))
+
+
+def adjoint_work(gals, tables, kpsf):
+    """What the adjoint must compute (6 gradients per galaxy): HBM bytes =
+    the upstream-gradient patch read + parameters read + 6 floats written;
+    MUFU ex2 as the forward (every Gaussian is evaluated once per bin or
+    pixel); FP32 flops = 5 N^2 log2 N (the forward real 2-D FFT of the
+    gradient patch) + (32 + 7 n_F) per bin (conj(G) P phase: 12, the six
+    gradient accumulations: 20; per component a scale and three
+    accumulations of value, q- and ramp-derivative) + 14 per real-space
+    term per pixel (the forward's 8 plus the three moments)."""
+    import numpy as np
+    nf, nr = split_counts(gals, tables, kpsf)
+    n = np.asarray(gals.size, dtype=np.float64)
+    bins = n * (n // 2 + 1)
+    ex2 = float((nf * bins + nr * n * n).sum())
+    flops = float((5.0 * n * n * np.log2(n) + bins * (32.0 + 7.0 * nf) + 14.0 * nr * n * n).sum())
+    hbm = float((n * n * 4 + PARAM_BYTES + 6 * 4).sum())
+    return dict(ex2=ex2, flops=flops, hbm_bytes=hbm)
+
+
+def add_work(a, b):
+    return {k: a[k] + b[k] for k in ("ex2", "flops", "hbm_bytes")}
+
+
+def roofline(work, ms, pk, kernel, traffic=None):
+    """Achieved / peak of the binding pipe for `work` done in `ms`, with the
+    fractions of all three (HBM bytes, MUFU ex2, FP32 flops)."""
+    t = {"hbm": work["hbm_bytes"] / pk["hbm"], "sfu": work["ex2"] / pk["sfu"], "fp32": work["flops"] / pk["fp32"]}
+    bound = max(t, key=t.get)
+    sec = ms / 1e3
+    if bound == "hbm":
+        roof = {"bound": "hbm", "achieved": work["hbm_bytes"] / sec / 1e9, "peak": pk["hbm"] / 1e9, "unit": "GB/s"}
+    elif bound == "sfu":
+        roof = {"bound": "alu", "pipe": "MUFU ex2", "achieved": work["ex2"] / sec / 1e12, "peak": pk["sfu"] / 1e12,
+                "unit": "Tex2/s"}
+    else:
+        roof = {"bound": "alu", "pipe": "FP32", "achieved": work["flops"] / sec / 1e12, "peak": pk["fp32"] / 1e12,
+                "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic
+    roof["kernel"] = kernel
+    roof["kernel_ms"] = ms
+    roof["peak_source"] = {"hbm": f"{pk['hbm_src']} HBM copy GB/s (MEASURED_PEAKS.json)",
+                           "sfu": f"{pk['num_sms']} SMs x {SFU_PER_CLK_SM} ex2/clk x {pk['sm_mhz']:.0f} MHz "
+                                  f"(ex2 rate measured, profiles/pipe_throughput.md)",
+                           "fp32": f"{pk['num_sms']} SMs x {FP32_FLOP_PER_CLK_SM} flop/clk x {pk['sm_mhz']:.0f} MHz "
+                                   f"(FFMA rate measured, profiles/pipe_throughput.md)"}[bound]
+    roof["fractions"] = {k: round(v / sec, 4) for k, v in t.items()}
+    roof["algorithmic_per_launch"] = {"hbm_bytes": work["hbm_bytes"], "ex2": work["ex2"], "flops": work["flops"]}
+    return roof
 
 
 def peaks(num_sms):
@@ -122,7 +183,7 @@ def peaks(num_sms):
         hbm, mhz, src = 6.8e12, 2070.0, "fallback"
     clk = mhz * 1e6
     return dict(hbm=hbm, hbm_src=src, sfu=num_sms * SFU_PER_CLK_SM * clk, fp32=num_sms * FP32_FLOP_PER_CLK_SM * clk,
-                sm_mhz=mhz)
+                sm_mhz=mhz, num_sms=num_sms)
 
 
 def kernel_source_sha():
@@ -302,7 +363,7 @@ def _event_ms(fn, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def extra_mixed(tables, device, steps):
+def extra_mixed(tables, device, steps, pk):
     """200k galaxies, Sersic n U(0.5, 6), N = smallest of 32..256 >= 8 r_e,
     64 PSFs: eager calls with default launch shapes vs one CUDA-graph launch
     per step after the autotuner."""
@@ -346,13 +407,29 @@ def extra_mixed(tables, device, steps):
         "autotuned_shapes": {f"{d}{n}": list(v) for (d, n), v in shapes.items()},
         "bytes_written": int(b.total) * 4,
     }
+    # roofline of the whole launch (the four size kernels run side by side in
+    # it) against the method's work for the 200k galaxies, and each size's
+    # kernel against its own galaxies' work over its event time
+    kpsf = psfs[0].mog.shape[0]
+    res["roofline"] = roofline(algorithmic_work(gals, tables, kpsf), graph_ms, pk,
+                               "graph: render_fwd_kernel<32|64|128> + render_fwd256_kernel")
+    per = {}
+    for i in range(4):
+        sel = np.flatnonzero(gals.size == (32 << i))
+        if len(sel) and kn[i]:
+            rf = roofline(algorithmic_work(gals.subset(sel), tables, kpsf), kms[i] / kn[i], pk, f"size {32 << i}")
+            per[32 << i] = {"bound": rf.get("pipe", rf["bound"]), "frac": round(rf["frac"], 4),
+                            "fractions": rf["fractions"]}
+    res["roofline_per_size"] = per
     r.close()
     return res
 
 
-def extra_render_grad(tables, psf, device, steps):
+def extra_render_grad(tables, psf, device, steps, pk):
     """50k galaxies at 64^2: render, inverse-variance-weighted residual
-    gradient (data from perturbed parameters + noise 0.01 peak), adjoint."""
+    gradient (data from perturbed parameters + noise 0.01 peak), adjoint.
+    The forward and adjoint kernels are also timed each on its own, for
+    their rooflines."""
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import Renderer, to_device
@@ -379,17 +456,29 @@ def extra_render_grad(tables, psf, device, steps):
     for _ in range(3):
         step()
     r.sync_status()
-    capi.mog_set_timing(r.ctx, True)
-    capi.mog_read_timing(r.ctx)
     ms = _event_ms(step, steps, st)
-    kms, kn = capi.mog_read_timing(r.ctx)
-    capi.mog_set_timing(r.ctx, False)
+
+    def kernel_ms(fn):
+        capi.mog_set_timing(r.ctx, True)
+        capi.mog_read_timing(r.ctx)
+        _event_ms(fn, steps, st)
+        kms, kn = capi.mog_read_timing(r.ctx)
+        capi.mog_set_timing(r.ctx, False)
+        return kms[1] / max(kn[1], 1)
+
+    fwd_ms = kernel_ms(lambda: r.render(bm, out))
+    bwd_ms = kernel_ms(lambda: r.render_backward(bm, gpix, gp))
     r.sync_status()
+    kpsf = psf.mog.shape[0]
+    wf, wb = algorithmic_work(model, tables, kpsf), adjoint_work(model, tables, kpsf)
     res = {"workload": "50000 galaxies as the fixed-size batch; loss = sum ivar (model - data)^2, data from "
                        "perturbed parameters + Gaussian noise sigma = 0.01 peak; gradients w.r.t. "
                        "(flux, x, y, log r_e, e1, e2)",
            "value": len(model) / (ms / 1e3), "unit": "patches rendered+grad/s", "ms_per_step": ms,
-           "kernel_ms_forward_plus_adjoint": kms[1] / max(kn[1], 1) * 2}
+           "kernel_ms_forward": fwd_ms, "kernel_ms_adjoint": bwd_ms,
+           "roofline": roofline(wb, bwd_ms, pk, "render_bwd_kernel<64>"),
+           "roofline_forward_plus_adjoint_kernels": roofline(add_work(wf, wb), fwd_ms + bwd_ms, pk,
+                                                             "render_fwd_kernel<64> + render_bwd_kernel<64>")}
     r.close()
     return res
 
@@ -648,6 +737,17 @@ def job_throughput(units_per_rank, world, ms):
 # Arms.
 # ----------------------------------------------------------------------------
 
+def workload_config(galaxies, world):
+    """The workload both arms report."""
+    return {"workload": f"{galaxies} galaxies x 64x64 patches per GPU per step: 50/50 exp (6 comp) / "
+                        f"deV (10 comp), r_e log-U(0.3, 20) px, |e| U(0, 0.6), flux log-U(1, 1e4), "
+                        f"offsets U[-0.5, 0.5), one 2-Gaussian PSF (sigma 1.5/3.0) + 3-Gaussian fit",
+            "galaxies_per_step": galaxies * world, "patch": N_PATCH, "parallelism": "replicas",
+            "l2": f"each step writes {galaxies * N_PATCH * N_PATCH * 4 / 1e9:.2f} GB of patches "
+                  f"(> 129 MB L2), which evicts the {galaxies * PARAM_BYTES / 1e6:.1f} MB of parameters; "
+                  f"no separate flush"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -732,35 +832,15 @@ def run_ours(args):
     pk = peaks(props.multi_processor_count)
     work = algorithmic_work(gals, tables, psf.mog.shape[0])
     k_ms = kms[1] / max(kn[1], 1)
-    t = {"hbm": work["hbm_bytes"] / pk["hbm"], "sfu": work["ex2"] / pk["sfu"], "fp32": work["flops"] / pk["fp32"]}
-    bound = max(t, key=t.get)
-    fracs = {k: v / (k_ms / 1e3) for k, v in t.items()}
-    if bound == "hbm":
-        roof = {"bound": "hbm", "achieved": work["hbm_bytes"] / (k_ms / 1e3) / 1e9, "peak": pk["hbm"] / 1e9,
-                "unit": "GB/s"}
-    elif bound == "sfu":
-        roof = {"bound": "alu", "pipe": "MUFU ex2", "achieved": work["ex2"] / (k_ms / 1e3) / 1e12,
-                "peak": pk["sfu"] / 1e12, "unit": "Tex2/s"}
-    else:
-        roof = {"bound": "alu", "pipe": "FP32", "achieved": work["flops"] / (k_ms / 1e3) / 1e12,
-                "peak": pk["fp32"] / 1e12, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = recorded_traffic(args.galaxies)
-    roof["kernel"] = "render_fwd_kernel<64>"
-    roof["kernel_ms"] = k_ms
-    roof["peak_source"] = (f"{pk['hbm_src']} HBM copy GB/s (MEASURED_PEAKS.json)" if bound == "hbm" else
-                           f"{props.multi_processor_count} SMs x {SFU_PER_CLK_SM if bound == 'sfu' else FP32_FLOP_PER_CLK_SM}"
-                           f"/clk x {pk['sm_mhz']:.0f} MHz")
-    roof["fractions"] = {k: round(v, 4) for k, v in fracs.items()}
-    roof["algorithmic_per_launch"] = {"hbm_bytes": work["hbm_bytes"], "ex2": work["ex2"], "flops": work["flops"]}
+    roof = roofline(work, k_ms, pk, "render_fwd_kernel<64>", traffic=recorded_traffic(args.galaxies))
 
     cpu = None
     if world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.galaxies, args.cpu_seconds)
     extra = None
     if world == 1 and not args.no_extra:
-        extra = {"mixed_sizes": extra_mixed(tables, local, args.extra_steps),
-                 "render_grad": extra_render_grad(tables, psf, local, args.extra_steps),
+        extra = {"mixed_sizes": extra_mixed(tables, local, args.extra_steps, pk),
+                 "render_grad": extra_render_grad(tables, psf, local, args.extra_steps, pk),
                  "lanczos_shift": extra_lanczos(tables, psf, local, args.extra_steps),
                  "eigen_psf": extra_eigen(tables, psf, local, args.extra_steps),
                  "composite": extra_composite(tables, psf, local, args.extra_steps),
@@ -773,13 +853,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.galaxies} galaxies x 64x64 patches per GPU per step: 50/50 exp (6 comp) / "
-                               f"deV (10 comp), r_e log-U(0.3, 20) px, |e| U(0, 0.6), flux log-U(1, 1e4), "
-                               f"offsets U[-0.5, 0.5), one 2-Gaussian PSF (sigma 1.5/3.0) + 3-Gaussian fit",
-                   "galaxies_per_step": args.galaxies * world, "patch": N_PATCH, "parallelism": "replicas",
-                   "l2": f"each step writes {args.galaxies * N_PATCH * N_PATCH * 4 / 1e9:.2f} GB of patches "
-                         f"(> 129 MB L2), which evicts the {args.galaxies * PARAM_BYTES / 1e6:.1f} MB of parameters; "
-                         f"no separate flush"},
+        "config": workload_config(args.galaxies, world),
         "real_space_component_fraction": work["real_fraction"],
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": args.steps * 4, "clocks": clocks,
@@ -789,22 +863,31 @@ def run_ours(args):
     r.close()
 
 
+REF_PER_WORKER = 400   # galaxies per worker per step of the reference arm (about 0.25 s of FP64 work)
+
+
+def _worker_range(args):
+    start, count = args
+    return _worker_render(range(start, start + count))
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     pool, cores = cpu_pool(args.galaxies)
-    per = 2
+    per = min(REF_PER_WORKER, max(1, args.galaxies // cores))
     try:
-        pool.map(_worker_render, [[i] for i in range(cores)])
+        pool.map(_worker_render, [range(i * 20, i * 20 + 20) for i in range(cores)])   # warm the workers
         nxt = 0
 
         def step():
+            # one contiguous range of `per` galaxies per worker: one message each way per worker and step
             nonlocal nxt
-            chunks = [list(range(nxt + c * per, nxt + (c + 1) * per)) for c in range(cores)]
-            nxt = (nxt + cores * per) % (args.galaxies - cores * per)
-            return sum(n for n, _ in pool.map(_worker_render, chunks))
+            chunks = [((nxt + c * per) % (args.galaxies - per), per) for c in range(cores)]
+            nxt = (nxt + cores * per) % args.galaxies
+            return sum(n for n, _ in pool.map(_worker_range, chunks))
 
         for _ in range(args.warmup):
             step()
@@ -815,13 +898,13 @@ def run_reference(args):
         pool.close()
         pool.join()
     value = done / wall
-    sample = (f"{cores * per} galaxies per step of the 100k fixed-size batch over {cores} spawn workers "
-              f"(FP64 numpy oracle)")
+    sample = (f"{cores * per} galaxies per step ({per} consecutive ones per worker) of the 100k fixed-size batch "
+              f"over {cores} spawn workers, FP64 numpy oracle")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": wall / max(args.steps, 1) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "the same 100k-galaxy 64x64 batch, bounded per-step samples", "patch": N_PATCH},
+        "config": workload_config(args.galaxies, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))

@@ -211,9 +211,10 @@ mog_status mog_render_batch_ex(mog_ctx* ctx, const mog_batch* batch, float* out,
  * lives in one fixed device array of about 4.3 MB defined in the library,
  * present on every GPU that loads it until the process exits.  At most
  * MOG_NOALLOC_MAX_GALAXIES galaxies per call; larger batches are rejected
- * with MOG_ERR_ARG (split them).  The first call on a device looks up the
- * array's device address for that device (once); make that first call before
- * any stream capture.  All calls share the one array: calls that overlap on
+ * with MOG_ERR_ARG (split them).  mog_create_context looks up the array's
+ * device address on its device (the first context on a device loads the
+ * array there), so the render calls themselves neither load nor allocate
+ * anything.  All calls share the one array: calls that overlap on
  * the GPU (different streams, or different contexts on the same device) race
  * and corrupt each other's output; serialise them.  The context, its tables
  * and PSFs must have been created beforehand (those calls allocate).

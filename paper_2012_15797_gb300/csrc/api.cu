@@ -3,7 +3,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ctx.h"
@@ -28,6 +31,23 @@ mog_status fail(mog_ctx* ctx, mog_status code, const char* fmt, ...) {
     ctx->last_error = buf;
   }
   return code;
+}
+
+int kernel_occupancy(const void* fn, int threads, size_t smem) {
+  static std::mutex lock;
+  static std::map<std::pair<int, const void*>, int> configured;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> guard(lock);
+  auto it = configured.find({device, fn});
+  if (it != configured.end()) return it->second;
+  int occ = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess)
+    return -1;
+  if (occ < 1) occ = 1;
+  configured[{device, fn}] = occ;
+  return occ;
 }
 
 mog_status cuda_fail(mog_ctx* ctx, cudaError_t e, const char* what) {
@@ -130,6 +150,10 @@ mog_status mog_create_context(mog_ctx** out, int device) {
   if (e == cudaSuccess) e = workspace_init(&ctx->ws);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dft_scratch, sizeof(double2) * 256 * 129);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
+  // the allocation-free render's scratch array: its address is looked up (and
+  // the array loaded on this device) here, not in a render call
+  unsigned char* noalloc_base = nullptr;
+  if (e == cudaSuccess) e = noalloc_scratch(device, &noalloc_base);
   if (e != cudaSuccess) {
     mog_destroy_context(ctx);
     return e == cudaErrorMemoryAllocation ? MOG_ERR_NOMEM : MOG_ERR_CUDA;

@@ -70,6 +70,13 @@ cudaError_t noalloc_scratch(int device, unsigned char** out);
 cudaError_t render_noalloc(const RenderParams& proto, int64_t count, uint32_t want, unsigned char* base,
                            int num_sms, int* status, cudaStream_t s);
 
+// Raises kernel `fn`'s dynamic shared-memory limit to `smem` bytes and
+// returns how many CTAs of `threads` threads fit on one SM, or -1 on
+// failure.  The limit belongs to the current device's context, so it is set
+// once per (device, kernel) pair: the first launch of a kernel on each
+// device configures it there.
+int kernel_occupancy(const void* fn, int threads, size_t smem);
+
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, cudaStream_t s);
 int render_fwd_max_ctas(int n);

@@ -10,7 +10,9 @@
 // latency-critical loops cannot afford cudaMalloc either, because it may
 // synchronise the device and its latency is unbounded.  Such callers create
 // the context, tables and PSFs once at start-up (those calls do allocate) and
-// then render with this entry point, which allocates nothing.
+// then render with this entry point, which allocates nothing.  Context
+// creation looks up the array's device address, which loads the array on that
+// device, so that no render call is the first use of it.
 #include <cstring>
 #include <mutex>
 
@@ -39,7 +41,7 @@ std::mutex g_lock;
 unsigned char* g_addr[MAX_DEVICES] = {};
 
 // Device address of the scratch on `device` (which must be current),
-// looked up once per device.
+// looked up once per device (by mog_create_context).
 cudaError_t scratch_address(int device, unsigned char** out) {
   std::lock_guard<std::mutex> guard(g_lock);
   if (!g_addr[device]) {

@@ -424,16 +424,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
 template <int N, bool WN = false, bool EIG = false>
 static int bwd_occupancy() {
   using C = BwdCfg<N>;
-  static int occ = -1;
-  if (occ < 0) {
-    if (cudaFuncSetAttribute(render_bwd_kernel<N, WN, EIG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)C::SMEM) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_bwd_kernel<N, WN, EIG>, C::THREADS, C::SMEM) !=
-            cudaSuccess)
-      return -1;
-    if (occ < 1) occ = 1;
-  }
-  return occ;
+  return kernel_occupancy(reinterpret_cast<const void*>(render_bwd_kernel<N, WN, EIG>), C::THREADS, C::SMEM);
 }
 
 template <int N, bool WN, bool EIG>

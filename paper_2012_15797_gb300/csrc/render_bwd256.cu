@@ -337,17 +337,9 @@ size_t render_bwd256_scratch_bytes(int num_sms) { return sizeof(float2) * (size_
 
 cudaError_t launch_render_bwd256(const RenderParams& p, const float* grad_out, float* grad_params, float2* scratch,
                                  int num_sms, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaSuccess;
-    for (auto fn : {render_bwd256_kernel<false, false>, render_bwd256_kernel<true, false>,
-                    render_bwd256_kernel<false, true>, render_bwd256_kernel<true, true>})
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
   auto fn = p.eigen ? (p.grad_n ? render_bwd256_kernel<true, true> : render_bwd256_kernel<false, true>)
                     : (p.grad_n ? render_bwd256_kernel<true, false> : render_bwd256_kernel<false, false>);
+  if (kernel_occupancy(reinterpret_cast<const void*>(fn), THREADS, SMEM) < 0) return cudaErrorInvalidConfiguration;
   fn<<<num_sms, THREADS, SMEM, s>>>(p, grad_out, grad_params, scratch);
   return cudaGetLastError();
 }

@@ -507,17 +507,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
 template <int N, bool LZ = false, bool EIG = false>
 static int fwd_occupancy() {
   using C = FwdCfg<N>;
-  static int occ = -1;
-  if (occ < 0) {
-    if (cudaFuncSetAttribute(render_fwd_kernel<N, LZ, EIG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)C::SMEM) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fwd_kernel<N, LZ, EIG>, C::THREADS, C::SMEM) !=
-            cudaSuccess)
-      return -1;
-    if (occ < 1) occ = 1;
-  }
-  return occ;
+  return kernel_occupancy(reinterpret_cast<const void*>(render_fwd_kernel<N, LZ, EIG>), C::THREADS, C::SMEM);
 }
 
 template <int N, bool LZ, bool EIG>

@@ -423,13 +423,8 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
 
 template <bool LZ, bool EIG>
 static cudaError_t launch_fwd256(const RenderParams& p, int num_sms, cudaStream_t s) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(render_fwd256_kernel<LZ, EIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  if (kernel_occupancy(reinterpret_cast<const void*>(render_fwd256_kernel<LZ, EIG>), THREADS, SMEM) < 0)
+    return cudaErrorInvalidConfiguration;
   render_fwd256_kernel<LZ, EIG><<<num_sms, THREADS, SMEM, s>>>(p);
   return cudaGetLastError();
 }
