@@ -37,8 +37,8 @@ N_PATCH = 64
 METRIC = "galaxy patches rendered/s at 64x64 (100k-galaxy fixed-size batch)"
 UNIT = "patches/s"
 PARAM_BYTES = 7 * 4 + 3 * 4 + 8      # float params, int ids, int64 offset
-SFU_PER_CLK_SM = 32                  # MUFU ex2 per SM per clock (31.7 measured on GB300 with an ex2 probe)
-FP32_FLOP_PER_CLK_SM = 256           # 128 FMA lanes x 2
+SFU_PER_CLK_SM = 32                  # MUFU ex2 per SM per clock (measured live: "pipe_rates" in the line)
+FP32_FLOP_PER_CLK_SM = 256           # 128 FMA lanes x 2 (measured live: "pipe_rates")
 KERNEL_SOURCES = ("paper_2012_15797_gb300/csrc/render_fwd.cu", "paper_2012_15797_gb300/csrc/common.cuh")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "render_fwd_64_config1.md")
 
@@ -58,7 +58,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the mixed-size / gradient / per-galaxy lines")
     ap.add_argument("--extra-steps", type=int, default=20)
-    ap.add_argument("--only", choices=("fwd", "grad", "mixed", "serving", "lanczos", "eigen"),
+    ap.add_argument("--only", choices=("fwd", "grad", "mixed", "serving", "lanczos", "eigen", "pipes"),
                     help="profiling mode: run just this workload (--galaxies of it) for --warmup + --steps "
                          "and print its time")
     return ap.parse_args()
@@ -206,6 +206,24 @@ def recorded_traffic(galaxies):
     if not sha or not per or sha.group(1) != kernel_source_sha():
         return None
     return float(per.group(1)) * galaxies
+
+
+def measure_pipes(r, gpu_index, reps=300):
+    """Rates of the MUFU ex2 and FP32 FMA pipes on this GPU (library probe
+    kernels), per SM and clock at the SM clock sampled meanwhile."""
+    from paper_2012_15797_gb300 import capi
+    capi.mog_measure_pipe_rates(r.ctx, 3)
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    ex2, fma = capi.mog_measure_pipe_rates(r.ctx, reps)
+    clocks = sampler.stop()
+    import torch
+    sms = torch.cuda.get_device_properties(gpu_index).multi_processor_count
+    mhz = clocks["sm_mhz"] or 2070.0
+    return {"ex2_per_s": ex2, "fma_per_s": fma, "sm_mhz": mhz, "clock_samples": clocks["samples"],
+            "ex2_per_clk_sm": ex2 / (sms * mhz * 1e6), "fma_lanes_per_clk_sm": fma / (sms * mhz * 1e6),
+            "method": f"{reps} launches each of 8 independent ex2.approx / FFMA chains of 4096 per thread, "
+                      f"8 x 256-thread CTAs per SM, CUDA events; per clock at the median sampled SM clock"}
 
 
 # ----------------------------------------------------------------------------
@@ -413,14 +431,26 @@ def extra_mixed(tables, device, steps, pk):
     kpsf = psfs[0].mog.shape[0]
     res["roofline"] = roofline(algorithmic_work(gals, tables, kpsf), graph_ms, pk,
                                "graph: render_fwd_kernel<32|64|128> + render_fwd256_kernel")
+    # each size's kernel alone (batch size mask = that side), CUDA events
+    # around its launches: its own time and roofline
     per = {}
     for i in range(4):
         sel = np.flatnonzero(gals.size == (32 << i))
-        if len(sel) and kn[i]:
-            rf = roofline(algorithmic_work(gals.subset(sel), tables, kpsf), kms[i] / kn[i], pk, f"size {32 << i}")
-            per[32 << i] = {"bound": rf.get("pipe", rf["bound"]), "frac": round(rf["frac"], 4),
-                            "fractions": rf["fractions"]}
-    res["roofline_per_size"] = per
+        if not len(sel):
+            continue
+        bi = capi.make_batch(b.count, b.ptrs(), 1 << i)
+        capi.mog_render_batch(r.ctx, bi, out.data_ptr(), st.cuda_stream)
+        capi.mog_set_timing(r.ctx, True)
+        capi.mog_read_timing(r.ctx)
+        _event_ms(lambda: capi.mog_render_batch(r.ctx, bi, out.data_ptr(), st.cuda_stream), steps, st)
+        kms1, kn1 = capi.mog_read_timing(r.ctx)
+        capi.mog_set_timing(r.ctx, False)
+        k_ms = kms1[i] / max(kn1[i], 1)
+        rf = roofline(algorithmic_work(gals.subset(sel), tables, kpsf), k_ms, pk, f"size {32 << i}")
+        per[32 << i] = {"galaxies": int(len(sel)), "kernel_ms_alone": k_ms, "bound": rf.get("pipe", rf["bound"]),
+                        "frac": round(rf["frac"], 4), "fractions": rf["fractions"]}
+    r.sync_status()
+    res["roofline_per_size_alone"] = per
     r.close()
     return res
 
@@ -617,6 +647,28 @@ def extra_psf_fit(tables, device):
     r.close()
     return {"workload": "64 PSFs of 64x64 (2-Gaussian core + Moffat wings), k = 3", "ms_per_call": ms,
             "value": 64 / (ms / 1e3), "unit": "PSF fits/s"}
+
+
+def extra_psf_create(tables, device, n=64):
+    """mog_create_psf for the 64 Moffat-winged 64x64 PSFs of the mixed
+    workload: each call embeds the PSF and takes its FP32 real 2-D FFT for
+    every patch side (32, 64, 128, 256) on the device; host clock around the
+    synchronous calls."""
+    from paper_2012_15797_gb300 import capi
+    from paper_2012_15797_gb300.renderer import Renderer
+    from workloads import config2_psfs
+    psfs = config2_psfs(n)
+    r = Renderer(tables, [], device=device)
+    for p in psfs[:4]:   # warm: loads the kernels
+        capi.mog_destroy_psf(r.ctx, capi.mog_create_psf(r.ctx, p.image, p.mog))
+    t0 = time.perf_counter()
+    ids = [capi.mog_create_psf(r.ctx, p.image, p.mog) for p in psfs]
+    ms = (time.perf_counter() - t0) * 1e3
+    for i in ids:
+        capi.mog_destroy_psf(r.ctx, i)
+    r.close()
+    return {"workload": f"{n} PSFs of 64x64, spectra for sides 32-256 (FP32 shared-memory FFTs)",
+            "ms_per_psf": ms / n, "value": n / (ms / 1e3), "unit": "PSFs created/s"}
 
 
 def extra_per_galaxy(tables, psf, device, n=2000):
@@ -827,6 +879,8 @@ def run_ours(args):
         r.close()
         return
 
+    pipes = measure_pipes(r, local)
+
     # roofline of the dominant kernel (64 x 64 render), from live CUDA events
     props = torch.cuda.get_device_properties(local)
     pk = peaks(props.multi_processor_count)
@@ -846,6 +900,7 @@ def run_ours(args):
                  "composite": extra_composite(tables, psf, local, args.extra_steps),
                  "sersic_gradient": extra_sersic_grad(tables, local, args.extra_steps),
                  "psf_fit": extra_psf_fit(tables, local),
+                 "psf_create": extra_psf_create(tables, local),
                  "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local),
                  "serving": extra_serving(tables, local)}
 
@@ -856,7 +911,7 @@ def run_ours(args):
         "config": workload_config(args.galaxies, world),
         "real_space_component_fraction": work["real_fraction"],
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": args.steps * 4, "clocks": clocks,
+        "gpu_launches": args.steps * 4, "clocks": clocks, "pipe_rates": pipes,
         "extra": extra,
     }
     print(json.dumps(line))
@@ -913,6 +968,15 @@ def run_reference(args):
 def run_only(args):
     """Small single-workload runs for profilers (no JSON bench line)."""
     import torch
+    if args.only == "pipes":
+        from paper_2012_15797_gb300.build import build
+        build()
+        from paper_2012_15797_gb300.renderer import Renderer
+        from workloads import load_profile_tables
+        r = Renderer(load_profile_tables(), [])
+        print(json.dumps(measure_pipes(r, 0)))
+        r.close()
+        return
     if args.only == "serving":
         from paper_2012_15797_gb300.build import build
         build()

@@ -374,6 +374,13 @@ typedef struct mog_request {
 } mog_request;
 mog_status mog_server_create(mog_ctx* ctx, const mog_server_config* cfg, mog_server** server);
 mog_status mog_server_add_fit(mog_server* server, const mog_fit_state* fit, int* fit_id);
+/* Rejects (MOG_ERR_ARG, nothing queued) a request outside its fit, larger
+ * than the budget, or with a non-finite parameter, |e| >= 1 or log_re >= 30.
+ * mog_server_add_fit likewise rejects a fit with a patch side outside
+ * {32, 64, 128, 256}, a profile without a table, a PSF id that is not
+ * registered or is an eigen-PSF (fits carry no image positions), a
+ * non-finite Sersic index or inverse variance, or a misaligned data offset,
+ * so that every admitted request is answered in full. */
 mog_status mog_server_submit(mog_server* server, const mog_request* req, uint64_t* ticket);
 /* Blocks until the request is done (or timeout_s passes: MOG_ERR_TIMEOUT). */
 mog_status mog_server_wait(mog_server* server, uint64_t ticket, double timeout_s, double* latency_s);
@@ -389,6 +396,23 @@ mog_status mog_server_stats(mog_server* server, int64_t* out);
 mog_status mog_server_destroy(mog_server* server);
 
 /*
+ * Host-side fault injection for tests of the server's failure handling (the
+ * paper has no counterpart).  Arms one fault, counted from this call:
+ *   MOG_FAULT_DROP    the completion of the nth request admitted is lost, as
+ *                     if its message were dropped: its mog_server_wait ends
+ *                     with MOG_ERR_TIMEOUT, the other requests complete;
+ *   MOG_FAULT_LAUNCH  the nth micro-batch fails as a failing CUDA call would,
+ *                     before any of its work is enqueued: its requests end
+ *                     with MOG_ERR_CUDA;
+ *   MOG_FAULT_NOMEM   the nth micro-batch's staging allocation fails: its
+ *                     requests end with MOG_ERR_NOMEM.
+ * The server keeps serving later requests.  nth = 0 disarms.  Nothing is
+ * injected on the device.
+ */
+enum { MOG_FAULT_DROP = 1, MOG_FAULT_LAUNCH = 2, MOG_FAULT_NOMEM = 3 };
+mog_status mog_server_inject_fault(mog_server* server, int kind, int64_t nth);
+
+/*
  * Kernel timing for measurement: while enabled, every render-kernel launch is
  * bracketed by CUDA events recorded on its own stream.  mog_read_timing
  * waits for the recorded events and returns, per patch side N = 32 << b
@@ -398,6 +422,29 @@ mog_status mog_server_destroy(mog_server* server);
  */
 mog_status mog_set_timing(mog_ctx* ctx, int enable);
 mog_status mog_read_timing(mog_ctx* ctx, double* ms, int64_t* launches);
+
+/*
+ * Measurement of the two ALU pipes the render kernels are bound by (the
+ * paper has no counterpart; it gives the roofline denominators of the
+ * Fourier evaluation's 2^x and FP32 arithmetic): runs `reps` launches
+ * (1..100000) of independent 2^x chains (ex2.approx) and of FP32 FMA chains
+ * on the context's device, 8 CTAs of 256 threads per SM, 8 chains of 4096
+ * operations per thread, on the legacy default stream, and returns the
+ * rates in operations per second (*ex2_per_s, *fma_per_s; one FMA = one
+ * operation).  Allocates and frees a small output buffer; synchronous.
+ */
+mog_status mog_measure_pipe_rates(mog_ctx* ctx, int reps, double* ex2_per_s, double* fma_per_s);
+
+/*
+ * Failure-detection check of the bounded device waits (the paper has no
+ * counterpart): launches one CTA on `stream` that waits, with the same
+ * bounded wait the render kernels put on their bulk copies, for an mbarrier
+ * phase that nothing completes, gives up after limit_s seconds
+ * (0 < limit_s <= 2) and records MOG_ERR_TIMEOUT in the context's status
+ * word, as a render kernel whose copy never lands does.  mog_sync_status then
+ * reports it and clears it; the context stays usable.  Nothing faults.
+ */
+mog_status mog_check_wait_timeout(mog_ctx* ctx, double limit_s, void* stream);
 
 /*
  * Reads the device status word after synchronising `stream` and resets it.

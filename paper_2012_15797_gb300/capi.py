@@ -36,7 +36,7 @@ EXPORTED = (
     "mog_server_create", "mog_server_add_fit", "mog_server_submit", "mog_server_wait", "mog_server_replay",
     "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
     "mog_create_eigen_psf", "mog_render_batch_ex", "mog_render_backward_ex", "mog_fit_psf_mixture",
-    "mog_render_batch_host",
+    "mog_render_batch_host", "mog_measure_pipe_rates", "mog_server_inject_fault", "mog_check_wait_timeout",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -111,6 +111,9 @@ def _load():
         "mog_sync_status": ([VP, VP], I),
         "mog_set_timing": ([VP, I], I),
         "mog_read_timing": ([VP, P(ctypes.c_double), P(ctypes.c_int64)], I),
+        "mog_measure_pipe_rates": ([VP, I, P(ctypes.c_double), P(ctypes.c_double)], I),
+        "mog_server_inject_fault": ([VP, I, ctypes.c_int64], I),
+        "mog_check_wait_timeout": ([VP, ctypes.c_double, VP], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -239,6 +242,7 @@ def mog_render_backward(ctx, batch, grad_out_ptr, grad_params_ptr, stream=0):
 
 
 MOG_GRAD_SERSIC = 1
+MOG_FAULT_DROP, MOG_FAULT_LAUNCH, MOG_FAULT_NOMEM = 1, 2, 3
 
 
 def mog_render_backward_ex(ctx, batch, grad_out_ptr, grad_params_ptr, stream=0, flags=0):
@@ -293,6 +297,17 @@ def mog_read_timing(ctx):
     n = (ctypes.c_int64 * 4)()
     _check(ctx, _lib.mog_read_timing(ctx, ms, n))
     return list(ms), list(n)
+
+
+def mog_measure_pipe_rates(ctx, reps=100):
+    """(ex2 per second, FP32 FMA per second) measured on the context's device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, _lib.mog_measure_pipe_rates(ctx, int(reps), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def mog_check_wait_timeout(ctx, limit_s, stream=0):
+    _check(ctx, _lib.mog_check_wait_timeout(ctx, float(limit_s), ctypes.c_void_p(int(stream))))
 
 
 def mog_sync_status(ctx, stream=0):

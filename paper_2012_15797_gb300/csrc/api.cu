@@ -148,7 +148,7 @@ mog_status mog_create_context(mog_ctx** out, int device) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = workspace_init(&ctx->ws);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dft_scratch, sizeof(double2) * 256 * 129);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_dft_scratch, sizeof(float2) * PSF_SCRATCH_ELEMS);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
   // the allocation-free render's scratch array: its address is looked up (and
   // the array loaded on this device) here, not in a render call
@@ -217,6 +217,7 @@ mog_status mog_set_profile_table(mog_ctx* ctx, int profile_id, int n_nodes, cons
     }
   MOG_CUDA(ctx, cudaSetDevice(ctx->device));
   MOG_CUDA(ctx, cudaMemcpy(ctx->d_profiles + profile_id, &h, sizeof(h), cudaMemcpyHostToDevice));
+  ctx->profile_set[profile_id] = true;
   return MOG_OK;
 }
 

@@ -78,6 +78,16 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// The same as one packed f32x2 instruction each (half the issue slots of two
+// FP32 adds at the same pipe rate); used by the FFT butterflies.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&d);
+}
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 // a * (s i) for s = +1 (inverse transform) or -1 (forward)
@@ -96,19 +106,21 @@ __device__ __forceinline__ float ex2(float x) {
 // ------------------------------------------------------------------------
 // Small in-register DFTs, sign S: +1 inverse (e^{+2 pi i/r}), -1 forward.
 // ------------------------------------------------------------------------
+// Sums and differences of complex values are packed f32x2 instructions; the
+// terms multiplied by +-i (a swap of real and imaginary parts) stay scalar.
 template <int S>
 __device__ __forceinline__ void dft2(float2& a, float2& b) {
   float2 t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
+  a = padd(t, b);
+  b = psub(t, b);
 }
 
 template <int S>
 __device__ __forceinline__ void dft4(float2* v) {
-  float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-  float2 c = cadd(v[1], v[3]), d = mul_si<S>(csub(v[1], v[3]));
-  v[0] = cadd(a, c);
-  v[2] = csub(a, c);
+  float2 a = padd(v[0], v[2]), b = psub(v[0], v[2]);
+  float2 c = padd(v[1], v[3]), d = mul_si<S>(psub(v[1], v[3]));
+  v[0] = padd(a, c);
+  v[2] = psub(a, c);
   v[1] = cadd(b, d);
   v[3] = csub(b, d);
 }
@@ -124,14 +136,14 @@ __device__ __forceinline__ void dft8(float2* v) {
   float2 o1 = make_float2(R * (o[1].x - S * o[1].y), R * (o[1].y + S * o[1].x));
   float2 o2 = mul_si<S>(o[2]);
   float2 o3 = make_float2(R * (-o[3].x - S * o[3].y), R * (-o[3].y + S * o[3].x));
-  v[0] = cadd(e[0], o[0]);
-  v[4] = csub(e[0], o[0]);
-  v[1] = cadd(e[1], o1);
-  v[5] = csub(e[1], o1);
+  v[0] = padd(e[0], o[0]);
+  v[4] = psub(e[0], o[0]);
+  v[1] = padd(e[1], o1);
+  v[5] = psub(e[1], o1);
   v[2] = cadd(e[2], o2);
   v[6] = csub(e[2], o2);
-  v[3] = cadd(e[3], o3);
-  v[7] = csub(e[3], o3);
+  v[3] = padd(e[3], o3);
+  v[7] = psub(e[3], o3);
 }
 
 template <int R, int S>
@@ -267,6 +279,28 @@ __device__ __forceinline__ void first_pass_load(const float2* buf, int j, float2
   for (int m = 0; m < 8; ++m) v[m] = swz_xor<N>() ? buf[swz<N>(j + m * TPF)] : src[m * TPF + ((m * TPF) >> 3)];
 }
 
+// Passes after the first of a length-N FFT held in work row `w` (sign S);
+// the result of the last pass is left in v, value q R + m at output index
+// stockham_out_index<N, R>(j, N / R, q, m) with R = LastPass<N>::R.
+template <int N, int S>
+__device__ __forceinline__ void fft_rest(float2* w, int j, const float2* tw1, const float2* tw2, float2* v) {
+  constexpr int R1 = Radix<N>::r[1];
+  stockham_load<N, R1, S>(w, j, tw1, v);
+  if constexpr (Radix<N>::P == 3) {
+    constexpr int R2 = Radix<N>::r[2];
+    __syncwarp();
+    stockham_store<N, R1>(w, j, 8, v);
+    __syncwarp();
+    stockham_load<N, R2, S>(w, j, tw2, v);
+  }
+}
+
+template <int N>
+struct LastPass {
+  static constexpr int R = Radix<N>::r[Radix<N>::P - 1];
+  static constexpr int NS = N / R;
+};
+
 // ------------------------------------------------------------------------
 // Bulk (TMA) copy global -> shared with an mbarrier, bounded wait.
 // ------------------------------------------------------------------------
@@ -316,9 +350,10 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// Waits for phase `parity` of the barrier; gives up after ~0.5 s and
-// returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits for phase `parity` of the barrier; gives up after `limit_ns`
+// nanoseconds (0.5 s by default) and returns false.
+constexpr uint64_t WAIT_LIMIT_NS = 500000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = WAIT_LIMIT_NS) {
   const uint32_t a = smem_u32(bar);
   uint64_t t0 = 0;
   for (uint32_t it = 0;; ++it) {
@@ -332,7 +367,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if ((it & 255) == 0) {
       const uint64_t t = globaltimer_ns();
       if (it == 0) t0 = t;
-      else if (t - t0 > 500000000ull) return false;
+      else if (t - t0 > limit_ns) return false;
     }
   }
 }

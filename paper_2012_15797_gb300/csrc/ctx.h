@@ -51,12 +51,13 @@ struct mog_ctx {
   int device = 0;
   int num_sms = 0;
   mog::DevProfile* d_profiles = nullptr;
+  bool profile_set[MOG_MAX_PROFILES] = {};   // which profile ids have a table
   mog::DevPsf* d_psfs = nullptr;
   std::vector<mog::DevPsf> h_psfs;
   std::vector<float2*> psf_mem;  // one allocation per PSF holding every bucket's spectrum
   int eigen_psfs = 0;            // registered eigen-PSFs (the kernels that handle them are launched only then)
   int* d_status = nullptr;
-  double2* d_dft_scratch = nullptr;
+  float2* d_dft_scratch = nullptr;   // PSF spectra: row transforms
   mog::Workspace ws;             // the workspace of the plain entry points
   mog::HostLane host_lanes[2];   // mog_render_batch_host
   std::string last_error;

@@ -59,7 +59,8 @@ cudaError_t launch_adjoint_prep(const RenderParams& p, int64_t count, unsigned c
 cudaError_t launch_render_bwd(int n, const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
                               int ctas_per_sm, cudaStream_t s);
 int render_bwd_max_ctas(int n);
-// 256 x 256 adjoint: needs render_bwd256_scratch_bytes(num_sms) of global scratch.
+// 256 x 256 adjoint (and forward render adding to its patches): need
+// render_bwd256_scratch_bytes(num_sms) of global scratch, one slice per CTA.
 size_t render_bwd256_scratch_bytes(int num_sms);
 cudaError_t launch_render_bwd256(const RenderParams& p, const float* grad_out, float* grad_params, float2* scratch,
                                  int num_sms, cudaStream_t s);
@@ -87,13 +88,15 @@ constexpr uint32_t LZ_BUCKETS = 0xF;    // Lanczos variant: 32, 64, 128, 256
 constexpr uint32_t BWD_BUCKETS = 0xF;   // 32, 64, 128, 256
 size_t render_fwd_smem(int n);
 
-// Spectrum of a PSF embedded with its centre at (n/2, n/2), written in the
-// psf_lstride layout.  `pix` is device memory (h x w float).
 // Gaussian-mixture fits of `count` h x w PSF images (psf_fit.cu).
 cudaError_t launch_psf_fit(const float* images, int count, int h, int w, int k, int iters, float* rows,
                            float* chi2, cudaStream_t s);
 
-cudaError_t launch_psf_spectrum(const float* pix, int h, int w, int n, double2* scratch, float2* spec,
+// Spectrum of a PSF embedded with its centre at (n/2, n/2), written in the
+// psf_lstride layout.  `pix` is device memory (h x w float); `scratch` holds
+// PSF_SCRATCH_ELEMS float2 (the row transforms of the largest side).
+constexpr size_t PSF_SCRATCH_ELEMS = (size_t)256 * (256 / 2 + 1);
+cudaError_t launch_psf_spectrum(const float* pix, int h, int w, int n, float2* scratch, float2* spec,
                                 cudaStream_t s);
 
 }  // namespace mog

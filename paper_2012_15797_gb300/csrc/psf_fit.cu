@@ -4,11 +4,13 @@
 // mixtures).  One CTA per image runs Levenberg-Marquardt on
 //   chi^2 = sum_p (sum_j w_j N(p - c - m_j; V_j) - image[p])^2,
 // w_j = exp(lw_j), V_j = L L^T with L = [[exp(la), 0], [b, exp(lc)]], from a
-// start set by the image's second moment.  J^T J and J^T r are summed in
-// FP32 over chunks of 256 pixels (their Jacobian rows staged in shared
-// memory, one matrix entry per thread) and in FP64 across chunks; the damped
-// normal equations are solved in FP64 by Cholesky.  Every loop is bounded by
-// the iteration count.
+// start set by the image's second moment.  Everything is FP32: J^T J and
+// J^T r are summed over chunks of 256 pixels (their Jacobian rows staged in
+// shared memory, one matrix entry per thread) and across chunks with
+// compensated (Kahan) addition; the damped normal equations are solved by
+// Cholesky after scaling by the diagonal, D^-1 (J^T J) D^-1 with unit
+// diagonal (Marquardt's scaling), which keeps the factorisation well
+// conditioned.  Every loop is bounded by the iteration count.
 #include "common.cuh"
 #include "internal.h"
 
@@ -24,22 +26,22 @@ constexpr int NENT = PMAX * (PMAX + 1) / 2 + PMAX + 1;   // J^T J (upper), J^T r
 constexpr float TWO_PI_F = 6.283185307179586f;
 
 struct FitShared {
-  double theta[PMAX], trial[PMAX];
-  double sums[NENT];
-  double red[FIT_THREADS / 32];
-  double lambda, chi, chi_trial;
-  double M[PMAX * PMAX], L[PMAX * PMAX];   // damped normal matrix and its Cholesky factor
+  float theta[PMAX], trial[PMAX];
+  float sums[NENT];
+  float red[FIT_THREADS / 32];
+  float lambda, chi;
+  float M[PMAX * PMAX], L[PMAX * PMAX], D[PMAX];   // scaled damped normal matrix, its Cholesky factor, scales
   float J[CHUNK * JST];
   int done;
 };
 
 // Mixture value, and (with jac) the derivatives of one component's terms
 // w.r.t. its six parameters, at offset (dx, dy) from the PSF centre.
-__device__ __forceinline__ float eval_pixel(const double* th, int k, float dx, float dy, float* jac) {
+__device__ __forceinline__ float eval_pixel(const float* th, int k, float dx, float dy, float* jac) {
   float model = 0.0f;
   for (int c = 0; c < k; ++c) {
-    const float wgt = expf((float)th[6 * c]), mx = (float)th[6 * c + 1], my = (float)th[6 * c + 2];
-    const float a = expf((float)th[6 * c + 3]), b = (float)th[6 * c + 4], cc = expf((float)th[6 * c + 5]);
+    const float wgt = expf(th[6 * c]), mx = th[6 * c + 1], my = th[6 * c + 2];
+    const float a = expf(th[6 * c + 3]), b = th[6 * c + 4], cc = expf(th[6 * c + 5]);
     const float vxx = a * a, vxy = a * b, vyy = b * b + cc * cc;
     const float det = vxx * vyy - vxy * vxy;   // = (a cc)^2 > 0
     const float idet = 1.0f / det;
@@ -62,15 +64,23 @@ __device__ __forceinline__ float eval_pixel(const double* th, int k, float dx, f
   return model;
 }
 
-__device__ double block_sum(double v, double* red) {
+__device__ float block_sum(float v, float* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  double t = 0.0;
+  float t = 0.0f;
   for (int i = 0; i < FIT_THREADS / 32; ++i) t += red[i];
   return t;
+}
+
+// acc += x with the rounding error carried in comp (Kahan).
+__device__ __forceinline__ void kahan_add(float& acc, float& comp, float x) {
+  const float y = x - comp;
+  const float t = acc + y;
+  comp = (t - acc) - y;
+  acc = t;
 }
 
 // Entry e of the summed quantities: (i, j) of the upper triangle of J^T J,
@@ -104,36 +114,36 @@ __global__ void __launch_bounds__(FIT_THREADS) psf_fit_kernel(const float* image
   const int nent = P * (P + 1) / 2 + P + 1;
 
   // start: weights and widths from the image sum and second moment
-  double tot = 0.0, mom = 0.0;
+  float tot = 0.0f, mom = 0.0f;
   for (int p = tid; p < npix; p += FIT_THREADS) {
-    const double dx = (double)(p % w - cx), dy = (double)(p / w - cy), v = img[p];
+    const float dx = (float)(p % w - cx), dy = (float)(p / w - cy), v = img[p];
     tot += v;
-    mom += v * (dx * dx + dy * dy);
+    mom = fmaf(v, dx * dx + dy * dy, mom);
   }
   tot = block_sum(tot, S.red);
   mom = block_sum(mom, S.red);
   if (tid == 0) {
-    const double scales[4] = {0.6, 1.1, 2.2, 4.0}, w0[4] = {0.55, 0.35, 0.08, 0.015};
-    double wsum = 0.0;
+    const float scales[4] = {0.6f, 1.1f, 2.2f, 4.0f}, w0[4] = {0.55f, 0.35f, 0.08f, 0.015f};
+    float wsum = 0.0f;
     for (int c = 0; c < k; ++c) wsum += w0[c];
-    const double s = sqrt(fmax(mom / (2.0 * tot), 0.25));
+    const float s = sqrtf(fmaxf(mom / (2.0f * tot), 0.25f));
     for (int c = 0; c < k; ++c) {
-      S.theta[6 * c + 0] = log(w0[c] / wsum * tot);
-      S.theta[6 * c + 1] = 0.0;
-      S.theta[6 * c + 2] = 0.0;
-      S.theta[6 * c + 3] = log(s * scales[c]);
-      S.theta[6 * c + 4] = 0.0;
-      S.theta[6 * c + 5] = log(s * scales[c]);
+      S.theta[6 * c + 0] = logf(w0[c] / wsum * tot);
+      S.theta[6 * c + 1] = 0.0f;
+      S.theta[6 * c + 2] = 0.0f;
+      S.theta[6 * c + 3] = logf(s * scales[c]);
+      S.theta[6 * c + 4] = 0.0f;
+      S.theta[6 * c + 5] = logf(s * scales[c]);
     }
-    S.lambda = 1e-3;
-    S.done = (tot > 0.0 && isfinite(tot)) ? 0 : 1;
+    S.lambda = 1e-3f;
+    S.done = (tot > 0.0f && isfinite(tot)) ? 0 : 1;
   }
   __syncthreads();
 
   for (int it = 0; it < iters && !S.done; ++it) {
     // ---- J^T J, J^T r and chi^2 at theta ----
     int e_i[2], e_j[2];
-    double acc[2] = {0.0, 0.0};
+    float acc[2] = {0.0f, 0.0f}, comp[2] = {0.0f, 0.0f};
     for (int q = 0; q < 2; ++q) {
       const int e = tid + q * FIT_THREADS;
       e_i[q] = e_j[q] = -1;
@@ -154,7 +164,7 @@ __global__ void __launch_bounds__(FIT_THREADS) psf_fit_kernel(const float* image
         if (e_i[q] < 0) continue;
         float part = 0.0f;
         for (int r = 0; r < CHUNK; ++r) part = fmaf(S.J[r * JST + e_i[q]], S.J[r * JST + e_j[q]], part);
-        acc[q] += (double)part;
+        kahan_add(acc[q], comp[q], part);
       }
       __syncthreads();
     }
@@ -162,45 +172,49 @@ __global__ void __launch_bounds__(FIT_THREADS) psf_fit_kernel(const float* image
       if (e_i[q] >= 0) S.sums[tid + q * FIT_THREADS] = acc[q];
     __syncthreads();
 
-    // ---- damped normal equations (thread 0, FP64 Cholesky) ----
+    // ---- damped normal equations (thread 0): with D = sqrt(diag J^T J),
+    // solve (D^-1 J^T J D^-1 + lambda I) z = -D^-1 J^T r by Cholesky and
+    // step by D^-1 z ----
     if (tid == 0) {
       const int ntri = P * (P + 1) / 2;
       S.chi = S.sums[ntri + P];
-      double* M = S.M;
-      double* L = S.L;
-      double y[PMAX];
+      float* M = S.M;
+      float* L = S.L;
+      float* D = S.D;
+      float y[PMAX];
+      for (int i = 0, e = 0; i < P; e += P - i, ++i) D[i] = sqrtf(fmaxf(S.sums[e], 1e-30f));
       int e = 0;
       for (int i = 0; i < P; ++i)
-        for (int j = i; j < P; ++j, ++e) M[i * PMAX + j] = M[j * PMAX + i] = S.sums[e];
-      for (int i = 0; i < P; ++i) M[i * PMAX + i] *= 1.0 + S.lambda;
+        for (int j = i; j < P; ++j, ++e) M[i * PMAX + j] = M[j * PMAX + i] = S.sums[e] / (D[i] * D[j]);
+      for (int i = 0; i < P; ++i) M[i * PMAX + i] = 1.0f + S.lambda;
       bool ok = true;
       for (int i = 0; i < P && ok; ++i) {
         for (int j = 0; j <= i; ++j) {
-          double v = M[i * PMAX + j];
+          float v = M[i * PMAX + j];
           for (int m = 0; m < j; ++m) v -= L[i * PMAX + m] * L[j * PMAX + m];
           if (i == j) {
-            if (!(v > 0.0)) {
+            if (!(v > 0.0f)) {
               ok = false;
               break;
             }
-            L[i * PMAX + i] = sqrt(v);
+            L[i * PMAX + i] = sqrtf(v);
           } else {
             L[i * PMAX + j] = v / L[j * PMAX + j];
           }
         }
       }
       if (ok) {
-        for (int i = 0; i < P; ++i) {   // L y = -J^T r
-          double v = -S.sums[ntri + i];
+        for (int i = 0; i < P; ++i) {   // L y = -D^-1 J^T r
+          float v = -S.sums[ntri + i] / D[i];
           for (int m = 0; m < i; ++m) v -= L[i * PMAX + m] * y[m];
           y[i] = v / L[i * PMAX + i];
         }
-        for (int i = P - 1; i >= 0; --i) {   // L^T d = y
-          double v = y[i];
+        for (int i = P - 1; i >= 0; --i) {   // L^T z = y
+          float v = y[i];
           for (int m = i + 1; m < P; ++m) v -= L[m * PMAX + i] * y[m];
           y[i] = v / L[i * PMAX + i];
         }
-        for (int i = 0; i < P; ++i) S.trial[i] = S.theta[i] + y[i];
+        for (int i = 0; i < P; ++i) S.trial[i] = S.theta[i] + y[i] / D[i];
       } else {
         for (int i = 0; i < P; ++i) S.trial[i] = S.theta[i];
       }
@@ -208,23 +222,23 @@ __global__ void __launch_bounds__(FIT_THREADS) psf_fit_kernel(const float* image
     __syncthreads();
 
     // ---- chi^2 at the trial point; accept or raise the damping ----
-    double c2 = 0.0;
+    float c2 = 0.0f, cc2 = 0.0f;
     for (int p = tid; p < npix; p += FIT_THREADS) {
       const float dx = (float)(p % w - cx), dy = (float)(p / w - cy);
-      const double r = (double)eval_pixel(S.trial, k, dx, dy, nullptr) - (double)img[p];
-      c2 += r * r;
+      const float r = eval_pixel(S.trial, k, dx, dy, nullptr) - img[p];
+      kahan_add(c2, cc2, r * r);
     }
     c2 = block_sum(c2, S.red);
     if (tid == 0) {
       if (isfinite(c2) && c2 < S.chi) {
-        const double rel = (S.chi - c2) / fmax(S.chi, 1e-300);
+        const float rel = (S.chi - c2) / fmaxf(S.chi, 1e-30f);
         for (int i = 0; i < P; ++i) S.theta[i] = S.trial[i];
-        S.lambda = fmax(S.lambda / 3.0, 1e-15);
+        S.lambda = fmaxf(S.lambda / 3.0f, 1e-7f);
         S.chi = c2;
-        if (rel < 1e-12) S.done = 1;
+        if (rel < 1e-6f) S.done = 1;
       } else {
-        S.lambda *= 4.0;
-        if (S.lambda > 1e15) S.done = 1;
+        S.lambda *= 4.0f;
+        if (S.lambda > 1e10f) S.done = 1;
       }
     }
     __syncthreads();
@@ -243,16 +257,16 @@ __global__ void __launch_bounds__(FIT_THREADS) psf_fit_kernel(const float* image
         }
     float* out = rows_out + (size_t)blockIdx.x * k * 6;
     for (int c = 0; c < k; ++c) {
-      const double* t = S.theta + 6 * order[c];
-      const double a = exp(t[3]), b = t[4], cc = exp(t[5]);
-      out[6 * c + 0] = (float)exp(t[0]);
-      out[6 * c + 1] = (float)t[1];
-      out[6 * c + 2] = (float)t[2];
-      out[6 * c + 3] = (float)(a * a);
-      out[6 * c + 4] = (float)(a * b);
-      out[6 * c + 5] = (float)(b * b + cc * cc);
+      const float* t = S.theta + 6 * order[c];
+      const float a = expf(t[3]), b = t[4], cc = expf(t[5]);
+      out[6 * c + 0] = expf(t[0]);
+      out[6 * c + 1] = t[1];
+      out[6 * c + 2] = t[2];
+      out[6 * c + 3] = a * a;
+      out[6 * c + 4] = a * b;
+      out[6 * c + 5] = b * b + cc * cc;
     }
-    if (chi2_out) chi2_out[blockIdx.x] = (float)S.chi;
+    if (chi2_out) chi2_out[blockIdx.x] = S.chi;
   }
 }
 

@@ -85,25 +85,6 @@ struct BwdCfg {
   static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB a CTA can have");
 };
 
-template <int N>
-struct BwdLast {
-  static constexpr int R = Radix<N>::r[Radix<N>::P - 1];
-  static constexpr int NS = N / R;
-};
-
-template <int N, int S>
-__device__ __forceinline__ void fft_rest_b(float2* w, int j, const float2* tw1, const float2* tw2, float2* v) {
-  constexpr int R1 = Radix<N>::r[1];
-  stockham_load<N, R1, S>(w, j, tw1, v);
-  if constexpr (Radix<N>::P == 3) {
-    constexpr int R2 = Radix<N>::r[2];
-    __syncwarp();
-    stockham_store<N, R1>(w, j, 8, v);
-    __syncwarp();
-    stockham_load<N, R2, S>(w, j, tw2, v);
-  }
-}
-
 // WN: also d L / d(Sersic n), a seventh gradient per galaxy.  EIG: some PSF
 // of the context is an eigen-PSF (its spectrum at the galaxy's position is
 // combined from the component spectra bin by bin where a bin is read).
@@ -286,9 +267,9 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
 #pragma unroll
       for (int m = 0; m < 8; ++m) wb[swz<N>(8 * j + m)] = v[m];
       __syncwarp();
-      fft_rest_b<N, -1>(wb, j, tw1, tw2, v);
+      fft_rest<N, -1>(wb, j, tw1, tw2, v);
       __syncwarp();
-      constexpr int R = BwdLast<N>::R, NS = BwdLast<N>::NS;
+      constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
       stockham_store<N, R>(wb, j, NS, v);
       __syncwarp();
       // untangle: row f has spectrum (Z[k] + conj Z[N-k]) / 2, row f + N/2
@@ -323,11 +304,11 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
 #pragma unroll
     for (int m = 0; m < 8; ++m) wa[swz<N>(8 * j + m)] = v[m];
     __syncwarp();
-    fft_rest_b<N, -1>(wa, j, tw1, tw2, v);
+    fft_rest<N, -1>(wa, j, tw1, tw2, v);
 
     // ---- contraction with the mixture's derivatives ----
     {
-      constexpr int R = BwdLast<N>::R, NS = BwdLast<N>::NS;
+      constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
       const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
       const int nf = r.nf;
       // every lane of the warp reaches both __syncwarp calls; only the

@@ -26,12 +26,19 @@
 
 namespace mog {
 
-template <int N>
+// CPG: columns (and row pairs) each group of TPF threads transforms, one
+// after the other.  CPG = 2 halves the CTA (512 threads at N = 128) and its
+// shared memory (the PSF spectrum is read from L2 instead of staged, and the
+// column transforms use one work row per group), so that two CTAs share an
+// SM and one computes while the other waits at a CTA barrier.
+template <int N, int CPG = 1>
 struct FwdCfg {
   static constexpr int H = N / 2 + 1;
   static constexpr int TPF = N / 8;          // threads per FFT
   static constexpr int NFFT = N / 2;         // FFTs per pass
-  static constexpr int THREADS = NFFT * TPF;
+  static constexpr int GROUPS = NFFT / CPG;  // thread groups of TPF threads
+  static constexpr int THREADS = GROUPS * TPF;
+  static constexpr bool PSF_SMEM = CPG == 1;  // PSF spectrum staged in shared memory
   static constexpr int LS = psf_lstride(N);
   static constexpr int PSF_ELEMS = psf_spec_elems(N);
   // FFT work row stride (float2).  A row touches wstride<N>() slots.
@@ -49,20 +56,21 @@ struct FwdCfg {
   static constexpr int SKEW = N == 64 ? 4 : 0;
   static_assert(SKEW <= WS - wstride<N>(), "shifted rows must not overlap");
   __host__ __device__ static constexpr int row(int r) { return r * WS + SKEW * ((r >> 1) & 1); }
-  static constexpr int W_ELEMS = NFFT * WS;
+  static constexpr int W_ELEMS = NFFT * WS;                 // row transforms (pass B): one row per row pair
+  static constexpr int WA_ELEMS = (CPG == 1 ? NFFT : GROUPS) * WS;   // column transforms (pass A)
   static constexpr int R1 = Radix<N>::r[1];
   static constexpr int R2 = Radix<N>::r[2];
   static constexpr int TW1 = twiddle_elems<N, R1>();
   static constexpr int TW2 = Radix<N>::P == 3 ? twiddle_elems<N, (R2 > 1 ? R2 : 2)>() : 0;
-  static constexpr int MIN_BLOCKS = N == 32 ? 16 : N == 64 ? 4 : 1;
+  static constexpr int MIN_BLOCKS = N == 32 ? 16 : N == 64 ? 4 : CPG;
   // N = 64: the row transforms reuse the column transforms' work rows (one
   // more CTA barrier per galaxy), which frees 18 KB of shared memory so that
   // four CTAs fit per SM (measured 6% faster than three without the barrier).
   static constexpr bool ALIAS_W = N == 64;
 
   static constexpr size_t off_psf = 0;
-  static constexpr size_t off_wa = off_psf + sizeof(float2) * PSF_ELEMS;
-  static constexpr size_t off_wb = ALIAS_W ? off_wa : off_wa + sizeof(float2) * W_ELEMS;
+  static constexpr size_t off_wa = off_psf + (PSF_SMEM ? sizeof(float2) * PSF_ELEMS : 0);
+  static constexpr size_t off_wb = ALIAS_W ? off_wa : off_wa + sizeof(float2) * WA_ELEMS;
   static constexpr size_t off_tw = off_wb + sizeof(float2) * W_ELEMS;
   static constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
   static constexpr size_t off_py = off_px + sizeof(float2) * H;
@@ -71,27 +79,6 @@ struct FwdCfg {
   static constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);   // two tables, one per record buffer
   static constexpr size_t off_bar = (off_rt + 2 * sizeof(RealTerms) + 15) & ~size_t(15);
   static constexpr size_t SMEM = off_bar + 3 * sizeof(uint64_t);
-};
-
-// Passes after the first of an FFT held in row `w` of the work buffer; the
-// result of the last pass is left in v (output index stockham_out_index).
-template <int N, int S>
-__device__ __forceinline__ void fft_rest(float2* w, int j, const float2* tw1, const float2* tw2, float2* v) {
-  constexpr int R1 = Radix<N>::r[1];
-  stockham_load<N, R1, S>(w, j, tw1, v);
-  if constexpr (Radix<N>::P == 3) {
-    constexpr int R2 = Radix<N>::r[2];
-    __syncwarp();
-    stockham_store<N, R1>(w, j, 8, v);
-    __syncwarp();
-    stockham_load<N, R2, S>(w, j, tw2, v);
-  }
-}
-
-template <int N>
-struct LastPass {
-  static constexpr int R = Radix<N>::r[Radix<N>::P - 1];
-  static constexpr int NS = N / R;
 };
 
 // Position of pixel x in an output row: the 16-byte pieces 8..15 swap in
@@ -185,10 +172,11 @@ __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, 
 // convolved in shared memory along x, then y, before it is added.
 // EIG: some PSF of the context is an eigen-PSF (the variant without it has
 // none of that code).
-template <int N, bool LZ, bool EIG>
-__global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
+template <int N, bool LZ, bool EIG, int CPG = 1>
+__global__ void __launch_bounds__(FwdCfg<N, CPG>::THREADS, FwdCfg<N, CPG>::MIN_BLOCKS)
     render_fwd_kernel(RenderParams p) {
-  using C = FwdCfg<N>;
+  using C = FwdCfg<N, CPG>;
+  static_assert(!(LZ && CPG > 1), "the Lanczos variant keeps one column per group");
   constexpr int TPF = C::TPF, LS = C::LS;
   constexpr int B = bucket_of(N);
   constexpr float INV_N = 1.0f / N;
@@ -243,7 +231,6 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1]);
   }
   float2* wa = WA + C::row(f);   // this group's row in pass A
-  float2* wb = WB + C::row(f);   // this group's row in pass B
   int cur_psf = -1;
   uint32_t psf_parity = 0, rec_parity = 0;   // rec_parity bit b: phase of record buffer b
   __syncthreads();
@@ -272,21 +259,29 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     // eigen-PSF: the spectrum at the galaxy's position, sum_c m_c S_c, is
     // formed in shared memory by every thread (read after S2); the set-up
     // tasks below take the bins they need straight from the components
+    // (without a staged spectrum, CPG > 1: where each bin is read)
     const float* pc = p.pcoef + ((size_t)first + pos) * PCOEF;
-    const bool eig = EIG && need_psf && p.psfs[r.psf].k_eig > 0;
+    const bool eig = EIG && rec_landed && r.ok && p.psfs[r.psf].k_eig > 0;
     if (eig) {
-      const DevPsf& ps = p.psfs[r.psf];
-      for (int e = tid; e < C::PSF_ELEMS; e += C::THREADS) psf_hat[e] = eigen_bin(ps.spec[B], C::PSF_ELEMS, ps.k_eig, pc, e);
+      if constexpr (C::PSF_SMEM) {
+        const DevPsf& ps = p.psfs[r.psf];
+        for (int e = tid; e < C::PSF_ELEMS; e += C::THREADS) psf_hat[e] = eigen_bin(ps.spec[B], C::PSF_ELEMS, ps.k_eig, pc, e);
+      }
       cur_psf = -1;   // the next galaxy forms its own
     } else if (need_psf) {   // uniform: every thread reads the same record
-      if (tid == 0) bulk_load(psf_hat, p.psfs[r.psf].spec[B], sizeof(float2) * C::PSF_ELEMS, &bar[0]);
-      psf_landed = mbar_wait(&bar[0], psf_parity);
-      psf_parity ^= 1u;
+      if constexpr (C::PSF_SMEM) {
+        if (tid == 0) bulk_load(psf_hat, p.psfs[r.psf].spec[B], sizeof(float2) * C::PSF_ELEMS, &bar[0]);
+        psf_landed = mbar_wait(&bar[0], psf_parity);
+        psf_parity ^= 1u;
+      }
       cur_psf = r.psf;
     }
     const bool landed = rec_landed && psf_landed;
     const bool work = landed && r.ok;
     RealTerms& rt = rts[buf];
+    // the spectrum in global memory (L2-resident) when it is not staged
+    const float2* psf_g = nullptr;
+    int k_eig = 0;
 
     // per-galaxy tables: shift phases, the nu = 1/2 column of the spectrum
     // (needed at +omega and -omega by the packed transform) and the
@@ -296,6 +291,10 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
       // shared-memory load less on the path to the set-up tasks
       const DevPsf& ps = p.psfs[EIG ? r.psf : cur_psf];
       const int kp = ps.k, nrt = r.nrc * kp, nr2 = real_terms_padded(nrt);
+      if constexpr (!C::PSF_SMEM) {
+        psf_g = ps.spec[B];
+        k_eig = eig ? ps.k_eig : 0;
+      }
       // what the store needs of the record is copied out: the record buffer
       // is refilled while slower warps may still be storing
       if (tid == 0) {
@@ -351,7 +350,7 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
             phy = cmul(phy, lanczos_response(w, om));
           }
           const float2 pn = eig ? eigen_bin(ps.spec[B], C::PSF_ELEMS, ps.k_eig, pc, (N / 2) * LS + l)
-                                : psf_hat[(N / 2) * LS + l];
+                                : (C::PSF_SMEM ? psf_hat[(N / 2) * LS + l] : __ldg(ps.spec[B] + (N / 2) * LS + l));
           nyq[l] = cscale(cmul(pn, cmul(phx, phy)), acc);
         } else {
           const int t = i - t0;
@@ -372,151 +371,173 @@ __global__ void __launch_bounds__(FwdCfg<N>::THREADS, FwdCfg<N>::MIN_BLOCKS)
     const int nf = r.nf;
     const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
     float2 v[8];
-    {
-      // column nu = f / N (group 0: nu = 0), 8 bins per thread
-      const float nu = f * INV_N;
-      const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
-      const float omj = (float)j * INV_N;
-      // bins (2k, 2k+1) of the thread share packed f32x2 instructions
-      float2 q[4], s[4];
-      float qmin = 3.4e38f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        // l = j + m TPF is below N/2 exactly for m < 4
-        const float om0 = omj + (float)(2 * k * TPF - (2 * k >= 4 ? N : 0)) * INV_N;
-        const float om1 = omj + (float)((2 * k + 1) * TPF - (2 * k + 1 >= 4 ? N : 0)) * INV_N;
-        q[k] = make_float2(fmaf(om0, fmaf(s22, om0, a1), a0), fmaf(om1, fmaf(s22, om1, a1), a0));
-        qmin = fminf(qmin, fminf(q[k].x, q[k].y));
-        s[k] = make_float2(0.0f, 0.0f);
-      }
-      for (int i = 0; i < nf; ++i) {
-        const float4 ac = s_fc[i];
-        if (!__any_sync(0xffffffffu, ac.z * qmin > NEGLIGIBLE_LOG2)) continue;
-        const float2 a2 = make_float2(ac.x, ac.y), c2 = make_float2(ac.z, ac.w);
+#pragma unroll 1
+    for (int cc = 0; cc < CPG; ++cc) {
+      const int col = f + cc * C::GROUPS;   // column nu = col / N (column 0: nu = 0 and 1/2 packed)
+      {
+        // 8 bins per thread
+        const float nu = col * INV_N;
+        const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
+        const float omj = (float)j * INV_N;
+        // bins (2k, 2k+1) of the thread share packed f32x2 instructions
+        float2 q[4], s[4];
+        float qmin = 3.4e38f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float2 e = __fmul2_rn(c2, q[k]);
-          s[k] = __ffma2_rn(a2, make_float2(ex2(e.x), ex2(e.y)), s[k]);
+          // l = j + m TPF is below N/2 exactly for m < 4
+          const float om0 = omj + (float)(2 * k * TPF - (2 * k >= 4 ? N : 0)) * INV_N;
+          const float om1 = omj + (float)((2 * k + 1) * TPF - (2 * k + 1 >= 4 ? N : 0)) * INV_N;
+          q[k] = make_float2(fmaf(om0, fmaf(s22, om0, a1), a0), fmaf(om1, fmaf(s22, om1, a1), a0));
+          qmin = fminf(qmin, fminf(q[k].x, q[k].y));
+          s[k] = make_float2(0.0f, 0.0f);
         }
-      }
-      const float2 pxf = px[f];
+        for (int i = 0; i < nf; ++i) {
+          const float4 ac = s_fc[i];
+          if (!__any_sync(0xffffffffu, ac.z * qmin > NEGLIGIBLE_LOG2)) continue;
+          const float2 a2 = make_float2(ac.x, ac.y), c2 = make_float2(ac.z, ac.w);
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int l = j + m * TPF;
-        v[m] = cscale(cmul(psf_hat[f * LS + l], cmul(pxf, py[l])), (m & 1) ? s[m >> 1].y : s[m >> 1].x);
-      }
-    }
-    if (f == 0) {
-      // Pack the Hermitian parts of the nu = 0 and nu = 1/2 columns as
-      // re + i im.  The nu = 0 column is Hermitian in omega by construction
-      // (its self-conjugate bin l = N/2 keeps its real part); the nu = 1/2
-      // column is symmetrised from both signs of omega.
-#pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int l = j + m * TPF;
-        const float2 dc = (l == N / 2) ? make_float2(v[m].x, 0.0f) : v[m];
-        const float2 a = nyq[l], b = nyq[(N - l) & (N - 1)];
-        const float2 hn = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
-        v[m] = make_float2(dc.x - hn.y, dc.y + hn.x);
-      }
-    }
-
-    // ---- Step 7a: inverse FFT of every column along omega ----
-    dft8<+1>(v);
-    first_pass_store<N>(wa, j, v);
-    __syncwarp();
-    fft_rest<N, +1>(wa, j, tw1, tw2, v);
-    if constexpr (C::ALIAS_W) __syncthreads();   // every column's last loads are done
-    {
-      // The last pass leaves rows n = j + q N/8 + m N/R of column f in this
-      // thread, so rows p and p + N/2 (outputs m and m + R/2, p < N/2) meet
-      // here without an exchange: Z_p[f] = A + iB and Z_p[N-f] = conj(A) +
-      // i conj(B) feed the row transform of pair p (any two real rows can
-      // share one complex transform).
-      constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
-#pragma unroll
-      for (int q = 0; q < 8 / R; ++q)
-#pragma unroll
-        for (int m = 0; m < R / 2; ++m) {
-          const float2 A = v[q * R + m], Bv = v[q * R + m + R / 2];
-          float2* row = WB + C::row(stockham_out_index<N, R>(j, NS, q, m));
-          if (f > 0) {
-            row[swz<N>(f)] = make_float2(A.x - Bv.y, A.y + Bv.x);
-            row[swz<N>(N - f)] = make_float2(A.x + Bv.y, Bv.x - A.y);
-          } else {
-            row[swz<N>(0)] = make_float2(A.x, Bv.x);
-            row[swz<N>(N / 2)] = make_float2(A.y, Bv.y);
+          for (int k = 0; k < 4; ++k) {
+            const float2 e = __fmul2_rn(c2, q[k]);
+            s[k] = __ffma2_rn(a2, make_float2(ex2(e.x), ex2(e.y)), s[k]);
           }
         }
-    }
+        const float2 pxf = px[col];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int l = j + m * TPF;
+          float2 pv;
+          if constexpr (C::PSF_SMEM) pv = psf_hat[col * LS + l];
+          else pv = (EIG && k_eig) ? eigen_bin(psf_g, C::PSF_ELEMS, k_eig, pc, col * LS + l) : __ldg(psf_g + col * LS + l);
+          v[m] = cscale(cmul(pv, cmul(pxf, py[l])), (m & 1) ? s[m >> 1].y : s[m >> 1].x);
+        }
+      }
+      if (col == 0) {
+        // Pack the Hermitian parts of the nu = 0 and nu = 1/2 columns as
+        // re + i im.  The nu = 0 column is Hermitian in omega by construction
+        // (its self-conjugate bin l = N/2 keeps its real part); the nu = 1/2
+        // column is symmetrised from both signs of omega.
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int l = j + m * TPF;
+          const float2 dc = (l == N / 2) ? make_float2(v[m].x, 0.0f) : v[m];
+          const float2 a = nyq[l], b = nyq[(N - l) & (N - 1)];
+          const float2 hn = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+          v[m] = make_float2(dc.x - hn.y, dc.y + hn.x);
+        }
+      }
+
+      // ---- Step 7a: inverse FFT of every column along omega ----
+      dft8<+1>(v);
+      if (cc > 0) __syncwarp();   // the group's loads of its previous column are done
+      first_pass_store<N>(wa, j, v);
+      __syncwarp();
+      fft_rest<N, +1>(wa, j, tw1, tw2, v);
+      if constexpr (C::ALIAS_W) __syncthreads();   // every column's last loads are done
+      {
+        // The last pass leaves rows n = j + q N/8 + m N/R of column f in this
+        // thread, so rows p and p + N/2 (outputs m and m + R/2, p < N/2) meet
+        // here without an exchange: Z_p[f] = A + iB and Z_p[N-f] = conj(A) +
+        // i conj(B) feed the row transform of pair p (any two real rows can
+        // share one complex transform).
+        constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
+#pragma unroll
+        for (int q = 0; q < 8 / R; ++q)
+#pragma unroll
+          for (int m = 0; m < R / 2; ++m) {
+            const float2 A = v[q * R + m], Bv = v[q * R + m + R / 2];
+            float2* row = WB + C::row(stockham_out_index<N, R>(j, NS, q, m));
+            if (col > 0) {
+              row[swz<N>(col)] = make_float2(A.x - Bv.y, A.y + Bv.x);
+              row[swz<N>(N - col)] = make_float2(A.x + Bv.y, Bv.x - A.y);
+            } else {
+              row[swz<N>(0)] = make_float2(A.x, Bv.x);
+              row[swz<N>(N / 2)] = make_float2(A.y, Bv.y);
+            }
+          }
+      }
+    }   // columns of this group
     __syncthreads();  // S3: every column has been transformed
 
-    // ---- Step 7b: real inverse FFT of row pairs (f, f + N/2) along nu ----
-    first_pass_load<N>(wb, j, v);
-    dft8<+1>(v);
-    __syncwarp();
-    first_pass_store<N>(wb, j, v);
-    __syncwarp();
-    fft_rest<N, +1>(wb, j, tw1, tw2, v);
-    __syncwarp();
-    float* orow = reinterpret_cast<float*>(wb);
-    {
-      // Rows f and f + N/2 of the patch overwrite this transform's own row.
-      // Pixel x is kept at x ^ 4 [bit 5 of x]: the 16-byte pieces 8..15 of a
-      // row swap in pairs, so the 8 lanes that read pieces 2j (then 2j+1)
-      // below touch 8 different bank groups.
-      constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
-#pragma unroll
-      for (int q = 0; q < 8 / R; ++q)
-#pragma unroll
-        for (int m = 0; m < R; ++m) {
-          const int n = stockham_out_index<N, R>(j, NS, q, m);
-          const int x = n ^ (((n >> 5) & 1) << 2);
-          orow[x] = v[q * R + m].x;
-          orow[N + x] = v[q * R + m].y;
-        }
-    }
-    __syncwarp();   // the group's two rows are complete
-    float* dst = s_dst[buf];
+    // ---- Step 7b: real inverse FFT of row pairs (prow, prow + N/2) along nu ----
+    float* const dst = s_dst[buf];
     const int nr = s_nr[buf];
-
-    // ---- Step 8: add the real-space terms and store rows f and f + N/2 ----
-    if constexpr (LZ) {
-      if (nr > 0) {   // uniform over the CTA
-        lanczos_real_and_store<N>(WB, orow, rt, nr, s_lzw[buf], f, j, dst, p.accumulate != 0);
-        continue;
-      }
-    }
-    // Each thread stores pixels 8j .. 8j+7 of both rows (runs of 4 with
-    // conflict-free reads were measured slower: twice the ex2 and term set-ups).
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      const int yy = f + h * (N / 2);
-      const int x0 = 8 * j;
-      const int sw = ((j >> 2) & 1) << 2;   // pieces 2j, 2j+1 swapped in the upper half of the row
-      const float* src = orow + h * N;
-      const float4 i0 = *reinterpret_cast<const float4*>(src + (x0 ^ sw));
-      const float4 i1 = *reinterpret_cast<const float4*>(src + ((x0 + 4) ^ sw));
-      float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
-      if (nr > 0) real_space_run(rt, nr, (float)yy, (float)x0, o);
-      store8(dst + yy * N + x0, o, p.accumulate != 0);
-    }
+    for (int rr = 0; rr < CPG; ++rr) {
+      const int prow = f + rr * C::GROUPS;
+      float2* wb = WB + C::row(prow);   // this row pair's row in pass B
+      first_pass_load<N>(wb, j, v);
+      dft8<+1>(v);
+      __syncwarp();
+      first_pass_store<N>(wb, j, v);
+      __syncwarp();
+      fft_rest<N, +1>(wb, j, tw1, tw2, v);
+      __syncwarp();
+      float* orow = reinterpret_cast<float*>(wb);
+      {
+        // Rows f and f + N/2 of the patch overwrite this transform's own row.
+        // Pixel x is kept at x ^ 4 [bit 5 of x]: the 16-byte pieces 8..15 of a
+        // row swap in pairs, so the 8 lanes that read pieces 2j (then 2j+1)
+        // below touch 8 different bank groups.
+        constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
+#pragma unroll
+        for (int q = 0; q < 8 / R; ++q)
+#pragma unroll
+          for (int m = 0; m < R; ++m) {
+            const int n = stockham_out_index<N, R>(j, NS, q, m);
+            const int x = n ^ (((n >> 5) & 1) << 2);
+            orow[x] = v[q * R + m].x;
+            orow[N + x] = v[q * R + m].y;
+          }
+      }
+      __syncwarp();   // the group's two rows are complete
+
+      // ---- Step 8: add the real-space terms and store rows prow and prow + N/2 ----
+      if constexpr (LZ) {
+        if (nr > 0) {   // uniform over the CTA
+          lanczos_real_and_store<N>(WB, orow, rt, nr, s_lzw[buf], f, j, dst, p.accumulate != 0);
+          continue;
+        }
+      }
+      // Each thread stores pixels 8j .. 8j+7 of both rows (runs of 4 with
+      // conflict-free reads were measured slower: twice the ex2 and term set-ups).
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int yy = prow + h * (N / 2);
+        const int x0 = 8 * j;
+        const int sw = ((j >> 2) & 1) << 2;   // pieces 2j, 2j+1 swapped in the upper half of the row
+        const float* src = orow + h * N;
+        const float4 i0 = *reinterpret_cast<const float4*>(src + (x0 ^ sw));
+        const float4 i1 = *reinterpret_cast<const float4*>(src + ((x0 + 4) ^ sw));
+        float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+        if (nr > 0) real_space_run(rt, nr, (float)yy, (float)x0, o);
+        store8(dst + yy * N + x0, o, p.accumulate != 0);
+      }
+    }   // row pairs of this group
   }
 }
 
+// Columns per group of the launched kernel: two at N = 128 (two 512-thread
+// CTAs per SM), except in the Lanczos variant.
+template <int N, bool LZ>
+constexpr int fwd_cpg() { return (N == 128 && !LZ) ? 2 : 1; }
+
+static_assert(2 * (FwdCfg<128, 2>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 CTAs share an SM's shared memory");
+
 template <int N, bool LZ = false, bool EIG = false>
 static int fwd_occupancy() {
-  using C = FwdCfg<N>;
-  return kernel_occupancy(reinterpret_cast<const void*>(render_fwd_kernel<N, LZ, EIG>), C::THREADS, C::SMEM);
+  constexpr int CPG = fwd_cpg<N, LZ>();
+  using C = FwdCfg<N, CPG>;
+  return kernel_occupancy(reinterpret_cast<const void*>(render_fwd_kernel<N, LZ, EIG, CPG>), C::THREADS, C::SMEM);
 }
 
 template <int N, bool LZ, bool EIG>
 static cudaError_t launch_fwd_mode(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
-  using C = FwdCfg<N>;
+  constexpr int CPG = fwd_cpg<N, LZ>();
+  using C = FwdCfg<N, CPG>;
   const int occ = fwd_occupancy<N, LZ, EIG>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_fwd_kernel<N, LZ, EIG><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
+  render_fwd_kernel<N, LZ, EIG, CPG><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -553,7 +574,7 @@ size_t render_fwd_smem(int n) {
   switch (n) {
     case 32: return FwdCfg<32>::SMEM;
     case 64: return FwdCfg<64>::SMEM;
-    case 128: return FwdCfg<128>::SMEM;
+    case 128: return FwdCfg<128, fwd_cpg<128, false>()>::SMEM;
     default: return 0;
   }
 }

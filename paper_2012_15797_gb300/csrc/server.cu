@@ -18,6 +18,7 @@
 // records each request's latency (submission to results available).
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -128,6 +129,7 @@ struct Request {
   Clock::time_point submitted;
   double latency = -1.0;
   bool done = false;
+  bool dropped = false;       // fault injection: its completion is lost
   int status = MOG_OK;
 };
 
@@ -235,6 +237,10 @@ struct mog_server {
   // stats
   int64_t n_requests = 0, n_galaxies = 0, n_batches = 0, max_batch = 0;
   int max_inflight = 0;
+  // host-side fault injection (mog_server_inject_fault): the nth request
+  // admitted (drop) or micro-batch launched (launch, nomem) since arming
+  int fault_kind = 0;
+  int64_t fault_nth = 0, fault_seen = 0;
 };
 
 namespace mog {
@@ -367,6 +373,14 @@ void scheduler(mog_server* S) {
       S->cv_sched.wait(lk, [&] { return S->stop || S->arena.largest() > avail; });
       continue;
     }
+    // injected faults are decided under the lock, like the admission itself
+    int injected = MOG_OK;
+    if (S->fault_kind == MOG_FAULT_DROP) {
+      for (auto& r : take)
+        if (++S->fault_seen == S->fault_nth) r->dropped = true;
+    } else if (S->fault_kind == MOG_FAULT_LAUNCH || S->fault_kind == MOG_FAULT_NOMEM) {
+      if (++S->fault_seen == S->fault_nth) injected = S->fault_kind == MOG_FAULT_LAUNCH ? MOG_ERR_CUDA : MOG_ERR_NOMEM;
+    }
     const size_t bytes = batch_bytes(g, pix);
     L->block = S->arena.alloc(bytes);
     L->block_bytes = bytes;
@@ -377,8 +391,11 @@ void scheduler(mog_server* S) {
     for (auto& l : S->lanes) inflight += l.busy;
     if (inflight > S->max_inflight) S->max_inflight = inflight;
     lk.unlock();
-    // fill staging (outside the lock)
-    int st = lane_reserve(*L, g) ? MOG_OK : MOG_ERR_NOMEM;
+    // fill staging (outside the lock); an injected allocation failure stands
+    // in for a failing cudaHostAlloc, an injected launch failure for a
+    // failing CUDA call before anything of the batch is enqueued
+    int st = injected == MOG_ERR_NOMEM ? MOG_ERR_NOMEM : (lane_reserve(*L, g) ? MOG_OK : MOG_ERR_NOMEM);
+    if (st == MOG_OK && injected != MOG_OK) st = injected;
     if (st == MOG_OK) {
       int64_t i = 0, off = 0;
       for (auto& r : take) {
@@ -433,11 +450,14 @@ void completer(mog_server* S) {
     }
     // results -> callers (lane is owned by this thread until freed)
     mog_server::Lane& L = *ready;
+    // a batch that failed part-way may still have work on its stream, which
+    // uses the lane's arena block: let it finish before the block is reused
+    if (L.status != MOG_OK) cudaStreamSynchronize(L.stream);
     const int64_t g = L.galaxies;
     int64_t i = 0;
     const auto now = Clock::now();
     for (auto& r : L.reqs) {
-      if (L.status == MOG_OK) {
+      if (L.status == MOG_OK && !r->dropped) {
         for (int64_t k = 0; k < r->count; ++k) {
           for (int c = 0; c < 6; ++c) r->grads[6 * k + c] = L.st.results[6 * (i + k) + c];
           if (r->chi2) r->chi2[k] = L.st.results[6 * g + i + k];
@@ -447,6 +467,7 @@ void completer(mog_server* S) {
     }
     std::unique_lock<std::mutex> lk(S->mu);
     for (auto& r : L.reqs) {
+      if (r->dropped) continue;   // injected: this completion is lost
       r->status = L.status;
       r->latency = std::chrono::duration<double>(now - r->submitted).count();
       r->done = true;
@@ -505,8 +526,29 @@ mog_status mog_server_add_fit(mog_server* S, const mog_fit_state* fit, int* fit_
     return MOG_ERR_ARG;
   mog_ctx* ctx = S->ctx;
   MOG_CUDA(ctx, cudaSetDevice(ctx->device));
-  std::vector<int32_t> sizes(fit->count);
+  std::vector<int32_t> sizes(fit->count), profile(fit->count), psf(fit->count);
+  std::vector<float> sersic(fit->count), ivar(fit->count);
+  std::vector<int64_t> doff(fit->count);
   MOG_CUDA(ctx, cudaMemcpy(sizes.data(), fit->size, sizeof(int32_t) * fit->count, cudaMemcpyDeviceToHost));
+  MOG_CUDA(ctx, cudaMemcpy(profile.data(), fit->profile, sizeof(int32_t) * fit->count, cudaMemcpyDeviceToHost));
+  MOG_CUDA(ctx, cudaMemcpy(psf.data(), fit->psf, sizeof(int32_t) * fit->count, cudaMemcpyDeviceToHost));
+  MOG_CUDA(ctx, cudaMemcpy(sersic.data(), fit->sersic_n, sizeof(float) * fit->count, cudaMemcpyDeviceToHost));
+  MOG_CUDA(ctx, cudaMemcpy(ivar.data(), fit->ivar, sizeof(float) * fit->count, cudaMemcpyDeviceToHost));
+  MOG_CUDA(ctx, cudaMemcpy(doff.data(), fit->data_offset, sizeof(int64_t) * fit->count, cudaMemcpyDeviceToHost));
+  // everything the kernels would otherwise reject galaxy by galaxy is
+  // rejected here, so that every admitted request can be answered in full
+  for (int64_t k = 0; k < fit->count; ++k) {
+    if (bucket_of(sizes[k]) < 0) return fail(ctx, MOG_ERR_ARG, "fit galaxy %lld: patch side %d not in {32, 64, 128, 256}", (long long)k, sizes[k]);
+    if (profile[k] < 0 || profile[k] >= MOG_MAX_PROFILES || !ctx->profile_set[profile[k]])
+      return fail(ctx, MOG_ERR_ARG, "fit galaxy %lld: no profile table %d", (long long)k, profile[k]);
+    if (psf[k] < 0 || psf[k] >= MOG_MAX_PSFS || ctx->h_psfs[psf[k]].k == 0)
+      return fail(ctx, MOG_ERR_ARG, "fit galaxy %lld: no PSF %d", (long long)k, psf[k]);
+    if (ctx->h_psfs[psf[k]].k_eig > 0)
+      return fail(ctx, MOG_ERR_ARG, "fit galaxy %lld: eigen-PSF %d needs image positions, which fits do not carry", (long long)k, psf[k]);
+    if (!std::isfinite(sersic[k]) || !std::isfinite(ivar[k]) || !(ivar[k] >= 0.0f))
+      return fail(ctx, MOG_ERR_ARG, "fit galaxy %lld: Sersic index and inverse variance must be finite, ivar >= 0", (long long)k);
+    if (doff[k] < 0 || (doff[k] & 3)) return fail(ctx, MOG_ERR_ARG, "fit galaxy %lld: data offset must be >= 0 and a multiple of 4", (long long)k);
+  }
   DevFit F{fit->sersic_n, fit->profile, fit->psf, fit->size, fit->data_offset, fit->data, fit->ivar, fit->count};
   std::lock_guard<std::mutex> lk(S->mu);
   if ((int)S->fits.size() + 1 > S->d_fits_cap) {
@@ -541,6 +583,14 @@ mog_status mog_server_submit(mog_server* S, const mog_request* req, uint64_t* ti
   }
   if (batch_bytes(req->count, pix) > S->arena.total())
     return fail(S->ctx, MOG_ERR_ARG, "request larger than the server's memory budget");
+  for (int64_t k = 0; k < req->count; ++k) {
+    const float* q = req->params + 6 * k;
+    bool ok = true;
+    for (int c = 0; c < 6; ++c) ok = ok && std::isfinite(q[c]);
+    ok = ok && std::hypot(q[4], q[5]) < 1.0f && q[3] < 30.0f;
+    if (!ok)
+      return fail(S->ctx, MOG_ERR_ARG, "request galaxy %lld: parameters must be finite, |e| < 1, log r_e < 30", (long long)k);
+  }
   auto r = std::make_shared<Request>();
   r->ticket = S->next_ticket++;
   r->fit = req->fit;
@@ -598,6 +648,15 @@ mog_status mog_server_replay(mog_server* S, const mog_request* reqs, const doubl
 mog_status mog_server_replay_join(mog_server* S) {
   if (!S) return MOG_ERR_ARG;
   if (S->replay.joinable()) S->replay.join();
+  return MOG_OK;
+}
+
+mog_status mog_server_inject_fault(mog_server* S, int kind, int64_t nth) {
+  if (!S || kind < 0 || kind > MOG_FAULT_NOMEM || nth < 0) return MOG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->fault_kind = nth > 0 ? kind : 0;
+  S->fault_nth = nth;
+  S->fault_seen = 0;
   return MOG_OK;
 }
 

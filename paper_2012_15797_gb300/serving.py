@@ -53,9 +53,15 @@ class Server:
         """Returns (grads (count, 6), chi2 (count,), latency seconds)."""
         lat = ctypes.c_double()
         st = capi.library().mog_server_wait(self.handle, ctypes.c_uint64(ticket), float(timeout), ctypes.byref(lat))
-        keep = self._live.pop(ticket)
+        # a request that timed out is still the server's: keep its buffers
+        keep = self._live.get(ticket) if st == capi.MOG_ERR_TIMEOUT else self._live.pop(ticket, None)
         capi._check(self.renderer.ctx, st)
         return keep[1], keep[2], lat.value
+
+    def inject_fault(self, kind, nth):
+        """Arms a host-side fault (capi.MOG_FAULT_DROP / _LAUNCH / _NOMEM) for
+        the nth request admitted or micro-batch launched from now on."""
+        capi._check(self.renderer.ctx, capi.library().mog_server_inject_fault(self.handle, int(kind), int(nth)))
 
     def replay(self, requests, arrival_s):
         """requests: list of (fit, first, params (count, 6)); submitted by a
