@@ -108,7 +108,12 @@ typedef struct mog_batch {
 } mog_batch;
 
 /* Creates a context on CUDA device `device` (makes it current).  *out gets
- * the handle; destroy it with mog_destroy_context. */
+ * the handle; destroy it with mog_destroy_context.  A context's batched
+ * render and adjoint calls share one workspace (planner counters, per-galaxy
+ * records): calls of one context must not overlap on the GPU, so issue them
+ * on one stream or order the streams (a context per stream runs
+ * concurrently; the serving runtime and the host-memory entry point keep
+ * workspaces of their own). */
 mog_status mog_create_context(mog_ctx** out, int device);
 mog_status mog_destroy_context(mog_ctx* ctx);
 
@@ -278,9 +283,22 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
  *                    e1, e2, sersic_n).  Zero for one-node (fixed) profiles
  *                    and outside the node range; at a node the derivative of
  *                    the interval above it.
+ *   MOG_GRAD_LANCZOS the gradient of the Lanczos variant's model
+ *                    (mog_render_batch_lanczos, Section 2, Step 8): the
+ *                    model is the render at the integer offset
+ *                    n = floor(x + 1/2) convolved with the Lanczos-3 weights
+ *                    of the fraction d = x - n, so d/dx (d/dy) is the
+ *                    derivative through the weights and the other
+ *                    gradients are those of the integer-offset render for
+ *                    the transposed-convolved upstream gradient.  Computed
+ *                    as three adjoint passes at the integer offsets (the
+ *                    upstream patches formed on the device); uses workspace
+ *                    memory of three times the gradient patches' extent and
+ *                    synchronises `stream` once (to read that extent).
+ *                    Combines with MOG_GRAD_SERSIC.
  * Other arguments and errors as mog_render_backward.
  */
-enum { MOG_GRAD_SERSIC = 1 };
+enum { MOG_GRAD_SERSIC = 1, MOG_GRAD_LANCZOS = 2 };
 
 /*
  * Fits a k-component Gaussian mixture (1 <= k <= 4) to each of `count`
@@ -304,14 +322,32 @@ mog_status mog_render_backward_ex(mog_ctx* ctx, const mog_batch* batch, const fl
 
 /*
  * Autotuner (the batching feature): for each size bucket present in the
- * batch (batch->size_mask, or all), times the render kernel over every
- * launch shape (CTAs per SM from 1 to what fits x work-queue chunk of
- * 1..32 galaxies) with CUDA events, `reps` renders per shape, and keeps the
- * fastest in the context for later calls.  With non-null grad_out and
- * grad_params the adjoint is tuned the same way.  Writes `out` and
- * grad_params as a side effect.  report (host, optional, 16 ints) receives
- * (ctas_per_sm, chunk) per [direction][bucket].  Synchronous.
+ * batch (batch->size_mask, or all), times that bucket's render kernel alone
+ * over every radix schedule of its FFTs (two per side: 32 = 8*4 or 8*2*2,
+ * 64 = 8*8 or 8*4*2, 128 = 8*8*2 or 8*4*4, 256 = 8*8*4 or 8*4*8) x every
+ * launch shape (CTAs per SM from 1 to what fits x work-queue chunk of 1..32
+ * galaxies) with CUDA events, `reps` renders per choice, and keeps the
+ * fastest in the context for later calls (the second schedule applies to the
+ * plain render; the Lanczos and eigen-PSF variants keep the first).  With
+ * several sizes in the batch it then times the whole render with the size
+ * kernels forked onto parallel streams and one after the other, and keeps the
+ * faster.  With non-null grad_out and grad_params the adjoint's launch shapes
+ * are tuned too (one schedule).  Writes `out` and grad_params as a side
+ * effect.  report (host, optional, MOG_AUTOTUNE_REPORT ints) receives
+ * (ctas_per_sm, chunk, schedule) per [direction][bucket] (zeros for buckets
+ * not tuned), then 1 if the size kernels run one after the other, 0 if
+ * forked.  Synchronous.
  */
+enum { MOG_AUTOTUNE_REPORT = 2 * 4 * 3 + 1 };
+
+/*
+ * Sets a launch shape by hand (as mog_autotune would keep it): direction
+ * dir (0 render, 1 adjoint), patch side n, CTAs per SM (0 = as many as fit,
+ * larger values are clamped to that), work-queue chunk (1..1024 galaxies),
+ * radix schedule (0 or 1, as listed for mog_autotune; the adjoint has
+ * schedule 0 only).  Synchronous; MOG_ERR_ARG for values outside these.
+ */
+mog_status mog_set_launch_shape(mog_ctx* ctx, int dir, int n, int ctas_per_sm, int chunk, int sched);
 mog_status mog_autotune(mog_ctx* ctx, const mog_batch* batch, float* out, const float* grad_out,
                         float* grad_params, void* stream, int reps, int* report);
 
@@ -319,8 +355,9 @@ mog_status mog_autotune(mog_ctx* ctx, const mog_batch* batch, float* out, const 
  * CUDA graph of one batched render: the planner, the record prologue and
  * the per-size kernels (on parallel branches) captured once for fixed
  * batch / output buffers; every mog_graph_launch renders whatever those
- * buffers hold at launch time.  Capture makes one eager render first (sizing
- * scratch, configuring kernels), so nothing allocates during capture.  The
+ * buffers hold at launch time.  Capture synchronises the device, then makes
+ * one eager render (sizing scratch, configuring kernels) on the library's
+ * own stream, so nothing allocates during capture.  The
  * batch count and buffers are baked in; capture again when they change.
  */
 typedef struct mog_graph mog_graph;

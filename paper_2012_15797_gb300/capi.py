@@ -37,6 +37,7 @@ EXPORTED = (
     "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
     "mog_create_eigen_psf", "mog_render_batch_ex", "mog_render_backward_ex", "mog_fit_psf_mixture",
     "mog_render_batch_host", "mog_measure_pipe_rates", "mog_server_inject_fault", "mog_check_wait_timeout",
+    "mog_set_launch_shape",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -114,6 +115,7 @@ def _load():
         "mog_measure_pipe_rates": ([VP, I, P(ctypes.c_double), P(ctypes.c_double)], I),
         "mog_server_inject_fault": ([VP, I, ctypes.c_int64], I),
         "mog_check_wait_timeout": ([VP, ctypes.c_double, VP], I),
+        "mog_set_launch_shape": ([VP, I, I, I, I, I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -242,6 +244,7 @@ def mog_render_backward(ctx, batch, grad_out_ptr, grad_params_ptr, stream=0):
 
 
 MOG_GRAD_SERSIC = 1
+MOG_GRAD_LANCZOS = 2
 MOG_FAULT_DROP, MOG_FAULT_LAUNCH, MOG_FAULT_NOMEM = 1, 2, 3
 
 
@@ -258,19 +261,30 @@ def mog_fit_psf_mixture(ctx, images_ptr, count, h, w, k, iters, rows_ptr, chi2_p
                                          ctypes.c_void_p(int(stream))))
 
 
+MOG_AUTOTUNE_REPORT = 2 * 4 * 3 + 1
+
+
 def mog_autotune(ctx, batch, out_ptr, grad_out_ptr=0, grad_params_ptr=0, stream=0, reps=3):
-    """Returns {("fwd"|"bwd", N): (ctas_per_sm, chunk)} for the tuned buckets."""
-    rep = (ctypes.c_int * 16)(*([0] * 16))
+    """Returns {("fwd"|"bwd", N): (ctas_per_sm, chunk, schedule)} for the
+    tuned buckets and {"serial": bool} (size kernels one after the other
+    rather than forked)."""
+    rep = (ctypes.c_int * MOG_AUTOTUNE_REPORT)()
     _check(ctx, _lib.mog_autotune(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
                                   ctypes.c_void_p(int(grad_out_ptr)), ctypes.c_void_p(int(grad_params_ptr)),
                                   ctypes.c_void_p(int(stream)), int(reps), rep))
     out = {}
     for d, name in enumerate(("fwd", "bwd")):
         for b in range(4):
-            c, ch = rep[(d * 4 + b) * 2], rep[(d * 4 + b) * 2 + 1]
+            c, ch, sc = rep[(d * 4 + b) * 3], rep[(d * 4 + b) * 3 + 1], rep[(d * 4 + b) * 3 + 2]
             if c:
-                out[(name, 32 << b)] = (c, ch)
+                out[(name, 32 << b)] = (c, ch, sc)
+    out["serial"] = bool(rep[MOG_AUTOTUNE_REPORT - 1])
     return out
+
+
+def mog_set_launch_shape(ctx, direction, n, ctas_per_sm=0, chunk=8, schedule=0):
+    """direction: 0 render, 1 adjoint."""
+    _check(ctx, _lib.mog_set_launch_shape(ctx, int(direction), int(n), int(ctas_per_sm), int(chunk), int(schedule)))
 
 
 def mog_graph_capture(ctx, batch, out_ptr):

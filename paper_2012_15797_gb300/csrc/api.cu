@@ -80,6 +80,9 @@ void workspace_free(Workspace* ws) {
   cudaFree(ws->lzw);
   cudaFree(ws->pcoef);
   cudaFree(ws->bwd256);
+  cudaFree(ws->lz_up);
+  cudaFree(ws->lz_aux);
+  cudaFree(ws->lz_extent);
   for (int b = 0; b < NBUCKET; ++b) {
     if (ws->side[b]) cudaStreamDestroy(ws->side[b]);
     if (ws->join_ev[b]) cudaEventDestroy(ws->join_ev[b]);
@@ -131,6 +134,18 @@ mog_status ensure_capacity(mog_ctx* ctx, Workspace* ws, int64_t count) {
 }
 
 }  // namespace
+
+namespace mog {
+
+mog_status workspace_reserve(mog_ctx* ctx, Workspace* ws, int64_t count) {
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  mog_status st = ensure_capacity(ctx, ws, count);
+  if (st != MOG_OK) return st;
+  if (!ws->bwd256) MOG_CUDA(ctx, cudaMalloc(&ws->bwd256, render_bwd256_scratch_bytes(ctx->num_sms)));
+  return MOG_OK;
+}
+
+}  // namespace mog
 
 extern "C" {
 
@@ -396,7 +411,7 @@ template <class Launch>
 mog_status launch_buckets(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, uint32_t supported, cudaStream_t s,
                           Launch&& launch) {
   const uint32_t want = batch->size_mask ? (batch->size_mask & supported) : supported;
-  const bool fork = __builtin_popcount(want) > 1;
+  const bool fork = __builtin_popcount(want) > 1 && !ctx->serial_buckets;
   if (fork) MOG_CUDA(ctx, cudaEventRecord(ws->fork_ev, s));
   for (int b = 0; b < NBUCKET; ++b) {
     if (!((want >> b) & 1)) continue;
@@ -451,6 +466,7 @@ mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, floa
   return launch_buckets(ctx, ws, batch, buckets, s, [&](int n, cudaStream_t bs) {
     RenderParams q = p;
     q.chunk = ctx->tune_fwd[bucket_of(n)].chunk;
+    q.sched = ctx->tune_fwd[bucket_of(n)].sched;
     return launch_render_fwd(n, q, ctx->num_sms, ctx->tune_fwd[bucket_of(n)].ctas_per_sm, bs);
   });
 }
@@ -519,10 +535,69 @@ mog_status mog_fit_psf_mixture(mog_ctx* ctx, const float* images, int count, int
   return MOG_OK;
 }
 
+// The adjoint of the Lanczos variant (lanczos_adj.cu): three upstream
+// patches formed by transposed Lanczos convolution, three adjoint passes at
+// the integer offsets, the gradients combined.
+static mog_status lanczos_backward(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, const float* grad_out,
+                                   float* grad_params, cudaStream_t s, bool grad_n) {
+  mog_status st = check_batch(ctx, batch);
+  if (st != MOG_OK) return st;
+  if (batch->count == 0) return MOG_OK;
+  if (!grad_out || (reinterpret_cast<uintptr_t>(grad_out) & 15))
+    return fail(ctx, MOG_ERR_ARG, "grad_out must be 16-byte aligned");
+  if (!grad_params) return fail(ctx, MOG_ERR_ARG, "null grad_params");
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t g = batch->count;
+  const BatchView bv = view_of(batch);
+  if (!ws->lz_extent) MOG_CUDA(ctx, cudaMalloc(&ws->lz_extent, sizeof(unsigned long long)));
+  // the upstream patches share the caller's patch offsets: their extent is
+  // read back once (this call synchronises the stream there)
+  MOG_CUDA(ctx, launch_patch_extent(bv, g, ws->lz_extent, s));
+  unsigned long long extent = 0;
+  MOG_CUDA(ctx, cudaMemcpyAsync(&extent, ws->lz_extent, sizeof(extent), cudaMemcpyDeviceToHost, s));
+  MOG_CUDA(ctx, cudaStreamSynchronize(s));
+  if (extent == 0) extent = 4;
+  if (extent > ws->lz_up_cap) {
+    if (ws->lz_up) MOG_CUDA(ctx, cudaFree(ws->lz_up));
+    ws->lz_up = nullptr;
+    ws->lz_up_cap = 0;
+    MOG_CUDA(ctx, cudaMalloc(&ws->lz_up, sizeof(float) * 3 * (size_t)extent));
+    ws->lz_up_cap = extent;
+  }
+  constexpr int AUX = 2 + 7 + 6 + 6;   // integer x, y; gradients of G0 (up to 7), Hx, Hy
+  if (g > ws->lz_aux_cap) {
+    if (ws->lz_aux) MOG_CUDA(ctx, cudaFree(ws->lz_aux));
+    ws->lz_aux = nullptr;
+    ws->lz_aux_cap = 0;
+    MOG_CUDA(ctx, cudaMalloc(&ws->lz_aux, sizeof(float) * AUX * (size_t)g));
+    ws->lz_aux_cap = g;
+  }
+  float* up0 = ws->lz_up;
+  float* upx = up0 + ws->lz_up_cap;
+  float* upy = upx + ws->lz_up_cap;
+  float* xi = ws->lz_aux;
+  float* yi = xi + g;
+  float* a0 = yi + g;
+  float* ax = a0 + 7 * g;
+  float* ay = ax + 6 * g;
+  MOG_CUDA(ctx, launch_lanczos_upstream(bv, g, grad_out, up0, upx, upy, xi, yi, s));
+  mog_batch at_n = *batch;   // the galaxies at their integer offsets
+  at_n.x = xi;
+  at_n.y = yi;
+  if ((st = backward_with(ctx, ws, &at_n, up0, a0, s, grad_n)) != MOG_OK) return st;
+  if ((st = backward_with(ctx, ws, &at_n, upx, ax, s, false)) != MOG_OK) return st;
+  if ((st = backward_with(ctx, ws, &at_n, upy, ay, s, false)) != MOG_OK) return st;
+  MOG_CUDA(ctx, launch_lanczos_combine(g, batch->flux, a0, ax, ay, grad_n ? 7 : 6, grad_params, s));
+  return MOG_OK;
+}
+
 mog_status mog_render_backward_ex(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,
                                   void* stream, unsigned flags) {
   if (!ctx) return MOG_ERR_ARG;
-  if (flags & ~(unsigned)MOG_GRAD_SERSIC) return fail(ctx, MOG_ERR_ARG, "unknown gradient flags");
+  if (flags & ~(unsigned)(MOG_GRAD_SERSIC | MOG_GRAD_LANCZOS)) return fail(ctx, MOG_ERR_ARG, "unknown gradient flags");
+  if (flags & MOG_GRAD_LANCZOS)
+    return lanczos_backward(ctx, &ctx->ws, batch, grad_out, grad_params, static_cast<cudaStream_t>(stream),
+                            (flags & MOG_GRAD_SERSIC) != 0);
   return backward_with(ctx, &ctx->ws, batch, grad_out, grad_params, static_cast<cudaStream_t>(stream),
                        (flags & MOG_GRAD_SERSIC) != 0);
 }
@@ -562,6 +637,8 @@ mog_status mog_autotune(mog_ctx* ctx, const mog_batch* batch, float* out, const 
   int64_t n[NBUCKET];
   // drain anything recorded before
   if ((st = mog_read_timing(ctx, ms, n)) != MOG_OK) return st;
+  if (report)
+    for (int i = 0; i < MOG_AUTOTUNE_REPORT; ++i) report[i] = 0;
   static const int chunks[] = {1, 2, 4, 8, 16, 32};
   for (int dir = 0; dir < 2; ++dir) {
     if (dir == 1 && (!grad_out || !grad_params)) break;
@@ -570,39 +647,94 @@ mog_status mog_autotune(mog_ctx* ctx, const mog_batch* batch, float* out, const 
     const uint32_t want = batch->size_mask ? (batch->size_mask & sup) : sup;
     for (int b = 0; b < NBUCKET; ++b) {
       if (!((want >> b) & 1)) continue;
+      // only this bucket's kernel runs while its shapes are timed
+      mog_batch one = *batch;
+      one.size_mask = 1u << b;
       const int n_side = bucket_side(b);
-      const int max_ctas = dir == 0 ? render_fwd_max_ctas(n_side) : render_bwd_max_ctas(n_side);
       LaunchShape best = tune[b];
       double best_ms = 1e300;
-      for (int c = 1; c <= max_ctas; ++c)
-        for (int ch : chunks) {
-          tune[b].ctas_per_sm = c;
-          tune[b].chunk = ch;
-          ctx->timing = true;
-          for (int r = 0; r < reps; ++r) {
-            st = dir == 0 ? mog_render_batch(ctx, batch, out, stream)
-                          : mog_render_backward(ctx, batch, grad_out, grad_params, stream);
-            if (st != MOG_OK) {
-              ctx->timing = timing_was;
-              return st;
+      for (int sched = 0; sched < (dir == 0 ? SCHEDULES : 1); ++sched) {
+        const int max_ctas = dir == 0 ? render_fwd_max_ctas(n_side, sched) : render_bwd_max_ctas(n_side);
+        for (int c = 1; c <= max_ctas; ++c)
+          for (int ch : chunks) {
+            tune[b].ctas_per_sm = c;
+            tune[b].chunk = ch;
+            tune[b].sched = sched;
+            ctx->timing = true;
+            for (int r = 0; r < reps; ++r) {
+              st = dir == 0 ? mog_render_batch(ctx, &one, out, stream)
+                            : mog_render_backward(ctx, &one, grad_out, grad_params, stream);
+              if (st != MOG_OK) {
+                ctx->timing = timing_was;
+                return st;
+              }
+            }
+            ctx->timing = false;
+            if ((st = mog_read_timing(ctx, ms, n)) != MOG_OK) return st;
+            const double t = n[b] ? ms[b] / (double)n[b] : 1e300;
+            if (t < best_ms) {
+              best_ms = t;
+              best = tune[b];
             }
           }
-          ctx->timing = false;
-          if ((st = mog_read_timing(ctx, ms, n)) != MOG_OK) return st;
-          const double t = n[b] ? ms[b] / (double)n[b] : 1e300;
-          if (t < best_ms) {
-            best_ms = t;
-            best = tune[b];
-          }
-        }
+      }
       tune[b] = best;
       if (report) {
-        report[(dir * NBUCKET + b) * 2] = best.ctas_per_sm;
-        report[(dir * NBUCKET + b) * 2 + 1] = best.chunk;
+        int* e = report + (dir * NBUCKET + b) * 3;
+        e[0] = best.ctas_per_sm;
+        e[1] = best.chunk;
+        e[2] = best.sched;
       }
     }
   }
+  // With several sizes in the batch: their kernels forked onto parallel
+  // branches (a size's tail overlaps the next) or one after the other on the
+  // caller's stream (no co-resident kernels of different sizes), whichever
+  // renders the whole batch faster.
+  const uint32_t want = batch->size_mask ? (batch->size_mask & FWD_BUCKETS) : FWD_BUCKETS;
+  if (__builtin_popcount(want) > 1) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, e = nullptr;
+    MOG_CUDA(ctx, take_event(ctx, &a));
+    MOG_CUDA(ctx, take_event(ctx, &e));
+    double best_ms = 1e300;
+    bool best_serial = false;
+    for (int serial = 0; serial < 2 && st == MOG_OK; ++serial) {
+      ctx->serial_buckets = serial != 0;
+      st = mog_render_batch(ctx, batch, out, stream);   // warm
+      if (st == MOG_OK) MOG_CUDA(ctx, cudaEventRecord(a, s));
+      for (int r = 0; r < reps && st == MOG_OK; ++r) st = mog_render_batch(ctx, batch, out, stream);
+      if (st != MOG_OK) break;
+      MOG_CUDA(ctx, cudaEventRecord(e, s));
+      MOG_CUDA(ctx, cudaEventSynchronize(e));
+      float t = 0.0f;
+      MOG_CUDA(ctx, cudaEventElapsedTime(&t, a, e));
+      if (t < best_ms) {
+        best_ms = t;
+        best_serial = serial != 0;
+      }
+    }
+    ctx->event_pool.push_back(a);
+    ctx->event_pool.push_back(e);
+    ctx->serial_buckets = best_serial;
+    if (st != MOG_OK) return st;
+  }
+  if (report) report[2 * NBUCKET * 3] = ctx->serial_buckets ? 1 : 0;
   ctx->timing = timing_was;
+  return MOG_OK;
+}
+
+mog_status mog_set_launch_shape(mog_ctx* ctx, int dir, int n, int ctas_per_sm, int chunk, int sched) {
+  if (!ctx) return MOG_ERR_ARG;
+  const int b = bucket_of(n);
+  if ((dir != 0 && dir != 1) || b < 0 || ctas_per_sm < 0 || ctas_per_sm > 64 || chunk < 1 || chunk > 1024 ||
+      sched < 0 || sched >= SCHEDULES || (dir == 1 && sched != 0))
+    return fail(ctx, MOG_ERR_ARG, "launch shape: dir 0/1, side 32..256, 0..64 CTAs per SM, chunk 1..1024, "
+                                  "schedule 0..%d (adjoint: 0)", SCHEDULES - 1);
+  LaunchShape& t = dir == 0 ? ctx->tune_fwd[b] : ctx->tune_bwd[b];
+  t.ctas_per_sm = ctas_per_sm;
+  t.chunk = chunk;
+  t.sched = sched;
   return MOG_OK;
 }
 
@@ -612,6 +744,10 @@ mog_status mog_graph_capture(mog_ctx* ctx, const mog_batch* batch, float* out, m
   mog_status st = check_batch(ctx, batch);
   if (st != MOG_OK) return st;
   MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  // the eager call below runs on the library's capture stream with the
+  // context's workspace: work of earlier calls on the caller's streams, which
+  // uses the same workspace, must be finished first
+  MOG_CUDA(ctx, cudaDeviceSynchronize());
   // one eager call sizes the scratch and configures the kernels, so that
   // nothing is allocated or configured while capturing
   if ((st = mog_render_batch(ctx, batch, out, ctx->capture)) != MOG_OK) return st;

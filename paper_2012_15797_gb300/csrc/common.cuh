@@ -155,19 +155,26 @@ __device__ __forceinline__ void dft_r(float2* v) {
 
 // ------------------------------------------------------------------------
 // Stockham autosort FFT of length N held in shared memory, one FFT per group
-// of N/8 threads, 8 complex values per thread.  Radix schedule: 32 = 8*4,
-// 64 = 8*8, 128 = 8*8*2, 256 = 8*8*4.  A pass of radix R with current
+// of N/8 threads, 8 complex values per thread.  Radix schedules (the first
+// pass is always radix 8 on the thread's 8 values): V = 0: 32 = 8*4,
+// 64 = 8*8, 128 = 8*8*2, 256 = 8*8*4; V = 1: 32 = 8*2*2, 64 = 8*4*2,
+// 128 = 8*4*4, 256 = 8*4*8 (the autotuner picks per patch side).  A pass of radix R with current
 // sub-length Ns: butterfly b reads x[b + m N/R] (m < R), multiplies by
 // w_{Ns R}^{m (b mod Ns)}, takes an R-point DFT and writes
 // x'[(b / Ns) Ns R + (b mod Ns) + m Ns].  Thread j owns butterflies
 // b = j + q N/8 (q < 8/R).
 // Buffer index swizzle i + i/8 spreads the stride-8 accesses over banks.
 // ------------------------------------------------------------------------
-template <int N> struct Radix;
+template <int N, int V = 0> struct Radix;
 template <> struct Radix<32> { static constexpr int P = 2; static constexpr int r[3] = {8, 4, 1}; };
 template <> struct Radix<64> { static constexpr int P = 2; static constexpr int r[3] = {8, 8, 1}; };
 template <> struct Radix<128> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 2}; };
 template <> struct Radix<256> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 4}; };
+template <> struct Radix<32, 1> { static constexpr int P = 3; static constexpr int r[3] = {8, 2, 2}; };
+template <> struct Radix<64, 1> { static constexpr int P = 3; static constexpr int r[3] = {8, 4, 2}; };
+template <> struct Radix<128, 1> { static constexpr int P = 3; static constexpr int r[3] = {8, 4, 4}; };
+template <> struct Radix<256, 1> { static constexpr int P = 3; static constexpr int r[3] = {8, 4, 8}; };
+constexpr int SCHEDULES = 2;
 
 // Work rows hold one length-N transform each.  N = 32, 64: index map
 // i + i/8 into rows padded to N + N/8 float2, which spreads the stride-8
@@ -282,12 +289,12 @@ __device__ __forceinline__ void first_pass_load(const float2* buf, int j, float2
 // Passes after the first of a length-N FFT held in work row `w` (sign S);
 // the result of the last pass is left in v, value q R + m at output index
 // stockham_out_index<N, R>(j, N / R, q, m) with R = LastPass<N>::R.
-template <int N, int S>
+template <int N, int S, int V = 0>
 __device__ __forceinline__ void fft_rest(float2* w, int j, const float2* tw1, const float2* tw2, float2* v) {
-  constexpr int R1 = Radix<N>::r[1];
+  constexpr int R1 = Radix<N, V>::r[1];
   stockham_load<N, R1, S>(w, j, tw1, v);
-  if constexpr (Radix<N>::P == 3) {
-    constexpr int R2 = Radix<N>::r[2];
+  if constexpr (Radix<N, V>::P == 3) {
+    constexpr int R2 = Radix<N, V>::r[2];
     __syncwarp();
     stockham_store<N, R1>(w, j, 8, v);
     __syncwarp();
@@ -295,9 +302,9 @@ __device__ __forceinline__ void fft_rest(float2* w, int j, const float2* tw1, co
   }
 }
 
-template <int N>
+template <int N, int V = 0>
 struct LastPass {
-  static constexpr int R = Radix<N>::r[Radix<N>::P - 1];
+  static constexpr int R = Radix<N, V>::r[Radix<N, V>::P - 1];
   static constexpr int NS = N / R;
 };
 

@@ -21,6 +21,13 @@ struct Workspace {
   float* lzw = nullptr;                  // 16 floats per planned galaxy (Lanczos weights)
   float* pcoef = nullptr;                // PCOEF floats per planned galaxy (eigen-PSF terms)
   float2* bwd256 = nullptr;              // per-CTA scratch of the 256 x 256 adjoint
+  // adjoint of the Lanczos variant: three upstream patches (3 x extent
+  // floats) and per galaxy the integer offsets and three gradient sets
+  float* lz_up = nullptr;
+  size_t lz_up_cap = 0;                  // floats per upstream patch set
+  float* lz_aux = nullptr;
+  int64_t lz_aux_cap = 0;                // galaxies
+  unsigned long long* lz_extent = nullptr;
   cudaStream_t side[NBUCKET] = {};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[NBUCKET] = {};
@@ -73,6 +80,7 @@ struct mog_ctx {
   int64_t acc_n[mog::NBUCKET] = {0, 0, 0, 0};
   // launch shapes per bucket (mog_autotune)
   mog::LaunchShape tune_fwd[mog::NBUCKET], tune_bwd[mog::NBUCKET];
+  bool serial_buckets = false;   // launch the size kernels one after the other instead of forked
   cudaStream_t capture = nullptr;
 };
 
@@ -88,6 +96,9 @@ mog_status cuda_fail(mog_ctx* ctx, cudaError_t e, const char* what);
   } while (0)
 
 mog_status check_batch(mog_ctx* ctx, const mog_batch* batch);
+// Sizes a workspace for batches of up to `count` galaxies, 256 x 256 scratch
+// included, so that later calls up to that size allocate (and free) nothing.
+mog_status workspace_reserve(mog_ctx* ctx, Workspace* ws, int64_t count);
 // Batched render / adjoint with an explicit workspace (grows it if needed).
 mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s,
                        bool lanczos = false, bool add = false);

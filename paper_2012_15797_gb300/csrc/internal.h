@@ -28,6 +28,7 @@ struct RenderParams {
   int accumulate = 0;           // 1: add the model to the patch instead of writing it
   int grad_n = 0;               // adjoint: 1 = also d/d(Sersic n), 7 gradients per galaxy
   float2* scratch256 = nullptr; // accumulate, N = 256: per-CTA transform intermediate (N/2 x N complex)
+  int sched = 0;                // radix schedule of the forward transforms (Radix<N, sched>), set per bucket
 };
 
 // Launch shape of one size bucket: CTAs per SM (clamped to what fits) and
@@ -36,6 +37,7 @@ struct RenderParams {
 struct LaunchShape {
   int ctas_per_sm = 0;   // 0 = as many as fit
   int chunk = 8;
+  int sched = 0;         // forward: radix schedule of the transforms (0 or 1)
 };
 
 struct PlanScratch {
@@ -65,6 +67,13 @@ size_t render_bwd256_scratch_bytes(int num_sms);
 cudaError_t launch_render_bwd256(const RenderParams& p, const float* grad_out, float* grad_params, float2* scratch,
                                  int num_sms, cudaStream_t s);
 
+// Adjoint of the Lanczos variant (lanczos_adj.cu).
+cudaError_t launch_patch_extent(const BatchView& b, int64_t count, unsigned long long* extent, cudaStream_t s);
+cudaError_t launch_lanczos_upstream(const BatchView& b, int64_t count, const float* g, float* g0, float* hx, float* hy,
+                                    float* xi, float* yi, cudaStream_t s);
+cudaError_t launch_lanczos_combine(int64_t count, const float* flux, const float* a0, const float* ax, const float* ay,
+                                   int ng, float* out, cudaStream_t s);
+
 // Allocation-free forward render (noalloc.cu): the scratch of one call lives
 // in a fixed device array; noalloc_scratch returns its address on `device`.
 cudaError_t noalloc_scratch(int device, unsigned char** out);
@@ -79,8 +88,11 @@ cudaError_t render_noalloc(const RenderParams& proto, int64_t count, uint32_t wa
 int kernel_occupancy(const void* fn, int threads, size_t smem);
 
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
-cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, cudaStream_t s);
-int render_fwd_max_ctas(int n);
+cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
+// Resident CTAs per SM of the plain forward kernel for side n and radix
+// schedule `sched` (what the autotuner searches up to).
+int render_fwd_max_ctas(int n, int sched);
+int render_fwd256_max_ctas(int sched);
 
 // Patch sides each direction supports (bit b: N = 32 << b).
 constexpr uint32_t FWD_BUCKETS = 0xF;   // 32, 64, 128, 256

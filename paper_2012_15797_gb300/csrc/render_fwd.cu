@@ -31,7 +31,7 @@ namespace mog {
 // shared memory (the PSF spectrum is read from L2 instead of staged, and the
 // column transforms use one work row per group), so that two CTAs share an
 // SM and one computes while the other waits at a CTA barrier.
-template <int N, int CPG = 1>
+template <int N, int CPG = 1, int V = 0>
 struct FwdCfg {
   static constexpr int H = N / 2 + 1;
   static constexpr int TPF = N / 8;          // threads per FFT
@@ -58,10 +58,10 @@ struct FwdCfg {
   __host__ __device__ static constexpr int row(int r) { return r * WS + SKEW * ((r >> 1) & 1); }
   static constexpr int W_ELEMS = NFFT * WS;                 // row transforms (pass B): one row per row pair
   static constexpr int WA_ELEMS = (CPG == 1 ? NFFT : GROUPS) * WS;   // column transforms (pass A)
-  static constexpr int R1 = Radix<N>::r[1];
-  static constexpr int R2 = Radix<N>::r[2];
+  static constexpr int R1 = Radix<N, V>::r[1];
+  static constexpr int R2 = Radix<N, V>::r[2];
   static constexpr int TW1 = twiddle_elems<N, R1>();
-  static constexpr int TW2 = Radix<N>::P == 3 ? twiddle_elems<N, (R2 > 1 ? R2 : 2)>() : 0;
+  static constexpr int TW2 = Radix<N, V>::P == 3 ? twiddle_elems<N, (R2 > 1 ? R2 : 2)>() : 0;
   static constexpr int MIN_BLOCKS = N == 32 ? 16 : N == 64 ? 4 : CPG;
   // N = 64: the row transforms reuse the column transforms' work rows (one
   // more CTA barrier per galaxy), which frees 18 KB of shared memory so that
@@ -172,10 +172,11 @@ __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, 
 // convolved in shared memory along x, then y, before it is added.
 // EIG: some PSF of the context is an eigen-PSF (the variant without it has
 // none of that code).
-template <int N, bool LZ, bool EIG, int CPG = 1>
-__global__ void __launch_bounds__(FwdCfg<N, CPG>::THREADS, FwdCfg<N, CPG>::MIN_BLOCKS)
+// V: the radix schedule of the transforms (Radix<N, V>).
+template <int N, bool LZ, bool EIG, int CPG = 1, int V = 0>
+__global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>::MIN_BLOCKS)
     render_fwd_kernel(RenderParams p) {
-  using C = FwdCfg<N, CPG>;
+  using C = FwdCfg<N, CPG, V>;
   static_assert(!(LZ && CPG > 1), "the Lanczos variant keeps one column per group");
   constexpr int TPF = C::TPF, LS = C::LS;
   constexpr int B = bucket_of(N);
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG>::THREADS, FwdCfg<N, CPG>::MIN_B
   const int tid = threadIdx.x;
   const int f = tid / TPF, j = tid % TPF;
   fill_twiddles<N, C::R1>(tw1, 8, tid, C::THREADS);
-  if constexpr (Radix<N>::P == 3) fill_twiddles<N, C::R2>(tw2, N / C::R2, tid, C::THREADS);
+  if constexpr (Radix<N, V>::P == 3) fill_twiddles<N, C::R2>(tw2, N / C::R2, tid, C::THREADS);
   const int count = p.bucket_count[B];
   const int first = p.bucket_start[B];   // planned position of this bucket's first galaxy
   const unsigned char* records = p.records + (size_t)first * RECORD_BYTES;
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG>::THREADS, FwdCfg<N, CPG>::MIN_B
       if (cc > 0) __syncwarp();   // the group's loads of its previous column are done
       first_pass_store<N>(wa, j, v);
       __syncwarp();
-      fft_rest<N, +1>(wa, j, tw1, tw2, v);
+      fft_rest<N, +1, V>(wa, j, tw1, tw2, v);
       if constexpr (C::ALIAS_W) __syncthreads();   // every column's last loads are done
       {
         // The last pass leaves rows n = j + q N/8 + m N/R of column f in this
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG>::THREADS, FwdCfg<N, CPG>::MIN_B
         // here without an exchange: Z_p[f] = A + iB and Z_p[N-f] = conj(A) +
         // i conj(B) feed the row transform of pair p (any two real rows can
         // share one complex transform).
-        constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
+        constexpr int R = LastPass<N, V>::R, NS = LastPass<N, V>::NS;
 #pragma unroll
         for (int q = 0; q < 8 / R; ++q)
 #pragma unroll
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG>::THREADS, FwdCfg<N, CPG>::MIN_B
       __syncwarp();
       first_pass_store<N>(wb, j, v);
       __syncwarp();
-      fft_rest<N, +1>(wb, j, tw1, tw2, v);
+      fft_rest<N, +1, V>(wb, j, tw1, tw2, v);
       __syncwarp();
       float* orow = reinterpret_cast<float*>(wb);
       {
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG>::THREADS, FwdCfg<N, CPG>::MIN_B
         // Pixel x is kept at x ^ 4 [bit 5 of x]: the 16-byte pieces 8..15 of a
         // row swap in pairs, so the 8 lanes that read pieces 2j (then 2j+1)
         // below touch 8 different bank groups.
-        constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
+        constexpr int R = LastPass<N, V>::R, NS = LastPass<N, V>::NS;
 #pragma unroll
         for (int q = 0; q < 8 / R; ++q)
 #pragma unroll
@@ -523,31 +524,34 @@ constexpr int fwd_cpg() { return (N == 128 && !LZ) ? 2 : 1; }
 
 static_assert(2 * (FwdCfg<128, 2>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 CTAs share an SM's shared memory");
 
-template <int N, bool LZ = false, bool EIG = false>
+template <int N, bool LZ = false, bool EIG = false, int V = 0>
 static int fwd_occupancy() {
   constexpr int CPG = fwd_cpg<N, LZ>();
-  using C = FwdCfg<N, CPG>;
-  return kernel_occupancy(reinterpret_cast<const void*>(render_fwd_kernel<N, LZ, EIG, CPG>), C::THREADS, C::SMEM);
+  using C = FwdCfg<N, CPG, V>;
+  return kernel_occupancy(reinterpret_cast<const void*>(render_fwd_kernel<N, LZ, EIG, CPG, V>), C::THREADS, C::SMEM);
 }
 
-template <int N, bool LZ, bool EIG>
+template <int N, bool LZ, bool EIG, int V>
 static cudaError_t launch_fwd_mode(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
   constexpr int CPG = fwd_cpg<N, LZ>();
-  using C = FwdCfg<N, CPG>;
-  const int occ = fwd_occupancy<N, LZ, EIG>();
+  using C = FwdCfg<N, CPG, V>;
+  const int occ = fwd_occupancy<N, LZ, EIG, V>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_fwd_kernel<N, LZ, EIG, CPG><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
+  render_fwd_kernel<N, LZ, EIG, CPG, V><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
+// The second radix schedule is compiled for the plain render (phase shift,
+// constant PSFs) only; the other variants keep the first.
 template <int N>
 static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
   if (p.eigen)
-    return p.lanczos ? launch_fwd_mode<N, true, true>(p, num_sms, ctas_per_sm, s)
-                     : launch_fwd_mode<N, false, true>(p, num_sms, ctas_per_sm, s);
-  return p.lanczos ? launch_fwd_mode<N, true, false>(p, num_sms, ctas_per_sm, s)
-                   : launch_fwd_mode<N, false, false>(p, num_sms, ctas_per_sm, s);
+    return p.lanczos ? launch_fwd_mode<N, true, true, 0>(p, num_sms, ctas_per_sm, s)
+                     : launch_fwd_mode<N, false, true, 0>(p, num_sms, ctas_per_sm, s);
+  if (p.lanczos) return launch_fwd_mode<N, true, false, 0>(p, num_sms, ctas_per_sm, s);
+  return p.sched == 1 ? launch_fwd_mode<N, false, false, 1>(p, num_sms, ctas_per_sm, s)
+                      : launch_fwd_mode<N, false, false, 0>(p, num_sms, ctas_per_sm, s);
 }
 
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
@@ -555,17 +559,17 @@ cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int cta
     case 32: return launch_fwd<32>(p, num_sms, ctas_per_sm, s);
     case 64: return launch_fwd<64>(p, num_sms, ctas_per_sm, s);
     case 128: return launch_fwd<128>(p, num_sms, ctas_per_sm, s);
-    case 256: return launch_render_fwd256(p, num_sms, s);
+    case 256: return launch_render_fwd256(p, num_sms, ctas_per_sm, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-int render_fwd_max_ctas(int n) {
+int render_fwd_max_ctas(int n, int sched) {
   switch (n) {
-    case 32: return fwd_occupancy<32>();
-    case 64: return fwd_occupancy<64>();
-    case 128: return fwd_occupancy<128>();
-    case 256: return 1;
+    case 32: return sched == 1 ? fwd_occupancy<32, false, false, 1>() : fwd_occupancy<32>();
+    case 64: return sched == 1 ? fwd_occupancy<64, false, false, 1>() : fwd_occupancy<64>();
+    case 128: return sched == 1 ? fwd_occupancy<128, false, false, 1>() : fwd_occupancy<128>();
+    case 256: return render_fwd256_max_ctas(sched);
     default: return 0;
   }
 }

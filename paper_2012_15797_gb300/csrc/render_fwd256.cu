@@ -7,11 +7,12 @@
 // occupies exactly the bytes of those two output rows (elements below N/2 in
 // row p, the rest in row p + N/2), which only that row transform overwrites.
 //
-// 1024 threads, one warp per length-256 transform:
-//   columns   4 rounds of 32 column IFFTs (round 0, warp 0: the packed nu = 0
+// 512 threads, one warp per length-256 transform, two CTAs per SM (while one
+// waits at a CTA barrier the other computes):
+//   columns   8 rounds of 16 column IFFTs (round 0, warp 0: the packed nu = 0
 //             and nu = 1/2 columns); each round's row-pair values are staged in
-//             shared memory and written as coalesced 256-byte row segments
-//   rows      4 rounds of 32 row-pair IFFTs, each warp independent: load its
+//             shared memory and written as coalesced 128-byte row segments
+//   rows      8 rounds of 16 row-pair IFFTs, each warp independent: load its
 //             row pair's input, transform, add the real-space terms, store
 //             the two pixel rows over the input
 // The PSF spectrum (272 KB) is read from global memory (L2-resident).
@@ -19,7 +20,7 @@
 // Lanczos variant (LZ): the Fourier part is shifted through the phase tables
 // (the Lanczos transfer function H(nu) H(omega)); a galaxy with real-space
 // terms then gets its real-space part convolved and added in two strips of
-// 128 rows: the 134 rows each strip needs are evaluated and convolved along x
+// 64 rows: the 70 rows each strip needs are evaluated and convolved along x
 // (one warp per row, neighbours by shuffle) into shared memory that the
 // transforms no longer use, then convolved along y and added to the patch.
 #include "common.cuh"
@@ -35,16 +36,19 @@ constexpr int N = 256;
 __device__ __forceinline__ int zpos(int p, int c) { return (c < N / 2 ? p : p + N / 2) * (N / 2) + (c & (N / 2 - 1)); }
 constexpr int H = N / 2 + 1;
 constexpr int TPF = N / 8;       // 32: one warp per transform
-constexpr int THREADS = 1024;
+constexpr int THREADS = 512;
 constexpr int WARPS = THREADS / 32;
-constexpr int ROUNDS = (N / 2) / WARPS;   // 4
+constexpr int ROUNDS = (N / 2) / WARPS;   // 8
+constexpr int CTAS_PER_SM = 2;
 constexpr int LS = psf_lstride(N);
 constexpr int PSF_ELEMS = psf_spec_elems(N);
 // transform rows keep N/8 float2 beyond wstride<N>(): the Lanczos strips
 // reuse that space
 constexpr int WS = wstride<N>() + N / 8;
-constexpr int R1 = Radix<N>::r[1], R2 = Radix<N>::r[2];
-constexpr int TW1 = twiddle_elems<N, R1>(), TW2 = twiddle_elems<N, R2>();
+// twiddle tables of passes 2 and 3, room for either radix schedule
+template <int V>
+constexpr int tw_elems() { return twiddle_elems<N, Radix<N, V>::r[1]>() + twiddle_elems<N, Radix<N, V>::r[2]>(); }
+constexpr int TWS = tw_elems<0>() > tw_elems<1>() ? tw_elems<0>() : tw_elems<1>();
 constexpr int B = bucket_of(N);
 
 // Staging rows hold the 32 columns of a round for one row pair, padded to 33
@@ -55,14 +59,15 @@ constexpr size_t off_w = 0;                                              // WARP
 constexpr size_t off_sa = off_w + sizeof(float2) * WARPS * WS;            // staging [p][SSTR]
 constexpr size_t off_sb = off_sa + sizeof(float2) * ((N / 2) * SSTR + 8); // mirrored columns
 constexpr size_t off_tw = off_sb + sizeof(float2) * (N / 2) * SSTR;
-constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
+constexpr size_t off_px = off_tw + sizeof(float2) * TWS;
 constexpr size_t off_py = off_px + sizeof(float2) * H;
 constexpr size_t off_nyq = off_py + sizeof(float2) * N;
 constexpr size_t off_rec = (off_nyq + sizeof(float2) * N + 15) & ~size_t(15);
 constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);
 constexpr size_t off_bar = (off_rt + sizeof(RealTerms) + 15) & ~size_t(15);
 constexpr size_t SMEM = off_bar + 2 * sizeof(uint64_t);
-constexpr int STRIP = 128;                                                // output rows per strip
+static_assert(CTAS_PER_SM * (SMEM + 1024) <= 228 * 1024, "two CTAs share an SM's shared memory");
+constexpr int STRIP = 64;                                                 // output rows per strip
 static_assert(sizeof(float) * (STRIP + 6) * N <= off_tw, "Lanczos strip must fit below the twiddles");
 
 // LZ, galaxy with real-space terms: patch += Lz(R), R the real-space terms at
@@ -129,8 +134,12 @@ __device__ __forceinline__ void lanczos_real_256(const RealTerms& rt, int nr, co
   }
 }
 
-template <bool LZ, bool EIG>
-__global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams p) {
+// V: the radix schedule of the transforms (Radix<256, V>).
+template <bool LZ, bool EIG, int V = 0>
+__global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(RenderParams p) {
+  constexpr int R1 = Radix<N, V>::r[1], R2 = Radix<N, V>::r[2];
+  constexpr int TW1 = twiddle_elems<N, R1>();
+  static_assert(Radix<N, V>::P == 3, "three passes");
   constexpr float INV_N = 1.0f / N;
   constexpr float NEGLIGIBLE_LOG2 = -40.0f;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -421,17 +430,34 @@ __global__ void __launch_bounds__(THREADS, 1) render_fwd256_kernel(RenderParams 
 
 }  // namespace
 
-template <bool LZ, bool EIG>
-static cudaError_t launch_fwd256(const RenderParams& p, int num_sms, cudaStream_t s) {
-  if (kernel_occupancy(reinterpret_cast<const void*>(render_fwd256_kernel<LZ, EIG>), THREADS, SMEM) < 0)
-    return cudaErrorInvalidConfiguration;
-  render_fwd256_kernel<LZ, EIG><<<num_sms, THREADS, SMEM, s>>>(p);
+template <bool LZ, bool EIG, int V = 0>
+static int fwd256_occupancy() {
+  const int occ = kernel_occupancy(reinterpret_cast<const void*>(render_fwd256_kernel<LZ, EIG, V>), THREADS, SMEM);
+  return occ < 0 ? occ : (occ < CTAS_PER_SM ? occ : CTAS_PER_SM);
+}
+
+template <bool LZ, bool EIG, int V = 0>
+static cudaError_t launch_fwd256(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  const int occ = fwd256_occupancy<LZ, EIG, V>();
+  if (occ < 0) return cudaErrorInvalidConfiguration;
+  // the accumulate mode's scratch holds one slice per CTA, CTAS_PER_SM per SM
+  const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
+  render_fwd256_kernel<LZ, EIG, V><<<num_sms * ctas, THREADS, SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, cudaStream_t s) {
-  if (p.eigen) return p.lanczos ? launch_fwd256<true, true>(p, num_sms, s) : launch_fwd256<false, true>(p, num_sms, s);
-  return p.lanczos ? launch_fwd256<true, false>(p, num_sms, s) : launch_fwd256<false, false>(p, num_sms, s);
+int render_fwd256_max_ctas(int sched) {
+  return sched == 1 ? fwd256_occupancy<false, false, 1>() : fwd256_occupancy<false, false, 0>();
+}
+
+// The second radix schedule is compiled for the plain render only.
+cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  if (p.eigen)
+    return p.lanczos ? launch_fwd256<true, true>(p, num_sms, ctas_per_sm, s)
+                     : launch_fwd256<false, true>(p, num_sms, ctas_per_sm, s);
+  if (p.lanczos) return launch_fwd256<true, false>(p, num_sms, ctas_per_sm, s);
+  return p.sched == 1 ? launch_fwd256<false, false, 1>(p, num_sms, ctas_per_sm, s)
+                      : launch_fwd256<false, false, 0>(p, num_sms, ctas_per_sm, s);
 }
 
 }  // namespace mog

@@ -252,8 +252,11 @@ void lane_free_staging(mog_server::Lane& L) {
   L.cap = 0;
 }
 
+// Grows geometrically: a cudaFreeHost waits for the whole device, so
+// reallocating staging while other lanes run stalls them all.
 bool lane_reserve(mog_server::Lane& L, int64_t g) {
   if (g <= L.cap) return true;
+  if (g < 2 * L.cap) g = 2 * L.cap;
   lane_free_staging(L);
   const size_t bytes = sizeof(float) * 6 * g + sizeof(int32_t) * 2 * g + sizeof(int64_t) * g + sizeof(float) * 7 * g + 64;
   if (cudaHostAlloc(&L.st.base, bytes, cudaHostAllocDefault) != cudaSuccess) return false;
@@ -512,6 +515,18 @@ mog_status mog_server_create(mog_ctx* ctx, const mog_server_config* cfg, mog_ser
     if (e != cudaSuccess) {
       mog_server_destroy(S);
       return cuda_fail(ctx, e, "server lane");
+    }
+    // every lane's staging and workspace sized for the largest micro-batch
+    // now, so that no allocation (and no device-wide free) happens while
+    // requests are served
+    if (cfg->max_batch_galaxies > 0) {
+      mog_status st = workspace_reserve(ctx, &L.ws, cfg->max_batch_galaxies);
+      if (st == MOG_OK && !lane_reserve(L, cfg->max_batch_galaxies)) st = MOG_ERR_NOMEM;
+      if (st != MOG_OK) {
+        mog_server_destroy(S);
+        return fail(ctx, st, "server lane: cannot reserve staging for %lld galaxies",
+                    (long long)cfg->max_batch_galaxies);
+      }
     }
   }
   S->sched = std::thread(scheduler, S);

@@ -153,18 +153,22 @@ class Renderer:
         out = self.render(disk, out, stream, shift)
         return self.render(bulge, out, stream, shift, add=True)
 
-    def render_backward(self, batch, grad_out, grad_params=None, stream=None, sersic=False):
+    def render_backward(self, batch, grad_out, grad_params=None, stream=None, sersic=False, shift="phase"):
         """Gradients (count, 6) of L w.r.t. (flux, x, y, log_re, e1, e2)
         given grad_out = dL/d(packed output); with ``sersic`` (count, 7), the
-        last column d L / d sersic_n."""
+        last column d L / d sersic_n.  ``shift``: the model differentiated,
+        "phase" (Fourier shift phase) or "lanczos" (the Lanczos-3 variant)."""
+        if shift not in ("phase", "lanczos"):
+            raise ValueError(f"unknown shift {shift!r}")
         k = 7 if sersic else 6
         if grad_params is None:
             grad_params = torch.empty(batch.count, k, dtype=torch.float32, device=self.device)
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
-        if sersic:
+        flags = (capi.MOG_GRAD_SERSIC if sersic else 0) | (capi.MOG_GRAD_LANCZOS if shift == "lanczos" else 0)
+        if flags:
             capi.mog_render_backward_ex(self.ctx, b, grad_out.data_ptr(), grad_params.data_ptr(), s.cuda_stream,
-                                        capi.MOG_GRAD_SERSIC)
+                                        flags)
         else:
             capi.mog_render_backward(self.ctx, b, grad_out.data_ptr(), grad_params.data_ptr(), s.cuda_stream)
         return grad_params

@@ -21,6 +21,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2012_15797_gb300", "csrc")
 SIZES = (32, 64, 128, 256)
 LAST_RADIX = {32: 4, 64: 8, 128: 2, 256: 4}
+# radix schedules per side (Radix<N, V> in common.cuh); the first pass is radix 8
+SCHEDULE = {0: {32: (8, 4), 64: (8, 8), 128: (8, 8, 2), 256: (8, 8, 4)},
+            1: {32: (8, 2, 2), 64: (8, 4, 2), 128: (8, 4, 4), 256: (8, 4, 8)}}
 
 
 def swz_xor(n):
@@ -64,6 +67,13 @@ def test_mirrors_match_the_source():
     assert "static constexpr int WS = wstride<N>() + (N == 128 ? 2 : N == 64 ? 16 : 0);" in fwd
     assert "static constexpr int SKEW = N == 64 ? 4 : 0;" in fwd
     assert re.search(r"row\(int r\) \{ return r \* WS \+ SKEW \* \(\(r >> 1\) & 1\); \}", fwd)
+    for v, table in SCHEDULE.items():
+        for n, r in table.items():
+            rr = list(r) + [1] * (3 - len(r))
+            spec = f"Radix<{n}>" if v == 0 else f"Radix<{n}, {v}>"
+            line = (f"template <> struct {spec} {{ static constexpr int P = {len(r)}; "
+                    f"static constexpr int r[3] = {{{rr[0]}, {rr[1]}, {rr[2]}}}; }};")
+            assert line in common, line
     bwd = open(os.path.join(CSRC, "render_bwd.cu")).read()
     assert "static constexpr int WSA = N == 64 ? 88 : N == 128 ? 129 : WS;" in bwd
     assert "static constexpr int SKEWA = N == 64 ? 4 : 0;" in bwd
@@ -88,11 +98,27 @@ def test_forward_work_rows_do_not_overlap(n):
         assert all(r % 2 == 0 for r in rows)
 
 
+def test_schedules_factor_the_sides():
+    for table in SCHEDULE.values():
+        for n, r in table.items():
+            assert r[0] == 8 and all(x in (2, 4, 8) for x in r)
+            prod = 1
+            for x in r:
+                prod *= x
+            assert prod == n
+            # passes after the first read with a stride N / R that the
+            # i + i/8 map needs to be a multiple of 8
+            assert all((n // x) % 8 == 0 for x in r[1:])
+
+
+@pytest.mark.parametrize("v", [0, 1])
 @pytest.mark.parametrize("n", SIZES)
-def test_row_pairs_meet_in_one_thread(n):
+def test_row_pairs_meet_in_one_thread(n, v):
     """The last column pass leaves outputs m and m + R/2 of a thread in rows p
-    and p + N/2; over all threads those p cover [0, N/2) once."""
-    r = LAST_RADIX[n]
+    and p + N/2; over all threads those p cover [0, N/2) once (both radix
+    schedules)."""
+    r = SCHEDULE[v][n][-1]
+    assert v != 0 or r == LAST_RADIX[n]
     ns = n // r
     seen = []
     for j in range(n // 8):

@@ -154,7 +154,7 @@ def config3_problem(g=50_000, seed=3):
 
 
 def serving_workload(n_fits=1000, per_fit=512, seed=4, rate_per_ms=20_000.0, duration_ms=1000.0,
-                     max_size=512, n_psf=64, max_side=256):
+                     max_size=512, n_psf=64, max_side=256, request_seed=None):
     """Serving workload: ``n_fits`` concurrent fits of ``per_fit`` galaxies
     each (drawn as in ``config2_galaxies``, patch sides <= max_side), and
     requests of 1..``max_size`` galaxies (uniform) arriving as a Poisson
@@ -162,8 +162,10 @@ def serving_workload(n_fits=1000, per_fit=512, seed=4, rate_per_ms=20_000.0, dur
     A request names a fit, a contiguous range of its galaxies and their
     current parameters: the fit's values perturbed as in
     ``config3_problem``.  Returns ``(fits, arrival_ms, requests)`` with
-    requests a list of (fit, first, params (count, 6) float32)."""
-    rng = np.random.default_rng(seed)
+    requests a list of (fit, first, params (count, 6) float32).
+    ``request_seed`` (default ``seed``) seeds the request stream alone, so
+    that streams of other rates share the same fits."""
+    rng = np.random.default_rng(seed if request_seed is None else request_seed)
     pool = config2_galaxies(int(n_fits * per_fit * 1.6) + 64, seed + 1, n_psf=n_psf)
     keep = np.nonzero(pool.size <= max_side)[0][:n_fits * per_fit]
     pool = pool.subset(keep)
