@@ -27,12 +27,20 @@
 
 namespace mog {
 
-template <int N>
+// CPG: row pairs (and columns) each group of TPF threads transforms, one
+// after the other.  CPG = 2 (N = 128) halves the CTA to 512 threads and its
+// shared memory (the gradient rows are read from global memory, L2-resident,
+// instead of being staged, and the row transforms use one work row per
+// group), so two CTAs share an SM and one computes while the other waits at a
+// CTA barrier.
+template <int N, int CPG = 1>
 struct BwdCfg {
   static constexpr int H = N / 2 + 1;
   static constexpr int TPF = N / 8;
   static constexpr int NFFT = N / 2;
-  static constexpr int THREADS = NFFT * TPF;
+  static constexpr int GROUPS = NFFT / CPG;
+  static constexpr int THREADS = GROUPS * TPF;
+  static constexpr bool G_SMEM = CPG == 1;   // gradient patch staged in shared memory
   static constexpr int WARPS = THREADS / 32;
   static constexpr int LS = psf_lstride(N);
   static constexpr int PSF_ELEMS = psf_spec_elems(N);
@@ -42,7 +50,7 @@ struct BwdCfg {
   // of both patterns: N = 64 shifts rows 2-3 of every 4 by 4 float2 in an
   // 88-float2 stride, N = 128 uses an odd stride.
   static constexpr int WS = wstride<N>();
-  static constexpr int W_ELEMS = NFFT * WS;
+  static constexpr int W_ELEMS = (CPG == 1 ? NFFT : GROUPS) * WS;
   static constexpr int WSA = N == 64 ? 88 : N == 128 ? 129 : WS;
   static constexpr int SKEWA = N == 64 ? 4 : 0;
   static_assert(SKEWA <= WSA - WS, "shifted rows must not overlap");
@@ -62,17 +70,17 @@ struct BwdCfg {
   // both would take the shared memory that the extra resident CTAs need, and
   // more resident warps hide more latency (measured: 32 x 32 1.06 -> 1.02 ms,
   // 64 x 64 2.68 -> 2.11 ms per 100k).
-  static constexpr int MIN_BLOCKS = N == 32 ? 10 : N == 64 ? 4 : 1;
+  static constexpr int MIN_BLOCKS = N == 32 ? 10 : N == 64 ? 4 : CPG;
   // N = 64: the gradient patch and the row transforms' work rows share one
   // region (both 18 KB): the real-space pass and the row transforms' first
   // loads read the patch, then a CTA barrier, then the work rows are written
-  static constexpr bool ALIAS_G = N == 64;
+  static constexpr bool ALIAS_G = N == 64 && CPG == 1;
   static_assert(!ALIAS_G || sizeof(float) * N * GS <= sizeof(float2) * NFFT * WS, "patch must fit the work rows");
 
   static constexpr size_t off_wa = 0;
   static constexpr size_t off_wb = off_wa + sizeof(float2) * WA_ELEMS;
   static constexpr size_t off_g = ALIAS_G ? off_wb : (off_wb + sizeof(float2) * W_ELEMS + 15) & ~size_t(15);
-  static constexpr size_t off_tw = ALIAS_G ? off_wb + sizeof(float2) * W_ELEMS : off_g + sizeof(float) * N * GS;
+  static constexpr size_t off_tw = (ALIAS_G || !G_SMEM) ? off_wb + sizeof(float2) * W_ELEMS : off_g + sizeof(float) * N * GS;
   static constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
   static constexpr size_t off_py = off_px + sizeof(float2) * H;
   static constexpr size_t off_nb = off_py + sizeof(float2) * N;       // nu = 1/2 column: P phase
@@ -88,10 +96,10 @@ struct BwdCfg {
 // WN: also d L / d(Sersic n), a seventh gradient per galaxy.  EIG: some PSF
 // of the context is an eigen-PSF (its spectrum at the galaxy's position is
 // combined from the component spectra bin by bin where a bin is read).
-template <int N, bool WN, bool EIG>
-__global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
+template <int N, bool WN, bool EIG, int CPG = 1>
+__global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_BLOCKS)
     render_bwd_kernel(RenderParams p, const float* __restrict__ grad_out, float* __restrict__ grad_params) {
-  using C = BwdCfg<N>;
+  using C = BwdCfg<N, CPG>;
   constexpr int TPF = C::TPF, WS = C::WS, LS = C::LS;
   constexpr int B = bucket_of(N);
   constexpr float INV_N = 1.0f / N;
@@ -148,8 +156,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
   }
   int cur_psf = -1;
   uint32_t rec_parity = 0, g_parity = 0;
-  float2* wa = WA + C::rowA(f);
-  float2* wb = WB + f * WS;
+  float2* wb = WB + f * WS;   // this group's row transforms
 
   for (int buf = 0;; buf ^= 1) {
     __syncthreads();  // S1
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
     rec_parity ^= 1u << buf;
     const AdjRecord& r = rec[buf];
     const bool go = rec_landed && r.ok;
-    if (go && warp == 0) {   // the gradient patch: one bulk copy per padded row, or one of the dense patch
+    if (C::G_SMEM && go && warp == 0) {   // the gradient patch: one bulk copy per padded row, or one of the dense patch
       if constexpr (C::GS == N) {
         if (lane == 0) bulk_load(gbuf, grad_out + r.off, sizeof(float) * N * N, &bar[2]);
       } else {
@@ -244,8 +251,11 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
         }
       }
     }
-    const bool g_landed = mbar_wait(&bar[2], g_parity);
-    g_parity ^= 1u;
+    bool g_landed = true;
+    if constexpr (C::G_SMEM) {
+      g_landed = mbar_wait(&bar[2], g_parity);
+      g_parity ^= 1u;
+    }
     if (__syncthreads_or(!g_landed)) {   // S2
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
       return;
@@ -253,16 +263,22 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
 
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float2 v[8];
+    // the gradient patch: staged in shared memory, or the caller's (L2)
+    const float* gsrc = C::G_SMEM ? gbuf : grad_out + r.off;
+    constexpr int GSTR = C::G_SMEM ? C::GS : N;
     if constexpr (C::ALIAS_G)   // the patch is read before the work rows overwrite it
-      adj_real_space<N, WN>(gbuf, C::GS, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
+      adj_real_space<N, WN>(gsrc, GSTR, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
                             r.s22);
-    // ---- forward FFT of row pairs (f, f + N/2) packed as g[f] + i g[f + N/2] ----
-    {
-      const float* ga = gbuf + f * C::GS;
-      const float* gb = gbuf + (f + N / 2) * C::GS;
+    // ---- forward FFT of row pairs (prow, prow + N/2) packed as g[prow] + i g[prow + N/2] ----
+#pragma unroll 1
+    for (int rr = 0; rr < CPG; ++rr) {
+      const int prow = f + rr * C::GROUPS;
+      const float* ga = gsrc + prow * GSTR;
+      const float* gb = gsrc + (prow + N / 2) * GSTR;
 #pragma unroll
       for (int m = 0; m < 8; ++m) v[m] = make_float2(ga[j + m * TPF], gb[j + m * TPF]);
       if constexpr (C::ALIAS_G) __syncthreads();   // every row of the patch is in registers
+      if (rr > 0) __syncwarp();   // the group's reads of its work row for the previous pair are done
       dft8<-1>(v);
 #pragma unroll
       for (int m = 0; m < 8; ++m) wb[swz<N>(8 * j + m)] = v[m];
@@ -281,101 +297,107 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
         if (k == 0) {
           // rows' nu = 0 and nu = 1/2 values are real: packed as re + i im
           const float2 zh = wb[swz<N>(N / 2)];
-          WA[swz<N>(f)] = make_float2(zk.x, zh.x);
-          WA[swz<N>(f + N / 2)] = make_float2(zk.y, zh.y);
+          WA[swz<N>(prow)] = make_float2(zk.x, zh.x);
+          WA[swz<N>(prow + N / 2)] = make_float2(zk.y, zh.y);
         } else if (k < N / 2) {
-          WA[C::rowA(k) + swz<N>(f)] = a;
-          WA[C::rowA(k) + swz<N>(f + N / 2)] = b;
+          WA[C::rowA(k) + swz<N>(prow)] = a;
+          WA[C::rowA(k) + swz<N>(prow + N / 2)] = b;
         }
       }
     }
 
     // ---- real-space terms: analytic derivatives, pixel by pixel ----
     if constexpr (!C::ALIAS_G)
-      adj_real_space<N, WN>(gbuf, C::GS, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
+      adj_real_space<N, WN>(gsrc, GSTR, at, real_terms_padded(r.nrc * s_kpsf), tid, C::THREADS, acc, r.s11, r.s12,
                             r.s22);
     __syncthreads();  // S3: every column input written
 
-    // ---- forward FFT of every column along y ----
+#pragma unroll 1
+    for (int cc = 0; cc < CPG; ++cc) {
+      const int col = f + cc * C::GROUPS;   // column nu = col / N (column 0: nu = 0 and 1/2 packed)
+      float2* wa = WA + C::rowA(col);
+      // ---- forward FFT of every column along y ----
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = wa[swz<N>(j + m * TPF)];
-    dft8<-1>(v);
-    __syncwarp();
+      for (int m = 0; m < 8; ++m) v[m] = wa[swz<N>(j + m * TPF)];
+      dft8<-1>(v);
+      __syncwarp();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) wa[swz<N>(8 * j + m)] = v[m];
-    __syncwarp();
-    fft_rest<N, -1>(wa, j, tw1, tw2, v);
+      for (int m = 0; m < 8; ++m) wa[swz<N>(8 * j + m)] = v[m];
+      __syncwarp();
+      fft_rest<N, -1>(wa, j, tw1, tw2, v);
 
-    // ---- contraction with the mixture's derivatives ----
-    {
-      constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
-      const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
-      const int nf = r.nf;
-      // every lane of the warp reaches both __syncwarp calls; only the
-      // packed group's lanes store
-      __syncwarp();
-      if (f == 0) stockham_store<N, R>(wa, j, NS, v);   // packed U[l], natural order
-      __syncwarp();
-      const float nu = f * INV_N;
-      const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
-      const float ck = f == 0 ? 1.0f : 2.0f;
-      const float2 pxf = px[f];
-      // mixture sums at the thread's bins b = q R + m, components outer and
-      // bins (2k, 2k+1) in packed f32x2, BH bins per sweep over the
-      // components: N = 64 takes two sweeps of 4 (its register budget at
-      // four CTAs per SM), N = 128 four sweeps of 2 (64 registers for 1024
-      // threads: half the spills of two sweeps, 4.02 -> 3.95 ms for the
-      // 32.8k 128 x 128 galaxies of the mixed workload).  No warp-level skip
-      // of negligible components: the per-component vote cost more than the
-      // work it saved (measured).
-      constexpr int BH = N >= 128 ? 2 : N >= 64 ? 4 : 8;
+      // ---- contraction with the mixture's derivatives ----
+      {
+        constexpr int R = LastPass<N>::R, NS = LastPass<N>::NS;
+        const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
+        const int nf = r.nf;
+        // every lane of the warp reaches both __syncwarp calls; only the
+        // packed group's lanes store
+        __syncwarp();
+        if (col == 0) stockham_store<N, R>(wa, j, NS, v);   // packed U[l], natural order
+        __syncwarp();
+        const float nu = col * INV_N;
+        const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
+        const float ck = col == 0 ? 1.0f : 2.0f;
+        const float2 pxf = px[col];
+        // mixture sums at the thread's bins b = q R + m, components outer and
+        // bins (2k, 2k+1) in packed f32x2, BH bins per sweep over the
+        // components: N = 64 takes two sweeps of 4 (its register budget at
+        // four CTAs per SM), N = 128 four sweeps of 2 (64 registers for 1024
+        // threads: half the spills of two sweeps, 4.02 -> 3.95 ms for the
+        // 32.8k 128 x 128 galaxies of the mixed workload).  No warp-level skip
+        // of negligible components: the per-component vote cost more than the
+        // work it saved (measured).
+        constexpr int BH = N >= 128 ? 2 : N >= 64 ? 4 : 8;
 #pragma unroll
-      for (int b0 = 0; b0 < 8; b0 += BH) {
-        float2 qp[BH / 2], S[BH / 2], SQ[BH / 2], SN[BH / 2], SD[BH / 2];
+        for (int b0 = 0; b0 < 8; b0 += BH) {
+          float2 qp[BH / 2], S[BH / 2], SQ[BH / 2], SN[BH / 2], SD[BH / 2];
 #pragma unroll
-        for (int k = 0; k < BH / 2; ++k) {
-          float qq[2];
+          for (int k = 0; k < BH / 2; ++k) {
+            float qq[2];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int b = b0 + 2 * k + h;
-            const int l = stockham_out_index<N, R>(j, NS, b / R, b % R);
+            for (int h = 0; h < 2; ++h) {
+              const int b = b0 + 2 * k + h;
+              const int l = stockham_out_index<N, R>(j, NS, b / R, b % R);
+              const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+              qq[h] = fmaf(om, fmaf(s22, om, a1), a0);
+            }
+            qp[k] = make_float2(qq[0], qq[1]);
+          }
+          adj_mixture_sums<BH / 2, WN>(s_fa, s_fc, s_fd, nf, qp, S, SQ, SN, SD);
+#pragma unroll
+          for (int bb = 0; bb < BH; ++bb) {
+            const int b = b0 + bb, q = b / R, m = b % R;
+            const int l = stockham_out_index<N, R>(j, NS, q, m);
             const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
-            qq[h] = fmaf(om, fmaf(s22, om, a1), a0);
-          }
-          qp[k] = make_float2(qq[0], qq[1]);
-        }
-        adj_mixture_sums<BH / 2, WN>(s_fa, s_fc, s_fd, nf, qp, S, SQ, SN, SD);
-#pragma unroll
-        for (int bb = 0; bb < BH; ++bb) {
-          const int b = b0 + bb, q = b / R, m = b % R;
-          const int l = stockham_out_index<N, R>(j, NS, q, m);
-          const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
-          float2 gk = v[b];
-          float2 gn = make_float2(0.f, 0.f);
-          if (f == 0) {
-            const float2 u = wa[swz<N>(l)], un = wa[swz<N>((N - l) & (N - 1))];
-            gk = make_float2(0.5f * (u.x + un.x), 0.5f * (u.y - un.y));
-            const float dr = u.x - un.x, di = u.y + un.y;
-            gn = make_float2(0.5f * di, -0.5f * dr);
-          }
-          const float s = (bb & 1) ? S[bb >> 1].y : S[bb >> 1].x;
-          const float sq = (bb & 1) ? SQ[bb >> 1].y : SQ[bb >> 1].x;
-          const float sn = (bb & 1) ? SN[bb >> 1].y : SN[bb >> 1].x;
-          const float sd = (bb & 1) ? SD[bb >> 1].y : SD[bb >> 1].x;
-          const float2 pv = k_eig > 0 ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, f * LS + l)
-                                      : __ldg(&psf_hat[f * LS + l]);
-          const float2 bph = cmul(pv, cmul(pxf, py[l]));
-          const float2 z = cscale(cmulc(bph, gk), ck);   // c_k conj(G) P phase
-          contract_bin(z, nu, om, s, sq, sn, acc);
-          if constexpr (WN) acc[6] = fmaf(z.x, sd, acc[6]);
-          if (f == 0) {
-            const float2 zn = cmulc(nyb[l], gn);
-            contract_bin(zn, 0.5f, om, nys[4 * l], nys[4 * l + 1], nys[4 * l + 2], acc);
-            if constexpr (WN) acc[6] = fmaf(zn.x, nys[4 * l + 3], acc[6]);
+            float2 gk = v[b];
+            float2 gn = make_float2(0.f, 0.f);
+            if (col == 0) {
+              const float2 u = wa[swz<N>(l)], un = wa[swz<N>((N - l) & (N - 1))];
+              gk = make_float2(0.5f * (u.x + un.x), 0.5f * (u.y - un.y));
+              const float dr = u.x - un.x, di = u.y + un.y;
+              gn = make_float2(0.5f * di, -0.5f * dr);
+            }
+            const float s = (bb & 1) ? S[bb >> 1].y : S[bb >> 1].x;
+            const float sq = (bb & 1) ? SQ[bb >> 1].y : SQ[bb >> 1].x;
+            const float sn = (bb & 1) ? SN[bb >> 1].y : SN[bb >> 1].x;
+            const float sd = (bb & 1) ? SD[bb >> 1].y : SD[bb >> 1].x;
+            const float2 pv = k_eig > 0 ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, col * LS + l)
+                                        : __ldg(&psf_hat[col * LS + l]);
+            const float2 bph = cmul(pv, cmul(pxf, py[l]));
+            const float2 z = cscale(cmulc(bph, gk), ck);   // c_k conj(G) P phase
+            contract_bin(z, nu, om, s, sq, sn, acc);
+            if constexpr (WN) acc[6] = fmaf(z.x, sd, acc[6]);
+            if (col == 0) {
+              const float2 zn = cmulc(nyb[l], gn);
+              contract_bin(zn, 0.5f, om, nys[4 * l], nys[4 * l + 1], nys[4 * l + 2], acc);
+              if constexpr (WN) acc[6] = fmaf(zn.x, nys[4 * l + 3], acc[6]);
+            }
           }
         }
       }
-    }
+
+    }   // columns of this group
 
     // ---- reduce the sums over the CTA and apply the chain rule ----
     constexpr int NACC = WN ? 7 : 6;
@@ -402,20 +424,29 @@ __global__ void __launch_bounds__(BwdCfg<N>::THREADS, BwdCfg<N>::MIN_BLOCKS)
   }
 }
 
+// Row pairs per group of the launched kernel: two at N = 128 (two 512-thread
+// CTAs per SM).
+template <int N>
+constexpr int bwd_cpg() { return N == 128 ? 2 : 1; }
+
+static_assert(2 * (BwdCfg<128, 2>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 adjoint CTAs share an SM");
+
 template <int N, bool WN = false, bool EIG = false>
 static int bwd_occupancy() {
-  using C = BwdCfg<N>;
-  return kernel_occupancy(reinterpret_cast<const void*>(render_bwd_kernel<N, WN, EIG>), C::THREADS, C::SMEM);
+  constexpr int CPG = bwd_cpg<N>();
+  using C = BwdCfg<N, CPG>;
+  return kernel_occupancy(reinterpret_cast<const void*>(render_bwd_kernel<N, WN, EIG, CPG>), C::THREADS, C::SMEM);
 }
 
 template <int N, bool WN, bool EIG>
 static cudaError_t launch_bwd_mode(const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
                                    int ctas_per_sm, cudaStream_t s) {
-  using C = BwdCfg<N>;
+  constexpr int CPG = bwd_cpg<N>();
+  using C = BwdCfg<N, CPG>;
   const int occ = bwd_occupancy<N, WN, EIG>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_bwd_kernel<N, WN, EIG><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p, grad_out, grad_params);
+  render_bwd_kernel<N, WN, EIG, CPG><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p, grad_out, grad_params);
   return cudaGetLastError();
 }
 

@@ -2,13 +2,14 @@
 // e1, e2; the same contraction as render_bwd.cu, see its header).
 //
 // Neither the gradient patch (256 KB) nor the half spectrum of its rows fits
-// one CTA's shared memory, so
-//   rows      4 rounds of 32 row-pair forward FFTs (one warp each, reading the
+// one CTA's shared memory, so, with 512-thread CTAs two per SM (one computes
+// while the other waits at a CTA barrier),
+//   rows      8 rounds of 16 row-pair forward FFTs (one warp each, reading the
 //             upstream-gradient rows from global memory), untangled into the
 //             two rows' half spectra, staged in shared memory and written as
 //             coalesced column segments to a per-CTA scratch in global memory
 //             (128 x 256 complex, L2-resident; column 0 packs nu = 0 and 1/2)
-//   columns   4 rounds of 32 column forward FFTs reading contiguous scratch
+//   columns   8 rounds of 16 column forward FFTs reading contiguous scratch
 //             rows; each warp contracts its column's bins with the mixture's
 //             derivatives
 //   real      analytic real-space derivatives over all pixels
@@ -24,9 +25,10 @@ namespace {
 constexpr int N = 256;
 constexpr int H = N / 2 + 1;
 constexpr int TPF = N / 8;   // 32
-constexpr int THREADS = 1024;
+constexpr int THREADS = 512;
 constexpr int WARPS = THREADS / 32;
-constexpr int ROUNDS = (N / 2) / WARPS;   // 4
+constexpr int ROUNDS = (N / 2) / WARPS;   // 8
+constexpr int CTAS_PER_SM = 2;
 constexpr int LS = psf_lstride(N);
 constexpr int PSF_ELEMS = psf_spec_elems(N);
 constexpr int WS = wstride<N>();
@@ -47,11 +49,12 @@ constexpr size_t off_terms = off_rec + 2 * sizeof(AdjRecord);
 constexpr size_t off_red = off_terms + sizeof(AdjTerms);
 constexpr size_t off_bar = (off_red + sizeof(float) * 8 * WARPS + 15) & ~size_t(15);
 constexpr size_t SMEM = off_bar + 2 * sizeof(uint64_t);
+static_assert(CTAS_PER_SM * (SMEM + 1024) <= 228 * 1024, "two CTAs share an SM's shared memory");
 
 // WN: also d L / d(Sersic n), a seventh gradient per galaxy.  EIG: some PSF of
 // the context is an eigen-PSF (its spectrum combined bin by bin where read).
 template <bool WN, bool EIG>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
     render_bwd256_kernel(RenderParams p, const float* __restrict__ grad_out, float* __restrict__ grad_params,
                          float2* __restrict__ scratch_all) {
   constexpr float INV_N = 1.0f / N;
@@ -333,14 +336,20 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 }  // namespace
 
-size_t render_bwd256_scratch_bytes(int num_sms) { return sizeof(float2) * (size_t)num_sms * (N / 2) * N; }
+// One N/2 x N slice per CTA: the adjoint and the forward kernel (adding to
+// patches) both run two CTAs per SM.
+size_t render_bwd256_scratch_bytes(int num_sms) {
+  return sizeof(float2) * (size_t)CTAS_PER_SM * num_sms * (N / 2) * N;
+}
 
 cudaError_t launch_render_bwd256(const RenderParams& p, const float* grad_out, float* grad_params, float2* scratch,
                                  int num_sms, cudaStream_t s) {
   auto fn = p.eigen ? (p.grad_n ? render_bwd256_kernel<true, true> : render_bwd256_kernel<false, true>)
                     : (p.grad_n ? render_bwd256_kernel<true, false> : render_bwd256_kernel<false, false>);
-  if (kernel_occupancy(reinterpret_cast<const void*>(fn), THREADS, SMEM) < 0) return cudaErrorInvalidConfiguration;
-  fn<<<num_sms, THREADS, SMEM, s>>>(p, grad_out, grad_params, scratch);
+  const int occ = kernel_occupancy(reinterpret_cast<const void*>(fn), THREADS, SMEM);
+  if (occ < 0) return cudaErrorInvalidConfiguration;
+  // the scratch holds one slice per CTA, CTAS_PER_SM per SM
+  fn<<<num_sms * (occ < CTAS_PER_SM ? occ : CTAS_PER_SM), THREADS, SMEM, s>>>(p, grad_out, grad_params, scratch);
   return cudaGetLastError();
 }
 
