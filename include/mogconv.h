@@ -323,8 +323,10 @@ mog_status mog_render_backward_ex(mog_ctx* ctx, const mog_batch* batch, const fl
 /*
  * Autotuner (the batching feature): for each size bucket present in the
  * batch (batch->size_mask, or all), times that bucket's render kernel alone
- * over every radix schedule of its FFTs (two per side: 32 = 8*4 or 8*2*2,
- * 64 = 8*8 or 8*4*2, 128 = 8*8*2 or 8*4*4, 256 = 8*8*4 or 8*4*8) x every
+ * over every transform schedule (schedules 0 and 1: radix schedules of its
+ * FFTs, 32 = 8*4 or 8*2*2, 64 = 8*8 or 8*4*2, 128 = 8*8*2 or 8*4*4,
+ * 256 = 8*8*4 or 8*4*8; for 64 x 64 also schedule 2: one warp per galaxy
+ * with the 64-point transforms in registers) x every
  * launch shape (CTAs per SM from 1 to what fits x work-queue chunk of 1..32
  * galaxies) with CUDA events, `reps` renders per choice, and keeps the
  * fastest in the context for later calls (the second schedule applies to the
@@ -344,8 +346,9 @@ enum { MOG_AUTOTUNE_REPORT = 2 * 4 * 3 + 1 };
  * Sets a launch shape by hand (as mog_autotune would keep it): direction
  * dir (0 render, 1 adjoint), patch side n, CTAs per SM (0 = as many as fit,
  * larger values are clamped to that), work-queue chunk (1..1024 galaxies),
- * radix schedule (0 or 1, as listed for mog_autotune; the adjoint has
- * schedule 0 only).  Synchronous; MOG_ERR_ARG for values outside these.
+ * transform schedule (0 or 1, and 2 for n = 64, as listed for mog_autotune;
+ * the adjoint has schedule 0 only).  Synchronous; MOG_ERR_ARG for values
+ * outside these.
  */
 mog_status mog_set_launch_shape(mog_ctx* ctx, int dir, int n, int ctas_per_sm, int chunk, int sched);
 mog_status mog_autotune(mog_ctx* ctx, const mog_batch* batch, float* out, const float* grad_out,

@@ -48,6 +48,9 @@ struct DevPsf {
   int k_eig, degree;
   float norm[4];                // u0, v0, su, sv
   float amp[KEIG][KPSF];
+  // the 64 x 64 spectrum again, l-major ([l][k], k = 0..32, row stride 36):
+  // the layout of the warp-per-galaxy 64 x 64 kernel; null for eigen-PSFs
+  const float2* spec64t;
 };
 
 // Polynomial terms 1, X, Y, X^2, X Y, Y^2 of an eigen-PSF at image position
@@ -175,6 +178,10 @@ template <> struct Radix<64, 1> { static constexpr int P = 3; static constexpr i
 template <> struct Radix<128, 1> { static constexpr int P = 3; static constexpr int r[3] = {8, 4, 4}; };
 template <> struct Radix<256, 1> { static constexpr int P = 3; static constexpr int r[3] = {8, 4, 8}; };
 constexpr int SCHEDULES = 2;
+// Transform schedules per patch side: the two radix schedules, and for
+// N = 64 a third, one warp per galaxy with register-resident 64-point
+// transforms (render_fwd64w.cu).
+__host__ __device__ constexpr int schedules_of(int n) { return n == 64 ? 3 : SCHEDULES; }
 
 // Work rows hold one length-N transform each.  N = 32, 64: index map
 // i + i/8 into rows padded to N + N/8 float2, which spreads the stride-8
@@ -790,9 +797,16 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
 // component j of the PSF mixture is rw * 2^(qa dx^2 + qb dx dy + qc dy^2) at
 // (dx, dy) = pixel - (mx, my); rrr = 2^(2 qa) steps the ratio of neighbouring
 // pixels along a row.
+// The constants of real-space term t are kept by pairs of terms, so that the
+// loop over term pairs reads a pair with four 16-byte loads (every lane of a
+// warp reads the same pair: broadcasts): p[t / 2] holds, term t at slot
+// t & 1 of each float2 field, (qa, my), (mx, qb), (qc, w), (r8, unused).
 struct RealTerms {
-  float rw[RMAX], rqa[RMAX], rqb[RMAX], rqc[RMAX], rmx[RMAX], rmy[RMAX], rrr[RMAX];
+  float4 p[RMAX / 2][4];
 };
+__device__ __forceinline__ float* real_term_slots(RealTerms* rt, int t) {
+  return reinterpret_cast<float*>(&rt->p[t >> 1][0]) + (t & 1);
+}
 
 // Term t = c * kpsf + j, computed by one thread.  psf_mog rows are
 // (weight, mean x, mean y, vxx, vxy, vyy).
@@ -807,13 +821,15 @@ __device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*p
   const float vxx = v * r.s11 + m[3], vxy = v * r.s12 + m[4], vyy = v * r.s22 + m[5];
   const float det = vxx * vyy - vxy * vxy;
   const float idet = 1.0f / det;
-  rt->rw[t] = r.ramp[c] * wj * rsqrtf(det) * (0.5f / PI_F);
-  rt->rqa[t] = -0.5f * LOG2E * vyy * idet;
-  rt->rrr[t] = ex2(-LOG2E * vyy * idet);
-  rt->rqb[t] = LOG2E * vxy * idet;
-  rt->rqc[t] = -0.5f * LOG2E * vxx * idet;
-  rt->rmx[t] = 0.5f * (float)n + r.x + m[1];
-  rt->rmy[t] = 0.5f * (float)n + r.y + m[2];
+  float* q = real_term_slots(rt, t);   // field k of term t at q[2 k]
+  q[0] = -0.5f * LOG2E * vyy * idet;               // qa
+  q[2] = 0.5f * (float)n + r.y + m[2];             // my
+  q[4] = 0.5f * (float)n + r.x + m[1];             // mx
+  q[6] = LOG2E * vxy * idet;                       // qb
+  q[8] = -0.5f * LOG2E * vxx * idet;               // qc
+  q[10] = r.ramp[c] * wj * rsqrtf(det) * (0.5f / PI_F);   // w
+  q[12] = ex2(-LOG2E * vyy * idet);                // r8
+  q[14] = 0.0f;
 }
 
 // Number of table entries for nr real-space terms: terms are evaluated in
@@ -822,13 +838,9 @@ __device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*p
 __host__ __device__ constexpr int real_terms_padded(int nr) { return (nr + 1) & ~1; }
 
 __device__ __forceinline__ void real_term_zero(int t, RealTerms* rt) {
-  rt->rw[t] = 0.0f;   // flat exponent (2^0 = 1) times weight 0
-  rt->rqa[t] = 0.0f;
-  rt->rqb[t] = 0.0f;
-  rt->rqc[t] = 0.0f;
-  rt->rmx[t] = 0.0f;
-  rt->rmy[t] = 0.0f;
-  rt->rrr[t] = 1.0f;
+  float* q = real_term_slots(rt, t);   // a flat exponent (2^0 = 1) times weight 0
+  for (int k = 0; k < 8; ++k) q[2 * k] = 0.0f;
+  q[12] = 1.0f;
 }
 
 // Adds the real-space terms [0, nr2) (nr2 even) to the L consecutive pixels
@@ -847,16 +859,16 @@ __device__ __forceinline__ void real_space_run(const RealTerms& rt, int nr2, flo
 #pragma unroll
   for (int u = 0; u < L; ++u) acc[u] = make_float2(0.0f, 0.0f);
   for (int t = 0; t < nr2; t += 2) {
-    const float2 qa = *reinterpret_cast<const float2*>(&rt.rqa[t]);
-    const float2 dy = __ffma2_rn(*reinterpret_cast<const float2*>(&rt.rmy[t]), NEG, Y);
-    const float2 dx = __ffma2_rn(*reinterpret_cast<const float2*>(&rt.rmx[t]), NEG, X);
-    const float2 ly = __fmul2_rn(dy, *reinterpret_cast<const float2*>(&rt.rqb[t]));
-    const float2 e0 = __ffma2_rn(dx, __ffma2_rn(qa, dx, ly),
-                                 __fmul2_rn(__fmul2_rn(*reinterpret_cast<const float2*>(&rt.rqc[t]), dy), dy));
+    const float4 p0 = rt.p[t >> 1][0], p1 = rt.p[t >> 1][1], p2 = rt.p[t >> 1][2], p3 = rt.p[t >> 1][3];
+    const float2 qa = make_float2(p0.x, p0.y);
+    const float2 dy = __ffma2_rn(make_float2(p0.z, p0.w), NEG, Y);
+    const float2 dx = __ffma2_rn(make_float2(p1.x, p1.y), NEG, X);
+    const float2 ly = __fmul2_rn(dy, make_float2(p1.z, p1.w));
+    const float2 e0 = __ffma2_rn(dx, __ffma2_rn(qa, dx, ly), __fmul2_rn(__fmul2_rn(make_float2(p2.x, p2.y), dy), dy));
     const float2 e1 = __ffma2_rn(qa, __ffma2_rn(TWO, dx, ONE), ly);
-    float2 g = __fmul2_rn(*reinterpret_cast<const float2*>(&rt.rw[t]), make_float2(ex2(e0.x), ex2(e0.y)));
+    float2 g = __fmul2_rn(make_float2(p2.z, p2.w), make_float2(ex2(e0.x), ex2(e0.y)));
     float2 rr = make_float2(ex2(e1.x), ex2(e1.y));
-    const float2 r8 = *reinterpret_cast<const float2*>(&rt.rrr[t]);
+    const float2 r8 = make_float2(p3.x, p3.y);
 #pragma unroll
     for (int u = 0; u < L; ++u) {
       acc[u] = __fadd2_rn(acc[u], g);

@@ -33,7 +33,7 @@ struct RenderParams {
 
 // Launch shape of one size bucket: CTAs per SM (clamped to what fits) and
 // the work-queue chunk.  Chosen by mog_autotune; defaults: as many CTAs as
-// fit, chunk 8.
+// fit, the chunk set per side by mog_create_context.
 struct LaunchShape {
   int ctas_per_sm = 0;   // 0 = as many as fit
   int chunk = 8;
@@ -92,6 +92,12 @@ cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, int ctas_pe
 // Resident CTAs per SM of the plain forward kernel for side n and radix
 // schedule `sched` (what the autotuner searches up to).
 int render_fwd_max_ctas(int n, int sched);
+// 64 x 64, schedule 2: one warp per galaxy, register-resident transforms
+// (render_fwd64w.cu; plain render only).
+cudaError_t launch_render_fwd64w(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
+int render_fwd64w_max_ctas();
+size_t psf_spec64t_elems();
+cudaError_t launch_transpose_spec64(const float2* spec, float2* dst, cudaStream_t s);
 int render_fwd256_max_ctas(int sched);
 
 // Patch sides each direction supports (bit b: N = 32 << b).

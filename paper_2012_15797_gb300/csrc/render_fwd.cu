@@ -550,6 +550,7 @@ static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_s
     return p.lanczos ? launch_fwd_mode<N, true, true, 0>(p, num_sms, ctas_per_sm, s)
                      : launch_fwd_mode<N, false, true, 0>(p, num_sms, ctas_per_sm, s);
   if (p.lanczos) return launch_fwd_mode<N, true, false, 0>(p, num_sms, ctas_per_sm, s);
+  if (N == 64 && p.sched == 2) return launch_render_fwd64w(p, num_sms, ctas_per_sm, s);
   return p.sched == 1 ? launch_fwd_mode<N, false, false, 1>(p, num_sms, ctas_per_sm, s)
                       : launch_fwd_mode<N, false, false, 0>(p, num_sms, ctas_per_sm, s);
 }
@@ -567,7 +568,8 @@ cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int cta
 int render_fwd_max_ctas(int n, int sched) {
   switch (n) {
     case 32: return sched == 1 ? fwd_occupancy<32, false, false, 1>() : fwd_occupancy<32>();
-    case 64: return sched == 1 ? fwd_occupancy<64, false, false, 1>() : fwd_occupancy<64>();
+    case 64: return sched == 2 ? render_fwd64w_max_ctas()
+                  : sched == 1 ? fwd_occupancy<64, false, false, 1>() : fwd_occupancy<64>();
     case 128: return sched == 1 ? fwd_occupancy<128, false, false, 1>() : fwd_occupancy<128>();
     case 256: return render_fwd256_max_ctas(sched);
     default: return 0;
