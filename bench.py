@@ -471,15 +471,19 @@ def extra_render_grad(tables, psf, device, steps, pk):
     data = r.render(to_device(truth, device=dev)).view(len(truth), 64, 64)
     sigma = 0.01 * data.amax(dim=(1, 2), keepdim=True)
     data = data + sigma * torch.from_numpy(noise).to(dev)
-    ivar = (1.0 / sigma ** 2).reshape(-1, 1, 1)
+    ivar = (1.0 / sigma ** 2).reshape(-1).contiguous()
+    data = data.reshape(-1).contiguous()
     bm = to_device(model, device=dev)
     out = torch.empty(bm.total, device=dev)
     gpix = torch.empty(bm.total, device=dev)
     gp = torch.empty(len(model), 6, device=dev)
+    chi2 = torch.empty(len(model), device=dev)
 
     def step():
+        # render, the loss gradient 2 ivar (model - data) and chi^2 per galaxy
+        # (mog_chi2_gradient), adjoint: every step in the library's kernels
         r.render(bm, out)
-        torch.mul(out.view(-1, 64, 64) - data, 2.0 * ivar, out=gpix.view(-1, 64, 64))
+        r.chi2_gradient(bm, out, data, ivar, gpix, chi2)
         r.render_backward(bm, gpix, gp)
 
     st = torch.cuda.current_stream()
@@ -503,7 +507,7 @@ def extra_render_grad(tables, psf, device, steps, pk):
     wf, wb = algorithmic_work(model, tables, kpsf), adjoint_work(model, tables, kpsf)
     res = {"workload": "50000 galaxies as the fixed-size batch; loss = sum ivar (model - data)^2, data from "
                        "perturbed parameters + Gaussian noise sigma = 0.01 peak; gradients w.r.t. "
-                       "(flux, x, y, log r_e, e1, e2)",
+                       "(flux, x, y, log r_e, e1, e2); step = render, mog_chi2_gradient, adjoint",
            "value": len(model) / (ms / 1e3), "unit": "patches rendered+grad/s", "ms_per_step": ms,
            "kernel_ms_forward": fwd_ms, "kernel_ms_adjoint": bwd_ms,
            "roofline": roofline(wb, bwd_ms, pk, "render_bwd_kernel<64>"),
@@ -719,18 +723,21 @@ def extra_serving(tables, device, full_ms=500.0, half_window_s=10.0, single_ms=2
         warm = min(300, len(reqs))
         t, k = srv.replay(reqs[:warm], np.zeros(warm))
         srv.wait_replayed(t, k)
+        srv.timing(reset=True)
         t0 = time.perf_counter()
         t, k = srv.replay(reqs, times_s)
         lat = srv.wait_replayed(t, k)
         wall = time.perf_counter() - t0
         stats = srv.stats()
+        breakdown = srv.timing()
         srv.close()
         return {"achieved_galaxies_per_s": float(gal.sum() / wall), "requests": len(reqs),
                 "window_s": float(times_s[-1]), "offered_galaxies_per_s": float(gal.sum() / max(times_s[-1], 1e-9)),
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "p999_ms": float(np.percentile(lat, 99.9) * 1e3), "max_ms": float(lat.max() * 1e3),
                 "mean_ms": float(lat.mean() * 1e3), "micro_batches": stats["batches"] - 1,
-                "largest_micro_batch": stats["max_batch_galaxies"], "max_lanes_in_flight": stats["max_lanes_in_flight"]}
+                "largest_micro_batch": stats["max_batch_galaxies"], "max_lanes_in_flight": stats["max_lanes_in_flight"],
+                "breakdown": breakdown}
 
     cfg = dict(budget_bytes=16 << 30, lanes=4, max_batch_galaxies=32768)
     full = run(reqs, arrival_ms / 1e3, **cfg)

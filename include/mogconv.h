@@ -301,6 +301,20 @@ mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float
 enum { MOG_GRAD_SERSIC = 1, MOG_GRAD_LANCZOS = 2 };
 
 /*
+ * The loss of a fit and its gradient with respect to the rendered patches
+ * (the upstream gradient mog_render_backward takes; the paper fits models by
+ * chi-squared, Section 1): per galaxy g with inverse variance ivar[g],
+ *   chi2[g]  = ivar[g] sum_pixels (model - data)^2      (optional, may be NULL)
+ *   grad_pix = 2 ivar[g] (model - data)                  on the galaxy's patch
+ * model, data and grad_pix: device float32 in the batch's patch layout
+ * (offsets, sizes; 16-byte aligned), grad_pix may be model itself; ivar:
+ * device, one float per galaxy.  A galaxy whose side is unsupported is
+ * skipped (chi2 NaN).  Asynchronous on `stream`.
+ */
+mog_status mog_chi2_gradient(mog_ctx* ctx, const mog_batch* batch, const float* model, const float* data,
+                             const float* ivar, float* grad_pix, float* chi2, void* stream);
+
+/*
  * Fits a k-component Gaussian mixture (1 <= k <= 4) to each of `count`
  * pixelized PSFs on the device: the mixture the real-space half convolves
  * with (Section 2, Step 4; the chi-squared fit of Section 1).  images: device
@@ -432,6 +446,14 @@ mog_status mog_server_replay_join(mog_server* server);
 /* out[6]: requests done, galaxies done, micro-batches, largest batch (galaxies),
  * most lanes in flight at once, requests pending. */
 mog_status mog_server_stats(mog_server* server, int64_t* out);
+/* Timing breakdown in milliseconds, out[12] (host): (p50, p99, max) of, in
+ * order, the host time to launch a micro-batch (admission to the last launch
+ * call returning), its device time (events around its work on the lane's
+ * stream), a request's queue wait (submission to admission) and its service
+ * time (admission to results available; latency = queue wait + service).
+ * Gathered since the server started or since the last call with reset != 0,
+ * which clears them. */
+mog_status mog_server_timing(mog_server* server, double* out, int reset);
 /* Finishes pending work (up to 60 s) and releases the server. */
 mog_status mog_server_destroy(mog_server* server);
 

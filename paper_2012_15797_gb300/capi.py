@@ -37,7 +37,7 @@ EXPORTED = (
     "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
     "mog_create_eigen_psf", "mog_render_batch_ex", "mog_render_backward_ex", "mog_fit_psf_mixture",
     "mog_render_batch_host", "mog_measure_pipe_rates", "mog_server_inject_fault", "mog_check_wait_timeout",
-    "mog_set_launch_shape",
+    "mog_set_launch_shape", "mog_chi2_gradient", "mog_server_timing",
 )
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
@@ -116,6 +116,8 @@ def _load():
         "mog_server_inject_fault": ([VP, I, ctypes.c_int64], I),
         "mog_check_wait_timeout": ([VP, ctypes.c_double, VP], I),
         "mog_set_launch_shape": ([VP, I, I, I, I, I], I),
+        "mog_chi2_gradient": ([VP, P(mog_batch), VP, VP, VP, VP, VP, VP], I),
+        "mog_server_timing": ([VP, P(ctypes.c_double), I], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -285,6 +287,13 @@ def mog_autotune(ctx, batch, out_ptr, grad_out_ptr=0, grad_params_ptr=0, stream=
 def mog_set_launch_shape(ctx, direction, n, ctas_per_sm=0, chunk=8, schedule=0):
     """direction: 0 render, 1 adjoint."""
     _check(ctx, _lib.mog_set_launch_shape(ctx, int(direction), int(n), int(ctas_per_sm), int(chunk), int(schedule)))
+
+
+def mog_chi2_gradient(ctx, batch, model_ptr, data_ptr, ivar_ptr, grad_ptr, chi2_ptr=0, stream=0):
+    _check(ctx, _lib.mog_chi2_gradient(ctx, ctypes.byref(batch), ctypes.c_void_p(int(model_ptr)),
+                                       ctypes.c_void_p(int(data_ptr)), ctypes.c_void_p(int(ivar_ptr)),
+                                       ctypes.c_void_p(int(grad_ptr)), ctypes.c_void_p(int(chi2_ptr)),
+                                       ctypes.c_void_p(int(stream))))
 
 
 def mog_graph_capture(ctx, batch, out_ptr):

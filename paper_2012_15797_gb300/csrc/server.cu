@@ -16,6 +16,7 @@
 // flight on different lanes while newly arrived requests queue for the next
 // free lane; a completion thread returns results, frees the memory and
 // records each request's latency (submission to results available).
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -127,6 +128,7 @@ struct Request {
   float* grads;               // caller's
   float* chi2;                // caller's
   Clock::time_point submitted;
+  Clock::time_point admitted;
   double latency = -1.0;
   bool done = false;
   bool dropped = false;       // fault injection: its completion is lost
@@ -223,6 +225,10 @@ struct mog_server {
     size_t block_bytes = 0;
     int64_t galaxies = 0;
     int status = MOG_OK;
+    // timing of the lane's micro-batch: host clock when admitted and when the
+    // launch calls returned; device events around its work
+    mog::Clock::time_point t_admit, t_launched;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   };
   std::vector<Lane> lanes;
   // queues
@@ -241,6 +247,9 @@ struct mog_server {
   // admitted (drop) or micro-batch launched (launch, nomem) since arming
   int fault_kind = 0;
   int64_t fault_nth = 0, fault_seen = 0;
+  // per micro-batch: host launch time and device time; per request: queue
+  // wait (submission to admission) and service (admission to results) [ms]
+  std::vector<double> t_launch, t_device, t_queue, t_service;
 };
 
 namespace mog {
@@ -304,6 +313,7 @@ int launch_batch(mog_server* S, mog_server::Lane& L, int64_t g, int64_t pix) {
   int32_t* in_fi = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 2 * g));
   int64_t* in_off = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * g));
   cudaStream_t s = L.stream;
+  if (cudaEventRecord(L.ev0, s) != cudaSuccess) return MOG_ERR_CUDA;
   // inputs: params, then offsets, fit, idx (contiguous in staging)
   if (cudaMemcpyAsync(in_params, L.st.params, sizeof(float) * 6 * g, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(in_off, L.st.offset, sizeof(int64_t) * g, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -331,7 +341,7 @@ int launch_batch(mog_server* S, mog_server::Lane& L, int64_t g, int64_t pix) {
   st = backward_with(ctx, &L.ws, &mb, b.model, b.grads, s);
   if (st != MOG_OK) return st;
   if (cudaMemcpyAsync(L.st.results, b.grads, sizeof(float) * 7 * g, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaEventRecord(L.done, s) != cudaSuccess)
+      cudaEventRecord(L.ev1, s) != cudaSuccess || cudaEventRecord(L.done, s) != cudaSuccess)
     return MOG_ERR_CUDA;
   return MOG_OK;
 }
@@ -390,6 +400,8 @@ void scheduler(mog_server* S) {
     L->busy = true;
     L->reqs = take;
     L->galaxies = g;
+    L->t_admit = Clock::now();
+    for (auto& r : take) r->admitted = L->t_admit;
     int inflight = 0;
     for (auto& l : S->lanes) inflight += l.busy;
     if (inflight > S->max_inflight) S->max_inflight = inflight;
@@ -413,6 +425,7 @@ void scheduler(mog_server* S) {
       }
       st = launch_batch(S, *L, g, pix);
     }
+    L->t_launched = Clock::now();
     lk.lock();
     L->status = st;
     L->launched = true;
@@ -468,7 +481,15 @@ void completer(mog_server* S) {
       }
       i += r->count;
     }
+    float dev_ms = -1.0f;
+    if (L.status == MOG_OK && cudaEventElapsedTime(&dev_ms, L.ev0, L.ev1) != cudaSuccess) dev_ms = -1.0f;
     std::unique_lock<std::mutex> lk(S->mu);
+    S->t_launch.push_back(std::chrono::duration<double, std::milli>(L.t_launched - L.t_admit).count());
+    if (dev_ms >= 0.0f) S->t_device.push_back(dev_ms);
+    for (auto& r : L.reqs) {
+      S->t_queue.push_back(std::chrono::duration<double, std::milli>(r->admitted - r->submitted).count());
+      S->t_service.push_back(std::chrono::duration<double, std::milli>(now - r->admitted).count());
+    }
     for (auto& r : L.reqs) {
       if (r->dropped) continue;   // injected: this completion is lost
       r->status = L.status;
@@ -511,6 +532,8 @@ mog_status mog_server_create(mog_ctx* ctx, const mog_server_config* cfg, mog_ser
   for (auto& L : S->lanes) {
     cudaError_t e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.ev1);
     if (e == cudaSuccess) e = workspace_init(&L.ws);
     if (e != cudaSuccess) {
       mog_server_destroy(S);
@@ -675,6 +698,22 @@ mog_status mog_server_inject_fault(mog_server* S, int kind, int64_t nth) {
   return MOG_OK;
 }
 
+mog_status mog_server_timing(mog_server* S, double* out, int reset) {
+  if (!S || !out) return MOG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  std::vector<double>* v[4] = {&S->t_launch, &S->t_device, &S->t_queue, &S->t_service};
+  for (int k = 0; k < 4; ++k) {
+    std::vector<double> c(*v[k]);
+    std::sort(c.begin(), c.end());
+    const size_t n = c.size();
+    out[3 * k + 0] = n ? c[(size_t)(0.50 * (n - 1))] : 0.0;
+    out[3 * k + 1] = n ? c[(size_t)(0.99 * (n - 1))] : 0.0;
+    out[3 * k + 2] = n ? c[n - 1] : 0.0;
+    if (reset) v[k]->clear();
+  }
+  return MOG_OK;
+}
+
 mog_status mog_server_stats(mog_server* S, int64_t* out) {
   if (!S || !out) return MOG_ERR_ARG;
   std::lock_guard<std::mutex> lk(S->mu);
@@ -711,6 +750,8 @@ mog_status mog_server_destroy(mog_server* S) {
   for (auto& L : S->lanes) {
     if (L.stream) cudaStreamDestroy(L.stream);
     if (L.done) cudaEventDestroy(L.done);
+    if (L.ev0) cudaEventDestroy(L.ev0);
+    if (L.ev1) cudaEventDestroy(L.ev1);
     workspace_free(&L.ws);
     lane_free_staging(L);
   }

@@ -173,6 +173,20 @@ class Renderer:
             capi.mog_render_backward(self.ctx, b, grad_out.data_ptr(), grad_params.data_ptr(), s.cuda_stream)
         return grad_params
 
+    def chi2_gradient(self, batch, model, data, ivar, grad_pix=None, chi2=None, stream=None):
+        """d chi^2 / d model = 2 ivar (model - data) on every patch (the
+        upstream gradient of render_backward) and chi^2 per galaxy;
+        ``ivar`` (count,) float32.  Returns (grad_pix, chi2)."""
+        if grad_pix is None:
+            grad_pix = torch.empty_like(model)
+        if chi2 is None:
+            chi2 = torch.empty(batch.count, dtype=torch.float32, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
+        capi.mog_chi2_gradient(self.ctx, b, model.data_ptr(), data.data_ptr(), ivar.contiguous().data_ptr(),
+                               grad_pix.data_ptr(), chi2.data_ptr(), s.cuda_stream)
+        return grad_pix, chi2
+
     def fit_psf_mixtures(self, images, k=3, iters=400, stream=None):
         """Gaussian-mixture fits of a (count, h, w) float32 device tensor of
         PSF images: returns ((count, k, 6) rows, (count,) chi^2)."""

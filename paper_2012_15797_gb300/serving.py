@@ -103,6 +103,14 @@ class Server:
         keys = ("requests", "galaxies", "batches", "max_batch_galaxies", "max_lanes_in_flight", "pending")
         return dict(zip(keys, list(out)))
 
+    def timing(self, reset=False):
+        """(p50, p99, max) in ms of micro-batch launch (host) and device
+        times and of request queue wait and service times."""
+        out = (ctypes.c_double * 12)()
+        capi._check(self.renderer.ctx, capi.library().mog_server_timing(self.handle, out, 1 if reset else 0))
+        keys = ("launch_host", "device", "queue_wait", "service")
+        return {k: {"p50_ms": out[3 * i], "p99_ms": out[3 * i + 1], "max_ms": out[3 * i + 2]} for i, k in enumerate(keys)}
+
     def close(self):
         if self.handle is not None:
             capi.library().mog_server_destroy(self.handle)
