@@ -40,7 +40,7 @@ PARAM_BYTES = 7 * 4 + 3 * 4 + 8      # float params, int ids, int64 offset
 SFU_PER_CLK_SM = 32                  # MUFU ex2 per SM per clock (measured live: "pipe_rates" in the line)
 FP32_FLOP_PER_CLK_SM = 256           # 128 FMA lanes x 2 (measured live: "pipe_rates")
 KERNEL_SOURCES = ("paper_2012_15797_gb300/csrc/render_fwd.cu", "paper_2012_15797_gb300/csrc/common.cuh")
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "render_fwd_64_config1.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "render_fwd_64_100k.md")
 
 
 def parse_args():
@@ -292,11 +292,11 @@ _W = {}
 def _worker_init(seed_g):
     os.environ["OMP_NUM_THREADS"] = "1"
     from oracle import render as R
-    from workloads import config0_psf, config1_galaxies, load_profile_tables
+    from workloads import single_psf, fixed_galaxies_64, load_profile_tables
     _W["R"] = R
     _W["tables"] = load_profile_tables()
-    _W["psf"] = config0_psf()
-    _W["gals"] = config1_galaxies(seed_g)
+    _W["psf"] = single_psf()
+    _W["gals"] = fixed_galaxies_64(seed_g)
     _W["hat"] = R.psf_spectrum(_W["psf"].image, N_PATCH)
 
 
@@ -389,10 +389,10 @@ def extra_mixed(tables, device, steps, pk):
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import Renderer, to_device
-    from workloads import config2_galaxies, config2_psfs
+    from workloads import mixed_galaxies, psf_set
 
-    psfs = config2_psfs(64)
-    gals = config2_galaxies(200_000)
+    psfs = psf_set(64)
+    gals = mixed_galaxies(200_000)
     r = Renderer(tables, psfs, device=device)
     b = to_device(gals, device=f"cuda:{device}")
     out = torch.empty(b.total, dtype=torch.float32, device=f"cuda:{device}")
@@ -463,9 +463,9 @@ def extra_render_grad(tables, psf, device, steps, pk):
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import Renderer, to_device
-    from workloads import config3_problem
+    from workloads import fit_problem
 
-    model, truth, noise = config3_problem(50_000)
+    model, truth, noise = fit_problem(50_000)
     r = Renderer(tables, [psf], device=device)
     dev = f"cuda:{device}"
     data = r.render(to_device(truth, device=dev)).view(len(truth), 64, 64)
@@ -524,9 +524,9 @@ def extra_lanczos(tables, psf, device, steps):
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import Renderer, to_device
-    from workloads import config1_galaxies
+    from workloads import fixed_galaxies_64
 
-    gals = config1_galaxies()
+    gals = fixed_galaxies_64()
     r = Renderer(tables, [psf], device=device)
     b = to_device(gals, device=f"cuda:{device}")
     out = torch.empty(b.total, device=f"cuda:{device}")
@@ -554,9 +554,9 @@ def extra_eigen(tables, psf, device, steps):
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import Renderer, to_device
-    from workloads import config1_galaxies, eigen_positions, eigen_psf
+    from workloads import fixed_galaxies_64, eigen_positions, eigen_psf
 
-    gals = config1_galaxies()
+    gals = fixed_galaxies_64()
     gals.psf[:] = 1
     r = Renderer(tables, [psf, eigen_psf()], device=device)
     b = to_device(gals, device=f"cuda:{device}", positions=eigen_positions(len(gals)))
@@ -611,10 +611,10 @@ def extra_sersic_grad(tables, device, steps):
     and the adjoint with d L / d sersic_n (7 gradients)."""
     import torch
     from paper_2012_15797_gb300.renderer import Renderer, to_device
-    from workloads import config2_galaxies, config2_psfs
+    from workloads import mixed_galaxies, psf_set
 
-    gals = config2_galaxies(200_000)
-    r = Renderer(tables, config2_psfs(64), device=device)
+    gals = mixed_galaxies(200_000)
+    r = Renderer(tables, psf_set(64), device=device)
     b = to_device(gals, device=f"cuda:{device}")
     go = torch.randn(b.total, device=f"cuda:{device}")
     g6 = torch.empty(len(gals), 6, device=f"cuda:{device}")
@@ -640,9 +640,9 @@ def extra_psf_fit(tables, device):
     import numpy as np
     import torch
     from paper_2012_15797_gb300.renderer import Renderer
-    from workloads import config2_psfs
+    from workloads import psf_set
 
-    imgs = torch.from_numpy(np.stack([p.image for p in config2_psfs(64, fit=False)])).cuda(device)
+    imgs = torch.from_numpy(np.stack([p.image for p in psf_set(64, fit=False)])).cuda(device)
     r = Renderer(tables, [], device=device)
     r.fit_psf_mixtures(imgs)
     torch.cuda.synchronize()
@@ -660,8 +660,8 @@ def extra_psf_create(tables, device, n=64):
     synchronous calls."""
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import Renderer
-    from workloads import config2_psfs
-    psfs = config2_psfs(n)
+    from workloads import psf_set
+    psfs = psf_set(n)
     r = Renderer(tables, [], device=device)
     for p in psfs[:4]:   # warm: loads the kernels
         capi.mog_destroy_psf(r.ctx, capi.mog_create_psf(r.ctx, p.image, p.mog))
@@ -680,9 +680,9 @@ def extra_per_galaxy(tables, psf, device, n=2000):
     render launches) per galaxy."""
     import torch
     from paper_2012_15797_gb300.renderer import Renderer, to_device
-    from workloads import config1_galaxies
+    from workloads import fixed_galaxies_64
 
-    gals = config1_galaxies(n, seed=5)
+    gals = fixed_galaxies_64(n, seed=5)
     r = Renderer(tables, [psf], device=device)
     singles = [to_device(gals.subset([i]), device=f"cuda:{device}") for i in range(n)]
     out = torch.empty(64 * 64, device=f"cuda:{device}")
@@ -708,10 +708,10 @@ def extra_serving(tables, device, full_ms=500.0, half_window_s=10.0, single_ms=2
     import torch
     from paper_2012_15797_gb300.renderer import Renderer
     from paper_2012_15797_gb300.serving import Server, make_fits
-    from workloads import config2_psfs, serving_workload
+    from workloads import psf_set, serving_workload
 
     fits, arrival_ms, reqs = serving_workload(n_fits=1000, duration_ms=full_ms, max_side=max_side)
-    r = Renderer(tables, config2_psfs(64), device=device)
+    r = Renderer(tables, psf_set(64), device=device)
     state = make_fits(r, fits)
     torch.cuda.synchronize()
 
@@ -830,11 +830,11 @@ def run_ours(args):
         build()
     barrier(world)
     from paper_2012_15797_gb300.renderer import Renderer, host_batch, to_device
-    from workloads import config0_psf, config1_galaxies, load_profile_tables
+    from workloads import single_psf, fixed_galaxies_64, load_profile_tables
 
     tables = load_profile_tables()
-    psf = config0_psf()
-    gals = config1_galaxies(args.galaxies)
+    psf = single_psf()
+    gals = fixed_galaxies_64(args.galaxies)
     r = Renderer(tables, [psf], device=local)
     batch = to_device(gals, device=f"cuda:{local}")
     out = torch.empty(batch.total, dtype=torch.float32, device=f"cuda:{local}")
@@ -1005,26 +1005,26 @@ def run_only(args):
     from paper_2012_15797_gb300.build import build
     build()
     from paper_2012_15797_gb300.renderer import Renderer, to_device
-    from workloads import config0_psf, config1_galaxies, config2_galaxies, config2_psfs, load_profile_tables
+    from workloads import single_psf, fixed_galaxies_64, mixed_galaxies, psf_set, load_profile_tables
     tables = load_profile_tables()
     pos = None
     if args.only == "mixed":
-        psfs = config2_psfs(8)
-        gals = config2_galaxies(args.galaxies, n_psf=8)
+        psfs = psf_set(8)
+        gals = mixed_galaxies(args.galaxies, n_psf=8)
     elif args.only == "eigen":
         from workloads import eigen_positions, eigen_psf
-        psfs = [config0_psf(), eigen_psf()]
-        gals = config1_galaxies(args.galaxies)
+        psfs = [single_psf(), eigen_psf()]
+        gals = fixed_galaxies_64(args.galaxies)
         gals.psf[:] = 1
         pos = eigen_positions(len(gals))
     elif args.size:
         import numpy as np
-        psfs = config2_psfs(16)
-        mixed = config2_galaxies(args.galaxies, n_psf=16)
+        psfs = psf_set(16)
+        mixed = mixed_galaxies(args.galaxies, n_psf=16)
         gals = mixed.subset(np.flatnonzero(mixed.size == args.size))
     else:
-        psfs = [config0_psf()]
-        gals = config1_galaxies(args.galaxies)
+        psfs = [single_psf()]
+        gals = fixed_galaxies_64(args.galaxies)
     r = Renderer(tables, psfs)
     b = to_device(gals, positions=pos)
     out = torch.empty(b.total, device="cuda")

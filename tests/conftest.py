@@ -21,8 +21,8 @@ def tables():
 
 @pytest.fixture(scope="session")
 def psf0():
-    from workloads import config0_psf
-    return config0_psf()
+    from workloads import single_psf
+    return single_psf()
 
 
 @pytest.fixture(scope="session")
@@ -35,8 +35,8 @@ def gpu_renderer(tables, psf0):
     from paper_2012_15797_gb300.build import build
     build()
     from paper_2012_15797_gb300.renderer import Renderer
-    from workloads import config2_psfs
-    psfs = [psf0] + config2_psfs(4)
+    from workloads import psf_set
+    psfs = [psf0] + psf_set(4)
     r = Renderer(tables, psfs)
     r.psfs = psfs
     yield r

@@ -10,7 +10,7 @@ import pytest
 
 from oracle import adjoint as A
 from oracle import render as R
-from workloads import Galaxies, config0_galaxy, config1_galaxies, config2_galaxies, config3_problem
+from workloads import Galaxies, single_galaxy_64, fixed_galaxies_64, mixed_galaxies, fit_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -23,7 +23,7 @@ def _gals(rows):
 
 
 def _row(**kw):
-    r = config0_galaxy().row(0)
+    r = single_galaxy_64().row(0)
     r.update(kw)
     return r
 
@@ -95,7 +95,7 @@ def test_adjoint_ramp_region(gpu_renderer, tables, size):
 
 
 def test_adjoint_batch_mixed(gpu_renderer, tables):
-    gals = config2_galaxies(160, seed=21, n_psf=5)
+    gals = mixed_galaxies(160, seed=21, n_psf=5)
     assert 256 in set(gals.size)
     gp = _random_grad(gals, 3)
     check(gpu_grads(gpu_renderer, gals, gp), oracle_grads(gals, gpu_renderer.psfs, tables, gp), gals, gp)
@@ -107,7 +107,7 @@ def test_adjoint_full_size_sampled(gpu_renderer, tables):
     32 sampled galaxies' gradients are checked against the oracle."""
     import torch
     from paper_2012_15797_gb300.renderer import to_device
-    model, _, field = config3_problem(50_000)
+    model, _, field = fit_problem(50_000)
     bm = to_device(model)
     go = torch.from_numpy(field.reshape(-1)).cuda()
     gp = gpu_renderer.render_backward(bm, go)
@@ -124,7 +124,7 @@ def test_loss_gradient_pipeline(gpu_renderer):
     equals the adjoint applied to dL/dpix."""
     import torch
     from paper_2012_15797_gb300.renderer import render, theta_of, to_device
-    model, truth, noise = config3_problem(2_000)
+    model, truth, noise = fit_problem(2_000)
     data = gpu_renderer.render(to_device(truth)).view(len(truth), 64, 64)
     sigma = 0.01 * data.amax(dim=(1, 2), keepdim=True)
     data = data + sigma * torch.from_numpy(noise).cuda()
@@ -144,7 +144,7 @@ def test_loss_gradient_pipeline(gpu_renderer):
 def test_autograd_matches_c_abi(gpu_renderer):
     import torch
     from paper_2012_15797_gb300.renderer import render, theta_of, to_device
-    gals = config1_galaxies(40, seed=31)
+    gals = fixed_galaxies_64(40, seed=31)
     b = to_device(gals)
     theta = theta_of(b).clone().requires_grad_(True)
     w = torch.randn(b.total, device="cuda")

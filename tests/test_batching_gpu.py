@@ -5,7 +5,7 @@ same way whichever CTA takes it)."""
 import numpy as np
 import pytest
 
-from workloads import config1_galaxies, config2_galaxies
+from workloads import fixed_galaxies_64, mixed_galaxies
 
 pytestmark = pytest.mark.gpu
 
@@ -18,10 +18,10 @@ def test_autotune_keeps_results(tables, psf0):
     import torch
     from paper_2012_15797_gb300.renderer import Renderer, to_device
     from parity import PIX_TOL
-    from workloads import config2_psfs
-    r = Renderer(tables, [psf0] + config2_psfs(4))
+    from workloads import psf_set
+    r = Renderer(tables, [psf0] + psf_set(4))
     try:
-        gals = config2_galaxies(4000, seed=51, n_psf=5)
+        gals = mixed_galaxies(4000, seed=51, n_psf=5)
         b = to_device(gals)
         ref = r.render(b)
         out = torch.empty_like(ref)
@@ -42,7 +42,7 @@ def test_autotune_keeps_results(tables, psf0):
 def test_autotune_adjoint(gpu_renderer):
     import torch
     from paper_2012_15797_gb300.renderer import to_device
-    gals = config1_galaxies(3000, seed=52)
+    gals = fixed_galaxies_64(3000, seed=52)
     b = to_device(gals)
     go = torch.randn(b.total, device="cuda")
     ref = gpu_renderer.render_backward(b, go)
@@ -59,7 +59,7 @@ def test_autotune_adjoint(gpu_renderer):
 def test_graph_launch_matches_eager_and_sees_new_inputs(gpu_renderer):
     import torch
     from paper_2012_15797_gb300.renderer import to_device
-    gals = config2_galaxies(3000, seed=53, n_psf=5)
+    gals = mixed_galaxies(3000, seed=53, n_psf=5)
     b = to_device(gals)
     ref = gpu_renderer.render(b)
     out = torch.full_like(ref, float("nan"))
@@ -78,7 +78,7 @@ def test_graph_launch_matches_eager_and_sees_new_inputs(gpu_renderer):
     g.close()
 
 
-def test_full_config2_graph_sampled(tables):
+def test_full_mixed_200k_graph_sampled(tables):
     """The benchmark's mixed-size launch at full size: 200k galaxies (Sersic n
     0.5-6, N = 32..256) with 64 Moffat-winged PSFs, launch shapes from the
     autotuner, one CUDA-graph launch; every pixel written, and 32 sampled
@@ -87,11 +87,11 @@ def test_full_config2_graph_sampled(tables):
     import torch
     from parity import check_parity, oracle_patches
     from paper_2012_15797_gb300.renderer import Renderer, to_device
-    from workloads import config2_psfs
-    psfs = config2_psfs(64)
+    from workloads import psf_set
+    psfs = psf_set(64)
     r = Renderer(tables, psfs)
     try:
-        gals = config2_galaxies()
+        gals = mixed_galaxies()
         b = to_device(gals)
         out = torch.empty(b.total, dtype=torch.float32, device="cuda")
         r.autotune(b, out, reps=1)

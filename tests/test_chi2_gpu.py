@@ -6,7 +6,7 @@ mixed patch sides, in place over the model, and unsupported sides skipped."""
 import numpy as np
 import pytest
 
-from workloads import config2_galaxies
+from workloads import mixed_galaxies
 
 pytestmark = pytest.mark.gpu
 
@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 def test_chi2_gradient_matches_float64(gpu_renderer):
     import torch
     from paper_2012_15797_gb300.renderer import patches, to_device
-    gals = config2_galaxies(300, seed=71, n_psf=5)
+    gals = mixed_galaxies(300, seed=71, n_psf=5)
     b = to_device(gals)
     model = gpu_renderer.render(b)
     gen = torch.Generator(device="cuda").manual_seed(3)
@@ -39,7 +39,7 @@ def test_chi2_gradient_skips_unsupported_sides(gpu_renderer):
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import to_device
-    gals = config2_galaxies(20, seed=72, n_psf=5)
+    gals = mixed_galaxies(20, seed=72, n_psf=5)
     b = to_device(gals)
     model = torch.ones(b.total, device="cuda")
     data = torch.zeros_like(model)

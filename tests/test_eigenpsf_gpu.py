@@ -9,7 +9,7 @@ from oracle import eigenpsf as E
 from oracle import lanczos as L
 from oracle import render as R
 from parity import check_parity
-from workloads import (Galaxies, config0_galaxy, config1_galaxies, config2_galaxies, eigen_psf, eigen_positions,
+from workloads import (Galaxies, single_galaxy_64, fixed_galaxies_64, mixed_galaxies, eigen_psf, eigen_positions,
                        PROFILE_DEV)
 from workloads.psf import EigenPsfInput
 
@@ -47,7 +47,7 @@ def _gals(rows):
 
 
 def _row(**kw):
-    r = config0_galaxy().row(0)
+    r = single_galaxy_64().row(0)
     r.update(kw)
     return r
 
@@ -89,13 +89,13 @@ def test_eigen_edge_cases_each_size(eig_renderer, eig, psf0, tables, size):
 
 def test_eigen_mixed_batch(eig_renderer, eig, psf0, tables):
     """Mixed sizes, eigen-PSF and constant-PSF galaxies interleaved."""
-    gals = config2_galaxies(120, seed=51, n_psf=2)   # psf ids 0 and 1
+    gals = mixed_galaxies(120, seed=51, n_psf=2)   # psf ids 0 and 1
     pos = eigen_positions(len(gals), seed=52)
     check_parity(gpu_render(eig_renderer, gals, pos), oracle_render(gals, pos, eig, psf0, tables), gals)
 
 
 def test_eigen_with_lanczos_shift(eig_renderer, eig, psf0, tables):
-    gals = config2_galaxies(60, seed=53, n_psf=2)
+    gals = mixed_galaxies(60, seed=53, n_psf=2)
     pos = eigen_positions(len(gals), seed=54)
     check_parity(gpu_render(eig_renderer, gals, pos, "lanczos"),
                  oracle_render(gals, pos, eig, psf0, tables, "lanczos"), gals)
@@ -131,7 +131,7 @@ def test_missing_positions_reported(eig_renderer):
 def test_eigen_full_batch_sampled(eig_renderer, eig, psf0, tables):
     """100k 64^2 galaxies of the fixed-size distribution on the eigen-PSF,
     24 sampled patches."""
-    gals = config1_galaxies()
+    gals = fixed_galaxies_64()
     gals.psf[:] = 1
     pos = eigen_positions(len(gals), seed=55)
     got = gpu_render(eig_renderer, gals, pos)
@@ -144,7 +144,7 @@ def test_eigen_full_batch_sampled(eig_renderer, eig, psf0, tables):
 def test_eigen_capable_kernels_match_for_constant_psfs(eig_renderer, gpu_renderer):
     """A context with an eigen-PSF launches the kernels that handle one; on
     constant-PSF galaxies they give the same bits as the plain kernels."""
-    gals = config2_galaxies(80, seed=56, n_psf=1)
+    gals = mixed_galaxies(80, seed=56, n_psf=1)
     pos = eigen_positions(len(gals), seed=57)
     a = gpu_render(eig_renderer, gals, pos)
     b = gpu_render(gpu_renderer, gals, pos)

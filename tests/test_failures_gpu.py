@@ -7,7 +7,7 @@ as a status within its limit, and the server and context keep working."""
 import numpy as np
 import pytest
 
-from workloads import config2_galaxies
+from workloads import mixed_galaxies
 
 pytestmark = pytest.mark.gpu
 
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def served(gpu_renderer):
     from paper_2012_15797_gb300.serving import make_fits
-    fits = [config2_galaxies(200, seed=81 + f, n_psf=5) for f in range(2)]
+    fits = [mixed_galaxies(200, seed=81 + f, n_psf=5) for f in range(2)]
     return fits, make_fits(gpu_renderer, fits)
 
 
@@ -144,7 +144,7 @@ def test_bounded_device_wait_runs_out_and_context_stays_usable(gpu_renderer):
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import to_device
-    from workloads import config1_galaxies
+    from workloads import fixed_galaxies_64
     gpu_renderer.sync_status()
     t0 = time.perf_counter()
     capi.mog_check_wait_timeout(gpu_renderer.ctx, 0.05, torch.cuda.current_stream().cuda_stream)
@@ -154,7 +154,7 @@ def test_bounded_device_wait_runs_out_and_context_stays_usable(gpu_renderer):
     assert ei.value.status == capi.MOG_ERR_TIMEOUT
     assert 0.04 <= elapsed < 5.0
     gpu_renderer.sync_status()   # the status word was cleared
-    b = to_device(config1_galaxies(50, seed=83))
+    b = to_device(fixed_galaxies_64(50, seed=83))
     out = gpu_renderer.render(b)
     gpu_renderer.sync_status()
     assert torch.isfinite(out).all()

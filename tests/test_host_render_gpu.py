@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import render as R
-from workloads import config1_galaxies, config2_galaxies
+from workloads import fixed_galaxies_64, mixed_galaxies
 
 pytestmark = pytest.mark.gpu
 
@@ -31,26 +31,26 @@ def _host_render(r, gals, chunk=0, shift="phase", pin=True):
 
 @pytest.mark.parametrize("chunk", [0, 1, 257, 1000])
 def test_fixed_size_equals_device_render(gpu_renderer, chunk):
-    gals = config1_galaxies(2500, seed=71)
+    gals = fixed_galaxies_64(2500, seed=71)
     assert np.array_equal(_host_render(gpu_renderer, gals, chunk), _device_render(gpu_renderer, gals))
 
 
 def test_mixed_sizes_and_psfs_equal_device_render(gpu_renderer):
-    gals = config2_galaxies(3000, seed=72, n_psf=5)
+    gals = mixed_galaxies(3000, seed=72, n_psf=5)
     want = _device_render(gpu_renderer, gals)
     assert np.array_equal(_host_render(gpu_renderer, gals, chunk=333), want)
     assert np.array_equal(_host_render(gpu_renderer, gals, chunk=0), want)
 
 
 def test_lanczos_and_pageable_memory(gpu_renderer):
-    gals = config2_galaxies(800, seed=73, n_psf=5)
+    gals = mixed_galaxies(800, seed=73, n_psf=5)
     want = _device_render(gpu_renderer, gals, shift="lanczos")
     assert np.array_equal(_host_render(gpu_renderer, gals, chunk=100, shift="lanczos"), want)
     assert np.array_equal(_host_render(gpu_renderer, gals, chunk=100, shift="lanczos", pin=False), want)
 
 
 def test_matches_the_oracle(gpu_renderer, tables):
-    gals = config1_galaxies(40, seed=74)
+    gals = fixed_galaxies_64(40, seed=74)
     got = _host_render(gpu_renderer, gals, chunk=7)
     off = 0
     for i in range(len(gals)):
@@ -68,7 +68,7 @@ def test_rejects_bad_layouts(gpu_renderer):
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import host_batch
-    gals = config1_galaxies(10, seed=75)
+    gals = fixed_galaxies_64(10, seed=75)
     t, total = host_batch(gals)
     out = torch.empty(total, dtype=torch.float32)
 

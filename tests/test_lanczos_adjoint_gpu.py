@@ -10,7 +10,7 @@ import pytest
 from oracle import lanczos as L
 from oracle import render as R
 from test_adjoint_gpu import _gals, _random_grad, _row, check
-from workloads import config2_galaxies
+from workloads import mixed_galaxies
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def test_lanczos_adjoint_every_side(gpu_renderer, tables, size):
 
 
 def test_lanczos_adjoint_mixed_batch(gpu_renderer, tables):
-    gals = config2_galaxies(160, seed=301, n_psf=5)
+    gals = mixed_galaxies(160, seed=301, n_psf=5)
     gp = _random_grad(gals, 302)
     gpu = gpu_grads_lanczos(gpu_renderer, gals, gp)
     idx = [int(i) for n in (32, 64, 128, 256) for i in np.flatnonzero(gals.size == n)[:3]]
@@ -78,7 +78,7 @@ def test_lanczos_adjoint_at_integer_offsets_is_the_phase_adjoint(gpu_renderer):
     # through the transposed convolution with weights 0 and 1)
     import torch
     from paper_2012_15797_gb300.renderer import to_device
-    gals = config2_galaxies(200, seed=304, n_psf=5)
+    gals = mixed_galaxies(200, seed=304, n_psf=5)
     gals.x[:] = np.round(gals.x * 4)
     gals.y[:] = np.round(gals.y * 4)
     b = to_device(gals)

@@ -8,7 +8,7 @@ import pytest
 from oracle import lanczos as L
 from oracle import render as R
 from parity import check_parity
-from workloads import Galaxies, config0_galaxy, config1_galaxies, config2_galaxies, PROFILE_DEV, PROFILE_SERSIC
+from workloads import Galaxies, single_galaxy_64, fixed_galaxies_64, mixed_galaxies, PROFILE_DEV, PROFILE_SERSIC
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +22,7 @@ def _gals(rows):
 
 
 def _row(**kw):
-    r = config0_galaxy().row(0)
+    r = single_galaxy_64().row(0)
     r.update(kw)
     return r
 
@@ -49,7 +49,7 @@ def lanczos_oracle(gals, psfs, tables):
 
 
 EDGE = [
-    dict(),                                                   # config 0
+    dict(),                                                   # the single 64x64 galaxy as drawn
     dict(x=0.5, y=-0.5), dict(x=-0.5, y=0.4999), dict(x=0.0, y=0.0),
     dict(x=3.7, y=-6.2),                                      # integer part beyond a pixel
     dict(log_re=np.log(1e-4)),                                # point-source limit
@@ -69,13 +69,13 @@ def test_lanczos_edge_cases_each_size(gpu_renderer, tables, size):
 
 def test_lanczos_batch_fixed_size(gpu_renderer, tables):
     """The 64x64 fixed-size distribution, 160 galaxies (many CTAs, ragged)."""
-    gals = config1_galaxies(160, seed=41)
+    gals = fixed_galaxies_64(160, seed=41)
     gpu, _, _ = lanczos_gpu(gpu_renderer, gals)
     check_parity(gpu, lanczos_oracle(gals, gpu_renderer.psfs, tables), gals)
 
 
 def test_lanczos_batch_mixed_sizes(gpu_renderer, tables):
-    gals = config2_galaxies(150, seed=42, n_psf=5)
+    gals = mixed_galaxies(150, seed=42, n_psf=5)
     assert set(np.unique(gals.size)) == {32, 64, 128, 256}
     gpu, _, _ = lanczos_gpu(gpu_renderer, gals)
     check_parity(gpu, lanczos_oracle(gals, gpu_renderer.psfs, tables), gals)
@@ -94,9 +94,9 @@ def test_integer_offsets_equal_the_phase_path(gpu_renderer):
         assert np.array_equal(a[i], b[i]), i
 
 
-def test_lanczos_full_config1_sampled(gpu_renderer, tables):
+def test_lanczos_full_100k_sampled(gpu_renderer, tables):
     """100k galaxies at 64^2 in one Lanczos call, 32 sampled patches."""
-    gals = config1_galaxies()
+    gals = fixed_galaxies_64()
     gpu, _, _ = lanczos_gpu(gpu_renderer, gals)
     idx = np.sort(np.random.default_rng(5).choice(len(gals), 32, replace=False))
     ora = lanczos_oracle(gals.subset(idx), gpu_renderer.psfs, tables)

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import adjoint as A
 from oracle import render as R
-from workloads import config0_galaxy
+from workloads import single_galaxy_64
 
 CASES = [
     # (log r_e, profile, e1, e2, x, y, N): all-Fourier, ramp, real-space, tiny
@@ -22,7 +22,7 @@ CASES = [
 @pytest.mark.parametrize("case", CASES)
 def test_jacobian_matches_central_differences(case, tables, psf0):
     lre, prof, e1, e2, x, y, n = case
-    g = config0_galaxy().row(0)
+    g = single_galaxy_64().row(0)
     g.update(log_re=lre, profile=prof, sersic_n=2.7 if prof == 2 else 1.0, e1=e1, e2=e2, x=x, y=y,
              flux=4.3, size=n)
     ph = R.psf_spectrum(psf0.image, n)
@@ -36,7 +36,7 @@ def test_jacobian_matches_central_differences(case, tables, psf0):
 
 
 def test_vjp_is_jacobian_contraction(tables, psf0):
-    g = config0_galaxy().row(0)
+    g = single_galaxy_64().row(0)
     ph = R.psf_spectrum(psf0.image, 64)
     rng = np.random.default_rng(3)
     gp = rng.normal(size=(64, 64))
@@ -66,7 +66,7 @@ def test_subpixel_motion_is_smooth_for_point_source(tables, psf0):
     every subpixel phase."""
     ph = R.psf_spectrum(psf0.image, 64)
     for x in np.linspace(-0.5, 0.5, 5):
-        g = config0_galaxy().row(0)
+        g = single_galaxy_64().row(0)
         g.update(log_re=np.log(1e-3), x=x, e1=0.1, e2=0.05)
         jac = A.jacobian(g, ph, psf0.mog, tables)
         fd = A.finite_difference(g, ph, psf0.mog, tables, step=1e-5)
@@ -78,7 +78,7 @@ def test_jacobian_with_wcs_matrix(cd, tables, psf0):
     """A general WCS matrix (Appendix A): the analytic Jacobian against central
     differences of the forward model rendered with the same CD."""
     for lre, prof in ((np.log(3.0), 0), (np.log(9.0), 1)):
-        g = config0_galaxy().row(0)
+        g = single_galaxy_64().row(0)
         g.update(log_re=lre, profile=prof, sersic_n=4.0 if prof == 1 else 1.0, e1=0.25, e2=-0.2, x=0.3, y=-0.1,
                  flux=2.0, size=64)
         ph = R.psf_spectrum(psf0.image, 64)
@@ -95,7 +95,7 @@ def test_sersic_derivative_matches_central_differences(sn, lre, n, tables, psf0)
     """d pixel / d n through the interpolated Sersic table (all-Fourier, ramp
     and real-space cases), against central differences in n away from the
     table's nodes (n = 0.5 + 0.25 k)."""
-    g = config0_galaxy().row(0)
+    g = single_galaxy_64().row(0)
     g.update(profile=2, sersic_n=sn, log_re=lre, e1=0.2, e2=-0.15, x=0.3, y=-0.2, flux=3.0, size=n)
     ph = R.psf_spectrum(psf0.image, n)
     got = A.sersic_derivative(g, ph, psf0.mog, tables)
@@ -106,7 +106,7 @@ def test_sersic_derivative_matches_central_differences(sn, lre, n, tables, psf0)
 
 
 def test_sersic_derivative_zero_for_fixed_profiles_and_outside_the_table(tables, psf0):
-    g = config0_galaxy().row(0)
+    g = single_galaxy_64().row(0)
     ph = R.psf_spectrum(psf0.image, 64)
     for prof, sn in ((0, 1.0), (1, 4.0), (2, 6.7), (2, 0.2)):
         g.update(profile=prof, sersic_n=sn, log_re=np.log(6.0))

@@ -8,7 +8,7 @@ import pytest
 
 from oracle import lanczos as L
 from oracle import render as R
-from workloads import config0_galaxy
+from workloads import single_galaxy_64
 
 
 def test_kernel_derivative_matches_differences():
@@ -48,7 +48,7 @@ CASES = [
 @pytest.mark.parametrize("case", CASES)
 def test_jacobian_matches_central_differences(case, tables, psf0):
     lre, prof, e1, e2, x, y, n = case
-    g = config0_galaxy().row(0)
+    g = single_galaxy_64().row(0)
     g.update(log_re=lre, profile=prof, sersic_n=2.7 if prof == 2 else 1.0, e1=e1, e2=e2, x=x, y=y,
              flux=4.3, size=n)
     ph = R.psf_spectrum(psf0.image, n)
@@ -65,7 +65,7 @@ def test_jacobian_matches_central_differences(case, tables, psf0):
 
 
 def test_sersic_derivative_matches_central_differences(tables, psf0):
-    g = config0_galaxy().row(0)
+    g = single_galaxy_64().row(0)
     g.update(log_re=np.log(5.0), profile=2, sersic_n=2.6, e1=0.2, e2=0.1, x=0.27, y=-0.38, size=64)
     ph = R.psf_spectrum(psf0.image, 64)
     d = L.sersic_derivative_lanczos(g, ph, psf0.mog, tables)
@@ -83,7 +83,7 @@ def test_vjp_reduces_to_the_phase_model_at_integer_offsets(tables, psf0):
     # the phase-shift model's; x and y then come from the weights' slope at
     # d = 0 applied to the same image
     from oracle import adjoint as A
-    g = config0_galaxy().row(0)
+    g = single_galaxy_64().row(0)
     g.update(x=2.0, y=-1.0)
     ph = R.psf_spectrum(psf0.image, 64)
     rng = np.random.default_rng(5)

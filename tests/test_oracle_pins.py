@@ -8,7 +8,7 @@ from scipy.special import gammainc
 
 from oracle import render as R
 from oracle import sersic as S
-from workloads import config0_galaxy, gaussian_mixture_psf
+from workloads import single_galaxy_64, gaussian_mixture_psf
 
 # ----------------------------------------------------------------------------
 # Helpers that restate the continuous quantities independently of the oracle.
@@ -49,7 +49,7 @@ def _mog_conv_mog(gal, tables, psf_mog, n):
 
 
 def _gal(**kw):
-    g = config0_galaxy().row(0)
+    g = single_galaxy_64().row(0)
     g.update(kw)
     return g
 

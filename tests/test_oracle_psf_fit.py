@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import psf_fit as F
-from workloads import config2_psfs
+from workloads import psf_set
 
 
 def _gauss_image(rows, n=32):
@@ -40,7 +40,7 @@ def test_exact_mixture_is_recovered(truth):
 
 
 def test_fit_of_a_winged_psf_improves_on_start_and_on_fewer_components():
-    psf = config2_psfs(1, seed=3)[0].image.astype(np.float64)
+    psf = psf_set(1, seed=3)[0].image.astype(np.float64)
     rows3, c3 = F.fit_mog(psf, 3)
     rows1, c1 = F.fit_mog(psf, 1)
     start = F.chi2(F.mixture_rows(F.initial_parameters(psf, 3)), psf)
@@ -55,7 +55,7 @@ def test_winged_psf_fit_reaches_the_multistart_optimum():
     out here with the plain Gaussian formula, so the fixed start finds the
     global optimum of the objective there, not merely a local one."""
     from scipy.optimize import minimize
-    psf = config2_psfs(1, seed=3)[0].image.astype(np.float64)
+    psf = psf_set(1, seed=3)[0].image.astype(np.float64)
     n = psf.shape[0]
     k = 3
     yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import psf_fit as F
-from workloads import config2_psfs
+from workloads import psf_set
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def test_exact_mixture_recovered(gpu_renderer, n, truth):
 
 
 def test_winged_psfs_match_the_oracle_fit(gpu_renderer):
-    psfs = [p.image.astype(np.float64) for p in config2_psfs(6, seed=31, fit=False)]
+    psfs = [p.image.astype(np.float64) for p in psf_set(6, seed=31, fit=False)]
     rows, chi2 = gpu_fit(gpu_renderer, psfs, k=3)
     for i, img in enumerate(psfs):
         ora_rows, ora_chi2 = F.fit_mog(img, 3)
@@ -53,7 +53,7 @@ def test_winged_psfs_match_the_oracle_fit(gpu_renderer):
 
 
 def test_batch_equals_single_calls(gpu_renderer):
-    psfs = [p.image for p in config2_psfs(5, seed=32, fit=False)]
+    psfs = [p.image for p in psf_set(5, seed=32, fit=False)]
     rows, chi2 = gpu_fit(gpu_renderer, psfs, k=3)
     for i in (0, 3):
         r1, c1 = gpu_fit(gpu_renderer, [psfs[i]], k=3)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from parity import check_parity, gpu_patches, oracle_patches
-from workloads import (Galaxies, config0_galaxy, config1_galaxies, config2_galaxies,
+from workloads import (Galaxies, single_galaxy_64, fixed_galaxies_64, mixed_galaxies,
                        PROFILE_EXP, PROFILE_DEV, PROFILE_SERSIC)
 
 pytestmark = pytest.mark.gpu
@@ -20,20 +20,20 @@ def _gals(rows):
 
 
 def _row(**kw):
-    r = config0_galaxy().row(0)
+    r = single_galaxy_64().row(0)
     r.update(kw)
     return r
 
 
-def test_config0_single_galaxy(gpu_renderer, tables):
-    gals = config0_galaxy()
+def test_single_galaxy_64(gpu_renderer, tables):
+    gals = single_galaxy_64()
     gpu, _, _ = gpu_patches(gpu_renderer, gals)
     ora = oracle_patches(gals, gpu_renderer.psfs, tables)
     check_parity(gpu, ora, gals)
 
 
 EDGE = [
-    dict(),                                                  # config 0
+    dict(),                                                  # the single 64x64 galaxy as drawn
     dict(e1=0.0, e2=0.0),                                     # round
     dict(e1=0.6 * np.cos(1.0), e2=0.6 * np.sin(1.0)),         # |e| = 0.6
     dict(flux=1e4), dict(x=0.5, y=-0.5), dict(x=-0.5, y=0.4999),
@@ -74,14 +74,14 @@ def test_ramp_boundaries(gpu_renderer, tables, size):
 
 def test_batch_fixed_size_ragged(gpu_renderer, tables):
     """333 config-1 galaxies (many CTAs, a ragged last chunk)."""
-    gals = config1_galaxies(333, seed=11)
+    gals = fixed_galaxies_64(333, seed=11)
     gpu, _, _ = gpu_patches(gpu_renderer, gals)
     ora = oracle_patches(gals, gpu_renderer.psfs, tables)
     check_parity(gpu, ora, gals)
 
 
 def test_batch_mixed_sizes_and_psfs(gpu_renderer, tables):
-    gals = config2_galaxies(301, seed=12, n_psf=5)
+    gals = mixed_galaxies(301, seed=12, n_psf=5)
     assert set(np.unique(gals.size)) == {32, 64, 128, 256}
     gpu, _, _ = gpu_patches(gpu_renderer, gals)
     ora = oracle_patches(gals, gpu_renderer.psfs, tables)
@@ -89,7 +89,7 @@ def test_batch_mixed_sizes_and_psfs(gpu_renderer, tables):
 
 
 def test_batch_equals_single(gpu_renderer):
-    gals = config2_galaxies(64, seed=13, n_psf=5)
+    gals = mixed_galaxies(64, seed=13, n_psf=5)
     full, _, _ = gpu_patches(gpu_renderer, gals)
     big = int(np.nonzero(gals.size == 256)[0][0])
     for i in (0, 5, big, len(gals) - 1):
@@ -100,7 +100,7 @@ def test_batch_equals_single(gpu_renderer):
 def test_every_pixel_written_once_and_gaps_untouched(gpu_renderer):
     import torch
     from paper_2012_15797_gb300.renderer import to_device
-    gals = config1_galaxies(50, seed=14)
+    gals = fixed_galaxies_64(50, seed=14)
     b = to_device(gals)
     # spread the patches out with 4-float gaps filled with a canary
     off = np.arange(50, dtype=np.int64) * (64 * 64 + 4)
@@ -114,7 +114,7 @@ def test_every_pixel_written_once_and_gaps_untouched(gpu_renderer):
 
 
 def test_empty_batch(gpu_renderer):
-    gals = config1_galaxies(0)
+    gals = fixed_galaxies_64(0)
     gpu, out, _ = gpu_patches(gpu_renderer, gals)
     assert gpu == [] and out.numel() == 0
 
@@ -123,7 +123,7 @@ def test_invalid_galaxy_reports_status_and_skips(gpu_renderer):
     import torch
     from paper_2012_15797_gb300.capi import MogError, MOG_ERR_DEVICE
     from paper_2012_15797_gb300.renderer import to_device
-    gals = config1_galaxies(3, seed=15)
+    gals = fixed_galaxies_64(3, seed=15)
     gals.log_re[1] = np.nan
     b = to_device(gals)
     out = torch.full((b.total,), -3.0, dtype=torch.float32, device="cuda")
@@ -140,7 +140,7 @@ def test_unsupported_size_reports_status(gpu_renderer):
     import torch
     from paper_2012_15797_gb300.capi import MogError
     from paper_2012_15797_gb300.renderer import to_device
-    gals = config1_galaxies(2, seed=16, size=48)
+    gals = fixed_galaxies_64(2, seed=16, size=48)
     b = to_device(gals)
     out = torch.zeros(b.total, dtype=torch.float32, device="cuda")
     gpu_renderer.render(b, out)
@@ -148,10 +148,10 @@ def test_unsupported_size_reports_status(gpu_renderer):
         gpu_renderer.sync_status()
 
 
-def test_full_config1_sampled(gpu_renderer, tables):
+def test_full_100k_64_sampled(gpu_renderer, tables):
     """100k galaxies at 64^2 in one call (the benchmark's launch), 48 sampled
     patches checked against the oracle."""
-    gals = config1_galaxies()
+    gals = fixed_galaxies_64()
     gpu, _, _ = gpu_patches(gpu_renderer, gals.subset(np.arange(len(gals))))
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(len(gals), 48, replace=False))

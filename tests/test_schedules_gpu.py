@@ -9,7 +9,7 @@ import pytest
 
 from parity import check_parity, gpu_patches, oracle_patches
 from test_render_gpu import EDGE, _gals, _row
-from workloads import config1_galaxies, config2_galaxies
+from workloads import fixed_galaxies_64, mixed_galaxies
 
 pytestmark = pytest.mark.gpu
 
@@ -24,8 +24,8 @@ def sched_renderer(tables, psf0):
     from paper_2012_15797_gb300.build import build
     build()
     from paper_2012_15797_gb300.renderer import Renderer
-    from workloads import config2_psfs
-    psfs = [psf0] + config2_psfs(4)
+    from workloads import psf_set
+    psfs = [psf0] + psf_set(4)
     r = Renderer(tables, psfs)
     r.psfs = psfs
     yield r
@@ -41,7 +41,7 @@ def _use(renderer, n, schedule, chunk=8):
 @pytest.mark.parametrize("n,schedule", CASES)
 def test_schedule_parity(sched_renderer, tables, n, schedule):
     _use(sched_renderer, n, schedule)
-    gals = config2_galaxies(1500, seed=91 + schedule, n_psf=5)
+    gals = mixed_galaxies(1500, seed=91 + schedule, n_psf=5)
     sub = gals.subset(np.flatnonzero(gals.size == n)[:12])
     gpu, _, _ = gpu_patches(sched_renderer, sub)
     ora = oracle_patches(sub, sched_renderer.psfs, tables)
@@ -58,7 +58,7 @@ def test_warp_kernel_sampled_fixed_size_batch_and_add_mode(sched_renderer, table
     # what the patches hold gives the plain render plus the old contents
     import torch
     from paper_2012_15797_gb300.renderer import patches, to_device
-    gals = config1_galaxies(3001, seed=95)
+    gals = fixed_galaxies_64(3001, seed=95)
     idx = np.arange(0, 3001, 150)
     for chunk in (1, 32):
         _use(sched_renderer, 64, 2, chunk)

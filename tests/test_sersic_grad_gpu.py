@@ -8,7 +8,7 @@ import pytest
 
 from oracle import adjoint as A
 from oracle import render as R
-from workloads import Galaxies, config0_galaxy, config2_galaxies, PROFILE_DEV, PROFILE_EXP, PROFILE_SERSIC
+from workloads import Galaxies, single_galaxy_64, mixed_galaxies, PROFILE_DEV, PROFILE_EXP, PROFILE_SERSIC
 
 pytestmark = pytest.mark.gpu
 
@@ -20,7 +20,7 @@ def _gals(rows):
 
 
 def _row(**kw):
-    r = config0_galaxy().row(0)
+    r = single_galaxy_64().row(0)
     r.update(profile=PROFILE_SERSIC, e1=0.2, e2=-0.15)
     r.update(kw)
     return r
@@ -63,7 +63,7 @@ def test_sersic_gradient_each_size(gpu_renderer, tables, size):
 
 
 def test_sersic_gradient_mixed_batch(gpu_renderer, tables):
-    gals = config2_galaxies(60, seed=102, n_psf=5)
+    gals = mixed_galaxies(60, seed=102, n_psf=5)
     rng = np.random.default_rng(103)
     grad = [rng.normal(size=(int(n), int(n))) for n in gals.size]
     check(gpu_grads(gpu_renderer, gals, grad), gals, gpu_renderer.psfs, tables, grad)

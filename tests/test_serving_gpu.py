@@ -7,7 +7,7 @@ under a tiny budget without changing results."""
 import numpy as np
 import pytest
 
-from workloads import config2_galaxies
+from workloads import mixed_galaxies
 
 pytestmark = pytest.mark.gpu
 
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 def _fits(n_fits=3, per_fit=300, seed=61):
     fits = []
     for f in range(n_fits):
-        g = config2_galaxies(per_fit, seed=seed + f, n_psf=5)
+        g = mixed_galaxies(per_fit, seed=seed + f, n_psf=5)
         fits.append(g)
     return fits
 

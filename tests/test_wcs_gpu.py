@@ -8,7 +8,7 @@ import pytest
 from oracle import adjoint as A
 from oracle import render as R
 from parity import check_parity
-from workloads import Galaxies, config0_galaxy, config2_galaxies, PROFILE_DEV
+from workloads import Galaxies, single_galaxy_64, mixed_galaxies, PROFILE_DEV
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +30,7 @@ def _gals(rows):
 
 
 def _row(**kw):
-    r = config0_galaxy().row(0)
+    r = single_galaxy_64().row(0)
     r.update(kw)
     return r
 
@@ -71,13 +71,13 @@ def test_wcs_forward_each_size(gpu_renderer, tables, size):
 
 
 def test_wcs_forward_mixed_batch(gpu_renderer, tables):
-    gals = config2_galaxies(120, seed=61, n_psf=5)
+    gals = mixed_galaxies(120, seed=61, n_psf=5)
     cd = _cds(len(gals), 62)
     check_parity(gpu_render(gpu_renderer, gals, cd), oracle_render(gals, cd, gpu_renderer.psfs, tables), gals)
 
 
 def test_identity_matrix_gives_the_same_bits(gpu_renderer):
-    gals = config2_galaxies(60, seed=63, n_psf=5)
+    gals = mixed_galaxies(60, seed=63, n_psf=5)
     eye = np.tile(np.eye(2, dtype=np.float32), (len(gals), 1, 1))
     a = gpu_render(gpu_renderer, gals, eye)
     b = gpu_render(gpu_renderer, gals, None)

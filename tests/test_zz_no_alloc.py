@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from parity import PIX_TOL
-from workloads import config1_galaxies, config2_galaxies
+from workloads import fixed_galaxies_64, mixed_galaxies
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +41,8 @@ def _check(ref, got, b, gals):
 def test_noalloc_matches_render_batch_two_calls(gpu_renderer):
     # first call: mixed sizes and PSFs; second call: a smaller batch, so stale
     # scratch from the first call would show up if it were read
-    g1 = config2_galaxies(3000, seed=41, n_psf=5)
-    g2 = config1_galaxies(700, seed=42)
+    g1 = mixed_galaxies(3000, seed=41, n_psf=5)
+    g2 = fixed_galaxies_64(700, seed=42)
     for gals in (g1, g2):
         ref, got, b = _render_both(gpu_renderer, gals)
         _check(ref, got, b, gals)
@@ -52,7 +52,7 @@ def test_noalloc_rejects_oversized_batch(gpu_renderer):
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import to_device
-    gals = config1_galaxies(capi.MOG_NOALLOC_MAX_GALAXIES + 1, seed=43)
+    gals = fixed_galaxies_64(capi.MOG_NOALLOC_MAX_GALAXIES + 1, seed=43)
     b = to_device(gals)
     out = torch.empty(b.total, device="cuda")
     with pytest.raises(capi.MogError) as ei:
@@ -67,7 +67,7 @@ def test_noalloc_call_allocates_nothing(gpu_renderer):
     import torch
     from paper_2012_15797_gb300 import capi
     from paper_2012_15797_gb300.renderer import to_device
-    b = to_device(config2_galaxies(2000, seed=44, n_psf=5))
+    b = to_device(mixed_galaxies(2000, seed=44, n_psf=5))
     out = torch.empty(b.total, device="cuda")
     batch = capi.make_batch(b.count, b.ptrs(), b.size_mask())
     stream = torch.cuda.current_stream().cuda_stream
@@ -91,7 +91,7 @@ def test_noalloc_skips_eigen_psf_galaxies(tables, psf0):
     from workloads import eigen_positions, eigen_psf
     r = Renderer(tables, [psf0, eigen_psf()])
     try:
-        gals = config1_galaxies(64, seed=45)
+        gals = fixed_galaxies_64(64, seed=45)
         gals.psf[5] = 1
         gals.psf[40] = 1
         b = to_device(gals, positions=eigen_positions(len(gals)))

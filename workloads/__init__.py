@@ -11,11 +11,11 @@ any of the method.
 
 from .galaxies import (  # noqa: F401
     PROFILE_EXP, PROFILE_DEV, PROFILE_SERSIC, SIZE_BUCKETS,
-    config0_galaxy, config1_galaxies, config2_galaxies, config3_problem,
+    single_galaxy_64, fixed_galaxies_64, mixed_galaxies, fit_problem,
     serving_workload, bucket_size, Galaxies, composite_galaxies,
 )
 from .psf import (  # noqa: F401
-    gaussian_mixture_psf, config0_psf, config2_psfs, fit_psf_mog, PsfInput,
+    gaussian_mixture_psf, single_psf, psf_set, fit_psf_mog, PsfInput,
     EigenPsfInput, eigen_psf, eigen_positions,
 )
 from .tables import load_profile_tables, ProfileTable  # noqa: F401

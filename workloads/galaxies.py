@@ -85,14 +85,14 @@ def _shapes(rng, g, emax=0.6):
     return emag * np.cos(2 * phi), emag * np.sin(2 * phi)
 
 
-def config0_galaxy():
+def single_galaxy_64():
     """One exponential galaxy: r_e = 3 px, e = (0.2, -0.1), flux 1, offset
     (0.3, -0.2), 64x64 patch, PSF 0."""
     return _cast(flux=[1.0], x=[0.3], y=[-0.2], log_re=[np.log(3.0)], e1=[0.2], e2=[-0.1],
                  sersic_n=[1.0], profile=[PROFILE_EXP], psf=[0], size=[64])
 
 
-def config1_galaxies(g=100_000, seed=1, size=64):
+def fixed_galaxies_64(g=100_000, seed=1, size=64):
     """Fixed-size batch: 50/50 exp/deV, r_e log-uniform 0.3-20 px, |e| uniform
     <= 0.6 at a uniform angle, flux log-uniform 1-1e4, offsets uniform in
     [-0.5, 0.5)^2, one shared PSF, N x N patches."""
@@ -108,10 +108,10 @@ def config1_galaxies(g=100_000, seed=1, size=64):
                  psf=np.zeros(g), size=np.full(g, size))
 
 
-def config2_galaxies(g=200_000, seed=2, n_psf=64):
+def mixed_galaxies(g=200_000, seed=2, n_psf=64):
     """Uneven sizes: Sersic n uniform 0.5-6, r_e log-uniform 0.3-20 px, patch
     side the smallest of {32, 64, 128, 256} >= 8 r_e, PSF id uniform over
-    ``n_psf`` PSFs; other parameters as in ``config1_galaxies``."""
+    ``n_psf`` PSFs; other parameters as in ``fixed_galaxies_64``."""
     rng = np.random.default_rng(seed)
     n = rng.uniform(0.5, 6.0, g)
     log_re = rng.uniform(np.log(0.3), np.log(20.0), g)
@@ -125,15 +125,15 @@ def config2_galaxies(g=200_000, seed=2, n_psf=64):
                  profile=np.full(g, PROFILE_SERSIC), psf=psf, size=size)
 
 
-def config3_problem(g=50_000, seed=3):
+def fit_problem(g=50_000, seed=3):
     """Differentiation workload.  Returns ``(model, truth, noise_unit)``:
     ``model`` are the parameters the gradient is taken at (drawn as in
-    ``config1_galaxies``), ``truth`` are perturbed parameters the synthetic
+    ``fixed_galaxies_64``), ``truth`` are perturbed parameters the synthetic
     data image is rendered from (flux x(1 + 0.05 z), x, y += 0.1 z px,
     log r_e += 0.05 z, e1, e2 += 0.02 z with |e| clipped to 0.6), and
     ``noise_unit`` is a standard-normal field (G, N, N) that the caller scales
     by sigma = 0.01 * peak of each rendered truth patch."""
-    model = config1_galaxies(g, seed)
+    model = fixed_galaxies_64(g, seed)
     rng = np.random.default_rng(seed + 1000)
     z = rng.standard_normal((g, 6))
     t = model.params6()
@@ -156,17 +156,17 @@ def config3_problem(g=50_000, seed=3):
 def serving_workload(n_fits=1000, per_fit=512, seed=4, rate_per_ms=20_000.0, duration_ms=1000.0,
                      max_size=512, n_psf=64, max_side=256, request_seed=None):
     """Serving workload: ``n_fits`` concurrent fits of ``per_fit`` galaxies
-    each (drawn as in ``config2_galaxies``, patch sides <= max_side), and
+    each (drawn as in ``mixed_galaxies``, patch sides <= max_side), and
     requests of 1..``max_size`` galaxies (uniform) arriving as a Poisson
     process of ``rate_per_ms`` galaxies per millisecond for ``duration_ms``.
     A request names a fit, a contiguous range of its galaxies and their
     current parameters: the fit's values perturbed as in
-    ``config3_problem``.  Returns ``(fits, arrival_ms, requests)`` with
+    ``fit_problem``.  Returns ``(fits, arrival_ms, requests)`` with
     requests a list of (fit, first, params (count, 6) float32).
     ``request_seed`` (default ``seed``) seeds the request stream alone, so
     that streams of other rates share the same fits."""
     rng = np.random.default_rng(seed if request_seed is None else request_seed)
-    pool = config2_galaxies(int(n_fits * per_fit * 1.6) + 64, seed + 1, n_psf=n_psf)
+    pool = mixed_galaxies(int(n_fits * per_fit * 1.6) + 64, seed + 1, n_psf=n_psf)
     keep = np.nonzero(pool.size <= max_side)[0][:n_fits * per_fit]
     pool = pool.subset(keep)
     fits = [pool.subset(np.arange(f * per_fit, (f + 1) * per_fit)) for f in range(n_fits)]

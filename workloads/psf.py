@@ -123,14 +123,14 @@ def fit_psf_mog(image, k=3):
     return comps
 
 
-def config0_psf(size=64, k_fit=3):
+def single_psf(size=64, k_fit=3):
     """0.8 N(sigma=1.5) + 0.2 N(sigma=3.0) px on a 64 x 64 grid, plus its
     k_fit-component mixture fit."""
     img, exact = gaussian_mixture_psf([0.8, 0.2], [1.5, 3.0], size)
     return PsfInput(image=img, mog=fit_psf_mog(img, k_fit), mog_exact=exact)
 
 
-def config2_psfs(n=64, seed=22, size=64, k_fit=3, fit=True):
+def psf_set(n=64, seed=22, size=64, k_fit=3, fit=True):
     """``n`` PSFs: a core 0.8 N(s) + 0.2 N(2 s) with s uniform in 1.2-2.5 px,
     plus Moffat (beta = 3) wings at weight 0.05 whose FWHM equals that of the
     N(2 s) core component (alpha = 4.62 s); each sampled at pixel centres on a
