@@ -695,6 +695,24 @@ def extra_per_galaxy(tables, psf, device, n=2000):
             "note": "one mog_render_batch call per 64x64 galaxy of the fixed-size distribution"}
 
 
+def trace_episode(tr, keys, before=4):
+    """The micro-batch that took longest from admission to completion, the
+    ones admitted just before it, and the largest gap between admissions."""
+    import numpy as np
+    if len(tr) == 0:
+        return None
+    col = {k: i for i, k in enumerate(keys)}
+    tr = tr[np.argsort(tr[:, col["admit_ms"]], kind="stable")]
+    span = tr[:, col["done_ms"]] - tr[:, col["admit_ms"]]
+    w = int(np.argmax(span))
+    rows = tr[max(0, w - before):w + 1]
+    gaps = np.diff(tr[:, col["admit_ms"]])
+    return {"columns": list(keys), "rows": [[round(float(v), 3) for v in r] for r in rows],
+            "admission_to_done_ms": round(float(span[w]), 3),
+            "max_admission_gap_ms": round(float(gaps.max()), 3) if len(gaps) else 0.0,
+            "batches_over_5ms_device": int((tr[:, col["device_ms"]] > 5.0).sum())}
+
+
 def extra_serving(tables, device, full_ms=500.0, half_window_s=10.0, single_ms=200.0, max_side=256,
                   kernel_bound=None):
     """1000 concurrent fits of 512 galaxies (Sersic, sizes as the mixed
@@ -730,6 +748,7 @@ def extra_serving(tables, device, full_ms=500.0, half_window_s=10.0, single_ms=2
         wall = time.perf_counter() - t0
         stats = srv.stats()
         breakdown = srv.timing()
+        episode = trace_episode(srv.trace(), Server.TRACE_KEYS)
         srv.close()
         return {"achieved_galaxies_per_s": float(gal.sum() / wall), "requests": len(reqs),
                 "window_s": float(times_s[-1]), "offered_galaxies_per_s": float(gal.sum() / max(times_s[-1], 1e-9)),
@@ -737,7 +756,7 @@ def extra_serving(tables, device, full_ms=500.0, half_window_s=10.0, single_ms=2
                 "p999_ms": float(np.percentile(lat, 99.9) * 1e3), "max_ms": float(lat.max() * 1e3),
                 "mean_ms": float(lat.mean() * 1e3), "micro_batches": stats["batches"] - 1,
                 "largest_micro_batch": stats["max_batch_galaxies"], "max_lanes_in_flight": stats["max_lanes_in_flight"],
-                "breakdown": breakdown}
+                "breakdown": breakdown, "slowest_batch": episode}
 
     cfg = dict(budget_bytes=16 << 30, lanes=4, max_batch_galaxies=32768)
     full = run(reqs, arrival_ms / 1e3, **cfg)

@@ -454,6 +454,21 @@ mog_status mog_server_stats(mog_server* server, int64_t* out);
  * Gathered since the server started or since the last call with reset != 0,
  * which clears them. */
 mog_status mog_server_timing(mog_server* server, double* out, int reset);
+/*
+ * Per micro-batch trace since the server started or since the last
+ * mog_server_timing call with reset != 0 (which also restarts the clock).
+ * Row i (MOG_TRACE_COLS doubles, in completion order): admission time [ms
+ * from the clock start], host launch time [ms, admission to the launch calls
+ * returning], device time [ms, CUDA events around the batch's work; -1 if it
+ * failed], completion time [ms from the clock start, when the completer saw
+ * the batch done], galaxies, lane index, galaxies still pending after the
+ * admission, lanes busy once the batch's lane was taken.  Copies the first
+ * min(max_rows, available) rows into out (host, max_rows * MOG_TRACE_COLS
+ * doubles; may be null when max_rows = 0) and sets *rows to the number
+ * available.  MOG_ERR_ARG for a null server or rows, or max_rows < 0.
+ */
+enum { MOG_TRACE_COLS = 8 };
+mog_status mog_server_trace(mog_server* server, double* out, int64_t max_rows, int64_t* rows);
 /* Finishes pending work (up to 60 s) and releases the server. */
 mog_status mog_server_destroy(mog_server* server);
 

@@ -37,8 +37,9 @@ EXPORTED = (
     "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
     "mog_create_eigen_psf", "mog_render_batch_ex", "mog_render_backward_ex", "mog_fit_psf_mixture",
     "mog_render_batch_host", "mog_measure_pipe_rates", "mog_server_inject_fault", "mog_check_wait_timeout",
-    "mog_set_launch_shape", "mog_chi2_gradient", "mog_server_timing",
+    "mog_set_launch_shape", "mog_chi2_gradient", "mog_server_timing", "mog_server_trace",
 )
+MOG_TRACE_COLS = 8
 MOG_NOALLOC_MAX_GALAXIES = 16384
 
 
@@ -118,6 +119,7 @@ def _load():
         "mog_set_launch_shape": ([VP, I, I, I, I, I], I),
         "mog_chi2_gradient": ([VP, P(mog_batch), VP, VP, VP, VP, VP, VP], I),
         "mog_server_timing": ([VP, P(ctypes.c_double), I], I),
+        "mog_server_trace": ([VP, P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_int64)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

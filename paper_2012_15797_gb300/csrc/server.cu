@@ -229,6 +229,8 @@ struct mog_server {
     // launch calls returned; device events around its work
     mog::Clock::time_point t_admit, t_launched;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t backlog = 0;   // galaxies left pending after this admission
+    int busy_at_admit = 0; // lanes busy once this one was taken
   };
   std::vector<Lane> lanes;
   // queues
@@ -250,6 +252,10 @@ struct mog_server {
   // per micro-batch: host launch time and device time; per request: queue
   // wait (submission to admission) and service (admission to results) [ms]
   std::vector<double> t_launch, t_device, t_queue, t_service;
+  // per micro-batch trace rows (MOG_TRACE_COLS values each), times from t0
+  std::vector<double> trace;
+  mog::Clock::time_point t0 = mog::Clock::now();
+  int64_t pending_galaxies = 0;
 };
 
 namespace mog {
@@ -379,6 +385,7 @@ void scheduler(mog_server* S) {
       g += r->count;
       pix += rpix;
       take.push_back(r);
+      S->pending_galaxies -= r->count;
       S->pending.pop_front();
       if (S->cfg.max_batch_galaxies <= 0) break;   // one request per launch
     }
@@ -405,6 +412,8 @@ void scheduler(mog_server* S) {
     int inflight = 0;
     for (auto& l : S->lanes) inflight += l.busy;
     if (inflight > S->max_inflight) S->max_inflight = inflight;
+    L->backlog = S->pending_galaxies;
+    L->busy_at_admit = inflight;
     lk.unlock();
     // fill staging (outside the lock); an injected allocation failure stands
     // in for a failing cudaHostAlloc, an injected launch failure for a
@@ -486,6 +495,14 @@ void completer(mog_server* S) {
     std::unique_lock<std::mutex> lk(S->mu);
     S->t_launch.push_back(std::chrono::duration<double, std::milli>(L.t_launched - L.t_admit).count());
     if (dev_ms >= 0.0f) S->t_device.push_back(dev_ms);
+    {
+      using ms = std::chrono::duration<double, std::milli>;
+      const double row[MOG_TRACE_COLS] = {ms(L.t_admit - S->t0).count(), ms(L.t_launched - L.t_admit).count(),
+                                          (double)dev_ms, ms(now - S->t0).count(), (double)g,
+                                          (double)(&L - S->lanes.data()), (double)L.backlog,
+                                          (double)L.busy_at_admit};
+      S->trace.insert(S->trace.end(), row, row + MOG_TRACE_COLS);
+    }
     for (auto& r : L.reqs) {
       S->t_queue.push_back(std::chrono::duration<double, std::milli>(r->admitted - r->submitted).count());
       S->t_service.push_back(std::chrono::duration<double, std::milli>(now - r->admitted).count());
@@ -639,6 +656,7 @@ mog_status mog_server_submit(mog_server* S, const mog_request* req, uint64_t* ti
   r->chi2 = req->chi2;
   r->submitted = Clock::now();
   S->requests[r->ticket] = r;
+  S->pending_galaxies += r->count;
   S->pending.push_back(r);
   *ticket = r->ticket;
   S->cv_sched.notify_one();
@@ -711,6 +729,20 @@ mog_status mog_server_timing(mog_server* S, double* out, int reset) {
     out[3 * k + 2] = n ? c[n - 1] : 0.0;
     if (reset) v[k]->clear();
   }
+  if (reset) {
+    S->trace.clear();
+    S->t0 = mog::Clock::now();
+  }
+  return MOG_OK;
+}
+
+mog_status mog_server_trace(mog_server* S, double* out, int64_t max_rows, int64_t* rows) {
+  if (!S || !rows || max_rows < 0 || (max_rows > 0 && !out)) return MOG_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  const int64_t n = (int64_t)S->trace.size() / MOG_TRACE_COLS;
+  const int64_t k = n < max_rows ? n : max_rows;
+  if (k > 0) std::copy(S->trace.begin(), S->trace.begin() + k * MOG_TRACE_COLS, out);
+  *rows = n;
   return MOG_OK;
 }
 

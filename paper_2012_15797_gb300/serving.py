@@ -111,6 +111,24 @@ class Server:
         keys = ("launch_host", "device", "queue_wait", "service")
         return {k: {"p50_ms": out[3 * i], "p99_ms": out[3 * i + 1], "max_ms": out[3 * i + 2]} for i, k in enumerate(keys)}
 
+    TRACE_KEYS = ("admit_ms", "launch_host_ms", "device_ms", "done_ms", "galaxies", "lane", "backlog_galaxies",
+                  "lanes_busy")
+
+    def trace(self):
+        """Per micro-batch rows (completion order) since the server started
+        or the last ``timing(reset=True)``: an (n, 8) float64 array with
+        columns ``TRACE_KEYS``."""
+        lib = capi.library()
+        n = ctypes.c_int64()
+        capi._check(self.renderer.ctx, lib.mog_server_trace(self.handle, None, 0, ctypes.byref(n)))
+        out = np.zeros((max(n.value, 0), capi.MOG_TRACE_COLS), dtype=np.float64)
+        if n.value:
+            got = ctypes.c_int64()
+            capi._check(self.renderer.ctx, lib.mog_server_trace(
+                self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value, ctypes.byref(got)))
+            out = out[:min(n.value, got.value)]
+        return out
+
     def close(self):
         if self.handle is not None:
             capi.library().mog_server_destroy(self.handle)

@@ -108,3 +108,31 @@ def test_admission_by_memory(gpu_renderer, setup):
     for (g1, c1), (g2, c2) in zip(ref, out):
         np.testing.assert_array_equal(g1, g2)
         np.testing.assert_array_equal(c1, c2)
+
+
+def test_trace_rows_account_for_every_batch(gpu_renderer, setup):
+    """The per micro-batch trace has one row per batch, its galaxies add up
+    to the requests', its times are ordered (admission <= completion) and a
+    timing reset clears it."""
+    from paper_2012_15797_gb300.serving import Server
+    fits, state, reqs = setup
+    srv = Server(gpu_renderer, budget_bytes=1 << 30, lanes=2, max_batch_galaxies=512)
+    for st in state:
+        srv.add_fit(**st)
+    tickets, keeps = srv.replay(reqs, np.arange(len(reqs)) * 2e-4)
+    srv.wait_replayed(tickets, keeps)
+    stats = srv.stats()
+    tr = srv.trace()
+    assert tr.shape == (stats["batches"], len(Server.TRACE_KEYS))
+    col = {k: i for i, k in enumerate(Server.TRACE_KEYS)}
+    assert int(tr[:, col["galaxies"]].sum()) == sum(len(q[2]) for q in reqs)
+    assert np.all(tr[:, col["admit_ms"]] >= 0)
+    assert np.all(tr[:, col["done_ms"]] >= tr[:, col["admit_ms"]])
+    assert np.all(tr[:, col["device_ms"]] > 0)
+    assert np.all(tr[:, col["launch_host_ms"]] >= 0)
+    assert set(np.unique(tr[:, col["lane"]]).astype(int)) <= {0, 1}
+    assert np.all((tr[:, col["lanes_busy"]] >= 1) & (tr[:, col["lanes_busy"]] <= 2))
+    assert np.all(tr[:, col["backlog_galaxies"]] >= 0)
+    srv.timing(reset=True)
+    assert srv.trace().shape[0] == 0
+    srv.close()
