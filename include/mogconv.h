@@ -339,11 +339,12 @@ mog_status mog_render_backward_ex(mog_ctx* ctx, const mog_batch* batch, const fl
  * batch (batch->size_mask, or all), times that bucket's render kernel alone
  * over every transform schedule (schedules 0 and 1: radix schedules of its
  * FFTs, 32 = 8*4 or 8*2*2, 64 = 8*8 or 8*4*2, 128 = 8*8*2 or 8*4*4,
- * 256 = 8*8*4 or 8*4*8; for 64 x 64 also schedule 2: one warp per galaxy
- * with the 64-point transforms in registers) x every
+ * 256 = 8*8*4 or 8*4*8; schedule 2: for 64 x 64 one warp per galaxy
+ * with the 64-point transforms in registers, for 128 x 128 8*8*2 with the
+ * radix-2 pass exchanged by warp shuffles instead of shared memory) x every
  * launch shape (CTAs per SM from 1 to what fits x work-queue chunk of 1..32
  * galaxies) with CUDA events, `reps` renders per choice, and keeps the
- * fastest in the context for later calls (the second schedule applies to the
+ * fastest in the context for later calls (schedules 1 and 2 apply to the
  * plain render; the Lanczos and eigen-PSF variants keep the first).  With
  * several sizes in the batch it then times the whole render with the size
  * kernels forked onto parallel streams and one after the other, and keeps the
@@ -360,7 +361,7 @@ enum { MOG_AUTOTUNE_REPORT = 2 * 4 * 3 + 1 };
  * Sets a launch shape by hand (as mog_autotune would keep it): direction
  * dir (0 render, 1 adjoint), patch side n, CTAs per SM (0 = as many as fit,
  * larger values are clamped to that), work-queue chunk (1..1024 galaxies),
- * transform schedule (0 or 1, and 2 for n = 64, as listed for mog_autotune;
+ * transform schedule (0 or 1, and 2 for n = 64 and 128, as listed for mog_autotune;
  * the adjoint has schedule 0 only).  Synchronous; MOG_ERR_ARG for values
  * outside these.
  */

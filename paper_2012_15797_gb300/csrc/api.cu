@@ -742,7 +742,7 @@ mog_status mog_set_launch_shape(mog_ctx* ctx, int dir, int n, int ctas_per_sm, i
   if ((dir != 0 && dir != 1) || b < 0 || ctas_per_sm < 0 || ctas_per_sm > 64 || chunk < 1 || chunk > 1024 ||
       sched < 0 || (b >= 0 && sched >= schedules_of(n)) || (dir == 1 && sched != 0))
     return fail(ctx, MOG_ERR_ARG, "launch shape: dir 0/1, side 32..256, 0..64 CTAs per SM, chunk 1..1024, "
-                                  "schedule 0..1 (64: 0..2; adjoint: 0)");
+                                  "schedule 0..1 (64 and 128: 0..2; adjoint: 0)");
   LaunchShape& t = dir == 0 ? ctx->tune_fwd[b] : ctx->tune_bwd[b];
   t.ctas_per_sm = ctas_per_sm;
   t.chunk = chunk;

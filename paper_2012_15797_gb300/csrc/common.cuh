@@ -177,11 +177,16 @@ template <> struct Radix<32, 1> { static constexpr int P = 3; static constexpr i
 template <> struct Radix<64, 1> { static constexpr int P = 3; static constexpr int r[3] = {8, 4, 2}; };
 template <> struct Radix<128, 1> { static constexpr int P = 3; static constexpr int r[3] = {8, 4, 4}; };
 template <> struct Radix<256, 1> { static constexpr int P = 3; static constexpr int r[3] = {8, 4, 8}; };
+// N = 128, third schedule: 8 x 8 x 2 with the radix-2 pass done across lane
+// pairs by warp shuffles instead of a shared-memory exchange (shfl_last).
+template <> struct Radix<128, 2> { static constexpr int P = 3; static constexpr int r[3] = {8, 8, 2}; };
+template <int N, int V>
+__host__ __device__ constexpr bool shfl_last() { return N == 128 && V == 2; }
 constexpr int SCHEDULES = 2;
-// Transform schedules per patch side: the two radix schedules, and for
-// N = 64 a third, one warp per galaxy with register-resident 64-point
-// transforms (render_fwd64w.cu).
-__host__ __device__ constexpr int schedules_of(int n) { return n == 64 ? 3 : SCHEDULES; }
+// Transform schedules per patch side: the two radix schedules; for N = 64 a
+// third, one warp per galaxy with register-resident 64-point transforms
+// (render_fwd64w.cu); for N = 128 a third, the shuffle radix-2 pass.
+__host__ __device__ constexpr int schedules_of(int n) { return (n == 64 || n == 128) ? 3 : SCHEDULES; }
 
 // Work rows hold one length-N transform each.  N = 32, 64: index map
 // i + i/8 into rows padded to N + N/8 float2, which spreads the stride-8
@@ -293,14 +298,53 @@ __device__ __forceinline__ void first_pass_load(const float2* buf, int j, float2
   for (int m = 0; m < 8; ++m) v[m] = swz_xor<N>() ? buf[swz<N>(j + m * TPF)] : src[m * TPF + ((m * TPF) >> 3)];
 }
 
+// The radix-2 pass of a 128-point transform across lane pairs (shfl_last).
+// After the radix-8 pass at sub-length 8, lane j of the 16 holds elements
+// e = 64 (j >> 3) + (j & 7) + 8 m (m = 0..7), so lanes j and j ^ 8 hold the
+// two inputs e and e + 64 of butterflies b = (j & 7) + 8 m.  Each lane sends
+// the four inputs its partner combines (the lower lane keeps m = 0..3, the
+// upper m = 4..7) and computes its four butterflies: out[b] = x0 + t x1,
+// out[b + 64] = x0 - t x1, t = w_128^b (conjugated for S < 0), from tw =
+// w_128^b, b < 64.  Result: v[i] = out[b_i], v[i + 4] = out[b_i + 64],
+// b_i = (j & 7) + 8 (i + 4 [j >= 8]) (shfl_out_index).
+template <int S>
+__device__ __forceinline__ void shfl_radix2_128(int j, const float2* tw, float2* v) {
+  const bool up = (j & 8) != 0;
+  float2 r[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 snd = up ? v[i] : v[4 + i];
+    r[i].x = __shfl_xor_sync(0xffffffffu, snd.x, 8);
+    r[i].y = __shfl_xor_sync(0xffffffffu, snd.y, 8);
+  }
+  const int base = (j & 7) + (up ? 32 : 0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 x0 = up ? r[i] : v[i];
+    const float2 x1 = up ? v[4 + i] : r[i];
+    const float2 t = tw[base + 8 * i];
+    const float2 y = (S > 0) ? cmul(x1, t) : cmulc(x1, t);
+    v[i] = padd(x0, y);
+    v[4 + i] = psub(x0, y);
+  }
+}
+
+// Element index of v[k] after shfl_radix2_128.
+__device__ __forceinline__ int shfl_out_index(int j, int k) {
+  return (j & 7) + 8 * ((k & 3) + ((j & 8) ? 4 : 0)) + 64 * (k >> 2);
+}
+
 // Passes after the first of a length-N FFT held in work row `w` (sign S);
 // the result of the last pass is left in v, value q R + m at output index
-// stockham_out_index<N, R>(j, N / R, q, m) with R = LastPass<N>::R.
+// stockham_out_index<N, R>(j, N / R, q, m) with R = LastPass<N>::R
+// (shfl_last schedules: v[k] at shfl_out_index(j, k)).
 template <int N, int S, int V = 0>
 __device__ __forceinline__ void fft_rest(float2* w, int j, const float2* tw1, const float2* tw2, float2* v) {
   constexpr int R1 = Radix<N, V>::r[1];
   stockham_load<N, R1, S>(w, j, tw1, v);
-  if constexpr (Radix<N, V>::P == 3) {
+  if constexpr (shfl_last<N, V>()) {
+    shfl_radix2_128<S>(j, tw2, v);
+  } else if constexpr (Radix<N, V>::P == 3) {
     constexpr int R2 = Radix<N, V>::r[2];
     __syncwarp();
     stockham_store<N, R1>(w, j, 8, v);

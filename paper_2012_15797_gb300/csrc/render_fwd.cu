@@ -440,13 +440,16 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
         // here without an exchange: Z_p[f] = A + iB and Z_p[N-f] = conj(A) +
         // i conj(B) feed the row transform of pair p (any two real rows can
         // share one complex transform).
+        // (the shuffle schedule leaves rows p and p + N/2 in v[i], v[i + 4])
         constexpr int R = LastPass<N, V>::R, NS = LastPass<N, V>::NS;
+        constexpr bool SH = shfl_last<N, V>();
 #pragma unroll
-        for (int q = 0; q < 8 / R; ++q)
+        for (int q = 0; q < (SH ? 1 : 8 / R); ++q)
 #pragma unroll
-          for (int m = 0; m < R / 2; ++m) {
-            const float2 A = v[q * R + m], Bv = v[q * R + m + R / 2];
-            float2* row = WB + C::row(stockham_out_index<N, R>(j, NS, q, m));
+          for (int m = 0; m < (SH ? 4 : R / 2); ++m) {
+            const int klo = SH ? m : q * R + m, khi = SH ? m + 4 : q * R + m + R / 2;
+            const float2 A = v[klo], Bv = v[khi];
+            float2* row = WB + C::row(SH ? shfl_out_index(j, m) : stockham_out_index<N, R>(j, NS, q, m));
             if (col > 0) {
               row[swz<N>(col)] = make_float2(A.x - Bv.y, A.y + Bv.x);
               row[swz<N>(N - col)] = make_float2(A.x + Bv.y, Bv.x - A.y);
@@ -480,11 +483,12 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
         // row swap in pairs, so the 8 lanes that read pieces 2j (then 2j+1)
         // below touch 8 different bank groups.
         constexpr int R = LastPass<N, V>::R, NS = LastPass<N, V>::NS;
+        constexpr bool SH = shfl_last<N, V>();
 #pragma unroll
         for (int q = 0; q < 8 / R; ++q)
 #pragma unroll
           for (int m = 0; m < R; ++m) {
-            const int n = stockham_out_index<N, R>(j, NS, q, m);
+            const int n = SH ? shfl_out_index(j, q * R + m) : stockham_out_index<N, R>(j, NS, q, m);
             const int x = n ^ (((n >> 5) & 1) << 2);
             orow[x] = v[q * R + m].x;
             orow[N + x] = v[q * R + m].y;
@@ -542,8 +546,8 @@ static cudaError_t launch_fwd_mode(const RenderParams& p, int num_sms, int ctas_
   return cudaGetLastError();
 }
 
-// The second radix schedule is compiled for the plain render (phase shift,
-// constant PSFs) only; the other variants keep the first.
+// The second and third schedules are compiled for the plain render (phase
+// shift, constant PSFs) only; the other variants keep the first.
 template <int N>
 static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
   if (p.eigen)
@@ -551,6 +555,8 @@ static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_s
                      : launch_fwd_mode<N, false, true, 0>(p, num_sms, ctas_per_sm, s);
   if (p.lanczos) return launch_fwd_mode<N, true, false, 0>(p, num_sms, ctas_per_sm, s);
   if (N == 64 && p.sched == 2) return launch_render_fwd64w(p, num_sms, ctas_per_sm, s);
+  if constexpr (N == 128)
+    if (p.sched == 2) return launch_fwd_mode<N, false, false, 2>(p, num_sms, ctas_per_sm, s);
   return p.sched == 1 ? launch_fwd_mode<N, false, false, 1>(p, num_sms, ctas_per_sm, s)
                       : launch_fwd_mode<N, false, false, 0>(p, num_sms, ctas_per_sm, s);
 }
@@ -570,7 +576,8 @@ int render_fwd_max_ctas(int n, int sched) {
     case 32: return sched == 1 ? fwd_occupancy<32, false, false, 1>() : fwd_occupancy<32>();
     case 64: return sched == 2 ? render_fwd64w_max_ctas()
                   : sched == 1 ? fwd_occupancy<64, false, false, 1>() : fwd_occupancy<64>();
-    case 128: return sched == 1 ? fwd_occupancy<128, false, false, 1>() : fwd_occupancy<128>();
+    case 128: return sched == 2   ? fwd_occupancy<128, false, false, 2>()
+                     : sched == 1 ? fwd_occupancy<128, false, false, 1>() : fwd_occupancy<128>();
     case 256: return render_fwd256_max_ctas(sched);
     default: return 0;
   }

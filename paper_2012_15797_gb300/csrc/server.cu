@@ -431,6 +431,10 @@ void scheduler(mog_server* S) {
           L->st.offset[i] = off;
           off += (int64_t)sz[r->first + k] * sz[r->first + k];
         }
+        // staged: the request's parameter copy goes back to the allocator
+        // now, so a long stream of requests reuses heap pages instead of
+        // faulting in fresh ones
+        std::vector<float>().swap(r->params);
       }
       st = launch_batch(S, *L, g, pix);
     }
@@ -546,6 +550,13 @@ mog_status mog_server_create(mog_ctx* ctx, const mog_server_config* cfg, mog_ser
     return fail(ctx, MOG_ERR_NOMEM, "server: cannot reserve the %lld-byte budget", (long long)cfg->budget_bytes);
   }
   S->lanes.resize(cfg->lanes);
+  // room for the timing records of a long window without regrowing them
+  // under the lock
+  S->t_launch.reserve(1 << 16);
+  S->t_device.reserve(1 << 16);
+  S->t_queue.reserve(1 << 18);
+  S->t_service.reserve(1 << 18);
+  S->trace.reserve((size_t)MOG_TRACE_COLS << 16);
   for (auto& L : S->lanes) {
     cudaError_t e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);

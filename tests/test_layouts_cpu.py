@@ -11,6 +11,7 @@ once; and, by a model of the shared-memory banks (32 banks of 4 bytes; an
 make every pass pattern of a 128- or 256-point transform take the minimum
 number of wavefronts, which the i + i/8 map does not."""
 
+import math
 import os
 import re
 from collections import defaultdict
@@ -168,3 +169,60 @@ def test_adjoint_untangle_writes_spread_over_the_banks():
                 f, j = divmod(w * 32 + lane, tpf)
                 addrs.append(2 * ((j + tpf * i) * wsa + swz(n, f)))
             assert wavefronts(addrs, 2) == 2
+
+
+def shfl_out_index(j, k):
+    return (j & 7) + 8 * ((k & 3) + (4 if j & 8 else 0)) + 64 * (k >> 2)
+
+
+def _dft(v, sign):
+    r = len(v)
+    return [sum(v[m] * complex(math.cos(2 * math.pi * m * k / r), sign * math.sin(2 * math.pi * m * k / r))
+                for m in range(r)) for k in range(r)]
+
+
+def test_shuffle_schedule_128_is_the_dft_and_pairs_rows():
+    """The third 128-point schedule (8 x 8 x 2, the radix-2 pass across lane
+    pairs j, j ^ 8 by shuffles), run as the kernel runs it, lane by lane: its
+    outputs, placed by shfl_out_index, are the length-128 inverse DFT; and
+    the row pairs p, p + 64 it leaves in one lane (v[i], v[i + 4]) cover
+    [0, 64) once."""
+    import numpy as np
+    common = open(os.path.join(CSRC, "common.cuh")).read()
+    assert "return (j & 7) + 8 * ((k & 3) + ((j & 8) ? 4 : 0)) + 64 * (k >> 2);" in common
+    assert ("template <> struct Radix<128, 2> { static constexpr int P = 3; "
+            "static constexpr int r[3] = {8, 8, 2}; };") in common
+    n, tpf = 128, 16
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    w = lambda e: complex(math.cos(2 * math.pi * e / n), math.sin(2 * math.pi * e / n))   # w_128^e, sign +1
+    buf = [0j] * n
+    for j in range(tpf):                       # pass 1 (sub-length 1): x[j + 16 m] -> slots 8 j + k
+        y = _dft([x[j + tpf * m] for m in range(8)], +1)
+        for k in range(8):
+            buf[8 * j + k] = y[k]
+    v = {}
+    for j in range(tpf):                       # pass 2 (radix 8 at sub-length 8), kept in registers
+        vals = [buf[j + 16 * m] * (w(m * (j & 7) * 2) if m else 1) for m in range(8)]
+        v[j] = _dft(vals, +1)
+        for k in range(8):
+            assert stockham_out_index(n, 8, j, 8, 0, k) == 64 * (j >> 3) + (j & 7) + 8 * k
+    out = {}
+    for j in range(tpf):                       # pass 3: lanes j and j ^ 8 exchange four values each
+        up = bool(j & 8)
+        recv = [v[j ^ 8][i] if (j ^ 8) & 8 else v[j ^ 8][4 + i] for i in range(4)]
+        res = [0j] * 8
+        for i in range(4):
+            x0 = recv[i] if up else v[j][i]
+            x1 = v[j][4 + i] if up else recv[i]
+            t = w((j & 7) + (32 if up else 0) + 8 * i)
+            res[i], res[4 + i] = x0 + t * x1, x0 - t * x1
+        for k in range(8):
+            out[shfl_out_index(j, k)] = res[k]
+    assert sorted(out) == list(range(n))
+    ref = np.fft.ifft(x) * n
+    got = np.array([out[e] for e in range(n)])
+    assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
+    rows = [shfl_out_index(j, i) for j in range(tpf) for i in range(4)]
+    assert all(shfl_out_index(j, i + 4) == shfl_out_index(j, i) + 64 for j in range(tpf) for i in range(4))
+    assert sorted(rows) == list(range(64))

@@ -13,7 +13,7 @@ from workloads import fixed_galaxies_64, mixed_galaxies
 
 pytestmark = pytest.mark.gpu
 
-CASES = [(32, 0), (32, 1), (64, 0), (64, 1), (64, 2), (128, 0), (128, 1), (256, 0), (256, 1)]
+CASES = [(32, 0), (32, 1), (64, 0), (64, 1), (64, 2), (128, 0), (128, 1), (128, 2), (256, 0), (256, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -75,6 +75,6 @@ def test_warp_kernel_sampled_fixed_size_batch_and_add_mode(sched_renderer, table
 def test_launch_shape_arguments_checked(sched_renderer):
     from paper_2012_15797_gb300 import capi
     for bad in [(2, 64, 0, 8, 0), (0, 48, 0, 8, 0), (0, 64, 0, 0, 0), (0, 64, 0, 8, 3), (0, 32, 0, 8, 2),
-                (1, 64, 0, 8, 1)]:
+                (0, 256, 0, 8, 2), (0, 128, 0, 8, 3), (1, 64, 0, 8, 1), (1, 128, 0, 8, 2)]:
         with pytest.raises(capi.MogError):
             capi.mog_set_launch_shape(sched_renderer.ctx, *bad)
