@@ -695,6 +695,35 @@ def extra_per_galaxy(tables, psf, device, n=2000):
             "note": "one mog_render_batch call per 64x64 galaxy of the fixed-size distribution"}
 
 
+def host_cpu_snapshot():
+    """Process CPU time, context switches and (where the cgroup exposes
+    them) CPU-quota throttling counters, to tell host-side stalls apart."""
+    import resource
+    ru = resource.getrusage(resource.RUSAGE_SELF)
+    snap = {"cpu_s": ru.ru_utime + ru.ru_stime, "involuntary_switches": ru.ru_nivcsw,
+            "voluntary_switches": ru.ru_nvcsw}
+    try:
+        with open("/sys/fs/cgroup/cpu.stat") as f:
+            for line in f:
+                k, v = line.split()
+                if k in ("nr_throttled", "throttled_usec", "nr_periods"):
+                    snap[k] = int(v)
+    except (OSError, ValueError):
+        pass
+    return snap
+
+
+def host_cpu_delta(a, b, wall_s):
+    d = {k: b[k] - a[k] for k in a if k in b}
+    d["cpu_cores_busy"] = d.pop("cpu_s") / max(wall_s, 1e-9)
+    try:
+        with open("/sys/fs/cgroup/cpu.max") as f:
+            d["cgroup_cpu_max"] = f.read().strip()
+    except OSError:
+        pass
+    return d
+
+
 def trace_episode(tr, keys, before=4):
     """The micro-batch that took longest from admission to completion, the
     ones admitted just before it, and the largest gap between admissions."""
@@ -742,10 +771,12 @@ def extra_serving(tables, device, full_ms=500.0, half_window_s=10.0, single_ms=2
         t, k = srv.replay(reqs[:warm], np.zeros(warm))
         srv.wait_replayed(t, k)
         srv.timing(reset=True)
+        h0 = host_cpu_snapshot()
         t0 = time.perf_counter()
         t, k = srv.replay(reqs, times_s)
         lat = srv.wait_replayed(t, k)
         wall = time.perf_counter() - t0
+        host = host_cpu_delta(h0, host_cpu_snapshot(), wall)
         stats = srv.stats()
         breakdown = srv.timing()
         episode = trace_episode(srv.trace(), Server.TRACE_KEYS)
@@ -756,7 +787,7 @@ def extra_serving(tables, device, full_ms=500.0, half_window_s=10.0, single_ms=2
                 "p999_ms": float(np.percentile(lat, 99.9) * 1e3), "max_ms": float(lat.max() * 1e3),
                 "mean_ms": float(lat.mean() * 1e3), "micro_batches": stats["batches"] - 1,
                 "largest_micro_batch": stats["max_batch_galaxies"], "max_lanes_in_flight": stats["max_lanes_in_flight"],
-                "breakdown": breakdown, "slowest_batch": episode}
+                "breakdown": breakdown, "slowest_batch": episode, "host": host}
 
     cfg = dict(budget_bytes=16 << 30, lanes=4, max_batch_galaxies=32768)
     full = run(reqs, arrival_ms / 1e3, **cfg)

@@ -231,6 +231,8 @@ struct mog_server {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t backlog = 0;   // galaxies left pending after this admission
     int busy_at_admit = 0; // lanes busy once this one was taken
+    mog_server* owner = nullptr;
+    int idx = 0;
   };
   std::vector<Lane> lanes;
   // queues
@@ -256,6 +258,9 @@ struct mog_server {
   std::vector<double> trace;
   mog::Clock::time_point t0 = mog::Clock::now();
   int64_t pending_galaxies = 0;
+  // per lane: set by the stream's host callback once the micro-batch's work
+  // is done (lane_done_cb), read by the completer
+  std::unique_ptr<std::atomic<int>[]> fired;
 };
 
 namespace mog {
@@ -288,6 +293,18 @@ bool lane_reserve(mog_server::Lane& L, int64_t g) {
 }
 
 // Launches one micro-batch on lane L (scheduler thread).
+// Host function enqueued after a micro-batch's work (cudaLaunchHostFunc):
+// marks the lane done and wakes the completer.  Runs on a CUDA driver
+// thread, so it calls no CUDA API; taking the mutex between the store and
+// the notification orders it against the completer's check-then-wait.
+void CUDART_CB lane_done_cb(void* arg) {
+  auto* L = static_cast<mog_server::Lane*>(arg);
+  mog_server* S = L->owner;
+  S->fired[L->idx].store(1, std::memory_order_release);
+  { std::lock_guard<std::mutex> lk(S->mu); }
+  S->cv_comp.notify_one();
+}
+
 int launch_batch(mog_server* S, mog_server::Lane& L, int64_t g, int64_t pix) {
   mog_ctx* ctx = S->ctx;
   unsigned char* p = L.block;
@@ -347,7 +364,8 @@ int launch_batch(mog_server* S, mog_server::Lane& L, int64_t g, int64_t pix) {
   st = backward_with(ctx, &L.ws, &mb, b.model, b.grads, s);
   if (st != MOG_OK) return st;
   if (cudaMemcpyAsync(L.st.results, b.grads, sizeof(float) * 7 * g, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaEventRecord(L.ev1, s) != cudaSuccess || cudaEventRecord(L.done, s) != cudaSuccess)
+      cudaEventRecord(L.ev1, s) != cudaSuccess || cudaEventRecord(L.done, s) != cudaSuccess ||
+      cudaLaunchHostFunc(s, lane_done_cb, &L) != cudaSuccess)
     return MOG_ERR_CUDA;
   return MOG_OK;
 }
@@ -405,6 +423,7 @@ void scheduler(mog_server* S) {
     L->block = S->arena.alloc(bytes);
     L->block_bytes = bytes;
     L->busy = true;
+    S->fired[L->idx].store(0, std::memory_order_relaxed);
     L->reqs = take;
     L->galaxies = g;
     L->t_admit = Clock::now();
@@ -454,12 +473,17 @@ void completer(mog_server* S) {
     mog_server::Lane* ready = nullptr;
     {
       std::unique_lock<std::mutex> lk(S->mu);
+      // woken by lane_done_cb; every 2 ms the lanes' events are also
+      // queried, so a batch whose callback did not run (its stream failed)
+      // still completes
+      bool poll = false;
       for (;;) {
         bool any = false;
         for (auto& L : S->lanes) {
           if (!L.busy || !L.launched) continue;
           any = true;
-          if (L.status != MOG_OK || cudaEventQuery(L.done) == cudaSuccess) {
+          if (L.status != MOG_OK || S->fired[L.idx].load(std::memory_order_acquire) ||
+              (poll && cudaEventQuery(L.done) != cudaErrorNotReady)) {
             ready = &L;
             break;
           }
@@ -468,13 +492,7 @@ void completer(mog_server* S) {
         bool launching = false;
         for (auto& L : S->lanes) launching |= L.busy && !L.launched;
         if (S->stop && !any && !launching) return;
-        if (!any) {
-          S->cv_comp.wait_for(lk, std::chrono::milliseconds(5));
-        } else {
-          lk.unlock();
-          std::this_thread::sleep_for(std::chrono::microseconds(20));
-          lk.lock();
-        }
+        poll = S->cv_comp.wait_for(lk, std::chrono::milliseconds(any ? 2 : 5)) == std::cv_status::timeout;
       }
     }
     // results -> callers (lane is owned by this thread until freed)
@@ -550,6 +568,12 @@ mog_status mog_server_create(mog_ctx* ctx, const mog_server_config* cfg, mog_ser
     return fail(ctx, MOG_ERR_NOMEM, "server: cannot reserve the %lld-byte budget", (long long)cfg->budget_bytes);
   }
   S->lanes.resize(cfg->lanes);
+  S->fired.reset(new std::atomic<int>[cfg->lanes]);
+  for (int i = 0; i < cfg->lanes; ++i) {
+    S->fired[i].store(0);
+    S->lanes[i].owner = S;
+    S->lanes[i].idx = i;
+  }
   // room for the timing records of a long window without regrowing them
   // under the lock
   S->t_launch.reserve(1 << 16);
