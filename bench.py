@@ -724,6 +724,24 @@ def host_cpu_delta(a, b, wall_s):
     return d
 
 
+def trace_steady_rate(tr, keys, lo=0.1, hi=0.9):
+    """Galaxies per second completed while the cumulative completed count
+    goes from lo to hi of the total: the server's rate with the start-up
+    (lanes filling, micro-batches growing) and the drain left out."""
+    import numpy as np
+    if len(tr) < 4:
+        return None
+    col = {k: i for i, k in enumerate(keys)}
+    tr = tr[np.argsort(tr[:, col["done_ms"]], kind="stable")]
+    cum = np.cumsum(tr[:, col["galaxies"]])
+    a = int(np.searchsorted(cum, lo * cum[-1]))
+    b = int(np.searchsorted(cum, hi * cum[-1]))
+    if b <= a:
+        return None
+    dt = (tr[b, col["done_ms"]] - tr[a, col["done_ms"]]) / 1e3
+    return float((cum[b] - cum[a]) / dt) if dt > 0 else None
+
+
 def trace_episode(tr, keys, before=4):
     """The micro-batch that took longest from admission to completion, the
     ones admitted just before it, and the largest gap between admissions."""
@@ -779,9 +797,12 @@ def extra_serving(tables, device, full_ms=500.0, half_window_s=10.0, single_ms=2
         host = host_cpu_delta(h0, host_cpu_snapshot(), wall)
         stats = srv.stats()
         breakdown = srv.timing()
-        episode = trace_episode(srv.trace(), Server.TRACE_KEYS)
+        tr = srv.trace()
+        episode = trace_episode(tr, Server.TRACE_KEYS)
+        steady = trace_steady_rate(tr, Server.TRACE_KEYS)
         srv.close()
-        return {"achieved_galaxies_per_s": float(gal.sum() / wall), "requests": len(reqs),
+        return {"achieved_galaxies_per_s": float(gal.sum() / wall), "steady_galaxies_per_s": steady,
+                "requests": len(reqs),
                 "window_s": float(times_s[-1]), "offered_galaxies_per_s": float(gal.sum() / max(times_s[-1], 1e-9)),
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "p999_ms": float(np.percentile(lat, 99.9) * 1e3), "max_ms": float(lat.max() * 1e3),
@@ -806,6 +827,11 @@ def extra_serving(tables, device, full_ms=500.0, half_window_s=10.0, single_ms=2
             "offered_load": full, "sustained_fraction_of_offered": cap / full["offered_galaxies_per_s"],
             "kernel_bound_galaxies_per_s": kernel_bound,
             "fraction_of_kernel_bound": (cap / kernel_bound) if kernel_bound else None,
+            "steady_fraction_of_kernel_bound": (full["steady_galaxies_per_s"] / kernel_bound)
+            if (kernel_bound and full["steady_galaxies_per_s"]) else None,
+            "capacity_note": "capacity = galaxies / wall time of the saturated window (start-up and drain "
+                             "included); steady = the rate while the middle 80% of its galaxies complete; "
+                             "the half load is half the former",
             "kernel_bound_note": "render + adjoint kernel time of the 200k mixed batch (one graph launch of the "
                                  "forward, one adjoint call): the galaxies per second the kernels allow",
             "half_capacity_load": half, "one_launch_per_request_at_half_load": single}
