@@ -26,19 +26,26 @@ class DeviceBatch:
         return {k: v.data_ptr() for k, v in self.tensors.items()}
 
     def size_mask(self):
-        return size_mask(self.sizes)
+        # computed once per batch: the sides do not change, and for batches of
+        # 10^5 galaxies recomputing it every call cost more host time than the
+        # render took on the device
+        m = self.__dict__.get("_size_mask")
+        if m is None:
+            m = self.__dict__["_size_mask"] = size_mask(self.sizes)
+        return m
+
+
+SIDES = (32, 64, 128, 256)
 
 
 def size_mask(sizes):
     """Bitmask of the patch sides present (bit b: N = 32 << b); 0 when a
     side is not one of them (the library then reports it)."""
-    m = 0
-    for n in np.unique(np.asarray(sizes)):
-        b = {32: 0, 64: 1, 128: 2, 256: 3}.get(int(n))
-        if b is None:
-            return 0
-        m |= 1 << b
-    return m
+    sizes = np.asarray(sizes)
+    hit = [bool(np.any(sizes == n)) for n in SIDES]
+    if sum(int(np.count_nonzero(sizes == n)) for n, h in zip(SIDES, hit) if h) != sizes.size:
+        return 0
+    return sum(1 << b for b, h in enumerate(hit) if h)
 
 
 def pack_offsets(sizes):
