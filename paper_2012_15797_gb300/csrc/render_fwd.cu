@@ -236,25 +236,16 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
   uint32_t psf_parity = 0, rec_parity = 0;   // rec_parity bit b: phase of record buffer b
   __syncthreads();
 
-  // Two CTA barriers per galaxy.  S_A, after the column transforms: every
-  // group has finished the previous galaxy's rows and this galaxy's column
-  // loads, so the pairing writes may fill every row (for N = 64 the column
-  // and row transforms share the work rows).  S3: every column has been
-  // transformed and the next galaxy's record, PSF spectrum and tables are
-  // ready: its set-up (stage) runs between S_A and S3, when this galaxy's
-  // record, spectrum, phase and component tables are no longer read (the
-  // rows use only the real-space table, patch pointer and term count, kept
-  // per record buffer).  A group runs from its rows into the next galaxy's
-  // columns without a barrier: until S_A it touches only its own work rows.
-  // The column phase's per-galaxy values, set by stage one galaxy ahead:
-  const float2* st_psf_g = nullptr;   // spectrum in global memory when not staged
-  int st_k_eig = 0;
-  const float* st_pc = nullptr;       // eigen-PSF coefficients
-  // stage(buf): thread 0 requests the record after it; every thread waits
-  // for the record in buffer buf (and a changed PSF spectrum) and fills the
-  // tables.  landed: every wait ended in time; work: landed and valid.
-  auto stage = [&](int buf, bool& landed_out, bool& work_out) {
+  // Three CTA barriers per galaxy (S2, S3 and, for N = 64, the work-row
+  // barrier).  There is none between galaxies: a group stores the two rows it
+  // transformed itself, so warps run on into the next galaxy's tables while
+  // others still store.  That is safe because every read of galaxy i's record,
+  // PSF spectrum, px/py/nyq tables and work rows by other warps is ordered
+  // before S3(i) or S2(i + 1), which the writer of galaxy i + 1's copies has
+  // passed, and the real-space tables alternate with the record buffers.
+  for (int buf = 0;; buf ^= 1) {
     const int pos = s_pos[buf];
+    if (pos < 0) break;
     if (tid == 0) {
       const int np = next_position();
       s_pos[buf ^ 1] = np;
@@ -370,133 +361,106 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
         }
       }
     }
-    landed_out = landed;
-    work_out = work;
-    st_psf_g = psf_g;
-    st_k_eig = k_eig;
-    st_pc = pc;
-  };
-
-  bool landed_n = true, work_n = false;
-  if (s_pos[0] >= 0) stage(0, landed_n, work_n);
-  if (__syncthreads_or(!landed_n)) {
-    if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
-    return;
-  }
-  for (int buf = 0;; buf ^= 1) {
-    if (s_pos[buf] < 0) break;
-    const bool work = work_n;   // uniform: set before a barrier every thread passed
-    const GalaxyRecord& r = rec[buf];
-    const float2* const psf_g = st_psf_g;
-    const int k_eig = st_k_eig;
-    const float* const pc = st_pc;
-    float2 v[8];
-    if (work) {
-      // ---- Steps 5-6: Fourier mixture times PSF spectrum and phase, in registers ----
-      const int nf = r.nf;
-      const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
-  #pragma unroll 1
-      for (int cc = 0; cc < CPG; ++cc) {
-        const int col = f + cc * C::GROUPS;   // column nu = col / N (column 0: nu = 0 and 1/2 packed)
-        {
-          // 8 bins per thread
-          const float nu = col * INV_N;
-          const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
-          const float omj = (float)j * INV_N;
-          // bins (2k, 2k+1) of the thread share packed f32x2 instructions
-          float2 q[4], s[4];
-          float qmin = 3.4e38f;
-  #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            // l = j + m TPF is below N/2 exactly for m < 4
-            const float om0 = omj + (float)(2 * k * TPF - (2 * k >= 4 ? N : 0)) * INV_N;
-            const float om1 = omj + (float)((2 * k + 1) * TPF - (2 * k + 1 >= 4 ? N : 0)) * INV_N;
-            q[k] = make_float2(fmaf(om0, fmaf(s22, om0, a1), a0), fmaf(om1, fmaf(s22, om1, a1), a0));
-            qmin = fminf(qmin, fminf(q[k].x, q[k].y));
-            s[k] = make_float2(0.0f, 0.0f);
-          }
-          for (int i = 0; i < nf; ++i) {
-            const float4 ac = s_fc[i];
-            if (!__any_sync(0xffffffffu, ac.z * qmin > NEGLIGIBLE_LOG2)) continue;
-            const float2 a2 = make_float2(ac.x, ac.y), c2 = make_float2(ac.z, ac.w);
-  #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const float2 e = __fmul2_rn(c2, q[k]);
-              s[k] = __ffma2_rn(a2, make_float2(ex2(e.x), ex2(e.y)), s[k]);
-            }
-          }
-          const float2 pxf = px[col];
-  #pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const int l = j + m * TPF;
-            float2 pv;
-            if constexpr (C::PSF_SMEM) pv = psf_hat[col * LS + l];
-            else pv = (EIG && k_eig) ? eigen_bin(psf_g, C::PSF_ELEMS, k_eig, pc, col * LS + l) : __ldg(psf_g + col * LS + l);
-            v[m] = cscale(cmul(pv, cmul(pxf, py[l])), (m & 1) ? s[m >> 1].y : s[m >> 1].x);
-          }
-        }
-        if (col == 0) {
-          // Pack the Hermitian parts of the nu = 0 and nu = 1/2 columns as
-          // re + i im.  The nu = 0 column is Hermitian in omega by construction
-          // (its self-conjugate bin l = N/2 keeps its real part); the nu = 1/2
-          // column is symmetrised from both signs of omega.
-  #pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            const int l = j + m * TPF;
-            const float2 dc = (l == N / 2) ? make_float2(v[m].x, 0.0f) : v[m];
-            const float2 a = nyq[l], b = nyq[(N - l) & (N - 1)];
-            const float2 hn = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
-            v[m] = make_float2(dc.x - hn.y, dc.y + hn.x);
-          }
-        }
-
-        // ---- Step 7a: inverse FFT of every column along omega ----
-        dft8<+1>(v);
-        if (cc > 0) __syncwarp();   // the group's loads of its previous column are done
-        first_pass_store<N>(wa, j, v);
-        __syncwarp();
-        fft_rest<N, +1, V>(wa, j, tw1, tw2, v);
-        if (cc == 0) __syncthreads();   // S_A: every group's work-row loads are done
-        {
-          // The last pass leaves rows n = j + q N/8 + m N/R of column f in this
-          // thread, so rows p and p + N/2 (outputs m and m + R/2, p < N/2) meet
-          // here without an exchange: Z_p[f] = A + iB and Z_p[N-f] = conj(A) +
-          // i conj(B) feed the row transform of pair p (any two real rows can
-          // share one complex transform).
-          // (the shuffle schedule leaves rows p and p + N/2 in v[i], v[i + 4])
-          constexpr int R = LastPass<N, V>::R, NS = LastPass<N, V>::NS;
-          constexpr bool SH = shfl_last<N, V>();
-  #pragma unroll
-          for (int q = 0; q < (SH ? 1 : 8 / R); ++q)
-  #pragma unroll
-            for (int m = 0; m < (SH ? 4 : R / 2); ++m) {
-              const int klo = SH ? m : q * R + m, khi = SH ? m + 4 : q * R + m + R / 2;
-              const float2 A = v[klo], Bv = v[khi];
-              float2* row = WB + C::row(SH ? shfl_out_index(j, m) : stockham_out_index<N, R>(j, NS, q, m));
-              if (col > 0) {
-                row[swz<N>(col)] = make_float2(A.x - Bv.y, A.y + Bv.x);
-                row[swz<N>(N - col)] = make_float2(A.x + Bv.y, Bv.x - A.y);
-              } else {
-                row[swz<N>(0)] = make_float2(A.x, Bv.x);
-                row[swz<N>(N / 2)] = make_float2(A.y, Bv.y);
-              }
-            }
-        }
-      }   // columns of this group
-    } else {
-      __syncthreads();   // S_A
-    }
-    // the next galaxy's set-up
-    landed_n = true;
-    work_n = false;
-    if (s_pos[buf ^ 1] >= 0) stage(buf ^ 1, landed_n, work_n);
-    // S3: every column has been transformed, the next galaxy's tables are complete
-    if (__syncthreads_or(!landed_n)) {
+    // S2: the tables are complete and every warp has stored the previous galaxy
+    if (__syncthreads_or(!landed)) {
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
       return;
     }
-    if (!work) continue;
-    const RealTerms& rt = rts[buf];
+    if (!work) continue;   // uniform once every wait has landed
+
+    // ---- Steps 5-6: Fourier mixture times PSF spectrum and phase, in registers ----
+    const int nf = r.nf;
+    const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
+    float2 v[8];
+#pragma unroll 1
+    for (int cc = 0; cc < CPG; ++cc) {
+      const int col = f + cc * C::GROUPS;   // column nu = col / N (column 0: nu = 0 and 1/2 packed)
+      {
+        // 8 bins per thread
+        const float nu = col * INV_N;
+        const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
+        const float omj = (float)j * INV_N;
+        // bins (2k, 2k+1) of the thread share packed f32x2 instructions
+        float2 q[4], s[4];
+        float qmin = 3.4e38f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          // l = j + m TPF is below N/2 exactly for m < 4
+          const float om0 = omj + (float)(2 * k * TPF - (2 * k >= 4 ? N : 0)) * INV_N;
+          const float om1 = omj + (float)((2 * k + 1) * TPF - (2 * k + 1 >= 4 ? N : 0)) * INV_N;
+          q[k] = make_float2(fmaf(om0, fmaf(s22, om0, a1), a0), fmaf(om1, fmaf(s22, om1, a1), a0));
+          qmin = fminf(qmin, fminf(q[k].x, q[k].y));
+          s[k] = make_float2(0.0f, 0.0f);
+        }
+        for (int i = 0; i < nf; ++i) {
+          const float4 ac = s_fc[i];
+          if (!__any_sync(0xffffffffu, ac.z * qmin > NEGLIGIBLE_LOG2)) continue;
+          const float2 a2 = make_float2(ac.x, ac.y), c2 = make_float2(ac.z, ac.w);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 e = __fmul2_rn(c2, q[k]);
+            s[k] = __ffma2_rn(a2, make_float2(ex2(e.x), ex2(e.y)), s[k]);
+          }
+        }
+        const float2 pxf = px[col];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int l = j + m * TPF;
+          float2 pv;
+          if constexpr (C::PSF_SMEM) pv = psf_hat[col * LS + l];
+          else pv = (EIG && k_eig) ? eigen_bin(psf_g, C::PSF_ELEMS, k_eig, pc, col * LS + l) : __ldg(psf_g + col * LS + l);
+          v[m] = cscale(cmul(pv, cmul(pxf, py[l])), (m & 1) ? s[m >> 1].y : s[m >> 1].x);
+        }
+      }
+      if (col == 0) {
+        // Pack the Hermitian parts of the nu = 0 and nu = 1/2 columns as
+        // re + i im.  The nu = 0 column is Hermitian in omega by construction
+        // (its self-conjugate bin l = N/2 keeps its real part); the nu = 1/2
+        // column is symmetrised from both signs of omega.
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int l = j + m * TPF;
+          const float2 dc = (l == N / 2) ? make_float2(v[m].x, 0.0f) : v[m];
+          const float2 a = nyq[l], b = nyq[(N - l) & (N - 1)];
+          const float2 hn = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+          v[m] = make_float2(dc.x - hn.y, dc.y + hn.x);
+        }
+      }
+
+      // ---- Step 7a: inverse FFT of every column along omega ----
+      dft8<+1>(v);
+      if (cc > 0) __syncwarp();   // the group's loads of its previous column are done
+      first_pass_store<N>(wa, j, v);
+      __syncwarp();
+      fft_rest<N, +1, V>(wa, j, tw1, tw2, v);
+      if constexpr (C::ALIAS_W) __syncthreads();   // every column's last loads are done
+      {
+        // The last pass leaves rows n = j + q N/8 + m N/R of column f in this
+        // thread, so rows p and p + N/2 (outputs m and m + R/2, p < N/2) meet
+        // here without an exchange: Z_p[f] = A + iB and Z_p[N-f] = conj(A) +
+        // i conj(B) feed the row transform of pair p (any two real rows can
+        // share one complex transform).
+        // (the shuffle schedule leaves rows p and p + N/2 in v[i], v[i + 4])
+        constexpr int R = LastPass<N, V>::R, NS = LastPass<N, V>::NS;
+        constexpr bool SH = shfl_last<N, V>();
+#pragma unroll
+        for (int q = 0; q < (SH ? 1 : 8 / R); ++q)
+#pragma unroll
+          for (int m = 0; m < (SH ? 4 : R / 2); ++m) {
+            const int klo = SH ? m : q * R + m, khi = SH ? m + 4 : q * R + m + R / 2;
+            const float2 A = v[klo], Bv = v[khi];
+            float2* row = WB + C::row(SH ? shfl_out_index(j, m) : stockham_out_index<N, R>(j, NS, q, m));
+            if (col > 0) {
+              row[swz<N>(col)] = make_float2(A.x - Bv.y, A.y + Bv.x);
+              row[swz<N>(N - col)] = make_float2(A.x + Bv.y, Bv.x - A.y);
+            } else {
+              row[swz<N>(0)] = make_float2(A.x, Bv.x);
+              row[swz<N>(N / 2)] = make_float2(A.y, Bv.y);
+            }
+          }
+      }
+    }   // columns of this group
+    __syncthreads();  // S3: every column has been transformed
 
     // ---- Step 7b: real inverse FFT of row pairs (prow, prow + N/2) along nu ----
     float* const dst = s_dst[buf];
@@ -554,11 +518,6 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
         store8(dst + yy * N + x0, o, p.accumulate != 0);
       }
     }   // row pairs of this group
-    if constexpr (LZ) {
-      // the y-convolution read other groups' rows: they are rewritten by the
-      // next galaxy's column transforms only after this barrier
-      if (s_nr[buf] > 0) __syncthreads();
-    }
   }
 }
 
