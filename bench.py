@@ -480,8 +480,14 @@ def extra_render_grad(tables, psf, device, steps, pk):
     chi2 = torch.empty(len(model), device=dev)
 
     def step():
-        # render, the loss gradient 2 ivar (model - data) and chi^2 per galaxy
-        # (mog_chi2_gradient), adjoint: every step in the library's kernels
+        # render with the loss (mog_render_chi2: the gradient 2 ivar (model -
+        # data) and chi^2 per galaxy, computed as the patches are stored),
+        # adjoint: every step in the library's kernels
+        r.render_chi2(bm, data, ivar, gpix, chi2)
+        r.render_backward(bm, gpix, gp)
+
+    def step_unfused():
+        # the same with the model written out and the loss as its own kernel
         r.render(bm, out)
         r.chi2_gradient(bm, out, data, ivar, gpix, chi2)
         r.render_backward(bm, gpix, gp)
@@ -489,8 +495,10 @@ def extra_render_grad(tables, psf, device, steps, pk):
     st = torch.cuda.current_stream()
     for _ in range(3):
         step()
+        step_unfused()
     r.sync_status()
     ms = _event_ms(step, steps, st)
+    ms_unfused = _event_ms(step_unfused, steps, st)
 
     def kernel_ms(fn):
         capi.mog_set_timing(r.ctx, True)
@@ -507,8 +515,10 @@ def extra_render_grad(tables, psf, device, steps, pk):
     wf, wb = algorithmic_work(model, tables, kpsf), adjoint_work(model, tables, kpsf)
     res = {"workload": "50000 galaxies as the fixed-size batch; loss = sum ivar (model - data)^2, data from "
                        "perturbed parameters + Gaussian noise sigma = 0.01 peak; gradients w.r.t. "
-                       "(flux, x, y, log r_e, e1, e2); step = render, mog_chi2_gradient, adjoint",
+                       "(flux, x, y, log r_e, e1, e2); step = mog_render_chi2 (render and loss in one pass), "
+                       "adjoint",
            "value": len(model) / (ms / 1e3), "unit": "patches rendered+grad/s", "ms_per_step": ms,
+           "ms_per_step_unfused": ms_unfused,
            "kernel_ms_forward": fwd_ms, "kernel_ms_adjoint": bwd_ms,
            "roofline": roofline(wb, bwd_ms, pk, "render_bwd_kernel<64>"),
            "roofline_forward_plus_adjoint_kernels": roofline(add_work(wf, wb), fwd_ms + bwd_ms, pk,

@@ -315,6 +315,27 @@ mog_status mog_chi2_gradient(mog_ctx* ctx, const mog_batch* batch, const float* 
                              const float* ivar, float* grad_pix, float* chi2, void* stream);
 
 /*
+ * Render and loss in one pass (the forward model of Section 2 followed by
+ * the chi-squared of mog_chi2_gradient, fused): the render kernels compare
+ * each model pixel with the data as they store it, so the model need not go
+ * through memory.  Per galaxy g:
+ *   grad_pix = 2 ivar[g] (model - data)   on the galaxy's patch
+ *   chi2[g]  = ivar[g] sum_pixels (model - data)^2
+ *   model    = the rendered patch          (optional: model may be NULL)
+ * The same values as mog_render_batch followed by mog_chi2_gradient, up to
+ * the order of the chi2 sum.  data, grad_pix, model: device float32 in the
+ * batch's patch layout (16-byte aligned; grad_pix, data and model distinct);
+ * ivar, chi2: device, one float per galaxy.  Phase shift, constant or
+ * eigen-PSFs, the first transform schedule.  A galaxy whose parameters are
+ * invalid or whose side is unsupported is skipped as by mog_render_batch
+ * (status MOG_ERR_DEVICE), its chi2 NaN.  Asynchronous on `stream`.
+ * Errors: MOG_ERR_ARG for a null data, ivar, grad_pix or chi2, or a
+ * misaligned buffer.
+ */
+mog_status mog_render_chi2(mog_ctx* ctx, const mog_batch* batch, const float* data, const float* ivar,
+                           float* grad_pix, float* chi2, float* model, void* stream);
+
+/*
  * Fits a k-component Gaussian mixture (1 <= k <= 4) to each of `count`
  * pixelized PSFs on the device: the mixture the real-space half convolves
  * with (Section 2, Step 4; the chi-squared fit of Section 1).  images: device

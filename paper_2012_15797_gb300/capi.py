@@ -37,7 +37,7 @@ EXPORTED = (
     "mog_server_replay_join", "mog_server_stats", "mog_server_destroy", "mog_render_batch_lanczos",
     "mog_create_eigen_psf", "mog_render_batch_ex", "mog_render_backward_ex", "mog_fit_psf_mixture",
     "mog_render_batch_host", "mog_measure_pipe_rates", "mog_server_inject_fault", "mog_check_wait_timeout",
-    "mog_set_launch_shape", "mog_chi2_gradient", "mog_server_timing", "mog_server_trace",
+    "mog_set_launch_shape", "mog_chi2_gradient", "mog_server_timing", "mog_server_trace", "mog_render_chi2",
 )
 MOG_TRACE_COLS = 8
 MOG_NOALLOC_MAX_GALAXIES = 16384
@@ -120,6 +120,7 @@ def _load():
         "mog_chi2_gradient": ([VP, P(mog_batch), VP, VP, VP, VP, VP, VP], I),
         "mog_server_timing": ([VP, P(ctypes.c_double), I], I),
         "mog_server_trace": ([VP, P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_int64)], I),
+        "mog_render_chi2": ([VP, P(mog_batch), VP, VP, VP, VP, VP, VP], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -289,6 +290,13 @@ def mog_autotune(ctx, batch, out_ptr, grad_out_ptr=0, grad_params_ptr=0, stream=
 def mog_set_launch_shape(ctx, direction, n, ctas_per_sm=0, chunk=8, schedule=0):
     """direction: 0 render, 1 adjoint."""
     _check(ctx, _lib.mog_set_launch_shape(ctx, int(direction), int(n), int(ctas_per_sm), int(chunk), int(schedule)))
+
+
+def mog_render_chi2(ctx, batch, data_ptr, ivar_ptr, grad_ptr, chi2_ptr, model_ptr=0, stream=0):
+    _check(ctx, _lib.mog_render_chi2(ctx, ctypes.byref(batch), ctypes.c_void_p(int(data_ptr)),
+                                     ctypes.c_void_p(int(ivar_ptr)), ctypes.c_void_p(int(grad_ptr)),
+                                     ctypes.c_void_p(int(chi2_ptr)), ctypes.c_void_p(int(model_ptr)),
+                                     ctypes.c_void_p(int(stream))))
 
 
 def mog_chi2_gradient(ctx, batch, model_ptr, data_ptr, ivar_ptr, grad_ptr, chi2_ptr=0, stream=0):

@@ -456,7 +456,7 @@ mog_status launch_buckets(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, u
 namespace mog {
 
 mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s,
-                       bool lanczos, bool add) {
+                       bool lanczos, bool add, const LossArgs* loss) {
   mog_status st = check_batch(ctx, batch);
   if (st != MOG_OK) return st;
   if (batch->count == 0) return MOG_OK;
@@ -474,6 +474,14 @@ mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, floa
   p.lzw = ws->lzw;
   p.accumulate = add ? 1 : 0;
   p.scratch256 = ws->bwd256;
+  if (loss) {
+    p.loss = 1;
+    p.data = loss->data;
+    p.dptr = loss->dptr;
+    p.ivar = loss->ivar;
+    p.chi2 = loss->chi2;
+    p.model = loss->model;
+  }
   MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ws->records, s));
   return launch_buckets(ctx, ws, batch, buckets, s, [&](int n, cudaStream_t bs) {
     RenderParams q = p;
@@ -526,6 +534,24 @@ mog_status mog_render_batch_ex(mog_ctx* ctx, const mog_batch* batch, float* out,
   if (flags & ~(unsigned)(MOG_RENDER_LANCZOS | MOG_RENDER_ADD)) return fail(ctx, MOG_ERR_ARG, "unknown render flags");
   return render_with(ctx, &ctx->ws, batch, out, static_cast<cudaStream_t>(stream), (flags & MOG_RENDER_LANCZOS) != 0,
                      (flags & MOG_RENDER_ADD) != 0);
+}
+
+mog_status mog_render_chi2(mog_ctx* ctx, const mog_batch* batch, const float* data, const float* ivar,
+                           float* grad_pix, float* chi2, float* model, void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  mog_status st = check_batch(ctx, batch);
+  if (st != MOG_OK) return st;
+  if (batch->count == 0) return MOG_OK;
+  if (!data || !ivar || !grad_pix || !chi2) return fail(ctx, MOG_ERR_ARG, "null data, ivar, grad_pix or chi2");
+  if ((reinterpret_cast<uintptr_t>(data) | reinterpret_cast<uintptr_t>(grad_pix) | reinterpret_cast<uintptr_t>(model)) &
+      15)
+    return fail(ctx, MOG_ERR_ARG, "data, grad_pix and model must be 16-byte aligned");
+  LossArgs loss;
+  loss.data = data;
+  loss.ivar = ivar;
+  loss.chi2 = chi2;
+  loss.model = model;
+  return render_with(ctx, &ctx->ws, batch, grad_pix, static_cast<cudaStream_t>(stream), false, false, &loss);
 }
 
 mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,

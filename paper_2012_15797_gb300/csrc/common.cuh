@@ -503,6 +503,27 @@ __device__ __forceinline__ void store8(float* p, const float* o, bool add) {
   d[1] = b;
 }
 
+// Loss mode of the forward kernels: eight model pixels o at patch element
+// `e` of a galaxy whose observed patch is `data` (same layout) become
+// residuals r = o - data, the stored values are the loss gradient
+// 2 ivar r (grad) and, when `model` is not null, the model itself; returns
+// sum r^2 over the eight (chi^2 = ivar times its sum over the patch).
+__device__ __forceinline__ float loss_store8(const float* data, float* grad, float* model, int64_t e,
+                                             const float* o, float two_iv) {
+  const float4 d0 = __ldg(reinterpret_cast<const float4*>(data + e));
+  const float4 d1 = __ldg(reinterpret_cast<const float4*>(data + e) + 1);
+  const float r[8] = {o[0] - d0.x, o[1] - d0.y, o[2] - d0.z, o[3] - d0.w,
+                      o[4] - d1.x, o[5] - d1.y, o[6] - d1.z, o[7] - d1.w};
+  float acc = 0.0f;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc = fmaf(r[u], r[u], acc);
+  float4* g = reinterpret_cast<float4*>(grad + e);
+  g[0] = make_float4(two_iv * r[0], two_iv * r[1], two_iv * r[2], two_iv * r[3]);
+  g[1] = make_float4(two_iv * r[4], two_iv * r[5], two_iv * r[6], two_iv * r[7]);
+  if (model) store8(model + e, o, false);
+  return acc;
+}
+
 // Per planned position: eigen-PSF polynomial terms [0, 6) and the mixture
 // weights at the galaxy's position [8, 12) (written by the record prologue).
 constexpr int PCOEF = 16;

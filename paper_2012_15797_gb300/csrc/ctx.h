@@ -99,9 +99,20 @@ mog_status check_batch(mog_ctx* ctx, const mog_batch* batch);
 // Sizes a workspace for batches of up to `count` galaxies, 256 x 256 scratch
 // included, so that later calls up to that size allocate (and free) nothing.
 mog_status workspace_reserve(mog_ctx* ctx, Workspace* ws, int64_t count);
+// The loss mode of a render (mog_render_chi2): `out` receives the gradient
+// 2 ivar (model - data); data of galaxy g at data + offset[g], or at dptr[g]
+// when dptr is set; chi2[g] = ivar[g] sum (model - data)^2; the model in
+// `model` too when it is set.
+struct LossArgs {
+  const float* data = nullptr;
+  const float* const* dptr = nullptr;
+  const float* ivar = nullptr;
+  float* chi2 = nullptr;
+  float* model = nullptr;
+};
 // Batched render / adjoint with an explicit workspace (grows it if needed).
 mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, float* out, cudaStream_t s,
-                       bool lanczos = false, bool add = false);
+                       bool lanczos = false, bool add = false, const LossArgs* loss = nullptr);
 mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, const float* grad_out,
                          float* grad_params, cudaStream_t s,
                          bool grad_n = false);

@@ -29,6 +29,16 @@ struct RenderParams {
   int grad_n = 0;               // adjoint: 1 = also d/d(Sersic n), 7 gradients per galaxy
   float2* scratch256 = nullptr; // accumulate, N = 256: per-CTA transform intermediate (N/2 x N complex)
   int sched = 0;                // radix schedule of the forward transforms (Radix<N, sched>), set per bucket
+  // loss mode (mog_render_chi2): `out` receives the gradient 2 ivar (model -
+  // data) instead of the model; data of galaxy g at data + offset[g] (or at
+  // dptr[g] when dptr is set), chi2[g] = ivar[g] sum (model - data)^2, and
+  // the model too when `model` is set (same layout as out)
+  int loss = 0;
+  const float* data = nullptr;
+  const float* const* dptr = nullptr;
+  const float* ivar = nullptr;
+  float* chi2 = nullptr;
+  float* model = nullptr;
 };
 
 // Launch shape of one size bucket: CTAs per SM (clamped to what fits) and

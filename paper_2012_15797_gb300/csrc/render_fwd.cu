@@ -173,11 +173,16 @@ __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, 
 // EIG: some PSF of the context is an eigen-PSF (the variant without it has
 // none of that code).
 // V: the radix schedule of the transforms (Radix<N, V>).
-template <int N, bool LZ, bool EIG, int CPG = 1, int V = 0>
+// LOSS: the loss mode of mog_render_chi2 (the stored values are the gradient
+// of chi^2 = ivar sum (model - data)^2 with respect to the pixels, chi^2 per
+// galaxy is reduced over the CTA).
+template <int N, bool LZ, bool EIG, int CPG = 1, int V = 0, bool LOSS = false>
 __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>::MIN_BLOCKS)
     render_fwd_kernel(RenderParams p) {
   using C = FwdCfg<N, CPG, V>;
   static_assert(!(LZ && CPG > 1), "the Lanczos variant keeps one column per group");
+  static_assert(!(LZ && LOSS), "the loss mode renders with the phase shift");
+  constexpr int WARPS = C::THREADS / 32;
   constexpr int TPF = C::TPF, LS = C::LS;
   constexpr int B = bucket_of(N);
   constexpr float INV_N = 1.0f / N;
@@ -200,6 +205,25 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
   __shared__ int s_nr[2];
   __shared__ float4 s_fc[KMAX];   // Fourier components as (a, a, c, c): operand pairs of f32x2
   __shared__ float s_lzw[2][16];  // LZ, per record buffer: Lanczos weights along x [0, 7) and y [8, 15)
+  // LOSS, per record buffer: the galaxy's data patch, model output (or null),
+  // ivar, index, and each warp's sum of squared residuals
+  __shared__ const float* s_dat[2];
+  __shared__ float* s_mdl[2];
+  __shared__ float s_iv[2];
+  __shared__ long long s_gal[2];
+  __shared__ float s_chi[2][LOSS ? WARPS : 1];
+  long long chi_gal = -1;   // thread 0: galaxy whose chi^2 is still to be written
+  float chi_iv = 0.0f;
+  int chi_buf = 0;
+  // thread 0, once every warp has added its residuals of galaxy chi_gal
+  auto write_chi2 = [&]() {
+    if (chi_gal >= 0) {
+      float t = 0.0f;
+      for (int w = 0; w < WARPS; ++w) t += s_chi[chi_buf][w];
+      p.chi2[chi_gal] = chi_iv * t;
+      chi_gal = -1;
+    }
+  };
 
   const int tid = threadIdx.x;
   const int f = tid / TPF, j = tid % TPF;
@@ -301,6 +325,12 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
       if (tid == 0) {
         s_dst[buf] = p.out + r.off;
         s_nr[buf] = nr2;
+        if constexpr (LOSS) {
+          s_dat[buf] = p.dptr ? p.dptr[r.gal] : p.data + r.off;
+          s_mdl[buf] = p.model ? p.model + r.off : nullptr;
+          s_iv[buf] = p.ivar[r.gal];
+          s_gal[buf] = r.gal;
+        }
       }
       const float gx = r.x, gy = r.y;
       const float* lzw = LZ ? p.lzw + ((size_t)first + pos) * 16 : nullptr;
@@ -365,6 +395,13 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
     if (__syncthreads_or(!landed)) {
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
       return;
+    }
+    if constexpr (LOSS) {
+      // every warp has stored the previous galaxy and added its residuals
+      if (tid == 0) {
+        write_chi2();
+        if (!r.ok) p.chi2[r.gal] = __int_as_float(0x7fc00000);   // NaN: a galaxy that is skipped
+      }
     }
     if (!work) continue;   // uniform once every wait has landed
 
@@ -465,6 +502,10 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
     // ---- Step 7b: real inverse FFT of row pairs (prow, prow + N/2) along nu ----
     float* const dst = s_dst[buf];
     const int nr = s_nr[buf];
+    [[maybe_unused]] float chi_acc = 0.0f;
+    [[maybe_unused]] const float* const dat = LOSS ? s_dat[buf] : nullptr;   // the galaxy's data patch
+    [[maybe_unused]] float* const mdl = LOSS ? s_mdl[buf] : nullptr;
+    [[maybe_unused]] const float two_iv = LOSS ? 2.0f * s_iv[buf] : 0.0f;
 #pragma unroll 1
     for (int rr = 0; rr < CPG; ++rr) {
       const int prow = f + rr * C::GROUPS;
@@ -515,9 +556,23 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
         const float4 i1 = *reinterpret_cast<const float4*>(src + ((x0 + 4) ^ sw));
         float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
         if (nr > 0) real_space_run(rt, nr, (float)yy, (float)x0, o);
-        store8(dst + yy * N + x0, o, p.accumulate != 0);
+        if constexpr (LOSS) chi_acc += loss_store8(dat, dst, mdl, (int64_t)yy * N + x0, o, two_iv);
+        else store8(dst + yy * N + x0, o, p.accumulate != 0);
       }
     }   // row pairs of this group
+    if constexpr (LOSS) {
+      for (int o2 = 16; o2 > 0; o2 >>= 1) chi_acc += __shfl_xor_sync(0xffffffffu, chi_acc, o2);
+      if ((tid & 31) == 0) s_chi[buf][tid >> 5] = chi_acc;
+      if (tid == 0) {
+        chi_gal = s_gal[buf];
+        chi_iv = s_iv[buf];
+        chi_buf = buf;
+      }
+    }
+  }
+  if constexpr (LOSS) {
+    __syncthreads();   // the last galaxy's residuals are in
+    if (tid == 0) write_chi2();
   }
 }
 
@@ -528,21 +583,22 @@ constexpr int fwd_cpg() { return (N == 128 && !LZ) ? 2 : 1; }
 
 static_assert(2 * (FwdCfg<128, 2>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 CTAs share an SM's shared memory");
 
-template <int N, bool LZ = false, bool EIG = false, int V = 0>
+template <int N, bool LZ = false, bool EIG = false, int V = 0, bool LOSS = false>
 static int fwd_occupancy() {
   constexpr int CPG = fwd_cpg<N, LZ>();
   using C = FwdCfg<N, CPG, V>;
-  return kernel_occupancy(reinterpret_cast<const void*>(render_fwd_kernel<N, LZ, EIG, CPG, V>), C::THREADS, C::SMEM);
+  return kernel_occupancy(reinterpret_cast<const void*>(render_fwd_kernel<N, LZ, EIG, CPG, V, LOSS>), C::THREADS,
+                          C::SMEM);
 }
 
-template <int N, bool LZ, bool EIG, int V>
+template <int N, bool LZ, bool EIG, int V, bool LOSS = false>
 static cudaError_t launch_fwd_mode(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
   constexpr int CPG = fwd_cpg<N, LZ>();
   using C = FwdCfg<N, CPG, V>;
-  const int occ = fwd_occupancy<N, LZ, EIG, V>();
+  const int occ = fwd_occupancy<N, LZ, EIG, V, LOSS>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_fwd_kernel<N, LZ, EIG, CPG, V><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
+  render_fwd_kernel<N, LZ, EIG, CPG, V, LOSS><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -550,6 +606,9 @@ static cudaError_t launch_fwd_mode(const RenderParams& p, int num_sms, int ctas_
 // shift, constant PSFs) only; the other variants keep the first.
 template <int N>
 static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  if (p.loss)   // the first schedule, phase shift
+    return p.eigen ? launch_fwd_mode<N, false, true, 0, true>(p, num_sms, ctas_per_sm, s)
+                   : launch_fwd_mode<N, false, false, 0, true>(p, num_sms, ctas_per_sm, s);
   if (p.eigen)
     return p.lanczos ? launch_fwd_mode<N, true, true, 0>(p, num_sms, ctas_per_sm, s)
                      : launch_fwd_mode<N, false, true, 0>(p, num_sms, ctas_per_sm, s);

@@ -134,9 +134,12 @@ __device__ __forceinline__ void lanczos_real_256(const RealTerms& rt, int nr, co
   }
 }
 
-// V: the radix schedule of the transforms (Radix<256, V>).
-template <bool LZ, bool EIG, int V = 0>
+// V: the radix schedule of the transforms (Radix<256, V>).  LOSS: the loss
+// mode of mog_render_chi2 (render_fwd.cu): the patch receives the gradient of
+// chi^2 (and serves as the transform intermediate as it does for the model).
+template <bool LZ, bool EIG, int V = 0, bool LOSS = false>
 __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(RenderParams p) {
+  static_assert(!(LZ && LOSS), "the loss mode renders with the phase shift");
   constexpr int R1 = Radix<N, V>::r[1], R2 = Radix<N, V>::r[2];
   constexpr int TW1 = twiddle_elems<N, R1>();
   static_assert(Radix<N, V>::P == 3, "three passes");
@@ -191,8 +194,19 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
   uint32_t rec_parity = 0;
   float2* w = W + f * WS;   // this warp's transform row
 
+  __shared__ float s_chi[WARPS];   // LOSS: each warp's sum of squared residuals
+  long long chi_gal = -1;          // thread 0: galaxy whose chi^2 is still to be written
+  float chi_iv = 0.0f;
   for (int buf = 0;; buf ^= 1) {
     __syncthreads();  // the previous galaxy is fully stored
+    if constexpr (LOSS) {
+      if (tid == 0 && chi_gal >= 0) {
+        float t = 0.0f;
+        for (int w = 0; w < WARPS; ++w) t += s_chi[w];
+        p.chi2[chi_gal] = chi_iv * t;
+        chi_gal = -1;
+      }
+    }
     const int pos = s_pos[buf];
     if (pos < 0) break;
     if (tid == 0) {
@@ -221,8 +235,16 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
       return;
     }
-    if (!r.ok) continue;
+    if (!r.ok) {
+      if constexpr (LOSS)
+        if (tid == 0) p.chi2[r.gal] = __int_as_float(0x7fc00000);   // NaN: a galaxy that is skipped
+      continue;
+    }
     float* dst = p.out + r.off;
+    [[maybe_unused]] const float* const dat = LOSS ? (p.dptr ? p.dptr[r.gal] : p.data + r.off) : nullptr;
+    [[maybe_unused]] float* const mdl = (LOSS && p.model) ? p.model + r.off : nullptr;
+    [[maybe_unused]] const float two_iv = LOSS ? 2.0f * p.ivar[r.gal] : 0.0f;
+    [[maybe_unused]] float chi_acc = 0.0f;
     // row-pair inputs, [p][k]: the patch itself, or, when adding to what the
     // patch holds, this CTA's slice of the workspace scratch
     float2* zbuf = p.accumulate ? p.scratch256 + (size_t)blockIdx.x * (N / 2) * N : reinterpret_cast<float2*>(dst);
@@ -415,9 +437,18 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
         const float4 i0 = *reinterpret_cast<const float4*>(orow), i1 = *reinterpret_cast<const float4*>(orow + 4);
         float o[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
         if (nr > 0 && !LZ) real_space_run(rt, nr, (float)yy, (float)x0, o);
-        store8(dst + yy * N + x0, o, p.accumulate != 0);
+        if constexpr (LOSS) chi_acc += loss_store8(dat, dst, mdl, (int64_t)yy * N + x0, o, two_iv);
+        else store8(dst + yy * N + x0, o, p.accumulate != 0);
       }
       __syncwarp();
+    }
+    if constexpr (LOSS) {
+      for (int o2 = 16; o2 > 0; o2 >>= 1) chi_acc += __shfl_xor_sync(0xffffffffu, chi_acc, o2);
+      if (j == 0) s_chi[f] = chi_acc;
+      if (tid == 0) {
+        chi_gal = r.gal;
+        chi_iv = 0.5f * two_iv;
+      }
     }
     if constexpr (LZ) {
       if (nr > 0) {   // uniform over the CTA
@@ -430,19 +461,20 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
 
 }  // namespace
 
-template <bool LZ, bool EIG, int V = 0>
+template <bool LZ, bool EIG, int V = 0, bool LOSS = false>
 static int fwd256_occupancy() {
-  const int occ = kernel_occupancy(reinterpret_cast<const void*>(render_fwd256_kernel<LZ, EIG, V>), THREADS, SMEM);
+  const int occ =
+      kernel_occupancy(reinterpret_cast<const void*>(render_fwd256_kernel<LZ, EIG, V, LOSS>), THREADS, SMEM);
   return occ < 0 ? occ : (occ < CTAS_PER_SM ? occ : CTAS_PER_SM);
 }
 
-template <bool LZ, bool EIG, int V = 0>
+template <bool LZ, bool EIG, int V = 0, bool LOSS = false>
 static cudaError_t launch_fwd256(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
-  const int occ = fwd256_occupancy<LZ, EIG, V>();
+  const int occ = fwd256_occupancy<LZ, EIG, V, LOSS>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   // the accumulate mode's scratch holds one slice per CTA, CTAS_PER_SM per SM
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_fwd256_kernel<LZ, EIG, V><<<num_sms * ctas, THREADS, SMEM, s>>>(p);
+  render_fwd256_kernel<LZ, EIG, V, LOSS><<<num_sms * ctas, THREADS, SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -452,6 +484,9 @@ int render_fwd256_max_ctas(int sched) {
 
 // The second radix schedule is compiled for the plain render only.
 cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  if (p.loss)   // the first schedule, phase shift
+    return p.eigen ? launch_fwd256<false, true, 0, true>(p, num_sms, ctas_per_sm, s)
+                   : launch_fwd256<false, false, 0, true>(p, num_sms, ctas_per_sm, s);
   if (p.eigen)
     return p.lanczos ? launch_fwd256<true, true>(p, num_sms, ctas_per_sm, s)
                      : launch_fwd256<false, true>(p, num_sms, ctas_per_sm, s);

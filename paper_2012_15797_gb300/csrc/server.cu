@@ -11,8 +11,9 @@
 // A scheduler thread admits pending requests into a micro-batch while the
 // batch fits the device-memory budget (a first-fit arena) and the per-batch
 // galaxy limit, and launches it on a free lane (stream + workspace + pinned
-// staging): upload parameters and index map, gather the batch, render,
-// residual and chi^2, adjoint, download results.  Several micro-batches are in
+// staging): upload parameters and index map, gather the batch, render with
+// the loss (the render kernels store dchi2/dpixel and reduce chi^2 as they
+// go), adjoint, download results.  Several micro-batches are in
 // flight on different lanes while newly arrived requests queue for the next
 // free lane; a completion thread returns results, frees the memory and
 // records each request's latency (submission to results available).
@@ -53,7 +54,7 @@ struct BatchDev {
   int32_t *profile, *psf, *size;
   int64_t *offset;          // of the model patch in `model`
   const float** dptr;       // the galaxy's observed patch
-  float* model;             // rendered patches, then dchi2/dpixel in place
+  float* model;             // dchi2/dpixel on the batch's patches (rendered with the loss)
   float* grads;             // 6 per galaxy, then chi2 (one per galaxy)
   float* chi2;
 };
@@ -86,37 +87,6 @@ __global__ void gather_kernel(int64_t g, const float* params, const int32_t* fit
     b.offset[i] = offset[i];
     b.dptr[i] = F.data + F.data_offset[k];
     b.ivar[i] = F.ivar[k];
-  }
-}
-
-// One CTA per galaxy: r = model - data, dchi2/dpixel = 2 ivar r written over
-// the model, chi2 = ivar sum r^2.
-__global__ void __launch_bounds__(256) residual_kernel(int64_t g, BatchDev b) {
-  __shared__ float red[8];
-  for (int64_t i = blockIdx.x; i < g; i += gridDim.x) {
-    const int n = b.size[i];
-    const int64_t np = (int64_t)n * n;
-    float* m = b.model + b.offset[i];
-    const float* d = b.dptr[i];
-    const float iv = b.ivar[i];
-    float acc = 0.0f;
-    for (int64_t p = threadIdx.x * 4; p < np; p += 4 * blockDim.x) {
-      float4 mv = *reinterpret_cast<const float4*>(m + p);
-      const float4 dv = *reinterpret_cast<const float4*>(d + p);
-      const float r0 = mv.x - dv.x, r1 = mv.y - dv.y, r2 = mv.z - dv.z, r3 = mv.w - dv.w;
-      acc += r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3;
-      mv = make_float4(2.0f * iv * r0, 2.0f * iv * r1, 2.0f * iv * r2, 2.0f * iv * r3);
-      *reinterpret_cast<float4*>(m + p) = mv;
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float t = 0.0f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-      b.chi2[i] = iv * t;
-    }
-    __syncthreads();
   }
 }
 
@@ -358,9 +328,14 @@ int launch_batch(mog_server* S, mog_server::Lane& L, int64_t g, int64_t pix) {
   mb.size = b.size;
   mb.offset = b.offset;
   mb.size_mask = 0;
-  int st = render_with(ctx, &L.ws, &mb, b.model, s);
+  // render and loss in one pass: the patches receive dchi2/dpixel = 2 ivar
+  // (model - data) (the model itself is not kept), then the adjoint
+  LossArgs loss;
+  loss.dptr = b.dptr;
+  loss.ivar = b.ivar;
+  loss.chi2 = b.chi2;
+  int st = render_with(ctx, &L.ws, &mb, b.model, s, false, false, &loss);
   if (st != MOG_OK) return st;
-  residual_kernel<<<(int)(g < 65536 ? g : 65536), 256, 0, s>>>(g, b);
   st = backward_with(ctx, &L.ws, &mb, b.model, b.grads, s);
   if (st != MOG_OK) return st;
   if (cudaMemcpyAsync(L.st.results, b.grads, sizeof(float) * 7 * g, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -194,6 +194,21 @@ class Renderer:
                                grad_pix.data_ptr(), chi2.data_ptr(), s.cuda_stream)
         return grad_pix, chi2
 
+    def render_chi2(self, batch, data, ivar, grad_pix=None, chi2=None, model=None, stream=None):
+        """Render and loss in one pass (mog_render_chi2): returns (grad_pix,
+        chi2) with grad_pix = 2 ivar (model - data) on every patch and chi2 =
+        ivar sum (model - data)^2 per galaxy; the model is written into
+        ``model`` too when a tensor is given."""
+        if grad_pix is None:
+            grad_pix = torch.empty(batch.total, dtype=torch.float32, device=self.device)
+        if chi2 is None:
+            chi2 = torch.empty(batch.count, dtype=torch.float32, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
+        capi.mog_render_chi2(self.ctx, b, data.data_ptr(), ivar.contiguous().data_ptr(), grad_pix.data_ptr(),
+                             chi2.data_ptr(), model.data_ptr() if model is not None else 0, s.cuda_stream)
+        return grad_pix, chi2
+
     def fit_psf_mixtures(self, images, k=3, iters=400, stream=None):
         """Gaussian-mixture fits of a (count, h, w) float32 device tensor of
         PSF images: returns ((count, k, 6) rows, (count,) chi^2)."""
