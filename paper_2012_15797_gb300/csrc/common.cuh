@@ -958,15 +958,18 @@ struct AdjTerms {
 };
 
 // Real-space term t = c * kpsf + j of the adjoint record (one thread).
+// eig_w: mixture weights at the galaxy's position for an eigen-PSF whose
+// rows in psf_mog carry the constant weights (null: psf_mog's own).
 __device__ __forceinline__ void adj_real_term(const AdjRecord& r, const float (*psf_mog)[6], int kp, int n, int t,
-                                              AdjTerms* at) {
+                                              AdjTerms* at, const float* eig_w = nullptr) {
   const int c = t / kp, jj = t - c * kp;
   const float* m = psf_mog[jj];
+  const float wj = eig_w ? eig_w[jj] : m[0];
   const float v = r.rvar[c];
   const float vxx = v * r.s11 + m[3], vxy = v * r.s12 + m[4], vyy = v * r.s22 + m[5];
   const float det = vxx * vyy - vxy * vxy;
   const float idet = 1.0f / det;
-  const float norm = m[0] * rsqrtf(det) * (0.5f / PI_F);
+  const float norm = wj * rsqrtf(det) * (0.5f / PI_F);
   at->base[t] = r.rbase[c] * norm;
   at->dna[t] = r.rda[c] * norm;
   at->dnv[t] = r.rdv[c] * norm;

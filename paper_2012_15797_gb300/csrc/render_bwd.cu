@@ -158,8 +158,19 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
   uint32_t rec_parity = 0, g_parity = 0;
   float2* wb = WB + f * WS;   // this group's row transforms
 
+  // CTA barriers per galaxy: S2 (record, tables and gradient patch ready),
+  // for N = 64 the work-row barrier, S3 (column inputs written) and S4
+  // (partial sums written).  None at the top of the loop: S4 of the previous
+  // galaxy orders every read of its tables, records, work rows and gradient
+  // patch before this galaxy's writes, and only thread 0 (the final sums)
+  // still reads anything of it, in program order before its own next writes.
+  // For N = 32 one more after the record lands (the set-up tasks read the PSF
+  // mixture from shared memory); the larger sides read it from global memory
+  // (L2) instead (measured: 128 x 128 3.38 -> 3.17 ms, 64 x 64 2.10 -> 2.07
+  // ms with both barriers gone, 32 x 32 0.816 -> 0.835 without the second).
+  constexpr bool REC_SYNC = N == 32;
+  __syncthreads();
   for (int buf = 0;; buf ^= 1) {
-    __syncthreads();  // S1
     const int pos = s_pos[buf];
     if (pos < 0) break;
     if (tid == 0) {
@@ -195,16 +206,27 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
       if (tid == 0) s_kpsf = ps.k;
       cur_psf = k_eig > 0 ? -1 : r.psf;   // an eigen-PSF's weights change with the position
     }
-    if (__syncthreads_or(!rec_landed)) {
-      if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
-      return;
+    if constexpr (REC_SYNC) {
+      if (__syncthreads_or(!rec_landed)) {
+        if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
+        return;
+      }
+      if (!r.ok) continue;
+    } else {
+      // every thread whose wait ended reads the same record: uniform unless
+      // a wait timed out, which S2 reports
+      if (rec_landed && !r.ok) continue;
     }
-    if (!r.ok) continue;
 
     // ---- per-galaxy tables ----
-    {
+    if (go) {
+      const DevPsf& psg = p.psfs[r.psf];
+      const float* pcg = p.pcoef + ((size_t)first + pos) * PCOEF;
+      const float(*mog)[6] = REC_SYNC ? s_psf_mog : psg.mog;   // eigen weights in column 0 when staged
+      const float* eig_w = (!REC_SYNC && k_eig > 0) ? pcg + 8 : nullptr;
+      const float* eig_m = REC_SYNC ? s_eigm : pcg;
       const float gx = r.x, gy = r.y;
-      const int kp = s_kpsf;
+      const int kp = REC_SYNC ? s_kpsf : psg.k;
       const int nrt = r.nrc * kp, nr2 = real_terms_padded(nrt);
       const int ntask = C::H + 2 * N + nr2 + r.nf;
       for (int i = tid; i < ntask; i += C::THREADS) {
@@ -232,7 +254,7 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
           sincospif(-gx, &sn, &cs);
-          const float2 pn = k_eig > 0 ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, s_eigm, (N / 2) * LS + l)
+          const float2 pn = k_eig > 0 ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, eig_m, (N / 2) * LS + l)
                                       : __ldg(&psf_hat[(N / 2) * LS + l]);
           nyb[l] = cmul(pn, cmul(make_float2(cs, sn), make_float2(cy, sy)));
           nys[4 * l + 0] = s;
@@ -242,7 +264,7 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
         } else {
           const int t = i - C::H - 2 * N;
           if (t < nrt) {
-            adj_real_term(r, s_psf_mog, kp, N, t, &at);
+            adj_real_term(r, mog, kp, N, t, &at, eig_w);
           } else if (t < nr2) {
             adj_real_term_zero(t, &at);
           } else {
@@ -253,10 +275,12 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
     }
     bool g_landed = true;
     if constexpr (C::G_SMEM) {
-      g_landed = mbar_wait(&bar[2], g_parity);
-      g_parity ^= 1u;
+      if (go) {
+        g_landed = mbar_wait(&bar[2], g_parity);
+        g_parity ^= 1u;
+      }
     }
-    if (__syncthreads_or(!g_landed)) {   // S2
+    if (__syncthreads_or(!g_landed || !rec_landed)) {   // S2
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
       return;
     }
