@@ -503,6 +503,12 @@ __device__ __forceinline__ void store8(float* p, const float* o, bool add) {
   d[1] = b;
 }
 
+// Starts bringing a 128-byte line of global memory into L2 (no fault, no
+// register written): the loss mode's data rows, read only at the store.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Loss mode of the forward kernels: eight model pixels o at patch element
 // `e` of a galaxy whose observed patch is `data` (same layout) become
 // residuals r = o - data, the stored values are the loss gradient

@@ -404,6 +404,12 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
       }
     }
     if (!work) continue;   // uniform once every wait has landed
+    if constexpr (LOSS) {
+      // the data patch is read by the stores at the end: its lines are on
+      // their way to L2 while the transforms run
+      const float* d = s_dat[buf];
+      for (int i = tid; i < N * N / 32; i += C::THREADS) prefetch_l2(d + 32 * i);
+    }
 
     // ---- Steps 5-6: Fourier mixture times PSF spectrum and phase, in registers ----
     const int nf = r.nf;

@@ -245,6 +245,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
     [[maybe_unused]] float* const mdl = (LOSS && p.model) ? p.model + r.off : nullptr;
     [[maybe_unused]] const float two_iv = LOSS ? 2.0f * p.ivar[r.gal] : 0.0f;
     [[maybe_unused]] float chi_acc = 0.0f;
+    if constexpr (LOSS)   // the data patch's lines on their way to L2 while the transforms run
+      for (int i = tid; i < N * N / 32; i += THREADS) prefetch_l2(dat + 32 * i);
     // row-pair inputs, [p][k]: the patch itself, or, when adding to what the
     // patch holds, this CTA's slice of the workspace scratch
     float2* zbuf = p.accumulate ? p.scratch256 + (size_t)blockIdx.x * (N / 2) * N : reinterpret_cast<float2*>(dst);
