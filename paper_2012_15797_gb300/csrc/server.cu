@@ -181,6 +181,8 @@ struct mog_server {
   std::vector<std::vector<int32_t>> fit_sizes;  // host copies of the patch sides
   mog::DevFit* d_fits = nullptr;
   int d_fits_cap = 0;
+  std::vector<mog::DevFit*> retired_fits;   // outgrown tables: freed at destroy (kernels may read them)
+  std::mutex fit_mu;                        // one mog_server_add_fit at a time
   // lanes
   struct Lane {
     cudaStream_t stream = nullptr;
@@ -451,14 +453,14 @@ void completer(mog_server* S) {
       // woken by lane_done_cb; every 2 ms the lanes' events are also
       // queried, so a batch whose callback did not run (its stream failed)
       // still completes
-      bool poll = false;
+      // (the queries run outside the lock: no CUDA call is made under it)
+      bool polled[16] = {};
       for (;;) {
         bool any = false;
         for (auto& L : S->lanes) {
           if (!L.busy || !L.launched) continue;
           any = true;
-          if (L.status != MOG_OK || S->fired[L.idx].load(std::memory_order_acquire) ||
-              (poll && cudaEventQuery(L.done) != cudaErrorNotReady)) {
+          if (L.status != MOG_OK || S->fired[L.idx].load(std::memory_order_acquire) || polled[L.idx]) {
             ready = &L;
             break;
           }
@@ -467,7 +469,19 @@ void completer(mog_server* S) {
         bool launching = false;
         for (auto& L : S->lanes) launching |= L.busy && !L.launched;
         if (S->stop && !any && !launching) return;
-        poll = S->cv_comp.wait_for(lk, std::chrono::milliseconds(any ? 2 : 5)) == std::cv_status::timeout;
+        const bool timed_out =
+            S->cv_comp.wait_for(lk, std::chrono::milliseconds(any ? 2 : 5)) == std::cv_status::timeout;
+        for (bool& b : polled) b = false;
+        if (timed_out) {
+          // only this thread frees lanes, so a lane busy and launched now
+          // stays so while the lock is released
+          int idx[16], n = 0;
+          for (auto& L : S->lanes)
+            if (L.busy && L.launched) idx[n++] = L.idx;
+          lk.unlock();
+          for (int k = 0; k < n; ++k) polled[idx[k]] = cudaEventQuery(S->lanes[idx[k]].done) != cudaErrorNotReady;
+          lk.lock();
+        }
       }
     }
     // results -> callers (lane is owned by this thread until freed)
@@ -615,28 +629,60 @@ mog_status mog_server_add_fit(mog_server* S, const mog_fit_state* fit, int* fit_
     if (doff[k] < 0 || (doff[k] & 3)) return fail(ctx, MOG_ERR_ARG, "fit galaxy %lld: data offset must be >= 0 and a multiple of 4", (long long)k);
   }
   DevFit F{fit->sersic_n, fit->profile, fit->psf, fit->size, fit->data_offset, fit->data, fit->ivar, fit->count};
-  std::lock_guard<std::mutex> lk(S->mu);
-  if ((int)S->fits.size() + 1 > S->d_fits_cap) {
-    // grow the device table; the scheduler is idle on it only between batches,
-    // so fits are added before requests for them are submitted
-    const int cap = S->d_fits_cap ? 2 * S->d_fits_cap : 64;
-    DevFit* d = nullptr;
-    MOG_CUDA(ctx, cudaMalloc(&d, sizeof(DevFit) * cap));
-    if (!S->fits.empty()) MOG_CUDA(ctx, cudaMemcpy(d, S->d_fits, sizeof(DevFit) * S->fits.size(), cudaMemcpyDeviceToDevice));
-    MOG_CUDA(ctx, cudaDeviceSynchronize());
-    if (S->d_fits) cudaFree(S->d_fits);
-    S->d_fits = d;
-    S->d_fits_cap = cap;
+  // No CUDA call is made under S->mu (the lanes' host callbacks take it): the
+  // table grows into a new allocation, the old one is kept until destroy,
+  // since kernels in flight may still read it, and the new entry is written
+  // before it is published.
+  std::lock_guard<std::mutex> fk(S->fit_mu);
+  int n, cap;
+  DevFit* cur;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    n = (int)S->fits.size();
+    cap = S->d_fits_cap;
+    cur = S->d_fits;
   }
-  MOG_CUDA(ctx, cudaMemcpy(S->d_fits + S->fits.size(), &F, sizeof(F), cudaMemcpyHostToDevice));
-  *fit_id = (int)S->fits.size();
-  S->fits.push_back(F);
-  S->fit_sizes.push_back(std::move(sizes));
+  DevFit* table = cur;
+  if (n + 1 > cap) {
+    cap = cap ? 2 * cap : 64;
+    MOG_CUDA(ctx, cudaMalloc(&table, sizeof(DevFit) * cap));
+    if (n) MOG_CUDA(ctx, cudaMemcpy(table, cur, sizeof(DevFit) * n, cudaMemcpyDeviceToDevice));
+  }
+  MOG_CUDA(ctx, cudaMemcpy(table + n, &F, sizeof(F), cudaMemcpyHostToDevice));
+  MOG_CUDA(ctx, cudaStreamSynchronize(cudaStreamLegacy));   // both copies have landed
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (table != cur) {
+      if (cur) S->retired_fits.push_back(cur);
+      S->d_fits = table;
+      S->d_fits_cap = cap;
+    }
+    *fit_id = n;
+    S->fits.push_back(F);
+    S->fit_sizes.push_back(std::move(sizes));
+  }
   return MOG_OK;
 }
 
 mog_status mog_server_submit(mog_server* S, const mog_request* req, uint64_t* ticket) {
   if (!S || !req || !ticket || !req->params || !req->grads) return MOG_ERR_ARG;
+  if (req->count < 1) return fail(S->ctx, MOG_ERR_ARG, "request outside its fit");
+  for (int64_t k = 0; k < req->count; ++k) {
+    const float* q = req->params + 6 * k;
+    bool ok = true;
+    for (int c = 0; c < 6; ++c) ok = ok && std::isfinite(q[c]);
+    ok = ok && std::hypot(q[4], q[5]) < 1.0f && q[3] < 30.0f;
+    if (!ok)
+      return fail(S->ctx, MOG_ERR_ARG, "request galaxy %lld: parameters must be finite, |e| < 1, log r_e < 30", (long long)k);
+  }
+  // built before the lock: allocations stay off the critical section
+  auto r = std::make_shared<Request>();
+  r->fit = req->fit;
+  r->first = req->first;
+  r->count = req->count;
+  r->params.assign(req->params, req->params + 6 * req->count);
+  r->grads = req->grads;
+  r->chi2 = req->chi2;
   std::unique_lock<std::mutex> lk(S->mu);
   if (req->fit < 0 || req->fit >= (int)S->fits.size() || req->count < 1 || req->first < 0 ||
       req->first + req->count > S->fits[req->fit].count)
@@ -648,22 +694,7 @@ mog_status mog_server_submit(mog_server* S, const mog_request* req, uint64_t* ti
   }
   if (batch_bytes(req->count, pix) > S->arena.total())
     return fail(S->ctx, MOG_ERR_ARG, "request larger than the server's memory budget");
-  for (int64_t k = 0; k < req->count; ++k) {
-    const float* q = req->params + 6 * k;
-    bool ok = true;
-    for (int c = 0; c < 6; ++c) ok = ok && std::isfinite(q[c]);
-    ok = ok && std::hypot(q[4], q[5]) < 1.0f && q[3] < 30.0f;
-    if (!ok)
-      return fail(S->ctx, MOG_ERR_ARG, "request galaxy %lld: parameters must be finite, |e| < 1, log r_e < 30", (long long)k);
-  }
-  auto r = std::make_shared<Request>();
   r->ticket = S->next_ticket++;
-  r->fit = req->fit;
-  r->first = req->first;
-  r->count = req->count;
-  r->params.assign(req->params, req->params + 6 * req->count);
-  r->grads = req->grads;
-  r->chi2 = req->chi2;
   r->submitted = Clock::now();
   S->requests[r->ticket] = r;
   S->pending_galaxies += r->count;
@@ -798,6 +829,7 @@ mog_status mog_server_destroy(mog_server* S) {
     lane_free_staging(L);
   }
   if (S->d_fits) cudaFree(S->d_fits);
+  for (auto* t : S->retired_fits) cudaFree(t);
   S->arena.destroy();
   delete S;
   return MOG_OK;
