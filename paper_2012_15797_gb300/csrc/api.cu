@@ -546,6 +546,10 @@ mog_status mog_render_chi2(mog_ctx* ctx, const mog_batch* batch, const float* da
   if ((reinterpret_cast<uintptr_t>(data) | reinterpret_cast<uintptr_t>(grad_pix) | reinterpret_cast<uintptr_t>(model)) &
       15)
     return fail(ctx, MOG_ERR_ARG, "data, grad_pix and model must be 16-byte aligned");
+  // NaN (all bits set) for the galaxies the kernels skip, unsupported sides
+  // included; the rendered galaxies overwrite theirs
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  MOG_CUDA(ctx, cudaMemsetAsync(chi2, 0xff, sizeof(float) * (size_t)batch->count, static_cast<cudaStream_t>(stream)));
   LossArgs loss;
   loss.data = data;
   loss.ivar = ivar;

@@ -109,8 +109,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM)
   uint32_t rec_parity = 0;
   float2* w = W + f * WS;
 
+  // No barrier at the top of the loop: the previous galaxy's last one (the
+  // partial sums) already orders every read of its tables, records and
+  // scratch before this galaxy's writes; after it only thread 0 reads (the
+  // final sums), in program order before its own next writes.
+  __syncthreads();
   for (int buf = 0;; buf ^= 1) {
-    __syncthreads();
     const int pos = s_pos[buf];
     if (pos < 0) break;
     if (tid == 0) {
