@@ -64,7 +64,7 @@ constexpr size_t off_py = off_px + sizeof(float2) * H;
 constexpr size_t off_nyq = off_py + sizeof(float2) * N;
 constexpr size_t off_rec = (off_nyq + sizeof(float2) * N + 15) & ~size_t(15);
 constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);
-constexpr size_t off_bar = (off_rt + sizeof(RealTerms) + 15) & ~size_t(15);
+constexpr size_t off_bar = (off_rt + 2 * sizeof(RealTerms) + 15) & ~size_t(15);   // two tables, one per record buffer
 constexpr size_t SMEM = off_bar + 2 * sizeof(uint64_t);
 static_assert(CTAS_PER_SM * (SMEM + 1024) <= 228 * 1024, "two CTAs share an SM's shared memory");
 constexpr int STRIP = 64;                                                 // output rows per strip
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
   float2* py = reinterpret_cast<float2*>(smem + off_py);
   float2* nyq = reinterpret_cast<float2*>(smem + off_nyq);
   GalaxyRecord* rec = reinterpret_cast<GalaxyRecord*>(smem + off_rec);
-  RealTerms& rt = *reinterpret_cast<RealTerms*>(smem + off_rt);
+  RealTerms* rts = reinterpret_cast<RealTerms*>(smem + off_rt);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + off_bar);   // records
   __shared__ int s_pos[2];
   __shared__ float s_psf_mog[KPSF][6];
@@ -197,16 +197,24 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
   __shared__ float s_chi[WARPS];   // LOSS: each warp's sum of squared residuals
   long long chi_gal = -1;          // thread 0: galaxy whose chi^2 is still to be written
   float chi_iv = 0.0f;
-  for (int buf = 0;; buf ^= 1) {
-    __syncthreads();  // the previous galaxy is fully stored
-    if constexpr (LOSS) {
-      if (tid == 0 && chi_gal >= 0) {
-        float t = 0.0f;
-        for (int w = 0; w < WARPS; ++w) t += s_chi[w];
-        p.chi2[chi_gal] = chi_iv * t;
-        chi_gal = -1;
-      }
+  // thread 0, once every warp has added its residuals of galaxy chi_gal
+  auto write_chi2 = [&]() {
+    if (chi_gal >= 0) {
+      float t = 0.0f;
+      for (int w = 0; w < WARPS; ++w) t += s_chi[w];
+      p.chi2[chi_gal] = chi_iv * t;
+      chi_gal = -1;
     }
+  };
+  // No barrier at the top of the loop: a warp runs from its last row pair
+  // into the next galaxy's set-up.  Every read of the previous galaxy's
+  // tables, spectrum and staging happens before one of its column-phase
+  // barriers; its rows read only their own work row, the patch and the
+  // real-space table (one per record buffer) and the term count taken before
+  // the columns; the next barrier (record landed) precedes any write they
+  // could see.
+  __syncthreads();
+  for (int buf = 0;; buf ^= 1) {
     const int pos = s_pos[buf];
     if (pos < 0) break;
     if (tid == 0) {
@@ -235,6 +243,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
       if (tid == 0) set_status(p.status, MOG_ERR_TIMEOUT);
       return;
     }
+    if constexpr (LOSS)   // every warp has stored the previous galaxy and added its residuals
+      if (tid == 0) write_chi2();
     if (!r.ok) {
       if constexpr (LOSS)
         if (tid == 0) p.chi2[r.gal] = __int_as_float(0x7fc00000);   // NaN: a galaxy that is skipped
@@ -307,8 +317,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
           nyq[l] = cscale(cmul(pn, cmul(phx, phy)), acc);
         } else {
           const int t = i - H - 2 * N;
-          if (t < nrt) real_term(r, s_psf_mog, nullptr, kp, N, t, &rt);
-          else real_term_zero(t, &rt);
+          if (t < nrt) real_term(r, s_psf_mog, nullptr, kp, N, t, &rts[buf]);
+          else real_term_zero(t, &rts[buf]);
         }
       }
     }
@@ -316,6 +326,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
 
     const int nf = r.nf;
     const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
+    // the rows' term count, read while the next galaxy cannot yet change s_kpsf
+    const int nr = real_terms_padded(r.nrc * s_kpsf);
     float2 v[8];
     // ---- Steps 5-7a: columns k = 32 round + warp ----
     for (int round = 0; round < ROUNDS; ++round) {
@@ -402,7 +414,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
     }
 
     // ---- Step 7b + 8: row pairs p = 32 round + warp, each warp on its own ----
-    const int nr = real_terms_padded(r.nrc * s_kpsf);
+    const RealTerms& rt = rts[buf];
     for (int round = 0; round < ROUNDS; ++round) {
       const int pr = WARPS * round + f;
 #pragma unroll
@@ -458,6 +470,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
         lanczos_real_256(rt, nr, s_lzw, reinterpret_cast<float*>(smem), dst, f, j);
       }
     }
+  }
+  if constexpr (LOSS) {
+    __syncthreads();   // the last galaxy's residuals are in
+    if (tid == 0) write_chi2();
   }
 }
 
