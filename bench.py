@@ -41,6 +41,7 @@ SFU_PER_CLK_SM = 32                  # MUFU ex2 per SM per clock (measured live:
 FP32_FLOP_PER_CLK_SM = 256           # 128 FMA lanes x 2 (measured live: "pipe_rates")
 KERNEL_SOURCES = ("paper_2012_15797_gb300/csrc/render_fwd.cu", "paper_2012_15797_gb300/csrc/common.cuh")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "render_fwd_64_100k.md")
+KERNELS_PER_RENDER = 5   # the planner's three kernels, the record prologue, the size kernel
 
 
 def parse_args():
@@ -1016,7 +1017,9 @@ def run_ours(args):
         "config": workload_config(args.galaxies, world),
         "real_space_component_fraction": work["real_fraction"],
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": args.steps * 4, "clocks": clocks, "pipe_rates": pipes,
+        # per step: plan_histogram, plan_scan, plan_scatter, galaxy_prep and
+        # render_fwd_kernel<64> (the launch list in profiles/render_fwd_64_100k.md)
+        "gpu_launches": args.steps * KERNELS_PER_RENDER, "clocks": clocks, "pipe_rates": pipes,
         "extra": extra,
     }
     print(json.dumps(line))
