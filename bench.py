@@ -322,6 +322,64 @@ def _worker_timed(args):
     return n
 
 
+# The oracle on the secondary workloads (the 200k mixed batch, the 50k fit
+# problem): each worker takes every `cores`-th galaxy from its start for a
+# bounded wall time.
+def _oracle_init(kind, psfs):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from oracle import adjoint as A
+    from oracle import render as R
+    from workloads import fixed_galaxies_64, load_profile_tables, mixed_galaxies
+    _W.update(R=R, A=A, tables=load_profile_tables(), kind=kind, psfs=psfs, hats={})
+    _W["gals"] = mixed_galaxies(200_000) if kind == "mixed" else fixed_galaxies_64(50_000, 3)
+
+
+def _oracle_timed(args):
+    import numpy as np
+    start, stride, budget = args
+    R, A, gals, psfs, tables, hats = _W["R"], _W["A"], _W["gals"], _W["psfs"], _W["tables"], _W["hats"]
+    t0 = time.perf_counter()
+    n, i = 0, start
+    while time.perf_counter() - t0 < budget and i < len(gals):
+        g = gals.row(int(i))
+        key = (int(g["psf"]), int(g["size"]))
+        if key not in hats:
+            hats[key] = R.psf_spectrum(psfs[key[0]].image, key[1])
+        mog = psfs[key[0]].mog
+        model = R.render(g, None, mog, tables, psf_hat=hats[key])
+        if _W["kind"] == "render_grad":
+            # the step: loss gradient 2 ivar (model - data) and its VJP; the
+            # data (here 1.01 x the model, ivar 1) do not change its cost
+            resid = model - 1.01 * model
+            _ = float(np.sum(resid * resid))
+            A.vjp(g, hats[key], mog, tables, 2.0 * resid)
+        n += 1
+        i += stride
+    return n
+
+
+def oracle_baseline(kind, psfs, seconds):
+    """The FP64 oracle on a bounded sample of a secondary workload, spawn
+    workers over every host core: galaxies per wall second."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(kind, psfs))
+    try:
+        pool.map(_oracle_timed, [(c, cores, 0.2) for c in range(cores)])   # warm
+        t0 = time.perf_counter()
+        counts = pool.map(_oracle_timed, [(c + cores * 64, cores, seconds) for c in range(cores)])
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    done = sum(counts)
+    what = ("the 200k mixed batch (every galaxy's own side and PSF)" if kind == "mixed" else
+            "the 50k fit problem: render, loss gradient and its vector-Jacobian product per galaxy")
+    return {"value": done / wall, "unit": UNIT if kind == "mixed" else "patches rendered+grad/s", "cores": cores,
+            "kind": "oracle", "sample": f"{done} galaxies of {what}, interleaved over {cores} spawn workers, "
+                                        f"{seconds:.0f} s wall budget, FP64 numpy oracle"}
+
+
 def cpu_pool(galaxies):
     import multiprocessing as mp
     cores = os.cpu_count() or 1
@@ -382,7 +440,7 @@ def _event_ms(fn, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def extra_mixed(tables, device, steps, pk):
+def extra_mixed(tables, device, steps, pk, cpu_seconds=0.0):
     """200k galaxies, Sersic n U(0.5, 6), N = smallest of 32..256 >= 8 r_e,
     64 PSFs: eager calls with default launch shapes vs one CUDA-graph launch
     per step after the autotuner."""
@@ -453,10 +511,12 @@ def extra_mixed(tables, device, steps, pk):
     r.sync_status()
     res["roofline_per_size_alone"] = per
     r.close()
+    if cpu_seconds > 0:
+        res["cpu_baseline"] = oracle_baseline("mixed", psfs, cpu_seconds)
     return res
 
 
-def extra_render_grad(tables, psf, device, steps, pk):
+def extra_render_grad(tables, psf, device, steps, pk, cpu_seconds=0.0):
     """50k galaxies at 64^2: render, inverse-variance-weighted residual
     gradient (data from perturbed parameters + noise 0.01 peak), adjoint.
     The forward and adjoint kernels are also timed each on its own, for
@@ -525,6 +585,8 @@ def extra_render_grad(tables, psf, device, steps, pk):
            "roofline_forward_plus_adjoint_kernels": roofline(add_work(wf, wb), fwd_ms + bwd_ms, pk,
                                                              "render_fwd_kernel<64> + render_bwd_kernel<64>")}
     r.close()
+    if cpu_seconds > 0:
+        res["cpu_baseline"] = oracle_baseline("render_grad", [psf], cpu_seconds)
     return res
 
 
@@ -998,8 +1060,9 @@ def run_ours(args):
         cpu = cpu_baseline(args.galaxies, args.cpu_seconds)
     extra = None
     if world == 1 and not args.no_extra:
-        extra = {"mixed_sizes": extra_mixed(tables, local, args.extra_steps, pk),
-                 "render_grad": extra_render_grad(tables, psf, local, args.extra_steps, pk),
+        ocpu = 0.0 if args.no_cpu else 8.0
+        extra = {"mixed_sizes": extra_mixed(tables, local, args.extra_steps, pk, ocpu),
+                 "render_grad": extra_render_grad(tables, psf, local, args.extra_steps, pk, ocpu),
                  "lanczos_shift": extra_lanczos(tables, psf, local, args.extra_steps),
                  "eigen_psf": extra_eigen(tables, psf, local, args.extra_steps),
                  "composite": extra_composite(tables, psf, local, args.extra_steps),
