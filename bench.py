@@ -510,6 +510,17 @@ def extra_mixed(tables, device, steps, pk, cpu_seconds=0.0):
                         "frac": round(rf["frac"], 4), "fractions": rf["fractions"]}
     r.sync_status()
     res["roofline_per_size_alone"] = per
+    # the plain form: one library call per galaxy, on 2000 of them
+    sample = np.arange(0, len(gals), len(gals) // 2000)[:2000]
+    singles = [to_device(gals.subset([int(i)]), device=f"cuda:{device}") for i in sample]
+    one = torch.empty(256 * 256, dtype=torch.float32, device=f"cuda:{device}")
+    for bb in singles[:20]:
+        r.render(bb, one)
+    r.sync_status()
+    ms1 = _event_ms(lambda: [r.render(bb, one) for bb in singles], 1, st)
+    res["one_launch_per_galaxy"] = {"value": len(singles) / (ms1 / 1e3), "unit": UNIT, "galaxies": len(singles),
+                                    "note": "one mog_render_batch call per galaxy of the mixed batch (every 100th)"}
+    r.sync_status()
     r.close()
     if cpu_seconds > 0:
         res["cpu_baseline"] = oracle_baseline("mixed", psfs, cpu_seconds)
@@ -584,6 +595,24 @@ def extra_render_grad(tables, psf, device, steps, pk, cpu_seconds=0.0):
            "roofline": roofline(wb, bwd_ms, pk, "render_bwd_kernel<64>"),
            "roofline_forward_plus_adjoint_kernels": roofline(add_work(wf, wb), fwd_ms + bwd_ms, pk,
                                                              "render_fwd_kernel<64> + render_bwd_kernel<64>")}
+    # the plain form: one render-with-loss and one adjoint call per galaxy, on 2000 of them
+    singles = [to_device(model.subset([i]), device=dev) for i in range(2000)]
+    g1 = torch.empty(64 * 64, device=dev)
+    c1 = torch.empty(1, device=dev)
+    p1 = torch.empty(1, 6, device=dev)
+
+    def per_galaxy():
+        for i, bb in enumerate(singles):
+            r.render_chi2(bb, data[i * 4096:(i + 1) * 4096], ivar[i:i + 1], g1, c1)
+            r.render_backward(bb, g1, p1)
+
+    per_galaxy()
+    r.sync_status()
+    ms1 = _event_ms(per_galaxy, 1, st)
+    res["one_launch_per_galaxy"] = {"value": len(singles) / (ms1 / 1e3), "unit": "patches rendered+grad/s",
+                                    "galaxies": len(singles),
+                                    "note": "one mog_render_chi2 and one mog_render_backward call per galaxy"}
+    r.sync_status()
     r.close()
     if cpu_seconds > 0:
         res["cpu_baseline"] = oracle_baseline("render_grad", [psf], cpu_seconds)
