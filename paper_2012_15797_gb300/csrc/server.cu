@@ -450,9 +450,12 @@ void completer(mog_server* S) {
     mog_server::Lane* ready = nullptr;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      // woken by lane_done_cb; every 2 ms the lanes' events are also
-      // queried, so a batch whose callback did not run (its stream failed)
-      // still completes
+      // woken by lane_done_cb.  A launched batch is done only once its
+      // callback has run: an event query that already reports success must
+      // not free the lane, or the late callback would mark the lane's next
+      // batch done while it still runs (and its arena block be reused under
+      // it).  Every 2 ms the events are queried for errors only, so a batch
+      // whose stream failed (and whose callback may not run) still completes.
       // (the queries run outside the lock: no CUDA call is made under it)
       bool polled[16] = {};
       for (;;) {
@@ -460,7 +463,9 @@ void completer(mog_server* S) {
         for (auto& L : S->lanes) {
           if (!L.busy || !L.launched) continue;
           any = true;
-          if (L.status != MOG_OK || S->fired[L.idx].load(std::memory_order_acquire) || polled[L.idx]) {
+          const bool fired = S->fired[L.idx].load(std::memory_order_acquire);
+          if (L.status != MOG_OK || fired || polled[L.idx]) {
+            if (!fired && polled[L.idx] && L.status == MOG_OK) L.status = MOG_ERR_CUDA;   // its stream failed
             ready = &L;
             break;
           }
@@ -479,7 +484,10 @@ void completer(mog_server* S) {
           for (auto& L : S->lanes)
             if (L.busy && L.launched) idx[n++] = L.idx;
           lk.unlock();
-          for (int k = 0; k < n; ++k) polled[idx[k]] = cudaEventQuery(S->lanes[idx[k]].done) != cudaErrorNotReady;
+          for (int k = 0; k < n; ++k) {
+            const cudaError_t q = cudaEventQuery(S->lanes[idx[k]].done);
+            polled[idx[k]] = q != cudaSuccess && q != cudaErrorNotReady;
+          }
           lk.lock();
         }
       }
