@@ -136,3 +136,26 @@ def test_trace_rows_account_for_every_batch(gpu_renderer, setup):
     srv.timing(reset=True)
     assert srv.trace().shape[0] == 0
     srv.close()
+
+
+def test_many_small_batches_match_one_per_launch(gpu_renderer, setup):
+    """Hundreds of micro-batches over four lanes (small batch limit, requests
+    arriving faster than they are served, then slower): every request's
+    gradients and chi2 equal the one-request-per-launch results bit for bit,
+    so no lane is reused while its batch still runs."""
+    fits, state, _ = setup
+    reqs = _requests(fits, n=400, seed=17)
+    ref, _, st_ref = _serve(gpu_renderer, state, reqs, budget_bytes=1 << 30, lanes=1, max_batch_galaxies=0)
+    from paper_2012_15797_gb300.serving import Server
+    srv = Server(gpu_renderer, budget_bytes=1 << 30, lanes=4, max_batch_galaxies=96)
+    for st in state:
+        srv.add_fit(**st)
+    times = np.concatenate([np.zeros(200), 0.004 * np.arange(1, 201)])   # a burst, then one every 4 ms
+    tickets, keeps = srv.replay(reqs, times)
+    srv.wait_replayed(tickets, keeps)
+    stats = srv.stats()
+    srv.close()
+    assert stats["batches"] > 150
+    for (g1, c1), k in zip(ref, keeps):
+        np.testing.assert_array_equal(g1, k[1])
+        np.testing.assert_array_equal(c1, k[2])
