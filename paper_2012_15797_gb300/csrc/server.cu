@@ -95,6 +95,7 @@ struct Request {
   int fit;
   int64_t first, count;
   std::vector<float> params;  // count x 6
+  const int32_t* sizes = nullptr;  // patch sides of galaxies first.. (the fit's own array: never moves)
   float* grads;               // caller's
   float* chi2;                // caller's
   Clock::time_point submitted;
@@ -419,13 +420,15 @@ void scheduler(mog_server* S) {
     if (st == MOG_OK) {
       int64_t i = 0, off = 0;
       for (auto& r : take) {
-        const auto& sz = S->fit_sizes[r->fit];
+        // (outside the lock: the request's own pointer into its fit's sides,
+        // not the fit table, which a concurrent add_fit may reallocate)
+        const int32_t* sz = r->sizes;
         for (int64_t k = 0; k < r->count; ++k, ++i) {
           for (int c = 0; c < 6; ++c) L->st.params[c * g + i] = r->params[6 * k + c];
           L->st.fi[i] = r->fit;
           L->st.fi[g + i] = (int32_t)(r->first + k);
           L->st.offset[i] = off;
-          off += (int64_t)sz[r->first + k] * sz[r->first + k];
+          off += (int64_t)sz[k] * sz[k];
         }
         // staged: the request's parameter copy goes back to the allocator
         // now, so a long stream of requests reuses heap pages instead of
@@ -702,6 +705,7 @@ mog_status mog_server_submit(mog_server* S, const mog_request* req, uint64_t* ti
   }
   if (batch_bytes(req->count, pix) > S->arena.total())
     return fail(S->ctx, MOG_ERR_ARG, "request larger than the server's memory budget");
+  r->sizes = S->fit_sizes[req->fit].data() + req->first;
   r->ticket = S->next_ticket++;
   r->submitted = Clock::now();
   S->requests[r->ticket] = r;
