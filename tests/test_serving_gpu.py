@@ -159,3 +159,30 @@ def test_many_small_batches_match_one_per_launch(gpu_renderer, setup):
     for (g1, c1), k in zip(ref, keeps):
         np.testing.assert_array_equal(g1, k[1])
         np.testing.assert_array_equal(c1, k[2])
+
+
+def test_add_fits_while_serving(gpu_renderer, setup):
+    """Fits added while micro-batches are in flight (the device fit table
+    grows from 64 to 128 entries under load): the requests in flight and the
+    requests on the new fits are answered, and a new fit holding the same
+    state as fit 0 answers as fit 0 does."""
+    from paper_2012_15797_gb300.serving import Server
+    fits, state, _ = setup
+    reqs = _requests(fits, n=300, seed=23)
+    srv = Server(gpu_renderer, budget_bytes=1 << 30, lanes=4, max_batch_galaxies=128)
+    for st in state:
+        srv.add_fit(**st)
+    tickets, keeps = srv.replay(reqs, 0.002 * np.arange(len(reqs)))
+    ids = [srv.add_fit(**state[0]) for _ in range(100)]
+    srv.wait_replayed(tickets, keeps)
+    assert ids == list(range(len(state), len(state) + 100))
+    p = _requests(fits, n=1, seed=29)[0][2]
+    first = 0
+    while len(p) > len(fits[0]) - first:
+        p = p[:-1]
+    g0, c0, _ = srv.wait(srv.submit(0, first, p))
+    g1, c1, _ = srv.wait(srv.submit(ids[-1], first, p))
+    srv.close()
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(c0, c1)
+    assert all(np.all(np.isfinite(k[1])) for k in keeps)
