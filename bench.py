@@ -777,6 +777,43 @@ def extra_psf_create(tables, device, n=64):
             "ms_per_psf": ms / n, "value": n / (ms / 1e3), "unit": "PSFs created/s"}
 
 
+def extra_cufft(tables, psf, device, steps, pk, cases=((64, 100_000), (256, 5_000))):
+    """The library comparator (mog_render_batch_cufft: every galaxy's half
+    spectrum written out, one batched cuFFT inverse real transform, a
+    real-space pass) timed beside the fused render on the same batch, with
+    their largest difference and the comparator's HBM floor (its stages move
+    8 (N/2 + 1) N bytes of spectrum twice and 4 N^2 bytes of image three
+    times per galaxy)."""
+    import torch
+    from paper_2012_15797_gb300.renderer import Renderer, to_device
+    from workloads import fixed_galaxies_64
+
+    r = Renderer(tables, [psf], device=device)
+    st = torch.cuda.current_stream()
+    res = {}
+    for n, g in cases:
+        gals = fixed_galaxies_64(g, seed=6, size=n)
+        b = to_device(gals, device=f"cuda:{device}")
+        out_f = torch.empty(b.total, device=f"cuda:{device}")
+        out_c = torch.empty(b.total, device=f"cuda:{device}")
+        for _ in range(3):
+            r.render(b, out_f)
+            r.render_cufft(b, out_c)
+        r.sync_status()
+        ms_f = _event_ms(lambda: r.render(b, out_f), steps, st)
+        ms_c = _event_ms(lambda: r.render_cufft(b, out_c), steps, st)
+        r.sync_status()
+        flux = torch.from_numpy(gals.flux.astype("float32")).to(out_f.device)
+        d = ((out_c - out_f).abs().view(g, -1).amax(dim=1) / flux).max().item()
+        hbm = g * (2 * 8 * (n // 2 + 1) * n + 3 * 4 * n * n)
+        res[f"{n}x{n}"] = {"galaxies": g, "ms_fused": ms_f, "ms_cufft": ms_c, "cufft_over_fused": ms_c / ms_f,
+                           "max_abs_diff_over_flux": d, "cufft_hbm_bytes": hbm,
+                           "cufft_hbm_floor_ms": hbm / (pk["hbm"] / 1e3) if pk.get("hbm") else None}
+        del out_f, out_c, b
+    r.close()
+    return res
+
+
 def extra_per_galaxy(tables, psf, device, n=2000):
     """The plain form: the same math with one library call (planner, record,
     render launches) per galaxy."""
@@ -1098,7 +1135,8 @@ def run_ours(args):
                  "sersic_gradient": extra_sersic_grad(tables, local, args.extra_steps),
                  "psf_fit": extra_psf_fit(tables, local),
                  "psf_create": extra_psf_create(tables, local),
-                 "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local)}
+                 "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local),
+                 "cufft_comparator": extra_cufft(tables, psf, local, args.extra_steps, pk)}
         bound = 200_000 / ((extra["mixed_sizes"]["ms_graph"] + extra["sersic_gradient"]["ms_grad6"]) / 1e3)
         extra["serving"] = extra_serving(tables, local, kernel_bound=bound)
 

@@ -258,6 +258,29 @@ mog_status mog_render_batch_noalloc(mog_ctx* ctx, const mog_batch* batch, float*
 mog_status mog_render_batch_host(mog_ctx* ctx, const mog_batch* batch, float* out, int64_t chunk, unsigned flags);
 
 /*
+ * Library comparator of mog_render_batch: the same model (Section 2, Steps
+ * 3-8, phase shift) in three stages that each go through device memory
+ * instead of the fused kernels: a kernel writes every galaxy's rfft half
+ * spectrum (Fourier mixture times PSF spectrum times shift phase, Steps 5-6),
+ * cuFFT runs one batched inverse real 2-D FFT over all of them (Step 7), and
+ * a kernel adds the real-space terms (Step 8) while copying each transform to
+ * the galaxy's patch.  It is there to be timed beside mog_render_batch; the
+ * values agree with it to float rounding.
+ *
+ * batch->size_mask must name exactly one patch side (one bit) unless the
+ * batch is empty; galaxies of other sides, eigen-PSF galaxies and invalid
+ * parameters are skipped with status MOG_ERR_DEVICE.  out: as
+ * mog_render_batch.  cuFFT is opened at run time; the context keeps the plan
+ * of the last (side, count) pair and scratch of 8 (N/2 + 1) N + 4 N^2 bytes
+ * per galaxy of the batch.
+ * Asynchronous on `stream` once the plan exists (creating it synchronises).
+ * Errors: MOG_ERR_ARG for a size_mask that is not one side, a misaligned
+ * out or more than 2^31-1 spectrum elements; MOG_ERR_STATE when cuFFT cannot
+ * be opened; MOG_ERR_CUDA when cuFFT fails.
+ */
+mog_status mog_render_batch_cufft(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);
+
+/*
  * Adjoint of mog_render_batch (gradients for model fitting; the paper's
  * forward model of Section 2 differentiated analytically): for every galaxy
  * of the batch, given grad_out = dL/d(patch pixel) laid out exactly like the

@@ -70,7 +70,7 @@ def build(verbose=False, force=False, extra_flags=()):
             if verbose and log:
                 print(f"[{os.path.basename(src)}]\n{log}", file=sys.stderr)
     if force or _stale(LIB, objs):
-        cmd = [exe, *ARCH, "-shared", "-o", LIB, *objs]
+        cmd = [exe, *ARCH, "-shared", "-o", LIB, *objs, "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -197,6 +197,7 @@ mog_status mog_destroy_context(mog_ctx* ctx) {
   cudaFree(ctx->d_status);
   workspace_free(&ctx->ws);
   host_lanes_free(ctx->host_lanes, 2);
+  cufft_release(ctx);
   cudaFree(ctx->d_dft_scratch);
   for (auto& t : ctx->pending) {
     cudaEventDestroy(t.a);
@@ -556,6 +557,24 @@ mog_status mog_render_chi2(mog_ctx* ctx, const mog_batch* batch, const float* da
   loss.chi2 = chi2;
   loss.model = model;
   return render_with(ctx, &ctx->ws, batch, grad_pix, static_cast<cudaStream_t>(stream), false, false, &loss);
+}
+
+mog_status mog_render_batch_cufft(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  mog_status st = check_batch(ctx, batch);
+  if (st != MOG_OK) return st;
+  if (batch->count == 0) return MOG_OK;
+  const uint32_t m = batch->size_mask;
+  if (m == 0 || (m & (m - 1)) || !(m & FWD_BUCKETS))
+    return fail(ctx, MOG_ERR_ARG, "the cuFFT comparator needs a size_mask naming one patch side");
+  if (!out || (reinterpret_cast<uintptr_t>(out) & 15)) return fail(ctx, MOG_ERR_ARG, "out must be 16-byte aligned");
+  if (!cufft_available()) return fail(ctx, MOG_ERR_STATE, "the cuFFT library could not be opened");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  RenderParams p;
+  if ((st = plan_batch(ctx, &ctx->ws, batch, out, m, s, &p)) != MOG_OK) return st;
+  p.records = ctx->ws.records;
+  MOG_CUDA(ctx, launch_galaxy_prep(p, batch->count, ctx->ws.records, s));
+  return render_cufft(ctx, p, batch->count, bucket_side(__builtin_ctz(m)), s);
 }
 
 mog_status mog_render_backward(mog_ctx* ctx, const mog_batch* batch, const float* grad_out, float* grad_params,

@@ -82,6 +82,18 @@ struct mog_ctx {
   mog::LaunchShape tune_fwd[mog::NBUCKET], tune_bwd[mog::NBUCKET];
   bool serial_buckets = false;   // launch the size kernels one after the other instead of forked
   cudaStream_t capture = nullptr;
+  // mog_render_batch_cufft (the library comparator): its cuFFT plan, cached
+  // for one (side, batch) pair, and the spectra and inverse transforms
+  struct CufftState {
+    int plan = 0;                  // cufftHandle
+    bool plan_ok = false;
+    int n = 0;
+    int64_t batch = 0;
+    float2* spec = nullptr;
+    size_t spec_cap = 0;           // float2
+    float* img = nullptr;
+    size_t img_cap = 0;            // float
+  } cufft;
 };
 
 namespace mog {
@@ -116,5 +128,10 @@ mog_status render_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, floa
 mog_status backward_with(mog_ctx* ctx, Workspace* ws, const mog_batch* batch, const float* grad_out,
                          float* grad_params, cudaStream_t s,
                          bool grad_n = false);
+// The library comparator (cufft_ref.cu): spectra, cuFFT C2R and the
+// real-space add for the planned galaxies of side n in `p`.
+mog_status render_cufft(mog_ctx* ctx, const RenderParams& p, int64_t count, int n, cudaStream_t s);
+bool cufft_available();
+void cufft_release(mog_ctx* ctx);
 
 }  // namespace mog

@@ -133,6 +133,17 @@ class Renderer:
         fn(self.ctx, b, out.data_ptr(), s.cuda_stream)
         return out
 
+    def render_cufft(self, batch, out=None, stream=None):
+        """The library comparator of ``render`` (mog_render_batch_cufft): the
+        same patches through written-out spectra, a batched cuFFT inverse
+        real transform and a real-space pass.  One patch side per batch."""
+        if out is None:
+            out = torch.empty(batch.total, dtype=torch.float32, device=self.device)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        b = capi.make_batch(batch.count, batch.ptrs(), batch.size_mask())
+        capi.mog_render_batch_cufft(self.ctx, b, out.data_ptr(), s.cuda_stream)
+        return out
+
     def render_host(self, host, out=None, chunk=0, shift="phase"):
         """Renders a batch held in host memory, ``host`` = ``host_batch(...)``
         (tensors, pinned for asynchronous copies; packed offsets), into a host
