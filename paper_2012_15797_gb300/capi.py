@@ -38,7 +38,7 @@ EXPORTED = (
     "mog_create_eigen_psf", "mog_render_batch_ex", "mog_render_backward_ex", "mog_fit_psf_mixture",
     "mog_render_batch_host", "mog_measure_pipe_rates", "mog_server_inject_fault", "mog_check_wait_timeout",
     "mog_set_launch_shape", "mog_chi2_gradient", "mog_server_timing", "mog_server_trace", "mog_render_chi2",
-    "mog_render_batch_cufft",
+    "mog_render_batch_cufft", "mog_render_composite",
 )
 MOG_TRACE_COLS = 8
 MOG_NOALLOC_MAX_GALAXIES = 16384
@@ -123,6 +123,7 @@ def _load():
         "mog_server_trace": ([VP, P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_int64)], I),
         "mog_render_chi2": ([VP, P(mog_batch), VP, VP, VP, VP, VP, VP], I),
         "mog_render_batch_cufft": ([VP, P(mog_batch), VP, VP], I),
+        "mog_render_composite": ([VP, P(mog_batch), P(mog_batch), VP, VP], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -228,6 +229,13 @@ MOG_RENDER_LANCZOS, MOG_RENDER_ADD = 1, 2
 def mog_render_batch_ex(ctx, batch, out_ptr, stream=0, flags=0):
     _check(ctx, _lib.mog_render_batch_ex(ctx, ctypes.byref(batch), ctypes.c_void_p(int(out_ptr)),
                                          ctypes.c_void_p(int(stream)), ctypes.c_uint(int(flags))))
+
+
+def mog_render_composite(ctx, first, second, out_ptr, stream=0):
+    """Composite galaxies in one pass (see include/mogconv.h): galaxy g of
+    ``first`` and of ``second`` are the two profiles of one galaxy."""
+    _check(ctx, _lib.mog_render_composite(ctx, ctypes.byref(first), ctypes.byref(second),
+                                          ctypes.c_void_p(int(out_ptr)), ctypes.c_void_p(int(stream))))
 
 
 def mog_render_batch_cufft(ctx, batch, out_ptr, stream=0):

@@ -559,6 +559,50 @@ mog_status mog_render_chi2(mog_ctx* ctx, const mog_batch* batch, const float* da
   return render_with(ctx, &ctx->ws, batch, grad_pix, static_cast<cudaStream_t>(stream), false, false, &loss);
 }
 
+mog_status mog_render_composite(mog_ctx* ctx, const mog_batch* first, const mog_batch* second, float* out,
+                                void* stream) {
+  if (!ctx) return MOG_ERR_ARG;
+  mog_status st = check_batch(ctx, first);
+  if (st != MOG_OK) return st;
+  if ((st = check_batch(ctx, second)) != MOG_OK) return st;
+  if (second->count != first->count) return fail(ctx, MOG_ERR_ARG, "the two profiles' batches differ in count");
+  if (first->count == 0) return MOG_OK;
+  if (!out || (reinterpret_cast<uintptr_t>(out) & 15)) return fail(ctx, MOG_ERR_ARG, "out must be 16-byte aligned");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Workspace* ws = &ctx->ws;
+  const int64_t g = first->count;
+  const uint32_t want = first->size_mask ? (first->size_mask & FWD_BUCKETS) : FWD_BUCKETS;
+  MOG_CUDA(ctx, cudaSetDevice(ctx->device));
+  // two records per galaxy: the second profile's after the first's
+  if ((st = ensure_capacity(ctx, ws, 2 * g)) != MOG_OK) return st;
+  if ((want & 0x8) && !ws->bwd256)
+    MOG_CUDA(ctx, cudaMalloc(&ws->bwd256, render_bwd256_scratch_bytes(ctx->num_sms)));
+  RenderParams p;
+  if ((st = plan_batch(ctx, ws, first, out, FWD_BUCKETS, s, &p)) != MOG_OK) return st;
+  unsigned char* rec2 = ws->records + (size_t)g * RECORD_BYTES;
+  p.records = ws->records;
+  p.records2 = rec2;
+  p.scratch256 = ws->bwd256;
+  p.eigen = 0;   // eigen-PSF galaxies are rejected by the record prologue
+  MOG_CUDA(ctx, launch_composite_prep(p, view_of(second), g, ws->records, rec2, s));
+  return launch_buckets(ctx, ws, first, FWD_BUCKETS, s, [&](int n, cudaStream_t bs) -> cudaError_t {
+    RenderParams q = p;
+    const LaunchShape& ls = ctx->tune_fwd[bucket_of(n)];
+    q.chunk = ls.chunk;
+    q.sched = 0;
+    if (n != 256) return launch_render_fwd_composite(n, q, ctx->num_sms, ls.ctas_per_sm, bs);
+    // 256 x 256: the first profile rendered, then the second added, each by
+    // the one-profile kernel (its work counter re-zeroed in between)
+    q.records2 = nullptr;
+    cudaError_t e = launch_render_fwd256(q, ctx->num_sms, ls.ctas_per_sm, bs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(q.queue + bucket_of(256), 0, sizeof(int32_t), bs);
+    q.records = rec2;
+    q.accumulate = 1;
+    if (e == cudaSuccess) e = launch_render_fwd256(q, ctx->num_sms, ls.ctas_per_sm, bs);
+    return e;
+  });
+}
+
 mog_status mog_render_batch_cufft(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream) {
   if (!ctx) return MOG_ERR_ARG;
   mog_status st = check_batch(ctx, batch);

@@ -872,10 +872,15 @@ __device__ inline void adjoint_record_warp(const BatchView& b, int64_t g, int n,
 // loop over term pairs reads a pair with four 16-byte loads (every lane of a
 // warp reads the same pair: broadcasts): p[t / 2] holds, term t at slot
 // t & 1 of each float2 field, (qa, my), (mx, qb), (qc, w), (r8, unused).
-struct RealTerms {
-  float4 p[RMAX / 2][4];
+// R: capacity in terms (RMAX for one galaxy; a composite of two profiles
+// takes twice that).
+template <int R>
+struct RealTermsN {
+  float4 p[R / 2][4];
 };
-__device__ __forceinline__ float* real_term_slots(RealTerms* rt, int t) {
+using RealTerms = RealTermsN<RMAX>;
+template <int R>
+__device__ __forceinline__ float* real_term_slots(RealTermsN<R>* rt, int t) {
   return reinterpret_cast<float*>(&rt->p[t >> 1][0]) + (t & 1);
 }
 
@@ -883,8 +888,11 @@ __device__ __forceinline__ float* real_term_slots(RealTerms* rt, int t) {
 // (weight, mean x, mean y, vxx, vxy, vyy).
 // eig_w: mixture weights at the galaxy's position for an eigen-PSF (null for
 // a constant PSF, whose weights are psf_mog[j][0]).
+// slot: the table entry it goes to (t unless the table holds the terms of
+// several records).
+template <int R>
 __device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*psf_mog)[6], const float* eig_w,
-                                          int kpsf, int n, int t, RealTerms* rt) {
+                                          int kpsf, int n, int t, RealTermsN<R>* rt, int slot = -1) {
   const int c = t / kpsf, jj = t - c * kpsf;
   const float* m = psf_mog[jj];
   const float wj = eig_w ? eig_w[jj] : m[0];
@@ -892,7 +900,7 @@ __device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*p
   const float vxx = v * r.s11 + m[3], vxy = v * r.s12 + m[4], vyy = v * r.s22 + m[5];
   const float det = vxx * vyy - vxy * vxy;
   const float idet = 1.0f / det;
-  float* q = real_term_slots(rt, t);   // field k of term t at q[2 k]
+  float* q = real_term_slots(rt, slot < 0 ? t : slot);   // field k of the term at q[2 k]
   q[0] = -0.5f * LOG2E * vyy * idet;               // qa
   q[2] = 0.5f * (float)n + r.y + m[2];             // my
   q[4] = 0.5f * (float)n + r.x + m[1];             // mx
@@ -908,7 +916,8 @@ __device__ __forceinline__ void real_term(const GalaxyRecord& r, const float (*p
 // padded with one term that contributes exactly zero.
 __host__ __device__ constexpr int real_terms_padded(int nr) { return (nr + 1) & ~1; }
 
-__device__ __forceinline__ void real_term_zero(int t, RealTerms* rt) {
+template <int R>
+__device__ __forceinline__ void real_term_zero(int t, RealTermsN<R>* rt) {
   float* q = real_term_slots(rt, t);   // a flat exponent (2^0 = 1) times weight 0
   for (int k = 0; k < 8; ++k) q[2 * k] = 0.0f;
   q[12] = 1.0f;
@@ -921,8 +930,8 @@ __device__ __forceinline__ void real_term_zero(int t, RealTerms* rt) {
 // packed f32x2 instructions, so each pixel step is three instructions for two
 // terms.  Real-space terms are wide (n_sigma < 4), so a start value that
 // underflows stays negligible over a run of at most 8 pixels.
-template <int L>
-__device__ __forceinline__ void real_space_run(const RealTerms& rt, int nr2, float yy, float x0, float (&out)[L]) {
+template <int L, int R>
+__device__ __forceinline__ void real_space_run(const RealTermsN<R>& rt, int nr2, float yy, float x0, float (&out)[L]) {
   const float2 Y = make_float2(yy, yy), X = make_float2(x0, x0);
   const float2 NEG = make_float2(-1.0f, -1.0f), TWO = make_float2(2.0f, 2.0f), ONE = make_float2(1.0f, 1.0f);
   static_assert(L >= 1 && L <= 8, "runs of at most 8 pixels");

@@ -19,6 +19,7 @@ struct RenderParams {
   const int32_t* bucket_count;  // [NBUCKET]
   int32_t* queue;               // [NBUCKET] work counters, zeroed by the planner
   const unsigned char* records; // RECORD_BYTES per planned position (GalaxyRecord)
+  const unsigned char* records2 = nullptr;   // composites: the second profile's record per planned position
   int* status;
   int chunk;                    // queue positions taken per request
   int lanczos = 0;              // 1: sub-pixel shift by Lanczos convolution
@@ -98,6 +99,13 @@ cudaError_t render_noalloc(const RenderParams& proto, int64_t count, uint32_t wa
 int kernel_occupancy(const void* fn, int threads, size_t smem);
 
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
+// Composites (mog_render_composite), N = 32, 64, 128: one transform per
+// galaxy for the two profiles of p.records and p.records2.
+cudaError_t launch_render_fwd_composite(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
+// Records of composites: the first profile's (batch p.b) at records, the
+// second's (batch `second`, same centre, size, PSF and patch) at records2.
+cudaError_t launch_composite_prep(const RenderParams& p, const BatchView& second, int64_t count,
+                                  unsigned char* records, unsigned char* records2, cudaStream_t s);
 cudaError_t launch_render_fwd256(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
 // Resident CTAs per SM of the plain forward kernel for side n and radix
 // schedule `sched` (what the autotuner searches up to).

@@ -124,6 +124,42 @@ cudaError_t launch_galaxy_prep(const RenderParams& p, int64_t count, unsigned ch
   return cudaGetLastError();
 }
 
+// Composites: one warp per planned position writes both profiles' records.
+// The second batch must give the galaxy the same centre, patch side, PSF and
+// patch offset (compared exactly); otherwise, or when either profile is
+// invalid, both records are marked skipped and the status word is set.
+__global__ void composite_prep(RenderParams p, BatchView second, unsigned char* records, unsigned char* records2) {
+  const int total = p.bucket_start[NBUCKET - 1] + p.bucket_count[NBUCKET - 1];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (int pos = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pos < total; pos += warps) {
+    const int64_t g = p.order[pos];
+    const int n = p.b.size[g];
+    GalaxyRecord* r1 = reinterpret_cast<GalaxyRecord*>(records + (size_t)pos * RECORD_BYTES);
+    GalaxyRecord* r2 = reinterpret_cast<GalaxyRecord*>(records2 + (size_t)pos * RECORD_BYTES);
+    galaxy_record_warp(p.b, g, n, p.profiles, p.psfs, p.status, false, false, r1);
+    galaxy_record_warp(second, g, n, p.profiles, p.psfs, p.status, false, false, r2);
+    __syncwarp();
+    if (lane == 0) {
+      const bool same = second.x[g] == p.b.x[g] && second.y[g] == p.b.y[g] && second.size[g] == n &&
+                        second.psf[g] == p.b.psf[g] && second.offset[g] == p.b.offset[g];
+      if (!same || !r1->ok || !r2->ok) {
+        if (!same) set_status(p.status, MOG_ERR_DEVICE);
+        r1->ok = 0;
+        r2->ok = 0;
+      }
+    }
+  }
+}
+
+cudaError_t launch_composite_prep(const RenderParams& p, const BatchView& second, int64_t count,
+                                  unsigned char* records, unsigned char* records2, cudaStream_t s) {
+  const int64_t blocks = (count + 7) / 8;
+  composite_prep<<<(int)(blocks < 8192 ? (blocks > 0 ? blocks : 1) : 8192), 256, 0, s>>>(p, second, records,
+                                                                                         records2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_plan(const BatchView& b, int64_t count, const PlanScratch& ps, int supported, int* status,
                         cudaStream_t s) {
   static_assert(NKEY % 1024 == 0, "scan assumes NKEY multiple of 1024");

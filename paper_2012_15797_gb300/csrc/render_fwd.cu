@@ -31,7 +31,9 @@ namespace mog {
 // shared memory (the PSF spectrum is read from L2 instead of staged, and the
 // column transforms use one work row per group), so that two CTAs share an
 // SM and one computes while the other waits at a CTA barrier.
-template <int N, int CPG = 1, int V = 0>
+// COMP: composites of two profiles (two records per galaxy, twice the
+// real-space terms).
+template <int N, int CPG = 1, int V = 0, bool COMP = false>
 struct FwdCfg {
   static constexpr int H = N / 2 + 1;
   static constexpr int TPF = N / 8;          // threads per FFT
@@ -75,9 +77,11 @@ struct FwdCfg {
   static constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
   static constexpr size_t off_py = off_px + sizeof(float2) * H;
   static constexpr size_t off_nyq = off_py + sizeof(float2) * N;
+  using RT = RealTermsN<COMP ? 2 * RMAX : RMAX>;
+  static constexpr int RECS = COMP ? 2 : 1;   // records per galaxy
   static constexpr size_t off_rec = (off_nyq + sizeof(float2) * N + 15) & ~size_t(15);
-  static constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);   // two tables, one per record buffer
-  static constexpr size_t off_bar = (off_rt + 2 * sizeof(RealTerms) + 15) & ~size_t(15);
+  static constexpr size_t off_rt = off_rec + 2 * RECS * sizeof(GalaxyRecord);   // two tables, one per record buffer
+  static constexpr size_t off_bar = (off_rt + 2 * sizeof(RT) + 15) & ~size_t(15);
   static constexpr size_t SMEM = off_bar + 3 * sizeof(uint64_t);
 };
 
@@ -176,12 +180,19 @@ __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, 
 // LOSS: the loss mode of mog_render_chi2 (the stored values are the gradient
 // of chi^2 = ivar sum (model - data)^2 with respect to the pixels, chi^2 per
 // galaxy is reduced over the CTA).
-template <int N, bool LZ, bool EIG, int CPG = 1, int V = 0, bool LOSS = false>
-__global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>::MIN_BLOCKS)
+// COMP: composite galaxies (mog_render_composite): each galaxy has a second
+// record (the bulge, p.records2) with the same centre, PSF and patch; both
+// profiles' Fourier mixtures, each with its own quadratic form, are summed
+// on the grid before the one transform, and both sets of real-space terms
+// are added at the store.
+template <int N, bool LZ, bool EIG, int CPG = 1, int V = 0, bool LOSS = false, bool COMP = false>
+__global__ void __launch_bounds__(FwdCfg<N, CPG, V, COMP>::THREADS, FwdCfg<N, CPG, V, COMP>::MIN_BLOCKS)
     render_fwd_kernel(RenderParams p) {
-  using C = FwdCfg<N, CPG, V>;
+  using C = FwdCfg<N, CPG, V, COMP>;
+  using RT = typename C::RT;
   static_assert(!(LZ && CPG > 1), "the Lanczos variant keeps one column per group");
   static_assert(!(LZ && LOSS), "the loss mode renders with the phase shift");
+  static_assert(!(COMP && (LZ || EIG || LOSS)), "composites: phase shift, constant PSFs, plain render");
   constexpr int WARPS = C::THREADS / 32;
   constexpr int TPF = C::TPF, LS = C::LS;
   constexpr int B = bucket_of(N);
@@ -198,12 +209,13 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
   float2* py = reinterpret_cast<float2*>(smem + C::off_py);
   float2* nyq = reinterpret_cast<float2*>(smem + C::off_nyq);
   GalaxyRecord* rec = reinterpret_cast<GalaxyRecord*>(smem + C::off_rec);
-  RealTerms* rts = reinterpret_cast<RealTerms*>(smem + C::off_rt);
+  [[maybe_unused]] GalaxyRecord* rec2 = rec + 2;   // COMP: the second record of each buffer
+  RT* rts = reinterpret_cast<RT*>(smem + C::off_rt);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + C::off_bar);   // [0] PSF, [1..2] records
   __shared__ int s_pos[2];
   __shared__ float* s_dst[2];   // per record buffer: output patch and padded real-space term count
   __shared__ int s_nr[2];
-  __shared__ float4 s_fc[KMAX];   // Fourier components as (a, a, c, c): operand pairs of f32x2
+  __shared__ float4 s_fc[C::RECS * KMAX];   // Fourier components as (a, a, c, c): operand pairs of f32x2
   __shared__ float s_lzw[2][16];  // LZ, per record buffer: Lanczos weights along x [0, 7) and y [8, 15)
   // LOSS, per record buffer: the galaxy's data patch, model output (or null),
   // ivar, index, and each warp's sum of squared residuals
@@ -232,6 +244,17 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
   const int count = p.bucket_count[B];
   const int first = p.bucket_start[B];   // planned position of this bucket's first galaxy
   const unsigned char* records = p.records + (size_t)first * RECORD_BYTES;
+  [[maybe_unused]] const unsigned char* records2 = COMP ? p.records2 + (size_t)first * RECORD_BYTES : nullptr;
+  // the record(s) of planned position pos into buffer b
+  auto load_records = [&](int b, int pos) {
+    if constexpr (COMP) {
+      mbar_expect_tx(&bar[1 + b], 2 * sizeof(GalaxyRecord));
+      bulk_copy(&rec[b], records + (size_t)pos * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1 + b]);
+      bulk_copy(&rec2[b], records2 + (size_t)pos * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1 + b]);
+    } else {
+      bulk_load(&rec[b], records + (size_t)pos * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1 + b]);
+    }
+  };
   // work queue, used by thread 0 only: positions are taken p.chunk at a time and
   // the next chunk is requested one chunk ahead, so the atomic's latency is
   // off the critical path
@@ -253,7 +276,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
     q_ahead = atomicAdd(&p.queue[B], p.chunk);
     const int p0 = next_position();
     s_pos[0] = p0;
-    if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1]);
+    if (p0 >= 0) load_records(0, p0);
   }
   float2* wa = WA + C::row(f);   // this group's row in pass A
   int cur_psf = -1;
@@ -273,8 +296,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
     if (tid == 0) {
       const int np = next_position();
       s_pos[buf ^ 1] = np;
-      if (np >= 0)
-        bulk_load(&rec[buf ^ 1], records + (size_t)np * RECORD_BYTES, sizeof(GalaxyRecord), &bar[1 + (buf ^ 1)]);
+      if (np >= 0) load_records(buf ^ 1, np);
     }
     const bool rec_landed = mbar_wait(&bar[1 + buf], (rec_parity >> buf) & 1u);
     rec_parity ^= 1u << buf;
@@ -303,7 +325,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
     }
     const bool landed = rec_landed && psf_landed;
     const bool work = landed && r.ok;
-    RealTerms& rt = rts[buf];
+    RT& rt = rts[buf];
     // the spectrum in global memory (L2-resident) when it is not staged
     const float2* psf_g = nullptr;
     int k_eig = 0;
@@ -315,7 +337,9 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
       // the PSF id from a register (cur_psf) unless eigen-PSFs reset it: one
       // shared-memory load less on the path to the set-up tasks
       const DevPsf& ps = p.psfs[EIG ? r.psf : cur_psf];
-      const int kp = ps.k, nrt = r.nrc * kp, nr2 = real_terms_padded(nrt);
+      // COMP: the bulge's terms follow the disk's (nrt1 of them)
+      const int kp = ps.k, nrt1 = r.nrc * kp, nrt = nrt1 + (COMP ? rec2[buf].nrc * kp : 0);
+      const int nr2 = real_terms_padded(nrt), nf1 = r.nf;
       if constexpr (!C::PSF_SMEM) {
         psf_g = ps.spec[B];
         k_eig = eig ? ps.k_eig : 0;
@@ -334,7 +358,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
       }
       const float gx = r.x, gy = r.y;
       const float* lzw = LZ ? p.lzw + ((size_t)first + pos) * 16 : nullptr;
-      const int t0 = C::H + 2 * N, ntask = t0 + nr2 + r.nf;
+      const int t0 = C::H + 2 * N, ntask = t0 + nr2 + nf1 + (COMP ? rec2[buf].nf : 0);
       for (int i = tid; i < ntask; i += C::THREADS) {
         float sn, cs;
         if (i < C::H) {
@@ -369,6 +393,11 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
           const float q = fmaf(om, fmaf(r.s22, om, r.s12), 0.25f * r.s11);
           float acc = 0.0f;
           for (int c = 0; c < r.nf; ++c) acc = fmaf(r.famp[c], ex2(r.fcoef[c] * q), acc);
+          if constexpr (COMP) {
+            const GalaxyRecord& r2 = rec2[buf];
+            const float q2 = fmaf(om, fmaf(r2.s22, om, r2.s12), 0.25f * r2.s11);
+            for (int c = 0; c < r2.nf; ++c) acc = fmaf(r2.famp[c], ex2(r2.fcoef[c] * q2), acc);
+          }
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
           sincospif(-gx, &sn, &cs);
@@ -385,9 +414,16 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
           nyq[l] = cscale(cmul(pn, cmul(phx, phy)), acc);
         } else {
           const int t = i - t0;
-          if (t < nrt) real_term(r, ps.mog, eig ? pc + 8 : nullptr, kp, N, t, &rt);
+          if (t < nrt1) real_term(r, ps.mog, eig ? pc + 8 : nullptr, kp, N, t, &rt);
+          else if (COMP && t < nrt) real_term(rec2[buf], ps.mog, nullptr, kp, N, t - nrt1, &rt, t);
           else if (t < nr2) real_term_zero(t, &rt);
-          else s_fc[t - nr2] = make_float4(r.famp[t - nr2], r.famp[t - nr2], r.fcoef[t - nr2], r.fcoef[t - nr2]);
+          else if (!COMP || t - nr2 < nf1)
+            s_fc[t - nr2] = make_float4(r.famp[t - nr2], r.famp[t - nr2], r.fcoef[t - nr2], r.fcoef[t - nr2]);
+          else if constexpr (COMP) {
+            const GalaxyRecord& r2 = rec2[buf];
+            const int c = t - nr2 - nf1;
+            s_fc[t - nr2] = make_float4(r2.famp[c], r2.famp[c], r2.fcoef[c], r2.fcoef[c]);
+          }
         }
       }
     }
@@ -443,6 +479,30 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V>::THREADS, FwdCfg<N, CPG, V>:
           for (int k = 0; k < 4; ++k) {
             const float2 e = __fmul2_rn(c2, q[k]);
             s[k] = __ffma2_rn(a2, make_float2(ex2(e.x), ex2(e.y)), s[k]);
+          }
+        }
+        if constexpr (COMP) {
+          // the bulge's components, on its own quadratic form
+          const GalaxyRecord& r2 = rec2[buf];
+          const float b0 = r2.s11 * nu * nu, b1 = 2.0f * r2.s12 * nu, t22 = r2.s22;
+          const int nf2 = r2.nf;
+          float qmin2 = 3.4e38f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float om0 = omj + (float)(2 * k * TPF - (2 * k >= 4 ? N : 0)) * INV_N;
+            const float om1 = omj + (float)((2 * k + 1) * TPF - (2 * k + 1 >= 4 ? N : 0)) * INV_N;
+            q[k] = make_float2(fmaf(om0, fmaf(t22, om0, b1), b0), fmaf(om1, fmaf(t22, om1, b1), b0));
+            qmin2 = fminf(qmin2, fminf(q[k].x, q[k].y));
+          }
+          for (int i = nf; i < nf + nf2; ++i) {
+            const float4 ac = s_fc[i];
+            if (!__any_sync(0xffffffffu, ac.z * qmin2 > NEGLIGIBLE_LOG2)) continue;
+            const float2 a2 = make_float2(ac.x, ac.y), c2 = make_float2(ac.z, ac.w);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float2 e = __fmul2_rn(c2, q[k]);
+              s[k] = __ffma2_rn(a2, make_float2(ex2(e.x), ex2(e.y)), s[k]);
+            }
           }
         }
         const float2 pxf = px[col];
@@ -589,22 +649,24 @@ constexpr int fwd_cpg() { return (N == 128 && !LZ) ? 2 : 1; }
 
 static_assert(2 * (FwdCfg<128, 2>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 CTAs share an SM's shared memory");
 
-template <int N, bool LZ = false, bool EIG = false, int V = 0, bool LOSS = false>
+static_assert(2 * (FwdCfg<128, 2, 0, true>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 composite CTAs share an SM");
+
+template <int N, bool LZ = false, bool EIG = false, int V = 0, bool LOSS = false, bool COMP = false>
 static int fwd_occupancy() {
   constexpr int CPG = fwd_cpg<N, LZ>();
-  using C = FwdCfg<N, CPG, V>;
-  return kernel_occupancy(reinterpret_cast<const void*>(render_fwd_kernel<N, LZ, EIG, CPG, V, LOSS>), C::THREADS,
-                          C::SMEM);
+  using C = FwdCfg<N, CPG, V, COMP>;
+  return kernel_occupancy(reinterpret_cast<const void*>(render_fwd_kernel<N, LZ, EIG, CPG, V, LOSS, COMP>),
+                          C::THREADS, C::SMEM);
 }
 
-template <int N, bool LZ, bool EIG, int V, bool LOSS = false>
+template <int N, bool LZ, bool EIG, int V, bool LOSS = false, bool COMP = false>
 static cudaError_t launch_fwd_mode(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
   constexpr int CPG = fwd_cpg<N, LZ>();
-  using C = FwdCfg<N, CPG, V>;
-  const int occ = fwd_occupancy<N, LZ, EIG, V, LOSS>();
+  using C = FwdCfg<N, CPG, V, COMP>;
+  const int occ = fwd_occupancy<N, LZ, EIG, V, LOSS, COMP>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_fwd_kernel<N, LZ, EIG, CPG, V, LOSS><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
+  render_fwd_kernel<N, LZ, EIG, CPG, V, LOSS, COMP><<<ctas * num_sms, C::THREADS, C::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -624,6 +686,15 @@ static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_s
     if (p.sched == 2) return launch_fwd_mode<N, false, false, 2>(p, num_sms, ctas_per_sm, s);
   return p.sched == 1 ? launch_fwd_mode<N, false, false, 1>(p, num_sms, ctas_per_sm, s)
                       : launch_fwd_mode<N, false, false, 0>(p, num_sms, ctas_per_sm, s);
+}
+
+cudaError_t launch_render_fwd_composite(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  switch (n) {
+    case 32: return launch_fwd_mode<32, false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
+    case 64: return launch_fwd_mode<64, false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
+    case 128: return launch_fwd_mode<128, false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {

@@ -1,6 +1,9 @@
-"""GPU composite (bulge + disk) galaxies through mog_render_batch_ex
-(MOG_RENDER_ADD) against the FP64 oracle: max |d pixel| <= 2e-6 of the
-composite's total flux, |d sum| <= 1e-5 of it; and the add mode itself."""
+"""GPU composite (bulge + disk) galaxies against the FP64 oracle, max
+|d pixel| <= 2e-6 of the composite's total flux and |d sum| <= 1e-5 of it,
+in both forms: one pass (mog_render_composite: both profiles' mixtures on
+one grid, one transform) and two (mog_render_batch_ex, MOG_RENDER_ADD); the
+two forms against each other; the one-pass form's checks (profiles that
+disagree, counts, eigen-PSFs); and the add mode itself."""
 
 import numpy as np
 import pytest
@@ -18,12 +21,12 @@ def _device(gals):
     return to_device(gals)
 
 
-def gpu_composite(renderer, disk, bulge, shift="phase"):
+def gpu_composite(renderer, disk, bulge, shift="phase", fused=True):
     import torch
     from paper_2012_15797_gb300.renderer import patches
     bd, bb = _device(disk), _device(bulge)
     out = torch.full((bd.total,), float("nan"), dtype=torch.float32, device="cuda")
-    renderer.render_composite(bd, bb, out, shift=shift)
+    renderer.render_composite(bd, bb, out, shift=shift, fused=fused)
     renderer.sync_status()
     return [p.double().cpu().numpy() for p in patches(out, bd)]
 
@@ -39,18 +42,88 @@ def check(gpu, disk, bulge, psfs, tables, shift="phase"):
         assert abs(gpu[i].sum() - ora.sum()) <= FLUX_TOL * tot, i
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("size", [32, 64, 128, 256])
-def test_composite_each_size(gpu_renderer, tables, size):
+def test_composite_each_size(gpu_renderer, tables, size, fused):
     disk, bulge = composite_galaxies(12, seed=80 + size, sizes=(size,))
     disk.size[:] = size
     bulge.size[:] = size
-    check(gpu_composite(gpu_renderer, disk, bulge), disk, bulge, gpu_renderer.psfs, tables)
+    check(gpu_composite(gpu_renderer, disk, bulge, fused=fused), disk, bulge, gpu_renderer.psfs, tables)
 
 
-def test_composite_mixed_sizes(gpu_renderer, tables):
+@pytest.mark.parametrize("fused", [True, False])
+def test_composite_mixed_sizes(gpu_renderer, tables, fused):
     disk, bulge = composite_galaxies(150, seed=91)
     assert {32, 64, 128} <= set(np.unique(disk.size).tolist())
-    check(gpu_composite(gpu_renderer, disk, bulge), disk, bulge, gpu_renderer.psfs, tables)
+    check(gpu_composite(gpu_renderer, disk, bulge, fused=fused), disk, bulge, gpu_renderer.psfs, tables)
+
+
+@pytest.mark.parametrize("size", [32, 64, 128, 256])
+def test_one_pass_equals_two_passes(gpu_renderer, size):
+    """Many composites, Sersic profiles of every index on both parts (up to
+    24 components with real-space terms), several PSFs: the one-pass form
+    within float rounding of the two-pass form."""
+    disk, bulge = composite_galaxies(1500 if size < 256 else 200, seed=100 + size, sizes=(size,))
+    rng = np.random.default_rng(size)
+    for part in (disk, bulge):
+        part.size[:] = size
+        part.profile[:] = 2
+        part.sersic_n[:] = rng.uniform(0.5, 6.0, len(part)).astype(np.float32)
+    disk.psf[:] = bulge.psf[:] = np.arange(len(disk)) % 5
+    one = np.stack(gpu_composite(gpu_renderer, disk, bulge, fused=True))
+    two = np.stack(gpu_composite(gpu_renderer, disk, bulge, fused=False))
+    tot = (disk.flux + bulge.flux).astype(np.float64)
+    d = np.abs(one - two).reshape(len(disk), -1).max(axis=1)
+    assert np.all(d <= 0.25 * PIX_TOL * tot), float(np.max(d / tot))
+
+
+def test_one_pass_checks(gpu_renderer, tables):
+    import torch
+    from paper_2012_15797_gb300 import capi
+    from paper_2012_15797_gb300.renderer import patches
+    disk, bulge = composite_galaxies(40, seed=97)
+    bulge.x[3] += 0.25                   # centres differ
+    bulge.psf[5] = 1                     # PSFs differ
+    bulge.log_re[7] = np.nan             # one profile invalid
+    bd, bb = _device(disk), _device(bulge)
+    out = torch.full((bd.total,), -9.0, dtype=torch.float32, device="cuda")
+    gpu_renderer.render_composite(bd, bb, out)
+    with pytest.raises(capi.MogError) as ei:
+        gpu_renderer.sync_status()
+    assert ei.value.status == capi.MOG_ERR_DEVICE
+    got = [p.double().cpu().numpy() for p in patches(out, bd)]
+    for i in range(len(disk)):
+        if i in (3, 5, 7):
+            assert np.all(got[i] == -9.0)
+    keep = [i for i in range(len(disk)) if i not in (3, 5, 7)]
+    check([got[i] for i in keep], disk.subset(keep), bulge.subset(keep), gpu_renderer.psfs, tables)
+    short = capi.make_batch(len(disk) - 1, bb.ptrs(), 0)
+    with pytest.raises(capi.MogError):
+        capi.mog_render_composite(gpu_renderer.ctx, capi.make_batch(bd.count, bd.ptrs(), bd.size_mask()), short,
+                                  out.data_ptr(), 0)
+
+
+def test_one_pass_rejects_eigen_psf_galaxies(tables, psf0):
+    import torch
+    from paper_2012_15797_gb300 import capi
+    from paper_2012_15797_gb300.renderer import Renderer, patches
+    from workloads import eigen_psf
+    r = Renderer(tables, [psf0, eigen_psf()])
+    try:
+        disk, bulge = composite_galaxies(10, seed=98, sizes=(64,))
+        disk.size[:] = bulge.size[:] = 64
+        disk.psf[2] = bulge.psf[2] = 1
+        bd, bb = _device(disk), _device(bulge)
+        out = torch.full((bd.total,), -9.0, dtype=torch.float32, device="cuda")
+        r.render_composite(bd, bb, out)
+        with pytest.raises(capi.MogError):
+            r.sync_status()
+        got = [p.double().cpu().numpy() for p in patches(out, bd)]
+        assert np.all(got[2] == -9.0)
+        keep = [i for i in range(10) if i != 2]
+        check([got[i] for i in keep], disk.subset(keep), bulge.subset(keep), [psf0], tables)
+    finally:
+        r.close()
 
 
 def test_composite_lanczos(gpu_renderer, tables):
