@@ -846,6 +846,27 @@ def extra_per_galaxy(tables, psf, device, n=2000):
             "note": "one mog_render_batch call per 64x64 galaxy of the fixed-size distribution"}
 
 
+def parse_node_list(spec):
+    """A kernel node list such as "0-1,4" as a list of ids."""
+    nodes = []
+    for part in spec.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            nodes.extend(range(int(a), int(b) + 1))
+        elif part:
+            nodes.append(int(part))
+    return nodes
+
+
+def host_numa_nodes():
+    """The host's online NUMA nodes (a list of node ids), or None."""
+    try:
+        with open("/sys/devices/system/node/online") as f:
+            return parse_node_list(f.read())
+    except (OSError, ValueError):
+        return None
+
+
 def host_cpu_snapshot():
     """Process CPU time, context switches and (where the cgroup exposes
     them) CPU-quota throttling counters, to tell host-side stalls apart."""
@@ -1119,6 +1140,14 @@ def run_ours(args):
                "api": "mog_render_batch_host: pinned host parameters in, pinned host patches out, chunks of "
                       "64 MiB of patches pipelined over two streams; host clock around the synchronous call"}
         r.sync_status()
+        # what bounds it on this machine: one plain device-to-host copy of the
+        # same bytes into the same pinned buffer
+        copy_ms = _event_ms(lambda: out_host.copy_(out, non_blocking=True), 3, stream)
+        gbs = d2h / (copy_ms / 1e3) / 1e9
+        e2e["d2h_copy"] = {"gb_per_s": gbs, "ms": copy_ms,
+                           "patches_per_s_bound": args.galaxies / (copy_ms / 1e3),
+                           "fraction_of_bound": e2e["value"] / world / (args.galaxies / (copy_ms / 1e3)),
+                           "numa_nodes": host_numa_nodes()}
 
     if rank != 0:
         r.close()

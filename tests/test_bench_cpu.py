@@ -71,3 +71,9 @@ def test_host_cpu_delta():
     d = bench.host_cpu_delta(a, b, 4.0)
     assert d["cpu_cores_busy"] == pytest.approx(0.5)
     assert d["involuntary_switches"] == 2 and d["voluntary_switches"] == 20
+
+
+def test_parse_node_list():
+    assert bench.parse_node_list("0\n") == [0]
+    assert bench.parse_node_list("0-1,4") == [0, 1, 4]
+    assert bench.parse_node_list("") == []
