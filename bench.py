@@ -709,9 +709,26 @@ def extra_composite(tables, psf, device, steps):
     offs, _ = pack_offsets(disk.size)
     diff = max(((out[int(o):int(o) + int(n) ** 2] - two[int(o):int(o) + int(n) ** 2]).abs().max() / tot[g]).item()
                for g, (o, n) in enumerate(zip(offs, disk.size)) if g % 997 == 0)
+    # the same distribution on 256 x 256 patches
+    d256, b256 = composite_galaxies(5000, seed=8, sizes=(256,))
+    d256.size[:] = 256
+    b256.size[:] = 256
+    bd2 = to_device(d256, device=f"cuda:{device}")
+    bb2 = to_device(b256, device=f"cuda:{device}")
+    o1 = torch.empty(bd2.total, device=f"cuda:{device}")
+    o2 = torch.empty(bd2.total, device=f"cuda:{device}")
+    for _ in range(3):
+        r.render_composite(bd2, bb2, o1)
+        r.render_composite(bd2, bb2, o2, fused=False)
+    r.sync_status()
+    ms256 = _event_ms(lambda: r.render_composite(bd2, bb2, o1), steps, st)
+    ms256_two = _event_ms(lambda: r.render_composite(bd2, bb2, o2, fused=False), steps, st)
+    r.sync_status()
     r.close()
     sizes, counts = np.unique(disk.size, return_counts=True)
-    return {"workload": "100000 bulge + disk composites: exp disk r_e log-U(0.5, 15) px, deV bulge r_e 0.2-0.6 of "
+    return {"side_256": {"galaxies": 5000, "ms_one_pass": ms256, "ms_two_pass": ms256_two,
+                         "value": 5000 / (ms256 / 1e3), "unit": "composite patches/s"},
+            "workload": "100000 bulge + disk composites: exp disk r_e log-U(0.5, 15) px, deV bulge r_e 0.2-0.6 of "
                         "the disk's, bulge fraction U(0, 1), sides by 8 r_e(disk)",
             "bucket_mix": {int(n): int(c) for n, c in zip(sizes, counts)},
             "value": len(disk) / (ms / 1e3), "unit": "composite patches/s", "ms_per_step": ms,

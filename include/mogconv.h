@@ -211,14 +211,11 @@ mog_status mog_render_batch_ex(mog_ctx* ctx, const mog_batch* batch, float* out,
  * must have the same x, y, size, psf and offset (each its own flux, log_re,
  * e1, e2, sersic_n, profile).  The method is linear in the model, so the
  * result is the sum of the two profiles' renders (mog_render_batch of
- * `first`, then MOG_RENDER_ADD of `second`) up to float rounding; for
- * N = 32, 64 and 128 it is computed with one transform per galaxy: both
- * profiles' Fourier mixtures, each on its own quadratic form, are summed on
- * the frequency grid before the inverse FFT, and both sets of real-space
- * terms are added at the store.  N = 256 galaxies are rendered in two passes
- * (the first profile, then the second added; workspace scratch of N/2 x N
- * complex values per SM, allocated on first use).  Phase shift, constant
- * PSFs.  Planned by first->size_mask (second->size_mask is not read); the
+ * `first`, then MOG_RENDER_ADD of `second`) up to float rounding, computed
+ * with one transform per galaxy: both profiles' Fourier mixtures, each on
+ * its own quadratic form, are summed on the frequency grid before the
+ * inverse FFT, and both sets of real-space terms are added at the store.
+ * Every patch side; phase shift, constant PSFs.  Planned by first->size_mask (second->size_mask is not read); the
  * workspace holds two records per galaxy.  A galaxy whose two profiles
  * disagree on centre, size, PSF or offset, or either of which is invalid or
  * on an eigen-PSF, is skipped (status MOG_ERR_DEVICE).  Asynchronous on

@@ -571,18 +571,14 @@ mog_status mog_render_composite(mog_ctx* ctx, const mog_batch* first, const mog_
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   Workspace* ws = &ctx->ws;
   const int64_t g = first->count;
-  const uint32_t want = first->size_mask ? (first->size_mask & FWD_BUCKETS) : FWD_BUCKETS;
   MOG_CUDA(ctx, cudaSetDevice(ctx->device));
   // two records per galaxy: the second profile's after the first's
   if ((st = ensure_capacity(ctx, ws, 2 * g)) != MOG_OK) return st;
-  if ((want & 0x8) && !ws->bwd256)
-    MOG_CUDA(ctx, cudaMalloc(&ws->bwd256, render_bwd256_scratch_bytes(ctx->num_sms)));
   RenderParams p;
   if ((st = plan_batch(ctx, ws, first, out, FWD_BUCKETS, s, &p)) != MOG_OK) return st;
   unsigned char* rec2 = ws->records + (size_t)g * RECORD_BYTES;
   p.records = ws->records;
   p.records2 = rec2;
-  p.scratch256 = ws->bwd256;
   p.eigen = 0;   // eigen-PSF galaxies are rejected by the record prologue
   MOG_CUDA(ctx, launch_composite_prep(p, view_of(second), g, ws->records, rec2, s));
   return launch_buckets(ctx, ws, first, FWD_BUCKETS, s, [&](int n, cudaStream_t bs) -> cudaError_t {
@@ -590,16 +586,8 @@ mog_status mog_render_composite(mog_ctx* ctx, const mog_batch* first, const mog_
     const LaunchShape& ls = ctx->tune_fwd[bucket_of(n)];
     q.chunk = ls.chunk;
     q.sched = 0;
-    if (n != 256) return launch_render_fwd_composite(n, q, ctx->num_sms, ls.ctas_per_sm, bs);
-    // 256 x 256: the first profile rendered, then the second added, each by
-    // the one-profile kernel (its work counter re-zeroed in between)
-    q.records2 = nullptr;
-    cudaError_t e = launch_render_fwd256(q, ctx->num_sms, ls.ctas_per_sm, bs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(q.queue + bucket_of(256), 0, sizeof(int32_t), bs);
-    q.records = rec2;
-    q.accumulate = 1;
-    if (e == cudaSuccess) e = launch_render_fwd256(q, ctx->num_sms, ls.ctas_per_sm, bs);
-    return e;
+    if (n == 256) return launch_render_fwd256_composite(q, ctx->num_sms, ls.ctas_per_sm, bs);
+    return launch_render_fwd_composite(n, q, ctx->num_sms, ls.ctas_per_sm, bs);
   });
 }
 

@@ -99,9 +99,10 @@ cudaError_t render_noalloc(const RenderParams& proto, int64_t count, uint32_t wa
 int kernel_occupancy(const void* fn, int threads, size_t smem);
 
 cudaError_t launch_render_fwd(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
-// Composites (mog_render_composite), N = 32, 64, 128: one transform per
-// galaxy for the two profiles of p.records and p.records2.
+// Composites (mog_render_composite): one transform per galaxy for the two
+// profiles of p.records and p.records2 (N = 32, 64, 128; and 256).
 cudaError_t launch_render_fwd_composite(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
+cudaError_t launch_render_fwd256_composite(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s);
 // Records of composites: the first profile's (batch p.b) at records, the
 // second's (batch `second`, same centre, size, PSF and patch) at records2.
 cudaError_t launch_composite_prep(const RenderParams& p, const BatchView& second, int64_t count,

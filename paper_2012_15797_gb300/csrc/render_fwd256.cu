@@ -63,8 +63,10 @@ constexpr size_t off_px = off_tw + sizeof(float2) * TWS;
 constexpr size_t off_py = off_px + sizeof(float2) * H;
 constexpr size_t off_nyq = off_py + sizeof(float2) * N;
 constexpr size_t off_rec = (off_nyq + sizeof(float2) * N + 15) & ~size_t(15);
-constexpr size_t off_rt = off_rec + 2 * sizeof(GalaxyRecord);
-constexpr size_t off_bar = (off_rt + 2 * sizeof(RealTerms) + 15) & ~size_t(15);   // two tables, one per record buffer
+// two record buffers of up to two records (composites), two real-space
+// tables (one per record buffer) with room for a composite's terms
+constexpr size_t off_rt = off_rec + 4 * sizeof(GalaxyRecord);
+constexpr size_t off_bar = (off_rt + 2 * sizeof(RealTermsN<2 * RMAX>) + 15) & ~size_t(15);
 constexpr size_t SMEM = off_bar + 2 * sizeof(uint64_t);
 static_assert(CTAS_PER_SM * (SMEM + 1024) <= 228 * 1024, "two CTAs share an SM's shared memory");
 constexpr int STRIP = 64;                                                 // output rows per strip
@@ -137,9 +139,14 @@ __device__ __forceinline__ void lanczos_real_256(const RealTerms& rt, int nr, co
 // V: the radix schedule of the transforms (Radix<256, V>).  LOSS: the loss
 // mode of mog_render_chi2 (render_fwd.cu): the patch receives the gradient of
 // chi^2 (and serves as the transform intermediate as it does for the model).
-template <bool LZ, bool EIG, int V = 0, bool LOSS = false>
+// COMP: composite galaxies (mog_render_composite): a second record per
+// galaxy (p.records2), both profiles' Fourier mixtures summed on the grid
+// before the one transform, both sets of real-space terms added.
+template <bool LZ, bool EIG, int V = 0, bool LOSS = false, bool COMP = false>
 __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(RenderParams p) {
   static_assert(!(LZ && LOSS), "the loss mode renders with the phase shift");
+  static_assert(!(COMP && (LZ || EIG || LOSS)), "composites: phase shift, constant PSFs, plain render");
+  using RT = RealTermsN<COMP ? 2 * RMAX : RMAX>;
   constexpr int R1 = Radix<N, V>::r[1], R2 = Radix<N, V>::r[2];
   constexpr int TW1 = twiddle_elems<N, R1>();
   static_assert(Radix<N, V>::P == 3, "three passes");
@@ -155,7 +162,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
   float2* py = reinterpret_cast<float2*>(smem + off_py);
   float2* nyq = reinterpret_cast<float2*>(smem + off_nyq);
   GalaxyRecord* rec = reinterpret_cast<GalaxyRecord*>(smem + off_rec);
-  RealTerms* rts = reinterpret_cast<RealTerms*>(smem + off_rt);
+  [[maybe_unused]] GalaxyRecord* rec2 = rec + 2;   // COMP: the second record of each buffer
+  RT* rts = reinterpret_cast<RT*>(smem + off_rt);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + off_bar);   // records
   __shared__ int s_pos[2];
   __shared__ float s_psf_mog[KPSF][6];
@@ -170,6 +178,17 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
   const int count = p.bucket_count[B];
   const int first = p.bucket_start[B];   // planned position of this bucket's first galaxy
   const unsigned char* records = p.records + (size_t)first * RECORD_BYTES;
+  [[maybe_unused]] const unsigned char* records2 = COMP ? p.records2 + (size_t)first * RECORD_BYTES : nullptr;
+  // the record(s) of planned position pos into buffer b
+  auto load_records = [&](int b, int pos) {
+    if constexpr (COMP) {
+      mbar_expect_tx(&bar[b], 2 * sizeof(GalaxyRecord));
+      bulk_copy(&rec[b], records + (size_t)pos * RECORD_BYTES, sizeof(GalaxyRecord), &bar[b]);
+      bulk_copy(&rec2[b], records2 + (size_t)pos * RECORD_BYTES, sizeof(GalaxyRecord), &bar[b]);
+    } else {
+      bulk_load(&rec[b], records + (size_t)pos * RECORD_BYTES, sizeof(GalaxyRecord), &bar[b]);
+    }
+  };
   int q_next = 0, q_end = 0, q_ahead = 0;
   auto next_position = [&]() -> int {
     if (q_next >= q_end) {
@@ -187,7 +206,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
     q_ahead = atomicAdd(&p.queue[B], p.chunk);
     const int p0 = next_position();
     s_pos[0] = p0;
-    if (p0 >= 0) bulk_load(&rec[0], records + (size_t)p0 * RECORD_BYTES, sizeof(GalaxyRecord), &bar[0]);
+    if (p0 >= 0) load_records(0, p0);
   }
   int cur_psf = -1, k_eig = 0;
   const float2* psf_hat = nullptr;
@@ -220,8 +239,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
     if (tid == 0) {
       const int np = next_position();
       s_pos[buf ^ 1] = np;
-      if (np >= 0)
-        bulk_load(&rec[buf ^ 1], records + (size_t)np * RECORD_BYTES, sizeof(GalaxyRecord), &bar[buf ^ 1]);
+      if (np >= 0) load_records(buf ^ 1, np);
     }
     const bool landed = mbar_wait(&bar[buf], (rec_parity >> buf) & 1u);
     rec_parity ^= 1u << buf;
@@ -266,7 +284,9 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
       const float gx = r.x, gy = r.y;
       const float* lzw = LZ ? p.lzw + ((size_t)first + pos) * 16 : nullptr;
       const int kp = s_kpsf;
-      const int nrt = r.nrc * kp, ntask = H + 2 * N + real_terms_padded(nrt);
+      // COMP: the second profile's terms follow the first's (nrt1 of them)
+      const int nrt1 = r.nrc * kp, nrt = nrt1 + (COMP ? rec2[buf].nrc * kp : 0);
+      const int ntask = H + 2 * N + real_terms_padded(nrt);
       for (int i = tid; i < ntask; i += THREADS) {
         float sn, cs;
         if (i < H) {
@@ -301,6 +321,11 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
           const float q = fmaf(om, fmaf(r.s22, om, r.s12), 0.25f * r.s11);
           float acc = 0.0f;
           for (int c = 0; c < r.nf; ++c) acc = fmaf(r.famp[c], ex2(r.fcoef[c] * q), acc);
+          if constexpr (COMP) {
+            const GalaxyRecord& r2 = rec2[buf];
+            const float q2 = fmaf(om, fmaf(r2.s22, om, r2.s12), 0.25f * r2.s11);
+            for (int c = 0; c < r2.nf; ++c) acc = fmaf(r2.famp[c], ex2(r2.fcoef[c] * q2), acc);
+          }
           float sy, cy;
           sincospif(-2.0f * gy * om, &sy, &cy);
           sincospif(-gx, &sn, &cs);
@@ -317,7 +342,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
           nyq[l] = cscale(cmul(pn, cmul(phx, phy)), acc);
         } else {
           const int t = i - H - 2 * N;
-          if (t < nrt) real_term(r, s_psf_mog, nullptr, kp, N, t, &rts[buf]);
+          if (t < nrt1) real_term(r, s_psf_mog, nullptr, kp, N, t, &rts[buf]);
+          else if (COMP && t < nrt) real_term(rec2[buf], s_psf_mog, nullptr, kp, N, t - nrt1, &rts[buf], t);
           else real_term_zero(t, &rts[buf]);
         }
       }
@@ -327,7 +353,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
     const int nf = r.nf;
     const float s11 = r.s11, s12x2 = 2.0f * r.s12, s22 = r.s22;
     // the rows' term count, read while the next galaxy cannot yet change s_kpsf
-    const int nr = real_terms_padded(r.nrc * s_kpsf);
+    const int nr = real_terms_padded((r.nrc + (COMP ? rec2[buf].nrc : 0)) * s_kpsf);
     float2 v[8];
     // ---- Steps 5-7a: columns k = 32 round + warp ----
     for (int round = 0; round < ROUNDS; ++round) {
@@ -350,6 +376,25 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
           if (!__any_sync(0xffffffffu, c * qmin > NEGLIGIBLE_LOG2)) continue;
 #pragma unroll
           for (int m = 0; m < 8; ++m) s[m] = fmaf(a, ex2(c * q[m]), s[m]);
+        }
+        if constexpr (COMP) {
+          // the second profile's components, on its own quadratic form
+          const GalaxyRecord& r2 = rec2[buf];
+          const float b0 = r2.s11 * nu * nu, b1 = 2.0f * r2.s12 * nu, t22 = r2.s22;
+          float qmin2 = 3.4e38f;
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const int l = j + m * TPF;
+            const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
+            q[m] = fmaf(om, fmaf(t22, om, b1), b0);
+            qmin2 = fminf(qmin2, q[m]);
+          }
+          for (int i = 0; i < r2.nf; ++i) {
+            const float a = r2.famp[i], c = r2.fcoef[i];
+            if (!__any_sync(0xffffffffu, c * qmin2 > NEGLIGIBLE_LOG2)) continue;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) s[m] = fmaf(a, ex2(c * q[m]), s[m]);
+          }
         }
         const float2 pxk = px[k];
 #pragma unroll
@@ -414,7 +459,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
     }
 
     // ---- Step 7b + 8: row pairs p = 32 round + warp, each warp on its own ----
-    const RealTerms& rt = rts[buf];
+    const RT& rt = rts[buf];
     for (int round = 0; round < ROUNDS; ++round) {
       const int pr = WARPS * round + f;
 #pragma unroll
@@ -479,21 +524,25 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(Ren
 
 }  // namespace
 
-template <bool LZ, bool EIG, int V = 0, bool LOSS = false>
+template <bool LZ, bool EIG, int V = 0, bool LOSS = false, bool COMP = false>
 static int fwd256_occupancy() {
-  const int occ =
-      kernel_occupancy(reinterpret_cast<const void*>(render_fwd256_kernel<LZ, EIG, V, LOSS>), THREADS, SMEM);
+  const int occ = kernel_occupancy(reinterpret_cast<const void*>(render_fwd256_kernel<LZ, EIG, V, LOSS, COMP>),
+                                   THREADS, SMEM);
   return occ < 0 ? occ : (occ < CTAS_PER_SM ? occ : CTAS_PER_SM);
 }
 
-template <bool LZ, bool EIG, int V = 0, bool LOSS = false>
+template <bool LZ, bool EIG, int V = 0, bool LOSS = false, bool COMP = false>
 static cudaError_t launch_fwd256(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
-  const int occ = fwd256_occupancy<LZ, EIG, V, LOSS>();
+  const int occ = fwd256_occupancy<LZ, EIG, V, LOSS, COMP>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   // the accumulate mode's scratch holds one slice per CTA, CTAS_PER_SM per SM
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-  render_fwd256_kernel<LZ, EIG, V, LOSS><<<num_sms * ctas, THREADS, SMEM, s>>>(p);
+  render_fwd256_kernel<LZ, EIG, V, LOSS, COMP><<<num_sms * ctas, THREADS, SMEM, s>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_render_fwd256_composite(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  return launch_fwd256<false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
 }
 
 int render_fwd256_max_ctas(int sched) {
