@@ -181,6 +181,14 @@ class Renderer:
         out = self.render(disk, out, stream, shift)
         return self.render(bulge, out, stream, shift, add=True)
 
+    def render_composite_backward(self, disk, bulge, grad_out, stream=None, sersic=False, shift="phase"):
+        """Gradients of a composite's loss with respect to each profile's
+        parameters, ((count, k), (count, k)): the adjoint of a sum is each
+        part's adjoint with the same upstream gradient.  The shared centre's
+        gradient is the sum of the two x (and y) columns."""
+        return (self.render_backward(disk, grad_out, stream=stream, sersic=sersic, shift=shift),
+                self.render_backward(bulge, grad_out, stream=stream, sersic=sersic, shift=shift))
+
     def render_backward(self, batch, grad_out, grad_params=None, stream=None, sersic=False, shift="phase"):
         """Gradients (count, 6) of L w.r.t. (flux, x, y, log_re, e1, e2)
         given grad_out = dL/d(packed output); with ``sersic`` (count, 7), the

@@ -158,10 +158,9 @@ def test_composite_gradients_are_the_parts(gpu_renderer, tables):
     rng = np.random.default_rng(96)
     grad = [rng.normal(size=(64, 64)) for _ in range(len(disk))]
     go = torch.from_numpy(np.concatenate([g.ravel() for g in grad]).astype(np.float32)).cuda()
-    for part in (disk, bulge):
-        gp = torch.full((len(part), 6), float("nan"), device="cuda")
-        gpu_renderer.render_backward(_device(part), go, gp)
-        gpu_renderer.sync_status()
+    grads = gpu_renderer.render_composite_backward(_device(disk), _device(bulge), go)
+    gpu_renderer.sync_status()
+    for part, gp in zip((disk, bulge), grads):
         got = gp.double().cpu().numpy()
         for i in range(len(part)):
             g = part.row(i)
