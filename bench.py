@@ -704,7 +704,13 @@ def extra_composite(tables, psf, device, steps):
     r.sync_status()
     ms = _event_ms(lambda: r.render_composite(bd, bb, out), steps, st)
     ms2 = _event_ms(lambda: r.render_composite(bd, bb, two, fused=False), steps, st)
+    for _ in range(2):
+        r.render_composite(bd, bb, two, shift="lanczos")
+        r.render_composite(bd, bb, two, shift="lanczos", fused=False)
+    ms_lz = _event_ms(lambda: r.render_composite(bd, bb, two, shift="lanczos"), steps, st)
+    ms_lz2 = _event_ms(lambda: r.render_composite(bd, bb, two, shift="lanczos", fused=False), steps, st)
     r.sync_status()
+    r.render_composite(bd, bb, two, fused=False)   # the phase-shift two-pass result again, compared below
     tot = torch.from_numpy((disk.flux + bulge.flux).astype(np.float32)).to(out.device)
     offs, _ = pack_offsets(disk.size)
     diff = max(((out[int(o):int(o) + int(n) ** 2] - two[int(o):int(o) + int(n) ** 2]).abs().max() / tot[g]).item()
@@ -734,6 +740,7 @@ def extra_composite(tables, psf, device, steps):
             "value": len(disk) / (ms / 1e3), "unit": "composite patches/s", "ms_per_step": ms,
             "two_pass": {"value": len(disk) / (ms2 / 1e3), "ms_per_step": ms2,
                          "note": "disks rendered, bulges added (MOG_RENDER_ADD)"},
+            "lanczos_shift": {"ms_one_pass": ms_lz, "ms_two_pass": ms_lz2, "value": len(disk) / (ms_lz / 1e3)},
             "max_abs_diff_over_flux_sampled": diff}
 
 

@@ -215,15 +215,18 @@ mog_status mog_render_batch_ex(mog_ctx* ctx, const mog_batch* batch, float* out,
  * with one transform per galaxy: both profiles' Fourier mixtures, each on
  * its own quadratic form, are summed on the frequency grid before the
  * inverse FFT, and both sets of real-space terms are added at the store.
- * Every patch side; phase shift, constant PSFs.  Planned by first->size_mask (second->size_mask is not read); the
+ * Every patch side, constant PSFs.  flags: 0 (phase shift) or
+ * MOG_RENDER_LANCZOS (the sub-pixel shift of mog_render_batch_lanczos
+ * applied to the sum: the Fourier part through the phase tables, both
+ * profiles' real-space terms by the periodic Lanczos convolution).  Planned by first->size_mask (second->size_mask is not read); the
  * workspace holds two records per galaxy.  A galaxy whose two profiles
  * disagree on centre, size, PSF or offset, or either of which is invalid or
  * on an eigen-PSF, is skipped (status MOG_ERR_DEVICE).  Asynchronous on
- * `stream`.  Errors: MOG_ERR_ARG as mog_render_batch, or batches of
- * different counts.
+ * `stream`.  Errors: MOG_ERR_ARG as mog_render_batch, batches of different
+ * counts, or unknown flags.
  */
 mog_status mog_render_composite(mog_ctx* ctx, const mog_batch* first, const mog_batch* second, float* out,
-                                void* stream);
+                                void* stream, unsigned flags);
 
 /*
  * Same result as mog_render_batch, but the call allocates no memory: no

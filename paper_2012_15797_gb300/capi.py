@@ -123,7 +123,7 @@ def _load():
         "mog_server_trace": ([VP, P(ctypes.c_double), ctypes.c_int64, P(ctypes.c_int64)], I),
         "mog_render_chi2": ([VP, P(mog_batch), VP, VP, VP, VP, VP, VP], I),
         "mog_render_batch_cufft": ([VP, P(mog_batch), VP, VP], I),
-        "mog_render_composite": ([VP, P(mog_batch), P(mog_batch), VP, VP], I),
+        "mog_render_composite": ([VP, P(mog_batch), P(mog_batch), VP, VP, ctypes.c_uint], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -231,11 +231,13 @@ def mog_render_batch_ex(ctx, batch, out_ptr, stream=0, flags=0):
                                          ctypes.c_void_p(int(stream)), ctypes.c_uint(int(flags))))
 
 
-def mog_render_composite(ctx, first, second, out_ptr, stream=0):
+def mog_render_composite(ctx, first, second, out_ptr, stream=0, flags=0):
     """Composite galaxies in one pass (see include/mogconv.h): galaxy g of
-    ``first`` and of ``second`` are the two profiles of one galaxy."""
+    ``first`` and of ``second`` are the two profiles of one galaxy; flags 0
+    or MOG_RENDER_LANCZOS."""
     _check(ctx, _lib.mog_render_composite(ctx, ctypes.byref(first), ctypes.byref(second),
-                                          ctypes.c_void_p(int(out_ptr)), ctypes.c_void_p(int(stream))))
+                                          ctypes.c_void_p(int(out_ptr)), ctypes.c_void_p(int(stream)),
+                                          ctypes.c_uint(int(flags))))
 
 
 def mog_render_batch_cufft(ctx, batch, out_ptr, stream=0):

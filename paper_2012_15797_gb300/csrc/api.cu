@@ -560,8 +560,10 @@ mog_status mog_render_chi2(mog_ctx* ctx, const mog_batch* batch, const float* da
 }
 
 mog_status mog_render_composite(mog_ctx* ctx, const mog_batch* first, const mog_batch* second, float* out,
-                                void* stream) {
+                                void* stream, unsigned flags) {
   if (!ctx) return MOG_ERR_ARG;
+  if (flags & ~(unsigned)MOG_RENDER_LANCZOS)
+    return fail(ctx, MOG_ERR_ARG, "mog_render_composite takes 0 or MOG_RENDER_LANCZOS");
   mog_status st = check_batch(ctx, first);
   if (st != MOG_OK) return st;
   if ((st = check_batch(ctx, second)) != MOG_OK) return st;
@@ -580,6 +582,8 @@ mog_status mog_render_composite(mog_ctx* ctx, const mog_batch* first, const mog_
   p.records = ws->records;
   p.records2 = rec2;
   p.eigen = 0;   // eigen-PSF galaxies are rejected by the record prologue
+  p.lanczos = (flags & MOG_RENDER_LANCZOS) ? 1 : 0;
+  p.lzw = ws->lzw;
   MOG_CUDA(ctx, launch_composite_prep(p, view_of(second), g, ws->records, rec2, s));
   return launch_buckets(ctx, ws, first, FWD_BUCKETS, s, [&](int n, cudaStream_t bs) -> cudaError_t {
     RenderParams q = p;

@@ -93,6 +93,21 @@ __global__ void plan_scatter(BatchView b, int64_t count, int supported, int32_t*
   }
 }
 
+// Lanczos weights of galaxy g at planned position pos, once per galaxy
+// (one warp): lanes 0-6 along x, 8-14 along y.
+__device__ __forceinline__ void lanczos_weights_warp(const RenderParams& p, int64_t g, int pos) {
+  const int lane = threadIdx.x & 31;
+  const float c = (lane & 8) ? p.b.y[g] : p.b.x[g];
+  const float d = c - floorf(c + 0.5f);
+  const int t = (lane & 7) - 3;
+  float w = 0.0f;
+  if (lane < 16 && (lane & 7) < 7) w = lanczos_tap((float)t - d);
+  float sum = w;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane < 16) p.lzw[(size_t)pos * 16 + lane] = (lane & 7) < 7 ? w / sum : 0.0f;
+}
+
 // One warp per planned position (lane = mixture component).
 __global__ void galaxy_prep(RenderParams p, unsigned char* records) {
   const int total = p.bucket_start[NBUCKET - 1] + p.bucket_count[NBUCKET - 1];
@@ -102,19 +117,7 @@ __global__ void galaxy_prep(RenderParams p, unsigned char* records) {
     galaxy_record_warp(p.b, g, p.b.size[g], p.profiles, p.psfs, p.status, p.lanczos != 0, p.pcoef != nullptr,
                        reinterpret_cast<GalaxyRecord*>(records + (size_t)pos * RECORD_BYTES));
     if (p.pcoef) eigen_coefficients_warp(p.b, g, p.psfs, p.pcoef, pos);
-    if (p.lanczos) {
-      // Lanczos weights once per galaxy: lanes 0-6 along x, 8-14 along y
-      const int lane = threadIdx.x & 31;
-      const float c = (lane & 8) ? p.b.y[g] : p.b.x[g];
-      const float d = c - floorf(c + 0.5f);
-      const int t = (lane & 7) - 3;
-      float w = 0.0f;
-      if (lane < 16 && (lane & 7) < 7) w = lanczos_tap((float)t - d);
-      float sum = w;
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-      if (lane < 16) p.lzw[(size_t)pos * 16 + lane] = (lane & 7) < 7 ? w / sum : 0.0f;
-    }
+    if (p.lanczos) lanczos_weights_warp(p, g, pos);
   }
 }
 
@@ -124,7 +127,8 @@ cudaError_t launch_galaxy_prep(const RenderParams& p, int64_t count, unsigned ch
   return cudaGetLastError();
 }
 
-// Composites: one warp per planned position writes both profiles' records.
+// Composites: one warp per planned position writes both profiles' records
+// (and, for the Lanczos variant, the shift's weights, from the shared centre).
 // The second batch must give the galaxy the same centre, patch side, PSF and
 // patch offset (compared exactly); otherwise, or when either profile is
 // invalid, both records are marked skipped and the status word is set.
@@ -137,8 +141,10 @@ __global__ void composite_prep(RenderParams p, BatchView second, unsigned char* 
     const int n = p.b.size[g];
     GalaxyRecord* r1 = reinterpret_cast<GalaxyRecord*>(records + (size_t)pos * RECORD_BYTES);
     GalaxyRecord* r2 = reinterpret_cast<GalaxyRecord*>(records2 + (size_t)pos * RECORD_BYTES);
-    galaxy_record_warp(p.b, g, n, p.profiles, p.psfs, p.status, false, false, r1);
-    galaxy_record_warp(second, g, n, p.profiles, p.psfs, p.status, false, false, r2);
+    const bool lz = p.lanczos != 0;
+    galaxy_record_warp(p.b, g, n, p.profiles, p.psfs, p.status, lz, false, r1);
+    galaxy_record_warp(second, g, n, p.profiles, p.psfs, p.status, lz, false, r2);
+    if (lz) lanczos_weights_warp(p, g, pos);
     __syncwarp();
     if (lane == 0) {
       const bool same = second.x[g] == p.b.x[g] && second.y[g] == p.b.y[g] && second.size[g] == n &&

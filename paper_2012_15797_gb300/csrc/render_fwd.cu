@@ -94,8 +94,8 @@ __device__ __forceinline__ int out_pos(int x) { return x ^ (((x >> 5) & 1) << 2)
 // (already shifted) Fourier part in the group's own rows, R the real-space
 // terms at the integer offset, Lz the periodic Lanczos convolution, done
 // along x in the group's rows, then (after a CTA barrier) along y.
-template <int N>
-__device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, const RealTerms& rt, int nr,
+template <int N, int RC>
+__device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, const RealTermsN<RC>& rt, int nr,
                                                        const float* wl, int f, int j, float* dst, bool add) {
   using C = FwdCfg<N>;
   const int x0 = 8 * j;
@@ -184,7 +184,7 @@ __device__ __forceinline__ void lanczos_real_and_store(float2* WB, float* orow, 
 // record (the bulge, p.records2) with the same centre, PSF and patch; both
 // profiles' Fourier mixtures, each with its own quadratic form, are summed
 // on the grid before the one transform, and both sets of real-space terms
-// are added at the store.
+// are added at the store (with LZ, shifted with the Fourier part).
 template <int N, bool LZ, bool EIG, int CPG = 1, int V = 0, bool LOSS = false, bool COMP = false>
 __global__ void __launch_bounds__(FwdCfg<N, CPG, V, COMP>::THREADS, FwdCfg<N, CPG, V, COMP>::MIN_BLOCKS)
     render_fwd_kernel(RenderParams p) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(FwdCfg<N, CPG, V, COMP>::THREADS, FwdCfg<N, CP
   using RT = typename C::RT;
   static_assert(!(LZ && CPG > 1), "the Lanczos variant keeps one column per group");
   static_assert(!(LZ && LOSS), "the loss mode renders with the phase shift");
-  static_assert(!(COMP && (LZ || EIG || LOSS)), "composites: phase shift, constant PSFs, plain render");
+  static_assert(!(COMP && (EIG || LOSS)), "composites: constant PSFs, plain render");
   constexpr int WARPS = C::THREADS / 32;
   constexpr int TPF = C::TPF, LS = C::LS;
   constexpr int B = bucket_of(N);
@@ -650,6 +650,7 @@ constexpr int fwd_cpg() { return (N == 128 && !LZ) ? 2 : 1; }
 static_assert(2 * (FwdCfg<128, 2>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 CTAs share an SM's shared memory");
 
 static_assert(2 * (FwdCfg<128, 2, 0, true>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 composite CTAs share an SM");
+static_assert(FwdCfg<128, 1, 0, true>::SMEM <= 227 * 1024, "the Lanczos composite CTA fits an SM's shared memory");
 
 template <int N, bool LZ = false, bool EIG = false, int V = 0, bool LOSS = false, bool COMP = false>
 static int fwd_occupancy() {
@@ -688,11 +689,17 @@ static cudaError_t launch_fwd(const RenderParams& p, int num_sms, int ctas_per_s
                       : launch_fwd_mode<N, false, false, 0>(p, num_sms, ctas_per_sm, s);
 }
 
+template <int N>
+static cudaError_t launch_fwd_composite(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
+  return p.lanczos ? launch_fwd_mode<N, true, false, 0, false, true>(p, num_sms, ctas_per_sm, s)
+                   : launch_fwd_mode<N, false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
+}
+
 cudaError_t launch_render_fwd_composite(int n, const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
   switch (n) {
-    case 32: return launch_fwd_mode<32, false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
-    case 64: return launch_fwd_mode<64, false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
-    case 128: return launch_fwd_mode<128, false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
+    case 32: return launch_fwd_composite<32>(p, num_sms, ctas_per_sm, s);
+    case 64: return launch_fwd_composite<64>(p, num_sms, ctas_per_sm, s);
+    case 128: return launch_fwd_composite<128>(p, num_sms, ctas_per_sm, s);
     default: return cudaErrorInvalidValue;
   }
 }

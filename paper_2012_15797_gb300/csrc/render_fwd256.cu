@@ -76,7 +76,8 @@ static_assert(sizeof(float) * (STRIP + 6) * N <= off_tw, "Lanczos strip must fit
 // the integer offset, Lz the periodic Lanczos convolution with weights wl
 // (x: [0, 7), y: [8, 15)).  Called by all threads after the patch holds the
 // Fourier part; `strip` is shared memory of (STRIP + 6) rows.
-__device__ __forceinline__ void lanczos_real_256(const RealTerms& rt, int nr, const float* wl, float* strip,
+template <int RC>
+__device__ __forceinline__ void lanczos_real_256(const RealTermsN<RC>& rt, int nr, const float* wl, float* strip,
                                                  float* dst, int f, int j) {
   const int x0 = 8 * j;
   float wx[7], wy[7];
@@ -141,11 +142,12 @@ __device__ __forceinline__ void lanczos_real_256(const RealTerms& rt, int nr, co
 // chi^2 (and serves as the transform intermediate as it does for the model).
 // COMP: composite galaxies (mog_render_composite): a second record per
 // galaxy (p.records2), both profiles' Fourier mixtures summed on the grid
-// before the one transform, both sets of real-space terms added.
+// before the one transform, both sets of real-space terms added (with LZ,
+// shifted with the Fourier part).
 template <bool LZ, bool EIG, int V = 0, bool LOSS = false, bool COMP = false>
 __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) render_fwd256_kernel(RenderParams p) {
   static_assert(!(LZ && LOSS), "the loss mode renders with the phase shift");
-  static_assert(!(COMP && (LZ || EIG || LOSS)), "composites: phase shift, constant PSFs, plain render");
+  static_assert(!(COMP && (EIG || LOSS)), "composites: constant PSFs, plain render");
   using RT = RealTermsN<COMP ? 2 * RMAX : RMAX>;
   constexpr int R1 = Radix<N, V>::r[1], R2 = Radix<N, V>::r[2];
   constexpr int TW1 = twiddle_elems<N, R1>();
@@ -542,7 +544,8 @@ static cudaError_t launch_fwd256(const RenderParams& p, int num_sms, int ctas_pe
 }
 
 cudaError_t launch_render_fwd256_composite(const RenderParams& p, int num_sms, int ctas_per_sm, cudaStream_t s) {
-  return launch_fwd256<false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
+  return p.lanczos ? launch_fwd256<true, false, 0, false, true>(p, num_sms, ctas_per_sm, s)
+                   : launch_fwd256<false, false, 0, false, true>(p, num_sms, ctas_per_sm, s);
 }
 
 int render_fwd256_max_ctas(int sched) {

@@ -168,15 +168,18 @@ class Renderer:
         """Composite (bulge + disk) galaxies: the sum of two profiles sharing
         the patch layout, PSF and centre.  ``disk`` and ``bulge`` are
         DeviceBatches with the same sizes, offsets, PSFs and (x, y).  With
-        the phase shift and ``fused`` one call renders both profiles
-        (mog_render_composite: one transform per galaxy); otherwise the disks
-        are rendered and the bulges added (mog_render_batch_ex, add mode)."""
-        if shift == "phase" and fused:
+        ``fused`` one call renders both profiles (mog_render_composite: one
+        transform per galaxy); otherwise the disks are rendered and the
+        bulges added (mog_render_batch_ex, add mode)."""
+        if shift not in ("phase", "lanczos"):
+            raise ValueError(f"unknown shift {shift!r}")
+        if fused:
             if out is None:
                 out = torch.empty(disk.total, dtype=torch.float32, device=self.device)
             s = stream if stream is not None else torch.cuda.current_stream(self.device)
             capi.mog_render_composite(self.ctx, capi.make_batch(disk.count, disk.ptrs(), disk.size_mask()),
-                                      capi.make_batch(bulge.count, bulge.ptrs(), 0), out.data_ptr(), s.cuda_stream)
+                                      capi.make_batch(bulge.count, bulge.ptrs(), 0), out.data_ptr(), s.cuda_stream,
+                                      capi.MOG_RENDER_LANCZOS if shift == "lanczos" else 0)
             return out
         out = self.render(disk, out, stream, shift)
         return self.render(bulge, out, stream, shift, add=True)

@@ -70,11 +70,12 @@ def test_one_pass_equals_two_passes(gpu_renderer, size):
         part.profile[:] = 2
         part.sersic_n[:] = rng.uniform(0.5, 6.0, len(part)).astype(np.float32)
     disk.psf[:] = bulge.psf[:] = np.arange(len(disk)) % 5
-    one = np.stack(gpu_composite(gpu_renderer, disk, bulge, fused=True))
-    two = np.stack(gpu_composite(gpu_renderer, disk, bulge, fused=False))
     tot = (disk.flux + bulge.flux).astype(np.float64)
-    d = np.abs(one - two).reshape(len(disk), -1).max(axis=1)
-    assert np.all(d <= 0.25 * PIX_TOL * tot), float(np.max(d / tot))
+    for shift in ("phase", "lanczos"):
+        one = np.stack(gpu_composite(gpu_renderer, disk, bulge, shift, fused=True))
+        two = np.stack(gpu_composite(gpu_renderer, disk, bulge, shift, fused=False))
+        d = np.abs(one - two).reshape(len(disk), -1).max(axis=1)
+        assert np.all(d <= 0.25 * PIX_TOL * tot), (shift, float(np.max(d / tot)))
 
 
 def test_one_pass_checks(gpu_renderer, tables):
@@ -98,9 +99,12 @@ def test_one_pass_checks(gpu_renderer, tables):
     keep = [i for i in range(len(disk)) if i not in (3, 5, 7)]
     check([got[i] for i in keep], disk.subset(keep), bulge.subset(keep), gpu_renderer.psfs, tables)
     short = capi.make_batch(len(disk) - 1, bb.ptrs(), 0)
+    first = capi.make_batch(bd.count, bd.ptrs(), bd.size_mask())
     with pytest.raises(capi.MogError):
-        capi.mog_render_composite(gpu_renderer.ctx, capi.make_batch(bd.count, bd.ptrs(), bd.size_mask()), short,
-                                  out.data_ptr(), 0)
+        capi.mog_render_composite(gpu_renderer.ctx, first, short, out.data_ptr(), 0)
+    with pytest.raises(capi.MogError):                      # unknown flags
+        capi.mog_render_composite(gpu_renderer.ctx, first, capi.make_batch(bb.count, bb.ptrs(), 0), out.data_ptr(),
+                                  0, capi.MOG_RENDER_ADD)
 
 
 def test_one_pass_rejects_eigen_psf_galaxies(tables, psf0):
@@ -126,8 +130,18 @@ def test_one_pass_rejects_eigen_psf_galaxies(tables, psf0):
         r.close()
 
 
-def test_composite_lanczos(gpu_renderer, tables):
+@pytest.mark.parametrize("fused", [True, False])
+def test_composite_lanczos(gpu_renderer, tables, fused):
     disk, bulge = composite_galaxies(80, seed=92)
+    check(gpu_composite(gpu_renderer, disk, bulge, "lanczos", fused), disk, bulge, gpu_renderer.psfs, tables,
+          "lanczos")
+
+
+@pytest.mark.parametrize("size", [32, 64, 128, 256])
+def test_composite_lanczos_each_size(gpu_renderer, tables, size):
+    disk, bulge = composite_galaxies(10, seed=120 + size, sizes=(size,))
+    disk.size[:] = bulge.size[:] = size
+    disk.x[:] = bulge.x[:] = np.linspace(-2.6, 3.4, 10).astype(np.float32)   # integer parts and fractions
     check(gpu_composite(gpu_renderer, disk, bulge, "lanczos"), disk, bulge, gpu_renderer.psfs, tables, "lanczos")
 
 
