@@ -299,7 +299,7 @@ mog_status mog_render_batch_host(mog_ctx* ctx, const mog_batch* batch, float* ou
  * per galaxy of the batch.
  * Asynchronous on `stream` once the plan exists (creating it synchronises).
  * Errors: MOG_ERR_ARG for a size_mask that is not one side, a misaligned
- * out or more than 2^31-1 spectrum elements; MOG_ERR_STATE when cuFFT cannot
+ * out or more than 2^31-1 pixels (count N^2); MOG_ERR_STATE when cuFFT cannot
  * be opened; MOG_ERR_CUDA when cuFFT fails.
  */
 mog_status mog_render_batch_cufft(mog_ctx* ctx, const mog_batch* batch, float* out, void* stream);

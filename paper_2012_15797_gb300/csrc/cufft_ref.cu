@@ -254,8 +254,8 @@ mog_status render_cufft(mog_ctx* ctx, const RenderParams& p, int64_t count, int 
   CufftApi& api = cufft_api();
   if (!api.lib) return fail(ctx, MOG_ERR_STATE, "the cuFFT library could not be opened");
   const int h = n / 2 + 1;
-  if ((int64_t)n * h * count > INT32_MAX)
-    return fail(ctx, MOG_ERR_ARG, "at most 2^31-1 spectrum elements per comparator call");
+  if ((int64_t)n * n * count > INT32_MAX)   // the plan's sizes are 32-bit (the images are the larger side)
+    return fail(ctx, MOG_ERR_ARG, "at most 2^31-1 pixels per comparator call");
   auto& st = ctx->cufft;
   const size_t spec_elems = (size_t)count * n * h, img_elems = (size_t)count * n * n;
   if (spec_elems > st.spec_cap) {
