@@ -33,7 +33,9 @@ namespace mog {
 // instead of being staged, and the row transforms use one work row per
 // group), so two CTAs share an SM and one computes while the other waits at a
 // CTA barrier.
-template <int N, int CPG = 1>
+// WN: the variant with the Sersic-index gradient (one more mixture sum per
+// bin of the nu = 1/2 column, one more partial sum per warp).
+template <int N, int CPG = 1, bool WN = false>
 struct BwdCfg {
   static constexpr int H = N / 2 + 1;
   static constexpr int TPF = N / 8;
@@ -81,25 +83,34 @@ struct BwdCfg {
   static constexpr size_t off_wb = off_wa + sizeof(float2) * WA_ELEMS;
   static constexpr size_t off_g = ALIAS_G ? off_wb : (off_wb + sizeof(float2) * W_ELEMS + 15) & ~size_t(15);
   static constexpr size_t off_tw = (ALIAS_G || !G_SMEM) ? off_wb + sizeof(float2) * W_ELEMS : off_g + sizeof(float) * N * GS;
-  static constexpr size_t off_px = off_tw + sizeof(float2) * (TW1 + TW2);
-  static constexpr size_t off_py = off_px + sizeof(float2) * H;
+  // (the shift phase along nu is computed where it is used, one value per
+  // thread and column: no table)
+  static constexpr int NYS = WN ? 4 : 3;   // nu = 1/2 column sums per bin: S, Sq, Sn (and Sd)
+  static constexpr int RED = WN ? 8 : 6;   // partial sums per warp
+  static constexpr size_t off_py = off_tw + sizeof(float2) * (TW1 + TW2);
   static constexpr size_t off_nb = off_py + sizeof(float2) * N;       // nu = 1/2 column: P phase
-  static constexpr size_t off_ns = off_nb + sizeof(float2) * N;       // and (S, Sq, Sn)
-  static constexpr size_t off_rec = (off_ns + sizeof(float) * 4 * N + 15) & ~size_t(15);
+  static constexpr size_t off_ns = off_nb + sizeof(float2) * N;       // and the mixture sums
+  static constexpr size_t off_rec = (off_ns + sizeof(float) * NYS * N + 15) & ~size_t(15);
   static constexpr size_t off_terms = off_rec + 2 * sizeof(AdjRecord);
   static constexpr size_t off_red = off_terms + sizeof(AdjTerms);
-  static constexpr size_t off_bar = (off_red + sizeof(float) * 8 * WARPS + 15) & ~size_t(15);
+  static constexpr size_t off_bar = (off_red + sizeof(float) * RED * WARPS + 15) & ~size_t(15);
   static constexpr size_t SMEM = off_bar + 3 * sizeof(uint64_t);
   static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB a CTA can have");
 };
+
+// 64 x 64: four CTAs and their static shared memory (about 0.5 KB each) fit
+// a 196 KB shared-memory carve-out, which leaves the L1 cache 60 KB for the
+// PSF spectrum (read from L2 through L1) and register spills; at 228 KB it
+// would have 28 KB (measured L1 hit rate of global loads: 56%).
+static_assert(4 * (BwdCfg<64>::SMEM + 512 + 1024) <= 196 * 1024, "64 x 64 adjoint: 196 KB carve-out");
 
 // WN: also d L / d(Sersic n), a seventh gradient per galaxy.  EIG: some PSF
 // of the context is an eigen-PSF (its spectrum at the galaxy's position is
 // combined from the component spectra bin by bin where a bin is read).
 template <int N, bool WN, bool EIG, int CPG = 1>
-__global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_BLOCKS)
+__global__ void __launch_bounds__(BwdCfg<N, CPG, WN>::THREADS, BwdCfg<N, CPG, WN>::MIN_BLOCKS)
     render_bwd_kernel(RenderParams p, const float* __restrict__ grad_out, float* __restrict__ grad_params) {
-  using C = BwdCfg<N, CPG>;
+  using C = BwdCfg<N, CPG, WN>;
   constexpr int TPF = C::TPF, WS = C::WS, LS = C::LS;
   constexpr int B = bucket_of(N);
   constexpr float INV_N = 1.0f / N;
@@ -111,10 +122,9 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
   float* gbuf = reinterpret_cast<float*>(smem + C::off_g);
   float2* tw1 = reinterpret_cast<float2*>(smem + C::off_tw);
   float2* tw2 = tw1 + C::TW1;
-  float2* px = reinterpret_cast<float2*>(smem + C::off_px);
   float2* py = reinterpret_cast<float2*>(smem + C::off_py);
   float2* nyb = reinterpret_cast<float2*>(smem + C::off_nb);
-  float* nys = reinterpret_cast<float*>(smem + C::off_ns);   // [l][4]: S, Sq, Sn
+  float* nys = reinterpret_cast<float*>(smem + C::off_ns);   // [l][NYS]: S, Sq, Sn (, Sd)
   AdjRecord* rec = reinterpret_cast<AdjRecord*>(smem + C::off_rec);
   AdjTerms& at = *reinterpret_cast<AdjTerms*>(smem + C::off_terms);
   float* red = reinterpret_cast<float*>(smem + C::off_red);
@@ -228,19 +238,16 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
       const float gx = r.x, gy = r.y;
       const int kp = REC_SYNC ? s_kpsf : psg.k;
       const int nrt = r.nrc * kp, nr2 = real_terms_padded(nrt);
-      const int ntask = C::H + 2 * N + nr2 + r.nf;
+      const int ntask = 2 * N + nr2 + r.nf;
       for (int i = tid; i < ntask; i += C::THREADS) {
         float sn, cs;
-        if (i < C::H) {
-          sincospif(-2.0f * gx * (float)i * INV_N, &sn, &cs);
-          px[i] = make_float2(cs, sn);
-        } else if (i < C::H + N) {
-          const int l = i - C::H;
+        if (i < N) {
+          const int l = i;
           sincospif(-2.0f * gy * (float)(l < N / 2 ? l : l - N) * INV_N, &sn, &cs);
           py[l] = make_float2(cs, sn);
-        } else if (i < C::H + 2 * N) {
-          // the nu = 1/2 column: P phase and the three mixture sums
-          const int l = i - C::H - N;
+        } else if (i < 2 * N) {
+          // the nu = 1/2 column: P phase and the mixture sums
+          const int l = i - N;
           const float om = (float)(l < N / 2 ? l : l - N) * INV_N;
           const float q = fmaf(om, fmaf(r.s22, om, r.s12), 0.25f * r.s11);
           float s = 0.0f, sq = 0.0f, sn2 = 0.0f, sd = 0.0f;
@@ -257,12 +264,12 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
           const float2 pn = k_eig > 0 ? eigen_bin(psf_hat, C::PSF_ELEMS, k_eig, eig_m, (N / 2) * LS + l)
                                       : __ldg(&psf_hat[(N / 2) * LS + l]);
           nyb[l] = cmul(pn, cmul(make_float2(cs, sn), make_float2(cy, sy)));
-          nys[4 * l + 0] = s;
-          nys[4 * l + 1] = sq;
-          nys[4 * l + 2] = sn2;
-          nys[4 * l + 3] = sd;
+          nys[C::NYS * l + 0] = s;
+          nys[C::NYS * l + 1] = sq;
+          nys[C::NYS * l + 2] = sn2;
+          if constexpr (WN) nys[C::NYS * l + 3] = sd;
         } else {
-          const int t = i - C::H - 2 * N;
+          const int t = i - 2 * N;
           if (t < nrt) {
             adj_real_term(r, mog, kp, N, t, &at, eig_w);
           } else if (t < nr2) {
@@ -363,7 +370,8 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
         const float nu = col * INV_N;
         const float a0 = s11 * nu * nu, a1 = s12x2 * nu;
         const float ck = col == 0 ? 1.0f : 2.0f;
-        const float2 pxf = px[col];
+        float2 pxf;   // e^{-2 pi i x nu}
+        sincospif(-2.0f * r.x * (float)col * INV_N, &pxf.y, &pxf.x);
         // mixture sums at the thread's bins b = q R + m, components outer and
         // bins (2k, 2k+1) in packed f32x2, BH bins per sweep over the
         // components: N = 64 takes two sweeps of 4 (its register budget at
@@ -414,8 +422,8 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
             if constexpr (WN) acc[6] = fmaf(z.x, sd, acc[6]);
             if (col == 0) {
               const float2 zn = cmulc(nyb[l], gn);
-              contract_bin(zn, 0.5f, om, nys[4 * l], nys[4 * l + 1], nys[4 * l + 2], acc);
-              if constexpr (WN) acc[6] = fmaf(zn.x, nys[4 * l + 3], acc[6]);
+              contract_bin(zn, 0.5f, om, nys[C::NYS * l], nys[C::NYS * l + 1], nys[C::NYS * l + 2], acc);
+              if constexpr (WN) acc[6] = fmaf(zn.x, nys[C::NYS * l + 3], acc[6]);
             }
           }
         }
@@ -430,13 +438,13 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
       float x = acc[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) red[warp * 8 + k] = x;
+      if (lane == 0) red[warp * C::RED + k] = x;
     }
     __syncthreads();  // S4
     if (tid == 0) {
       float t[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       for (int w = 0; w < C::WARPS; ++w)
-        for (int k = 0; k < NACC; ++k) t[k] += red[w * 8 + k];
+        for (int k = 0; k < NACC; ++k) t[k] += red[w * C::RED + k];
       float* out = grad_params + r.gal * NACC;
       if constexpr (WN) out[6] = t[6];
       out[0] = t[0] / r.flux;
@@ -453,12 +461,12 @@ __global__ void __launch_bounds__(BwdCfg<N, CPG>::THREADS, BwdCfg<N, CPG>::MIN_B
 template <int N>
 constexpr int bwd_cpg() { return N == 128 ? 2 : 1; }
 
-static_assert(2 * (BwdCfg<128, 2>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 adjoint CTAs share an SM");
+static_assert(2 * (BwdCfg<128, 2, true>::SMEM + 1024) <= 228 * 1024, "two 128 x 128 adjoint CTAs share an SM");
 
 template <int N, bool WN = false, bool EIG = false>
 static int bwd_occupancy() {
   constexpr int CPG = bwd_cpg<N>();
-  using C = BwdCfg<N, CPG>;
+  using C = BwdCfg<N, CPG, WN>;
   return kernel_occupancy(reinterpret_cast<const void*>(render_bwd_kernel<N, WN, EIG, CPG>), C::THREADS, C::SMEM);
 }
 
@@ -466,7 +474,7 @@ template <int N, bool WN, bool EIG>
 static cudaError_t launch_bwd_mode(const RenderParams& p, const float* grad_out, float* grad_params, int num_sms,
                                    int ctas_per_sm, cudaStream_t s) {
   constexpr int CPG = bwd_cpg<N>();
-  using C = BwdCfg<N, CPG>;
+  using C = BwdCfg<N, CPG, WN>;
   const int occ = bwd_occupancy<N, WN, EIG>();
   if (occ < 0) return cudaErrorInvalidConfiguration;
   const int ctas = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
