@@ -39,6 +39,9 @@ def test_null_arguments_rejected_without_device():
     assert lib.mog_destroy_context(None) == capi.MOG_ERR_ARG
     assert lib.mog_render_batch(None, None, None, None) == capi.MOG_ERR_ARG
     assert lib.mog_sync_status(None, None) == capi.MOG_ERR_ARG
+    assert lib.mog_render_composite(None, None, None, None, None, 0) == capi.MOG_ERR_ARG
+    assert lib.mog_render_batch_cufft(None, None, None, None) == capi.MOG_ERR_ARG
+    assert lib.mog_render_chi2(None, None, None, None, None, None, None, None) == capi.MOG_ERR_ARG
     assert lib.mog_last_error(None) == b"null context"
 
 
