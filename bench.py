@@ -850,6 +850,16 @@ def extra_cufft(tables, psf, device, steps, pk, cases=((64, 100_000), (256, 5_00
     return res
 
 
+def cufft_or_reason(tables, psf, device, steps, pk):
+    """extra_cufft, or why it could not run (the comparator needs the cuFFT
+    library at run time; the rest of the line does not)."""
+    from paper_2012_15797_gb300 import capi
+    try:
+        return extra_cufft(tables, psf, device, steps, pk)
+    except capi.MogError as e:
+        return {"unavailable": str(e)}
+
+
 def extra_per_galaxy(tables, psf, device, n=2000):
     """The plain form: the same math with one library call (planner, record,
     render launches) per galaxy."""
@@ -1201,7 +1211,7 @@ def run_ours(args):
                  "psf_fit": extra_psf_fit(tables, local),
                  "psf_create": extra_psf_create(tables, local),
                  "one_launch_per_galaxy": extra_per_galaxy(tables, psf, local),
-                 "cufft_comparator": extra_cufft(tables, psf, local, args.extra_steps, pk)}
+                 "cufft_comparator": cufft_or_reason(tables, psf, local, args.extra_steps, pk)}
         bound = 200_000 / ((extra["mixed_sizes"]["ms_graph"] + extra["sersic_gradient"]["ms_grad6"]) / 1e3)
         extra["serving"] = extra_serving(tables, local, kernel_bound=bound)
 
