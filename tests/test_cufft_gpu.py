@@ -104,3 +104,34 @@ def test_arguments_and_status(gpu_renderer):
         capi.mog_render_batch_cufft(gpu_renderer.ctx, bb, out.data_ptr() + 4, 0)
     empty = to_device(fixed_galaxies_64(0))
     gpu_renderer.render_cufft(empty, torch.empty(0, device="cuda"))
+
+
+def test_eigen_psf_galaxies_skipped_and_plan_rebuilt(tables, psf0):
+    """Galaxies on an eigen-PSF are skipped with MOG_ERR_DEVICE (the others
+    render); calls of different counts and sides re-plan and stay correct."""
+    from paper_2012_15797_gb300 import capi
+    from paper_2012_15797_gb300.renderer import Renderer, patches, to_device
+    from workloads import eigen_positions, eigen_psf
+    r = Renderer(tables, [psf0, eigen_psf()])
+    try:
+        gals = fixed_galaxies_64(12, seed=98)
+        gals.psf[[3, 8]] = 1
+        b = to_device(gals, positions=eigen_positions(len(gals)))
+        out = torch.full((b.total,), -4.0, dtype=torch.float32, device="cuda")
+        r.render_cufft(b, out)
+        with pytest.raises(capi.MogError):
+            r.sync_status()
+        got = [p.double().cpu().numpy() for p in patches(out, b)]
+        keep = [i for i in range(len(gals)) if i not in (3, 8)]
+        assert np.all(got[3] == -4.0) and np.all(got[8] == -4.0)
+        check_parity([got[i] for i in keep], oracle_patches(gals, [psf0], tables, keep), gals, keep)
+        for n, count in ((32, 7), (64, 19), (32, 7)):
+            g2 = fixed_galaxies_64(count, seed=99 + n + count, size=n)
+            one, _, b2 = _cufft_patches(r, g2)
+            fused = r.render(b2)
+            r.sync_status()
+            d = max(float(np.max(np.abs(one[i] - p.double().cpu().numpy()))) / float(g2.flux[i])
+                    for i, p in enumerate(patches(fused, b2)))
+            assert d <= 0.25 * PIX_TOL, d
+    finally:
+        r.close()
